@@ -1,0 +1,196 @@
+/*
+ * t2s2.h - C ABI of the GB300 (sm_103a) T^2S^2 hot path.
+ *
+ * T^2S^2 (tensor-train superconsistent spectral collocation, arXiv 2506.04732)
+ * solves the convection-diffusion problem of the paper's eq. pblm:time:A-C,
+ *
+ *     du/dt - eps Laplace(u) + beta . grad(u) = b  on [-1,1]^d,  u = g on the boundary,
+ *
+ * with a Lagrange basis on the n Gauss-Lobatto-Legendre (GLL) points of each
+ * dimension (Overview (i)), collocation on per-dimension superconsistent
+ * points (Overview (ii), Fig. 1, Fig. 3) and tensor-train (TT) storage of all
+ * grid functions and of the operator (Overview (iii), Methods).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - n[k] is the number of GLL nodes of dimension k (polynomial degree n[k]-1,
+ *   3 <= n[k] <= T2S2_MAX_N).  With zero Dirichlet data the unknowns are the
+ *   m[k] = n[k]-2 interior nodes, so every TT handled here has mode sizes m[k].
+ * - A TT is d cores; core k is a row-major array [r[k]][m[k]][r[k+1]] of
+ *   doubles (the paper's G_k(alpha, i, beta), eq. TT-format:elementwise), with
+ *   r[0] = r[d] = 1.  A TT with `loc == T2S2_DEVICE` holds device pointers of
+ *   the current CUDA device; `loc == T2S2_HOST` holds host pointers (the
+ *   library stages them through device memory; pinned memory is fastest).
+ * - The caller owns every TT buffer.  `cap[k]` is the capacity of core k in
+ *   doubles.  Entry points that write a TT set its ranks `r[]`; if a core
+ *   would exceed its capacity they fail with T2S2_ENOMEM and leave the
+ *   output unspecified.  Ranks are bounded by `rmax` where one is taken.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Entry points
+ *   that return host scalars (norms, residuals, ranks) synchronise with it.
+ * - Every entry point returns a status; nothing aborts the process.
+ * - An operator handle owns its device matrices and its workspace; calls that
+ *   share one handle must not run concurrently (they share the workspace).
+ */
+#ifndef T2S2_H
+#define T2S2_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define T2S2_MAX_D 16
+#define T2S2_MAX_N 128
+
+typedef enum {
+  T2S2_OK = 0,
+  T2S2_EINVAL = 1,     /* bad argument (sizes, NULL pointers, tolerances) */
+  T2S2_ENOMEM = 2,     /* device allocation failed, or a TT core exceeds its capacity */
+  T2S2_ECUDA = 3,      /* a CUDA call or kernel launch failed */
+  T2S2_ENOCONV = 4,    /* the solver hit its sweep cap; best iterate and residual written */
+  T2S2_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+  T2S2_ENOTIMPL = 6,   /* feature not provided (e.g. non-zero Dirichlet data) */
+  T2S2_ENODEV = 7      /* no usable sm_103 device */
+} t2s2_status;
+
+/* Arithmetic of the heavy kernels.  T2S2_FP64: everything in binary64.
+ * T2S2_FP32_REFINE: inner alternating solve in binary32 (SIMT) wrapped in an
+ * FP64 residual / iterative-refinement loop; QR/SVD of rounding, the residual
+ * norm and the 1D matrices stay FP64.  T2S2_TF32_REFINE / T2S2_BF16_REFINE:
+ * as FP32_REFINE with the core contractions on tcgen05 tensor cores. */
+typedef enum {
+  T2S2_FP64 = 0,
+  T2S2_FP32_REFINE = 1,
+  T2S2_TF32_REFINE = 2,
+  T2S2_BF16_REFINE = 3
+} t2s2_precision;
+
+typedef enum { T2S2_DEVICE = 0, T2S2_HOST = 1 } t2s2_location;
+
+/* The problem of eq. pblm:time:A with rho = 0: d, GLL nodes per dimension,
+ * convection field beta (d entries), diffusion eps > 0.  plain_sc = 1
+ * collocates at the GLL points themselves (the paper's Plain-SC baseline,
+ * Overview (i)); 0 uses the superconsistent points. */
+typedef struct {
+  int d;
+  const int* n;
+  const double* beta;
+  double eps;
+  int plain_sc;
+} t2s2_problem;
+
+typedef struct t2s2_op_s* t2s2_op;
+
+typedef struct {
+  int d;
+  const int* m;        /* mode sizes m[k] = n[k] - 2 (d entries) */
+  int* r;              /* ranks r[0..d], r[0] = r[d] = 1; read on input, written on output */
+  double** cores;      /* d core pointers, core k: [r[k]][m[k]][r[k+1]] row-major */
+  const size_t* cap;   /* d capacities in doubles */
+  int loc;             /* t2s2_location */
+} t2s2_tt;
+
+typedef struct {
+  double residual;     /* achieved ||b - A x||_F / ||b||_F on the collocation system */
+  int sweeps;          /* alternating sweeps (the paper's AMEn "swaps") performed */
+  int max_rank;        /* largest TT rank of the returned solution */
+  int refinements;     /* outer FP64 refinement steps (mixed precision only) */
+  long long local_iters; /* total Krylov iterations of the local solves */
+} t2s2_solve_info;
+
+/* Human-readable name of a status code; never NULL. */
+const char* t2s2_strerror(t2s2_status s);
+
+/* Number of usable devices (compute capability 10.3) or a negative status. */
+int t2s2_device_count(void);
+
+/*
+ * Build the d-dimensional collocation operator (Overview (ii)-(iii)).
+ * Per dimension, on the host in FP64: GLL nodes, superconsistent collocation
+ * points eta (roots in (-1,1) of eps P_N' - beta_k P_N, dropping the root
+ * nearest the outflow end when N of them fall inside, N = n-1; see the design doc
+ * for this reading of the paper), Lagrange matrices Rt = l_i(eta_j),
+ * D, D2 on the interior nodes, Lt = beta_k D - eps D2, the interpolation
+ * inverse and B_k = Rt^{-1} Lt.  The collocation operator is the rank-2
+ * TT-matrix (eq. tt-matrix-format)
+ *     A = sum_k Rt_1 x ... x Lt_k x ... x Rt_d,
+ * and the collocated time derivative has mass matrix M = Rt_1 x ... x Rt_d.
+ * Uploads the matrices to the current device and allocates the workspace.
+ * Errors: T2S2_EINVAL for d outside [1, T2S2_MAX_D], n outside [3, T2S2_MAX_N],
+ * eps <= 0, NULL pointers; T2S2_ENOMEM / T2S2_ECUDA for device failures.
+ */
+t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op* out);
+
+/* Free an operator and its workspace.  NULL is accepted. */
+t2s2_status t2s2_op_destroy(t2s2_op op);
+
+/* Copy dimension k's GLL nodes x (n values) and collocation points eta
+ * (n-2 values) into host arrays; either pointer may be NULL. */
+t2s2_status t2s2_op_nodes(t2s2_op op, int k, double* x, double* eta);
+
+/* Copy dimension k's interior matrices Rt and Lt ((n-2)^2 doubles each,
+ * row-major, row = collocation point, column = interior GLL node) to host
+ * arrays; either pointer may be NULL. */
+t2s2_status t2s2_op_matrices(t2s2_op op, int k, double* Rt, double* Lt);
+
+/*
+ * TT-matrix-by-TT product y = (c_mass M + c_op A) x (Methods: operations raise
+ * TT ranks; this one doubles them).  Output ranks: r_y[k] = 2 r_x[k] for
+ * 0 < k < d.  Core k of y is built from Rt_k X_k and Lt_k X_k (the mode-k
+ * contractions) in the block pattern of the rank-2 TT-matrix:
+ *     first [G_1 X, Rt_1 X], middle [[Rt X, 0], [G_k X, Rt X]], last [Rt X; G_d X],
+ * G_k = c_op Lt_k (+ c_mass Rt_1 for k = 1).  x and y must not alias.
+ * prec selects the contraction arithmetic (results always stored as FP64).
+ */
+t2s2_status t2s2_apply(t2s2_op op, const t2s2_tt* x, t2s2_tt* y, double c_mass,
+                       double c_op, t2s2_precision prec, void* stream);
+
+/*
+ * TT rounding rndg (Methods, "Tensor-train (TT) decomposition"): in place,
+ * right-to-left orthogonalisation, then left-to-right truncated SVDs with
+ * per-unfolding threshold tol ||x||_F / sqrt(d-1), then the cap rmax
+ * (rmax <= 0: no cap).  Guarantees ||x - rndg(x)||_F <= tol ||x||_F when the
+ * cap does not bind.  All arithmetic FP64.  Uses `op` for its workspace.
+ */
+t2s2_status t2s2_round(t2s2_op op, t2s2_tt* x, double tol, int rmax, void* stream);
+
+/* ||x||_F (accurate: orthogonalise and take the norm of the first core). */
+t2s2_status t2s2_norm(t2s2_op op, const t2s2_tt* x, double* out, void* stream);
+
+/* ||b - (c_mass M + c_op A) x||_F / ||b||_F, accurate difference norm, FP64. */
+t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double c_mass,
+                          double c_op, double* out, void* stream);
+
+/*
+ * Solve (c_mass M + c_op A) x = b in TT format with the alternating solver
+ * the paper uses (AMEn, Results "Superconsistent Stabilization", Fig. 6):
+ * sweeps over the cores with local solves, local SVD truncation at
+ * tol/sqrt(d), residual-based rank enrichment, until the true relative
+ * residual ||b - (c_mass M + c_op A) x||_F / ||b||_F <= tol or max_sweeps.
+ * b is the right-hand side sampled on the collocation grid; x holds the
+ * initial guess on input and the solution on output (ranks <= rmax + 4).
+ * Returns T2S2_ENOCONV (with x and info filled) if the sweep cap is hit.
+ * The plain solve is c_mass = 0, c_op = 1.
+ */
+t2s2_status t2s2_solve(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double c_mass, double c_op,
+                       double tol, int rmax, int max_sweeps, t2s2_precision prec,
+                       void* stream, t2s2_solve_info* info);
+
+/*
+ * One Crank-Nicolson step (eq. ttss-Crank-Nicolson) with the collocated time
+ * derivative (mass matrix M):  rhs = rndg((M - dt/2 A) u), then solve
+ * (M + dt/2 A) u+ = rhs from the initial guess u; u is overwritten by u+.
+ */
+t2s2_status t2s2_cn_step(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax,
+                         t2s2_precision prec, void* stream, t2s2_solve_info* info);
+
+/* One backward-Euler step (eq. ttss-backward-Euler): (M + dt A) u+ = M u. */
+t2s2_status t2s2_be_step(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax,
+                         t2s2_precision prec, void* stream, t2s2_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* T2S2_H */

@@ -1,0 +1,322 @@
+"""GB300 (sm_103a) hot path of T^2S^2 (arXiv 2506.04732): thin Python binding.
+
+Every function here marshals arguments and calls the C ABI declared in
+``include/t2s2.h`` (``libt2s2.so``, built in-tree by ``build.py``); all
+arithmetic of the path runs in that library's CUDA kernels.  PyTorch only
+provides device / pinned-host memory and the current CUDA stream.  There is
+no CPU fallback: if the library is missing, ``load()`` raises.
+
+Names follow the C entry points: ``t2s2_build_operator``, ``t2s2_apply``,
+``t2s2_round``, ``t2s2_solve``, ``t2s2_cn_step`` and helpers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REFINE",
+           "TF32_REFINE", "BF16_REFINE", "t2s2_build_operator", "t2s2_apply", "t2s2_round",
+           "t2s2_norm", "t2s2_residual", "t2s2_solve", "t2s2_cn_step", "t2s2_be_step",
+           "t2s2_device_count", "t2s2_strerror", "lib_path"]
+
+FP64, FP32_REFINE, TF32_REFINE, BF16_REFINE = 0, 1, 2, 3
+_DEVICE, _HOST = 0, 1
+MAX_D = 16
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_HERE, "libt2s2.so")
+_lib = None
+
+
+class T2S2Error(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {t2s2_strerror(status)} (status {status})")
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.POINTER(ctypes.c_int)),
+                ("beta", ctypes.POINTER(ctypes.c_double)), ("eps", ctypes.c_double),
+                ("plain_sc", ctypes.c_int)]
+
+
+class _TT(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("m", ctypes.POINTER(ctypes.c_int)),
+                ("r", ctypes.POINTER(ctypes.c_int)),
+                ("cores", ctypes.POINTER(ctypes.c_void_p)),
+                ("cap", ctypes.POINTER(ctypes.c_size_t)), ("loc", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("residual", ctypes.c_double), ("sweeps", ctypes.c_int),
+                ("max_rank", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("local_iters", ctypes.c_longlong)]
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    residual: float
+    sweeps: int
+    max_rank: int
+    refinements: int
+    local_iters: int
+
+
+_SIGS = {
+    "t2s2_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "t2s2_device_count": (ctypes.c_int, []),
+    "t2s2_build_operator": (ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "t2s2_op_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "t2s2_op_nodes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
+    "t2s2_op_matrices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "t2s2_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.POINTER(_TT),
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    "t2s2_round": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_double,
+                                  ctypes.c_int, ctypes.c_void_p]),
+    "t2s2_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "t2s2_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.POINTER(_TT),
+                                     ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "t2s2_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.POINTER(_TT),
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.POINTER(_Info)]),
+    "t2s2_cn_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.POINTER(_Info)]),
+    "t2s2_be_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.POINTER(_Info)]),
+}
+
+
+def load():
+    """Load libt2s2.so (built in-tree).  Raises if it is missing: no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(lib_path):
+        raise RuntimeError(f"{lib_path} is missing; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(lib_path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def t2s2_strerror(status: int) -> str:
+    try:
+        return load().t2s2_strerror(int(status)).decode()
+    except Exception:  # library not loadable: still give a message
+        return f"status {status}"
+
+
+def t2s2_device_count() -> int:
+    return int(load().t2s2_device_count())
+
+
+def _check(status: int, what: str, ok=(0,)):
+    if status not in ok:
+        raise T2S2Error(status, what)
+    return status
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Operator:
+    """Handle on the library's operator (t2s2_build_operator / t2s2_op_destroy)."""
+
+    def __init__(self, handle, d, n, beta, eps, plain_sc):
+        self._h = handle
+        self.d, self.n, self.beta, self.eps, self.plain_sc = d, tuple(n), tuple(beta), eps, plain_sc
+        self.m = tuple(v - 2 for v in self.n)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("operator destroyed")
+        return self._h
+
+    def nodes(self, k):
+        x = np.zeros(self.n[k])
+        eta = np.zeros(self.m[k])
+        _check(load().t2s2_op_nodes(self.handle, k, x.ctypes.data, eta.ctypes.data), "t2s2_op_nodes")
+        return x, eta
+
+    def matrices(self, k):
+        m = self.m[k]
+        Rt = np.zeros((m, m))
+        Lt = np.zeros((m, m))
+        _check(load().t2s2_op_matrices(self.handle, k, Rt.ctypes.data, Lt.ctypes.data),
+               "t2s2_op_matrices")
+        return Rt, Lt
+
+    def destroy(self):
+        if self._h is not None:
+            load().t2s2_op_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def t2s2_build_operator(d, n, beta, eps, plain_sc=False, stream=None) -> Operator:
+    lib = load()
+    n = [int(v) for v in (n if np.ndim(n) else [n] * d)]
+    beta = [float(v) for v in beta]
+    na = (ctypes.c_int * d)(*n)
+    ba = (ctypes.c_double * d)(*beta)
+    prob = _Problem(d, na, ba, float(eps), int(bool(plain_sc)))
+    h = ctypes.c_void_p()
+    _check(lib.t2s2_build_operator(ctypes.byref(prob), _stream_handle(stream), ctypes.byref(h)),
+           "t2s2_build_operator")
+    return Operator(h, d, n, beta, float(eps), bool(plain_sc))
+
+
+class TT:
+    """A tensor train whose cores live in torch tensors (device or pinned host).
+
+    Core k holds r[k] * m[k] * r[k+1] doubles ([r_k][m_k][r_{k+1}] row-major)
+    inside a buffer of capacity ``cap[k]``.
+    """
+
+    def __init__(self, m, r, buffers, loc):
+        self.d = len(m)
+        self.m = [int(v) for v in m]
+        self.r = [int(v) for v in r]
+        self.buffers = buffers
+        self.loc = loc
+
+    @classmethod
+    def empty(cls, m, rcap, device="cuda", ranks=None):
+        import torch
+        d = len(m)
+        bufs = []
+        for k in range(d):
+            a = 1 if k == 0 else rcap
+            b = 1 if k == d - 1 else rcap
+            if device == "cpu":
+                bufs.append(torch.zeros(a * m[k] * b, dtype=torch.float64).pin_memory())
+            else:
+                bufs.append(torch.zeros(a * m[k] * b, dtype=torch.float64, device=device))
+        r = ranks if ranks is not None else [1] * (d + 1)
+        return cls(m, r, bufs, _HOST if device == "cpu" else _DEVICE)
+
+    @classmethod
+    def from_cores(cls, cores, rcap=None, device="cuda"):
+        import torch
+        m = [c.shape[1] for c in cores]
+        r = [cores[0].shape[0]] + [c.shape[2] for c in cores]
+        rcap = max(r) if rcap is None else max(rcap, max(r))
+        t = cls.empty(m, rcap, device=device, ranks=r)
+        for k, c in enumerate(cores):
+            flat = torch.from_numpy(np.ascontiguousarray(c, dtype=np.float64).ravel())
+            t.buffers[k][: flat.numel()].copy_(flat)
+        return t
+
+    def cores(self):
+        out = []
+        for k in range(self.d):
+            n = self.r[k] * self.m[k] * self.r[k + 1]
+            out.append(self.buffers[k][:n].detach().cpu().numpy().reshape(self.r[k], self.m[k],
+                                                                            self.r[k + 1]).copy())
+        return out
+
+    def _struct(self):
+        d = self.d
+        self._m_arr = (ctypes.c_int * d)(*self.m)
+        self._r_arr = (ctypes.c_int * (d + 1))(*self.r)
+        self._p_arr = (ctypes.c_void_p * d)(*[b.data_ptr() for b in self.buffers])
+        self._c_arr = (ctypes.c_size_t * d)(*[b.numel() for b in self.buffers])
+        self._s = _TT(d, self._m_arr, self._r_arr, self._p_arr, self._c_arr, self.loc)
+        return self._s
+
+    def _sync_ranks(self):
+        self.r = [int(self._r_arr[k]) for k in range(self.d + 1)]
+
+
+def t2s2_apply(op: Operator, x: TT, y: TT, c_mass=0.0, c_op=1.0, prec=FP64, stream=None):
+    sx, sy = x._struct(), y._struct()
+    _check(load().t2s2_apply(op.handle, ctypes.byref(sx), ctypes.byref(sy), float(c_mass),
+                             float(c_op), int(prec), _stream_handle(stream)), "t2s2_apply")
+    y._sync_ranks()
+    return y
+
+
+def t2s2_round(op: Operator, x: TT, tol, rmax=0, stream=None):
+    sx = x._struct()
+    _check(load().t2s2_round(op.handle, ctypes.byref(sx), float(tol), int(rmax),
+                             _stream_handle(stream)), "t2s2_round")
+    x._sync_ranks()
+    return x
+
+
+def t2s2_norm(op: Operator, x: TT, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(load().t2s2_norm(op.handle, ctypes.byref(x._struct()), ctypes.byref(out),
+                            _stream_handle(stream)), "t2s2_norm")
+    return out.value
+
+
+def t2s2_residual(op: Operator, b: TT, x: TT, c_mass=0.0, c_op=1.0, stream=None) -> float:
+    out = ctypes.c_double()
+    sb, sx = b._struct(), x._struct()
+    _check(load().t2s2_residual(op.handle, ctypes.byref(sb), ctypes.byref(sx), float(c_mass),
+                                float(c_op), ctypes.byref(out), _stream_handle(stream)),
+           "t2s2_residual")
+    return out.value
+
+
+def _info(status, info):
+    return SolveInfo(status, info.residual, info.sweeps, info.max_rank, info.refinements,
+                     info.local_iters)
+
+
+def t2s2_solve(op: Operator, b: TT, x: TT, tol, rmax, max_sweeps=50, prec=FP64, c_mass=0.0,
+               c_op=1.0, stream=None, allow_noconv=False) -> SolveInfo:
+    info = _Info()
+    sb, sx = b._struct(), x._struct()
+    st = load().t2s2_solve(op.handle, ctypes.byref(sb), ctypes.byref(sx), float(c_mass),
+                           float(c_op), float(tol), int(rmax), int(max_sweeps), int(prec),
+                           _stream_handle(stream), ctypes.byref(info))
+    _check(st, "t2s2_solve", ok=(0, 4) if allow_noconv else (0,))
+    x._sync_ranks()
+    return _info(st, info)
+
+
+def t2s2_cn_step(op: Operator, u: TT, dt, tol, rmax, prec=FP64, stream=None) -> SolveInfo:
+    info = _Info()
+    su = u._struct()
+    st = load().t2s2_cn_step(op.handle, ctypes.byref(su), float(dt), float(tol), int(rmax),
+                             int(prec), _stream_handle(stream), ctypes.byref(info))
+    _check(st, "t2s2_cn_step")
+    u._sync_ranks()
+    return _info(st, info)
+
+
+def t2s2_be_step(op: Operator, u: TT, dt, tol, rmax, prec=FP64, stream=None) -> SolveInfo:
+    info = _Info()
+    su = u._struct()
+    st = load().t2s2_be_step(op.handle, ctypes.byref(su), float(dt), float(tol), int(rmax),
+                             int(prec), _stream_handle(stream), ctypes.byref(info))
+    _check(st, "t2s2_be_step")
+    u._sync_ranks()
+    return _info(st, info)

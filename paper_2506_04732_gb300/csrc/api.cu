@@ -1,0 +1,352 @@
+// C ABI entry points (include/t2s2.h): operator construction, TT apply,
+// rounding, norms and residuals.  The solver entry points live in solve.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "api_internal.h"
+
+namespace t2s2 {
+
+static thread_local char g_last_error[256] = "";
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s at %s:%d: %s", cudaGetErrorString(e), file, line,
+           what);
+}
+
+t2s2_status ensure_arena(t2s2_op op, size_t bytes) {
+  if (op->arena.size >= bytes) {
+    op->arena.top = 0;
+    return T2S2_OK;
+  }
+  if (op->arena.base) {
+    cudaFree(op->arena.base);
+    op->arena.base = nullptr;
+    op->arena.size = 0;
+  }
+  size_t want = std::max(bytes, (size_t)64 << 20);
+  void* p = nullptr;
+  T2S2_CUDA_TRY(cudaMalloc(&p, want));
+  op->arena.base = static_cast<char*>(p);
+  op->arena.size = want;
+  op->arena.top = 0;
+  return T2S2_OK;
+}
+
+Ctx make_ctx(t2s2_op op, void* stream) {
+  Ctx cx;
+  cx.st = static_cast<cudaStream_t>(stream);
+  cx.ar = &op->arena;
+  cx.hbuf = op->hbuf;
+  cx.dstat = op->dstat;
+  return cx;
+}
+
+size_t tt_bytes(const t2s2_tt* t) {
+  size_t s = 0;
+  for (int k = 0; k < t->d; ++k) s += t->cap[k];
+  return s * sizeof(double);
+}
+
+t2s2_status check_tt(t2s2_op op, const t2s2_tt* t) {
+  if (!t || !t->r || !t->cores || !t->cap || !t->m) return T2S2_EINVAL;
+  if (t->d != op->d) return T2S2_EINVAL;
+  if (t->loc != T2S2_DEVICE && t->loc != T2S2_HOST) return T2S2_EINVAL;
+  if (t->r[0] != 1 || t->r[t->d] != 1) return T2S2_EINVAL;
+  for (int k = 0; k < t->d; ++k) {
+    if (t->m[k] != op->m[k]) return T2S2_EINVAL;
+    if (t->r[k + 1] < 1 || !t->cores[k]) return T2S2_EINVAL;
+    if ((size_t)t->r[k] * t->m[k] * t->r[k + 1] > t->cap[k]) return T2S2_ENOMEM;
+  }
+  return T2S2_OK;
+}
+
+// Bind a user TT to a DevTT; host TTs get device staging in the arena and,
+// if `upload`, their contents copied in.
+t2s2_status bind_tt(Ctx& cx, const t2s2_tt* t, DevTT& dv, bool upload) {
+  dv.d = t->d;
+  for (int k = 0; k <= t->d; ++k) dv.r[k] = t->r[k];
+  for (int k = 0; k < t->d; ++k) {
+    dv.m[k] = t->m[k];
+    dv.cap[k] = t->cap[k];
+    if (t->loc == T2S2_DEVICE) {
+      dv.c[k] = t->cores[k];
+    } else {
+      dv.c[k] = aget<double>(cx, t->cap[k]);
+      if (!dv.c[k]) return T2S2_ENOMEM;
+      if (upload)
+        T2S2_CUDA_TRY(cudaMemcpyAsync(dv.c[k], t->cores[k], sizeof(double) * dv.core_elems(k),
+                                      cudaMemcpyHostToDevice, cx.st));
+    }
+  }
+  return T2S2_OK;
+}
+
+// Write ranks (and, for host TTs, contents) of dv back to the user TT.
+t2s2_status unbind_tt(Ctx& cx, const DevTT& dv, t2s2_tt* t) {
+  for (int k = 0; k < dv.d; ++k)
+    if (dv.core_elems(k) > t->cap[k]) return T2S2_ENOMEM;
+  for (int k = 0; k <= dv.d; ++k) t->r[k] = dv.r[k];
+  if (t->loc == T2S2_HOST) {
+    for (int k = 0; k < dv.d; ++k)
+      T2S2_CUDA_TRY(cudaMemcpyAsync(t->cores[k], dv.c[k], sizeof(double) * dv.core_elems(k),
+                                    cudaMemcpyDeviceToHost, cx.st));
+  } else {
+    for (int k = 0; k < dv.d; ++k)
+      if (dv.c[k] != t->cores[k])
+        T2S2_CUDA_TRY(cudaMemcpyAsync(t->cores[k], dv.c[k], sizeof(double) * dv.core_elems(k),
+                                      cudaMemcpyDeviceToDevice, cx.st));
+  }
+  T2S2_CUDA_TRY(cudaStreamSynchronize(cx.st));
+  return T2S2_OK;
+}
+
+// y = (c_mass M + c_op A) x  (S = Rt, L = Lt) or the transformed operator
+// (S = I, L = B) when `transformed`.
+t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass, double c_op,
+                     bool transformed) {
+  const int d = op->d;
+  y.d = d;
+  y.r[0] = 1;
+  y.r[d] = 1;
+  for (int k = 1; k < d; ++k) y.r[k] = 2 * x.r[k];
+  for (int k = 0; k < d; ++k) {
+    y.m[k] = x.m[k];
+    if (y.core_elems(k) > y.cap[k]) return T2S2_ENOMEM;
+  }
+  ApplyBatch b;
+  b.ncores = d;
+  for (int k = 0; k < d; ++k) {
+    ApplyCore& c = b.c[k];
+    c.S = transformed ? op->dI[k] : op->dRt[k];
+    c.L = transformed ? op->dB[k] : op->dLt[k];
+    c.X = x.c[k];
+    c.Y = y.c[k];
+    c.ra = x.r[k];
+    c.m = x.m[k];
+    c.rb = x.r[k + 1];
+    c.kind = (d == 1) ? kApplySingle : (k == 0 ? kApplyFirst : (k == d - 1 ? kApplyLast : kApplyMiddle));
+    c.g_op = c_op;
+    c.g_mass = (k == 0) ? c_mass : 0.0;
+  }
+  return apply_fp64(b, cx.st);
+}
+
+size_t max_core(const t2s2_tt* t) {
+  size_t s = 0;
+  for (int k = 0; k < t->d; ++k) s = std::max(s, t->cap[k]);
+  return s;
+}
+
+t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
+                          double c_op, bool transformed, double* out, double* bnorm_io) {
+  size_t mark = cx.ar->mark();
+  DevTT y;
+  int r2[T2S2_MAX_D + 1];
+  for (int k = 0; k <= op->d; ++k) r2[k] = (k == 0 || k == op->d) ? 1 : 2 * x.r[k];
+  T2S2_TRY(tt_alloc(cx, y, op->d, x.m, r2, 0));
+  T2S2_TRY(apply_op(op, cx, x, y, c_mass, c_op, transformed));
+  DevTT z;
+  T2S2_TRY(tt_axpby(cx, 1.0, b, -1.0, y, z));
+  T2S2_TRY(tt_orth_right(cx, z));
+  double rn;
+  T2S2_TRY(core_norm(cx, z.c[0], z.core_elems(0), &rn));
+  double bn = bnorm_io ? *bnorm_io : -1.0;
+  if (bn < 0) {
+    T2S2_TRY(tt_norm(cx, b, &bn));
+    if (bnorm_io) *bnorm_io = bn;
+  }
+  *out = (bn > 0) ? rn / bn : rn;
+  cx.ar->release(mark);
+  return T2S2_OK;
+}
+
+}  // namespace t2s2
+
+using namespace t2s2;
+
+extern "C" {
+
+const char* t2s2_strerror(t2s2_status s) {
+  switch (s) {
+    case T2S2_OK: return "ok";
+    case T2S2_EINVAL: return "invalid argument";
+    case T2S2_ENOMEM: return "out of memory or TT capacity exceeded";
+    case T2S2_ECUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+    case T2S2_ENOCONV: return "solver did not reach the tolerance within the sweep cap";
+    case T2S2_ETIMEOUT: return "bounded device wait timed out";
+    case T2S2_ENOTIMPL: return "not implemented";
+    case T2S2_ENODEV: return "no sm_103 CUDA device";
+  }
+  return "unknown status";
+}
+
+int t2s2_device_count(void) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) return 0;
+  int good = 0;
+  for (int i = 0; i < n; ++i) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, i) == cudaSuccess && p.major == 10 && p.minor == 3) ++good;
+  }
+  return good;
+}
+
+t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op* out) {
+  if (!prob || !out || !prob->n || !prob->beta) return T2S2_EINVAL;
+  *out = nullptr;
+  if (prob->d < 1 || prob->d > T2S2_MAX_D || !(prob->eps > 0.0) || !std::isfinite(prob->eps))
+    return T2S2_EINVAL;
+  for (int k = 0; k < prob->d; ++k) {
+    if (prob->n[k] < 3 || prob->n[k] > T2S2_MAX_N || !std::isfinite(prob->beta[k])) return T2S2_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return T2S2_ENODEV;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess || p.major != 10 || p.minor != 3) return T2S2_ENODEV;
+  t2s2_op op = new t2s2_op_s();
+  op->device = dev;
+  op->d = prob->d;
+  op->eps = prob->eps;
+  op->plain = prob->plain_sc;
+  op->dims.resize(op->d);
+  size_t total = 0;
+  for (int k = 0; k < op->d; ++k) {
+    op->n[k] = prob->n[k];
+    op->m[k] = prob->n[k] - 2;
+    op->beta[k] = prob->beta[k];
+    if (!build_dimension(op->n[k], op->eps, op->beta[k], op->plain, &op->dims[k])) {
+      delete op;
+      return T2S2_EINVAL;
+    }
+    total += (size_t)kMatsPerDim * op->m[k] * op->m[k];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<double> host(total, 0.0);
+  size_t off = 0;
+  std::vector<size_t> offs(op->d);
+  for (int k = 0; k < op->d; ++k) {
+    const int m = op->m[k];
+    const size_t mm = (size_t)m * m;
+    offs[k] = off;
+    const Dim1D& D = op->dims[k];
+    std::copy(D.Rt.begin(), D.Rt.end(), host.begin() + off + 0 * mm);
+    std::copy(D.Lt.begin(), D.Lt.end(), host.begin() + off + 1 * mm);
+    std::copy(D.Rinv.begin(), D.Rinv.end(), host.begin() + off + 2 * mm);
+    std::copy(D.B.begin(), D.B.end(), host.begin() + off + 3 * mm);
+    for (int i = 0; i < m; ++i) host[off + 4 * mm + (size_t)i * m + i] = 1.0;
+    std::copy(D.H.begin(), D.H.end(), host.begin() + off + 5 * mm);
+    std::copy(D.W.begin(), D.W.end(), host.begin() + off + 6 * mm);
+    off += kMatsPerDim * mm;
+  }
+  cudaError_t e = cudaMalloc(&op->dmat, sizeof(double) * total);
+  if (e != cudaSuccess) { delete op; return T2S2_ENOMEM; }
+  e = cudaMemcpyAsync(op->dmat, host.data(), sizeof(double) * total, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMallocHost(&op->hbuf, sizeof(double) * 4096);
+  if (e == cudaSuccess) e = cudaMalloc(&op->dstat, sizeof(int) * 64);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "operator upload", __FILE__, __LINE__);
+    t2s2_op_destroy(op);
+    return T2S2_ECUDA;
+  }
+  for (int k = 0; k < op->d; ++k) {
+    const size_t mm = (size_t)op->m[k] * op->m[k];
+    double* base = op->dmat + offs[k];
+    op->dRt[k] = base;
+    op->dLt[k] = base + mm;
+    op->dRinv[k] = base + 2 * mm;
+    op->dB[k] = base + 3 * mm;
+    op->dI[k] = base + 4 * mm;
+    op->dH[k] = base + 5 * mm;
+    op->dW[k] = base + 6 * mm;
+  }
+  *out = op;
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_op_destroy(t2s2_op op) {
+  if (!op) return T2S2_OK;
+  if (op->dmat) cudaFree(op->dmat);
+  if (op->arena.base) cudaFree(op->arena.base);
+  if (op->hbuf) cudaFreeHost(op->hbuf);
+  if (op->dstat) cudaFree(op->dstat);
+  op->free_solver_buffers();
+  delete op;
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_op_nodes(t2s2_op op, int k, double* x, double* eta) {
+  if (!op || k < 0 || k >= op->d) return T2S2_EINVAL;
+  const Dim1D& D = op->dims[k];
+  if (x) std::copy(D.x.begin(), D.x.end(), x);
+  if (eta) std::copy(D.eta.begin(), D.eta.end(), eta);
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_op_matrices(t2s2_op op, int k, double* Rt, double* Lt) {
+  if (!op || k < 0 || k >= op->d) return T2S2_EINVAL;
+  const Dim1D& D = op->dims[k];
+  if (Rt) std::copy(D.Rt.begin(), D.Rt.end(), Rt);
+  if (Lt) std::copy(D.Lt.begin(), D.Lt.end(), Lt);
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_apply(t2s2_op op, const t2s2_tt* x, t2s2_tt* y, double c_mass, double c_op,
+                       t2s2_precision prec, void* stream) {
+  if (!op || !x || !y) return T2S2_EINVAL;
+  if (prec < T2S2_FP64 || prec > T2S2_BF16_REFINE) return T2S2_EINVAL;
+  T2S2_TRY(check_tt(op, x));
+  if (!y->r || !y->cores || !y->cap || y->d != op->d) return T2S2_EINVAL;
+  for (int k = 0; k < op->d; ++k)
+    if (y->cores[k] == x->cores[k]) return T2S2_EINVAL;
+  T2S2_TRY(ensure_arena(op, tt_bytes(x) + tt_bytes(y) + ((size_t)1 << 20)));
+  Ctx cx = make_ctx(op, stream);
+  DevTT dx, dy;
+  T2S2_TRY(bind_tt(cx, x, dx, true));
+  T2S2_TRY(bind_tt(cx, y, dy, false));
+  T2S2_TRY(apply_dispatch(op, cx, dx, dy, c_mass, c_op, prec));
+  return unbind_tt(cx, dy, y);
+}
+
+t2s2_status t2s2_round(t2s2_op op, t2s2_tt* x, double tol, int rmax, void* stream) {
+  if (!op || !x || !(tol >= 0.0)) return T2S2_EINVAL;
+  T2S2_TRY(check_tt(op, x));
+  size_t mc = max_core(x);
+  T2S2_TRY(ensure_arena(op, tt_bytes(x) * 3 + 10 * mc * sizeof(double) + ((size_t)8 << 20)));
+  Ctx cx = make_ctx(op, stream);
+  DevTT dx;
+  T2S2_TRY(bind_tt(cx, x, dx, true));
+  T2S2_TRY(tt_round(cx, dx, tol, rmax));
+  return unbind_tt(cx, dx, x);
+}
+
+t2s2_status t2s2_norm(t2s2_op op, const t2s2_tt* x, double* out, void* stream) {
+  if (!op || !x || !out) return T2S2_EINVAL;
+  T2S2_TRY(check_tt(op, x));
+  size_t mc = max_core(x);
+  T2S2_TRY(ensure_arena(op, tt_bytes(x) * 3 + 10 * mc * sizeof(double) + ((size_t)8 << 20)));
+  Ctx cx = make_ctx(op, stream);
+  DevTT dx;
+  T2S2_TRY(bind_tt(cx, x, dx, true));
+  return tt_norm(cx, dx, out);
+}
+
+t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double c_mass, double c_op,
+                          double* out, void* stream) {
+  if (!op || !b || !x || !out) return T2S2_EINVAL;
+  T2S2_TRY(check_tt(op, b));
+  T2S2_TRY(check_tt(op, x));
+  size_t mc = std::max(max_core(x) * 4, max_core(b)) + 4 * max_core(x);
+  T2S2_TRY(ensure_arena(op, (tt_bytes(b) + tt_bytes(x)) * 12 + 20 * mc * sizeof(double) + ((size_t)8 << 20)));
+  Ctx cx = make_ctx(op, stream);
+  DevTT db, dx;
+  T2S2_TRY(bind_tt(cx, b, db, true));
+  T2S2_TRY(bind_tt(cx, x, dx, true));
+  return residual_impl(op, cx, db, dx, c_mass, c_op, false, out, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// Internal state behind the C ABI: the operator handle and shared helpers.
+#pragma once
+#include <vector>
+
+#include "apply.h"
+#include "host_1d.h"
+#include "tt.h"
+
+// Per dimension the device holds kMatsPerDim m x m FP64 matrices:
+// Rt, Lt, Rt^{-1}, B = Rt^{-1} Lt, I, H (Hessenberg form of B), W (its basis).
+constexpr int kMatsPerDim = 7;
+
+struct t2s2_op_s {
+  int device = 0;
+  int d = 0;
+  int n[T2S2_MAX_D] = {0}, m[T2S2_MAX_D] = {0};
+  double beta[T2S2_MAX_D] = {0};
+  double eps = 0;
+  int plain = 0;
+  std::vector<t2s2::Dim1D> dims;
+  double* dmat = nullptr;
+  double *dRt[T2S2_MAX_D] = {nullptr}, *dLt[T2S2_MAX_D] = {nullptr}, *dRinv[T2S2_MAX_D] = {nullptr},
+         *dB[T2S2_MAX_D] = {nullptr}, *dI[T2S2_MAX_D] = {nullptr}, *dH[T2S2_MAX_D] = {nullptr},
+         *dW[T2S2_MAX_D] = {nullptr};
+  float* fmat = nullptr;  // FP32 copies of B, H, W for the mixed-precision inner solve
+  float *fB[T2S2_MAX_D] = {nullptr}, *fH[T2S2_MAX_D] = {nullptr}, *fW[T2S2_MAX_D] = {nullptr};
+  t2s2::Arena arena;
+  double* hbuf = nullptr;  // pinned host scratch
+  int* dstat = nullptr;    // device status words
+  void free_solver_buffers();
+};
+
+namespace t2s2 {
+t2s2_status ensure_arena(t2s2_op op, size_t bytes);
+Ctx make_ctx(t2s2_op op, void* stream);
+size_t tt_bytes(const t2s2_tt* t);
+size_t max_core(const t2s2_tt* t);
+t2s2_status check_tt(t2s2_op op, const t2s2_tt* t);
+t2s2_status bind_tt(Ctx& cx, const t2s2_tt* t, DevTT& dv, bool upload);
+t2s2_status unbind_tt(Ctx& cx, const DevTT& dv, t2s2_tt* t);
+t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass, double c_op,
+                     bool transformed);
+t2s2_status apply_dispatch(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass,
+                           double c_op, t2s2_precision prec);
+t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
+                          double c_op, bool transformed, double* out, double* bnorm_io);
+}  // namespace t2s2

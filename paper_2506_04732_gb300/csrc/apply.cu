@@ -1,0 +1,139 @@
+// TT-matrix-by-TT product for the rank-2 collocation operator (eq.
+// tt-matrix-format): y = (c_mass M + c_op A) x with
+//     A = sum_k Rt_1 x ... x Lt_k x ... x Rt_d,   M = Rt_1 x ... x Rt_d.
+// Core k of y needs the two mode-k contractions S X_k and G X_k with
+// S = Rt_k and G = c_op Lt_k (+ c_mass Rt_1 on the first core).  Each CTA
+// computes a 64 x 64 tile of [S; G] X_k[a] (rows: the 2m stacked output rows,
+// columns: the r_{k+1} right-rank index) and writes it straight into the block
+// pattern of Y_k:
+//     first  [G X, S X]            (1      x m x 2 r1)
+//     middle [[S X, 0], [G X, S X]] (2 r0  x m x 2 r1)
+//     last   [S X; G X]            (2 r0  x m x 1)
+//     d = 1  G X                   (1      x m x 1)
+// All d cores go in one launch; the zero block of middle cores is written by
+// the S-row tiles.
+#include "apply.h"
+
+namespace t2s2 {
+
+namespace {
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+struct TileMap {
+  int start[T2S2_MAX_D + 1];  // prefix sum of CTA counts per core
+};
+
+__global__ void __launch_bounds__(NT) apply_kernel(ApplyBatch p, TileMap tm) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  int core = 0;
+  while (core + 1 < p.ncores && (int)blockIdx.x >= tm.start[core + 1]) ++core;
+  const ApplyCore& c = p.c[core];
+  const int local = blockIdx.x - tm.start[core];
+  const int mt = cdiv_dev(2 * c.m, BM), nt = cdiv_dev(c.rb, BN);
+  const int a = local / (mt * nt);
+  const int rem = local % (mt * nt);
+  const int m0 = (rem / nt) * BM, n0 = (rem % nt) * BN;
+  const double* X = c.X + (long)a * c.m * c.rb;  // m x rb
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < c.m; k0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += NT) {
+      int kk = e % BK, mm = e / BK;
+      int row = m0 + mm, col = k0 + kk;
+      double v = 0.0;
+      if (row < 2 * c.m && col < c.m) {
+        if (row < c.m) {
+          v = c.S[(long)row * c.m + col];
+        } else {
+          long o = (long)(row - c.m) * c.m + col;
+          v = c.g_op * c.L[o];
+          if (c.g_mass != 0.0) v += c.g_mass * c.S[o];
+        }
+      }
+      As[kk][mm] = v;
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += NT) {
+      int nn = e % BN, kk = e / BN;
+      int col = n0 + nn, row = k0 + kk;
+      Bs[kk][nn] = (row < c.m && col < c.rb) ? X[(long)row * c.rb + col] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  // scatter
+  const int ra = c.ra, rb = c.rb, m = c.m;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int row = m0 + ty + 16 * i;
+    if (row >= 2 * m) continue;
+    const bool gpart = row >= m;
+    const int ii = gpart ? row - m : row;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int b = n0 + tx + 16 * j;
+      if (b >= rb) continue;
+      double v = acc[i][j];
+      double* Y = c.Y;
+      switch (c.kind) {
+        case kApplySingle:  // 1 x m x 1
+          if (gpart) Y[ii] = v;
+          break;
+        case kApplyFirst: {  // 1 x m x 2rb: [G X, S X]
+          long base = (long)ii * 2 * rb;
+          if (gpart) Y[base + b] = v; else Y[base + rb + b] = v;
+          break;
+        }
+        case kApplyLast: {  // 2ra x m x 1: [S X; G X]
+          long r = gpart ? (ra + a) : a;
+          Y[r * m + ii] = v;
+          break;
+        }
+        default: {  // middle: 2ra x m x 2rb
+          long w = 2L * rb;
+          if (gpart) {
+            Y[((long)(ra + a) * m + ii) * w + b] = v;            // (1,0): G X
+          } else {
+            Y[((long)a * m + ii) * w + b] = v;                   // (0,0): S X
+            Y[((long)(ra + a) * m + ii) * w + rb + b] = v;       // (1,1): S X
+            Y[((long)a * m + ii) * w + rb + b] = 0.0;            // (0,1): 0
+          }
+        }
+      }
+    }
+  }
+}
+}  // namespace
+
+t2s2_status apply_fp64(const ApplyBatch& p, cudaStream_t st) {
+  TileMap tm;
+  int total = 0;
+  for (int k = 0; k < p.ncores; ++k) {
+    tm.start[k] = total;
+    const ApplyCore& c = p.c[k];
+    total += c.ra * cdiv(2 * c.m, BM) * cdiv(c.rb, BN);
+  }
+  tm.start[p.ncores] = total;
+  if (total == 0) return T2S2_OK;
+  apply_kernel<<<total, NT, 0, st>>>(p, tm);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+
+}  // namespace t2s2

@@ -1,0 +1,27 @@
+// Fused TT-apply of the rank-2 collocation operator (see apply.cu).
+#pragma once
+#include "common.cuh"
+
+namespace t2s2 {
+
+enum { kApplyMiddle = 0, kApplyFirst = 1, kApplyLast = 2, kApplySingle = 3 };
+
+struct ApplyCore {
+  const double* S;   // m x m (Rt_k, or the identity)
+  const double* L;   // m x m (Lt_k, or B_k)
+  const double* X;   // ra x m x rb
+  double* Y;         // output core (layout set by kind)
+  int ra, m, rb, kind;
+  double g_mass, g_op;  // G = g_op * L + g_mass * S
+};
+
+struct ApplyBatch {
+  int ncores;
+  ApplyCore c[T2S2_MAX_D];
+};
+
+__host__ __device__ inline int cdiv_dev(int a, int b) { return (a + b - 1) / b; }
+
+t2s2_status apply_fp64(const ApplyBatch& p, cudaStream_t st);
+
+}  // namespace t2s2

@@ -1,0 +1,166 @@
+// Tiled SIMT GEMM for the small dense contractions of the TT sweeps.
+// 64x64 output tile per CTA, 256 threads with a 4x4 register micro-tile,
+// K staged through shared memory in slices of 16.  Used for FP64 work, whose
+// throughput on sm_103 is bounded by the DFMA pipe rather than by memory.
+#include "gemm.h"
+
+namespace t2s2 {
+
+namespace {
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(NT) gemm_kernel(Gemm<T> g, int splits, int kchunk, T* ws) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int bz = blockIdx.z;
+  const int b = bz / splits, sidx = bz % splits;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int k_begin = sidx * kchunk;
+  const int k_end = min(g.K, k_begin + kchunk);
+  const T* A = g.A + (long)b * g.sA;
+  const T* B = g.B + (long)b * g.sB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+
+  for (int k0 = k_begin; k0 < k_end; k0 += BK) {
+    // load A tile: BM x BK elements of op(A)
+    for (int e = threadIdx.x; e < BM * BK; e += NT) {
+      int mm, kk;
+      if (g.tA) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+      int gm = m0 + mm, gk = k0 + kk;
+      T v = 0;
+      if (gm < g.M && gk < k_end) v = g.tA ? A[(long)gk * g.lda + gm] : A[(long)gm * g.lda + gk];
+      As[kk][mm] = v;
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += NT) {
+      int nn, kk;
+      if (g.tB) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+      int gn = n0 + nn, gk = k0 + kk;
+      T v = 0;
+      if (gn < g.N && gk < k_end) v = g.tB ? B[(long)gn * g.ldb + gk] : B[(long)gk * g.ldb + gn];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  if (splits == 1) {
+    T* C = g.C + (long)b * g.sC;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int gm = m0 + ty + 16 * i;
+      if (gm >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int gn = n0 + tx + 16 * j;
+        if (gn >= g.N) continue;
+        T* c = C + (long)gm * g.ldc + gn;
+        T v = g.alpha * acc[i][j];
+        if (g.beta != T(0)) v = fma(g.beta, *c, v);
+        *c = v;
+      }
+    }
+  } else {
+    T* P = ws + ((long)sidx * g.batch + b) * (long)g.M * g.N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int gm = m0 + ty + 16 * i;
+      if (gm >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int gn = n0 + tx + 16 * j;
+        if (gn < g.N) P[(long)gm * g.N + gn] = acc[i][j];
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void splitk_reduce(Gemm<T> g, int splits, const T* ws) {
+  long total = (long)g.batch * g.M * g.N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    long b = e / ((long)g.M * g.N);
+    long rem = e % ((long)g.M * g.N);
+    int gm = (int)(rem / g.N), gn = (int)(rem % g.N);
+    T s = 0;
+    for (int p = 0; p < splits; ++p) s += ws[((long)p * g.batch + b) * (long)g.M * g.N + rem];
+    T* c = g.C + b * g.sC + (long)gm * g.ldc + gn;
+    T v = g.alpha * s;
+    if (g.beta != T(0)) v = fma(g.beta, *c, v);
+    *c = v;
+  }
+}
+
+template <typename T>
+int choose_splits(const Gemm<T>& g, int* kchunk) {
+  if (g.K <= 0) {
+    *kchunk = 0;
+    return 1;
+  }
+  long tiles = (long)cdiv(g.M, BM) * cdiv(g.N, BN) * g.batch;
+  int splits = 1;
+  if (tiles < 2 * kNumSMs && g.K > 4 * BK) {
+    long want = (2 * kNumSMs + tiles - 1) / tiles;
+    long maxs = g.K / (4 * BK);
+    splits = (int)std::max(1L, std::min(std::min(want, maxs), 64L));
+  }
+  int kc = cdiv(g.K, splits);
+  kc = cdiv(kc, BK) * BK;
+  splits = cdiv(g.K, kc);
+  *kchunk = kc;
+  return splits;
+}
+}  // namespace
+
+template <typename T>
+size_t gemm_workspace(const Gemm<T>& g) {
+  int kc;
+  int s = choose_splits(g, &kc);
+  return s > 1 ? (size_t)s * g.batch * g.M * g.N : 0;
+}
+
+template <typename T>
+t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return T2S2_OK;
+  int kc;
+  int splits = choose_splits(g, &kc);
+  if (splits > 1 && (ws == nullptr || ws_elems < (size_t)splits * g.batch * g.M * g.N)) {
+    splits = 1;
+    kc = g.K;
+  }
+  if (g.batch * (long)splits > 65535L) return T2S2_EINVAL;
+  dim3 grid(cdiv(g.N, BN), cdiv(g.M, BM), g.batch * splits);
+  gemm_kernel<T><<<grid, NT, 0, st>>>(g, splits, std::max(kc, 1), ws);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  if (splits > 1) {
+    long total = (long)g.batch * g.M * g.N;
+    int blocks = (int)std::min<long>(cdiv(total, 256), 4L * kNumSMs);
+    splitk_reduce<T><<<blocks, 256, 0, st>>>(g, splits, ws);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  return T2S2_OK;
+}
+
+template size_t gemm_workspace<double>(const Gemm<double>&);
+template size_t gemm_workspace<float>(const Gemm<float>&);
+template t2s2_status gemm<double>(const Gemm<double>&, double*, size_t, cudaStream_t);
+template t2s2_status gemm<float>(const Gemm<float>&, float*, size_t, cudaStream_t);
+
+}  // namespace t2s2

@@ -1,0 +1,28 @@
+// Host-side FP64 construction of the per-dimension collocation matrices.
+#pragma once
+#include <vector>
+
+namespace t2s2 {
+
+struct Dim1D {
+  int n = 0;                 // GLL nodes (polynomial degree n-1); m = n-2 interior unknowns
+  std::vector<double> x;     // n GLL points
+  std::vector<double> eta;   // m collocation points
+  std::vector<double> Rt;    // m x m: l_i(eta_j), interior i
+  std::vector<double> Lt;    // m x m: beta l_i'(eta_j) - eps l_i''(eta_j)
+  std::vector<double> Rinv;  // Rt^{-1}
+  std::vector<double> B;     // Rt^{-1} Lt
+  std::vector<double> H;     // upper Hessenberg form of B: H = W^T B W
+  std::vector<double> W;     // orthogonal Hessenberg basis
+};
+
+void gll_points(int N, double* x);
+void gauss_points(int N, double* g);
+void collocation_points(int N, double eps, double beta, int plain, double* eta);
+void lagrange_matrices(int N, const double* x, int npts, const double* t, double* R, double* D,
+                       double* D2);
+bool invert(int m, double* A);
+void hessenberg(int m, double* B, double* W);
+bool build_dimension(int n, double eps, double beta, int plain, Dim1D* out);
+
+}  // namespace t2s2

@@ -1,0 +1,223 @@
+// Small dense factorisations (c x c, c <= kSmallMax) done by one CTA in
+// shared memory, FP64:
+//  * chol_inv: G + s I = L L^T (Cholesky) and L^{-1}, for CholeskyQR.  The
+//    shift s makes the first pass of shifted CholeskyQR3 (Fukaya, Kannan,
+//    Nakatsukasa, Yamamoto, Yanagisawa 2020) succeed for any conditioning.
+//  * jacobi_svd: one-sided Jacobi SVD A = U diag(s) V^T of a p x q matrix
+//    (Hestenes' method, columns orthogonalised by plane rotations in a
+//    round-robin ordering; singular values sorted in decreasing order).
+#include "small.h"
+
+#include <cmath>
+
+namespace t2s2 {
+
+namespace {
+
+constexpr int kThreads = 512;
+
+// G (c x c, row-major, ld c) -> L lower (G + shift I = L L^T), Linv = L^{-1}.
+__global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __restrict__ G, int c,
+                                                            double shift_rel, double* __restrict__ L,
+                                                            double* __restrict__ Linv, int* status) {
+  extern __shared__ double sm[];
+  double* A = sm;           // c x c
+  double* Iv = sm + c * c;  // c x c
+  __shared__ double shift;
+  __shared__ int bad;
+  const int t = threadIdx.x;
+  for (int e = t; e < c * c; e += blockDim.x) A[e] = G[e];
+  if (t == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < c; ++i) tr += G[i * c + i];
+    shift = shift_rel * tr;
+    if (!(tr > 0.0)) shift = 1e-300;
+    bad = 0;
+  }
+  __syncthreads();
+  for (int i = t; i < c; i += blockDim.x) A[i * c + i] += shift;
+  __syncthreads();
+  // right-looking Cholesky, lower triangle
+  for (int j = 0; j < c; ++j) {
+    if (t == 0) {
+      double v = A[j * c + j];
+      if (!(v > 0.0)) { bad = 1; v = 1e-300; }
+      A[j * c + j] = sqrt(v);
+    }
+    __syncthreads();
+    double djj = A[j * c + j];
+    for (int i = j + 1 + t; i < c; i += blockDim.x) A[i * c + j] /= djj;
+    __syncthreads();
+    int rem = c - j - 1;
+    for (int e = t; e < rem * rem; e += blockDim.x) {
+      int i = j + 1 + e / rem, k = j + 1 + e % rem;
+      if (k <= i) A[i * c + k] -= A[i * c + j] * A[k * c + j];
+    }
+    __syncthreads();
+  }
+  // inverse of lower triangular L: column k solves L x = e_k (one thread per column)
+  for (int e = t; e < c * c; e += blockDim.x) Iv[e] = 0.0;
+  __syncthreads();
+  for (int k = t; k < c; k += blockDim.x) {
+    for (int i = k; i < c; ++i) {
+      double s = (i == k) ? 1.0 : 0.0;
+      for (int l = k; l < i; ++l) s -= A[i * c + l] * Iv[l * c + k];
+      Iv[i * c + k] = s / A[i * c + i];
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < c * c; e += blockDim.x) {
+    int i = e / c, k = e % c;
+    L[e] = (k <= i) ? A[e] : 0.0;
+    Linv[e] = (k <= i) ? Iv[e] : 0.0;
+  }
+  if (t == 0 && status) *status = bad;
+}
+
+// One-sided Jacobi on the columns of W (p x q, p >= q) held in shared memory.
+// V (q x q) accumulates the rotations.  Returns sorted s, U = W / s, V.
+__global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __restrict__ A, int p,
+                                                              int q, int transpose,
+                                                              double* __restrict__ U,
+                                                              double* __restrict__ s_out,
+                                                              double* __restrict__ V, int* sweeps_out) {
+  // Working matrix W is rows x cols with rows >= cols (transposed input if p < q).
+  extern __shared__ double sm[];
+  const int rows = transpose ? q : p, cols = transpose ? p : q;
+  double* W = sm;                        // rows x cols, column-major for rotations
+  double* Vs = sm + rows * cols;         // cols x cols, column-major
+  double* nrm = Vs + cols * cols;        // cols
+  __shared__ int rotated;
+  __shared__ int order[kSmallMax];
+  const int t = threadIdx.x;
+  for (int e = t; e < rows * cols; e += blockDim.x) {
+    int i = e % rows, j = e / rows;  // W(i,j)
+    W[j * rows + i] = transpose ? A[j * q + i] : A[i * q + j];
+  }
+  for (int e = t; e < cols * cols; e += blockDim.x) Vs[e] = (e % cols == e / cols) ? 1.0 : 0.0;
+  __syncthreads();
+  const int warp = t / 32, lane = t % 32, nwarps = blockDim.x / 32;
+  const int npair = (cols + 1) / 2;  // round-robin with a dummy column when cols is odd
+  const int ncol = 2 * npair;
+  int sweep = 0;
+  for (sweep = 0; sweep < 60; ++sweep) {
+    if (t == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < ncol - 1; ++round) {
+      for (int pr = warp; pr < npair; pr += nwarps) {
+        // round-robin pairing: position 0 fixed, others rotate
+        int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (ncol - 1);
+        int b = 1 + (ncol - 2 - pr + round) % (ncol - 1);
+        if (a >= cols || b >= cols) continue;
+        if (a > b) { int tmp = a; a = b; b = tmp; }
+        double* wa = W + a * rows;
+        double* wb = W + b * rows;
+        double alpha = 0, beta = 0, gamma = 0;
+        for (int i = lane; i < rows; i += 32) {
+          alpha += wa[i] * wa[i];
+          beta += wb[i] * wb[i];
+          gamma += wa[i] * wb[i];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+          beta += __shfl_xor_sync(0xffffffffu, beta, o);
+          gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+        }
+        if (fabs(gamma) > 1e-15 * sqrt(alpha * beta) && gamma != 0.0) {
+          double zeta = (beta - alpha) / (2.0 * gamma);
+          double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+          for (int i = lane; i < rows; i += 32) {
+            double x = wa[i], y = wb[i];
+            wa[i] = cs * x - sn * y;
+            wb[i] = sn * x + cs * y;
+          }
+          double* va = Vs + a * cols;
+          double* vb = Vs + b * cols;
+          for (int i = lane; i < cols; i += 32) {
+            double x = va[i], y = vb[i];
+            va[i] = cs * x - sn * y;
+            vb[i] = sn * x + cs * y;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  for (int j = warp; j < cols; j += nwarps) {
+    double s = 0;
+    for (int i = lane; i < rows; i += 32) s += W[j * rows + i] * W[j * rows + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) nrm[j] = sqrt(s);
+  }
+  __syncthreads();
+  if (t == 0) {  // selection sort of column order by decreasing norm (cols <= kSmallMax)
+    for (int j = 0; j < cols; ++j) order[j] = j;
+    for (int j = 0; j < cols; ++j) {
+      int best = j;
+      for (int l = j + 1; l < cols; ++l)
+        if (nrm[order[l]] > nrm[order[best]]) best = l;
+      int tmp = order[j]; order[j] = order[best]; order[best] = tmp;
+    }
+    if (sweeps_out) *sweeps_out = sweep;
+  }
+  __syncthreads();
+  // Outputs: A = U diag(s) V^T with U p x k, V q x k, k = cols (= min(p,q)).
+  // Working problem: W0 = Wfinal V^T.  If transpose, A = W0^T = V diag(s) U_w^T.
+  const int k = cols;
+  for (int j = t; j < k; j += blockDim.x) s_out[j] = nrm[order[j]];
+  for (int e = t; e < rows * k; e += blockDim.x) {
+    int i = e / k, j = e % k;
+    int cj = order[j];
+    double sj = nrm[cj];
+    double u = (sj > 0) ? W[cj * rows + i] / sj : ((i == j) ? 1.0 : 0.0);
+    if (!transpose) U[i * k + j] = u;   // U: p x k
+    else V[i * k + j] = u;              // V: q x k (rows == q)
+  }
+  for (int e = t; e < cols * k; e += blockDim.x) {
+    int i = e / k, j = e % k;
+    double v = Vs[order[j] * cols + i];
+    if (!transpose) V[i * k + j] = v;   // V: q x k
+    else U[i * k + j] = v;              // U: p x k (cols == p)
+  }
+}
+
+}  // namespace
+
+t2s2_status chol_inv(const double* G, int c, double shift_rel, double* L, double* Linv, int* status,
+                     cudaStream_t st) {
+  if (c <= 0 || c > kSmallMax) return T2S2_EINVAL;
+  size_t smem = (size_t)2 * c * c * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    T2S2_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       2 * kSmallMax * kSmallMax * (int)sizeof(double)));
+    attr = true;
+  }
+  chol_inv_kernel<<<1, kThreads, smem, st>>>(G, c, shift_rel, L, Linv, status);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+
+t2s2_status jacobi_svd(const double* A, int p, int q, double* U, double* s, double* V, int* sweeps,
+                       cudaStream_t st) {
+  if (p <= 0 || q <= 0 || p > kSmallMax || q > kSmallMax) return T2S2_EINVAL;
+  int transpose = p < q;
+  int rows = transpose ? q : p, cols = transpose ? p : q;
+  size_t smem = ((size_t)rows * cols + (size_t)cols * cols + cols) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    T2S2_CUDA_TRY(cudaFuncSetAttribute(
+        jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)((2 * kSmallMax * kSmallMax + kSmallMax) * sizeof(double))));
+    attr = true;
+  }
+  jacobi_svd_kernel<<<1, kThreads, smem, st>>>(A, p, q, transpose, U, s, V, sweeps);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+
+}  // namespace t2s2

@@ -1,0 +1,408 @@
+// FP64 tensor-train arithmetic on the device.
+//
+// Orthogonalisation uses shifted CholeskyQR3 (Fukaya et al. 2020): three
+// Gram / Cholesky / triangular-multiply passes whose heavy parts are GEMMs
+// spread over all SMs, instead of a Householder QR that would serialise on
+// one SM's FP64 pipe.  Truncation takes a one-sided Jacobi SVD of the small
+// triangular factor.  Rounding follows the TT paper's rndg (Methods): right-to-
+// left orthogonalisation, then left-to-right truncated SVDs with threshold
+// tol ||x|| / sqrt(d-1) per unfolding.
+#include "tt.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace t2s2 {
+
+namespace {
+
+__global__ void k_scale_copy(double* dst, const double* src, size_t n, double alpha) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = alpha * src[e];
+}
+__global__ void k_axpy(double* dst, const double* src, size_t n, double beta) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    dst[e] += beta * src[e];
+}
+__global__ void k_fill(double* dst, size_t n, double v) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = v;
+}
+__global__ void k_identity(double* dst, int n) {
+  size_t nn = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn;
+       e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+__global__ void k_copy_block(double* dst, int rd0, int rd1, int a0, int b0, const double* src, int ra,
+                             int m, int rb, double alpha) {
+  size_t n = (size_t)ra * m * rb;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int b = (int)(e % rb);
+    size_t t = e / rb;
+    int i = (int)(t % m);
+    int a = (int)(t / m);
+    dst[((size_t)(a0 + a) * m + i) * rd1 + b0 + b] = alpha * src[e];
+  }
+}
+__global__ void k_sv_t(double* M, const double* s, const double* V, int r, int q, int ldv) {
+  int n = r * q;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    int i = e / q, j = e % q;
+    M[e] = s[i] * V[(size_t)j * ldv + i];
+  }
+}
+// sum of squares, one block, fixed order per thread then tree (deterministic)
+__global__ void k_sumsq(const double* v, size_t n, double* out) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (size_t e = threadIdx.x; e < n; e += blockDim.x) s += v[e] * v[e];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+inline int blocks_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 8 * kNumSMs)); }
+
+}  // namespace
+
+t2s2_status dev_scale_copy(Ctx& cx, double* dst, const double* src, size_t n, double alpha) {
+  if (n == 0) return T2S2_OK;
+  k_scale_copy<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n, alpha);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+t2s2_status dev_axpy(Ctx& cx, double* dst, const double* src, size_t n, double beta) {
+  if (n == 0) return T2S2_OK;
+  k_axpy<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n, beta);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+t2s2_status dev_fill(Ctx& cx, double* dst, size_t n, double v) {
+  if (n == 0) return T2S2_OK;
+  k_fill<<<blocks_for(n), 256, 0, cx.st>>>(dst, n, v);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+t2s2_status dev_identity(Ctx& cx, double* dst, int n) {
+  k_identity<<<blocks_for((size_t)n * n), 256, 0, cx.st>>>(dst, n);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+t2s2_status dev_copy_block(Ctx& cx, double* dst, int rd0, int rd1, int a0, int b0, const double* src,
+                           int ra, int m, int rb, double alpha) {
+  (void)rd0;
+  size_t n = (size_t)ra * m * rb;
+  if (n == 0) return T2S2_OK;
+  k_copy_block<<<blocks_for(n), 256, 0, cx.st>>>(dst, rd0, rd1, a0, b0, src, ra, m, rb, alpha);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+t2s2_status dev_sv_t(Ctx& cx, double* M, const double* s, const double* V, int r, int q, int ldv) {
+  if (r * q == 0) return T2S2_OK;
+  k_sv_t<<<blocks_for((size_t)r * q), 256, 0, cx.st>>>(M, s, V, r, q, ldv);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+
+t2s2_status core_norm(Ctx& cx, const double* v, size_t n, double* out) {
+  size_t mk = cx.ar->mark();
+  double* d = aget<double>(cx, 1);
+  if (!d) return T2S2_ENOMEM;
+  k_sumsq<<<1, 1024, 0, cx.st>>>(v, n, d);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  T2S2_CUDA_TRY(cudaMemcpyAsync(cx.hbuf, d, sizeof(double), cudaMemcpyDeviceToHost, cx.st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(cx.st));
+  *out = std::sqrt(cx.hbuf[0]);
+  cx.ar->release(mk);
+  return T2S2_OK;
+}
+
+int trunc_rank(const double* s, int n, double delta, int rmax) {
+  // tail[j] = ||s[j:]||; smallest j >= 1 with tail[j] < delta (ties keep the larger rank)
+  std::vector<double> tail(n + 1, 0.0);
+  for (int j = n - 1; j >= 0; --j) tail[j] = std::sqrt(tail[j + 1] * tail[j + 1] + s[j] * s[j]);
+  int r = n;
+  for (int j = 1; j < n; ++j)
+    if (tail[j] < delta * (1.0 - 1e-14)) { r = j; break; }
+  if (rmax > 0) r = std::min(r, rmax);
+  return std::max(r, 1);
+}
+
+static constexpr double kUnit = 1.1102230246251565e-16;
+
+namespace {
+__global__ void k_transpose(double* dst, const double* src, int r, int c) {
+  int n = r * c;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    int i = e / c, j = e % c;
+    dst[(size_t)j * r + i] = src[e];
+  }
+}
+}  // namespace
+
+t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, double* R) {
+  if (cols > kSmallMax || rows < cols || cols <= 0) return T2S2_EINVAL;
+  size_t mk = cx.ar->mark();
+  const int c = cols;
+  double* G = aget<double>(cx, (size_t)c * c);
+  double* L = aget<double>(cx, (size_t)c * c);
+  double* Li = aget<double>(cx, (size_t)c * c);
+  double* Lacc = aget<double>(cx, (size_t)c * c);
+  double* Ltmp = aget<double>(cx, (size_t)c * c);
+  double* T0 = aget<double>(cx, (size_t)rows * c);
+  double* T1 = aget<double>(cx, (size_t)rows * c);
+  if (!G || !L || !Li || !Lacc || !Ltmp || !T0 || !T1) return T2S2_ENOMEM;
+  const double shift = 11.0 * ((double)rows * c + (double)c * (c + 1)) * kUnit;
+  const double* cur = W;
+  double* outs[3] = {T0, T1, Q};
+  for (int pass = 0; pass < 3; ++pass) {
+    T2S2_TRY(gemm_ex<double>(cx, c, c, rows, true, false, 1.0, cur, c, cur, c, 0.0, G, c));
+    T2S2_TRY(chol_inv(G, c, pass == 0 ? shift : 0.0, L, Li, cx.dstat, cx.st));
+    // cur = next * L^T  =>  next = cur * L^{-T}
+    T2S2_TRY(gemm_ex<double>(cx, rows, c, c, false, true, 1.0, cur, c, Li, c, 0.0, outs[pass], c));
+    if (pass == 0) {
+      T2S2_CUDA_TRY(cudaMemcpyAsync(Lacc, L, sizeof(double) * c * c, cudaMemcpyDeviceToDevice, cx.st));
+    } else {
+      T2S2_TRY(gemm_ex<double>(cx, c, c, c, false, false, 1.0, Lacc, c, L, c, 0.0, Ltmp, c));
+      std::swap(Lacc, Ltmp);
+    }
+    cur = outs[pass];
+  }
+  // W = Q (L1 L2 L3)^T  ->  R = Lacc^T
+  k_transpose<<<blocks_for((size_t)c * c), 256, 0, cx.st>>>(R, Lacc, c, c);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  cx.ar->release(mk);
+  return T2S2_OK;
+}
+
+t2s2_status lq_wide(Ctx& cx, const double* W, int rows, int cols, double* Q, double* Lout) {
+  if (rows > kSmallMax || rows > cols || rows <= 0) return T2S2_EINVAL;
+  size_t mk = cx.ar->mark();
+  const int c = rows;
+  double* G = aget<double>(cx, (size_t)c * c);
+  double* L = aget<double>(cx, (size_t)c * c);
+  double* Li = aget<double>(cx, (size_t)c * c);
+  double* Lacc = aget<double>(cx, (size_t)c * c);
+  double* Ltmp = aget<double>(cx, (size_t)c * c);
+  double* T0 = aget<double>(cx, (size_t)rows * cols);
+  double* T1 = aget<double>(cx, (size_t)rows * cols);
+  if (!G || !L || !Li || !Lacc || !Ltmp || !T0 || !T1) return T2S2_ENOMEM;
+  const double shift = 11.0 * ((double)rows * cols + (double)c * (c + 1)) * kUnit;
+  const double* cur = W;
+  double* outs[3] = {T0, T1, Q};
+  for (int pass = 0; pass < 3; ++pass) {
+    // G = cur cur^T
+    T2S2_TRY(gemm_ex<double>(cx, c, c, cols, false, true, 1.0, cur, cols, cur, cols, 0.0, G, c));
+    T2S2_TRY(chol_inv(G, c, pass == 0 ? shift : 0.0, L, Li, cx.dstat, cx.st));
+    // cur = L next  =>  next = L^{-1} cur
+    T2S2_TRY(gemm_ex<double>(cx, c, cols, c, false, false, 1.0, Li, c, cur, cols, 0.0, outs[pass], cols));
+    if (pass == 0) {
+      T2S2_CUDA_TRY(cudaMemcpyAsync(Lacc, L, sizeof(double) * c * c, cudaMemcpyDeviceToDevice, cx.st));
+    } else {
+      T2S2_TRY(gemm_ex<double>(cx, c, c, c, false, false, 1.0, Lacc, c, L, c, 0.0, Ltmp, c));
+      std::swap(Lacc, Ltmp);
+    }
+    cur = outs[pass];
+  }
+  T2S2_CUDA_TRY(cudaMemcpyAsync(Lout, Lacc, sizeof(double) * c * c, cudaMemcpyDeviceToDevice, cx.st));
+  cx.ar->release(mk);
+  return T2S2_OK;
+}
+
+t2s2_status tt_alloc(Ctx& cx, DevTT& t, int d, const int* m, const int* r, int rcap) {
+  t.d = d;
+  for (int k = 0; k <= d; ++k) t.r[k] = r[k];
+  for (int k = 0; k < d; ++k) {
+    t.m[k] = m[k];
+    int r0 = (k == 0) ? 1 : std::max(r[k], rcap);
+    int r1 = (k == d - 1) ? 1 : std::max(r[k + 1], rcap);
+    t.cap[k] = (size_t)r0 * m[k] * r1;
+    t.c[k] = aget<double>(cx, t.cap[k]);
+    if (!t.c[k]) return T2S2_ENOMEM;
+  }
+  return T2S2_OK;
+}
+
+t2s2_status tt_copy(Ctx& cx, const DevTT& src, DevTT& dst) {
+  for (int k = 0; k < src.d; ++k)
+    if (src.core_elems(k) > dst.cap[k]) return T2S2_ENOMEM;
+  dst.d = src.d;
+  for (int k = 0; k <= src.d; ++k) dst.r[k] = src.r[k];
+  for (int k = 0; k < src.d; ++k) {
+    dst.m[k] = src.m[k];
+    T2S2_CUDA_TRY(cudaMemcpyAsync(dst.c[k], src.c[k], sizeof(double) * src.core_elems(k),
+                                  cudaMemcpyDeviceToDevice, cx.st));
+  }
+  return T2S2_OK;
+}
+
+t2s2_status tt_axpby(Ctx& cx, double alpha, const DevTT& x, double beta, const DevTT& y, DevTT& z) {
+  const int d = x.d;
+  if (y.d != d) return T2S2_EINVAL;
+  int r[T2S2_MAX_D + 1];
+  r[0] = 1;
+  r[d] = 1;
+  for (int k = 1; k < d; ++k) r[k] = x.r[k] + y.r[k];
+  T2S2_TRY(tt_alloc(cx, z, d, x.m, r, 0));
+  for (int k = 0; k < d; ++k) {
+    const int m = x.m[k];
+    T2S2_TRY(dev_fill(cx, z.c[k], z.core_elems(k), 0.0));
+    if (d == 1) {  // single core: alpha X + beta Y
+      T2S2_TRY(dev_scale_copy(cx, z.c[k], x.c[k], m, alpha));
+      T2S2_TRY(dev_axpy(cx, z.c[k], y.c[k], m, beta));
+      continue;
+    }
+    const double ax = (k == 0) ? alpha : 1.0, by = (k == 0) ? beta : 1.0;
+    const int a0y = (k == 0) ? 0 : x.r[k];
+    const int b0y = (k == d - 1) ? 0 : x.r[k + 1];
+    T2S2_TRY(dev_copy_block(cx, z.c[k], z.r[k], z.r[k + 1], 0, 0, x.c[k], x.r[k], m, x.r[k + 1], ax));
+    T2S2_TRY(dev_copy_block(cx, z.c[k], z.r[k], z.r[k + 1], a0y, b0y, y.c[k], y.r[k], m, y.r[k + 1], by));
+  }
+  return T2S2_OK;
+}
+
+t2s2_status tt_orth_right(Ctx& cx, DevTT& x) {
+  const int d = x.d;
+  for (int k = d - 1; k >= 1; --k) {
+    const int rk = x.r[k], mk_ = x.m[k], rk1 = x.r[k + 1];
+    const int cols = mk_ * rk1;
+    const int rp = x.r[k - 1], mp = x.m[k - 1];
+    size_t mark = cx.ar->mark();
+    if (rk <= cols) {
+      if (rk > kSmallMax) return T2S2_EINVAL;
+      double* Q = aget<double>(cx, (size_t)rk * cols);
+      double* L = aget<double>(cx, (size_t)rk * rk);
+      double* P = aget<double>(cx, (size_t)rp * mp * rk);
+      if (!Q || !L || !P) return T2S2_ENOMEM;
+      T2S2_TRY(lq_wide(cx, x.c[k], rk, cols, Q, L));
+      T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k], Q, sizeof(double) * rk * cols, cudaMemcpyDeviceToDevice, cx.st));
+      // core k-1 <- core k-1 x_3 L
+      T2S2_TRY(gemm_ex<double>(cx, rp * mp, rk, rk, false, false, 1.0, x.c[k - 1], rk, L, rk, 0.0, P, rk));
+      T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k - 1], P, sizeof(double) * rp * mp * rk, cudaMemcpyDeviceToDevice, cx.st));
+    } else {
+      // rank reduces to cols: core k-1 <- core k-1 x_3 W, core k <- identity
+      if ((size_t)rp * mp * cols > x.cap[k - 1] || (size_t)cols * cols > x.cap[k]) return T2S2_ENOMEM;
+      double* P = aget<double>(cx, (size_t)rp * mp * cols);
+      if (!P) return T2S2_ENOMEM;
+      T2S2_TRY(gemm_ex<double>(cx, rp * mp, cols, rk, false, false, 1.0, x.c[k - 1], rk, x.c[k], cols, 0.0, P, cols));
+      T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k - 1], P, sizeof(double) * rp * mp * cols, cudaMemcpyDeviceToDevice, cx.st));
+      T2S2_TRY(dev_identity(cx, x.c[k], cols));
+      x.r[k] = cols;
+    }
+    cx.ar->release(mark);
+  }
+  return T2S2_OK;
+}
+
+t2s2_status tt_orth_left(Ctx& cx, DevTT& x) {
+  const int d = x.d;
+  for (int k = 0; k + 1 < d; ++k) {
+    const int rk = x.r[k], mk_ = x.m[k], rk1 = x.r[k + 1];
+    const int rows = rk * mk_;
+    const int mn = x.m[k + 1], rn = x.r[k + 2];
+    size_t mark = cx.ar->mark();
+    if (rows >= rk1) {
+      if (rk1 > kSmallMax) return T2S2_EINVAL;
+      double* Q = aget<double>(cx, (size_t)rows * rk1);
+      double* R = aget<double>(cx, (size_t)rk1 * rk1);
+      double* P = aget<double>(cx, (size_t)rk1 * mn * rn);
+      if (!Q || !R || !P) return T2S2_ENOMEM;
+      T2S2_TRY(qr_tall(cx, x.c[k], rows, rk1, Q, R));
+      T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k], Q, sizeof(double) * rows * rk1, cudaMemcpyDeviceToDevice, cx.st));
+      T2S2_TRY(gemm_ex<double>(cx, rk1, mn * rn, rk1, false, false, 1.0, R, rk1, x.c[k + 1], mn * rn, 0.0, P, mn * rn));
+      T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k + 1], P, sizeof(double) * rk1 * mn * rn, cudaMemcpyDeviceToDevice, cx.st));
+    } else {
+      if ((size_t)rows * mn * rn > x.cap[k + 1] || (size_t)rows * rows > x.cap[k]) return T2S2_ENOMEM;
+      double* P = aget<double>(cx, (size_t)rows * mn * rn);
+      if (!P) return T2S2_ENOMEM;
+      T2S2_TRY(gemm_ex<double>(cx, rows, mn * rn, rk1, false, false, 1.0, x.c[k], rk1, x.c[k + 1], mn * rn, 0.0, P, mn * rn));
+      T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k + 1], P, sizeof(double) * rows * mn * rn, cudaMemcpyDeviceToDevice, cx.st));
+      T2S2_TRY(dev_identity(cx, x.c[k], rows));
+      x.r[k + 1] = rows;
+    }
+    cx.ar->release(mark);
+  }
+  return T2S2_OK;
+}
+
+t2s2_status tt_norm(Ctx& cx, const DevTT& x, double* out) {
+  size_t mark = cx.ar->mark();
+  DevTT t;
+  int rc = 0;
+  for (int k = 0; k <= x.d; ++k) rc = std::max(rc, x.r[k]);
+  T2S2_TRY(tt_alloc(cx, t, x.d, x.m, x.r, rc));
+  T2S2_TRY(tt_copy(cx, x, t));
+  T2S2_TRY(tt_orth_right(cx, t));
+  T2S2_TRY(core_norm(cx, t.c[0], t.core_elems(0), out));
+  cx.ar->release(mark);
+  return T2S2_OK;
+}
+
+t2s2_status tt_round(Ctx& cx, DevTT& x, double tol, int rmax) {
+  const int d = x.d;
+  if (d == 1) return T2S2_OK;
+  T2S2_TRY(tt_orth_right(cx, x));
+  double nrm;
+  T2S2_TRY(core_norm(cx, x.c[0], x.core_elems(0), &nrm));
+  if (nrm == 0.0) {
+    for (int k = 0; k < d; ++k) {
+      x.r[k] = 1;
+      T2S2_TRY(dev_fill(cx, x.c[k], x.m[k], 0.0));
+    }
+    x.r[d] = 1;
+    return T2S2_OK;
+  }
+  const double delta = tol * nrm / std::sqrt((double)(d - 1));
+  for (int k = 0; k + 1 < d; ++k) {
+    const int rk = x.r[k], mk_ = x.m[k], rk1 = x.r[k + 1];
+    const int rows = rk * mk_;
+    const int mn = x.m[k + 1], rn = x.r[k + 2];
+    size_t mark = cx.ar->mark();
+    const int kk = std::min(rows, rk1);
+    double* U = aget<double>(cx, (size_t)kk * kk);
+    double* s = aget<double>(cx, (size_t)kk);
+    double* V = aget<double>(cx, (size_t)rk1 * kk);
+    double* Q = aget<double>(cx, (size_t)rows * rk1);
+    double* R = aget<double>(cx, (size_t)rk1 * rk1);
+    double* SV = aget<double>(cx, (size_t)kk * rk1);
+    double* P = aget<double>(cx, (size_t)kk * mn * rn);
+    if (!U || !s || !V || !Q || !R || !SV || !P) return T2S2_ENOMEM;
+    if (rk1 > kSmallMax || kk > kSmallMax) return T2S2_EINVAL;
+    if (rows >= rk1) {
+      T2S2_TRY(qr_tall(cx, x.c[k], rows, rk1, Q, R));
+      T2S2_TRY(jacobi_svd(R, rk1, rk1, U, s, V, nullptr, cx.st));
+    } else {
+      T2S2_TRY(jacobi_svd(x.c[k], rows, rk1, U, s, V, nullptr, cx.st));
+    }
+    T2S2_CUDA_TRY(cudaMemcpyAsync(cx.hbuf, s, sizeof(double) * kk, cudaMemcpyDeviceToHost, cx.st));
+    T2S2_CUDA_TRY(cudaStreamSynchronize(cx.st));
+    const int rn_new = trunc_rank(cx.hbuf, kk, delta, rmax);
+    // core k <- Q U[:, :rn_new]  (or U[:, :rn_new] when the unfolding is wide)
+    if (rows >= rk1) {
+      T2S2_TRY(gemm_ex<double>(cx, rows, rn_new, rk1, false, false, 1.0, Q, rk1, U, kk, 0.0, x.c[k], rn_new));
+    } else {
+      // U is rows x kk with kk = rows; take its first rn_new columns
+      T2S2_CUDA_TRY(cudaMemcpy2DAsync(x.c[k], sizeof(double) * rn_new, U, sizeof(double) * kk,
+                                      sizeof(double) * rn_new, rows, cudaMemcpyDeviceToDevice, cx.st));
+    }
+    // core k+1 <- diag(s) V^T [:rn_new] x_1 core k+1
+    T2S2_TRY(dev_sv_t(cx, SV, s, V, rn_new, rk1, kk));
+    T2S2_TRY(gemm_ex<double>(cx, rn_new, mn * rn, rk1, false, false, 1.0, SV, rk1, x.c[k + 1], mn * rn, 0.0, P, mn * rn));
+    T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k + 1], P, sizeof(double) * rn_new * mn * rn, cudaMemcpyDeviceToDevice, cx.st));
+    x.r[k + 1] = rn_new;
+    cx.ar->release(mark);
+  }
+  return T2S2_OK;
+}
+
+}  // namespace t2s2

@@ -1,0 +1,99 @@
+// Device tensor trains and their FP64 arithmetic (Methods, "Tensor Train
+// representation"): orthogonalisation, rounding, norms, sums.
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+#include "gemm.h"
+#include "small.h"
+
+namespace t2s2 {
+
+// Bump allocator over one device buffer; `mark`/`release` give stack scoping.
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, top = 0, peak = 0;
+  void* get(size_t bytes) {
+    size_t a = (top + 255) & ~(size_t)255;
+    if (a + bytes > size) return nullptr;
+    top = a + bytes;
+    if (top > peak) peak = top;
+    return base + a;
+  }
+  size_t mark() const { return top; }
+  void release(size_t m) { top = m; }
+};
+
+struct DevTT {
+  int d = 0;
+  int m[T2S2_MAX_D] = {0};
+  int r[T2S2_MAX_D + 1] = {0};
+  double* c[T2S2_MAX_D] = {nullptr};
+  size_t cap[T2S2_MAX_D] = {0};
+  size_t core_elems(int k) const { return (size_t)r[k] * m[k] * r[k + 1]; }
+};
+
+struct Ctx {
+  cudaStream_t st = 0;
+  Arena* ar = nullptr;
+  double* hbuf = nullptr;   // pinned host scratch (>= 4 * kSmallMax doubles)
+  int* dstat = nullptr;     // device status word
+};
+
+template <typename T>
+inline T* aget(Ctx& cx, size_t n) {
+  return static_cast<T*>(cx.ar->get(n * sizeof(T)));
+}
+
+// Allocate a TT in the arena with given ranks (capacities = exact sizes).
+t2s2_status tt_alloc(Ctx& cx, DevTT& t, int d, const int* m, const int* r, int rcap);
+t2s2_status tt_copy(Ctx& cx, const DevTT& src, DevTT& dst);
+// z = alpha x + beta y as block-diagonal concatenation (ranks add); z in arena.
+t2s2_status tt_axpby(Ctx& cx, double alpha, const DevTT& x, double beta, const DevTT& y, DevTT& z);
+// In place: cores 1..d-1 right-orthonormal (rows), weight in core 0.
+t2s2_status tt_orth_right(Ctx& cx, DevTT& x);
+// In place: cores 0..d-2 left-orthonormal (columns), weight in core d-1.
+t2s2_status tt_orth_left(Ctx& cx, DevTT& x);
+// In place rounding with ||x - rndg(x)|| <= tol ||x|| (cap rmax <= 0: none).
+t2s2_status tt_round(Ctx& cx, DevTT& x, double tol, int rmax);
+// ||x||_F of a TT already right-orthogonalised (norm of core 0).
+t2s2_status core_norm(Ctx& cx, const double* v, size_t n, double* out);
+// ||x||_F for any TT (works on a copy).
+t2s2_status tt_norm(Ctx& cx, const DevTT& x, double* out);
+
+// Dense helpers used by the solver.
+// W (rows x cols, rows >= cols) = Q R, Q orthonormal columns (shifted CholeskyQR3).
+t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, double* R);
+// W (rows x cols, rows <= cols) = L Q, Q orthonormal rows.
+t2s2_status lq_wide(Ctx& cx, const double* W, int rows, int cols, double* Q, double* L);
+// Smallest r >= 1 with sqrt(sum_{j >= r} s_j^2) <= delta, capped by rmax (> 0).
+int trunc_rank(const double* s, int n, double delta, int rmax);
+
+template <typename T>
+inline t2s2_status gemm_ex(Ctx& cx, int M, int N, int K, bool tA, bool tB, T alpha, const T* A,
+                           long lda, const T* B, long ldb, T beta, T* C, long ldc, int batch = 1,
+                           long sA = 0, long sB = 0, long sC = 0) {
+  Gemm<T> g;
+  g.M = M; g.N = N; g.K = K; g.tA = tA; g.tB = tB; g.alpha = alpha; g.beta = beta;
+  g.A = A; g.lda = lda; g.sA = sA; g.B = B; g.ldb = ldb; g.sB = sB;
+  g.C = C; g.ldc = ldc; g.sC = sC; g.batch = batch;
+  size_t need = gemm_workspace(g);
+  size_t mk = cx.ar->mark();
+  T* ws = need ? aget<T>(cx, need) : nullptr;
+  t2s2_status s = gemm(g, ws, ws ? need : 0, cx.st);
+  cx.ar->release(mk);
+  return s;
+}
+
+// Elementwise kernels
+t2s2_status dev_scale_copy(Ctx& cx, double* dst, const double* src, size_t n, double alpha);
+t2s2_status dev_fill(Ctx& cx, double* dst, size_t n, double v);
+t2s2_status dev_axpy(Ctx& cx, double* dst, const double* src, size_t n, double beta);
+t2s2_status dev_identity(Ctx& cx, double* dst, int n);
+// dst (rd0 x m x rd1) block at (a0, b0) = alpha * src (ra x m x rb)
+t2s2_status dev_copy_block(Ctx& cx, double* dst, int rd0, int rd1, int a0, int b0,
+                           const double* src, int ra, int m, int rb, double alpha);
+// M[i][j] = s[i] * V[j][i] for i < r, j < q (V: q x ldv)
+t2s2_status dev_sv_t(Ctx& cx, double* M, const double* s, const double* V, int r, int q, int ldv);
+
+}  // namespace t2s2

@@ -1,0 +1,167 @@
+"""GPU parity: 1D matrices, TT apply, rounding, norms and residuals against the oracle.
+
+Tolerances: FP64 everywhere; apply and norms match to 1e-12 relative (a few
+ulps times the contraction length), rounding is compared through the full
+tensors (gauges differ) against its own error bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import operator as O
+from oracle import tt as OT
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2506_04732_gb300 as pkg
+    torch.cuda.set_device(0)
+    return pkg
+
+
+def _op(T, p):
+    from paper_2506_04732_gb300 import problem as P
+    return P.build_operator(p), O.build(p)
+
+
+CASES = [W.config0(), W.config1(d=3, n=10), W.config1(d=4, n=33), W.config3(0), W.config3(5),
+         W.config2(d=3, n=64)]
+
+
+@pytest.mark.parametrize("p", CASES, ids=lambda p: p.name)
+def test_nodes_and_matrices_match_oracle(T, p):
+    op, ops = _op(T, p)
+    for k in range(p.d):
+        x, eta = op.nodes(k)
+        assert np.max(np.abs(x - ops[k].x)) < 1e-14
+        assert np.max(np.abs(eta - ops[k].eta)) < 1e-13
+        Rt, Lt = op.matrices(k)
+        assert np.max(np.abs(Rt - ops[k].Rt)) < 1e-11 * max(1, np.abs(ops[k].Rt).max())
+        assert np.max(np.abs(Lt - ops[k].Lt)) < 1e-11 * np.abs(ops[k].Lt).max()
+
+
+def test_plain_switch(T):
+    p = W.config0()
+    p.plain_sc = True
+    op, ops = _op(T, p)
+    x, eta = op.nodes(1)
+    assert np.allclose(eta, x[1:-1], atol=0, rtol=0)
+
+
+APPLY = [
+    (3, 14, [1, 3, 4, 1]),
+    (6, 30, [1, 5, 7, 20, 9, 3, 1]),      # ragged ranks, 2m = 60 < 64 rows
+    (4, 31, [1, 33, 70, 65, 1]),          # ranks beyond one 64-wide tile
+    (5, 46, [1, 16, 16, 16, 16, 1]),      # 2m = 92: two row tiles
+    (2, 62, [1, 40, 1]),
+    (1, 20, [1, 1]),
+]
+
+
+@pytest.mark.parametrize("d,m,r", APPLY)
+@pytest.mark.parametrize("cm,co", [(0.0, 1.0), (1.0, -0.05), (1.0, 0.5)])
+def test_apply_matches_oracle(T, d, m, r, cm, co):
+    p = W.config1(d=d, n=m + 2, ratio=3e-3)
+    op, ops = _op(T, p)
+    x = W.random_tt(d, m, r, seed=d * 100 + m)
+    tx = T.TT.from_cores(x)
+    ty = T.TT.empty(tx.m, 2 * max(r))
+    T.t2s2_apply(op, tx, ty, c_mass=cm, c_op=co)
+    assert ty.r == [1] + [2 * v for v in r[1:-1]] + [1]
+    ref = OT.matvec(O.ttm_cores(ops, cm, co), x)
+    # cores are built exactly, so compare core by core
+    for a, b in zip(ty.cores(), ref):
+        assert a.shape == b.shape
+        assert np.max(np.abs(a - b)) <= 1e-12 * max(1.0, np.abs(b).max())
+
+
+def test_apply_host_buffers(T):
+    p = W.config1(d=4, n=20)
+    op, ops = _op(T, p)
+    x = W.random_tt(4, 18, [1, 3, 5, 2, 1], seed=3)
+    tx = T.TT.from_cores(x, device="cpu")
+    ty = T.TT.empty(tx.m, 10, device="cpu")
+    T.t2s2_apply(op, tx, ty)
+    ref = OT.matvec(O.ttm_cores(ops), x)
+    assert OT.diff_norm(ty.cores(), ref) <= 1e-13 * OT.norm(ref)
+
+
+@pytest.mark.parametrize("d,m,r,tol", [(3, 14, [1, 6, 9, 1], 1e-10), (5, 30, [1, 12, 20, 17, 8, 1], 1e-6),
+                                       (4, 62, [1, 40, 80, 40, 1], 1e-8), (6, 8, [1, 8, 30, 40, 30, 8, 1], 1e-4),
+                                       (2, 5, [1, 3, 1], 1e-12)])
+def test_round_error_bound_and_ranks(T, d, m, r, tol):
+    p = W.config1(d=d, n=m + 2)
+    op, _ = _op(T, p)
+    # a TT with redundant rank: sum of a low-rank TT and a small perturbation
+    base = W.random_tt(d, m, [1] + [min(v, 4) for v in r[1:-1]] + [1], seed=7)
+    noise = W.random_tt(d, m, r, seed=8)
+    x = OT.add(base, OT.scale(noise, 1e-3))
+    tx = T.TT.from_cores(x)
+    T.t2s2_round(op, tx, tol)
+    y = tx.cores()
+    err = OT.diff_norm(y, x) / OT.norm(x)
+    assert err <= tol * (1 + 1e-8)
+    # ranks agree with the oracle's rounding except at singular-value ties
+    ref = OT.round_tt(x, tol)
+    for a, b in zip(OT.ranks(y), OT.ranks(ref)):
+        assert abs(a - b) <= 1
+    assert OT.diff_norm(y, ref) <= 2 * tol * OT.norm(x)
+
+
+def test_round_with_cap(T):
+    p = W.config1(d=4, n=22)
+    op, _ = _op(T, p)
+    x = W.random_tt(4, 20, [1, 12, 15, 10, 1], seed=9)
+    tx = T.TT.from_cores(x)
+    T.t2s2_round(op, tx, 1e-14, rmax=5)
+    assert max(tx.r) <= 5
+    ref = OT.round_tt(x, 1e-14, 5)
+    assert OT.diff_norm(tx.cores(), ref) <= 1e-8 * OT.norm(x)
+
+
+def test_round_exact_low_rank(T):
+    # duplicated rank-1 cores (rank 2 by construction) round back to rank 1
+    p = W.config1(d=5, n=12)
+    op, _ = _op(T, p)
+    rng = np.random.default_rng(1)
+    x = [rng.standard_normal((1, 10, 1)) for _ in range(5)]
+    xx = OT.add(x, OT.scale(x, 0.5))
+    tx = T.TT.from_cores(xx)
+    T.t2s2_round(op, tx, 1e-12)
+    assert tx.r == [1] * 6
+    assert OT.diff_norm(tx.cores(), OT.scale(x, 1.5)) <= 1e-13 * OT.norm(x)
+
+
+def test_norm_and_residual(T):
+    p = W.config1(d=4, n=18)
+    op, ops = _op(T, p)
+    x = W.random_tt(4, 16, [1, 4, 6, 3, 1], seed=11)
+    b = W.random_tt(4, 16, [1, 2, 2, 2, 1], seed=12)
+    tx, tb = T.TT.from_cores(x), T.TT.from_cores(b)
+    assert abs(T.t2s2_norm(op, tx) - OT.norm(x)) <= 1e-13 * OT.norm(x)
+    res = T.t2s2_residual(op, tb, tx)
+    ref = OT.diff_norm(b, OT.matvec(O.ttm_cores(ops), x)) / OT.norm(b)
+    assert abs(res - ref) <= 1e-12 * ref
+    res2 = T.t2s2_residual(op, tb, tx, c_mass=1.0, c_op=0.01)
+    ref2 = OT.diff_norm(b, OT.matvec(O.ttm_cores(ops, 1.0, 0.01), x)) / OT.norm(b)
+    assert abs(res2 - ref2) <= 1e-12 * ref2
+
+
+def test_errors_are_status_codes(T):
+    with pytest.raises(T.T2S2Error) as e:
+        T.t2s2_build_operator(3, [2, 5, 5], [1, 1, 1], 0.1)
+    assert e.value.status == 1
+    with pytest.raises(T.T2S2Error):
+        T.t2s2_build_operator(3, [5, 5, 5], [1, 1, 1], -0.1)
+    p = W.config1(d=3, n=10)
+    op, _ = _op(T, p)
+    x = T.TT.from_cores(W.random_tt(3, 8, [1, 4, 4, 1], seed=1))
+    small = T.TT.empty(x.m, 2)           # too small for rank 8 output
+    with pytest.raises(T.T2S2Error) as e:
+        T.t2s2_apply(op, x, small)
+    assert e.value.status == 2
