@@ -189,6 +189,25 @@ t2s2_status t2s2_cn_step(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax
 t2s2_status t2s2_be_step(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax,
                          t2s2_precision prec, void* stream, t2s2_solve_info* info);
 
+/* ---- diagnostics ---------------------------------------------------------
+ * Kernel families for tracing: 0 GEMM (SIMT contractions), 1 TT apply,
+ * 2 local solve, 3 small factorisations (Cholesky, Jacobi SVD), 4 elementwise.
+ */
+
+/* Number of CUDA kernels this library has launched in this process. */
+long long t2s2_kernel_launches(void);
+
+/* Clear the per-family counters and turn event timing on (1) or off (0).
+ * While on, every launch is bracketed by two CUDA events on its stream. */
+t2s2_status t2s2_trace(int enable);
+
+/* Totals since the last t2s2_trace call for one family: launches, summed
+ * event time in ms, algorithmic FLOPs and algorithmic bytes (operands read
+ * once, results written once).  Synchronises on the recorded events.
+ * Errors: T2S2_EINVAL for an unknown family. */
+t2s2_status t2s2_trace_read(int family, long long* launches, double* ms, double* flops,
+                            double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

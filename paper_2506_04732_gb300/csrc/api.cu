@@ -238,13 +238,20 @@ t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op*
     std::copy(D.Rinv.begin(), D.Rinv.end(), host.begin() + off + 2 * mm);
     std::copy(D.B.begin(), D.B.end(), host.begin() + off + 3 * mm);
     for (int i = 0; i < m; ++i) host[off + 4 * mm + (size_t)i * m + i] = 1.0;
-    std::copy(D.H.begin(), D.H.end(), host.begin() + off + 5 * mm);
-    std::copy(D.W.begin(), D.W.end(), host.begin() + off + 6 * mm);
+    std::copy(D.Tr.begin(), D.Tr.end(), host.begin() + off + 5 * mm);
+    std::copy(D.Ti.begin(), D.Ti.end(), host.begin() + off + 6 * mm);
+    std::copy(D.Zr.begin(), D.Zr.end(), host.begin() + off + 7 * mm);
+    std::copy(D.Zi.begin(), D.Zi.end(), host.begin() + off + 8 * mm);
     off += kMatsPerDim * mm;
   }
+  std::vector<float> hostf(host.begin(), host.end());
   cudaError_t e = cudaMalloc(&op->dmat, sizeof(double) * total);
   if (e != cudaSuccess) { delete op; return T2S2_ENOMEM; }
+  e = cudaMalloc(&op->fmat, sizeof(float) * total);
+  if (e != cudaSuccess) { t2s2_op_destroy(op); return T2S2_ENOMEM; }
   e = cudaMemcpyAsync(op->dmat, host.data(), sizeof(double) * total, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(op->fmat, hostf.data(), sizeof(float) * total, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMallocHost(&op->hbuf, sizeof(double) * 4096);
   if (e == cudaSuccess) e = cudaMalloc(&op->dstat, sizeof(int) * 64);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -261,8 +268,11 @@ t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op*
     op->dRinv[k] = base + 2 * mm;
     op->dB[k] = base + 3 * mm;
     op->dI[k] = base + 4 * mm;
-    op->dH[k] = base + 5 * mm;
-    op->dW[k] = base + 6 * mm;
+    op->dTr[k] = base + 5 * mm;
+    op->dTi[k] = base + 6 * mm;
+    op->dZr[k] = base + 7 * mm;
+    op->dZi[k] = base + 8 * mm;
+    for (int j = 0; j < kMatsPerDim; ++j) op->fptr[j][k] = op->fmat + offs[k] + j * mm;
   }
   *out = op;
   return T2S2_OK;
@@ -271,6 +281,7 @@ t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op*
 t2s2_status t2s2_op_destroy(t2s2_op op) {
   if (!op) return T2S2_OK;
   if (op->dmat) cudaFree(op->dmat);
+  if (op->fmat) cudaFree(op->fmat);
   if (op->arena.base) cudaFree(op->arena.base);
   if (op->hbuf) cudaFreeHost(op->hbuf);
   if (op->dstat) cudaFree(op->dstat);

@@ -7,8 +7,9 @@
 #include "tt.h"
 
 // Per dimension the device holds kMatsPerDim m x m FP64 matrices:
-// Rt, Lt, Rt^{-1}, B = Rt^{-1} Lt, I, H (Hessenberg form of B), W (its basis).
-constexpr int kMatsPerDim = 7;
+// Rt, Lt, Rt^{-1}, B = Rt^{-1} Lt, I, and the complex Schur form B = Z T Z^H
+// as Re T, Im T, Re Z, Im Z.
+constexpr int kMatsPerDim = 9;
 
 struct t2s2_op_s {
   int device = 0;
@@ -20,10 +21,10 @@ struct t2s2_op_s {
   std::vector<t2s2::Dim1D> dims;
   double* dmat = nullptr;
   double *dRt[T2S2_MAX_D] = {nullptr}, *dLt[T2S2_MAX_D] = {nullptr}, *dRinv[T2S2_MAX_D] = {nullptr},
-         *dB[T2S2_MAX_D] = {nullptr}, *dI[T2S2_MAX_D] = {nullptr}, *dH[T2S2_MAX_D] = {nullptr},
-         *dW[T2S2_MAX_D] = {nullptr};
-  float* fmat = nullptr;  // FP32 copies of B, H, W for the mixed-precision inner solve
-  float *fB[T2S2_MAX_D] = {nullptr}, *fH[T2S2_MAX_D] = {nullptr}, *fW[T2S2_MAX_D] = {nullptr};
+         *dB[T2S2_MAX_D] = {nullptr}, *dI[T2S2_MAX_D] = {nullptr}, *dTr[T2S2_MAX_D] = {nullptr},
+         *dTi[T2S2_MAX_D] = {nullptr}, *dZr[T2S2_MAX_D] = {nullptr}, *dZi[T2S2_MAX_D] = {nullptr};
+  float* fmat = nullptr;  // FP32 copies of all of the above, same layout
+  float* fptr[kMatsPerDim][T2S2_MAX_D] = {{nullptr}};
   t2s2::Arena arena;
   double* hbuf = nullptr;  // pinned host scratch
   int* dstat = nullptr;    // device status words

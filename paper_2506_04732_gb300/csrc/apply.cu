@@ -13,6 +13,7 @@
 // All d cores go in one launch; the zero block of middle cores is written by
 // the S-row tiles.
 #include "apply.h"
+#include "trace.h"
 
 namespace t2s2 {
 
@@ -124,13 +125,18 @@ __global__ void __launch_bounds__(NT) apply_kernel(ApplyBatch p, TileMap tm) {
 t2s2_status apply_fp64(const ApplyBatch& p, cudaStream_t st) {
   TileMap tm;
   int total = 0;
+  double fl = 0.0, by = 0.0;
   for (int k = 0; k < p.ncores; ++k) {
     tm.start[k] = total;
     const ApplyCore& c = p.c[k];
     total += c.ra * cdiv(2 * c.m, BM) * cdiv(c.rb, BN);
+    fl += 2.0 * (2.0 * c.m) * c.m * (double)c.ra * c.rb;
+    const int ny = (c.kind == kApplyMiddle) ? 4 : ((c.kind == kApplySingle) ? 1 : 2);
+    by += 8.0 * ((double)c.ra * c.m * c.rb * (1 + ny) + 2.0 * c.m * c.m);
   }
   tm.start[p.ncores] = total;
   if (total == 0) return T2S2_OK;
+  TraceScope ts(kTrApply, st, fl, by);
   apply_kernel<<<total, NT, 0, st>>>(p, tm);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;

@@ -3,6 +3,7 @@
 // K staged through shared memory in slices of 16.  Used for FP64 work, whose
 // throughput on sm_103 is bounded by the DFMA pipe rather than by memory.
 #include "gemm.h"
+#include "trace.h"
 
 namespace t2s2 {
 
@@ -147,11 +148,17 @@ t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st) {
   }
   if (g.batch * (long)splits > 65535L) return T2S2_EINVAL;
   dim3 grid(cdiv(g.N, BN), cdiv(g.M, BM), g.batch * splits);
-  gemm_kernel<T><<<grid, NT, 0, st>>>(g, splits, std::max(kc, 1), ws);
+  {
+    const double fl = 2.0 * g.M * g.N * (double)g.K * g.batch;
+    const double by = (double)sizeof(T) * g.batch * ((double)g.M * g.K + (double)g.K * g.N + 2.0 * g.M * g.N);
+    TraceScope ts(kTrGemm, st, fl, by);
+    gemm_kernel<T><<<grid, NT, 0, st>>>(g, splits, std::max(kc, 1), ws);
+  }
   T2S2_CUDA_TRY(cudaGetLastError());
   if (splits > 1) {
     long total = (long)g.batch * g.M * g.N;
     int blocks = (int)std::min<long>(cdiv(total, 256), 4L * kNumSMs);
+    TraceScope ts(kTrElem, st, 0.0, (double)sizeof(T) * total * (splits + 2));
     splitk_reduce<T><<<blocks, 256, 0, st>>>(g, splits, ws);
     T2S2_CUDA_TRY(cudaGetLastError());
   }

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 
 namespace t2s2 {
@@ -233,6 +234,96 @@ void hessenberg(int m, double* B, double* W) {
   delete[] v;
 }
 
+// Complex Schur form A = Z T Z^H (T upper triangular, Z unitary) of a real
+// m x m matrix: Householder reduction to Hessenberg form, then single-shift
+// QR sweeps (bulge chasing with Givens rotations) with Wilkinson shifts and
+// deflation of negligible subdiagonal entries.  Unitary transformations only,
+// so the form is backward stable however non-normal A is.
+bool complex_schur(int m, const double* A, std::complex<double>* T, std::complex<double>* Z) {
+  typedef std::complex<double> C;
+  std::vector<double> H(A, A + (size_t)m * m), W((size_t)m * m);
+  hessenberg(m, H.data(), W.data());
+  for (size_t e = 0; e < (size_t)m * m; ++e) {
+    T[e] = C(H[e], 0.0);
+    Z[e] = C(W[e], 0.0);
+  }
+  auto t = [&](int i, int j) -> C& { return T[(size_t)i * m + j]; };
+  auto z = [&](int i, int j) -> C& { return Z[(size_t)i * m + j]; };
+  const double eps = 2.220446049250313e-16;
+  int hi = m - 1, iter = 0, total = 0;
+  while (hi > 0) {
+    int l = hi;
+    while (l > 0) {
+      double sub = std::abs(t(l, l - 1));
+      double diag = std::abs(t(l - 1, l - 1)) + std::abs(t(l, l));
+      if (sub <= eps * (diag > 0 ? diag : 1.0)) {
+        t(l, l - 1) = 0.0;
+        break;
+      }
+      --l;
+    }
+    if (l == hi) {  // 1 x 1 block converged
+      --hi;
+      iter = 0;
+      continue;
+    }
+    if (++total > 100 * m) return false;
+    ++iter;
+    C mu;
+    if (iter % 11 == 0) {  // exceptional shift
+      mu = t(hi, hi) + C(0.75 * std::abs(t(hi, hi - 1)), 0.0);
+    } else {
+      C a = t(hi - 1, hi - 1), b = t(hi - 1, hi), c = t(hi, hi - 1), d = t(hi, hi);
+      C half = 0.5 * (a - d);
+      C disc = std::sqrt(half * half + b * c);
+      C l1 = 0.5 * (a + d) + disc, l2 = 0.5 * (a + d) - disc;
+      mu = (std::abs(l1 - d) < std::abs(l2 - d)) ? l1 : l2;
+    }
+    C x = t(l, l) - mu, y = t(l + 1, l);
+    for (int k = l; k < hi; ++k) {
+      double ax = std::abs(x), ay = std::abs(y);
+      double r = std::hypot(ax, ay);
+      double c;
+      C s;
+      if (r == 0.0) {
+        c = 1.0;
+        s = 0.0;
+      } else if (ax == 0.0) {
+        c = 0.0;
+        s = std::conj(y) / ay;
+      } else {
+        c = ax / r;
+        s = (x / ax) * std::conj(y) / r;
+      }
+      // rows k, k+1 from column max(l, k-1): G = [[c, s], [-conj(s), c]]
+      for (int j = std::max(l, k - 1); j < m; ++j) {
+        C u = t(k, j), v = t(k + 1, j);
+        t(k, j) = c * u + s * v;
+        t(k + 1, j) = -std::conj(s) * u + c * v;
+      }
+      // columns k, k+1 (right multiplication by G^H), rows up to min(k+2, hi)
+      int rmax = std::min(k + 2, hi);
+      for (int i = 0; i <= rmax; ++i) {
+        C u = t(i, k), v = t(i, k + 1);
+        t(i, k) = c * u + std::conj(s) * v;
+        t(i, k + 1) = -s * u + c * v;
+      }
+      for (int i = 0; i < m; ++i) {
+        C u = z(i, k), v = z(i, k + 1);
+        z(i, k) = c * u + std::conj(s) * v;
+        z(i, k + 1) = -s * u + c * v;
+      }
+      if (k + 2 <= hi) {
+        x = t(k + 1, k);
+        y = t(k + 2, k);
+      }
+    }
+  }
+  for (int i = 1; i < m; ++i)
+    for (int j = 0; j < i; ++j) t(i, j) = 0.0;
+  return true;
+}
+
 bool build_dimension(int n, double eps, double beta, int plain, Dim1D* out) {
   const int N = n - 1, m = n - 2;
   out->n = n;
@@ -258,9 +349,18 @@ bool build_dimension(int n, double eps, double beta, int plain, Dim1D* out) {
       for (int l = 0; l < m; ++l) s += out->Rinv[(size_t)i * m + l] * out->Lt[(size_t)l * m + j];
       out->B[(size_t)i * m + j] = s;
     }
-  out->H = out->B;
-  out->W.assign((size_t)m * m, 0.0);
-  hessenberg(m, out->H.data(), out->W.data());
+  std::vector<std::complex<double>> T((size_t)m * m), Z((size_t)m * m);
+  if (!complex_schur(m, out->B.data(), T.data(), Z.data())) return false;
+  out->Tr.resize((size_t)m * m);
+  out->Ti.resize((size_t)m * m);
+  out->Zr.resize((size_t)m * m);
+  out->Zi.resize((size_t)m * m);
+  for (size_t e = 0; e < (size_t)m * m; ++e) {
+    out->Tr[e] = T[e].real();
+    out->Ti[e] = T[e].imag();
+    out->Zr[e] = Z[e].real();
+    out->Zi[e] = Z[e].imag();
+  }
   return true;
 }
 

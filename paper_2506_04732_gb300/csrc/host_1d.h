@@ -1,5 +1,6 @@
 // Host-side FP64 construction of the per-dimension collocation matrices.
 #pragma once
+#include <complex>
 #include <vector>
 
 namespace t2s2 {
@@ -12,8 +13,8 @@ struct Dim1D {
   std::vector<double> Lt;    // m x m: beta l_i'(eta_j) - eps l_i''(eta_j)
   std::vector<double> Rinv;  // Rt^{-1}
   std::vector<double> B;     // Rt^{-1} Lt
-  std::vector<double> H;     // upper Hessenberg form of B: H = W^T B W
-  std::vector<double> W;     // orthogonal Hessenberg basis
+  std::vector<double> Tr, Ti;  // complex Schur form of B: B = Z T Z^H, T upper triangular
+  std::vector<double> Zr, Zi;  // unitary Schur basis
 };
 
 void gll_points(int N, double* x);
@@ -23,6 +24,7 @@ void lagrange_matrices(int N, const double* x, int npts, const double* t, double
                        double* D2);
 bool invert(int m, double* A);
 void hessenberg(int m, double* B, double* W);
+bool complex_schur(int m, const double* A, std::complex<double>* T, std::complex<double>* Z);
 bool build_dimension(int n, double eps, double beta, int plain, Dim1D* out);
 
 }  // namespace t2s2

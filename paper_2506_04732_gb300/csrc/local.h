@@ -1,0 +1,36 @@
+// Local solves of the alternating TT solver (see local.cu).
+#pragma once
+#include "common.cuh"
+
+namespace t2s2 {
+
+constexpr int kLocalMaxM = 128;        // largest mode size handled by the local solver
+constexpr int kLocalMaxRestart = 40;   // largest GMRES restart length
+
+template <typename T>
+struct LocalProblem {
+  int ra = 0, m = 0, rb = 0;           // local core shape; N = ra * m * rb
+  const double* PL = nullptr;          // ra x ra left interface (Kronecker-sum part)
+  const double* PR = nullptr;          // rb x rb right interface
+  const double* Bp = nullptr;          // m x m  B' = c_op B + shift I
+  const T *Tr = nullptr, *Ti = nullptr, *Zr = nullptr, *Zi = nullptr;  // Schur B = Z T Z^H
+  double c_op = 1.0, shift = 0.0;
+  const T* rhs = nullptr;              // N
+  T* x = nullptr;                      // N, initial guess in, solution out
+  T* work = nullptr;                   // local_work_elems(N, mr)
+  double* part = nullptr;              // 2 * team * (kLocalMaxRestart + 2)
+  double tol_rel = 1e-10;              // stop at ||rhs - K x|| <= tol_rel ||rhs||
+  int maxit = 400, mr = 30, team = 0;  // team = 0: pick the number of CTAs
+  int* iters_out = nullptr;            // total GMRES iterations
+  double* res_out = nullptr;           // [final residual norm, ||rhs||]
+};
+
+template <typename T>
+size_t local_work_elems(long N, int mr);
+
+constexpr size_t kLocalPartElems = 2 * 160 * (kLocalMaxRestart + 2);
+
+template <typename T>
+t2s2_status local_gmres(const LocalProblem<T>& P, cudaStream_t st);
+
+}  // namespace t2s2

@@ -7,6 +7,7 @@
 //    (Hestenes' method, columns orthogonalised by plane rotations in a
 //    round-robin ordering; singular values sorted in decreasing order).
 #include "small.h"
+#include "trace.h"
 
 #include <cmath>
 
@@ -23,30 +24,40 @@ __global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __rest
   extern __shared__ double sm[];
   double* A = sm;           // c x c
   double* Iv = sm + c * c;  // c x c
-  __shared__ double shift;
+  __shared__ double shift, tau;
   __shared__ int bad;
   const int t = threadIdx.x;
   for (int e = t; e < c * c; e += blockDim.x) A[e] = G[e];
   if (t == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < c; ++i) tr += G[i * c + i];
+    double tr = 0.0, mx = 0.0;
+    for (int i = 0; i < c; ++i) {
+      tr += G[i * c + i];
+      mx = fmax(mx, G[i * c + i]);
+    }
     shift = shift_rel * tr;
-    if (!(tr > 0.0)) shift = 1e-300;
+    // pivots below tau are roundoff-level directions (the matrix is only
+    // positive semidefinite): their column of L is zeroed, so W = L Q still
+    // holds and the matching row / column of Q is zero
+    tau = 64.0 * 1.1102230246251565e-16 * (mx + shift);
     bad = 0;
   }
   __syncthreads();
   for (int i = t; i < c; i += blockDim.x) A[i * c + i] += shift;
   __syncthreads();
-  // right-looking Cholesky, lower triangle
+  // right-looking semidefinite Cholesky, lower triangle
   for (int j = 0; j < c; ++j) {
-    if (t == 0) {
-      double v = A[j * c + j];
-      if (!(v > 0.0)) { bad = 1; v = 1e-300; }
-      A[j * c + j] = sqrt(v);
-    }
+    const double v = A[j * c + j];
+    const bool zero = !(v > tau);
     __syncthreads();
-    double djj = A[j * c + j];
+    if (zero) {
+      for (int i = j + t; i < c; i += blockDim.x) A[i * c + j] = 0.0;
+      if (t == 0) bad = 1;
+      __syncthreads();
+      continue;
+    }
+    const double djj = sqrt(v);
     for (int i = j + 1 + t; i < c; i += blockDim.x) A[i * c + j] /= djj;
+    if (t == 0) A[j * c + j] = djj;
     __syncthreads();
     int rem = c - j - 1;
     for (int e = t; e < rem * rem; e += blockDim.x) {
@@ -55,14 +66,20 @@ __global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __rest
     }
     __syncthreads();
   }
-  // inverse of lower triangular L: column k solves L x = e_k (one thread per column)
+  // pseudo-inverse of the lower-triangular L: column k solves L x = e_k with
+  // x_i = 0 wherever L_ii = 0 (one thread per column)
   for (int e = t; e < c * c; e += blockDim.x) Iv[e] = 0.0;
   __syncthreads();
   for (int k = t; k < c; k += blockDim.x) {
     for (int i = k; i < c; ++i) {
+      const double dii = A[i * c + i];
+      if (dii == 0.0) {
+        Iv[i * c + k] = 0.0;
+        continue;
+      }
       double s = (i == k) ? 1.0 : 0.0;
       for (int l = k; l < i; ++l) s -= A[i * c + l] * Iv[l * c + k];
-      Iv[i * c + k] = s / A[i * c + i];
+      Iv[i * c + k] = s / dii;
     }
   }
   __syncthreads();
@@ -197,6 +214,7 @@ t2s2_status chol_inv(const double* G, int c, double shift_rel, double* L, double
                                        2 * kSmallMax * kSmallMax * (int)sizeof(double)));
     attr = true;
   }
+  TraceScope ts(kTrSmall, st, (double)c * c * c, 8.0 * 3 * c * c);
   chol_inv_kernel<<<1, kThreads, smem, st>>>(G, c, shift_rel, L, Linv, status);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
@@ -215,6 +233,7 @@ t2s2_status jacobi_svd(const double* A, int p, int q, double* U, double* s, doub
         (int)((2 * kSmallMax * kSmallMax + kSmallMax) * sizeof(double))));
     attr = true;
   }
+  TraceScope ts(kTrSmall, st, 6.0 * 8 * (double)rows * cols * cols, 8.0 * (2.0 * p * q + q * q));
   jacobi_svd_kernel<<<1, kThreads, smem, st>>>(A, p, q, transpose, U, s, V, sweeps);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;

@@ -1,32 +1,512 @@
-// Alternating TT solver (AMEn) and time steps.
+// Alternating TT solver (AMEn) and the Crank-Nicolson / backward-Euler steps.
+//
+// The paper solves its collocation systems with AMEn (Results,
+// "Superconsistent Stabilization", Fig. 6), sweeping over the cores and solving
+// a local problem at each.  This implementation works on the equivalent
+// Kronecker-sum system: with M = Rt_1 x ... x Rt_d,
+//     M^{-1} (c_mass M + c_op A) = sum_k I x ... x B'_k x ... x I,
+//     B'_k = c_op Rt_k^{-1} Lt_k + (c_mass / d) I,      rhs f = M^{-1} b,
+// so that, with orthonormal left/right frames, each local operator is the
+// three-term Kronecker sum P_L (+) B'_k (+) P_R (local.cu).  Per core and sweep:
+// local right-hand side, local GMRES solve, SVD truncation at tol/sqrt(d),
+// enrichment of the new core with the residual projected onto a rank-4 TT z
+// (Dolgov & Savostyanov's AMEn, cited by the paper), orthogonalisation, and
+// the interface updates -- all as GEMM chains on the device.  After each sweep
+// the true residual ||b - (c_mass M + c_op A) x|| / ||b|| of the ORIGINAL
+// collocation system is evaluated in FP64 and decides convergence.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <random>
+#include <vector>
+
 #include "api_internal.h"
+#include "local.h"
 
 void t2s2_op_s::free_solver_buffers() {}
 
 namespace t2s2 {
+
+namespace {
+
+t2s2_status mode1(Ctx& cx, const double* P, int rn, int ro, const double* X, int m, int rb, double* Y,
+                  double alpha = 1.0, double beta = 0.0) {
+  return gemm_ex<double>(cx, rn, m * rb, ro, false, false, alpha, P, ro, X, (long)m * rb, beta, Y,
+                         (long)m * rb);
+}
+t2s2_status mode2(Ctx& cx, const double* B, int m, const double* X, int ra, int rb, double* Y,
+                  double alpha = 1.0, double beta = 0.0) {
+  return gemm_ex<double>(cx, m, rb, m, false, false, alpha, B, m, X, rb, beta, Y, rb, ra, 0,
+                         (long)m * rb, (long)m * rb);
+}
+// Y[a,i,c] = sum_b X[a,i,b] Q[c,b]
+t2s2_status mode3(Ctx& cx, const double* X, int ra, int m, int ro, const double* Q, int rn, double* Y,
+                  double alpha = 1.0, double beta = 0.0) {
+  return gemm_ex<double>(cx, ra * m, rn, ro, false, true, alpha, X, ro, Q, ro, beta, Y, rn);
+}
+// out[b][c] = sum_{a,i} U[a,i,b] T[a,i,c]
+t2s2_status contract_left(Ctx& cx, const double* U, int ra, int m, int rb, const double* T, int rc,
+                          double* out) {
+  return gemm_ex<double>(cx, rb, rc, ra * m, true, false, 1.0, U, rb, T, rc, 0.0, out, rc);
+}
+// out[a][c] = sum_{i,b} U[a,i,b] T[c,i,b]
+t2s2_status contract_right(Ctx& cx, const double* U, int ra, int m, int rb, const double* T, int rc,
+                           double* out) {
+  return gemm_ex<double>(cx, ra, rc, m * rb, false, true, 1.0, U, (long)m * rb, T, (long)m * rb, 0.0,
+                         out, rc);
+}
+t2s2_status d2d(Ctx& cx, double* dst, const double* src, size_t n) {
+  if (n == 0) return T2S2_OK;
+  T2S2_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, cx.st));
+  return T2S2_OK;
+}
+t2s2_status set_scalar(Ctx& cx, double* dst, double v) { return dev_fill(cx, dst, 1, v); }
+
+struct Amen {
+  t2s2_op op = nullptr;
+  Ctx* cx = nullptr;
+  int d = 0, kick = 4, rcap = 0, rmax = 0, mmax = 0, R = 0;
+  double ltol = 0.0;
+  DevTT x, f, z;
+  double* Bp[T2S2_MAX_D] = {nullptr};
+  double *PL[T2S2_MAX_D + 1], *FL[T2S2_MAX_D + 1], *ZIL[T2S2_MAX_D + 1], *ZBL[T2S2_MAX_D + 1],
+      *ZFL[T2S2_MAX_D + 1];
+  double *PR[T2S2_MAX_D + 1], *FR[T2S2_MAX_D + 1], *ZIR[T2S2_MAX_D + 1], *ZBR[T2S2_MAX_D + 1],
+      *ZFR[T2S2_MAX_D + 1];
+  double* tmp[12] = {nullptr};
+  size_t tmp_elems = 0;
+  double* gm_work = nullptr;
+  double* gm_part = nullptr;
+  int* gm_iters = nullptr;
+  double* gm_res = nullptr;
+  double* svals = nullptr;
+  long long local_iters = 0;
+  double c_op = 1.0, c_mass = 0.0;
+  int gm_restart = 40, gm_maxit = 600;
+
+  static size_t bytes_needed(int d, const int* m, int rcap, int rfmax, int kick, int mr) {
+    int mm = 0;
+    for (int k = 0; k < d; ++k) mm = std::max(mm, m[k]);
+    size_t R = std::max(std::max(rcap, rfmax), kick);
+    size_t core = R * mm * R;
+    size_t s = 0;
+    s += 3 * (size_t)d * core;                  // x, f, z
+    s += 10 * (size_t)(d + 1) * R * R;          // interfaces
+    s += 12 * core;                             // temporaries
+    s += (size_t)(mr + 3) * rcap * mm * rcap;   // GMRES basis
+    s += kLocalPartElems + 64;
+    s += (size_t)d * mm * mm;                   // B'
+    // residual evaluation: apply output, sum, orthogonalisation temporaries
+    size_t rr = (size_t)rfmax + 2 * rcap;
+    s += 4 * (size_t)d * rr * mm * rr + 16 * rr * rr;
+    // SVD / QR temporaries inside orth / qr_tall
+    s += 8 * core + 16 * (size_t)kSmallMax * kSmallMax;
+    return s * sizeof(double) + ((size_t)16 << 20);
+  }
+
+  t2s2_status init(t2s2_op o, Ctx& c, const DevTT& b, const DevTT& x0, double cm, double co, double tol,
+                   int rmax_) {
+    op = o;
+    cx = &c;
+    d = op->d;
+    c_mass = cm;
+    c_op = co;
+    rmax = rmax_;
+    rcap = rmax + kick;
+    if (rcap > kSmallMax) return T2S2_EINVAL;
+    ltol = tol / std::sqrt((double)d);
+    int rfmax = 1;
+    for (int k = 0; k <= d; ++k) rfmax = std::max(rfmax, b.r[k]);
+    if (rfmax > kSmallMax) return T2S2_EINVAL;
+    for (int k = 0; k < d; ++k) mmax = std::max(mmax, op->m[k]);
+    if (mmax > kLocalMaxM) return T2S2_EINVAL;
+    R = std::max(std::max(rcap, rfmax), kick);
+    const size_t core = (size_t)R * mmax * R;
+    // B'_k = c_op B_k + (c_mass / d) I
+    for (int k = 0; k < d; ++k) {
+      const int m = op->m[k];
+      Bp[k] = aget<double>(c, (size_t)m * m);
+      if (!Bp[k]) return T2S2_ENOMEM;
+      T2S2_TRY(dev_scale_copy(c, Bp[k], op->dB[k], (size_t)m * m, c_op));
+      T2S2_TRY(dev_axpy(c, Bp[k], op->dI[k], (size_t)m * m, c_mass / d));
+    }
+    // transformed right-hand side f = M^{-1} b (mode-k products with Rt_k^{-1})
+    T2S2_TRY(tt_alloc(c, f, d, op->m, b.r, 0));
+    for (int k = 0; k < d; ++k)
+      T2S2_TRY(mode2(c, op->dRinv[k], op->m[k], b.c[k], b.r[k], b.r[k + 1], f.c[k]));
+    // x: copy of the initial guess with capacity rcap
+    int rx[T2S2_MAX_D + 1];
+    for (int k = 0; k <= d; ++k) rx[k] = x0.r[k];
+    T2S2_TRY(tt_alloc(c, x, d, op->m, rx, R));
+    T2S2_TRY(tt_copy(c, x0, x));
+    int rx0 = 1;
+    for (int k = 0; k <= d; ++k) rx0 = std::max(rx0, x0.r[k]);
+    if (rx0 > rcap) T2S2_TRY(tt_round(c, x, 1e-15, rcap));
+    // z: random rank-kick TT (bounded by the mode-size products)
+    int rz[T2S2_MAX_D + 1];
+    rz[0] = rz[d] = 1;
+    for (int k = 1; k < d; ++k) {
+      double left = 1, right = 1;
+      for (int j = 0; j < k; ++j) left *= op->m[j];
+      for (int j = k; j < d; ++j) right *= op->m[j];
+      rz[k] = (int)std::min<double>(kick, std::min(left, right));
+    }
+    T2S2_TRY(tt_alloc(c, z, d, op->m, rz, kick));
+    {
+      std::mt19937_64 gen(0x5eedULL + d);
+      std::normal_distribution<double> nd(0.0, 1.0);
+      for (int k = 0; k < d; ++k) {
+        std::vector<double> h(z.core_elems(k));
+        for (auto& v : h) v = nd(gen);
+        T2S2_CUDA_TRY(cudaMemcpyAsync(z.c[k], h.data(), h.size() * sizeof(double),
+                                      cudaMemcpyHostToDevice, c.st));
+        T2S2_CUDA_TRY(cudaStreamSynchronize(c.st));
+      }
+    }
+    T2S2_TRY(tt_orth_right(c, z));
+    for (int k = 0; k <= d; ++k) {
+      double** arrs[10] = {PL, FL, ZIL, ZBL, ZFL, PR, FR, ZIR, ZBR, ZFR};
+      for (auto a : arrs) {
+        a[k] = aget<double>(c, (size_t)R * R);
+        if (!a[k]) return T2S2_ENOMEM;
+      }
+    }
+    tmp_elems = core;
+    for (auto& t : tmp) {
+      t = aget<double>(c, core);
+      if (!t) return T2S2_ENOMEM;
+    }
+    gm_work = aget<double>(c, local_work_elems<double>((long)rcap * mmax * rcap, gm_restart));
+    gm_part = aget<double>(c, kLocalPartElems);
+    gm_iters = reinterpret_cast<int*>(aget<double>(c, 2));
+    gm_res = aget<double>(c, 4);
+    svals = aget<double>(c, kSmallMax);
+    if (!gm_work || !gm_part || !gm_iters || !gm_res || !svals) return T2S2_ENOMEM;
+    return T2S2_OK;
+  }
+
+  // Right interfaces for bonds d-1 .. 1 from right-orthonormal x (and z).
+  t2s2_status right_interfaces() {
+    Ctx& c = *cx;
+    T2S2_TRY(set_scalar(c, PR[d], 0.0));
+    T2S2_TRY(set_scalar(c, FR[d], 1.0));
+    T2S2_TRY(set_scalar(c, ZIR[d], 1.0));
+    T2S2_TRY(set_scalar(c, ZBR[d], 0.0));
+    T2S2_TRY(set_scalar(c, ZFR[d], 1.0));
+    for (int k = d - 1; k >= 1; --k) {
+      const int m = op->m[k];
+      const int ra = x.r[k], rb = x.r[k + 1], fa = f.r[k], fb = f.r[k + 1], za = z.r[k], zb = z.r[k + 1];
+      const double *X = x.c[k], *F = f.c[k], *Z = z.c[k];
+      double *T1 = tmp[0], *T2 = tmp[1], *BX = tmp[2];
+      // PR[k] = X (X x_3 PR[k+1] + B' x_2 X)
+      T2S2_TRY(mode2(c, Bp[k], m, X, ra, rb, BX));
+      T2S2_TRY(d2d(c, T1, BX, (size_t)ra * m * rb));
+      T2S2_TRY(mode3(c, X, ra, m, rb, PR[k + 1], rb, T1, 1.0, 1.0));
+      T2S2_TRY(contract_right(c, X, ra, m, rb, T1, ra, PR[k]));
+      // FR[k] = X (F x_3 FR[k+1])
+      T2S2_TRY(mode3(c, F, fa, m, fb, FR[k + 1], rb, T2));
+      T2S2_TRY(contract_right(c, X, ra, m, rb, T2, fa, FR[k]));
+      // ZIR[k] = Z (X x_3 ZIR[k+1])
+      T2S2_TRY(mode3(c, X, ra, m, rb, ZIR[k + 1], zb, T1));
+      T2S2_TRY(contract_right(c, Z, za, m, zb, T1, ra, ZIR[k]));
+      // ZBR[k] = Z (X x_3 ZBR[k+1] + (B' X) x_3 ZIR[k+1])
+      T2S2_TRY(mode3(c, X, ra, m, rb, ZBR[k + 1], zb, T1));
+      T2S2_TRY(mode3(c, BX, ra, m, rb, ZIR[k + 1], zb, T1, 1.0, 1.0));
+      T2S2_TRY(contract_right(c, Z, za, m, zb, T1, ra, ZBR[k]));
+      // ZFR[k] = Z (F x_3 ZFR[k+1])
+      T2S2_TRY(mode3(c, F, fa, m, fb, ZFR[k + 1], zb, T2));
+      T2S2_TRY(contract_right(c, Z, za, m, zb, T2, fa, ZFR[k]));
+    }
+    return T2S2_OK;
+  }
+
+  t2s2_status left_boundary() {
+    Ctx& c = *cx;
+    T2S2_TRY(set_scalar(c, PL[0], 0.0));
+    T2S2_TRY(set_scalar(c, FL[0], 1.0));
+    T2S2_TRY(set_scalar(c, ZIL[0], 1.0));
+    T2S2_TRY(set_scalar(c, ZBL[0], 0.0));
+    T2S2_TRY(set_scalar(c, ZFL[0], 1.0));
+    return T2S2_OK;
+  }
+
+  t2s2_status local_solve(int k, double* rhs, double* X) {
+    Ctx& c = *cx;
+    LocalProblem<double> P;
+    P.ra = x.r[k];
+    P.m = op->m[k];
+    P.rb = x.r[k + 1];
+    P.PL = PL[k];
+    P.PR = PR[k + 1];
+    P.Bp = Bp[k];
+    P.Tr = op->dTr[k];
+    P.Ti = op->dTi[k];
+    P.Zr = op->dZr[k];
+    P.Zi = op->dZi[k];
+    P.c_op = c_op;
+    P.shift = c_mass / d;
+    P.rhs = rhs;
+    P.x = X;
+    P.work = gm_work;
+    P.part = gm_part;
+    P.tol_rel = ltol;
+    P.maxit = gm_maxit;
+    P.mr = gm_restart;
+    P.iters_out = gm_iters;
+    P.res_out = gm_res;
+    return local_gmres<double>(P, c.st);
+  }
+
+  // One forward sweep k = 0 .. d-1.
+  t2s2_status sweep() {
+    Ctx& c = *cx;
+    T2S2_TRY(right_interfaces());
+    T2S2_TRY(left_boundary());
+    for (int k = 0; k < d; ++k) {
+      const int m = op->m[k];
+      const int ra = x.r[k], rb = x.r[k + 1], fa = f.r[k], fb = f.r[k + 1], za = z.r[k], zb = z.r[k + 1];
+      const double* F = f.c[k];
+      double *rhs = tmp[3], *X = tmp[4], *T1 = tmp[0], *T2 = tmp[1];
+      // local rhs = FL[k] x_1 F x_3 FR[k+1]
+      T2S2_TRY(mode1(c, FL[k], ra, fa, F, m, fb, T1));
+      T2S2_TRY(mode3(c, T1, ra, m, fb, FR[k + 1], rb, rhs));
+      T2S2_TRY(d2d(c, X, x.c[k], (size_t)ra * m * rb));
+      T2S2_TRY(local_solve(k, rhs, X));
+      if (k == d - 1) {
+        T2S2_TRY(d2d(c, x.c[k], X, (size_t)ra * m * rb));
+        T2S2_CUDA_TRY(cudaMemcpyAsync(c.hbuf + 8, gm_iters, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+        T2S2_CUDA_TRY(cudaStreamSynchronize(c.st));
+        int it;
+        std::memcpy(&it, c.hbuf + 8, sizeof(int));
+        local_iters += it;
+        break;
+      }
+      // --- truncation: X (rows x rb) = U S V^T
+      const int rows = ra * m;
+      double *Qx = tmp[5], *Ux = tmp[6], *Vx = tmp[7], *Rx = tmp[8];
+      int kk;
+      if (rows >= rb) {
+        T2S2_TRY(qr_tall(c, X, rows, rb, Qx, Rx));
+        T2S2_TRY(jacobi_svd(Rx, rb, rb, Ux, svals, Vx, nullptr, c.st));
+        kk = rb;
+      } else {
+        T2S2_TRY(jacobi_svd(X, rows, rb, Ux, svals, Vx, nullptr, c.st));
+        kk = rows;
+      }
+      T2S2_CUDA_TRY(cudaMemcpyAsync(c.hbuf, svals, sizeof(double) * kk, cudaMemcpyDeviceToHost, c.st));
+      T2S2_CUDA_TRY(cudaMemcpyAsync(c.hbuf + kSmallMax, gm_iters, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+      T2S2_CUDA_TRY(cudaStreamSynchronize(c.st));
+      {
+        int it;
+        std::memcpy(&it, c.hbuf + kSmallMax, sizeof(int));
+        local_iters += it;
+      }
+      double snorm = 0.0;
+      for (int j = 0; j < kk; ++j) snorm += c.hbuf[j] * c.hbuf[j];
+      snorm = std::sqrt(snorm);
+      const int rk = trunc_rank(c.hbuf, kk, ltol * snorm, rmax);
+      double *U = tmp[9], *SV = tmp[10], *Xt = tmp[11];
+      if (rows >= rb) {
+        T2S2_TRY(gemm_ex<double>(c, rows, rk, rb, false, false, 1.0, Qx, rb, Ux, kk, 0.0, U, rk));
+      } else {
+        T2S2_CUDA_TRY(cudaMemcpy2DAsync(U, sizeof(double) * rk, Ux, sizeof(double) * kk,
+                                        sizeof(double) * rk, rows, cudaMemcpyDeviceToDevice, c.st));
+      }
+      T2S2_TRY(dev_sv_t(c, SV, svals, Vx, rk, rb, kk));
+      T2S2_TRY(gemm_ex<double>(c, rows, rb, rk, false, false, 1.0, U, rk, SV, rb, 0.0, Xt, rb));
+      // --- enrichment directions: residual on (x-left) x m x (z-right)
+      double *BX = tmp[5], *Y1 = tmp[6], *res = tmp[7], *zres = tmp[8];
+      T2S2_TRY(mode2(c, Bp[k], m, Xt, ra, rb, BX));
+      T2S2_TRY(d2d(c, Y1, BX, (size_t)ra * m * rb));
+      T2S2_TRY(mode1(c, PL[k], ra, ra, Xt, m, rb, Y1, 1.0, 1.0));
+      T2S2_TRY(mode1(c, FL[k], ra, fa, F, m, fb, T1));
+      T2S2_TRY(mode3(c, T1, ra, m, fb, ZFR[k + 1], zb, res));
+      T2S2_TRY(mode3(c, Y1, ra, m, rb, ZIR[k + 1], zb, res, -1.0, 1.0));
+      T2S2_TRY(mode3(c, Xt, ra, m, rb, ZBR[k + 1], zb, res, -1.0, 1.0));
+      // --- z update: residual on (z-left) x m x (z-right)
+      T2S2_TRY(mode1(c, ZFL[k], za, fa, F, m, fb, T1));
+      T2S2_TRY(mode3(c, T1, za, m, fb, ZFR[k + 1], zb, zres));
+      T2S2_TRY(mode1(c, ZBL[k], za, ra, Xt, m, rb, T2));
+      T2S2_TRY(mode1(c, ZIL[k], za, ra, BX, m, rb, T2, 1.0, 1.0));
+      T2S2_TRY(mode3(c, T2, za, m, rb, ZIR[k + 1], zb, zres, -1.0, 1.0));
+      T2S2_TRY(mode1(c, ZIL[k], za, ra, Xt, m, rb, T2));
+      T2S2_TRY(mode3(c, T2, za, m, rb, ZBR[k + 1], zb, zres, -1.0, 1.0));
+      {
+        double* Rz = tmp[1];
+        double* Qz = tmp[0];
+        T2S2_TRY(qr_tall(c, zres, za * m, zb, Qz, Rz));
+        T2S2_TRY(d2d(c, z.c[k], Qz, (size_t)za * m * zb));
+      }
+      // --- new core: orthonormal basis of [U | res]
+      int cols = rk + zb;
+      double* Q = tmp[2];
+      int rn;
+      if (rows >= cols) {
+        double* cat = tmp[1];
+        T2S2_CUDA_TRY(cudaMemcpy2DAsync(cat, sizeof(double) * cols, U, sizeof(double) * rk,
+                                        sizeof(double) * rk, rows, cudaMemcpyDeviceToDevice, c.st));
+        T2S2_CUDA_TRY(cudaMemcpy2DAsync(cat + rk, sizeof(double) * cols, res, sizeof(double) * zb,
+                                        sizeof(double) * zb, rows, cudaMemcpyDeviceToDevice, c.st));
+        double* Rq = tmp[8];
+        T2S2_TRY(qr_tall(c, cat, rows, cols, Q, Rq));
+        rn = cols;
+      } else {
+        T2S2_TRY(dev_identity(c, Q, rows));
+        rn = rows;
+      }
+      // next core: (Q^T U SV) x_1 x[k+1]
+      {
+        const int mn = op->m[k + 1], rnn = x.r[k + 2];
+        double* C = tmp[6];
+        double* CS = tmp[7];
+        double* P = tmp[0];
+        T2S2_TRY(gemm_ex<double>(c, rn, rk, rows, true, false, 1.0, Q, rn, U, rk, 0.0, C, rk));
+        T2S2_TRY(gemm_ex<double>(c, rn, rb, rk, false, false, 1.0, C, rk, SV, rb, 0.0, CS, rb));
+        if ((size_t)rn * mn * rnn > x.cap[k + 1] || (size_t)ra * m * rn > x.cap[k]) return T2S2_ENOMEM;
+        T2S2_TRY(mode1(c, CS, rn, rb, x.c[k + 1], mn, rnn, P));
+        T2S2_TRY(d2d(c, x.c[k + 1], P, (size_t)rn * mn * rnn));
+        T2S2_TRY(d2d(c, x.c[k], Q, (size_t)rows * rn));
+        x.r[k + 1] = rn;
+      }
+      // --- left interfaces for bond k+1
+      {
+        const double* Qc = x.c[k];
+        const double* Z = z.c[k];
+        double *T3 = tmp[3], *BQ = tmp[4];
+        T2S2_TRY(mode2(c, Bp[k], m, Qc, ra, rn, BQ));
+        T2S2_TRY(d2d(c, T3, BQ, (size_t)ra * m * rn));
+        T2S2_TRY(mode1(c, PL[k], ra, ra, Qc, m, rn, T3, 1.0, 1.0));
+        T2S2_TRY(contract_left(c, Qc, ra, m, rn, T3, rn, PL[k + 1]));
+        T2S2_TRY(mode1(c, FL[k], ra, fa, F, m, fb, T3));
+        T2S2_TRY(contract_left(c, Qc, ra, m, rn, T3, fb, FL[k + 1]));
+        T2S2_TRY(mode1(c, ZIL[k], za, ra, Qc, m, rn, T3));
+        T2S2_TRY(contract_left(c, Z, za, m, zb, T3, rn, ZIL[k + 1]));
+        T2S2_TRY(mode1(c, ZBL[k], za, ra, Qc, m, rn, T3));
+        T2S2_TRY(mode1(c, ZIL[k], za, ra, BQ, m, rn, T3, 1.0, 1.0));
+        T2S2_TRY(contract_left(c, Z, za, m, zb, T3, rn, ZBL[k + 1]));
+        T2S2_TRY(mode1(c, ZFL[k], za, fa, F, m, fb, T3));
+        T2S2_TRY(contract_left(c, Z, za, m, zb, T3, fb, ZFL[k + 1]));
+      }
+    }
+    return T2S2_OK;
+  }
+};
+
+t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c_mass, double c_op,
+                       double tol, int rmax, int max_sweeps, t2s2_precision prec, t2s2_solve_info* info) {
+  (void)prec;
+  Amen am;
+  T2S2_TRY(am.init(op, cx, b, xio, c_mass, c_op, tol, rmax));
+  T2S2_TRY(tt_orth_right(cx, am.x));
+  double bnorm = -1.0, res = 0.0;
+  T2S2_TRY(residual_impl(op, cx, b, am.x, c_mass, c_op, false, &res, &bnorm));
+  int sweeps = 0;
+  const char* ev = std::getenv("T2S2_VERBOSE");
+  const bool verbose = ev && ev[0] == '1';
+  if (verbose) fprintf(stderr, "[t2s2] solve d=%d c_mass=%g c_op=%g tol=%g rmax=%d initial residual %.3e\n",
+                       op->d, c_mass, c_op, tol, rmax, res);
+  while (res > tol && sweeps < max_sweeps) {
+    T2S2_TRY(am.sweep());
+    ++sweeps;
+    T2S2_TRY(residual_impl(op, cx, b, am.x, c_mass, c_op, false, &res, &bnorm));
+    if (verbose) {
+      double rt = 0.0;
+      T2S2_TRY(residual_impl(op, cx, am.f, am.x, c_mass, c_op, true, &rt, nullptr));
+      fprintf(stderr, "[t2s2] sweep %d residual %.3e (transformed %.3e) ranks", sweeps, res, rt);
+      for (int k = 0; k <= op->d; ++k) fprintf(stderr, " %d", am.x.r[k]);
+      fprintf(stderr, " local_iters %lld\n", am.local_iters);
+    }
+    if (res <= tol) break;
+    T2S2_TRY(tt_orth_right(cx, am.x));
+  }
+  // copy out
+  for (int k = 0; k < op->d; ++k)
+    if (am.x.core_elems(k) > xio.cap[k]) return T2S2_ENOMEM;
+  T2S2_TRY(tt_copy(cx, am.x, xio));
+  if (info) {
+    info->residual = res;
+    info->sweeps = sweeps;
+    int mr = 1;
+    for (int k = 0; k <= op->d; ++k) mr = std::max(mr, am.x.r[k]);
+    info->max_rank = mr;
+    info->refinements = 0;
+    info->local_iters = am.local_iters;
+  }
+  return res <= tol ? T2S2_OK : T2S2_ENOCONV;
+}
+
+}  // namespace
+
 t2s2_status apply_dispatch(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass,
                            double c_op, t2s2_precision prec) {
   (void)prec;
   return apply_op(op, cx, x, y, c_mass, c_op, false);
 }
+
+static t2s2_status solve_entry(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double c_mass, double c_op,
+                               double tol, int rmax, int max_sweeps, t2s2_precision prec, void* stream,
+                               t2s2_solve_info* info) {
+  if (!op || !b || !x) return T2S2_EINVAL;
+  if (!(tol > 0.0) || rmax < 1 || max_sweeps < 0) return T2S2_EINVAL;
+  if (prec < T2S2_FP64 || prec > T2S2_BF16_REFINE) return T2S2_EINVAL;
+  T2S2_TRY(check_tt(op, b));
+  T2S2_TRY(check_tt(op, x));
+  int rfmax = 1;
+  for (int k = 0; k <= op->d; ++k) rfmax = std::max(rfmax, b->r[k]);
+  size_t need = Amen::bytes_needed(op->d, op->m, rmax + 4, rfmax, 4, 40) + 2 * (tt_bytes(b) + tt_bytes(x));
+  T2S2_TRY(ensure_arena(op, need));
+  Ctx cx = make_ctx(op, stream);
+  DevTT db, dx;
+  T2S2_TRY(bind_tt(cx, b, db, true));
+  T2S2_TRY(bind_tt(cx, x, dx, true));
+  t2s2_status st = solve_impl(op, cx, db, dx, c_mass, c_op, tol, rmax, max_sweeps, prec, info);
+  if (st != T2S2_OK && st != T2S2_ENOCONV) return st;
+  t2s2_status st2 = unbind_tt(cx, dx, x);
+  return st2 != T2S2_OK ? st2 : st;
+}
+
+static t2s2_status step_entry(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax, bool cn,
+                              t2s2_precision prec, void* stream, t2s2_solve_info* info) {
+  if (!op || !u || !(dt > 0.0) || !(tol > 0.0) || rmax < 1) return T2S2_EINVAL;
+  T2S2_TRY(check_tt(op, u));
+  const int d = op->d;
+  size_t need = Amen::bytes_needed(d, op->m, rmax + 4, 2 * (rmax + 4), 4, 40) + 8 * tt_bytes(u);
+  T2S2_TRY(ensure_arena(op, need));
+  Ctx cx = make_ctx(op, stream);
+  DevTT du;
+  T2S2_TRY(bind_tt(cx, u, du, true));
+  // rhs = rndg((M - dt/2 A) u)  (CN)  or  rndg(M u)  (BE)
+  int r2[T2S2_MAX_D + 1];
+  for (int k = 0; k <= d; ++k) r2[k] = (k == 0 || k == d) ? 1 : 2 * du.r[k];
+  DevTT rhs;
+  T2S2_TRY(tt_alloc(cx, rhs, d, du.m, r2, 0));
+  T2S2_TRY(apply_op(op, cx, du, rhs, 1.0, cn ? -0.5 * dt : 0.0, false));
+  T2S2_TRY(tt_round(cx, rhs, tol, rmax));
+  const double co = cn ? 0.5 * dt : dt;
+  t2s2_status st = solve_impl(op, cx, rhs, du, 1.0, co, tol, rmax, 20, prec, info);
+  if (st != T2S2_OK && st != T2S2_ENOCONV) return st;
+  t2s2_status st2 = unbind_tt(cx, du, u);
+  return st2 != T2S2_OK ? st2 : st;
+}
+
 }  // namespace t2s2
+
+using namespace t2s2;
 
 extern "C" {
 t2s2_status t2s2_solve(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double c_mass, double c_op,
                        double tol, int rmax, int max_sweeps, t2s2_precision prec, void* stream,
                        t2s2_solve_info* info) {
-  (void)op; (void)b; (void)x; (void)c_mass; (void)c_op; (void)tol; (void)rmax; (void)max_sweeps;
-  (void)prec; (void)stream; (void)info;
-  return T2S2_ENOTIMPL;
+  return solve_entry(op, b, x, c_mass, c_op, tol, rmax, max_sweeps, prec, stream, info);
 }
 t2s2_status t2s2_cn_step(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax,
                          t2s2_precision prec, void* stream, t2s2_solve_info* info) {
-  (void)op; (void)u; (void)dt; (void)tol; (void)rmax; (void)prec; (void)stream; (void)info;
-  return T2S2_ENOTIMPL;
+  return step_entry(op, u, dt, tol, rmax, true, prec, stream, info);
 }
 t2s2_status t2s2_be_step(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax,
                          t2s2_precision prec, void* stream, t2s2_solve_info* info) {
-  (void)op; (void)u; (void)dt; (void)tol; (void)rmax; (void)prec; (void)stream; (void)info;
-  return T2S2_ENOTIMPL;
+  return step_entry(op, u, dt, tol, rmax, false, prec, stream, info);
 }
 }

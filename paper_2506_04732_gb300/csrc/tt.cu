@@ -8,6 +8,7 @@
 // left orthogonalisation, then left-to-right truncated SVDs with threshold
 // tol ||x|| / sqrt(d-1) per unfolding.
 #include "tt.h"
+#include "trace.h"
 
 #include <algorithm>
 #include <cmath>
@@ -77,24 +78,24 @@ inline int blocks_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_
 
 t2s2_status dev_scale_copy(Ctx& cx, double* dst, const double* src, size_t n, double alpha) {
   if (n == 0) return T2S2_OK;
-  k_scale_copy<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n, alpha);
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * n); k_scale_copy<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n, alpha); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 t2s2_status dev_axpy(Ctx& cx, double* dst, const double* src, size_t n, double beta) {
   if (n == 0) return T2S2_OK;
-  k_axpy<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n, beta);
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 24.0 * n); k_axpy<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n, beta); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 t2s2_status dev_fill(Ctx& cx, double* dst, size_t n, double v) {
   if (n == 0) return T2S2_OK;
-  k_fill<<<blocks_for(n), 256, 0, cx.st>>>(dst, n, v);
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 8.0 * n); k_fill<<<blocks_for(n), 256, 0, cx.st>>>(dst, n, v); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 t2s2_status dev_identity(Ctx& cx, double* dst, int n) {
-  k_identity<<<blocks_for((size_t)n * n), 256, 0, cx.st>>>(dst, n);
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 8.0 * n * n); k_identity<<<blocks_for((size_t)n * n), 256, 0, cx.st>>>(dst, n); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
@@ -103,13 +104,13 @@ t2s2_status dev_copy_block(Ctx& cx, double* dst, int rd0, int rd1, int a0, int b
   (void)rd0;
   size_t n = (size_t)ra * m * rb;
   if (n == 0) return T2S2_OK;
-  k_copy_block<<<blocks_for(n), 256, 0, cx.st>>>(dst, rd0, rd1, a0, b0, src, ra, m, rb, alpha);
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * n); k_copy_block<<<blocks_for(n), 256, 0, cx.st>>>(dst, rd0, rd1, a0, b0, src, ra, m, rb, alpha); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 t2s2_status dev_sv_t(Ctx& cx, double* M, const double* s, const double* V, int r, int q, int ldv) {
   if (r * q == 0) return T2S2_OK;
-  k_sv_t<<<blocks_for((size_t)r * q), 256, 0, cx.st>>>(M, s, V, r, q, ldv);
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * r * q); k_sv_t<<<blocks_for((size_t)r * q), 256, 0, cx.st>>>(M, s, V, r, q, ldv); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
@@ -118,7 +119,7 @@ t2s2_status core_norm(Ctx& cx, const double* v, size_t n, double* out) {
   size_t mk = cx.ar->mark();
   double* d = aget<double>(cx, 1);
   if (!d) return T2S2_ENOMEM;
-  k_sumsq<<<1, 1024, 0, cx.st>>>(v, n, d);
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 8.0 * n); k_sumsq<<<1, 1024, 0, cx.st>>>(v, n, d); }
   T2S2_CUDA_TRY(cudaGetLastError());
   T2S2_CUDA_TRY(cudaMemcpyAsync(cx.hbuf, d, sizeof(double), cudaMemcpyDeviceToHost, cx.st));
   T2S2_CUDA_TRY(cudaStreamSynchronize(cx.st));
@@ -179,7 +180,7 @@ t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, dou
     cur = outs[pass];
   }
   // W = Q (L1 L2 L3)^T  ->  R = Lacc^T
-  k_transpose<<<blocks_for((size_t)c * c), 256, 0, cx.st>>>(R, Lacc, c, c);
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * c * c); k_transpose<<<blocks_for((size_t)c * c), 256, 0, cx.st>>>(R, Lacc, c, c); }
   T2S2_CUDA_TRY(cudaGetLastError());
   cx.ar->release(mk);
   return T2S2_OK;

@@ -165,3 +165,21 @@ def test_errors_are_status_codes(T):
     with pytest.raises(T.T2S2Error) as e:
         T.t2s2_apply(op, x, small)
     assert e.value.status == 2
+
+
+def test_rank_deficient_orthogonalisation_is_finite(T):
+    # TT sums whose stored ranks exceed their true ranks (x - x, 2x = x + x,
+    # b - A x with b = A x) must orthogonalise without NaN / Inf.
+    p = W.config1(d=4, n=14)
+    op, ops = _op(T, p)
+    x = W.random_tt(4, 12, [1, 3, 5, 2, 1], seed=21)
+    zero = OT.add(x, OT.scale(x, -1.0))
+    assert T.t2s2_norm(op, T.TT.from_cores(zero)) <= 1e-13 * OT.norm(x)
+    two = T.TT.from_cores(OT.add(x, x))
+    assert abs(T.t2s2_norm(op, two) - 2 * OT.norm(x)) <= 1e-13 * OT.norm(x)
+    T.t2s2_round(op, two, 1e-12)
+    assert OT.ranks(two.cores()) == OT.ranks(OT.round_tt(x, 1e-12))
+    assert OT.diff_norm(two.cores(), OT.scale(x, 2.0)) <= 1e-12 * OT.norm(x)
+    b = OT.matvec(O.ttm_cores(ops, 1.0, 0.3), x)
+    r = T.t2s2_residual(op, T.TT.from_cores(b), T.TT.from_cores(x), c_mass=1.0, c_op=0.3)
+    assert np.isfinite(r) and r <= 1e-13

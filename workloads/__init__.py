@@ -25,7 +25,7 @@ import math
 import numpy as np
 
 __all__ = ["Factor", "Term", "Problem", "config0", "config1", "config2",
-           "config3", "config4", "random_tt", "random_unit_vector",
+           "config3", "config4", "random_tt", "sine_problem", "random_unit_vector",
            "EDGE_LENGTH"]
 
 EDGE_LENGTH = 2.0
@@ -202,6 +202,15 @@ def config4(seed: int, d: int = 6, n: int = 32) -> Problem:
     p = np.concatenate([a, w, mu])
     return Problem(f"warm#{seed} d={d} n={n}", d, (n,) * d, beta, ratio * EDGE_LENGTH,
                    terms, tol=1e-8, rmax=20, max_sweeps=50, seed=seed, params=p)
+
+
+def sine_problem(d: int, n: int, ratio: float, seed: int = 5, tol: float = 1e-8,
+                 rmax: int = 12) -> Problem:
+    """Small well-resolved steady problem: u* = prod sin(pi(x+1)/2) + 0.5 prod sin(pi(x+1))."""
+    beta = random_unit_vector(d, np.random.default_rng(seed))
+    terms = [Term(1.0, (Factor("sine", m=1),) * d), Term(0.5, (Factor("sine", m=2),) * d)]
+    return Problem(f"sines d={d} n={n} ratio={ratio:g}", d, (n,) * d, beta, ratio * EDGE_LENGTH,
+                   terms, tol=tol, rmax=rmax, max_sweeps=30, seed=seed)
 
 
 def random_tt(d: int, n, ranks, seed: int, dtype=np.float64):
