@@ -8,10 +8,12 @@
 namespace t2s2 {
 
 namespace {
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
-template <typename T>
+// Tile of (16*TM) x (16*TN) outputs; 16 x 16 threads, each a TM x TN micro-tile.
+template <typename T, int TM, int TN>
 __global__ void __launch_bounds__(NT) gemm_kernel(Gemm<T> g, int splits, int kchunk, T* ws) {
+  constexpr int BM = 16 * TM, BN = 16 * TN;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int bz = blockIdx.z;
@@ -22,14 +24,13 @@ __global__ void __launch_bounds__(NT) gemm_kernel(Gemm<T> g, int splits, int kch
   const T* A = g.A + (long)b * g.sA;
   const T* B = g.B + (long)b * g.sB;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[4][4];
+  T acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0;
 
   for (int k0 = k_begin; k0 < k_end; k0 += BK) {
-    // load A tile: BM x BK elements of op(A)
     for (int e = threadIdx.x; e < BM * BK; e += NT) {
       int mm, kk;
       if (g.tA) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
@@ -49,26 +50,26 @@ __global__ void __launch_bounds__(NT) gemm_kernel(Gemm<T> g, int splits, int kch
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[4], bb[4];
+      T a[TM], bb[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
     }
     __syncthreads();
   }
   if (splits == 1) {
     T* C = g.C + (long)b * g.sC;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TM; ++i) {
       int gm = m0 + ty + 16 * i;
       if (gm >= g.M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < TN; ++j) {
         int gn = n0 + tx + 16 * j;
         if (gn >= g.N) continue;
         T* c = C + (long)gm * g.ldc + gn;
@@ -80,11 +81,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(Gemm<T> g, int splits, int kch
   } else {
     T* P = ws + ((long)sidx * g.batch + b) * (long)g.M * g.N;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TM; ++i) {
       int gm = m0 + ty + 16 * i;
       if (gm >= g.M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < TN; ++j) {
         int gn = n0 + tx + 16 * j;
         if (gn < g.N) P[(long)gm * g.N + gn] = acc[i][j];
       }
@@ -109,24 +110,45 @@ __global__ void splitk_reduce(Gemm<T> g, int splits, const T* ws) {
   }
 }
 
+inline int tile_code(int x) { return x <= 16 ? 1 : (x <= 32 ? 2 : 4); }
+
 template <typename T>
 int choose_splits(const Gemm<T>& g, int* kchunk) {
   if (g.K <= 0) {
     *kchunk = 0;
     return 1;
   }
+  const int BM = 16 * tile_code(g.M), BN = 16 * tile_code(g.N);
   long tiles = (long)cdiv(g.M, BM) * cdiv(g.N, BN) * g.batch;
+  // FP64 runs at 2 DFMA/clk/SM on this part: spread long-K products over all SMs
+  const long target = (sizeof(T) == 8) ? 2L * kNumSMs : kNumSMs;
   int splits = 1;
-  if (tiles < 2 * kNumSMs && g.K > 4 * BK) {
-    long want = (2 * kNumSMs + tiles - 1) / tiles;
-    long maxs = g.K / (4 * BK);
-    splits = (int)std::max(1L, std::min(std::min(want, maxs), 64L));
+  if (tiles < target && g.K > 2 * BK) {
+    long want = (target + tiles - 1) / tiles;
+    long maxs = g.K / (2 * BK);
+    splits = (int)std::max(1L, std::min(std::min(want, maxs), 128L));
   }
   int kc = cdiv(g.K, splits);
   kc = cdiv(kc, BK) * BK;
   splits = cdiv(g.K, kc);
   *kchunk = kc;
   return splits;
+}
+
+template <typename T, int TM, int TN>
+void launch_tile(const Gemm<T>& g, int splits, int kc, T* ws, cudaStream_t st) {
+  dim3 grid(cdiv(g.N, 16 * TN), cdiv(g.M, 16 * TM), g.batch * splits);
+  gemm_kernel<T, TM, TN><<<grid, NT, 0, st>>>(g, splits, std::max(kc, 1), ws);
+}
+
+template <typename T>
+void launch_any(const Gemm<T>& g, int splits, int kc, T* ws, cudaStream_t st) {
+  const int tm = tile_code(g.M), tn = tile_code(g.N);
+#define T2S2_TILE(a, b) if (tm == a && tn == b) { launch_tile<T, a, b>(g, splits, kc, ws, st); return; }
+  T2S2_TILE(1, 1) T2S2_TILE(1, 2) T2S2_TILE(1, 4)
+  T2S2_TILE(2, 1) T2S2_TILE(2, 2) T2S2_TILE(2, 4)
+  T2S2_TILE(4, 1) T2S2_TILE(4, 2) T2S2_TILE(4, 4)
+#undef T2S2_TILE
 }
 }  // namespace
 
@@ -147,12 +169,11 @@ t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st) {
     kc = g.K;
   }
   if (g.batch * (long)splits > 65535L) return T2S2_EINVAL;
-  dim3 grid(cdiv(g.N, BN), cdiv(g.M, BM), g.batch * splits);
   {
     const double fl = 2.0 * g.M * g.N * (double)g.K * g.batch;
     const double by = (double)sizeof(T) * g.batch * ((double)g.M * g.K + (double)g.K * g.N + 2.0 * g.M * g.N);
     TraceScope ts(kTrGemm, st, fl, by);
-    gemm_kernel<T><<<grid, NT, 0, st>>>(g, splits, std::max(kc, 1), ws);
+    launch_any<T>(g, splits, kc, ws, st);
   }
   T2S2_CUDA_TRY(cudaGetLastError());
   if (splits > 1) {

@@ -30,15 +30,11 @@ namespace {
 constexpr int NT = 256;
 constexpr int NW = NT / 32;
 
+// Vectors written during the kernel (basis, preconditioned vector, iterate)
+// are read with coherent loads; only launch-constant data may use __ldg.
 template <typename T>
-struct Ops;
-template <>
-struct Ops<double> {
-  static __device__ double ld(const double* p) { return __ldg(p); }
-};
-template <>
-struct Ops<float> {
-  static __device__ float ld(const float* p) { return __ldg(p); }
+struct Ops {
+  static __device__ T ld(const T* p) { return *p; }
 };
 
 // block-wide sum of nv values per thread (vals[0..nv-1]) into smem red[nv][NW]
@@ -59,238 +55,348 @@ __device__ void block_sum(double* vals, int nv, double* red) {
   __syncthreads();
 }
 
+// Each CTA owns a contiguous range of fibres (a, b) and all m elements of
+// each: the preconditioner then touches only the CTA's own data, and only the
+// matrix-vector product needs the whole vector.
 template <typename T>
 struct Team {
   LocalProblem<T> P;
-  long N;
+  long N, nf;
   int G, g;
-  long e0, e1;
+  long f0, f1;   // owned fibres
+  long nown;     // owned elements = (f1 - f0) * m
   cg::grid_group grid;
   __device__ Team(const LocalProblem<T>& p) : P(p), grid(cg::this_grid()) {
     N = (long)P.ra * P.m * P.rb;
+    nf = (long)P.ra * P.rb;
     G = gridDim.x;
     g = blockIdx.x;
-    long chunk = (N + G - 1) / G;
-    e0 = min(N, (long)g * chunk);
-    e1 = min(N, e0 + chunk);
+    long chunk = (nf + G - 1) / G;
+    f0 = min(nf, (long)g * chunk);
+    f1 = min(nf, f0 + chunk);
+    nown = (f1 - f0) * P.m;
   }
   __device__ void sync() { grid.sync(); }
+  // global element index of the k-th owned element (fibre fastest: coalesced in b)
+  __device__ long elem(long k) const {
+    const long nfl = f1 - f0;
+    const long f = f0 + k % nfl;
+    const int i = (int)(k / nfl);
+    const long a = f / P.rb, b = f % P.rb;
+    return (a * P.m + i) * P.rb + b;
+  }
 
   // y = K x on this CTA's elements (x complete in global memory)
   __device__ void matvec(const T* __restrict__ x, T* __restrict__ y) {
     const int ra = P.ra, m = P.m, rb = P.rb;
-    for (long e = e0 + threadIdx.x; e < e1; e += NT) {
+    for (long k = threadIdx.x; k < nown; k += NT) {
+      const long e = elem(k);
       int b = (int)(e % rb);
       long t = e / rb;
       int i = (int)(t % m);
       int a = (int)(t / m);
-      double s = 0.0;
+      // three independent accumulation chains (FP64 latency is long on this part)
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
       const double* pl = P.PL + (long)a * ra;
-      for (int p = 0; p < ra; ++p) s += pl[p] * (double)Ops<T>::ld(x + ((long)p * m + i) * rb + b);
+      for (int p = 0; p < ra; ++p) s0 = fma(pl[p], (double)Ops<T>::ld(x + ((long)p * m + i) * rb + b), s0);
       const double* bp = P.Bp + (long)i * m;
       const T* xa = x + (long)a * m * rb + b;
-      for (int j = 0; j < m; ++j) s += bp[j] * (double)Ops<T>::ld(xa + (long)j * rb);
+      for (int j = 0; j < m; ++j) s1 = fma(bp[j], (double)Ops<T>::ld(xa + (long)j * rb), s1);
       const double* pr = P.PR + (long)b * rb;
       const T* xi = x + ((long)a * m + i) * rb;
-      for (int q = 0; q < rb; ++q) s += pr[q] * (double)Ops<T>::ld(xi + q);
-      y[e] = (T)s;
+      for (int q = 0; q < rb; ++q) s2 = fma(pr[q], (double)Ops<T>::ld(xi + q), s2);
+      y[e] = (T)(s0 + s1 + s2);
     }
   }
 
-  // z = M^{-1} v over fibres (warp per fibre); v complete in global memory
-  __device__ void precond(const T* __restrict__ v, T* __restrict__ z, T* sm_re, T* sm_im) {
+  // z = M^{-1} v over the CTA's own fibres (warp per fibre), arithmetic in
+  // binary32: the preconditioner only steers the Krylov space (flexible GMRES
+  // keeps every z_j), so its precision does not limit the solution's accuracy,
+  // while binary32 runs the m-step triangular recurrences at full SIMT speed.
+  // Ttr/Tti: (c_op T)^T, Zr/Zi: Z, row stride ld.  scratch: per-warp 5 * kLocalMaxM floats.
+  __device__ void precond(const T* __restrict__ v, T* __restrict__ z, const float* Ttr,
+                          const float* Tti, const float* Zr, const float* Zi, int ld, float* scratch) {
     const int ra = P.ra, m = P.m, rb = P.rb;
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-    const long nf = (long)ra * rb;
-    T* vr = sm_re + w * kLocalMaxM;  // per-warp scratch (length m)
-    T* vi = sm_im + w * kLocalMaxM;
-    const T* Zr = P.Zr;
-    const T* Zi = P.Zi;
-    const T* Tr = P.Tr;
-    const T* Ti = P.Ti;
-    const T cop = (T)P.c_op;
-    for (long f = (long)g * NW + w; f < nf; f += (long)G * NW) {
+    float* sv = scratch + w * 5 * kLocalMaxM;  // fibre input
+    float* yr = sv + kLocalMaxM;               // solution of the triangular system
+    float* yi = yr + kLocalMaxM;
+    float* idr = yi + kLocalMaxM;              // reciprocal diagonal
+    float* idi = idr + kLocalMaxM;
+    for (long f = f0 + w; f < f1; f += NW) {
       const int a = (int)(f / rb), b = (int)(f % rb);
-      const T sig = (T)(P.PL[(long)a * ra + a] + P.PR[(long)b * rb + b] + P.shift);
+      const float sig = (float)(P.PL[(long)a * ra + a] + P.PR[(long)b * rb + b] + P.shift);
       const T* vf = v + (long)a * m * rb + b;
-      // vt = Z^H v : vt_i = sum_j conj(Z_ji) v_j
       for (int i = lane; i < m; i += 32) {
-        T sr = 0, si = 0;
-        for (int j = 0; j < m; ++j) {
-          T vj = Ops<T>::ld(vf + (long)j * rb);
-          sr += Ops<T>::ld(Zr + (long)j * m + i) * vj;
-          si -= Ops<T>::ld(Zi + (long)j * m + i) * vj;
-        }
-        vr[i] = sr;
-        vi[i] = si;
+        sv[i] = (float)vf[(long)i * rb];
+        float dr = Ttr[(long)i * ld + i] + sig, di = Tti[(long)i * ld + i];
+        float den = __frcp_rn(dr * dr + di * di);
+        idr[i] = dr * den;
+        idi[i] = -di * den;
       }
       __syncwarp();
-      // back substitution with (c_op T + sig I), column oriented
-      for (int i = m - 1; i >= 0; --i) {
-        T yr = 0, yi = 0;
-        if (lane == 0) {
-          T dr = cop * Ops<T>::ld(Tr + (long)i * m + i) + sig;
-          T di = cop * Ops<T>::ld(Ti + (long)i * m + i);
-          T den = dr * dr + di * di;
-          T nr = vr[i], ni = vi[i];
-          yr = (nr * dr + ni * di) / den;
-          yi = (ni * dr - nr * di) / den;
-          vr[i] = yr;
-          vi[i] = yi;
+      // vt = Z^H v, lane-owned entries i = lane + 32 s
+      float vr[4], vi[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        float sr = 0.f, si = 0.f;
+        if (i < m) {
+          for (int j = 0; j < m; ++j) {
+            const float vj = sv[j];
+            sr = fmaf(Zr[(long)j * ld + i], vj, sr);
+            si = fmaf(-Zi[(long)j * ld + i], vj, si);
+          }
         }
-        yr = __shfl_sync(0xffffffffu, yr, 0);
-        yi = __shfl_sync(0xffffffffu, yi, 0);
-        for (int j = lane; j < i; j += 32) {
-          T tr = cop * Ops<T>::ld(Tr + (long)j * m + i), ti = cop * Ops<T>::ld(Ti + (long)j * m + i);
-          vr[j] -= tr * yr - ti * yi;
-          vi[j] -= tr * yi + ti * yr;
-        }
-        __syncwarp();
+        vr[s] = sr;
+        vi[s] = si;
       }
+      // column-oriented back substitution with (c_op T + sig I)
+      for (int i = m - 1; i >= 0; --i) {
+        const int owner = i & 31, si_ = i >> 5;
+        float ar = 0.f, ai = 0.f;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (s == si_) { ar = vr[s]; ai = vi[s]; }
+        float cr = ar * idr[i] - ai * idi[i];
+        float ci = ar * idi[i] + ai * idr[i];
+        cr = __shfl_sync(0xffffffffu, cr, owner);
+        ci = __shfl_sync(0xffffffffu, ci, owner);
+        const float* tcr = Ttr + (long)i * ld;  // column i of c_op T = row i of its transpose
+        const float* tci = Tti + (long)i * ld;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int j = lane + 32 * s;
+          if (s == si_ && lane == owner) {
+            vr[s] = cr;
+            vi[s] = ci;
+          } else if (j < i) {
+            const float tr = tcr[j], ti = tci[j];
+            vr[s] -= tr * cr - ti * ci;
+            vi[s] -= tr * ci + ti * cr;
+          }
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        if (i < m) {
+          yr[i] = vr[s];
+          yi[i] = vi[s];
+        }
+      }
+      __syncwarp();
       // z = Re(Z y)
       T* zf = z + (long)a * m * rb + b;
       for (int i = lane; i < m; i += 32) {
-        T s = 0;
-        for (int j = 0; j < m; ++j)
-          s += Ops<T>::ld(Zr + (long)i * m + j) * vr[j] - Ops<T>::ld(Zi + (long)i * m + j) * vi[j];
-        zf[(long)i * rb] = s;
+        float acc0 = 0.f, acc1 = 0.f;
+        const float* zr = Zr + (long)i * ld;
+        const float* zi = Zi + (long)i * ld;
+        for (int j = 0; j < m; ++j) {
+          acc0 = fmaf(zr[j], yr[j], acc0);
+          acc1 = fmaf(-zi[j], yi[j], acc1);
+        }
+        zf[(long)i * rb] = (T)(acc0 + acc1);
       }
       __syncwarp();
     }
   }
 };
 
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
   Team<T> tm(P);
+  // optional phase timestamps (CTA 0, thread 0): slot 0 start, then 8 per
+  // iteration for the first kLocalTimingIts iterations
+  unsigned long long* tsb = (P.tstamp && blockIdx.x == 0 && threadIdx.x == 0) ? P.tstamp : nullptr;
+  int tsi = 0;
+  auto stamp = [&]() {
+    if (tsb && tsi < 2 + 8 * kLocalTimingIts) tsb[tsi++] = gtimer();
+  };
+  stamp();
   const int mr = P.mr;
   __shared__ double H[(kLocalMaxRestart + 1) * kLocalMaxRestart];
   __shared__ double cs[kLocalMaxRestart], sn[kLocalMaxRestart], gv[kLocalMaxRestart + 1],
       yv[kLocalMaxRestart];
   __shared__ double red[(kLocalMaxRestart + 2) * NW];
   __shared__ double hcol[kLocalMaxRestart + 2];
-  __shared__ T pre_re[NW * kLocalMaxM], pre_im[NW * kLocalMaxM];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  float* scratch = reinterpret_cast<float*>(dyn_smem);  // NW * 5 * kLocalMaxM
+  const float *Ttr, *Tti, *Zr, *Zi;
+  int ld;
+  {
+    const int m = P.m;
+    if (P.smem_mats) {
+      ld = m + 1;
+      float* base = scratch + NW * 5 * kLocalMaxM;
+      float* ttr = base;
+      float* tti = ttr + (long)m * ld;
+      float* zr = tti + (long)m * ld;
+      float* zi = zr + (long)m * ld;
+      const float cop = (float)P.c_op;
+      for (int e = threadIdx.x; e < m * m; e += NT) {
+        const int i = e / m, j = e % m;
+        ttr[(long)j * ld + i] = cop * P.Tr[e];  // transpose of c_op T
+        tti[(long)j * ld + i] = cop * P.Ti[e];
+        zr[(long)i * ld + j] = P.Zr[e];
+        zi[(long)i * ld + j] = P.Zi[e];
+      }
+      __syncthreads();
+      Ttr = ttr; Tti = tti; Zr = zr; Zi = zi;
+    } else {
+      ld = m;
+      Ttr = P.Ttc_r; Tti = P.Ttc_i; Zr = P.Zr; Zi = P.Zi;
+    }
+  }
   const long N = tm.N;
-  T* V = P.work;                       // (mr+1) x N
-  T* Zv = V + (long)(mr + 1) * N;      // N
-  T* Wv = Zv + N;                      // N
+  T* V = P.work;                       // (mr+1) x N   Arnoldi basis
+  T* Zs = V + (long)(mr + 1) * N;      // mr x N      preconditioned basis (flexible GMRES)
+  T* Wv = Zs + (long)mr * N;           // N
   double* part = P.part;               // 2 x G x (mr+2)
   const int G = tm.G, g = tm.g;
   const int stride = kLocalMaxRestart + 2;
   int pbuf = 0;
   auto partial = [&](int buf, int gi, int v) -> double& { return part[((long)buf * G + gi) * stride + v]; };
-  auto team_sum = [&](int buf, int nv) {  // sums partials into hcol[0..nv-1]
-    if (threadIdx.x < nv) {
+  // Sums the G per-CTA partials of nv values into hcol[0..nv-1]: one warp per
+  // value, lanes stride over the CTAs (independent loads in flight), then a
+  // fixed-order shuffle tree -- every CTA computes bitwise identical sums.
+  auto team_sum = [&](int buf, int nv) {
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    for (int v = w; v < nv; v += NW) {
       double s = 0;
-      for (int gi = 0; gi < G; ++gi) s += partial(buf, gi, threadIdx.x);
-      hcol[threadIdx.x] = s;
+      for (int gi = lane; gi < G; gi += 32) s += partial(buf, gi, v);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) hcol[v] = s;
     }
     __syncthreads();
+  };
+  auto publish = [&](double* v, int nv) {  // block-reduce nv values and publish them
+    block_sum(v, nv, red);
+    if (threadIdx.x < nv) partial(pbuf, g, threadIdx.x) = red[threadIdx.x * NW];
+  };
+  auto gather = [&](int nv) {  // after the grid barrier: team-wide sums into hcol
+    team_sum(pbuf, nv);
+    pbuf ^= 1;
   };
 
   // ||rhs||
   {
     double v[1] = {0.0};
-    for (long e = tm.e0 + threadIdx.x; e < tm.e1; e += NT) {
-      double r = (double)P.rhs[e];
+    for (long k = threadIdx.x; k < tm.nown; k += NT) {
+      double r = (double)P.rhs[tm.elem(k)];
       v[0] += r * r;
     }
-    block_sum(v, 1, red);
-    if (threadIdx.x == 0) partial(pbuf, g, 0) = red[0];
+    publish(v, 1);
   }
   tm.sync();
-  team_sum(pbuf, 1);
-  pbuf ^= 1;
+  gather(1);
   const double rhs_norm = sqrt(hcol[0]);
   const double tol_abs = P.tol_rel * rhs_norm;
   int its = 0;
   double resid = 0.0;
-  bool done = false;
-  for (int cycle = 0; !done; ++cycle) {
-    // r = rhs - K x  -> Wv ; beta = ||r||
+  for (int cycle = 0;; ++cycle) {
+    // r = rhs - K x -> Wv (own elements) ; beta = ||r||   (x complete)
     tm.matvec(P.x, Wv);
     {
       double v[1] = {0.0};
-      for (long e = tm.e0 + threadIdx.x; e < tm.e1; e += NT) {
+      for (long k = threadIdx.x; k < tm.nown; k += NT) {
+        const long e = tm.elem(k);
         double r = (double)P.rhs[e] - (double)Wv[e];
         Wv[e] = (T)r;
         v[0] += r * r;
       }
-      block_sum(v, 1, red);
-      if (threadIdx.x == 0) partial(pbuf, g, 0) = red[0];
+      publish(v, 1);
     }
     tm.sync();
-    team_sum(pbuf, 1);
-    pbuf ^= 1;
+    gather(1);
     const double beta = sqrt(hcol[0]);
     resid = beta;
     if (beta <= tol_abs || its >= P.maxit || beta == 0.0) break;
-    for (long e = tm.e0 + threadIdx.x; e < tm.e1; e += NT) V[e] = (T)((double)Wv[e] / beta);
+    for (long k = threadIdx.x; k < tm.nown; k += NT) {
+      const long e = tm.elem(k);
+      V[e] = (T)((double)Wv[e] / beta);
+    }
     if (threadIdx.x == 0) {
       gv[0] = beta;
       for (int i = 1; i <= mr; ++i) gv[i] = 0.0;
     }
     __syncthreads();
-    tm.sync();
     int jend = 0;
     for (int j = 0; j < mr; ++j) {
       const T* vj = V + (long)j * N;
-      tm.precond(vj, Zv, pre_re, pre_im);
-      tm.sync();
-      tm.matvec(Zv, Wv);
+      T* zj = Zs + (long)j * N;
+      stamp();
+      tm.precond(vj, zj, Ttr, Tti, Zr, Zi, ld, scratch);   // own fibres only
+      stamp();
+      tm.sync();                                            // barrier 1: z_j complete
+      stamp();
+      tm.matvec(zj, Wv);
       // CGS pass 1: h_i = <w, v_i>, i <= j
       {
         double v[kLocalMaxRestart + 1];
         for (int i = 0; i <= j; ++i) v[i] = 0.0;
-        for (long e = tm.e0 + threadIdx.x; e < tm.e1; e += NT) {
-          double we = (double)Wv[e];
+        for (long k = threadIdx.x; k < tm.nown; k += NT) {
+          const long e = tm.elem(k);
+          const double we = (double)Wv[e];
           for (int i = 0; i <= j; ++i) v[i] += we * (double)V[(long)i * N + e];
         }
-        block_sum(v, j + 1, red);
-        if (threadIdx.x <= j) partial(pbuf, g, threadIdx.x) = red[threadIdx.x * NW];
+        publish(v, j + 1);
       }
-      tm.sync();
-      team_sum(pbuf, j + 1);
-      pbuf ^= 1;
+      stamp();
+      tm.sync();                                            // barrier 2
+      gather(j + 1);
+      stamp();
       if (threadIdx.x <= j) H[threadIdx.x * mr + j] = hcol[threadIdx.x];
       __syncthreads();
-      // w -= V h ; CGS pass 2 dots
+      // w -= V h ; CGS pass 2 dots and ||w||^2 (Pythagoras gives the norm after pass 2)
       {
-        double v[kLocalMaxRestart + 1];
-        for (int i = 0; i <= j; ++i) v[i] = 0.0;
-        for (long e = tm.e0 + threadIdx.x; e < tm.e1; e += NT) {
-          double we = (double)Wv[e];
-          for (int i = 0; i <= j; ++i) we -= H[i * mr + j] * (double)V[(long)i * N + e];
-          for (int i = 0; i <= j; ++i) v[i] += we * (double)V[(long)i * N + e];
+        double v[kLocalMaxRestart + 2];
+        for (int i = 0; i <= j + 1; ++i) v[i] = 0.0;
+        for (long k = threadIdx.x; k < tm.nown; k += NT) {
+          const long e = tm.elem(k);
+          double w0 = (double)Wv[e], w1 = 0.0;
+          int i = 0;
+          for (; i + 1 <= j; i += 2) {
+            w0 = fma(-H[i * mr + j], (double)V[(long)i * N + e], w0);
+            w1 = fma(-H[(i + 1) * mr + j], (double)V[(long)(i + 1) * N + e], w1);
+          }
+          if (i <= j) w0 = fma(-H[i * mr + j], (double)V[(long)i * N + e], w0);
+          const double we = w0 + w1;
+          for (int i2 = 0; i2 <= j; ++i2) v[i2] += we * (double)V[(long)i2 * N + e];
+          v[j + 1] += we * we;
           Wv[e] = (T)we;
         }
-        block_sum(v, j + 1, red);
-        if (threadIdx.x <= j) partial(pbuf, g, threadIdx.x) = red[threadIdx.x * NW];
+        publish(v, j + 2);
       }
-      tm.sync();
-      team_sum(pbuf, j + 1);
-      pbuf ^= 1;
-      // w -= V h2 ; h += h2 ; ||w||^2
-      {
-        double v[1] = {0.0};
-        for (long e = tm.e0 + threadIdx.x; e < tm.e1; e += NT) {
-          double we = (double)Wv[e];
-          for (int i = 0; i <= j; ++i) we -= hcol[i] * (double)V[(long)i * N + e];
-          Wv[e] = (T)we;
-          v[0] += we * we;
+      stamp();
+      tm.sync();                                            // barrier 3
+      gather(j + 2);
+      stamp();
+      double h2n = 0.0;
+      for (int i = 0; i <= j; ++i) h2n += hcol[i] * hcol[i];
+      const double hn = sqrt(fmax(hcol[j + 1] - h2n, 0.0));
+      const double hinv = hn > 0 ? 1.0 / hn : 0.0;
+      // w -= V h2 ; v_{j+1} = w / hn  (own elements: the next preconditioner reads only these)
+      for (long k = threadIdx.x; k < tm.nown; k += NT) {
+        const long e = tm.elem(k);
+        double w0 = (double)Wv[e], w1 = 0.0;
+        int i = 0;
+        for (; i + 1 <= j; i += 2) {
+          w0 = fma(-hcol[i], (double)V[(long)i * N + e], w0);
+          w1 = fma(-hcol[i + 1], (double)V[(long)(i + 1) * N + e], w1);
         }
-        __syncthreads();
-        if (threadIdx.x <= j) H[threadIdx.x * mr + j] += hcol[threadIdx.x];
-        block_sum(v, 1, red);
-        if (threadIdx.x == 0) partial(pbuf, g, 0) = red[0];
+        if (i <= j) w0 = fma(-hcol[i], (double)V[(long)i * N + e], w0);
+        V[(long)(j + 1) * N + e] = (T)(hn > 0 ? (w0 + w1) * hinv : 0.0);
       }
-      tm.sync();
-      team_sum(pbuf, 1);
-      pbuf ^= 1;
-      const double hn = sqrt(hcol[0]);
-      for (long e = tm.e0 + threadIdx.x; e < tm.e1; e += NT)
-        V[(long)(j + 1) * N + e] = (T)(hn > 0 ? (double)Wv[e] / hn : 0.0);
+      __syncthreads();
       if (threadIdx.x == 0) {
+        for (int i = 0; i <= j; ++i) H[i * mr + j] += hcol[i];
         // apply previous rotations to column j, then a new one
         for (int i = 0; i < j; ++i) {
           double a = H[i * mr + j], b = H[(i + 1) * mr + j];
@@ -307,13 +413,13 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
         gv[j] = c * gv[j];
       }
       __syncthreads();
+      stamp();
       ++its;
       jend = j + 1;
       resid = fabs(gv[j + 1]);
       if (resid <= tol_abs || its >= P.maxit || hn == 0.0) break;
-      tm.sync();
     }
-    // y = H^{-1} g ; u = V y -> Wv ; x += M^{-1} u
+    // y = H^{-1} g ; x += Z y (own elements)
     if (threadIdx.x == 0) {
       for (int i = jend - 1; i >= 0; --i) {
         double s = gv[i];
@@ -322,32 +428,18 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
       }
     }
     __syncthreads();
-    for (long e = tm.e0 + threadIdx.x; e < tm.e1; e += NT) {
-      double s = 0.0;
-      for (int i = 0; i < jend; ++i) s += yv[i] * (double)V[(long)i * N + e];
-      Wv[e] = (T)s;
-    }
-    tm.sync();
-    tm.precond(Wv, Zv, pre_re, pre_im);
-    tm.sync();
-    for (long e = tm.e0 + threadIdx.x; e < tm.e1; e += NT) P.x[e] = (T)((double)P.x[e] + (double)Zv[e]);
-    tm.sync();
-    if (its >= P.maxit) {
-      // recompute the true residual once more for the report
-      tm.matvec(P.x, Wv);
-      double v[1] = {0.0};
-      for (long e = tm.e0 + threadIdx.x; e < tm.e1; e += NT) {
-        double r = (double)P.rhs[e] - (double)Wv[e];
-        v[0] += r * r;
+    for (long k = threadIdx.x; k < tm.nown; k += NT) {
+      const long e = tm.elem(k);
+      double s0 = 0.0, s1 = 0.0;
+      int i = 0;
+      for (; i + 1 < jend; i += 2) {
+        s0 = fma(yv[i], (double)Zs[(long)i * N + e], s0);
+        s1 = fma(yv[i + 1], (double)Zs[(long)(i + 1) * N + e], s1);
       }
-      block_sum(v, 1, red);
-      if (threadIdx.x == 0) partial(pbuf, g, 0) = red[0];
-      tm.sync();
-      team_sum(pbuf, 1);
-      pbuf ^= 1;
-      resid = sqrt(hcol[0]);
-      done = true;
+      if (i < jend) s0 = fma(yv[i], (double)Zs[(long)i * N + e], s0);
+      P.x[e] = (T)((double)P.x[e] + s0 + s1);
     }
+    tm.sync();  // x complete before the residual of the next cycle
   }
   if (g == 0 && threadIdx.x == 0) {
     if (P.iters_out) *P.iters_out = its;
@@ -358,12 +450,17 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
   }
 }
 
-int g_team_blocks[2] = {0, 0};
 }  // namespace
 
 template <typename T>
 size_t local_work_elems(long N, int mr) {
-  return (size_t)(mr + 3) * N;
+  return (size_t)(2 * mr + 2) * N;
+}
+
+size_t local_smem_bytes(int m, bool mats) {
+  size_t s = (size_t)NW * 5 * kLocalMaxM * sizeof(float);
+  if (mats) s += (size_t)4 * m * (m + 1) * sizeof(float);
+  return s;
 }
 
 template <typename T>
@@ -371,24 +468,43 @@ t2s2_status local_gmres(const LocalProblem<T>& P, cudaStream_t st) {
   if (P.m > kLocalMaxM || P.mr > kLocalMaxRestart || P.mr < 1) return T2S2_EINVAL;
   const long N = (long)P.ra * P.m * P.rb;
   const int ti = sizeof(T) == 8 ? 0 : 1;
-  if (g_team_blocks[ti] == 0) {
-    int per_sm = 0;
-    T2S2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gmres_team_kernel<T>, NT, 0));
-    int dev = 0, sms = 0;
-    T2S2_CUDA_TRY(cudaGetDevice(&dev));
-    T2S2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    g_team_blocks[ti] = std::max(1, per_sm) * sms;
-  }
-  long want = std::max((N + NT * 2 - 1) / (NT * 2), ((long)P.ra * P.rb + NW - 1) / NW);
-  int G = (int)std::max(1L, std::min<long>(want, std::min(g_team_blocks[ti], kNumSMs)));
-  if (P.team > 0) G = std::min(G, P.team);
   LocalProblem<T> Q = P;
+  Q.smem_mats = local_smem_bytes(P.m, true) <= kLocalSmemCap;
+  if (!Q.smem_mats && (!Q.Ttc_r || !Q.Ttc_i)) return T2S2_EINVAL;
+  const size_t smem = local_smem_bytes(P.m, Q.smem_mats);
+  static int attr_done[2] = {0, 0};
+  if (!attr_done[ti]) {
+    T2S2_CUDA_TRY(cudaFuncSetAttribute(gmres_team_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kLocalSmemCap));
+    attr_done[ti] = 1;
+  }
+  int per_sm = 0;
+  T2S2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gmres_team_kernel<T>, NT, smem));
+  int dev = 0, sms = 0;
+  T2S2_CUDA_TRY(cudaGetDevice(&dev));
+  T2S2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long resident = (long)std::max(1, per_sm) * sms;
+  // FP64 runs at 2 DFMA/clk/SM: spread the team over every SM.  FP32 is
+  // latency bound: size the team by the work (fibres per warp, elements).
+  long want = (sizeof(T) == 8)
+                  ? (long)sms
+                  : std::max((N + NT * 4 - 1) / (NT * 4), ((long)P.ra * P.rb + NW - 1) / NW);
+  int G = (int)std::max(1L, std::min<long>(want, std::min<long>(resident, sms)));
+  if (P.team > 0) G = std::min(G, P.team);
   void* args[] = {&Q};
   {
     TraceScope ts(kTrLocal, st, 0.0, 0.0);
-    T2S2_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gmres_team_kernel<T>, dim3(G), dim3(NT), args, 0, st));
+    T2S2_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gmres_team_kernel<T>, dim3(G), dim3(NT), args, smem, st));
   }
   return T2S2_OK;
+}
+
+double local_flops(int ra, int m, int rb, int its, int mr) {
+  const double N = (double)ra * m * rb;
+  const double jbar = 0.5 * std::min(its, mr) + 1.0;
+  const double per_it = 2.0 * N * (ra + m + rb) + 12.0 * m * m * (double)ra * rb + 8.0 * N * jbar + 3.0 * N;
+  const int restarts = its / std::max(1, mr) + 1;
+  return per_it * its + restarts * (2.0 * N * (ra + m + rb) + 12.0 * m * m * (double)ra * rb + 4.0 * N);
 }
 
 template size_t local_work_elems<double>(long, int);

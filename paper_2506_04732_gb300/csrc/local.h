@@ -6,6 +6,7 @@ namespace t2s2 {
 
 constexpr int kLocalMaxM = 128;        // largest mode size handled by the local solver
 constexpr int kLocalMaxRestart = 40;   // largest GMRES restart length
+constexpr int kLocalTimingIts = 12;    // iterations covered by the optional phase timestamps
 
 template <typename T>
 struct LocalProblem {
@@ -13,7 +14,7 @@ struct LocalProblem {
   const double* PL = nullptr;          // ra x ra left interface (Kronecker-sum part)
   const double* PR = nullptr;          // rb x rb right interface
   const double* Bp = nullptr;          // m x m  B' = c_op B + shift I
-  const T *Tr = nullptr, *Ti = nullptr, *Zr = nullptr, *Zi = nullptr;  // Schur B = Z T Z^H
+  const float *Tr = nullptr, *Ti = nullptr, *Zr = nullptr, *Zi = nullptr;  // Schur B = Z T Z^H (binary32)
   double c_op = 1.0, shift = 0.0;
   const T* rhs = nullptr;              // N
   T* x = nullptr;                      // N, initial guess in, solution out
@@ -21,6 +22,9 @@ struct LocalProblem {
   double* part = nullptr;              // 2 * team * (kLocalMaxRestart + 2)
   double tol_rel = 1e-10;              // stop at ||rhs - K x|| <= tol_rel ||rhs||
   int maxit = 400, mr = 30, team = 0;  // team = 0: pick the number of CTAs
+  const float *Ttc_r = nullptr, *Ttc_i = nullptr;  // (c_op T)^T in global memory when m is too big for smem
+  int smem_mats = 0;                   // set by the launcher
+  unsigned long long* tstamp = nullptr;  // optional phase timestamps (diagnostics)
   int* iters_out = nullptr;            // total GMRES iterations
   double* res_out = nullptr;           // [final residual norm, ||rhs||]
 };
@@ -28,7 +32,11 @@ struct LocalProblem {
 template <typename T>
 size_t local_work_elems(long N, int mr);
 
+constexpr size_t kLocalSmemCap = 200 * 1024;
 constexpr size_t kLocalPartElems = 2 * 160 * (kLocalMaxRestart + 2);
+
+// Algorithmic FLOPs of one local GMRES solve that took `its` iterations.
+double local_flops(int ra, int m, int rb, int its, int mr);
 
 template <typename T>
 t2s2_status local_gmres(const LocalProblem<T>& P, cudaStream_t st);

@@ -6,6 +6,7 @@
 //  * jacobi_svd: one-sided Jacobi SVD A = U diag(s) V^T of a p x q matrix
 //    (Hestenes' method, columns orthogonalised by plane rotations in a
 //    round-robin ordering; singular values sorted in decreasing order).
+#include "fastmath.cuh"
 #include "small.h"
 #include "trace.h"
 
@@ -55,9 +56,9 @@ __global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __rest
       __syncthreads();
       continue;
     }
-    const double djj = sqrt(v);
-    for (int i = j + 1 + t; i < c; i += blockDim.x) A[i * c + j] /= djj;
-    if (t == 0) A[j * c + j] = djj;
+    const double rinv = drsqrt(v);  // 1 / L_jj
+    for (int i = j + 1 + t; i < c; i += blockDim.x) A[i * c + j] *= rinv;
+    if (t == 0) A[j * c + j] = v * rinv;
     __syncthreads();
     int rem = c - j - 1;
     for (int e = t; e < rem * rem; e += blockDim.x) {
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __rest
       }
       double s = (i == k) ? 1.0 : 0.0;
       for (int l = k; l < i; ++l) s -= A[i * c + l] * Iv[l * c + k];
-      Iv[i * c + k] = s / dii;
+      Iv[i * c + k] = s * drcp(dii);
     }
   }
   __syncthreads();
@@ -140,10 +141,13 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
           beta += __shfl_xor_sync(0xffffffffu, beta, o);
           gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
         }
-        if (fabs(gamma) > 1e-15 * sqrt(alpha * beta) && gamma != 0.0) {
-          double zeta = (beta - alpha) / (2.0 * gamma);
-          double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        if (gamma != 0.0 && gamma * gamma > 1e-30 * alpha * beta) {
+          // tan of the rotation angle: t = 2 gamma sign(beta - alpha) /
+          // (|beta - alpha| + sqrt((beta - alpha)^2 + 4 gamma^2)), the smaller root
+          const double diff = beta - alpha;
+          const double root = dsqrt(fma(diff, diff, 4.0 * gamma * gamma));
+          const double tt = (diff >= 0.0 ? 2.0 * gamma : -2.0 * gamma) * drcp(fabs(diff) + root);
+          const double cs = drsqrt(fma(tt, tt, 1.0)), sn = cs * tt;
           for (int i = lane; i < rows; i += 32) {
             double x = wa[i], y = wb[i];
             wa[i] = cs * x - sn * y;
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
     double s = 0;
     for (int i = lane; i < rows; i += 32) s += W[j * rows + i] * W[j * rows + i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) nrm[j] = sqrt(s);
+    if (lane == 0) nrm[j] = dsqrt(s);
   }
   __syncthreads();
   if (t == 0) {  // selection sort of column order by decreasing norm (cols <= kSmallMax)
@@ -215,7 +219,8 @@ t2s2_status chol_inv(const double* G, int c, double shift_rel, double* L, double
     attr = true;
   }
   TraceScope ts(kTrSmall, st, (double)c * c * c, 8.0 * 3 * c * c);
-  chol_inv_kernel<<<1, kThreads, smem, st>>>(G, c, shift_rel, L, Linv, status);
+  const int nt = c <= 32 ? 32 : (c <= 64 ? 128 : 256);
+  chol_inv_kernel<<<1, nt, smem, st>>>(G, c, shift_rel, L, Linv, status);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }

@@ -24,6 +24,7 @@
 
 #include "api_internal.h"
 #include "local.h"
+#include "trace.h"
 
 void t2s2_op_s::free_solver_buffers() {}
 
@@ -82,9 +83,14 @@ struct Amen {
   int* gm_iters = nullptr;
   double* gm_res = nullptr;
   double* svals = nullptr;
+  float* fbuf = nullptr;     // FP32 rhs / x / GMRES basis for the mixed-precision local solves
+  bool fp32_local = false;
   long long local_iters = 0;
   double c_op = 1.0, c_mass = 0.0;
   int gm_restart = 40, gm_maxit = 600;
+  bool tstamp_req = false, tstamp_done = false;
+  int tstamp_target = 0, local_count = 0;
+  unsigned long long* tstamp_dev = nullptr;
 
   static size_t bytes_needed(int d, const int* m, int rcap, int rfmax, int kick, int mr) {
     int mm = 0;
@@ -95,7 +101,7 @@ struct Amen {
     s += 3 * (size_t)d * core;                  // x, f, z
     s += 10 * (size_t)(d + 1) * R * R;          // interfaces
     s += 12 * core;                             // temporaries
-    s += (size_t)(mr + 3) * rcap * mm * rcap;   // GMRES basis
+    s += (size_t)(2 * mr + 2) * rcap * mm * rcap;  // flexible GMRES bases
     s += kLocalPartElems + 64;
     s += (size_t)d * mm * mm;                   // B'
     // residual evaluation: apply output, sum, orthogonalisation temporaries
@@ -179,10 +185,24 @@ struct Amen {
       if (!t) return T2S2_ENOMEM;
     }
     gm_work = aget<double>(c, local_work_elems<double>((long)rcap * mmax * rcap, gm_restart));
+    if (fp32_local) {
+      fbuf = aget<float>(c, 2 * core + local_work_elems<float>((long)rcap * mmax * rcap, gm_restart));
+      if (!fbuf) return T2S2_ENOMEM;
+    }
     gm_part = aget<double>(c, kLocalPartElems);
     gm_iters = reinterpret_cast<int*>(aget<double>(c, 2));
     gm_res = aget<double>(c, 4);
     svals = aget<double>(c, kSmallMax);
+    {
+      const char* e = std::getenv("T2S2_LOCAL_TIMING");
+      tstamp_req = e && e[0] >= '0' && e[0] <= '9';
+      tstamp_target = tstamp_req ? std::atoi(e) : 0;
+      if (tstamp_req) {
+        tstamp_dev = reinterpret_cast<unsigned long long*>(aget<double>(c, 2 + 8 * kLocalTimingIts));
+        if (!tstamp_dev) return T2S2_ENOMEM;
+        T2S2_CUDA_TRY(cudaMemsetAsync(tstamp_dev, 0, sizeof(unsigned long long) * (2 + 8 * kLocalTimingIts), c.st));
+      }
+    }
     if (!gm_work || !gm_part || !gm_iters || !gm_res || !svals) return T2S2_ENOMEM;
     return T2S2_OK;
   }
@@ -233,6 +253,7 @@ struct Amen {
   }
 
   t2s2_status local_solve(int k, double* rhs, double* X) {
+    if (fp32_local) return local_solve_f32(k, rhs, X);
     Ctx& c = *cx;
     LocalProblem<double> P;
     P.ra = x.r[k];
@@ -241,10 +262,10 @@ struct Amen {
     P.PL = PL[k];
     P.PR = PR[k + 1];
     P.Bp = Bp[k];
-    P.Tr = op->dTr[k];
-    P.Ti = op->dTi[k];
-    P.Zr = op->dZr[k];
-    P.Zi = op->dZi[k];
+    P.Tr = op->fptr[5][k];
+    P.Ti = op->fptr[6][k];
+    P.Zr = op->fptr[7][k];
+    P.Zi = op->fptr[8][k];
     P.c_op = c_op;
     P.shift = c_mass / d;
     P.rhs = rhs;
@@ -256,7 +277,56 @@ struct Amen {
     P.mr = gm_restart;
     P.iters_out = gm_iters;
     P.res_out = gm_res;
-    return local_gmres<double>(P, c.st);
+    const bool stamp_this = tstamp_req && !tstamp_done && local_count == tstamp_target;
+    ++local_count;
+    if (stamp_this) P.tstamp = tstamp_dev;
+    T2S2_TRY(local_gmres<double>(P, c.st));
+    if (stamp_this) {
+      tstamp_done = true;
+      unsigned long long h[2 + 8 * kLocalTimingIts];
+      T2S2_CUDA_TRY(cudaMemcpyAsync(h, tstamp_dev, sizeof(h), cudaMemcpyDeviceToHost, c.st));
+      T2S2_CUDA_TRY(cudaStreamSynchronize(c.st));
+      fprintf(stderr, "[t2s2] local solve phase times (ns) ra=%d m=%d rb=%d:", P.ra, P.m, P.rb);
+      for (int i = 1; i < 2 + 8 * kLocalTimingIts; ++i) fprintf(stderr, " %lld", (long long)(h[i] - h[i - 1]));
+      fprintf(stderr, "\n");
+    }
+    return T2S2_OK;
+  }
+
+  // FP32 local solve (mixed precision): the caller's FP64 rhs / guess are
+  // rounded to binary32, solved, and the result widened back.
+  t2s2_status local_solve_f32(int k, double* rhs, double* X) {
+    Ctx& c = *cx;
+    const size_t N = (size_t)x.r[k] * op->m[k] * x.r[k + 1];
+    float* frhs = fbuf;
+    float* fx = fbuf + tmp_elems;
+    float* fwork = fbuf + 2 * tmp_elems;
+    T2S2_TRY(dev_d2f(c, frhs, rhs, N));
+    T2S2_TRY(dev_d2f(c, fx, X, N));
+    LocalProblem<float> P;
+    P.ra = x.r[k];
+    P.m = op->m[k];
+    P.rb = x.r[k + 1];
+    P.PL = PL[k];
+    P.PR = PR[k + 1];
+    P.Bp = Bp[k];
+    P.Tr = op->fptr[5][k];
+    P.Ti = op->fptr[6][k];
+    P.Zr = op->fptr[7][k];
+    P.Zi = op->fptr[8][k];
+    P.c_op = c_op;
+    P.shift = c_mass / d;
+    P.rhs = frhs;
+    P.x = fx;
+    P.work = fwork;
+    P.part = gm_part;
+    P.tol_rel = std::max(ltol, 2e-6);
+    P.maxit = gm_maxit;
+    P.mr = gm_restart;
+    P.iters_out = gm_iters;
+    P.res_out = gm_res;
+    T2S2_TRY(local_gmres<float>(P, c.st));
+    return dev_f2d(c, X, fx, N);
   }
 
   // One forward sweep k = 0 .. d-1.
@@ -281,6 +351,7 @@ struct Amen {
         int it;
         std::memcpy(&it, c.hbuf + 8, sizeof(int));
         local_iters += it;
+        trace_add_work(kTrLocal, local_flops(ra, m, rb, it, gm_restart), 0.0);
         break;
       }
       // --- truncation: X (rows x rb) = U S V^T
@@ -302,6 +373,7 @@ struct Amen {
         int it;
         std::memcpy(&it, c.hbuf + kSmallMax, sizeof(int));
         local_iters += it;
+        trace_add_work(kTrLocal, local_flops(ra, m, rb, it, gm_restart), 0.0);
       }
       double snorm = 0.0;
       for (int j = 0; j < kk; ++j) snorm += c.hbuf[j] * c.hbuf[j];

@@ -58,6 +58,16 @@ __global__ void k_sv_t(double* M, const double* s, const double* V, int r, int q
     M[e] = s[i] * V[(size_t)j * ldv + i];
   }
 }
+__global__ void k_d2f(float* dst, const double* src, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (float)src[e];
+}
+__global__ void k_f2d(double* dst, const float* src, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (double)src[e];
+}
 // sum of squares, one block, fixed order per thread then tree (deterministic)
 __global__ void k_sumsq(const double* v, size_t n, double* out) {
   __shared__ double red[1024];
@@ -111,6 +121,19 @@ t2s2_status dev_copy_block(Ctx& cx, double* dst, int rd0, int rd1, int a0, int b
 t2s2_status dev_sv_t(Ctx& cx, double* M, const double* s, const double* V, int r, int q, int ldv) {
   if (r * q == 0) return T2S2_OK;
   { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * r * q); k_sv_t<<<blocks_for((size_t)r * q), 256, 0, cx.st>>>(M, s, V, r, q, ldv); }
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+
+t2s2_status dev_d2f(Ctx& cx, float* dst, const double* src, size_t n) {
+  if (n == 0) return T2S2_OK;
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 12.0 * n); k_d2f<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n); }
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+t2s2_status dev_f2d(Ctx& cx, double* dst, const float* src, size_t n) {
+  if (n == 0) return T2S2_OK;
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 12.0 * n); k_f2d<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }

@@ -89,6 +89,8 @@ inline t2s2_status gemm_ex(Ctx& cx, int M, int N, int K, bool tA, bool tB, T alp
 t2s2_status dev_scale_copy(Ctx& cx, double* dst, const double* src, size_t n, double alpha);
 t2s2_status dev_fill(Ctx& cx, double* dst, size_t n, double v);
 t2s2_status dev_axpy(Ctx& cx, double* dst, const double* src, size_t n, double beta);
+t2s2_status dev_d2f(Ctx& cx, float* dst, const double* src, size_t n);
+t2s2_status dev_f2d(Ctx& cx, double* dst, const float* src, size_t n);
 t2s2_status dev_identity(Ctx& cx, double* dst, int n);
 // dst (rd0 x m x rd1) block at (a0, b0) = alpha * src (ra x m x rb)
 t2s2_status dev_copy_block(Ctx& cx, double* dst, int rd0, int rd1, int a0, int b0,
