@@ -37,24 +37,6 @@ struct Ops {
   static __device__ T ld(const T* p) { return *p; }
 };
 
-// block-wide sum of nv values per thread (vals[0..nv-1]) into smem red[nv][NW]
-__device__ void block_sum(double* vals, int nv, double* red) {
-  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-  for (int v = 0; v < nv; ++v) {
-    double s = vals[v];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) red[v * NW + w] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    double s = 0;
-    for (int i = 0; i < NW; ++i) s += red[threadIdx.x * NW + i];
-    vals[threadIdx.x] = s;  // only valid in thread v for value v
-    red[threadIdx.x * NW] = s;
-  }
-  __syncthreads();
-}
-
 // Each CTA owns a contiguous range of fibres (a, b) and all m elements of
 // each: the preconditioner then touches only the CTA's own data, and only the
 // matrix-vector product needs the whole vector.
@@ -224,18 +206,23 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
   __shared__ double H[(kLocalMaxRestart + 1) * kLocalMaxRestart];
   __shared__ double cs[kLocalMaxRestart], sn[kLocalMaxRestart], gv[kLocalMaxRestart + 1],
       yv[kLocalMaxRestart];
-  __shared__ double red[(kLocalMaxRestart + 2) * NW];
   __shared__ double hcol[kLocalMaxRestart + 2];
+  __shared__ double dots[kLocalMaxRestart + 2];
+  __shared__ double red2[(kLocalMaxRestart + 2) * 8];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   float* scratch = reinterpret_cast<float*>(dyn_smem);  // NW * 5 * kLocalMaxM
+  int* eidx = reinterpret_cast<int*>(scratch + NW * 5 * kLocalMaxM);  // own element indices
   const float *Ttr, *Tti, *Zr, *Zi;
   int ld;
+  const bool own_in_smem = tm.nown <= kLocalOwnMax;
   {
     const int m = P.m;
+    float* after_idx = reinterpret_cast<float*>(eidx + kLocalOwnMax);
+    if (own_in_smem)
+      for (long k = threadIdx.x; k < tm.nown; k += NT) eidx[k] = (int)tm.elem(k);
     if (P.smem_mats) {
       ld = m + 1;
-      float* base = scratch + NW * 5 * kLocalMaxM;
-      float* ttr = base;
+      float* ttr = after_idx;
       float* tti = ttr + (long)m * ld;
       float* zr = tti + (long)m * ld;
       float* zi = zr + (long)m * ld;
@@ -247,53 +234,66 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
         zr[(long)i * ld + j] = P.Zr[e];
         zi[(long)i * ld + j] = P.Zi[e];
       }
-      __syncthreads();
       Ttr = ttr; Tti = tti; Zr = zr; Zi = zi;
     } else {
       ld = m;
       Ttr = P.Ttc_r; Tti = P.Ttc_i; Zr = P.Zr; Zi = P.Zi;
     }
+    __syncthreads();
   }
+  auto E = [&](long k) -> long { return own_in_smem ? (long)eidx[k] : tm.elem(k); };
   const long N = tm.N;
   T* V = P.work;                       // (mr+1) x N   Arnoldi basis
   T* Zs = V + (long)(mr + 1) * N;      // mr x N      preconditioned basis (flexible GMRES)
   T* Wv = Zs + (long)mr * N;           // N
-  double* part = P.part;               // 2 x G x (mr+2)
+  double* part = P.part;               // 2 x G x (kLocalMaxRestart + 2)
   const int G = tm.G, g = tm.g;
   const int stride = kLocalMaxRestart + 2;
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
   int pbuf = 0;
   auto partial = [&](int buf, int gi, int v) -> double& { return part[((long)buf * G + gi) * stride + v]; };
-  // Sums the G per-CTA partials of nv values into hcol[0..nv-1]: one warp per
-  // value, lanes stride over the CTAs (independent loads in flight), then a
-  // fixed-order shuffle tree -- every CTA computes bitwise identical sums.
-  auto team_sum = [&](int buf, int nv) {
-    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-    for (int v = w; v < nv; v += NW) {
-      double s = 0;
-      for (int gi = lane; gi < G; gi += 32) s += partial(buf, gi, v);
+  // CTA-local dot products over the own elements: dots[i] = <a, V_i> for i < nvec,
+  // and dots[nvec] = <a, a> if with_norm; one warp per product, then published.
+  auto own_dots = [&](const T* a, int nvec, bool with_norm) {
+    const int nv = nvec + (with_norm ? 1 : 0);
+    for (int v = wid; v < nv; v += NW) {
+      const T* b = (v < nvec) ? V + (long)v * N : a;
+      double s0 = 0.0, s1 = 0.0;
+      long k = lane;
+      for (; k + 32 < tm.nown; k += 64) {
+        const long e0 = E(k), e1 = E(k + 32);
+        s0 = fma((double)a[e0], (double)b[e0], s0);
+        s1 = fma((double)a[e1], (double)b[e1], s1);
+      }
+      if (k < tm.nown) {
+        const long e0 = E(k);
+        s0 = fma((double)a[e0], (double)b[e0], s0);
+      }
+      double s = s0 + s1;
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) hcol[v] = s;
+      if (lane == 0) partial(pbuf, g, v) = s;
+    }
+  };
+  // After a grid barrier: hcol[v] = sum over CTAs of the published partials,
+  // in a fixed order (bitwise identical in every CTA).
+  auto gather = [&](int nv) {
+    for (int idx = threadIdx.x; idx < nv * 8; idx += NT) {
+      const int v = idx >> 3, sub = idx & 7;
+      double s = 0.0;
+      for (int gi = sub; gi < G; gi += 8) s += partial(pbuf, gi, v);
+      red2[v * 8 + sub] = s;
     }
     __syncthreads();
-  };
-  auto publish = [&](double* v, int nv) {  // block-reduce nv values and publish them
-    block_sum(v, nv, red);
-    if (threadIdx.x < nv) partial(pbuf, g, threadIdx.x) = red[threadIdx.x * NW];
-  };
-  auto gather = [&](int nv) {  // after the grid barrier: team-wide sums into hcol
-    team_sum(pbuf, nv);
+    if (threadIdx.x < nv) {
+      const double* r = red2 + threadIdx.x * 8;
+      hcol[threadIdx.x] = ((r[0] + r[1]) + (r[2] + r[3])) + ((r[4] + r[5]) + (r[6] + r[7]));
+    }
+    __syncthreads();
     pbuf ^= 1;
   };
 
   // ||rhs||
-  {
-    double v[1] = {0.0};
-    for (long k = threadIdx.x; k < tm.nown; k += NT) {
-      double r = (double)P.rhs[tm.elem(k)];
-      v[0] += r * r;
-    }
-    publish(v, 1);
-  }
+  own_dots(P.rhs, 0, true);
   tm.sync();
   gather(1);
   const double rhs_norm = sqrt(hcol[0]);
@@ -303,24 +303,21 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
   for (int cycle = 0;; ++cycle) {
     // r = rhs - K x -> Wv (own elements) ; beta = ||r||   (x complete)
     tm.matvec(P.x, Wv);
-    {
-      double v[1] = {0.0};
-      for (long k = threadIdx.x; k < tm.nown; k += NT) {
-        const long e = tm.elem(k);
-        double r = (double)P.rhs[e] - (double)Wv[e];
-        Wv[e] = (T)r;
-        v[0] += r * r;
-      }
-      publish(v, 1);
+    for (long k = threadIdx.x; k < tm.nown; k += NT) {
+      const long e = E(k);
+      Wv[e] = (T)((double)P.rhs[e] - (double)Wv[e]);
     }
+    __syncthreads();
+    own_dots(Wv, 0, true);
     tm.sync();
     gather(1);
     const double beta = sqrt(hcol[0]);
     resid = beta;
     if (beta <= tol_abs || its >= P.maxit || beta == 0.0) break;
+    const double binv = 1.0 / beta;
     for (long k = threadIdx.x; k < tm.nown; k += NT) {
-      const long e = tm.elem(k);
-      V[e] = (T)((double)Wv[e] / beta);
+      const long e = E(k);
+      V[e] = (T)((double)Wv[e] * binv);
     }
     if (threadIdx.x == 0) {
       gv[0] = beta;
@@ -337,66 +334,58 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
       tm.sync();                                            // barrier 1: z_j complete
       stamp();
       tm.matvec(zj, Wv);
-      // CGS pass 1: h_i = <w, v_i>, i <= j
-      {
-        double v[kLocalMaxRestart + 1];
-        for (int i = 0; i <= j; ++i) v[i] = 0.0;
-        for (long k = threadIdx.x; k < tm.nown; k += NT) {
-          const long e = tm.elem(k);
-          const double we = (double)Wv[e];
-          for (int i = 0; i <= j; ++i) v[i] += we * (double)V[(long)i * N + e];
-        }
-        publish(v, j + 1);
-      }
+      __syncthreads();
+      own_dots(Wv, j + 1, true);                            // h_i = <w, v_i>, and ||w||^2
       stamp();
       tm.sync();                                            // barrier 2
-      gather(j + 1);
-      stamp();
-      if (threadIdx.x <= j) H[threadIdx.x * mr + j] = hcol[threadIdx.x];
-      __syncthreads();
-      // w -= V h ; CGS pass 2 dots and ||w||^2 (Pythagoras gives the norm after pass 2)
-      {
-        double v[kLocalMaxRestart + 2];
-        for (int i = 0; i <= j + 1; ++i) v[i] = 0.0;
-        for (long k = threadIdx.x; k < tm.nown; k += NT) {
-          const long e = tm.elem(k);
-          double w0 = (double)Wv[e], w1 = 0.0;
-          int i = 0;
-          for (; i + 1 <= j; i += 2) {
-            w0 = fma(-H[i * mr + j], (double)V[(long)i * N + e], w0);
-            w1 = fma(-H[(i + 1) * mr + j], (double)V[(long)(i + 1) * N + e], w1);
-          }
-          if (i <= j) w0 = fma(-H[i * mr + j], (double)V[(long)i * N + e], w0);
-          const double we = w0 + w1;
-          for (int i2 = 0; i2 <= j; ++i2) v[i2] += we * (double)V[(long)i2 * N + e];
-          v[j + 1] += we * we;
-          Wv[e] = (T)we;
-        }
-        publish(v, j + 2);
-      }
-      stamp();
-      tm.sync();                                            // barrier 3
       gather(j + 2);
       stamp();
-      double h2n = 0.0;
-      for (int i = 0; i <= j; ++i) h2n += hcol[i] * hcol[i];
-      const double hn = sqrt(fmax(hcol[j + 1] - h2n, 0.0));
-      const double hinv = hn > 0 ? 1.0 / hn : 0.0;
-      // w -= V h2 ; v_{j+1} = w / hn  (own elements: the next preconditioner reads only these)
+      double hsq = 0.0;
+      for (int i = 0; i <= j; ++i) hsq += hcol[i] * hcol[i];
+      const double ww = hcol[j + 1];
+      if (threadIdx.x <= j) H[threadIdx.x * mr + j] = hcol[threadIdx.x];
+      __syncthreads();
+      double hn2 = ww - hsq;
+      // w <- w - V h   (own elements)
       for (long k = threadIdx.x; k < tm.nown; k += NT) {
-        const long e = tm.elem(k);
+        const long e = E(k);
         double w0 = (double)Wv[e], w1 = 0.0;
         int i = 0;
         for (; i + 1 <= j; i += 2) {
-          w0 = fma(-hcol[i], (double)V[(long)i * N + e], w0);
-          w1 = fma(-hcol[i + 1], (double)V[(long)(i + 1) * N + e], w1);
+          w0 = fma(-H[i * mr + j], (double)V[(long)i * N + e], w0);
+          w1 = fma(-H[(i + 1) * mr + j], (double)V[(long)(i + 1) * N + e], w1);
         }
-        if (i <= j) w0 = fma(-hcol[i], (double)V[(long)i * N + e], w0);
-        V[(long)(j + 1) * N + e] = (T)(hn > 0 ? (w0 + w1) * hinv : 0.0);
+        if (i <= j) w0 = fma(-H[i * mr + j], (double)V[(long)i * N + e], w0);
+        Wv[e] = (T)(w0 + w1);
       }
       __syncthreads();
+      stamp();
+      if (!(hn2 > 0.5 * ww)) {
+        // severe cancellation: a second Gram-Schmidt pass (DGKS criterion)
+        own_dots(Wv, j + 1, true);
+        tm.sync();                                          // barrier 3 (rare)
+        gather(j + 2);
+        double h2 = 0.0;
+        for (int i = 0; i <= j; ++i) h2 += hcol[i] * hcol[i];
+        hn2 = hcol[j + 1] - h2;
+        for (long k = threadIdx.x; k < tm.nown; k += NT) {
+          const long e = E(k);
+          double w0 = (double)Wv[e];
+          for (int i = 0; i <= j; ++i) w0 = fma(-hcol[i], (double)V[(long)i * N + e], w0);
+          Wv[e] = (T)w0;
+        }
+        __syncthreads();
+        if (threadIdx.x <= j) H[threadIdx.x * mr + j] += hcol[threadIdx.x];
+        __syncthreads();
+      }
+      stamp();
+      const double hn = sqrt(fmax(hn2, 0.0));
+      const double hinv = hn > 0 ? 1.0 / hn : 0.0;
+      for (long k = threadIdx.x; k < tm.nown; k += NT) {
+        const long e = E(k);
+        V[(long)(j + 1) * N + e] = (T)((double)Wv[e] * hinv);
+      }
       if (threadIdx.x == 0) {
-        for (int i = 0; i <= j; ++i) H[i * mr + j] += hcol[i];
         // apply previous rotations to column j, then a new one
         for (int i = 0; i < j; ++i) {
           double a = H[i * mr + j], b = H[(i + 1) * mr + j];
@@ -414,6 +403,7 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
       }
       __syncthreads();
       stamp();
+      stamp();
       ++its;
       jend = j + 1;
       resid = fabs(gv[j + 1]);
@@ -429,7 +419,7 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
     }
     __syncthreads();
     for (long k = threadIdx.x; k < tm.nown; k += NT) {
-      const long e = tm.elem(k);
+      const long e = E(k);
       double s0 = 0.0, s1 = 0.0;
       int i = 0;
       for (; i + 1 < jend; i += 2) {
@@ -458,7 +448,7 @@ size_t local_work_elems(long N, int mr) {
 }
 
 size_t local_smem_bytes(int m, bool mats) {
-  size_t s = (size_t)NW * 5 * kLocalMaxM * sizeof(float);
+  size_t s = (size_t)NW * 5 * kLocalMaxM * sizeof(float) + (size_t)kLocalOwnMax * sizeof(int);
   if (mats) s += (size_t)4 * m * (m + 1) * sizeof(float);
   return s;
 }

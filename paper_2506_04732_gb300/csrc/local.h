@@ -6,7 +6,8 @@ namespace t2s2 {
 
 constexpr int kLocalMaxM = 128;        // largest mode size handled by the local solver
 constexpr int kLocalMaxRestart = 40;   // largest GMRES restart length
-constexpr int kLocalTimingIts = 12;    // iterations covered by the optional phase timestamps
+constexpr int kLocalTimingIts = 12;
+constexpr int kLocalOwnMax = 4096;     // own-element index list kept in shared memory up to this size    // iterations covered by the optional phase timestamps
 
 template <typename T>
 struct LocalProblem {
