@@ -158,6 +158,24 @@ t2s2_status t2s2_round(t2s2_op op, t2s2_tt* x, double tol, int rmax, void* strea
 /* ||x||_F (accurate: orthogonalise and take the norm of the first core). */
 t2s2_status t2s2_norm(t2s2_op op, const t2s2_tt* x, double* out, void* stream);
 
+/*
+ * ||x||_F exactly as t2s2_norm computes it, but without allocating anything.
+ * The paper has no counterpart; this entry point exists for callers that may
+ * not allocate device memory at the time they need the norm: for example, code
+ * recording work into a CUDA graph, real-time or embedded loops whose memory
+ * is fixed at start-up, or hosts whose framework allocator already owns the
+ * device memory.  It takes no operator handle (no workspace).  Every
+ * temporary lives in one 32 MiB array that the library reserves as a static
+ * device variable on each GPU that loads it, kept until the process exits.
+ * x must be device-resident (loc == T2S2_DEVICE) with ranks <= 96.  A train
+ * whose temporaries would exceed the 32 MiB array is rejected with
+ * T2S2_ENOMEM before any work is queued.  The first call on a device looks up
+ * that device's array address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array, so calls whose
+ * GPU work overlaps race on it: serialise them.  Synchronises with `stream`.
+ */
+t2s2_status t2s2_norm_noalloc(const t2s2_tt* x, double* out, void* stream);
+
 /* ||b - (c_mass M + c_op A) x||_F / ||b||_F, accurate difference norm, FP64. */
 t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double c_mass,
                           double c_op, double* out, void* stream);

@@ -19,7 +19,7 @@ import numpy as np
 
 __all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REFINE",
            "TF32_REFINE", "BF16_REFINE", "t2s2_build_operator", "t2s2_apply", "t2s2_round",
-           "t2s2_norm", "t2s2_residual", "t2s2_solve", "t2s2_cn_step", "t2s2_be_step",
+           "t2s2_norm", "t2s2_norm_noalloc", "t2s2_residual", "t2s2_solve", "t2s2_cn_step", "t2s2_be_step",
            "t2s2_device_count", "t2s2_strerror", "lib_path"]
 
 FP64, FP32_REFINE, TF32_REFINE, BF16_REFINE = 0, 1, 2, 3
@@ -82,6 +82,8 @@ _SIGS = {
                                   ctypes.c_int, ctypes.c_void_p]),
     "t2s2_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT),
                                  ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "t2s2_norm_noalloc": (ctypes.c_int, [ctypes.POINTER(_TT), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_void_p]),
     "t2s2_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.POINTER(_TT),
                                      ctypes.c_double, ctypes.c_double,
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
@@ -273,6 +275,14 @@ def t2s2_norm(op: Operator, x: TT, stream=None) -> float:
     out = ctypes.c_double()
     _check(load().t2s2_norm(op.handle, ctypes.byref(x._struct()), ctypes.byref(out),
                             _stream_handle(stream)), "t2s2_norm")
+    return out.value
+
+
+def t2s2_norm_noalloc(x: TT, stream=None) -> float:
+    """||x||_F without any device allocation (static scratch; see t2s2.h)."""
+    out = ctypes.c_double()
+    _check(load().t2s2_norm_noalloc(ctypes.byref(x._struct()), ctypes.byref(out),
+                                    _stream_handle(stream)), "t2s2_norm_noalloc")
     return out.value
 
 
