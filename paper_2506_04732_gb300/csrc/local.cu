@@ -18,6 +18,7 @@
 // so all CTAs hold identical Hessenberg / Givens data without a broadcast.
 #include <cooperative_groups.h>
 
+#include "eig.cuh"
 #include "local.h"
 #include "trace.h"
 
@@ -185,6 +186,152 @@ struct Team {
   }
 };
 
+// Exact Kronecker-sum preconditioner (used when the interface eigendecompositions
+// P_L = V_L diag(lL) V_L^{-1}, P_R = V_R diag(lR) V_R^{-1} are available):
+//   K^{-1} = (V_L x Z x V_R) (lL (+) (c_op T + s I) (+) lR)^{-1} (V_L^{-1} x Z^H x V_R^{-1}),
+// whose middle factor is, fibre by fibre, an upper-triangular solve with the
+// complex shift lL[a'] + lR[b'].  Complex binary32.
+struct FlsSmem {
+  cf *VL, *VLi, *VR, *VRi, *lamL, *lamR, *Wst;  // eigen data and the m x max(ra,rb) staging slab
+  float* fib;                                  // per-warp fibre scratch, 8 * kLocalMaxM floats
+};
+
+// Phase A: Y[a',i,b'] over the CTA's own fibres, reading the whole vector v.
+template <typename T>
+__device__ void fls_phase_a(const Team<T>& tm, const T* __restrict__ v, cf* __restrict__ Y, const FlsSmem& F,
+                            const float* Ttr, const float* Tti, const float* Zr, const float* Zi, int ld) {
+  const int ra = tm.P.ra, m = tm.P.m, rb = tm.P.rb;
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  const float shift = (float)tm.P.shift;
+  if (tm.f1 <= tm.f0) return;
+  const int a_lo = (int)(tm.f0 / rb), a_hi = (int)((tm.f1 - 1) / rb);
+  float* sr = F.fib + w * 8 * kLocalMaxM;
+  float* si = sr + kLocalMaxM;
+  float* yr = si + kLocalMaxM;
+  float* yi = yr + kLocalMaxM;
+  for (int ap = a_lo; ap <= a_hi; ++ap) {
+    // W[i][b] = sum_a VLi[ap][a] v[a,i,b]
+    for (int idx = threadIdx.x; idx < m * rb; idx += NT) {
+      const int i = idx / rb, b = idx % rb;
+      float xr = 0.f, xi = 0.f;
+      for (int a = 0; a < ra; ++a) {
+        const cf c = F.VLi[ap * ra + a];
+        const float vv = (float)v[((long)a * m + i) * rb + b];
+        xr = fmaf(c.x, vv, xr);
+        xi = fmaf(c.y, vv, xi);
+      }
+      F.Wst[idx] = cmk(xr, xi);
+    }
+    __syncthreads();
+    const long fb0 = max(tm.f0, (long)ap * rb), fb1 = min(tm.f1, (long)(ap + 1) * rb);
+    for (long f = fb0 + w; f < fb1; f += NW) {
+      const int bp = (int)(f - (long)ap * rb);
+      // vt_i = sum_b VRi[bp][b] W[i][b]
+      for (int i = lane; i < m; i += 32) {
+        cf acc = cmk(0.f, 0.f);
+        for (int b = 0; b < rb; ++b) acc = cadd(acc, cmul(F.VRi[bp * rb + b], F.Wst[i * rb + b]));
+        sr[i] = acc.x;
+        si[i] = acc.y;
+      }
+      __syncwarp();
+      // Z^H vt
+      float vr[4], vi[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        float ar = 0.f, ai = 0.f;
+        if (i < m) {
+          for (int j = 0; j < m; ++j) {
+            const float zr = Zr[(long)j * ld + i], zi = Zi[(long)j * ld + i];  // conj(Z_ji)
+            ar = fmaf(zr, sr[j], fmaf(zi, si[j], ar));
+            ai = fmaf(zr, si[j], fmaf(-zi, sr[j], ai));
+          }
+        }
+        vr[s] = ar;
+        vi[s] = ai;
+      }
+      const cf sh = cadd(cadd(F.lamL[ap], F.lamR[bp]), cmk(shift, 0.f));
+      // back substitution with (c_op T + shift I + lL + lR), column oriented
+      for (int i = m - 1; i >= 0; --i) {
+        const int owner = i & 31, si_ = i >> 5;
+        float ar = 0.f, ai = 0.f;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (s == si_) { ar = vr[s]; ai = vi[s]; }
+        const cf dg = cadd(cmk(Ttr[(long)i * ld + i], Tti[(long)i * ld + i]), sh);
+        const cf q = cdiv(cmk(ar, ai), dg);
+        const float cr = __shfl_sync(0xffffffffu, q.x, owner);
+        const float ci = __shfl_sync(0xffffffffu, q.y, owner);
+        const float* tcr = Ttr + (long)i * ld;
+        const float* tci = Tti + (long)i * ld;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int j = lane + 32 * s;
+          if (s == si_ && lane == owner) {
+            vr[s] = cr;
+            vi[s] = ci;
+          } else if (j < i) {
+            const float tr = tcr[j], ti = tci[j];
+            vr[s] -= tr * cr - ti * ci;
+            vi[s] -= tr * ci + ti * cr;
+          }
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        if (i < m) {
+          yr[i] = vr[s];
+          yi[i] = vi[s];
+        }
+      }
+      __syncwarp();
+      // Y = Z y
+      for (int i = lane; i < m; i += 32) {
+        float ar = 0.f, ai = 0.f;
+        const float* zr = Zr + (long)i * ld;
+        const float* zi = Zi + (long)i * ld;
+        for (int j = 0; j < m; ++j) {
+          ar = fmaf(zr[j], yr[j], fmaf(-zi[j], yi[j], ar));
+          ai = fmaf(zr[j], yi[j], fmaf(zi[j], yr[j], ai));
+        }
+        Y[((long)ap * m + i) * rb + bp] = cmk(ar, ai);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// Phase B: z[a,i,b] = Re sum_{a',b'} VL[a][a'] VR[b][b'] Y[a',i,b'] on own fibres (Y complete).
+template <typename T>
+__device__ void fls_phase_b(const Team<T>& tm, const cf* __restrict__ Y, T* __restrict__ z, const FlsSmem& F) {
+  const int ra = tm.P.ra, m = tm.P.m, rb = tm.P.rb;
+  if (tm.f1 <= tm.f0) return;
+  const int a_lo = (int)(tm.f0 / rb), a_hi = (int)((tm.f1 - 1) / rb);
+  for (int a = a_lo; a <= a_hi; ++a) {
+    for (int idx = threadIdx.x; idx < m * rb; idx += NT) {
+      const int i = idx / rb, bp = idx % rb;
+      cf acc = cmk(0.f, 0.f);
+      for (int ap = 0; ap < ra; ++ap) acc = cadd(acc, cmul(F.VL[a * ra + ap], Y[((long)ap * m + i) * rb + bp]));
+      F.Wst[idx] = acc;
+    }
+    __syncthreads();
+    const long fb0 = max(tm.f0, (long)a * rb), fb1 = min(tm.f1, (long)(a + 1) * rb);
+    const int nb = (int)(fb1 - fb0);
+    for (int idx = threadIdx.x; idx < nb * m; idx += NT) {
+      const int b = (int)(fb0 - (long)a * rb) + idx % nb, i = idx / nb;
+      float acc = 0.f;
+      for (int bp = 0; bp < rb; ++bp) {
+        const cf c = F.VR[b * rb + bp], wv = F.Wst[i * rb + bp];
+        acc = fmaf(c.x, wv.x, fmaf(-c.y, wv.y, acc));
+      }
+      z[((long)a * m + i) * rb + b] = (T)acc;
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -241,6 +388,28 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
     }
     __syncthreads();
   }
+  // exact (FLS) preconditioner data, when both eigendecompositions succeeded
+  FlsSmem F;
+  const bool fls_on = P.fls && P.eig_status[0] == 0 && P.eig_status[1] == 0;
+  if (fls_on) {
+    const int ra = P.ra, rb = P.rb, m = P.m;
+    float* base = reinterpret_cast<float*>(eidx + kLocalOwnMax) + (P.smem_mats ? 4 * m * (m + 1) : 0);
+    cf* c = reinterpret_cast<cf*>((reinterpret_cast<uintptr_t>(base) + 15) & ~(uintptr_t)15);
+    F.lamL = c;
+    F.VL = F.lamL + ra;
+    F.VLi = F.VL + ra * ra;
+    F.lamR = F.VLi + ra * ra;
+    F.VR = F.lamR + rb;
+    F.VRi = F.VR + rb * rb;
+    F.Wst = F.VRi + rb * rb;
+    F.fib = reinterpret_cast<float*>(F.Wst + m * (ra > rb ? ra : rb));
+    const cf* gl = reinterpret_cast<const cf*>(P.eigL);
+    const cf* gr = reinterpret_cast<const cf*>(P.eigR);
+    for (int e = threadIdx.x; e < ra + 2 * ra * ra; e += NT) F.lamL[e] = gl[e];
+    for (int e = threadIdx.x; e < rb + 2 * rb * rb; e += NT) F.lamR[e] = gr[e];
+    __syncthreads();
+  }
+  cf* Ybuf = reinterpret_cast<cf*>(P.ybuf);
   auto E = [&](long k) -> long { return own_in_smem ? (long)eidx[k] : tm.elem(k); };
   const long N = tm.N;
   T* V = P.work;                       // (mr+1) x N   Arnoldi basis
@@ -329,7 +498,14 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
       const T* vj = V + (long)j * N;
       T* zj = Zs + (long)j * N;
       stamp();
-      tm.precond(vj, zj, Ttr, Tti, Zr, Zi, ld, scratch);   // own fibres only
+      if (fls_on) {
+        tm.sync();                                          // v_j complete
+        fls_phase_a(tm, vj, Ybuf, F, Ttr, Tti, Zr, Zi, ld);
+        tm.sync();                                          // Y complete
+        fls_phase_b(tm, Ybuf, zj, F);
+      } else {
+        tm.precond(vj, zj, Ttr, Tti, Zr, Zi, ld, scratch);  // own fibres only
+      }
       stamp();
       tm.sync();                                            // barrier 1: z_j complete
       stamp();
@@ -442,14 +618,32 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
 
 }  // namespace
 
+// Eigendecompositions of the two interface matrices, one warp each; output
+// layout per side: lam[r], V[r*r], Vinv[r*r] (complex binary32).
+__global__ void local_eig_kernel(const double* PL, int ra, const double* PR, int rb, cf* outL, cf* outR,
+                                 int* status) {
+  extern __shared__ __align__(16) unsigned char esm[];
+  const int w = threadIdx.x / 32;
+  const int r = (w == 0) ? ra : rb;
+  const double* A = (w == 0) ? PL : PR;
+  cf* out = (w == 0) ? outL : outR;
+  const size_t off = (w == 0) ? 0 : ((eig_smem_bytes(ra) + 15) & ~(size_t)15);
+  EigSmem es = eig_smem(esm + off, r);
+  const bool ok = warp_eig(A, r, r, es, out, out + r, r, out + r + (long)r * r, r);
+  if ((threadIdx.x & 31) == 0) status[w] = ok ? 0 : 1;
+}
+
 template <typename T>
 size_t local_work_elems(long N, int mr) {
   return (size_t)(2 * mr + 2) * N;
 }
 
-size_t local_smem_bytes(int m, bool mats) {
+size_t local_smem_bytes(int m, bool mats, int ra = 0, int rb = 0, bool fls = false) {
   size_t s = (size_t)NW * 5 * kLocalMaxM * sizeof(float) + (size_t)kLocalOwnMax * sizeof(int);
   if (mats) s += (size_t)4 * m * (m + 1) * sizeof(float);
+  if (fls)
+    s += sizeof(cf) * ((size_t)2 * ra * ra + (size_t)2 * rb * rb + ra + rb + (size_t)m * std::max(ra, rb)) +
+         (size_t)NW * 8 * kLocalMaxM * sizeof(float) + 64;
   return s;
 }
 
@@ -461,7 +655,22 @@ t2s2_status local_gmres(const LocalProblem<T>& P, cudaStream_t st) {
   LocalProblem<T> Q = P;
   Q.smem_mats = local_smem_bytes(P.m, true) <= kLocalSmemCap;
   if (!Q.smem_mats && (!Q.Ttc_r || !Q.Ttc_i)) return T2S2_EINVAL;
-  const size_t smem = local_smem_bytes(P.m, Q.smem_mats);
+  Q.fls = P.fls && Q.smem_mats && P.eigL && P.eigR && P.ybuf && P.eig_status && P.ra <= kEigMax &&
+          P.rb <= kEigMax && local_smem_bytes(P.m, true, P.ra, P.rb, true) <= kLocalSmemCap;
+  const size_t smem = local_smem_bytes(P.m, Q.smem_mats, P.ra, P.rb, Q.fls);
+  if (Q.fls) {
+    static bool eattr = false;
+    const size_t esm = ((eig_smem_bytes(P.ra) + 15) & ~(size_t)15) + eig_smem_bytes(P.rb);
+    if (!eattr) {
+      T2S2_CUDA_TRY(cudaFuncSetAttribute(local_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * eig_smem_bytes(kEigMax) + 16)));
+      eattr = true;
+    }
+    TraceScope ts(kTrSmall, st, 40.0 * ((double)P.ra * P.ra * P.ra + (double)P.rb * P.rb * P.rb), 0.0);
+    local_eig_kernel<<<1, 64, esm, st>>>(P.PL, P.ra, P.PR, P.rb, reinterpret_cast<cf*>(P.eigL),
+                                          reinterpret_cast<cf*>(P.eigR), P.eig_status);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
   static int attr_done[2] = {0, 0};
   if (!attr_done[ti]) {
     T2S2_CUDA_TRY(cudaFuncSetAttribute(gmres_team_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

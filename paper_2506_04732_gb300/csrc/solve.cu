@@ -83,6 +83,10 @@ struct Amen {
   int* gm_iters = nullptr;
   double* gm_res = nullptr;
   double* svals = nullptr;
+  double* eig_buf = nullptr;  // complex binary32 eigen data of both interfaces
+  double* ybuf = nullptr;     // complex binary32 intermediate of the exact preconditioner
+  int* eig_status = nullptr;
+  bool use_fls = true;
   float* fbuf = nullptr;     // FP32 rhs / x / GMRES basis for the mixed-precision local solves
   bool fp32_local = false;
   long long local_iters = 0;
@@ -102,6 +106,7 @@ struct Amen {
     s += 10 * (size_t)(d + 1) * R * R;          // interfaces
     s += 12 * core;                             // temporaries
     s += (size_t)(2 * mr + 2) * rcap * mm * rcap;  // flexible GMRES bases
+    s += (size_t)rcap * mm * rcap + 2 * (R + 2 * R * R) + 8;  // exact preconditioner buffers
     s += kLocalPartElems + 64;
     s += (size_t)d * mm * mm;                   // B'
     // residual evaluation: apply output, sum, orthogonalisation temporaries
@@ -194,6 +199,15 @@ struct Amen {
     gm_res = aget<double>(c, 4);
     svals = aget<double>(c, kSmallMax);
     {
+      const char* e = std::getenv("T2S2_LOCAL_PRECOND");
+      use_fls = !(e && e[0] == 'd');  // "diag": per-fibre diagonal shifts only
+      const size_t side = (size_t)R + 2 * (size_t)R * R;  // complex values per side
+      eig_buf = aget<double>(c, 2 * side);                 // 8 bytes per complex binary32
+      ybuf = aget<double>(c, (size_t)rcap * mmax * rcap);
+      eig_status = reinterpret_cast<int*>(aget<double>(c, 1));
+      if (!eig_buf || !ybuf || !eig_status) return T2S2_ENOMEM;
+    }
+    {
       const char* e = std::getenv("T2S2_LOCAL_TIMING");
       tstamp_req = e && e[0] >= '0' && e[0] <= '9';
       tstamp_target = tstamp_req ? std::atoi(e) : 0;
@@ -277,6 +291,11 @@ struct Amen {
     P.mr = gm_restart;
     P.iters_out = gm_iters;
     P.res_out = gm_res;
+    P.fls = use_fls ? 1 : 0;
+    P.eigL = eig_buf;
+    P.eigR = eig_buf + (size_t)R + 2 * (size_t)R * R;
+    P.eig_status = eig_status;
+    P.ybuf = ybuf;
     const bool stamp_this = tstamp_req && !tstamp_done && local_count == tstamp_target;
     ++local_count;
     if (stamp_this) P.tstamp = tstamp_dev;
