@@ -42,6 +42,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle CPU work for the cpu_baseline sample")
+    ap.add_argument("--workload", default="steady", choices=["steady", "batched", "cn"],
+                    help="steady: d=6 n=32 solve (headline); batched: 256 d=5 instances; "
+                         "cn: Crank-Nicolson steps at d=7 n=64")
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--workers", type=int, default=8)
     return ap.parse_args()
 
 
@@ -217,10 +222,96 @@ def run_reference(args):
 SWEEPS_NEEDED_HINT = 7
 
 
+def run_batched(args, T, P, W, torch):
+    """256 independent d=5 instances (n in {16,24,32,48}) solved by one batched call."""
+    import numpy as np
+    probs = [W.config3(i) for i in range(args.instances)]
+    ops, bs, xs0 = [], [], []
+    for p in probs:
+        op = P.build_operator(p)
+        ops.append(op)
+        bs.append(T.TT.from_cores(P.source_cores(p, op)))
+        xs0.append([np.ones((1, n - 2, 1)) for n in p.n])
+
+    def fresh():
+        return [T.TT.from_cores(c, rcap=20) for c in xs0]
+
+    for _ in range(max(1, args.warmup)):
+        T.t2s2_solve_batched(ops, bs, fresh(), 1e-8, 16, 50, workers=args.workers, allow_noconv=True)
+    torch.cuda.synchronize()
+    times, infos = [], None
+    for _ in range(args.steps):
+        xs = fresh()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = T.t2s2_solve_batched(ops, bs, xs, 1e-8, 16, 50, workers=args.workers, allow_noconv=True)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    batched = args.instances * len(times) / sum(times)
+    # sequential plain solves of a subset, one instance after the other
+    nseq = min(32, args.instances)
+    xs = fresh()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(nseq):
+        T.t2s2_solve(ops[i], bs[i], xs[i], 1e-8, 16, 50, allow_noconv=True)
+    torch.cuda.synchronize()
+    seq = nseq / (time.perf_counter() - t0)
+    conv = sum(1 for inf in infos if inf.residual <= 1e-8)
+    line = {"metric": "solves/sec to rel. residual 1e-8 (256 batched d=5 instances)", "value": batched,
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.instances} instances d=5 n in {{16,24,32,48}}",
+                       "workers": args.workers, "converged": conv,
+                       "max_sweeps": max(inf.sweeps for inf in infos),
+                       "sequential_solves_per_s": seq, "sequential_sample": nseq}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_cn(args, T, P, W, torch):
+    """Crank-Nicolson steps of the d=7, n=64 Gaussian pulse (dt = 1e-3, rmax 40, tol 1e-8)."""
+    p = W.config2()
+    op = P.build_operator(p)
+    u = T.TT.from_cores(P.solution_cores(p, op), rcap=p.rmax + 4)
+    infos = []
+    for _ in range(args.warmup):
+        infos.append(T.t2s2_cn_step(op, u, p.dt, p.tol, p.rmax))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        infos.append(T.t2s2_cn_step(op, u, p.dt, p.tol, p.rmax))
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": "Crank-Nicolson steps/sec (d=7, n=64, dt=1e-3, tol 1e-8)", "value": 1e3 / ms,
+            "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": p.name, "rmax": p.rmax, "ranks": u.r,
+                       "step_residuals": [inf.residual for inf in infos],
+                       "sweeps": [inf.sweeps for inf in infos]}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "steady":
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__ as g
+        g.build()
+        import paper_2506_04732_gb300 as T
+        from paper_2506_04732_gb300 import problem as P
+        import workloads as W
+        return (run_batched if args.workload == "batched" else run_cn)(args, T, P, W, torch)
     ws, rank, local = dist_env()
     import torch
     if ws > 1:

@@ -196,6 +196,22 @@ t2s2_status t2s2_solve(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double c_mass, 
                        void* stream, t2s2_solve_info* info);
 
 /*
+ * Batched form of t2s2_solve (c_mass = 0, c_op = 1): `count` independent
+ * instances, instance i with operator ops[i] (distinct handles: each owns its
+ * workspace), right-hand side b[i] and initial guess / solution x[i].
+ * Instances run concurrently on `workers` host threads (<= 0: 8), each with
+ * its own CUDA stream; every instance's cooperative local solves use at most
+ * 152 / workers CTAs so that the workers share the GPU.  Per-instance
+ * statuses go to statuses[i] and, if infos != NULL, details to infos[i].
+ * Returns the first hard error, else T2S2_ENOCONV if any instance hit its
+ * sweep cap, else T2S2_OK.  Errors: T2S2_EINVAL for NULL arrays or a repeated
+ * operator handle.
+ */
+t2s2_status t2s2_solve_batched(const t2s2_op* ops, const t2s2_tt* b, t2s2_tt* x, int count, double tol,
+                               int rmax, int max_sweeps, t2s2_precision prec, int workers,
+                               t2s2_solve_info* infos, t2s2_status* statuses);
+
+/*
  * One Crank-Nicolson step (eq. ttss-Crank-Nicolson) with the collocated time
  * derivative (mass matrix M):  rhs = rndg((M - dt/2 A) u), then solve
  * (M + dt/2 A) u+ = rhs from the initial guess u; u is overwritten by u+.

@@ -19,7 +19,7 @@ import numpy as np
 
 __all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REFINE",
            "TF32_REFINE", "BF16_REFINE", "t2s2_build_operator", "t2s2_apply", "t2s2_round",
-           "t2s2_norm", "t2s2_norm_noalloc", "t2s2_residual", "t2s2_solve", "t2s2_cn_step", "t2s2_be_step",
+           "t2s2_norm", "t2s2_norm_noalloc", "t2s2_residual", "t2s2_solve", "t2s2_solve_batched", "t2s2_cn_step", "t2s2_be_step",
            "t2s2_device_count", "t2s2_strerror", "lib_path"]
 
 FP64, FP32_REFINE, TF32_REFINE, BF16_REFINE = 0, 1, 2, 3
@@ -91,6 +91,10 @@ _SIGS = {
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.POINTER(_Info)]),
+    "t2s2_solve_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_TT),
+                                          ctypes.POINTER(_TT), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(_Info), ctypes.POINTER(ctypes.c_int)]),
     "t2s2_cn_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.POINTER(_Info)]),
@@ -310,6 +314,23 @@ def t2s2_solve(op: Operator, b: TT, x: TT, tol, rmax, max_sweeps=50, prec=FP64, 
     _check(st, "t2s2_solve", ok=(0, 4) if allow_noconv else (0,))
     x._sync_ranks()
     return _info(st, info)
+
+
+def t2s2_solve_batched(ops, bs, xs, tol, rmax, max_sweeps=50, prec=FP64, workers=8,
+                       allow_noconv=False):
+    """Solve len(ops) independent steady problems concurrently; returns SolveInfo per instance."""
+    n = len(ops)
+    harr = (ctypes.c_void_p * n)(*[o.handle.value if hasattr(o.handle, "value") else o.handle for o in ops])
+    barr = (_TT * n)(*[b._struct() for b in bs])
+    xarr = (_TT * n)(*[x._struct() for x in xs])
+    infos = (_Info * n)()
+    sts = (ctypes.c_int * n)()
+    st = load().t2s2_solve_batched(harr, barr, xarr, n, float(tol), int(rmax), int(max_sweeps), int(prec),
+                                   int(workers), infos, sts)
+    _check(st, "t2s2_solve_batched", ok=(0, 4) if allow_noconv else (0,))
+    for i, x in enumerate(xs):
+        x.r = [int(xarr[i].r[k]) for k in range(x.d + 1)]
+    return [_info(sts[i], infos[i]) for i in range(n)]
 
 
 def t2s2_cn_step(op: Operator, u: TT, dt, tol, rmax, prec=FP64, stream=None) -> SolveInfo:

@@ -26,6 +26,7 @@ struct t2s2_op_s {
   float* fmat = nullptr;  // FP32 copies of all of the above, same layout
   float* fptr[kMatsPerDim][T2S2_MAX_D] = {{nullptr}};
   t2s2::Arena arena;
+  int team = 0;            // CTAs per cooperative local solve (0: whole GPU)
   double* hbuf = nullptr;  // pinned host scratch
   int* dstat = nullptr;    // device status words
   void free_solver_buffers();
@@ -43,6 +44,9 @@ t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mas
                      bool transformed);
 t2s2_status apply_dispatch(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass,
                            double c_op, t2s2_precision prec);
+t2s2_status tt_dot(Ctx& cx, const DevTT& u, const DevTT& v, double* out);
+t2s2_status residual_estimate(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
+                              double c_op, double bb, double* out);
 t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
                           double c_op, bool transformed, double* out, double* bnorm_io);
 }  // namespace t2s2

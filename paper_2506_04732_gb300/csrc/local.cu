@@ -357,14 +357,14 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
   __shared__ double dots[kLocalMaxRestart + 2];
   __shared__ double red2[(kLocalMaxRestart + 2) * 8];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  float* scratch = reinterpret_cast<float*>(dyn_smem);  // NW * 5 * kLocalMaxM
-  int* eidx = reinterpret_cast<int*>(scratch + NW * 5 * kLocalMaxM);  // own element indices
+  float* scratch = reinterpret_cast<float*>(dyn_smem);  // NW * 8 * kLocalMaxM, either preconditioner
+  int* eidx = reinterpret_cast<int*>(scratch + NW * 8 * kLocalMaxM);  // own element indices
   const float *Ttr, *Tti, *Zr, *Zi;
   int ld;
-  const bool own_in_smem = tm.nown <= kLocalOwnMax;
+  const bool own_in_smem = tm.nown <= P.own_cap;
   {
     const int m = P.m;
-    float* after_idx = reinterpret_cast<float*>(eidx + kLocalOwnMax);
+    float* after_idx = reinterpret_cast<float*>(eidx + P.own_cap);
     if (own_in_smem)
       for (long k = threadIdx.x; k < tm.nown; k += NT) eidx[k] = (int)tm.elem(k);
     if (P.smem_mats) {
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
   const bool fls_on = P.fls && P.eig_status[0] == 0 && P.eig_status[1] == 0;
   if (fls_on) {
     const int ra = P.ra, rb = P.rb, m = P.m;
-    float* base = reinterpret_cast<float*>(eidx + kLocalOwnMax) + (P.smem_mats ? 4 * m * (m + 1) : 0);
+    float* base = reinterpret_cast<float*>(eidx + P.own_cap) + (P.smem_mats ? 4 * m * (m + 1) : 0);
     cf* c = reinterpret_cast<cf*>((reinterpret_cast<uintptr_t>(base) + 15) & ~(uintptr_t)15);
     F.lamL = c;
     F.VL = F.lamL + ra;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
     F.VR = F.lamR + rb;
     F.VRi = F.VR + rb * rb;
     F.Wst = F.VRi + rb * rb;
-    F.fib = reinterpret_cast<float*>(F.Wst + m * (ra > rb ? ra : rb));
+    F.fib = scratch;
     const cf* gl = reinterpret_cast<const cf*>(P.eigL);
     const cf* gr = reinterpret_cast<const cf*>(P.eigR);
     for (int e = threadIdx.x; e < ra + 2 * ra * ra; e += NT) F.lamL[e] = gl[e];
@@ -638,12 +638,11 @@ size_t local_work_elems(long N, int mr) {
   return (size_t)(2 * mr + 2) * N;
 }
 
-size_t local_smem_bytes(int m, bool mats, int ra = 0, int rb = 0, bool fls = false) {
-  size_t s = (size_t)NW * 5 * kLocalMaxM * sizeof(float) + (size_t)kLocalOwnMax * sizeof(int);
+size_t local_smem_bytes(int m, bool mats, int own_cap, int ra = 0, int rb = 0, bool fls = false) {
+  size_t s = (size_t)NW * 8 * kLocalMaxM * sizeof(float) + (size_t)own_cap * sizeof(int);
   if (mats) s += (size_t)4 * m * (m + 1) * sizeof(float);
   if (fls)
-    s += sizeof(cf) * ((size_t)2 * ra * ra + (size_t)2 * rb * rb + ra + rb + (size_t)m * std::max(ra, rb)) +
-         (size_t)NW * 8 * kLocalMaxM * sizeof(float) + 64;
+    s += sizeof(cf) * ((size_t)2 * ra * ra + (size_t)2 * rb * rb + ra + rb + (size_t)m * std::max(ra, rb)) + 64;
   return s;
 }
 
@@ -653,11 +652,21 @@ t2s2_status local_gmres(const LocalProblem<T>& P, cudaStream_t st) {
   const long N = (long)P.ra * P.m * P.rb;
   const int ti = sizeof(T) == 8 ? 0 : 1;
   LocalProblem<T> Q = P;
-  Q.smem_mats = local_smem_bytes(P.m, true) <= kLocalSmemCap;
+  int dev0 = 0, sms0 = 0;
+  T2S2_CUDA_TRY(cudaGetDevice(&dev0));
+  T2S2_CUDA_TRY(cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0));
+  {
+    // own-element list sized for the smallest team this launch may use
+    const long nf = (long)P.ra * P.rb;
+    const int gmin = (P.team > 0) ? std::min(P.team, sms0) : sms0;  // larger than the team only if occupancy-limited: then indices are recomputed
+    const long per = ((nf + gmin - 1) / gmin) * P.m;
+    Q.own_cap = (int)std::min<long>(per, kLocalOwnMax);
+  }
+  Q.smem_mats = local_smem_bytes(P.m, true, Q.own_cap) <= kLocalSmemCap;
   if (!Q.smem_mats && (!Q.Ttc_r || !Q.Ttc_i)) return T2S2_EINVAL;
   Q.fls = P.fls && Q.smem_mats && P.eigL && P.eigR && P.ybuf && P.eig_status && P.ra <= kEigMax &&
-          P.rb <= kEigMax && local_smem_bytes(P.m, true, P.ra, P.rb, true) <= kLocalSmemCap;
-  const size_t smem = local_smem_bytes(P.m, Q.smem_mats, P.ra, P.rb, Q.fls);
+          P.rb <= kEigMax && local_smem_bytes(P.m, true, Q.own_cap, P.ra, P.rb, true) <= kLocalSmemCap;
+  const size_t smem = local_smem_bytes(P.m, Q.smem_mats, Q.own_cap, P.ra, P.rb, Q.fls);
   if (Q.fls) {
     static bool eattr = false;
     const size_t esm = ((eig_smem_bytes(P.ra) + 15) & ~(size_t)15) + eig_smem_bytes(P.rb);

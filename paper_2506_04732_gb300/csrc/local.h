@@ -25,6 +25,7 @@ struct LocalProblem {
   int maxit = 400, mr = 30, team = 0;  // team = 0: pick the number of CTAs
   const float *Ttc_r = nullptr, *Ttc_i = nullptr;  // (c_op T)^T in global memory when m is too big for smem
   int smem_mats = 0;                   // set by the launcher
+  int own_cap = 0;                     // set by the launcher: own-element indices kept in smem
   int fls = 0;                         // 1: exact Kronecker-sum preconditioner (needs the buffers below)
   void* eigL = nullptr;                // complex binary32: lam[ra], V[ra*ra], Vinv[ra*ra]
   void* eigR = nullptr;                // complex binary32: lam[rb], V[rb*rb], Vinv[rb*rb]

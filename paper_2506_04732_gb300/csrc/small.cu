@@ -142,12 +142,33 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
           gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
         }
         if (gamma != 0.0 && gamma * gamma > 1e-30 * alpha * beta) {
-          // tan of the rotation angle: t = 2 gamma sign(beta - alpha) /
-          // (|beta - alpha| + sqrt((beta - alpha)^2 + 4 gamma^2)), the smaller root
-          const double diff = beta - alpha;
-          const double root = dsqrt(fma(diff, diff, 4.0 * gamma * gamma));
-          const double tt = (diff >= 0.0 ? 2.0 * gamma : -2.0 * gamma) * drcp(fabs(diff) + root);
-          const double cs = drsqrt(fma(tt, tt, 1.0)), sn = cs * tt;
+          // Rotation angle in binary32 (only its orthogonality must be exact):
+          // t = 2 gamma sign(beta - alpha) / (|beta - alpha| + sqrt((beta - alpha)^2 + 4 gamma^2)).
+          // Near convergence a binary32 angle still cuts gamma by ~1e-7 per sweep.
+          const double diff = beta - alpha, g2 = 2.0 * gamma;
+          const double mm = fmax(fabs(diff), fabs(g2));
+          float df, gf;
+          if (mm > 1e-30 && mm < 1e30) {
+            const float inv = 1.0f / (float)mm;
+            df = (float)diff * inv;
+            gf = (float)g2 * inv;
+          } else {
+            const double inv = 1.0 / mm;
+            df = (float)(diff * inv);
+            gf = (float)(g2 * inv);
+          }
+          const float tf = (df >= 0.f ? gf : -gf) / (fabsf(df) + sqrtf(fmaf(df, df, gf * gf)));
+          double cs = (double)rsqrtf(fmaf(tf, tf, 1.0f));
+          double sn = cs * (double)tf;
+          // renormalise in binary64: two Newton steps on 1/sqrt(cs^2 + sn^2)
+          double n2 = fma(cs, cs, sn * sn);
+          double f = fma(-0.5, n2, 1.5);
+          cs *= f;
+          sn *= f;
+          n2 = fma(cs, cs, sn * sn);
+          f = fma(-0.5, n2, 1.5);
+          cs *= f;
+          sn *= f;
           for (int i = lane; i < rows; i += 32) {
             double x = wa[i], y = wb[i];
             wa[i] = cs * x - sn * y;

@@ -19,7 +19,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <random>
+#include <thread>
 #include <vector>
 
 #include "api_internal.h"
@@ -65,7 +67,50 @@ t2s2_status d2d(Ctx& cx, double* dst, const double* src, size_t n) {
 }
 t2s2_status set_scalar(Ctx& cx, double* dst, double v) { return dev_fill(cx, dst, 1, v); }
 
+// Optional per-phase timing of the solver (T2S2_PHASES=1): CUDA events at the
+// phase boundaries on the solver's stream, summed and printed per solve.
+struct PhaseTimer {
+  static constexpr int kPhases = 11;
+  bool on = false;
+  cudaStream_t st = 0;
+  int cur = -1;
+  std::vector<std::pair<int, cudaEvent_t>> marks;
+  void start(cudaStream_t s) {
+    const char* e = std::getenv("T2S2_PHASES");
+    on = e && e[0] == '1';
+    st = s;
+  }
+  void phase(int p) {
+    if (!on) return;
+    cudaEvent_t ev;
+    cudaEventCreate(&ev);
+    cudaEventRecord(ev, st);
+    marks.push_back({p, ev});
+  }
+  void report() {
+    if (!on || marks.empty()) return;
+    static const char* names[kPhases] = {"init", "right_ifaces", "local_rhs", "local_solve", "truncate",
+                                         "enrich", "z_update", "new_core", "left_ifaces", "residual", "orth_x"};
+    double tot[kPhases] = {0};
+    cudaEventSynchronize(marks.back().second);
+    for (size_t i = 0; i + 1 < marks.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, marks[i].second, marks[i + 1].second);
+      tot[marks[i].first] += ms;
+    }
+    fprintf(stderr, "[t2s2] phases (ms):");
+    for (int i = 0; i < kPhases; ++i) fprintf(stderr, " %s %.2f", names[i], tot[i]);
+    fprintf(stderr, "\n");
+    for (auto& m : marks) cudaEventDestroy(m.second);
+    marks.clear();
+  }
+};
+
 struct Amen {
+  PhaseTimer* pt = nullptr;
+  void ph(int p) {
+    if (pt) pt->phase(p);
+  }
   t2s2_op op = nullptr;
   Ctx* cx = nullptr;
   int d = 0, kick = 4, rcap = 0, rmax = 0, mmax = 0, R = 0;
@@ -292,6 +337,7 @@ struct Amen {
     P.iters_out = gm_iters;
     P.res_out = gm_res;
     P.fls = use_fls ? 1 : 0;
+    P.team = op->team;
     P.eigL = eig_buf;
     P.eigR = eig_buf + (size_t)R + 2 * (size_t)R * R;
     P.eig_status = eig_status;
@@ -351,9 +397,11 @@ struct Amen {
   // One forward sweep k = 0 .. d-1.
   t2s2_status sweep() {
     Ctx& c = *cx;
+    ph(1);
     T2S2_TRY(right_interfaces());
     T2S2_TRY(left_boundary());
     for (int k = 0; k < d; ++k) {
+      ph(2);
       const int m = op->m[k];
       const int ra = x.r[k], rb = x.r[k + 1], fa = f.r[k], fb = f.r[k + 1], za = z.r[k], zb = z.r[k + 1];
       const double* F = f.c[k];
@@ -362,7 +410,9 @@ struct Amen {
       T2S2_TRY(mode1(c, FL[k], ra, fa, F, m, fb, T1));
       T2S2_TRY(mode3(c, T1, ra, m, fb, FR[k + 1], rb, rhs));
       T2S2_TRY(d2d(c, X, x.c[k], (size_t)ra * m * rb));
+      ph(3);
       T2S2_TRY(local_solve(k, rhs, X));
+      ph(4);
       if (k == d - 1) {
         T2S2_TRY(d2d(c, x.c[k], X, (size_t)ra * m * rb));
         T2S2_CUDA_TRY(cudaMemcpyAsync(c.hbuf + 8, gm_iters, sizeof(int), cudaMemcpyDeviceToHost, c.st));
@@ -407,6 +457,7 @@ struct Amen {
       }
       T2S2_TRY(dev_sv_t(c, SV, svals, Vx, rk, rb, kk));
       T2S2_TRY(gemm_ex<double>(c, rows, rb, rk, false, false, 1.0, U, rk, SV, rb, 0.0, Xt, rb));
+      ph(5);
       // --- enrichment directions: residual on (x-left) x m x (z-right)
       double *BX = tmp[5], *Y1 = tmp[6], *res = tmp[7], *zres = tmp[8];
       T2S2_TRY(mode2(c, Bp[k], m, Xt, ra, rb, BX));
@@ -416,6 +467,7 @@ struct Amen {
       T2S2_TRY(mode3(c, T1, ra, m, fb, ZFR[k + 1], zb, res));
       T2S2_TRY(mode3(c, Y1, ra, m, rb, ZIR[k + 1], zb, res, -1.0, 1.0));
       T2S2_TRY(mode3(c, Xt, ra, m, rb, ZBR[k + 1], zb, res, -1.0, 1.0));
+      ph(6);
       // --- z update: residual on (z-left) x m x (z-right)
       T2S2_TRY(mode1(c, ZFL[k], za, fa, F, m, fb, T1));
       T2S2_TRY(mode3(c, T1, za, m, fb, ZFR[k + 1], zb, zres));
@@ -430,6 +482,7 @@ struct Amen {
         T2S2_TRY(qr_tall(c, zres, za * m, zb, Qz, Rz));
         T2S2_TRY(d2d(c, z.c[k], Qz, (size_t)za * m * zb));
       }
+      ph(7);
       // --- new core: orthonormal basis of [U | res]
       int cols = rk + zb;
       double* Q = tmp[2];
@@ -461,6 +514,7 @@ struct Amen {
         T2S2_TRY(d2d(c, x.c[k], Q, (size_t)rows * rn));
         x.r[k + 1] = rn;
       }
+      ph(8);
       // --- left interfaces for bond k+1
       {
         const double* Qc = x.c[k];
@@ -489,6 +543,10 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
                        double tol, int rmax, int max_sweeps, t2s2_precision prec, t2s2_solve_info* info) {
   (void)prec;
   Amen am;
+  PhaseTimer pt;
+  pt.start(cx.st);
+  am.pt = &pt;
+  am.ph(0);
   T2S2_TRY(am.init(op, cx, b, xio, c_mass, c_op, tol, rmax));
   T2S2_TRY(tt_orth_right(cx, am.x));
   double bnorm = -1.0, res = 0.0;
@@ -501,7 +559,17 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
   while (res > tol && sweeps < max_sweeps) {
     T2S2_TRY(am.sweep());
     ++sweeps;
-    T2S2_TRY(residual_impl(op, cx, b, am.x, c_mass, c_op, false, &res, &bnorm));
+    am.ph(9);
+    // Screen with the dot-product residual while it is far above tolerance
+    // (there its cancellation error, ~sqrt(eps), is irrelevant); the
+    // accurate orthogonalised residual alone decides convergence.
+    double est = 0.0;
+    if (tol < 1e-6) T2S2_TRY(residual_estimate(op, cx, b, am.x, c_mass, c_op, bnorm * bnorm, &est));
+    if (tol < 1e-6 && est > 1e-5) {
+      res = est;
+    } else {
+      T2S2_TRY(residual_impl(op, cx, b, am.x, c_mass, c_op, false, &res, &bnorm));
+    }
     if (verbose) {
       double rt = 0.0;
       T2S2_TRY(residual_impl(op, cx, am.f, am.x, c_mass, c_op, true, &rt, nullptr));
@@ -510,8 +578,11 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
       fprintf(stderr, " local_iters %lld\n", am.local_iters);
     }
     if (res <= tol) break;
+    am.ph(10);
     T2S2_TRY(tt_orth_right(cx, am.x));
   }
+  am.ph(0);
+  pt.report();
   // copy out
   for (int k = 0; k < op->d; ++k)
     if (am.x.core_elems(k) > xio.cap[k]) return T2S2_ENOMEM;
@@ -582,11 +653,64 @@ static t2s2_status step_entry(t2s2_op op, t2s2_tt* u, double dt, double tol, int
   return st2 != T2S2_OK ? st2 : st;
 }
 
+// Batched steady solves: `count` independent instances, each with its own
+// operator (and so its own workspace).  Worker threads take instances from a
+// shared counter; each worker owns a CUDA stream, and every instance's
+// cooperative local solves are limited to kNumSMs / workers CTAs so that the
+// workers' teams fit on the GPU side by side.
+static t2s2_status solve_batched_entry(const t2s2_op* ops, const t2s2_tt* b, t2s2_tt* x, int count,
+                                       double tol, int rmax, int max_sweeps, t2s2_precision prec,
+                                       int workers, t2s2_solve_info* infos, t2s2_status* statuses) {
+  if (!ops || !b || !x || count < 0 || !statuses) return T2S2_EINVAL;
+  if (count == 0) return T2S2_OK;
+  for (int i = 0; i < count; ++i) {
+    if (!ops[i]) return T2S2_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ops[j] == ops[i]) return T2S2_EINVAL;  // instances may not share a workspace
+  }
+  if (workers <= 0) workers = 8;
+  workers = std::min(workers, count);
+  int dev = 0;
+  T2S2_CUDA_TRY(cudaGetDevice(&dev));
+  std::vector<cudaStream_t> streams(workers);
+  for (auto& s : streams) T2S2_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  const int team = std::max(1, kNumSMs / workers);
+  std::atomic<int> next{0};
+  auto work = [&](int w) {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) break;
+      const int saved = ops[i]->team;
+      ops[i]->team = team;
+      statuses[i] = solve_entry(ops[i], &b[i], &x[i], 0.0, 1.0, tol, rmax, max_sweeps, prec, streams[w],
+                                infos ? &infos[i] : nullptr);
+      ops[i]->team = saved;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < workers; ++w) th.emplace_back(work, w);
+  work(0);
+  for (auto& t : th) t.join();
+  for (auto& s : streams) cudaStreamDestroy(s);
+  for (int i = 0; i < count; ++i)
+    if (statuses[i] != T2S2_OK && statuses[i] != T2S2_ENOCONV) return statuses[i];
+  for (int i = 0; i < count; ++i)
+    if (statuses[i] == T2S2_ENOCONV) return T2S2_ENOCONV;
+  return T2S2_OK;
+}
+
 }  // namespace t2s2
 
 using namespace t2s2;
 
 extern "C" {
+t2s2_status t2s2_solve_batched(const t2s2_op* ops, const t2s2_tt* b, t2s2_tt* x, int count, double tol,
+                               int rmax, int max_sweeps, t2s2_precision prec, int workers,
+                               t2s2_solve_info* infos, t2s2_status* statuses) {
+  return solve_batched_entry(ops, b, x, count, tol, rmax, max_sweeps, prec, workers, infos, statuses);
+}
+
 t2s2_status t2s2_solve(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double c_mass, double c_op,
                        double tol, int rmax, int max_sweeps, t2s2_precision prec, void* stream,
                        t2s2_solve_info* info) {

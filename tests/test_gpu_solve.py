@@ -138,3 +138,42 @@ def test_solve_config1_full_size(T):
     assert r_or <= p.tol * 1.01
     us = O.solution_tt(p, ops)
     assert OT.diff_norm(x.cores(), us) <= 1e-6 * OT.norm(us)
+
+
+def test_solve_batched_matches_sequential(T):
+    from paper_2506_04732_gb300 import problem as P
+    probs = [W.config3(i) for i in range(6)]
+    ops, bs, xs, xs_seq = [], [], [], []
+    for p in probs:
+        op = P.build_operator(p)
+        ops.append(op)
+        bs.append(T.TT.from_cores(P.source_cores(p, op)))
+        m = [n - 2 for n in p.n]
+        xs.append(T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + 4))
+        xs_seq.append(T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + 4))
+    infos = T.t2s2_solve_batched(ops, bs, xs, 1e-8, 16, 50, workers=3)
+    for i, p in enumerate(probs):
+        assert infos[i].status == 0 and infos[i].residual <= 1e-8
+        seq = T.t2s2_solve(ops[i], bs[i], xs_seq[i], 1e-8, 16, 50)
+        # identical arithmetic on each instance: same iterates
+        assert abs(seq.residual - infos[i].residual) <= 1e-12
+        ops_o = O.build(p)
+        r = OS.residual(O.ttm_cores(ops_o), O.source_tt(p, ops_o), xs[i].cores())
+        assert r <= 1.01e-8
+
+
+def test_cn_step_config2_full_size_checked_by_oracle(T):
+    # d=7, n=64 Gaussian pulse: the oracle recomputes the step equation
+    # (M + dt/2 A) u1 = (M - dt/2 A) u0 on the GPU's u1; the bound is the rhs
+    # rounding tolerance plus the solve tolerance.
+    from paper_2506_04732_gb300 import problem as P
+    p = W.config2()
+    op = P.build_operator(p)
+    u = T.TT.from_cores(P.solution_cores(p, op), rcap=p.rmax + 4)
+    info = T.t2s2_cn_step(op, u, p.dt, p.tol, p.rmax)
+    assert info.residual <= p.tol and max(u.r) <= p.rmax + 4
+    ops = O.build(p)
+    u0 = O.solution_tt(p, ops)
+    lhs = OT.matvec(O.ttm_cores(ops, 1.0, 0.5 * p.dt), u.cores())
+    rhs = OT.matvec(O.ttm_cores(ops, 1.0, -0.5 * p.dt), u0)
+    assert OT.diff_norm(lhs, rhs) <= 2.0 * p.tol * OT.norm(rhs)
