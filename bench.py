@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solves/sec to rel. residual 1e-8 (d=6,n=32)"
 UNIT = "solves/s"
-FAMILIES = ["gemm", "apply", "local_solve", "small_factor", "elementwise"]
+FAMILIES = ["gemm", "apply", "local_solve", "small_factor", "elementwise", "apply_tc", "gemm_tc", "mlp"]
 
 
 def parse():

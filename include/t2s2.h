@@ -223,9 +223,29 @@ t2s2_status t2s2_cn_step(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax
 t2s2_status t2s2_be_step(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax,
                          t2s2_precision prec, void* stream, t2s2_solve_info* info);
 
+/*
+ * Strided-batched GEMM of the solver's core contractions, exported so that
+ * those kernels can be checked and timed on their own (the paper has no such
+ * call).  For b = 0 .. batch-1, with row-major FP64 device matrices,
+ *     C_b = alpha op(A_b) op(B_b) + beta C_b,   op(X) = X (t = 0) or X^T (t = 1),
+ * op(A_b) M x K at A + b sA (leading dimension lda), op(B_b) K x N at
+ * B + b sB (ldb), C_b M x N at C + b sC (ldc).  prec T2S2_FP64 or
+ * T2S2_FP32_REFINE: FP64 SIMT kernel; T2S2_TF32_REFINE / T2S2_BF16_REFINE:
+ * tcgen05 kernel with operands rounded to TF32 / BF16 and FP32 accumulation.
+ * Split-K workspace comes from the operator's arena.  Asynchronous on
+ * `stream` except for the tensor-core status check, which synchronises it.
+ * Errors: T2S2_EINVAL for negative sizes, null pointers or leading
+ * dimensions shorter than a stored row; T2S2_ETIMEOUT if a device wait gave up.
+ */
+t2s2_status t2s2_gemm(t2s2_op op, int M, int N, int K, int tA, int tB, double alpha, const double* A,
+                      long lda, long sA, const double* B, long ldb, long sB, double beta, double* C,
+                      long ldc, long sC, int batch, t2s2_precision prec, void* stream);
+
 /* ---- diagnostics ---------------------------------------------------------
- * Kernel families for tracing: 0 GEMM (SIMT contractions), 1 TT apply,
- * 2 local solve, 3 small factorisations (Cholesky, Jacobi SVD), 4 elementwise.
+ * Kernel families for tracing: 0 GEMM (SIMT contractions), 1 TT apply
+ * (FP64), 2 local solve, 3 small factorisations (Cholesky, Jacobi SVD),
+ * 4 elementwise, 5 TT apply on tensor cores (BF16/TF32), 6 GEMM on tensor
+ * cores (BF16/TF32), 7 warm-start network (forward, backward, Adam).
  */
 
 /* Number of CUDA kernels this library has launched in this process. */

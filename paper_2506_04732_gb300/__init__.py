@@ -20,7 +20,8 @@ import numpy as np
 __all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REFINE",
            "TF32_REFINE", "BF16_REFINE", "t2s2_build_operator", "t2s2_apply", "t2s2_round",
            "t2s2_norm", "t2s2_norm_noalloc", "t2s2_residual", "t2s2_solve", "t2s2_solve_batched", "t2s2_cn_step", "t2s2_be_step",
-           "t2s2_device_count", "t2s2_strerror", "lib_path"]
+           "t2s2_device_count", "t2s2_strerror", "t2s2_gemm", "t2s2_kernel_launches", "t2s2_trace",
+           "t2s2_trace_read", "TRACE_FAMILIES", "lib_path"]
 
 FP64, FP32_REFINE, TF32_REFINE, BF16_REFINE = 0, 1, 2, 3
 _DEVICE, _HOST = 0, 1
@@ -101,7 +102,21 @@ _SIGS = {
     "t2s2_be_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.POINTER(_Info)]),
+    "t2s2_gemm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_long, ctypes.c_long,
+                                 ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_double,
+                                 ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_void_p]),
+    "t2s2_kernel_launches": (ctypes.c_longlong, []),
+    "t2s2_trace": (ctypes.c_int, [ctypes.c_int]),
+    "t2s2_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
 }
+
+# Kernel families of t2s2_trace_read, in the library's order.
+TRACE_FAMILIES = ["gemm", "apply", "local_solve", "small_factor", "elementwise", "apply_tc", "gemm_tc",
+                  "mlp"]
 
 
 def load():
@@ -129,6 +144,53 @@ def t2s2_strerror(status: int) -> str:
 
 def t2s2_device_count() -> int:
     return int(load().t2s2_device_count())
+
+
+def t2s2_gemm(op: Operator, A, B, C, tA=False, tB=False, alpha=1.0, beta=0.0, prec=FP64, stream=None):
+    """C = alpha op(A) op(B) + beta C (t2s2_gemm) on float64 CUDA tensors.
+
+    2-D operands, or 3-D with a leading batch dimension; the last dimension
+    of each must be contiguous.  Returns C.
+    """
+    def lay(t):
+        if t.dim() == 2:
+            return t.shape[0], t.shape[1], t.stride(0), 0, 1
+        return t.shape[1], t.shape[2], t.stride(1), t.stride(0), t.shape[0]
+    ra, ca, lda, sA, ba = lay(A)
+    rb, cb, ldb, sB, bb = lay(B)
+    rc, cc, ldc, sC, bc = lay(C)
+    for t in (A, B, C):
+        if t.dtype.is_floating_point is False or t.element_size() != 8 or t.stride(-1) != 1:
+            raise ValueError("float64 tensors with a contiguous last dimension expected")
+    M, K = (ca, ra) if tA else (ra, ca)
+    K2, N = (cb, rb) if tB else (rb, cb)
+    if K2 != K or (rc, cc) != (M, N):
+        raise ValueError("shape mismatch")
+    batch = max(ba, bb, bc)
+    _check(load().t2s2_gemm(op.handle, M, N, K, int(tA), int(tB), float(alpha), A.data_ptr(), lda, sA,
+                            B.data_ptr(), ldb, sB, float(beta), C.data_ptr(), ldc, sC, batch, int(prec),
+                            _stream_handle(stream)), "t2s2_gemm")
+    return C
+
+
+def t2s2_kernel_launches() -> int:
+    """Kernels this library has launched in this process."""
+    return int(load().t2s2_kernel_launches())
+
+
+def t2s2_trace(enable: bool):
+    """Clear the per-family counters; turn CUDA-event timing on or off."""
+    _check(load().t2s2_trace(1 if enable else 0), "t2s2_trace")
+
+
+def t2s2_trace_read(family) -> dict:
+    """Launches, event ms, algorithmic FLOPs and bytes of one kernel family."""
+    idx = TRACE_FAMILIES.index(family) if isinstance(family, str) else int(family)
+    n = ctypes.c_longlong(0)
+    ms, fl, by = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().t2s2_trace_read(idx, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                  ctypes.byref(by)), "t2s2_trace_read")
+    return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
 
 
 def _check(status: int, what: str, ok=(0,)):

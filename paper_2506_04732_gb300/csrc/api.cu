@@ -106,8 +106,8 @@ t2s2_status unbind_tt(Ctx& cx, const DevTT& dv, t2s2_tt* t) {
 
 // y = (c_mass M + c_op A) x  (S = Rt, L = Lt) or the transformed operator
 // (S = I, L = B) when `transformed`.
-t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass, double c_op,
-                     bool transformed) {
+t2s2_status apply_batch(t2s2_op op, const DevTT& x, DevTT& y, double c_mass, double c_op, bool transformed,
+                        ApplyBatch& b) {
   const int d = op->d;
   y.d = d;
   y.r[0] = 1;
@@ -117,7 +117,6 @@ t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mas
     y.m[k] = x.m[k];
     if (y.core_elems(k) > y.cap[k]) return T2S2_ENOMEM;
   }
-  ApplyBatch b;
   b.ncores = d;
   for (int k = 0; k < d; ++k) {
     ApplyCore& c = b.c[k];
@@ -132,7 +131,41 @@ t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mas
     c.g_op = c_op;
     c.g_mass = (k == 0) ? c_mass : 0.0;
   }
+  return T2S2_OK;
+}
+
+t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass, double c_op,
+                     bool transformed) {
+  ApplyBatch b;
+  T2S2_TRY(apply_batch(op, x, y, c_mass, c_op, transformed, b));
   return apply_fp64(b, cx.st);
+}
+
+t2s2_status contract_gemm(Ctx& cx, const Gemm<double>& g) {
+  if (cx.contract_prec == T2S2_BF16_REFINE || cx.contract_prec == T2S2_TF32_REFINE) {
+    const size_t need = gemm_tc_workspace(g, cx.contract_prec);
+    const size_t mk = cx.ar->mark();
+    double* ws = need ? aget<double>(cx, need) : nullptr;
+    if (need && !ws) return T2S2_ENOMEM;
+    const t2s2_status s = gemm_tc(g, cx.contract_prec, ws, need, cx.dstat + kStatTensorCore, cx.st);
+    cx.ar->release(mk);
+    return s;
+  }
+  const size_t need = gemm_workspace(g);
+  const size_t mk = cx.ar->mark();
+  double* ws = need ? aget<double>(cx, need) : nullptr;
+  if (need && !ws) return T2S2_ENOMEM;
+  const t2s2_status s = gemm(g, ws, need, cx.st);
+  cx.ar->release(mk);
+  return s;
+}
+
+t2s2_status tensor_core_status(Ctx& cx) {
+  int h = 0;
+  T2S2_CUDA_TRY(cudaMemcpyAsync(cx.hbuf, cx.dstat + kStatTensorCore, sizeof(int), cudaMemcpyDeviceToHost, cx.st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(cx.st));
+  std::memcpy(&h, cx.hbuf, sizeof(int));
+  return h ? T2S2_ETIMEOUT : T2S2_OK;
 }
 
 size_t max_core(const t2s2_tt* t) {
@@ -372,6 +405,29 @@ t2s2_status t2s2_apply(t2s2_op op, const t2s2_tt* x, t2s2_tt* y, double c_mass, 
   T2S2_TRY(bind_tt(cx, y, dy, false));
   T2S2_TRY(apply_dispatch(op, cx, dx, dy, c_mass, c_op, prec));
   return unbind_tt(cx, dy, y);
+}
+
+t2s2_status t2s2_gemm(t2s2_op op, int M, int N, int K, int tA, int tB, double alpha, const double* A,
+                      long lda, long sA, const double* B, long ldb, long sB, double beta, double* C,
+                      long ldc, long sC, int batch, t2s2_precision prec, void* stream) {
+  if (!op || M < 0 || N < 0 || K < 0 || batch < 0) return T2S2_EINVAL;
+  if (prec < T2S2_FP64 || prec > T2S2_BF16_REFINE) return T2S2_EINVAL;
+  if (M == 0 || N == 0 || batch == 0) return T2S2_OK;
+  if (!C || ldc < N || (K > 0 && (!A || !B))) return T2S2_EINVAL;
+  if (K > 0 && (lda < (tA ? M : K) || ldb < (tB ? K : N))) return T2S2_EINVAL;
+  if (sA < 0 || sB < 0 || sC < 0) return T2S2_EINVAL;
+  Gemm<double> g;
+  g.M = M; g.N = N; g.K = K; g.tA = tA != 0; g.tB = tB != 0; g.alpha = alpha; g.beta = beta;
+  g.A = A; g.lda = lda; g.sA = sA; g.B = B; g.ldb = ldb; g.sB = sB;
+  g.C = C; g.ldc = ldc; g.sC = sC; g.batch = batch;
+  const bool tc = prec == T2S2_BF16_REFINE || prec == T2S2_TF32_REFINE;
+  const size_t ws = tc ? gemm_tc_workspace(g, prec) : gemm_workspace(g);
+  T2S2_TRY(ensure_arena(op, ws * sizeof(double) + ((size_t)1 << 20)));
+  Ctx cx = make_ctx(op, stream);
+  cx.contract_prec = tc ? prec : T2S2_FP64;
+  if (tc) T2S2_CUDA_TRY(cudaMemsetAsync(cx.dstat + kStatTensorCore, 0, sizeof(int), cx.st));
+  T2S2_TRY(contract_gemm(cx, g));
+  return tc ? tensor_core_status(cx) : T2S2_OK;
 }
 
 t2s2_status t2s2_round(t2s2_op op, t2s2_tt* x, double tol, int rmax, void* stream) {

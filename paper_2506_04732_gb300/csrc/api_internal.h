@@ -3,6 +3,7 @@
 #include <vector>
 
 #include "apply.h"
+#include "gemm_tc.h"
 #include "host_1d.h"
 #include "tt.h"
 
@@ -40,6 +41,15 @@ size_t max_core(const t2s2_tt* t);
 t2s2_status check_tt(t2s2_op op, const t2s2_tt* t);
 t2s2_status bind_tt(Ctx& cx, const t2s2_tt* t, DevTT& dv, bool upload);
 t2s2_status unbind_tt(Ctx& cx, const DevTT& dv, t2s2_tt* t);
+// Status words in op->dstat: word 0 for the small factorisations, word
+// kStatTensorCore for the tensor-core kernels' bounded waits.
+constexpr int kStatTensorCore = 16;
+// GEMM of the sweep's contractions in the context's contraction arithmetic.
+t2s2_status contract_gemm(Ctx& cx, const Gemm<double>& g);
+// Reads (synchronising) and reports the tensor-core wait status word.
+t2s2_status tensor_core_status(Ctx& cx);
+t2s2_status apply_batch(t2s2_op op, const DevTT& x, DevTT& y, double c_mass, double c_op, bool transformed,
+                        ApplyBatch& b);
 t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass, double c_op,
                      bool transformed);
 t2s2_status apply_dispatch(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass,

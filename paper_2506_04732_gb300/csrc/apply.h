@@ -24,4 +24,10 @@ __host__ __device__ inline int cdiv_dev(int a, int b) { return (a + b - 1) / b; 
 
 t2s2_status apply_fp64(const ApplyBatch& p, cudaStream_t st);
 
+// Same product on tcgen05 tensor cores with BF16 (prec = T2S2_BF16_REFINE) or
+// TF32 (T2S2_TF32_REFINE) operands and FP32 accumulation; needs m <= 64 for
+// every core.  A device wait that gives up sets *err (device int) to 1.
+bool apply_tc_supported(const ApplyBatch& p);
+t2s2_status apply_tc(const ApplyBatch& p, int prec, int* err, cudaStream_t st);
+
 }  // namespace t2s2

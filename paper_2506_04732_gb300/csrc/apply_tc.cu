@@ -1,0 +1,213 @@
+// TT apply of the rank-2 collocation operator on the 5th-generation tensor
+// cores (tcgen05): BF16 or TF32 operands, FP32 accumulation in tensor memory.
+//
+// The mode-k contraction of core k is the GEMM
+//     D[(a,b), ii] = sum_j X_k[a, j, b] * M2[ii, j],   M2 = [S_k ; G_k]  (2m x m),
+// with the (a, b) pairs as the MMA's M dimension (128 per CTA), the 2m
+// stacked operator rows as N (<= 128) and j as K (<= 64).  Both operands are
+// K-major.  Each CTA rounds its slice of X (FP64 in HBM, read coalesced along
+// b) and the two operator matrices to the operand type and stores them in
+// shared memory in the 128-byte-swizzled canonical layout; one thread issues
+// the K/kMmaK MMAs and commits their completion to an mbarrier; each warp then
+// reads its 32 TMEM lanes (tcgen05.ld) and writes the FP32 sums as FP64 into
+// the block pattern of Y (the same pattern as the FP64 kernel in apply.cu).
+// All cores of the train go in one launch.
+//
+// The wait on the mbarrier is bounded: on timeout the CTA sets *err, waits
+// once more (bounded) for its MMAs, frees its TMEM and returns without
+// writing Y.
+#include "apply.h"
+#include "tc_common.cuh"
+#include "trace.h"
+
+namespace t2s2 {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kTileM = 128;    // (a, b) rows per CTA = TMEM lanes
+constexpr int kMaxK = 64;      // contraction length m (zero padded)
+constexpr int kTileN = 128;    // 2m stacked rows (zero padded) = TMEM columns
+constexpr int kThreads = 128;  // 4 warps: one per 32 TMEM lanes
+// Dynamic shared memory per CTA: the two operand tiles plus alignment slack,
+// and never less than 48 KB, so that at most 4 CTAs share an SM and the
+// 4 x 128 TMEM columns they allocate never exceed the SM's 512.
+constexpr int smem_bytes(int elem_bytes) {
+  return 2 * kTileM * kMaxK * elem_bytes + 2048 > 48 * 1024 ? 2 * kTileM * kMaxK * elem_bytes + 2048
+                                                            : 48 * 1024;
+}
+
+struct TileMapTc {
+  int start[T2S2_MAX_D + 1];
+};
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) apply_tc_kernel(ApplyBatch p, TileMapTc tm, int* err) {
+  using O = Op<P>;
+  constexpr int E = O::kBytes;
+  constexpr int kTileBytes = kTileM * kMaxK * E;  // 16 KB (BF16) or 32 KB (TF32)
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment of both tiles (the swizzle pattern repeats every 1024 B)
+  unsigned char* sA = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  unsigned char* sB = sA + kTileBytes;
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sB + kTileBytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  int core = 0;
+  while (core + 1 < p.ncores && (int)blockIdx.x >= tm.start[core + 1]) ++core;
+  const ApplyCore& c = p.c[core];
+  const int m = c.m, ra = c.ra, rb = c.rb;
+  const long nrows = (long)ra * rb;
+  const long row0 = (long)(blockIdx.x - tm.start[core]) * kTileM;
+  // K padded to whole MMAs; N = 2m padded to a multiple of 16 (M = 128 form)
+  const int kpad = ((m + O::kMmaK - 1) / O::kMmaK) * O::kMmaK;
+  const int npad = ((2 * m + 15) / 16) * 16;
+
+  if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kTileN);
+  if (tid == 0) mbar_init(smem_u32(mbar), 1);
+  // A tile: row t <-> pair g = row0 + t = (a, b); zero rows past the core
+  {
+    const long g = row0 + tid;
+    const bool valid = g < nrows;
+    const long a = valid ? g / rb : 0, b = valid ? g % rb : 0;
+    const double* xr = c.X + a * (long)m * rb + b;
+    for (int j = 0; j < kpad; ++j) {
+      const double v = (valid && j < m) ? xr[(long)j * rb] : 0.0;
+      O::store(sA + sw128_off<E>(tid, j, kTileM), v);
+    }
+  }
+  // B tile: row ii < m: S row ii; m <= ii < 2m: G row ii - m; zero padded
+  for (int e = tid; e < npad * kpad; e += kThreads) {
+    const int ii = e / kpad, j = e % kpad;
+    double v = 0.0;
+    if (ii < 2 * m && j < m) {
+      if (ii < m) {
+        v = c.S[(long)ii * m + j];
+      } else {
+        const long o = (long)(ii - m) * m + j;
+        v = c.g_op * c.L[o];
+        if (c.g_mass != 0.0) v += c.g_mass * c.S[o];
+      }
+    }
+    O::store(sB + sw128_off<E>(ii, j, kTileM), v);
+  }
+  // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
+  fence_smem_to_async();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t bar = smem_u32(mbar);
+  if (tid == 0) {
+    const uint32_t idesc = make_idesc(O::kFmt, kTileM, npad);
+    constexpr int W = 128 / E;  // elements per swizzle row
+    for (int k0 = 0; k0 < kpad; k0 += O::kMmaK) {
+      // K-block base, then 32 bytes per MMA step inside the 128-byte row
+      const uint32_t off = (uint32_t)((k0 / W) * (kTileM * 128) + (k0 % W) * E);
+      const uint64_t da = sdesc_sw128(smem_u32(sA) + off);
+      const uint64_t db = sdesc_sw128(smem_u32(sB) + off);
+      issue_mma<P>(tmem, da, db, idesc, k0 > 0 ? 1u : 0u);
+    }
+    mma_commit(bar);
+  }
+  // every thread waits (bounded); the block-wide vote keeps the warp-collective
+  // TMEM loads below uniform even if one thread's wait ran out
+  const bool ok = __syncthreads_and(mbar_wait(bar, 0)) != 0;
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    mbar_wait(bar, 0);  // bounded second wait for MMAs still in flight
+  }
+  fence_after_sync();
+  if (ok) {
+    // epilogue: warp w owns TMEM lanes 32w .. 32w+31 = tile rows
+    const int t = warp * 32 + lane;
+    const long g = row0 + t;
+    const bool valid = g < nrows;
+    const long a = valid ? g / rb : 0, b = valid ? g % rb : 0;
+    double* Y = c.Y;
+    for (int c0 = 0; c0 < 2 * m; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (!valid) continue;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int row = c0 + q;
+        if (row >= 2 * m) break;
+        const double val = (double)__uint_as_float(v[q]);
+        const bool gpart = row >= m;
+        const int ii = gpart ? row - m : row;
+        switch (c.kind) {
+          case kApplySingle:  // 1 x m x 1: G X
+            if (gpart) Y[ii] = val;
+            break;
+          case kApplyFirst: {  // 1 x m x 2rb: [G X, S X]
+            const long base = (long)ii * 2 * rb;
+            if (gpart) Y[base + b] = val; else Y[base + rb + b] = val;
+            break;
+          }
+          case kApplyLast: {  // 2ra x m x 1: [S X; G X]
+            const long r = gpart ? (ra + a) : a;
+            Y[r * m + ii] = val;
+            break;
+          }
+          default: {  // middle: 2ra x m x 2rb
+            const long w = 2L * rb;
+            if (gpart) {
+              Y[((long)(ra + a) * m + ii) * w + b] = val;
+            } else {
+              Y[((long)a * m + ii) * w + b] = val;
+              Y[((long)(ra + a) * m + ii) * w + rb + b] = val;
+              Y[((long)a * m + ii) * w + rb + b] = 0.0;
+            }
+          }
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTileN);
+}
+
+template <int P>
+t2s2_status launch_tc(const ApplyBatch& p, const TileMapTc& tm, int total, int* err, cudaStream_t st) {
+  constexpr int kSmem = smem_bytes(Op<P>::kBytes);
+  // the attribute is per function and device; setting it each call is cheap
+  T2S2_CUDA_TRY(cudaFuncSetAttribute(apply_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  apply_tc_kernel<P><<<total, kThreads, kSmem, st>>>(p, tm, err);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+
+}  // namespace
+
+bool apply_tc_supported(const ApplyBatch& p) {
+  for (int k = 0; k < p.ncores; ++k)
+    if (p.c[k].m > kMaxK || p.c[k].m < 1) return false;
+  return true;
+}
+
+t2s2_status apply_tc(const ApplyBatch& p, int prec, int* err, cudaStream_t st) {
+  if (prec != T2S2_BF16_REFINE && prec != T2S2_TF32_REFINE) return T2S2_EINVAL;
+  if (!apply_tc_supported(p) || !err) return T2S2_EINVAL;
+  TileMapTc tm;
+  int total = 0;
+  double fl = 0.0, by = 0.0;
+  for (int k = 0; k < p.ncores; ++k) {
+    tm.start[k] = total;
+    const ApplyCore& c = p.c[k];
+    total += (int)((((long)c.ra * c.rb) + kTileM - 1) / kTileM);
+    fl += 2.0 * (2.0 * c.m) * c.m * (double)c.ra * c.rb;
+    const int ny = (c.kind == kApplyMiddle) ? 4 : ((c.kind == kApplySingle) ? 1 : 2);
+    by += 8.0 * ((double)c.ra * c.m * c.rb * (1 + ny) + 2.0 * c.m * c.m);
+  }
+  tm.start[p.ncores] = total;
+  if (total == 0) return T2S2_OK;
+  TraceScope ts(kTrApplyTc, st, fl, by);
+  if (prec == T2S2_BF16_REFINE) return launch_tc<T2S2_BF16_REFINE>(p, tm, total, err, st);
+  return launch_tc<T2S2_TF32_REFINE>(p, tm, total, err, st);
+}
+
+}  // namespace t2s2

@@ -34,31 +34,44 @@ namespace t2s2 {
 
 namespace {
 
+Gemm<double> gdesc(int M, int N, int K, bool tA, bool tB, double alpha, const double* A, long lda,
+                   const double* B, long ldb, double beta, double* C, long ldc, int batch = 1, long sA = 0,
+                   long sB = 0, long sC = 0) {
+  Gemm<double> g;
+  g.M = M; g.N = N; g.K = K; g.tA = tA; g.tB = tB; g.alpha = alpha; g.beta = beta;
+  g.A = A; g.lda = lda; g.sA = sA; g.B = B; g.ldb = ldb; g.sB = sB;
+  g.C = C; g.ldc = ldc; g.sC = sC; g.batch = batch;
+  return g;
+}
+// Mode products of a core X (ra x m x rb) and the interface contractions, in
+// the context's contraction arithmetic.
+// Y[c,i,b] = sum_a P[c,a] X[a,i,b]
 t2s2_status mode1(Ctx& cx, const double* P, int rn, int ro, const double* X, int m, int rb, double* Y,
                   double alpha = 1.0, double beta = 0.0) {
-  return gemm_ex<double>(cx, rn, m * rb, ro, false, false, alpha, P, ro, X, (long)m * rb, beta, Y,
-                         (long)m * rb);
+  return contract_gemm(cx, gdesc(rn, m * rb, ro, false, false, alpha, P, ro, X, (long)m * rb, beta, Y,
+                                 (long)m * rb));
 }
+// Y[a,i,b] = sum_j B[i,j] X[a,j,b]
 t2s2_status mode2(Ctx& cx, const double* B, int m, const double* X, int ra, int rb, double* Y,
                   double alpha = 1.0, double beta = 0.0) {
-  return gemm_ex<double>(cx, m, rb, m, false, false, alpha, B, m, X, rb, beta, Y, rb, ra, 0,
-                         (long)m * rb, (long)m * rb);
+  return contract_gemm(cx, gdesc(m, rb, m, false, false, alpha, B, m, X, rb, beta, Y, rb, ra, 0,
+                                 (long)m * rb, (long)m * rb));
 }
 // Y[a,i,c] = sum_b X[a,i,b] Q[c,b]
 t2s2_status mode3(Ctx& cx, const double* X, int ra, int m, int ro, const double* Q, int rn, double* Y,
                   double alpha = 1.0, double beta = 0.0) {
-  return gemm_ex<double>(cx, ra * m, rn, ro, false, true, alpha, X, ro, Q, ro, beta, Y, rn);
+  return contract_gemm(cx, gdesc(ra * m, rn, ro, false, true, alpha, X, ro, Q, ro, beta, Y, rn));
 }
 // out[b][c] = sum_{a,i} U[a,i,b] T[a,i,c]
 t2s2_status contract_left(Ctx& cx, const double* U, int ra, int m, int rb, const double* T, int rc,
                           double* out) {
-  return gemm_ex<double>(cx, rb, rc, ra * m, true, false, 1.0, U, rb, T, rc, 0.0, out, rc);
+  return contract_gemm(cx, gdesc(rb, rc, ra * m, true, false, 1.0, U, rb, T, rc, 0.0, out, rc));
 }
 // out[a][c] = sum_{i,b} U[a,i,b] T[c,i,b]
 t2s2_status contract_right(Ctx& cx, const double* U, int ra, int m, int rb, const double* T, int rc,
                            double* out) {
-  return gemm_ex<double>(cx, ra, rc, m * rb, false, true, 1.0, U, (long)m * rb, T, (long)m * rb, 0.0,
-                         out, rc);
+  return contract_gemm(cx, gdesc(ra, rc, m * rb, false, true, 1.0, U, (long)m * rb, T, (long)m * rb, 0.0,
+                                 out, rc));
 }
 t2s2_status d2d(Ctx& cx, double* dst, const double* src, size_t n) {
   if (n == 0) return T2S2_OK;
@@ -601,10 +614,19 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
 
 }  // namespace
 
+// The public apply: FP64 and FP32_REFINE take the FP64 kernel; BF16 / TF32
+// take the tcgen05 kernel when every core has m <= 64 (else the FP64 one).
 t2s2_status apply_dispatch(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass,
                            double c_op, t2s2_precision prec) {
-  (void)prec;
-  return apply_op(op, cx, x, y, c_mass, c_op, false);
+  ApplyBatch b;
+  T2S2_TRY(apply_batch(op, x, y, c_mass, c_op, false, b));
+  if ((prec == T2S2_BF16_REFINE || prec == T2S2_TF32_REFINE) && apply_tc_supported(b)) {
+    int* err = cx.dstat + kStatTensorCore;
+    T2S2_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), cx.st));
+    T2S2_TRY(apply_tc(b, prec, err, cx.st));
+    return tensor_core_status(cx);
+  }
+  return apply_fp64(b, cx.st);
 }
 
 static t2s2_status solve_entry(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double c_mass, double c_op,

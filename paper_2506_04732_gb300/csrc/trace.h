@@ -4,7 +4,17 @@
 
 namespace t2s2 {
 
-enum TraceFamily { kTrGemm = 0, kTrApply = 1, kTrLocal = 2, kTrSmall = 3, kTrElem = 4, kTrFamilies = 5 };
+enum TraceFamily {
+  kTrGemm = 0,
+  kTrApply = 1,
+  kTrLocal = 2,
+  kTrSmall = 3,
+  kTrElem = 4,
+  kTrApplyTc = 5,
+  kTrGemmTc = 6,
+  kTrMlp = 7,
+  kTrFamilies = 8
+};
 
 // Count one launch of `fam` with its algorithmic FLOPs and DRAM-level bytes;
 // when tracing is on, `begin` must have been called on the same stream first.

@@ -38,6 +38,10 @@ struct Ctx {
   Arena* ar = nullptr;
   double* hbuf = nullptr;   // pinned host scratch (>= 4 * kSmallMax doubles)
   int* dstat = nullptr;     // device status word
+  // Arithmetic of the sweep's contractions (mode products, interfaces):
+  // T2S2_FP64 (SIMT FP64 GEMM) or T2S2_TF32_REFINE / T2S2_BF16_REFINE
+  // (tcgen05 GEMM).  QR, SVD and norms always run in FP64.
+  int contract_prec = T2S2_FP64;
 };
 
 template <typename T>
