@@ -42,9 +42,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle CPU work for the cpu_baseline sample")
-    ap.add_argument("--workload", default="steady", choices=["steady", "batched", "cn"],
+    ap.add_argument("--workload", default="steady", choices=["steady", "batched", "cn", "warm"],
                     help="steady: d=6 n=32 solve (headline); batched: 256 d=5 instances; "
-                         "cn: Crank-Nicolson steps at d=7 n=64")
+                         "cn: Crank-Nicolson steps at d=7 n=64; warm: learned warm start "
+                         "(--instances training solves)")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--workers", type=int, default=8)
     return ap.parse_args()
@@ -299,6 +300,155 @@ def run_cn(args, T, P, W, torch):
     return 0
 
 
+def run_warm(args, T, P, W, torch):
+    """Learned warm start on the d=6, n=32 parameter family: generate solutions
+    with the solver itself, train the network on the GPU (forward, backward and
+    Adam kernels of the library), then solve held-out problems cold and warm
+    to the same tolerance."""
+    import numpy as np
+    ntrain, nhold = args.instances, 16
+    d, n, rmax, tol = 6, 32, 20, 1e-8
+    m = n - 2
+
+    def solve(p, net=None):
+        op = P.build_operator(p)
+        b = T.TT.from_cores(P.source_cores(p, op))
+        x = T.TT.from_cores([np.ones((1, m, 1))] * d, rcap=rmax + 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if net is not None:
+            net.predict(W.warm_features(p), x)
+        info = T.t2s2_solve(op, b, x, tol, rmax, 50, allow_noconv=True)
+        torch.cuda.synchronize()
+        return op, x, info, time.perf_counter() - t0
+
+    t0 = time.perf_counter()
+    train = [W.config4(10000 + i, d=d, n=n) for i in range(ntrain)]
+    sols = [solve(p) for p in train]
+    t_data = time.perf_counter() - t0
+    net = T.WarmStartNet(W.WARM_IN_DIM, 256, [m] * d, 8, rmax + 4, seed=1)
+    tg, uu = net.pack_targets(sols[0][0], [s[1] for s in sols])
+    Pf = torch.tensor(np.stack([W.warm_features(p) for p in train]), device="cuda")
+    steps, batch = 1500, min(64, ntrain)
+    T.t2s2_trace(True)
+    t0 = time.perf_counter()
+    losses = []
+    for it in range(steps):
+        lo = (it * batch) % max(1, ntrain - batch + 1)
+        lr = 2e-3 if it < int(0.7 * steps) else 4e-4
+        losses.append(net.train_step(Pf, tg, uu, lr, lo=lo, hi=lo + batch))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    mlp = T.t2s2_trace_read("mlp")
+    gemm = T.t2s2_trace_read("gemm_tc")
+    T.t2s2_trace(False)
+    hold = [W.config4(90000 + i, d=d, n=n) for i in range(nhold)]
+    for p in hold[:2]:  # warm-up
+        solve(p)
+        solve(p, net)
+    cold_t = warm_t = 0.0
+    cold_sw = warm_sw = 0
+    conv_c = conv_w = 0
+    diffs = []
+    for p in hold:
+        op, xc, ic, tc = solve(p)
+        _, xw, iw, tw = solve(p, net)
+        cold_t += tc
+        warm_t += tw
+        cold_sw += ic.sweeps
+        warm_sw += iw.sweeps
+        conv_c += ic.residual <= tol
+        conv_w += iw.residual <= tol
+        diffs.append(T.t2s2_diff_norm(op, xc, xw) / T.t2s2_norm(op, xc))
+    line = {"metric": "solves/sec to rel. residual 1e-8 with the learned warm start (d=6,n=32 family)",
+            "value": nhold / warm_t, "unit": "solves/s", "n_gpus": 1, "steps": nhold, "warmup": 2,
+            "ms_per_step": 1e3 * warm_t / nhold, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 solve, bf16/fp32 network", "data": "synthetic",
+            "config": {"workload": f"config-4 family d={d} n={n}: {ntrain} training solves, {nhold} held-out",
+                       "cold_solves_per_s": nhold / cold_t, "cold_sweeps": cold_sw, "warm_sweeps": warm_sw,
+                       "cold_converged": conv_c, "warm_converged": conv_w,
+                       "max_rel_diff_cold_vs_warm": max(diffs), "train_steps": steps, "batch": batch,
+                       "loss_first": losses[0], "loss_last": float(np.mean(losses[-20:])),
+                       "data_generation_s": t_data, "training_s": t_train,
+                       "mlp_kernels": mlp, "mlp_gemm_tc": gemm,
+                       "network": "15 -> 256 -> 256 -> TT cores rank 8 (8160 outputs), ReLU, Adam"}}
+    print(json.dumps(line))
+    return 0
+
+
+def measure_contraction(T, P, W, torch, instances=256, reps=10):
+    """Grouped core contractions (t2s2_apply_batched): every core of `instances`
+    d=5 problems (n in {16,24,32,48}, TT ranks 16) in one persistent launch.
+    Kernel time from the library's per-launch CUDA events; algorithmic FLOPs
+    4 m^2 r_a r_b and bytes 8 (r_a m r_b (1 + blocks written) + 2 m^2) per core."""
+    import numpy as np
+    probs = [W.config3(i) for i in range(instances)]
+    ops, xs, ys = [], [], []
+    for i, p in enumerate(probs):
+        m = p.n[0] - 2
+        r = [1] + [16] * (p.d - 1) + [1]
+        ops.append(P.build_operator(p))
+        xs.append(T.TT.from_cores(W.random_tt(p.d, m, r, seed=700 + i)))
+        ys.append(T.TT.empty([m] * p.d, 32))
+    pk, src = peaks()
+    out = {"workload": f"{instances} instances d=5 n in {{16,24,32,48}}, ranks 16, one launch per apply",
+           "data_bytes": int(sum(8 * sum(c.numel() for c in x.buffers) for x in xs)
+                             + sum(8 * sum(c.numel() for c in y.buffers) for y in ys))}
+    for name, prec in (("bf16", T.BF16_REFINE), ("tf32", T.TF32_REFINE), ("fp64", T.FP64)):
+        T.t2s2_apply_batched(ops, xs, ys, 0.0, 1.0, prec)  # tunes the launch shape
+        T.t2s2_apply_batched(ops, xs, ys, 0.0, 1.0, prec)
+        torch.cuda.synchronize()
+        T.t2s2_trace(True)
+        for _ in range(reps):
+            T.t2s2_apply_batched(ops, xs, ys, 0.0, 1.0, prec)
+        fam = T.t2s2_trace_read("apply" if name == "fp64" else "apply_tc")
+        T.t2s2_trace(False)
+        ms = fam["ms"] / max(1, fam["launches"])
+        tf = fam["flops"] / max(1, fam["launches"]) / (ms * 1e-3) / 1e12
+        gbs = fam["bytes"] / max(1, fam["launches"]) / (ms * 1e-3) / 1e9
+        e = {"ms_per_launch": ms, "tflops": tf, "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"],
+             "flops_per_launch": fam["flops"] / max(1, fam["launches"]),
+             "bytes_per_launch": fam["bytes"] / max(1, fam["launches"])}
+        if name == "bf16":
+            e["tensor_peak_tflops"] = pk["bf16_tflops"]
+            e["tensor_frac"] = tf / pk["bf16_tflops"]
+        elif name == "tf32":
+            e["tensor_peak_tflops"] = pk["bf16_tflops"] / 2  # dense TF32 is half the BF16 rate
+            e["tensor_frac"] = tf / e["tensor_peak_tflops"]
+        out[name] = e
+    out["autotune"] = T.t2s2_autotune_report().strip().splitlines()
+    out["bound"] = "hbm: arithmetic intensity m/10 flop/byte (<= 4.6 at m = 46) is far below the tensor ridge"
+    out["peak_source"] = src
+    return out
+
+
+def measure_precisions(T, P, W, torch, op, b, x_ref, steps=3):
+    """Mixed-precision solves (FP64 iterative refinement) of the same problem:
+    solves/s, FP64 residual, sweeps, refinements and distance to the FP64
+    solution ||x - x_fp64|| / ||x_fp64|| (t2s2_diff_norm)."""
+    import numpy as np
+    p = W.config1()
+    m = [n - 2 for n in p.n]
+    ref_norm = T.t2s2_norm(op, x_ref)
+    out = {}
+    for name, prec in (("fp32_refine", T.FP32_REFINE), ("tf32_refine", T.TF32_REFINE),
+                       ("bf16_refine", T.BF16_REFINE)):
+        times, info, x = [], None, None
+        for i in range(steps + 1):
+            x = T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + 4)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = T.t2s2_solve(op, b, x, p.tol, p.rmax, p.max_sweeps, prec=prec, allow_noconv=True)
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+        out[name] = {"solves_per_s": len(times) / sum(times), "residual": info.residual,
+                     "converged": info.residual <= p.tol, "sweeps": info.sweeps,
+                     "refinements": info.refinements, "max_rank": info.max_rank,
+                     "rel_diff_vs_fp64_solution": T.t2s2_diff_norm(op, x, x_ref) / ref_norm}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -311,7 +461,8 @@ def main():
         import paper_2506_04732_gb300 as T
         from paper_2506_04732_gb300 import problem as P
         import workloads as W
-        return (run_batched if args.workload == "batched" else run_cn)(args, T, P, W, torch)
+        fn = {"batched": run_batched, "cn": run_cn, "warm": run_warm}[args.workload]
+        return fn(args, T, P, W, torch)
     ws, rank, local = dist_env()
     import torch
     if ws > 1:
@@ -423,6 +574,15 @@ def main():
         e2e = {"value": ws * args.steps / tt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    extras = {}
+    if rank == 0 and ws == 1 and args.prec == "fp64":
+        for key, fn in (("precision_variants", lambda: measure_precisions(T, P, W, torch, op, b, x)),
+                        ("contraction", lambda: measure_contraction(T, P, W, torch))):
+            try:
+                extras[key] = fn()
+            except Exception as exc:  # recorded, never hides the headline number
+                extras[key] = {"error": repr(exc)}
+
     # roofline of the dominant kernel family (largest share of traced time)
     pk, src = peaks()
     dom = max(fam, key=lambda k: fam[k]["ms"])
@@ -461,6 +621,7 @@ def main():
                            "local_iters": last.local_iters},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "kernel_families": fam}
+        line.update(extras)
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -147,6 +147,26 @@ t2s2_status t2s2_apply(t2s2_op op, const t2s2_tt* x, t2s2_tt* y, double c_mass,
                        double c_op, t2s2_precision prec, void* stream);
 
 /*
+ * Grouped apply: y_i = (c_mass M_i + c_op A_i) x_i for `count` independent
+ * instances (each its own operator; uneven n and ranks allowed), every core
+ * of every instance in ONE persistent launch (tensor cores for TF32 / BF16
+ * when every m <= 64, else the FP64 kernel).  x and y must be device TTs;
+ * y ranks are written as in t2s2_apply.  The launch shape (CTAs per SM) is
+ * picked by timing the candidates on the first call for each shape class
+ * (see t2s2_autotune_report).  Returns after the work is done.
+ * Errors: as t2s2_apply for any instance; T2S2_ETIMEOUT if a tensor-core
+ * wait gave up.  The paper applies one operator at a time.
+ */
+t2s2_status t2s2_apply_batched(const t2s2_op* ops, const t2s2_tt* x, t2s2_tt* y, int count,
+                               double c_mass, double c_op, t2s2_precision prec, void* stream);
+
+/* Text table of the launch shapes the grouped apply has tuned so far (one
+ * line per shape class with each candidate's time); copies at most len-1
+ * characters into buf (NUL-terminated, buf may be NULL) and returns the full
+ * length. */
+int t2s2_autotune_report(char* buf, int len);
+
+/*
  * TT rounding rndg (Methods, "Tensor-train (TT) decomposition"): in place,
  * right-to-left orthogonalisation, then left-to-right truncated SVDs with
  * per-unfolding threshold tol ||x||_F / sqrt(d-1), then the cap rmax
@@ -175,6 +195,13 @@ t2s2_status t2s2_norm(t2s2_op op, const t2s2_tt* x, double* out, void* stream);
  * GPU work overlaps race on it: serialise them.  Synchronises with `stream`.
  */
 t2s2_status t2s2_norm_noalloc(const t2s2_tt* x, double* out, void* stream);
+
+/* ||x - y||_F for two TTs on the same grid, accurate to rounding level even
+ * when x and y agree to many digits: the difference is formed as a TT
+ * (ranks r_x + r_y), right-orthogonalised, and the norm of its first core
+ * taken -- never sqrt(<x,x> - 2<x,y> + <y,y>), which cancels.  FP64.
+ * Errors: T2S2_EINVAL for mismatched shapes. */
+t2s2_status t2s2_diff_norm(t2s2_op op, const t2s2_tt* x, const t2s2_tt* y, double* out, void* stream);
 
 /* ||b - (c_mass M + c_op A) x||_F / ||b||_F, accurate difference norm, FP64. */
 t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double c_mass,
@@ -240,6 +267,53 @@ t2s2_status t2s2_be_step(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax
 t2s2_status t2s2_gemm(t2s2_op op, int M, int N, int K, int tA, int tB, double alpha, const double* A,
                       long lda, long sA, const double* B, long ldb, long sB, double beta, double* C,
                       long ldc, long sC, int batch, t2s2_precision prec, void* stream);
+
+/* ---- learned warm start -------------------------------------------------
+ * A small network maps a problem's parameters p to the TT cores of an
+ * initial guess X(p) for t2s2_solve (the paper's solver takes any initial
+ * guess; the tolerance, and so the answer, does not depend on it).
+ *     h1 = relu(W1 p + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3,
+ * y = the cores of X(p): (1 x m_1 x r), (r x m_k x r) ..., (r x m_d x 1),
+ * row-major, concatenated.  Training minimises the mean over a batch of
+ * ||X(p) - U||^2 / ||U||^2 (U: a solution the solver produced), a loss that
+ * does not depend on the TT gauge, with Adam (beta1 0.9, beta2 0.999, 1e-8).
+ * The layer products run on tcgen05 tensor cores with BF16 operands and FP32
+ * accumulation; parameters, gradients and Adam moments are FP32.  Parameter
+ * order everywhere: W1 (hidden x in), b1, W2 (hidden x hidden), b2,
+ * W3 (out x hidden), b3, each row-major.  The paper has no such network.
+ */
+typedef struct t2s2_mlp_s* t2s2_mlp;
+
+/* Create a network for d >= 2 modes of sizes m[0..d-1] (<= 64), output rank
+ * r (<= 16) and targets of rank <= ru (<= 32); He-normal weights from `seed`,
+ * zero biases.  Errors: T2S2_EINVAL for sizes out of range, T2S2_ENOMEM. */
+t2s2_status t2s2_mlp_create(int in_dim, int hidden, int d, const int* m, int r, int ru,
+                            unsigned long long seed, t2s2_mlp* out);
+t2s2_status t2s2_mlp_destroy(t2s2_mlp net);
+/* Number of parameters and the length of y. */
+t2s2_status t2s2_mlp_info(t2s2_mlp net, long long* nparams, int* out_dim);
+/* Copy parameters and/or the last gradient (nparams floats each; host or
+ * device pointers, either may be NULL) out of / into the network. */
+t2s2_status t2s2_mlp_get_params(t2s2_mlp net, float* params, float* grads, void* stream);
+t2s2_status t2s2_mlp_set_params(t2s2_mlp net, const float* params, void* stream);
+/* Store the device TT u (ranks <= ru, mode sizes m) as a training target:
+ * slot (device, d * ru * mmax * ru floats) receives its cores zero-padded to
+ * ru x mmax x ru, uu (device, 1 float) its squared norm (FP64 TT norm). */
+t2s2_status t2s2_mlp_pack_target(t2s2_mlp net, t2s2_op op, const t2s2_tt* u, float* slot, float* uu,
+                                 void* stream);
+/* Loss and gradient of a batch: P (device, batch x in_dim), targets and uu
+ * (device, as packed above).  The gradient stays in the network (see
+ * t2s2_mlp_get_params); *loss (may be NULL) receives the mean loss.
+ * Synchronises the stream.  T2S2_ETIMEOUT if a tensor-core wait gave up. */
+t2s2_status t2s2_mlp_loss_grad(t2s2_mlp net, const float* P, int batch, const float* targets,
+                               const float* uu, float* loss, void* stream);
+/* As t2s2_mlp_loss_grad followed by one Adam update with learning rate lr. */
+t2s2_status t2s2_mlp_train_step(t2s2_mlp net, const float* P, int batch, const float* targets,
+                                const float* uu, float lr, float* loss, void* stream);
+/* Warm start: the cores of X(p) (p: host or device, in_dim floats) as FP64
+ * into x (device or host cores with room for them); x->r is set to the
+ * network's ranks. */
+t2s2_status t2s2_mlp_predict(t2s2_mlp net, const float* p, t2s2_tt* x, void* stream);
 
 /* ---- diagnostics ---------------------------------------------------------
  * Kernel families for tracing: 0 GEMM (SIMT contractions), 1 TT apply

@@ -19,8 +19,9 @@ import numpy as np
 
 __all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REFINE",
            "TF32_REFINE", "BF16_REFINE", "t2s2_build_operator", "t2s2_apply", "t2s2_round",
-           "t2s2_norm", "t2s2_norm_noalloc", "t2s2_residual", "t2s2_solve", "t2s2_solve_batched", "t2s2_cn_step", "t2s2_be_step",
-           "t2s2_device_count", "t2s2_strerror", "t2s2_gemm", "t2s2_kernel_launches", "t2s2_trace",
+           "t2s2_norm", "t2s2_diff_norm", "t2s2_norm_noalloc", "t2s2_residual", "t2s2_solve", "t2s2_solve_batched", "t2s2_cn_step", "t2s2_be_step",
+           "t2s2_device_count", "t2s2_strerror", "t2s2_gemm", "WarmStartNet", "t2s2_apply_batched",
+           "t2s2_autotune_report", "t2s2_kernel_launches", "t2s2_trace",
            "t2s2_trace_read", "TRACE_FAMILIES", "lib_path"]
 
 FP64, FP32_REFINE, TF32_REFINE, BF16_REFINE = 0, 1, 2, 3
@@ -107,6 +108,28 @@ _SIGS = {
                                  ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_double,
                                  ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_void_p]),
+    "t2s2_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "t2s2_mlp_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "t2s2_mlp_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_int)]),
+    "t2s2_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "t2s2_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "t2s2_mlp_pack_target": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_TT),
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "t2s2_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
+    "t2s2_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                                           ctypes.c_void_p]),
+    "t2s2_mlp_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_void_p]),
+    "t2s2_apply_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_TT), ctypes.POINTER(_TT),
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_void_p]),
+    "t2s2_autotune_report": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
+    "t2s2_diff_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.POINTER(_TT),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "t2s2_kernel_launches": (ctypes.c_longlong, []),
     "t2s2_trace": (ctypes.c_int, [ctypes.c_int]),
     "t2s2_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -153,15 +176,18 @@ def t2s2_gemm(op: Operator, A, B, C, tA=False, tB=False, alpha=1.0, beta=0.0, pr
     of each must be contiguous.  Returns C.
     """
     def lay(t):
+        if t.dtype != torch.float64 or (t.numel() > 0 and t.stride(-1) != 1):
+            raise ValueError("float64 tensors with a contiguous last dimension expected")
+        if t.numel() == 0:  # empty: strides carry no layout
+            rows, cols = t.shape[-2], t.shape[-1]
+            return rows, cols, cols, 0, (t.shape[0] if t.dim() == 3 else 1)
         if t.dim() == 2:
             return t.shape[0], t.shape[1], t.stride(0), 0, 1
         return t.shape[1], t.shape[2], t.stride(1), t.stride(0), t.shape[0]
+    import torch
     ra, ca, lda, sA, ba = lay(A)
     rb, cb, ldb, sB, bb = lay(B)
     rc, cc, ldc, sC, bc = lay(C)
-    for t in (A, B, C):
-        if t.dtype.is_floating_point is False or t.element_size() != 8 or t.stride(-1) != 1:
-            raise ValueError("float64 tensors with a contiguous last dimension expected")
     M, K = (ca, ra) if tA else (ra, ca)
     K2, N = (cb, rb) if tB else (rb, cb)
     if K2 != K or (rc, cc) != (M, N):
@@ -171,6 +197,98 @@ def t2s2_gemm(op: Operator, A, B, C, tA=False, tB=False, alpha=1.0, beta=0.0, pr
                             B.data_ptr(), ldb, sB, float(beta), C.data_ptr(), ldc, sC, batch, int(prec),
                             _stream_handle(stream)), "t2s2_gemm")
     return C
+
+
+class WarmStartNet:
+    """The learned warm start (t2s2_mlp_*): p -> TT cores of an initial guess.
+
+    ``m`` are the interior mode sizes, ``r`` the output rank and ``ru`` the
+    largest target rank.  Training data live on the device: ``P`` a float32
+    (N, in_dim) tensor, targets packed by :meth:`pack_targets`.
+    """
+
+    def __init__(self, in_dim, hidden, m, r, ru, seed=0):
+        import torch
+        h = ctypes.c_void_p()
+        m_arr = (ctypes.c_int * len(m))(*[int(v) for v in m])
+        _check(load().t2s2_mlp_create(int(in_dim), int(hidden), len(m), m_arr, int(r), int(ru),
+                                      int(seed), ctypes.byref(h)), "t2s2_mlp_create")
+        self._h = h
+        self.in_dim, self.hidden, self.m, self.r, self.ru = in_dim, hidden, list(m), r, ru
+        self.d, self.mmax = len(m), max(m)
+        n, od = ctypes.c_longlong(), ctypes.c_int()
+        _check(load().t2s2_mlp_info(h, ctypes.byref(n), ctypes.byref(od)), "t2s2_mlp_info")
+        self.nparams, self.out_dim = n.value, od.value
+        self._torch = torch
+
+    def close(self):
+        if self._h:
+            load().t2s2_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        t = self._torch.empty(self.nparams, dtype=self._torch.float32, device="cuda")
+        _check(load().t2s2_mlp_get_params(self._h, t.data_ptr(), None, _stream_handle(None)),
+               "t2s2_mlp_get_params")
+        return t
+
+    def grads(self):
+        t = self._torch.empty(self.nparams, dtype=self._torch.float32, device="cuda")
+        _check(load().t2s2_mlp_get_params(self._h, None, t.data_ptr(), _stream_handle(None)),
+               "t2s2_mlp_get_params")
+        return t
+
+    def set_params(self, flat):
+        t = flat.to(device="cuda", dtype=self._torch.float32).contiguous()
+        _check(load().t2s2_mlp_set_params(self._h, t.data_ptr(), _stream_handle(None)), "t2s2_mlp_set_params")
+
+    def pack_targets(self, op: "Operator", tts):
+        """Device arrays (targets, uu) for a list of device TTs."""
+        n = len(tts)
+        per = self.d * self.ru * self.mmax * self.ru
+        targets = self._torch.zeros(n * per, dtype=self._torch.float32, device="cuda")
+        uu = self._torch.zeros(n, dtype=self._torch.float32, device="cuda")
+        for i, u in enumerate(tts):
+            s = u._struct()
+            _check(load().t2s2_mlp_pack_target(self._h, op.handle, ctypes.byref(s),
+                                               targets.data_ptr() + 4 * i * per, uu.data_ptr() + 4 * i,
+                                               _stream_handle(None)), "t2s2_mlp_pack_target")
+        return targets, uu
+
+    def _batch_ptrs(self, P, targets, uu, lo, hi):
+        per = self.d * self.ru * self.mmax * self.ru
+        return (P.data_ptr() + 4 * lo * self.in_dim, targets.data_ptr() + 4 * lo * per, uu.data_ptr() + 4 * lo)
+
+    def loss_grad(self, P, targets, uu, lo=0, hi=None):
+        hi = P.shape[0] if hi is None else hi
+        pp, tp, up = self._batch_ptrs(P, targets, uu, lo, hi)
+        loss = ctypes.c_float()
+        _check(load().t2s2_mlp_loss_grad(self._h, pp, hi - lo, tp, up, ctypes.byref(loss), _stream_handle(None)),
+               "t2s2_mlp_loss_grad")
+        return loss.value
+
+    def train_step(self, P, targets, uu, lr, lo=0, hi=None):
+        hi = P.shape[0] if hi is None else hi
+        pp, tp, up = self._batch_ptrs(P, targets, uu, lo, hi)
+        loss = ctypes.c_float()
+        _check(load().t2s2_mlp_train_step(self._h, pp, hi - lo, tp, up, float(lr), ctypes.byref(loss),
+                                          _stream_handle(None)), "t2s2_mlp_train_step")
+        return loss.value
+
+    def predict(self, p, x: "TT"):
+        """Write the network's guess for parameter vector p (in_dim floats) into x."""
+        v = self._torch.as_tensor(np.asarray(p, dtype=np.float32)).contiguous()
+        s = x._struct()
+        _check(load().t2s2_mlp_predict(self._h, v.data_ptr(), ctypes.byref(s), _stream_handle(None)),
+               "t2s2_mlp_predict")
+        x._sync_ranks()
+        return x
 
 
 def t2s2_kernel_launches() -> int:
@@ -329,6 +447,29 @@ def t2s2_apply(op: Operator, x: TT, y: TT, c_mass=0.0, c_op=1.0, prec=FP64, stre
     return y
 
 
+def t2s2_apply_batched(ops, xs, ys, c_mass=0.0, c_op=1.0, prec=FP64, stream=None):
+    """Grouped apply over many instances in one persistent launch."""
+    n = len(ops)
+    if not (len(xs) == len(ys) == n):
+        raise ValueError("ops, xs and ys must have the same length")
+    h = (ctypes.c_void_p * n)(*[o.handle for o in ops])
+    sx = (_TT * n)(*[x._struct() for x in xs])
+    sy = (_TT * n)(*[y._struct() for y in ys])
+    _check(load().t2s2_apply_batched(h, sx, sy, n, float(c_mass), float(c_op), int(prec),
+                                     _stream_handle(stream)), "t2s2_apply_batched")
+    for y, s in zip(ys, sy):
+        y.r = [int(s.r[k]) for k in range(y.d + 1)]
+    return ys
+
+
+def t2s2_autotune_report() -> str:
+    """The grouped apply's tuned launch shapes, one line per shape class."""
+    n = load().t2s2_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    load().t2s2_autotune_report(buf, n + 1)
+    return buf.value.decode()
+
+
 def t2s2_round(op: Operator, x: TT, tol, rmax=0, stream=None):
     sx = x._struct()
     _check(load().t2s2_round(op.handle, ctypes.byref(sx), float(tol), int(rmax),
@@ -341,6 +482,14 @@ def t2s2_norm(op: Operator, x: TT, stream=None) -> float:
     out = ctypes.c_double()
     _check(load().t2s2_norm(op.handle, ctypes.byref(x._struct()), ctypes.byref(out),
                             _stream_handle(stream)), "t2s2_norm")
+    return out.value
+
+
+def t2s2_diff_norm(op: Operator, x: TT, y: TT, stream=None) -> float:
+    """||x - y||_F through the TT difference (accurate for nearly equal x, y)."""
+    out = ctypes.c_double()
+    _check(load().t2s2_diff_norm(op.handle, ctypes.byref(x._struct()), ctypes.byref(y._struct()),
+                                 ctypes.byref(out), _stream_handle(stream)), "t2s2_diff_norm")
     return out.value
 
 

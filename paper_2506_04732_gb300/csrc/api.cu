@@ -143,9 +143,9 @@ t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mas
 
 t2s2_status contract_gemm(Ctx& cx, const Gemm<double>& g) {
   if (cx.contract_prec == T2S2_BF16_REFINE || cx.contract_prec == T2S2_TF32_REFINE) {
-    const size_t need = gemm_tc_workspace(g, cx.contract_prec);
+    const size_t need = gemm_tc_workspace_bytes(g, cx.contract_prec);
     const size_t mk = cx.ar->mark();
-    double* ws = need ? aget<double>(cx, need) : nullptr;
+    void* ws = need ? cx.ar->get(need) : nullptr;
     if (need && !ws) return T2S2_ENOMEM;
     const t2s2_status s = gemm_tc(g, cx.contract_prec, ws, need, cx.dstat + kStatTensorCore, cx.st);
     cx.ar->release(mk);
@@ -421,8 +421,8 @@ t2s2_status t2s2_gemm(t2s2_op op, int M, int N, int K, int tA, int tB, double al
   g.A = A; g.lda = lda; g.sA = sA; g.B = B; g.ldb = ldb; g.sB = sB;
   g.C = C; g.ldc = ldc; g.sC = sC; g.batch = batch;
   const bool tc = prec == T2S2_BF16_REFINE || prec == T2S2_TF32_REFINE;
-  const size_t ws = tc ? gemm_tc_workspace(g, prec) : gemm_workspace(g);
-  T2S2_TRY(ensure_arena(op, ws * sizeof(double) + ((size_t)1 << 20)));
+  const size_t ws = tc ? gemm_tc_workspace_bytes(g, prec) : gemm_workspace(g) * sizeof(double);
+  T2S2_TRY(ensure_arena(op, ws + ((size_t)1 << 20)));
   Ctx cx = make_ctx(op, stream);
   cx.contract_prec = tc ? prec : T2S2_FP64;
   if (tc) T2S2_CUDA_TRY(cudaMemsetAsync(cx.dstat + kStatTensorCore, 0, sizeof(int), cx.st));
@@ -451,6 +451,21 @@ t2s2_status t2s2_norm(t2s2_op op, const t2s2_tt* x, double* out, void* stream) {
   DevTT dx;
   T2S2_TRY(bind_tt(cx, x, dx, true));
   return tt_norm(cx, dx, out);
+}
+
+t2s2_status t2s2_diff_norm(t2s2_op op, const t2s2_tt* x, const t2s2_tt* y, double* out, void* stream) {
+  if (!op || !x || !y || !out) return T2S2_EINVAL;
+  T2S2_TRY(check_tt(op, x));
+  T2S2_TRY(check_tt(op, y));
+  size_t mc = max_core(x) + max_core(y);
+  T2S2_TRY(ensure_arena(op, (tt_bytes(x) + tt_bytes(y)) * 6 + 10 * mc * sizeof(double) + ((size_t)8 << 20)));
+  Ctx cx = make_ctx(op, stream);
+  DevTT dx, dy, z;
+  T2S2_TRY(bind_tt(cx, x, dx, true));
+  T2S2_TRY(bind_tt(cx, y, dy, true));
+  T2S2_TRY(tt_axpby(cx, 1.0, dx, -1.0, dy, z));
+  T2S2_TRY(tt_orth_right(cx, z));
+  return core_norm(cx, z.c[0], z.core_elems(0), out);
 }
 
 t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double c_mass, double c_op,

@@ -12,6 +12,8 @@
 //     d = 1  G X                   (1      x m x 1)
 // All d cores go in one launch; the zero block of middle cores is written by
 // the S-row tiles.
+#include <algorithm>
+
 #include "apply.h"
 #include "trace.h"
 
@@ -20,100 +22,125 @@ namespace t2s2 {
 namespace {
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
-struct TileMap {
-  int start[T2S2_MAX_D + 1];  // prefix sum of CTA counts per core
+struct ParamWork {
+  ApplyBatch p;
+  int start[T2S2_MAX_D + 1];  // first tile of each core; start[ncores] = total
+  __device__ int n() const { return p.ncores; }
+  __device__ int first(int i) const { return start[i]; }
+  __device__ ApplyCore core(int i) const { return p.c[i]; }
+};
+struct GlobalWork {
+  const ApplyCore* c;
+  const int* start;
+  int ncores;
+  __device__ int n() const { return ncores; }
+  __device__ int first(int i) const { return start[i]; }
+  __device__ ApplyCore core(int i) const { return c[i]; }
 };
 
-__global__ void __launch_bounds__(NT) apply_kernel(ApplyBatch p, TileMap tm) {
+template <class Work>
+__device__ __forceinline__ int find_core(const Work& w, int tile) {
+  int lo = 0, hi = w.n() - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (w.first(mid) <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Persistent over tiles: CTA b takes tiles b, b + gridDim.x, ...
+template <class Work>
+__global__ void __launch_bounds__(NT) apply_kernel(Work w, int total) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
-  int core = 0;
-  while (core + 1 < p.ncores && (int)blockIdx.x >= tm.start[core + 1]) ++core;
-  const ApplyCore& c = p.c[core];
-  const int local = blockIdx.x - tm.start[core];
-  const int mt = cdiv_dev(2 * c.m, BM), nt = cdiv_dev(c.rb, BN);
-  const int a = local / (mt * nt);
-  const int rem = local % (mt * nt);
-  const int m0 = (rem / nt) * BM, n0 = (rem % nt) * BN;
-  const double* X = c.X + (long)a * c.m * c.rb;  // m x rb
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4];
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const int ci = find_core(w, tile);
+    const ApplyCore c = w.core(ci);
+    const int local = tile - w.first(ci);
+    const int mt = cdiv_dev(2 * c.m, BM), nt = cdiv_dev(c.rb, BN);
+    const int a = local / (mt * nt);
+    const int rem = local % (mt * nt);
+    const int m0 = (rem / nt) * BM, n0 = (rem % nt) * BN;
+    const double* X = c.X + (long)a * c.m * c.rb;  // m x rb
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int k0 = 0; k0 < c.m; k0 += BK) {
-    for (int e = threadIdx.x; e < BM * BK; e += NT) {
-      int kk = e % BK, mm = e / BK;
-      int row = m0 + mm, col = k0 + kk;
-      double v = 0.0;
-      if (row < 2 * c.m && col < c.m) {
-        if (row < c.m) {
-          v = c.S[(long)row * c.m + col];
-        } else {
-          long o = (long)(row - c.m) * c.m + col;
-          v = c.g_op * c.L[o];
-          if (c.g_mass != 0.0) v += c.g_mass * c.S[o];
-        }
-      }
-      As[kk][mm] = v;
-    }
-    for (int e = threadIdx.x; e < BN * BK; e += NT) {
-      int nn = e % BN, kk = e / BN;
-      int col = n0 + nn, row = k0 + kk;
-      Bs[kk][nn] = (row < c.m && col < c.rb) ? X[(long)row * c.rb + col] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      double av[4], bv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-  // scatter
-  const int ra = c.ra, rb = c.rb, m = c.m;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int row = m0 + ty + 16 * i;
-    if (row >= 2 * m) continue;
-    const bool gpart = row >= m;
-    const int ii = gpart ? row - m : row;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int b = n0 + tx + 16 * j;
-      if (b >= rb) continue;
-      double v = acc[i][j];
-      double* Y = c.Y;
-      switch (c.kind) {
-        case kApplySingle:  // 1 x m x 1
-          if (gpart) Y[ii] = v;
-          break;
-        case kApplyFirst: {  // 1 x m x 2rb: [G X, S X]
-          long base = (long)ii * 2 * rb;
-          if (gpart) Y[base + b] = v; else Y[base + rb + b] = v;
-          break;
-        }
-        case kApplyLast: {  // 2ra x m x 1: [S X; G X]
-          long r = gpart ? (ra + a) : a;
-          Y[r * m + ii] = v;
-          break;
-        }
-        default: {  // middle: 2ra x m x 2rb
-          long w = 2L * rb;
-          if (gpart) {
-            Y[((long)(ra + a) * m + ii) * w + b] = v;            // (1,0): G X
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < c.m; k0 += BK) {
+      for (int e = threadIdx.x; e < BM * BK; e += NT) {
+        int kk = e % BK, mm = e / BK;
+        int row = m0 + mm, col = k0 + kk;
+        double v = 0.0;
+        if (row < 2 * c.m && col < c.m) {
+          if (row < c.m) {
+            v = c.S[(long)row * c.m + col];
           } else {
-            Y[((long)a * m + ii) * w + b] = v;                   // (0,0): S X
-            Y[((long)(ra + a) * m + ii) * w + rb + b] = v;       // (1,1): S X
-            Y[((long)a * m + ii) * w + rb + b] = 0.0;            // (0,1): 0
+            long o = (long)(row - c.m) * c.m + col;
+            v = c.g_op * c.L[o];
+            if (c.g_mass != 0.0) v += c.g_mass * c.S[o];
+          }
+        }
+        As[kk][mm] = v;
+      }
+      for (int e = threadIdx.x; e < BN * BK; e += NT) {
+        int nn = e % BN, kk = e / BN;
+        int col = n0 + nn, row = k0 + kk;
+        Bs[kk][nn] = (row < c.m && col < c.rb) ? X[(long)row * c.rb + col] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+    // scatter
+    const int ra = c.ra, rb = c.rb, m = c.m;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int row = m0 + ty + 16 * i;
+      if (row >= 2 * m) continue;
+      const bool gpart = row >= m;
+      const int ii = gpart ? row - m : row;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int b = n0 + tx + 16 * j;
+        if (b >= rb) continue;
+        double v = acc[i][j];
+        double* Y = c.Y;
+        switch (c.kind) {
+          case kApplySingle:  // 1 x m x 1
+            if (gpart) Y[ii] = v;
+            break;
+          case kApplyFirst: {  // 1 x m x 2rb: [G X, S X]
+            long base = (long)ii * 2 * rb;
+            if (gpart) Y[base + b] = v; else Y[base + rb + b] = v;
+            break;
+          }
+          case kApplyLast: {  // 2ra x m x 1: [S X; G X]
+            long r = gpart ? (ra + a) : a;
+            Y[r * m + ii] = v;
+            break;
+          }
+          default: {  // middle: 2ra x m x 2rb
+            long wd = 2L * rb;
+            if (gpart) {
+              Y[((long)(ra + a) * m + ii) * wd + b] = v;            // (1,0): G X
+            } else {
+              Y[((long)a * m + ii) * wd + b] = v;                   // (0,0): S X
+              Y[((long)(ra + a) * m + ii) * wd + rb + b] = v;       // (1,1): S X
+              Y[((long)a * m + ii) * wd + rb + b] = 0.0;            // (0,1): 0
+            }
           }
         }
       }
@@ -122,22 +149,34 @@ __global__ void __launch_bounds__(NT) apply_kernel(ApplyBatch p, TileMap tm) {
 }
 }  // namespace
 
+int apply_fp64_tiles(const ApplyCore& c) { return c.ra * cdiv(2 * c.m, BM) * cdiv(c.rb, BN); }
+
 t2s2_status apply_fp64(const ApplyBatch& p, cudaStream_t st) {
-  TileMap tm;
+  ParamWork w;
+  w.p = p;
   int total = 0;
   double fl = 0.0, by = 0.0;
   for (int k = 0; k < p.ncores; ++k) {
-    tm.start[k] = total;
+    w.start[k] = total;
     const ApplyCore& c = p.c[k];
-    total += c.ra * cdiv(2 * c.m, BM) * cdiv(c.rb, BN);
-    fl += 2.0 * (2.0 * c.m) * c.m * (double)c.ra * c.rb;
-    const int ny = (c.kind == kApplyMiddle) ? 4 : ((c.kind == kApplySingle) ? 1 : 2);
-    by += 8.0 * ((double)c.ra * c.m * c.rb * (1 + ny) + 2.0 * c.m * c.m);
+    total += apply_fp64_tiles(c);
+    apply_work_totals(c, &fl, &by);
   }
-  tm.start[p.ncores] = total;
+  w.start[p.ncores] = total;
   if (total == 0) return T2S2_OK;
   TraceScope ts(kTrApply, st, fl, by);
-  apply_kernel<<<total, NT, 0, st>>>(p, tm);
+  apply_kernel<ParamWork><<<total, NT, 0, st>>>(w, total);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+
+t2s2_status apply_fp64_grouped(const ApplyCore* dcores, const int* dstart, int ncores, int total, int grid,
+                               double flops, double bytes, cudaStream_t st) {
+  if (ncores < 1 || total < 0 || grid < 1) return T2S2_EINVAL;
+  if (total == 0) return T2S2_OK;
+  GlobalWork w{dcores, dstart, ncores};
+  TraceScope ts(kTrApply, st, flops, bytes);
+  apply_kernel<GlobalWork><<<std::min(grid, total), NT, 0, st>>>(w, total);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }

@@ -30,4 +30,18 @@ t2s2_status apply_fp64(const ApplyBatch& p, cudaStream_t st);
 bool apply_tc_supported(const ApplyBatch& p);
 t2s2_status apply_tc(const ApplyBatch& p, int prec, int* err, cudaStream_t st);
 
+// Grouped, persistent launches over the cores of many trains: dcores (device)
+// holds ncores descriptors, dstart (device) the prefix sums of their tile
+// counts (apply_fp64_tiles / apply_tc_tiles), dstart[ncores] = total; `grid`
+// CTAs loop over the tiles.  flops / bytes are the algorithmic totals for
+// tracing (apply_work_totals summed over the cores).
+int apply_fp64_tiles(const ApplyCore& c);
+int apply_tc_tiles(const ApplyCore& c);
+int apply_tc_max_ctas_per_sm(int prec);
+void apply_work_totals(const ApplyCore& c, double* flops, double* bytes);
+t2s2_status apply_fp64_grouped(const ApplyCore* dcores, const int* dstart, int ncores, int total, int grid,
+                               double flops, double bytes, cudaStream_t st);
+t2s2_status apply_tc_grouped(const ApplyCore* dcores, const int* dstart, int ncores, int total, int grid,
+                             double flops, double bytes, int prec, int* err, cudaStream_t st);
+
 }  // namespace t2s2

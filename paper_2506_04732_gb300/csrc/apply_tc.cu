@@ -16,6 +16,8 @@
 // The wait on the mbarrier is bounded: on timeout the CTA sets *err, waits
 // once more (bounded) for its MMAs, frees its TMEM and returns without
 // writing Y.
+#include <algorithm>
+
 #include "apply.h"
 #include "tc_common.cuh"
 #include "trace.h"
@@ -38,89 +40,125 @@ constexpr int smem_bytes(int elem_bytes) {
                                                             : 48 * 1024;
 }
 
-struct TileMapTc {
+// Where a CTA finds its work: the cores of one train in kernel parameters, or
+// a device array of cores from many trains (grouped launch).  start[i] is the
+// first tile of core i; start[n] the total.
+struct ParamWork {
+  ApplyBatch p;
   int start[T2S2_MAX_D + 1];
+  __device__ int n() const { return p.ncores; }
+  __device__ int first(int i) const { return start[i]; }
+  __device__ ApplyCore core(int i) const { return p.c[i]; }
+};
+struct GlobalWork {
+  const ApplyCore* c;
+  const int* start;
+  int ncores;
+  __device__ int n() const { return ncores; }
+  __device__ int first(int i) const { return start[i]; }
+  __device__ ApplyCore core(int i) const { return c[i]; }
 };
 
-template <int P>
-__global__ void __launch_bounds__(kThreads) apply_tc_kernel(ApplyBatch p, TileMapTc tm, int* err) {
+template <class Work>
+__device__ __forceinline__ int find_core(const Work& w, int tile) {
+  int lo = 0, hi = w.n() - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (w.first(mid) <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Persistent: CTA b handles tiles b, b + gridDim.x, ...  TMEM and the
+// mbarrier are set up once; the operator tile is restaged only when the core
+// changes.
+template <int P, class Work>
+__global__ void __launch_bounds__(kThreads) apply_tc_kernel(Work w, int total, int* err) {
   using O = Op<P>;
   constexpr int E = O::kBytes;
   constexpr int kTileBytes = kTileM * kMaxK * E;  // 16 KB (BF16) or 32 KB (TF32)
+  constexpr int W = 128 / E;                      // elements per swizzle row
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of both tiles (the swizzle pattern repeats every 1024 B)
   unsigned char* sA = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   unsigned char* sB = sA + kTileBytes;
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sB + kTileBytes);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
-
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  int core = 0;
-  while (core + 1 < p.ncores && (int)blockIdx.x >= tm.start[core + 1]) ++core;
-  const ApplyCore& c = p.c[core];
-  const int m = c.m, ra = c.ra, rb = c.rb;
-  const long nrows = (long)ra * rb;
-  const long row0 = (long)(blockIdx.x - tm.start[core]) * kTileM;
-  // K padded to whole MMAs; N = 2m padded to a multiple of 16 (M = 128 form)
-  const int kpad = ((m + O::kMmaK - 1) / O::kMmaK) * O::kMmaK;
-  const int npad = ((2 * m + 15) / 16) * 16;
 
   if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kTileN);
   if (tid == 0) mbar_init(smem_u32(mbar), 1);
-  // A tile: row t <-> pair g = row0 + t = (a, b); zero rows past the core
-  {
-    const long g = row0 + tid;
-    const bool valid = g < nrows;
-    const long a = valid ? g / rb : 0, b = valid ? g % rb : 0;
-    const double* xr = c.X + a * (long)m * rb + b;
-    for (int j = 0; j < kpad; ++j) {
-      const double v = (valid && j < m) ? xr[(long)j * rb] : 0.0;
-      O::store(sA + sw128_off<E>(tid, j, kTileM), v);
-    }
-  }
-  // B tile: row ii < m: S row ii; m <= ii < 2m: G row ii - m; zero padded
-  for (int e = tid; e < npad * kpad; e += kThreads) {
-    const int ii = e / kpad, j = e % kpad;
-    double v = 0.0;
-    if (ii < 2 * m && j < m) {
-      if (ii < m) {
-        v = c.S[(long)ii * m + j];
-      } else {
-        const long o = (long)(ii - m) * m + j;
-        v = c.g_op * c.L[o];
-        if (c.g_mass != 0.0) v += c.g_mass * c.S[o];
-      }
-    }
-    O::store(sB + sw128_off<E>(ii, j, kTileM), v);
-  }
-  // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
-  fence_smem_to_async();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const uint32_t bar = smem_u32(mbar);
-  if (tid == 0) {
-    const uint32_t idesc = make_idesc(O::kFmt, kTileM, npad);
-    constexpr int W = 128 / E;  // elements per swizzle row
-    for (int k0 = 0; k0 < kpad; k0 += O::kMmaK) {
-      // K-block base, then 32 bytes per MMA step inside the 128-byte row
-      const uint32_t off = (uint32_t)((k0 / W) * (kTileM * 128) + (k0 % W) * E);
-      const uint64_t da = sdesc_sw128(smem_u32(sA) + off);
-      const uint64_t db = sdesc_sw128(smem_u32(sB) + off);
-      issue_mma<P>(tmem, da, db, idesc, k0 > 0 ? 1u : 0u);
+
+  int staged = -1;  // core whose operator tile sits in sB
+  uint32_t phase = 0;
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x, phase ^= 1u) {
+    const int ci = find_core(w, tile);
+    const ApplyCore c = w.core(ci);
+    const int m = c.m, ra = c.ra, rb = c.rb;
+    const long nrows = (long)ra * rb;
+    const long row0 = (long)(tile - w.first(ci)) * kTileM;
+    // K padded to whole MMAs; N = 2m padded to a multiple of 16 (M = 128 form)
+    const int kpad = ((m + O::kMmaK - 1) / O::kMmaK) * O::kMmaK;
+    const int npad = ((2 * m + 15) / 16) * 16;
+    // A tile: row t <-> pair g = row0 + t = (a, b); zero rows past the core
+    {
+      const long g = row0 + tid;
+      const bool valid = g < nrows;
+      const long a = valid ? g / rb : 0, b = valid ? g % rb : 0;
+      const double* xr = c.X + a * (long)m * rb + b;
+      for (int j = 0; j < kpad; ++j) {
+        const double v = (valid && j < m) ? xr[(long)j * rb] : 0.0;
+        O::store(sA + sw128_off<E>(tid, j, kTileM), v);
+      }
     }
-    mma_commit(bar);
-  }
-  // every thread waits (bounded); the block-wide vote keeps the warp-collective
-  // TMEM loads below uniform even if one thread's wait ran out
-  const bool ok = __syncthreads_and(mbar_wait(bar, 0)) != 0;
-  if (!ok) {
-    if (tid == 0) atomicExch(err, 1);
-    mbar_wait(bar, 0);  // bounded second wait for MMAs still in flight
-  }
-  fence_after_sync();
-  if (ok) {
+    // B tile: row ii < m: S row ii; m <= ii < 2m: G row ii - m; zero padded
+    if (ci != staged) {
+      for (int e = tid; e < npad * kpad; e += kThreads) {
+        const int ii = e / kpad, j = e % kpad;
+        double v = 0.0;
+        if (ii < 2 * m && j < m) {
+          if (ii < m) {
+            v = c.S[(long)ii * m + j];
+          } else {
+            const long o = (long)(ii - m) * m + j;
+            v = c.g_op * c.L[o];
+            if (c.g_mass != 0.0) v += c.g_mass * c.S[o];
+          }
+        }
+        O::store(sB + sw128_off<E>(ii, j, kTileM), v);
+      }
+      staged = ci;
+    }
+    // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
+    fence_smem_to_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (tid == 0) {
+      const uint32_t idesc = make_idesc(O::kFmt, kTileM, npad);
+      for (int k0 = 0; k0 < kpad; k0 += O::kMmaK) {
+        // K-block base, then 32 bytes per MMA step inside the 128-byte row
+        const uint32_t off = (uint32_t)((k0 / W) * (kTileM * 128) + (k0 % W) * E);
+        const uint64_t da = sdesc_sw128(smem_u32(sA) + off);
+        const uint64_t db = sdesc_sw128(smem_u32(sB) + off);
+        issue_mma<P>(tmem, da, db, idesc, k0 > 0 ? 1u : 0u);
+      }
+      mma_commit(bar);
+    }
+    // every thread waits (bounded); the block-wide vote keeps the
+    // warp-collective TMEM loads below uniform even if one wait ran out
+    const bool ok = __syncthreads_and(mbar_wait(bar, phase)) != 0;
+    if (!ok) {
+      if (tid == 0) atomicExch(err, 1);
+      mbar_wait(bar, phase);  // bounded second wait for MMAs still in flight
+      break;
+    }
+    fence_after_sync();
     // epilogue: warp w owns TMEM lanes 32w .. 32w+31 = tile rows
     const int t = warp * 32 + lane;
     const long g = row0 + t;
@@ -153,32 +191,39 @@ __global__ void __launch_bounds__(kThreads) apply_tc_kernel(ApplyBatch p, TileMa
             break;
           }
           default: {  // middle: 2ra x m x 2rb
-            const long w = 2L * rb;
+            const long wd = 2L * rb;
             if (gpart) {
-              Y[((long)(ra + a) * m + ii) * w + b] = val;
+              Y[((long)(ra + a) * m + ii) * wd + b] = val;
             } else {
-              Y[((long)a * m + ii) * w + b] = val;
-              Y[((long)(ra + a) * m + ii) * w + rb + b] = val;
-              Y[((long)a * m + ii) * w + rb + b] = 0.0;
+              Y[((long)a * m + ii) * wd + b] = val;
+              Y[((long)(ra + a) * m + ii) * wd + rb + b] = val;
+              Y[((long)a * m + ii) * wd + rb + b] = 0.0;
             }
           }
         }
       }
     }
+    fence_before_sync();  // TMEM reads done before the next tile's MMAs
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, kTileN);
 }
 
-template <int P>
-t2s2_status launch_tc(const ApplyBatch& p, const TileMapTc& tm, int total, int* err, cudaStream_t st) {
+template <int P, class Work>
+t2s2_status launch_tc(const Work& w, int total, int grid, int* err, cudaStream_t st) {
   constexpr int kSmem = smem_bytes(Op<P>::kBytes);
   // the attribute is per function and device; setting it each call is cheap
-  T2S2_CUDA_TRY(cudaFuncSetAttribute(apply_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
-  apply_tc_kernel<P><<<total, kThreads, kSmem, st>>>(p, tm, err);
+  T2S2_CUDA_TRY(cudaFuncSetAttribute(apply_tc_kernel<P, Work>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  apply_tc_kernel<P, Work><<<grid, kThreads, kSmem, st>>>(w, total, err);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
+}
+
+void work_totals(const ApplyCore& c, double& fl, double& by) {
+  fl += 2.0 * (2.0 * c.m) * c.m * (double)c.ra * c.rb;
+  const int ny = (c.kind == kApplyMiddle) ? 4 : ((c.kind == kApplySingle) ? 1 : 2);
+  by += 8.0 * ((double)c.ra * c.m * c.rb * (1 + ny) + 2.0 * c.m * c.m);
 }
 
 }  // namespace
@@ -189,25 +234,43 @@ bool apply_tc_supported(const ApplyBatch& p) {
   return true;
 }
 
+int apply_tc_tiles(const ApplyCore& c) { return (int)((((long)c.ra * c.rb) + kTileM - 1) / kTileM); }
+
+int apply_tc_max_ctas_per_sm(int prec) {
+  const int smem = smem_bytes(prec == T2S2_BF16_REFINE ? 2 : 4);
+  return std::min(512 / kTileN, (227 * 1024) / smem);
+}
+
 t2s2_status apply_tc(const ApplyBatch& p, int prec, int* err, cudaStream_t st) {
   if (prec != T2S2_BF16_REFINE && prec != T2S2_TF32_REFINE) return T2S2_EINVAL;
   if (!apply_tc_supported(p) || !err) return T2S2_EINVAL;
-  TileMapTc tm;
+  ParamWork w;
+  w.p = p;
   int total = 0;
   double fl = 0.0, by = 0.0;
   for (int k = 0; k < p.ncores; ++k) {
-    tm.start[k] = total;
-    const ApplyCore& c = p.c[k];
-    total += (int)((((long)c.ra * c.rb) + kTileM - 1) / kTileM);
-    fl += 2.0 * (2.0 * c.m) * c.m * (double)c.ra * c.rb;
-    const int ny = (c.kind == kApplyMiddle) ? 4 : ((c.kind == kApplySingle) ? 1 : 2);
-    by += 8.0 * ((double)c.ra * c.m * c.rb * (1 + ny) + 2.0 * c.m * c.m);
+    w.start[k] = total;
+    total += apply_tc_tiles(p.c[k]);
+    work_totals(p.c[k], fl, by);
   }
-  tm.start[p.ncores] = total;
+  w.start[p.ncores] = total;
   if (total == 0) return T2S2_OK;
   TraceScope ts(kTrApplyTc, st, fl, by);
-  if (prec == T2S2_BF16_REFINE) return launch_tc<T2S2_BF16_REFINE>(p, tm, total, err, st);
-  return launch_tc<T2S2_TF32_REFINE>(p, tm, total, err, st);
+  if (prec == T2S2_BF16_REFINE) return launch_tc<T2S2_BF16_REFINE>(w, total, total, err, st);
+  return launch_tc<T2S2_TF32_REFINE>(w, total, total, err, st);
 }
+
+t2s2_status apply_tc_grouped(const ApplyCore* dcores, const int* dstart, int ncores, int total, int grid,
+                             double flops, double bytes, int prec, int* err, cudaStream_t st) {
+  if (prec != T2S2_BF16_REFINE && prec != T2S2_TF32_REFINE) return T2S2_EINVAL;
+  if (!err || ncores < 1 || total < 0 || grid < 1) return T2S2_EINVAL;
+  if (total == 0) return T2S2_OK;
+  GlobalWork w{dcores, dstart, ncores};
+  TraceScope ts(kTrApplyTc, st, flops, bytes);
+  if (prec == T2S2_BF16_REFINE) return launch_tc<T2S2_BF16_REFINE>(w, total, std::min(grid, total), err, st);
+  return launch_tc<T2S2_TF32_REFINE>(w, total, std::min(grid, total), err, st);
+}
+
+void apply_work_totals(const ApplyCore& c, double* flops, double* bytes) { work_totals(c, *flops, *bytes); }
 
 }  // namespace t2s2

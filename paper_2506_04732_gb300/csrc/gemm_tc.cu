@@ -1,7 +1,8 @@
-// Strided-batched GEMM on tcgen05 tensor cores for the mixed-precision solver:
+// Strided-batched GEMM on tcgen05 tensor cores (the mixed-precision solver's
+// contractions and the warm-start network's layers):
 //   C_b = alpha * op(A_b) * op(B_b) + beta * C_b
-// with FP64 operands and result in HBM, operands rounded to BF16 or TF32 while
-// they are staged in shared memory, and FP32 accumulation in TMEM.
+// with FP64 or FP32 operands and result in HBM, operands rounded to BF16 or
+// TF32 while they are staged in shared memory, and FP32 accumulation in TMEM.
 //
 // The MMA's M side (128 TMEM lanes per CTA) takes the longer of the two
 // output dimensions: when N > M the kernel computes C^T = op(B)^T op(A)^T and
@@ -29,15 +30,16 @@ using namespace tc;
 constexpr int kRows = 128;    // MMA M = TMEM lanes
 constexpr int kThreads = 128;
 
+template <typename T>
 struct TcGemm {
   int M, N, K;  // after the optional swap: M rows (MMA M), N cols (MMA N)
-  const double* R;  // row operand, element (i, k)
+  const T* R;  // row operand, element (i, k)
   long ldr, sR;
   int r_kc;  // 1: (i, k) at R[i * ldr + k]; 0: at R[k * ldr + i]
-  const double* Q;  // column operand, element (j, k)
+  const T* Q;  // column operand, element (j, k)
   long ldq, sQ;
   int q_kc;
-  double* C;
+  T* C;
   long ldc, sC;
   int c_trans;  // 1: C(i, j) at C[j * ldc + i]; 0: at C[i * ldc + j]
   double alpha, beta;
@@ -56,8 +58,8 @@ constexpr int gemm_smem_bytes() {
   return tiles > floor_bytes ? tiles : floor_bytes;
 }
 
-template <int P, int BN>
-__global__ void __launch_bounds__(kThreads) gemm_tc_kernel(TcGemm g, int* err) {
+template <int P, int BN, typename T>
+__global__ void __launch_bounds__(kThreads) gemm_tc_kernel(TcGemm<T> g, int* err) {
   using O = Op<P>;
   constexpr int E = O::kBytes;
   constexpr int BK = 128 / E;  // K elements per stage (one swizzle row)
@@ -73,8 +75,8 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(TcGemm g, int* err) {
   const int i0 = blockIdx.x * kRows, j0 = blockIdx.y * BN;
   const int k_begin = sidx * g.kchunk;
   const int k_end = min(g.K, k_begin + g.kchunk);
-  const double* R = g.R + (long)b * g.sR;
-  const double* Q = g.Q + (long)b * g.sQ;
+  const T* R = g.R + (long)b * g.sR;
+  const T* Q = g.Q + (long)b * g.sQ;
 
   if (warp == 0) tmem_alloc(smem_u32(tmem_slot), BN);
   if (tid == 0) mbar_init(smem_u32(mbar), 1);
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(TcGemm g, int* err) {
       for (int e = tid; e < kRows * BK; e += kThreads) {
         const int i = e / BK, k = e % BK;
         const int gi = i0 + i;
-        const double v = (gi < g.M && k < kn) ? R[(long)gi * g.ldr + (k0 + k)] : 0.0;
+        const double v = (gi < g.M && k < kn) ? (double)R[(long)gi * g.ldr + (k0 + k)] : 0.0;
         O::store(sR + sw128_off<E>(i, k, kRows), v);
       }
     } else {
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(TcGemm g, int* err) {
       for (int e = tid; e < kRows * BK; e += kThreads) {
         const int k = e / kRows, i = e % kRows;
         const int gi = i0 + i;
-        const double v = (gi < g.M && k < kn) ? R[(long)(k0 + k) * g.ldr + gi] : 0.0;
+        const double v = (gi < g.M && k < kn) ? (double)R[(long)(k0 + k) * g.ldr + gi] : 0.0;
         O::store(sR + sw128_off<E>(i, k, kRows), v);
       }
     }
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(TcGemm g, int* err) {
       for (int e = tid; e < BN * BK; e += kThreads) {
         const int j = e / BK, k = e % BK;
         const int gj = j0 + j;
-        const double v = (gj < g.N && k < kn) ? Q[(long)gj * g.ldq + (k0 + k)] : 0.0;
+        const double v = (gj < g.N && k < kn) ? (double)Q[(long)gj * g.ldq + (k0 + k)] : 0.0;
         O::store(sQ + sw128_off<E>(j, k, BN), v);
       }
     } else {
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(TcGemm g, int* err) {
       for (int e = tid; e < BN * BK; e += kThreads) {
         const int k = e / BN, j = e % BN;
         const int gj = j0 + j;
-        const double v = (gj < g.N && k < kn) ? Q[(long)(k0 + k) * g.ldq + gj] : 0.0;
+        const double v = (gj < g.N && k < kn) ? (double)Q[(long)(k0 + k) * g.ldq + gj] : 0.0;
         O::store(sQ + sw128_off<E>(j, k, BN), v);
       }
     }
@@ -171,10 +173,10 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(TcGemm g, int* err) {
         if (g.splits > 1) {
           g.ws[(((long)b * g.splits + sidx) * g.M + i) * g.N + j] = acc;
         } else {
-          double* c = g.C + (long)b * g.sC + (g.c_trans ? (long)j * g.ldc + i : (long)i * g.ldc + j);
+          T* c = g.C + (long)b * g.sC + (g.c_trans ? (long)j * g.ldc + i : (long)i * g.ldc + j);
           double r = g.alpha * (double)acc;
-          if (g.beta != 0.0) r = fma(g.beta, *c, r);
-          *c = r;
+          if (g.beta != 0.0) r = fma(g.beta, (double)*c, r);
+          *c = (T)r;
         }
       }
     }
@@ -185,7 +187,8 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(TcGemm g, int* err) {
 }
 
 // C = alpha * sum_s ws[b][s] + beta * C, summed over s in order.
-__global__ void splitk_sum_kernel(TcGemm g) {
+template <typename T>
+__global__ void splitk_sum_kernel(TcGemm<T> g) {
   const long total = (long)g.batch * g.M * g.N;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
     const int j = (int)(e % g.N);
@@ -194,16 +197,17 @@ __global__ void splitk_sum_kernel(TcGemm g) {
     const int b = (int)(t / g.M);
     double s = 0.0;
     for (int p = 0; p < g.splits; ++p) s += (double)g.ws[(((long)b * g.splits + p) * g.M + i) * g.N + j];
-    double* c = g.C + (long)b * g.sC + (g.c_trans ? (long)j * g.ldc + i : (long)i * g.ldc + j);
+    T* c = g.C + (long)b * g.sC + (g.c_trans ? (long)j * g.ldc + i : (long)i * g.ldc + j);
     double r = g.alpha * s;
-    if (g.beta != 0.0) r = fma(g.beta, *c, r);
-    *c = r;
+    if (g.beta != 0.0) r = fma(g.beta, (double)*c, r);
+    *c = (T)r;
   }
 }
 
 // Convert the public description into the kernel's, choosing the swap.
-TcGemm describe(const Gemm<double>& in) {
-  TcGemm g{};
+template <typename T>
+TcGemm<T> describe(const Gemm<T>& in) {
+  TcGemm<T> g{};
   const bool swap = in.N > in.M;
   g.K = in.K;
   g.alpha = in.alpha;
@@ -235,7 +239,8 @@ int pick_bn(int N) {
 }
 
 // Split K so that the grid reaches about two CTAs per SM.
-void plan_splits(TcGemm& g, int bn, int bk) {
+template <typename T>
+void plan_splits(TcGemm<T>& g, int bn, int bk) {
   const long tiles = (long)cdiv(g.M, kRows) * cdiv(g.N, bn) * g.batch;
   const int stages = std::max(1, cdiv(g.K, bk));
   int splits = 1;
@@ -247,52 +252,54 @@ void plan_splits(TcGemm& g, int bn, int bk) {
   if ((long)g.batch * g.splits > 65535) g.splits = 1, g.kchunk = std::max(g.K, 1);
 }
 
-template <int P, int BN>
-t2s2_status launch(const TcGemm& g, int* err, cudaStream_t st) {
+template <int P, int BN, typename T>
+t2s2_status launch(const TcGemm<T>& g, int* err, cudaStream_t st) {
   constexpr int smem = gemm_smem_bytes<Op<P>::kBytes, BN>();
-  T2S2_CUDA_TRY(cudaFuncSetAttribute(gemm_tc_kernel<P, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  T2S2_CUDA_TRY(cudaFuncSetAttribute(gemm_tc_kernel<P, BN, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   dim3 grid(cdiv(g.M, kRows), cdiv(g.N, BN), g.batch * g.splits);
-  gemm_tc_kernel<P, BN><<<grid, kThreads, smem, st>>>(g, err);
+  gemm_tc_kernel<P, BN, T><<<grid, kThreads, smem, st>>>(g, err);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 
-template <int P>
-t2s2_status launch_bn(const TcGemm& g, int bn, int* err, cudaStream_t st) {
+template <int P, typename T>
+t2s2_status launch_bn(const TcGemm<T>& g, int bn, int* err, cudaStream_t st) {
   switch (bn) {
-    case 32: return launch<P, 32>(g, err, st);
-    case 64: return launch<P, 64>(g, err, st);
-    case 128: return launch<P, 128>(g, err, st);
-    default: return launch<P, 256>(g, err, st);
+    case 32: return launch<P, 32, T>(g, err, st);
+    case 64: return launch<P, 64, T>(g, err, st);
+    case 128: return launch<P, 128, T>(g, err, st);
+    default: return launch<P, 256, T>(g, err, st);
   }
 }
 
 }  // namespace
 
-size_t gemm_tc_workspace(const Gemm<double>& in, int prec) {
-  TcGemm g = describe(in);
+template <typename T>
+size_t gemm_tc_workspace_bytes(const Gemm<T>& in, int prec) {
+  TcGemm<T> g = describe(in);
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return 0;
   const int bk = prec == T2S2_BF16_REFINE ? 64 : 32;
   plan_splits(g, pick_bn(g.N), bk);
   if (g.splits <= 1) return 0;
-  // floats, rounded up to whole doubles for the caller's FP64 arena
-  return ((size_t)g.batch * g.splits * g.M * g.N + 1) / 2;
+  return (size_t)g.batch * g.splits * g.M * g.N * sizeof(float);
 }
 
-t2s2_status gemm_tc(const Gemm<double>& in, int prec, double* ws, size_t ws_elems, int* err, cudaStream_t st) {
+template <typename T>
+t2s2_status gemm_tc(const Gemm<T>& in, int prec, void* ws, size_t ws_bytes, int* err, cudaStream_t st) {
   if (prec != T2S2_BF16_REFINE && prec != T2S2_TF32_REFINE) return T2S2_EINVAL;
   if (!err || in.M < 0 || in.N < 0 || in.K < 0 || in.batch < 0) return T2S2_EINVAL;
   if (in.M == 0 || in.N == 0 || in.batch == 0) return T2S2_OK;
-  TcGemm g = describe(in);
+  TcGemm<T> g = describe(in);
   const int bk = prec == T2S2_BF16_REFINE ? 64 : 32;
   const int bn = pick_bn(g.N);
   plan_splits(g, bn, bk);
   if (g.splits > 1) {
-    if (!ws || ws_elems < gemm_tc_workspace(in, prec)) return T2S2_ENOMEM;
+    if (!ws || ws_bytes < gemm_tc_workspace_bytes(in, prec)) return T2S2_ENOMEM;
     g.ws = reinterpret_cast<float*>(ws);
   }
   const double fl = 2.0 * in.M * in.N * (double)in.K * in.batch;
-  const double by = 8.0 * in.batch * ((double)in.M * in.K + (double)in.K * in.N + (in.beta != 0.0 ? 2.0 : 1.0) * in.M * in.N);
+  const double by = (double)sizeof(T) * in.batch *
+                    ((double)in.M * in.K + (double)in.K * in.N + (in.beta != 0 ? 2.0 : 1.0) * in.M * in.N);
   {
     TraceScope ts(kTrGemmTc, st, fl, by);
     if (prec == T2S2_BF16_REFINE) {
@@ -305,10 +312,15 @@ t2s2_status gemm_tc(const Gemm<double>& in, int prec, double* ws, size_t ws_elem
     TraceScope ts(kTrGemmTc, st, 0.0, 0.0);
     const long total = (long)g.batch * g.M * g.N;
     const int blocks = (int)std::min<long>(cdiv(total, 256), 4L * kNumSMs);
-    splitk_sum_kernel<<<blocks, 256, 0, st>>>(g);
+    splitk_sum_kernel<T><<<blocks, 256, 0, st>>>(g);
     T2S2_CUDA_TRY(cudaGetLastError());
   }
   return T2S2_OK;
 }
+
+template size_t gemm_tc_workspace_bytes<double>(const Gemm<double>&, int);
+template size_t gemm_tc_workspace_bytes<float>(const Gemm<float>&, int);
+template t2s2_status gemm_tc<double>(const Gemm<double>&, int, void*, size_t, int*, cudaStream_t);
+template t2s2_status gemm_tc<float>(const Gemm<float>&, int, void*, size_t, int*, cudaStream_t);
 
 }  // namespace t2s2

@@ -1,0 +1,628 @@
+// Learned warm start: an MLP from problem parameters to the TT cores of an
+// initial guess for the alternating solver, trained on the GPU by this file's
+// kernels.  The solver accepts any initial guess and always runs to the same
+// residual tolerance, so the network can only change the number of sweeps,
+// never the answer.
+//
+//   h1 = relu(W1 p + b1),  h2 = relu(W2 h1 + b2),  y = W3 h2 + b3,
+//
+// y holds the cores of X(p): core 0 (1 x m_1 x r), middle cores (r x m_k x r),
+// last core (r x m_d x 1), row-major, concatenated.  Loss per sample with
+// target U: ||X - U||^2 / ||U||^2 = (<X,X> - 2 <X,U> + <U,U>) / <U,U>, which
+// does not depend on the TT gauge of X; its gradient with respect to core k
+// comes from the left and right environments of <X,X> and <X,U>.
+//
+// Kernels: the six layer products (three forward, three backward per layer
+// pair) run on the tcgen05 GEMM with BF16 operands (weights and activations
+// rounded as they are staged) and FP32 accumulation; bias/ReLU, the TT loss
+// and its core gradient (one CTA per sample, environments in shared memory),
+// the column sums for the bias gradients and Adam are FP32 SIMT kernels.
+// Parameters, gradients and Adam moments are FP32 master copies.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "api_internal.h"
+#include "gemm_tc.h"
+#include "trace.h"
+
+struct t2s2_mlp_s {
+  int device = 0;
+  int in_dim = 0, hidden = 0, d = 0, r = 0, ru = 0, odim = 0, mmax = 0;
+  int m[T2S2_MAX_D] = {0};
+  int off[T2S2_MAX_D + 1] = {0};  // offsets of the cores in y
+  long long nparams = 0;
+  long long oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
+  float* params = nullptr;  // W1 b1 W2 b2 W3 b3
+  float* grads = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  long long step = 0;
+  int bcap = 0;  // batch capacity of the activation buffers
+  float *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *y = nullptr, *dy = nullptr;
+  float *dh = nullptr, *dz = nullptr, *loss = nullptr;
+  float* pbuf = nullptr;  // in_dim floats: the input of a single prediction
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int* dstat = nullptr;
+  float* hbuf = nullptr;  // pinned host scratch (bcap floats)
+};
+
+namespace t2s2 {
+
+namespace {
+
+constexpr int kLossThreads = 256;
+constexpr int kMlpMaxRank = 16;
+constexpr int kMlpMaxTargetRank = 32;
+constexpr int kMlpMaxM = 64;
+
+struct LossArgs {
+  const float* y;        // batch x odim
+  const float* targets;  // batch x d x ru x mmax x ru (zero padded)
+  const float* uu;       // batch: <U,U>
+  float* dy;             // batch x odim: dL/dy, already divided by the batch size
+  float* loss;           // batch
+  int batch, odim, d, r, ru, mmax;
+  int m[T2S2_MAX_D];
+  int off[T2S2_MAX_D + 1];
+  float inv_batch;
+};
+
+size_t loss_smem_floats(const LossArgs& a) {
+  const size_t env = (size_t)(a.d + 1) * (2 * a.r * a.r + 2 * a.r * a.ru);
+  const size_t W = (size_t)std::max(a.r, a.ru) * a.mmax * a.r;
+  const size_t G = (size_t)a.r * a.mmax * a.r;
+  return (size_t)a.odim + env + W + G;
+}
+
+// One CTA per sample.  Every core of X is treated as r x m_k x r with zeros
+// outside its true shape (the boundary cores have one row / column), and every
+// target core as ru x m_k x ru (zero padded), so the same contraction loops
+// serve all cores; the zeros leave every inner product unchanged.
+__global__ void __launch_bounds__(kLossThreads) tt_loss_grad_kernel(LossArgs a) {
+  extern __shared__ float sm[];
+  const int s = blockIdx.x, tid = threadIdx.x;
+  const int d = a.d, r = a.r, ru = a.ru, mmax = a.mmax;
+  float* sX = sm;
+  float* Lxx = sX + a.odim;
+  float* Rxx = Lxx + (d + 1) * r * r;
+  float* Lxu = Rxx + (d + 1) * r * r;
+  float* Rxu = Lxu + (d + 1) * r * ru;
+  float* W = Rxu + (d + 1) * r * ru;
+  float* G = W + max(r, ru) * mmax * r;
+  const float* U = a.targets + (size_t)s * d * ru * mmax * ru;
+  for (int e = tid; e < a.odim; e += kLossThreads) sX[e] = a.y[(size_t)s * a.odim + e];
+  for (int e = tid; e < (d + 1) * r * r; e += kLossThreads) Lxx[e] = Rxx[e] = 0.f;
+  for (int e = tid; e < (d + 1) * r * ru; e += kLossThreads) Lxu[e] = Rxu[e] = 0.f;
+  __syncthreads();
+  if (tid == 0) {
+    Lxx[0] = 1.f;
+    Lxu[0] = 1.f;
+    Rxx[d * r * r] = 1.f;
+    Rxu[d * r * ru] = 1.f;
+  }
+  __syncthreads();
+  auto X = [&](int k, int aa, int i, int b) -> float {
+    const int ra = (k == 0) ? 1 : r, rb = (k == d - 1) ? 1 : r;
+    return (aa < ra && b < rb) ? sX[a.off[k] + (aa * a.m[k] + i) * rb + b] : 0.f;
+  };
+  auto Ut = [&](int k, int c, int i, int c2) -> float {
+    return U[(((size_t)k * ru + c) * mmax + i) * ru + c2];
+  };
+  // left environments
+  for (int k = 0; k < d; ++k) {
+    const int mk = a.m[k];
+    const float* L = Lxx + k * r * r;
+    // W[a2, i, b] = sum_a L[a, a2] X[a, i, b]
+    for (int e = tid; e < r * mk * r; e += kLossThreads) {
+      const int a2 = e / (mk * r), rem = e % (mk * r), i = rem / r, b = rem % r;
+      float acc = 0.f;
+      for (int aa = 0; aa < r; ++aa) acc = fmaf(L[aa * r + a2], X(k, aa, i, b), acc);
+      W[e] = acc;
+    }
+    __syncthreads();
+    // Lxx[k+1][b, b2] = sum_{a2, i} W[a2, i, b] X[a2, i, b2]
+    for (int e = tid; e < r * r; e += kLossThreads) {
+      const int b = e / r, b2 = e % r;
+      float acc = 0.f;
+      for (int a2 = 0; a2 < r; ++a2)
+        for (int i = 0; i < mk; ++i) acc = fmaf(W[(a2 * mk + i) * r + b], X(k, a2, i, b2), acc);
+      Lxx[(k + 1) * r * r + e] = acc;
+    }
+    __syncthreads();
+    const float* F = Lxu + k * r * ru;
+    // W[c, i, b] = sum_a F[a, c] X[a, i, b]
+    for (int e = tid; e < ru * mk * r; e += kLossThreads) {
+      const int c = e / (mk * r), rem = e % (mk * r), i = rem / r, b = rem % r;
+      float acc = 0.f;
+      for (int aa = 0; aa < r; ++aa) acc = fmaf(F[aa * ru + c], X(k, aa, i, b), acc);
+      W[e] = acc;
+    }
+    __syncthreads();
+    // Lxu[k+1][b, c2] = sum_{c, i} W[c, i, b] U[c, i, c2]
+    for (int e = tid; e < r * ru; e += kLossThreads) {
+      const int b = e / ru, c2 = e % ru;
+      float acc = 0.f;
+      for (int c = 0; c < ru; ++c)
+        for (int i = 0; i < mk; ++i) acc = fmaf(W[(c * mk + i) * r + b], Ut(k, c, i, c2), acc);
+      Lxu[(k + 1) * r * ru + e] = acc;
+    }
+    __syncthreads();
+  }
+  // right environments
+  for (int k = d - 1; k >= 1; --k) {
+    const int mk = a.m[k];
+    const float* Rn = Rxx + (k + 1) * r * r;
+    // W[a2, i, b] = sum_b2 X[a2, i, b2] Rn[b, b2]
+    for (int e = tid; e < r * mk * r; e += kLossThreads) {
+      const int a2 = e / (mk * r), rem = e % (mk * r), i = rem / r, b = rem % r;
+      float acc = 0.f;
+      for (int b2 = 0; b2 < r; ++b2) acc = fmaf(X(k, a2, i, b2), Rn[b * r + b2], acc);
+      W[e] = acc;
+    }
+    __syncthreads();
+    // Rxx[k][aa, a2] = sum_{i, b} X[aa, i, b] W[a2, i, b]
+    for (int e = tid; e < r * r; e += kLossThreads) {
+      const int aa = e / r, a2 = e % r;
+      float acc = 0.f;
+      for (int i = 0; i < mk; ++i)
+        for (int b = 0; b < r; ++b) acc = fmaf(X(k, aa, i, b), W[(a2 * mk + i) * r + b], acc);
+      Rxx[k * r * r + e] = acc;
+    }
+    __syncthreads();
+    const float* Fn = Rxu + (k + 1) * r * ru;
+    // W[c, i, b] = sum_c2 U[c, i, c2] Fn[b, c2]
+    for (int e = tid; e < ru * mk * r; e += kLossThreads) {
+      const int c = e / (mk * r), rem = e % (mk * r), i = rem / r, b = rem % r;
+      float acc = 0.f;
+      for (int c2 = 0; c2 < ru; ++c2) acc = fmaf(Ut(k, c, i, c2), Fn[b * ru + c2], acc);
+      W[e] = acc;
+    }
+    __syncthreads();
+    // Rxu[k][aa, c] = sum_{i, b} X[aa, i, b] W[c, i, b]
+    for (int e = tid; e < r * ru; e += kLossThreads) {
+      const int aa = e / ru, c = e % ru;
+      float acc = 0.f;
+      for (int i = 0; i < mk; ++i)
+        for (int b = 0; b < r; ++b) acc = fmaf(X(k, aa, i, b), W[(c * mk + i) * r + b], acc);
+      Rxu[k * r * ru + e] = acc;
+    }
+    __syncthreads();
+  }
+  const float xx = Lxx[d * r * r], xu = Lxu[d * r * ru], uu = a.uu[s];
+  if (tid == 0) a.loss[s] = (xx - 2.f * xu + uu) / uu;
+  const float scale = a.inv_batch / uu;
+  // gradient, core by core
+  for (int k = 0; k < d; ++k) {
+    const int mk = a.m[k];
+    const float* L = Lxx + k * r * r;
+    const float* Rn = Rxx + (k + 1) * r * r;
+    // W[a2, i, b] = sum_b2 X[a2, i, b2] Rn[b, b2];  G[a, i, b] = 2 sum_a2 L[a, a2] W[a2, i, b]
+    for (int e = tid; e < r * mk * r; e += kLossThreads) {
+      const int a2 = e / (mk * r), rem = e % (mk * r), i = rem / r, b = rem % r;
+      float acc = 0.f;
+      for (int b2 = 0; b2 < r; ++b2) acc = fmaf(X(k, a2, i, b2), Rn[b * r + b2], acc);
+      W[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < r * mk * r; e += kLossThreads) {
+      const int aa = e / (mk * r), rem = e % (mk * r);
+      float acc = 0.f;
+      for (int a2 = 0; a2 < r; ++a2) acc = fmaf(L[aa * r + a2], W[a2 * mk * r + rem], acc);
+      G[e] = 2.f * acc;
+    }
+    __syncthreads();
+    const float* F = Lxu + k * r * ru;
+    const float* Fn = Rxu + (k + 1) * r * ru;
+    // W[c, i, b] = sum_c2 U[c, i, c2] Fn[b, c2];  G[a, i, b] -= 2 sum_c F[a, c] W[c, i, b]
+    for (int e = tid; e < ru * mk * r; e += kLossThreads) {
+      const int c = e / (mk * r), rem = e % (mk * r), i = rem / r, b = rem % r;
+      float acc = 0.f;
+      for (int c2 = 0; c2 < ru; ++c2) acc = fmaf(Ut(k, c, i, c2), Fn[b * ru + c2], acc);
+      W[e] = acc;
+    }
+    __syncthreads();
+    const int ra = (k == 0) ? 1 : r, rb = (k == d - 1) ? 1 : r;
+    for (int e = tid; e < r * mk * r; e += kLossThreads) {
+      const int aa = e / (mk * r), rem = e % (mk * r), i = rem / r, b = rem % r;
+      float acc = 0.f;
+      for (int c = 0; c < ru; ++c) acc = fmaf(F[aa * ru + c], W[c * mk * r + rem], acc);
+      if (aa < ra && b < rb)
+        a.dy[(size_t)s * a.odim + a.off[k] + (aa * mk + i) * rb + b] = (G[e] - 2.f * acc) * scale;
+    }
+    __syncthreads();
+  }
+}
+
+// z += bias (per column); h = relu(z) if h != nullptr.
+__global__ void bias_act_kernel(float* z, float* h, const float* bias, int rows, int cols) {
+  const long n = (long)rows * cols;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const float v = z[e] + bias[e % cols];
+    z[e] = v;
+    if (h) h[e] = v > 0.f ? v : 0.f;
+  }
+}
+
+// dz = dh * (z > 0)
+__global__ void relu_back_kernel(float* dz, const float* dh, const float* z, long n) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    dz[e] = z[e] > 0.f ? dh[e] : 0.f;
+}
+
+// out[j] = sum_i v[i][j] (rows summed in order: deterministic)
+__global__ void colsum_kernel(float* out, const float* v, int rows, int cols) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cols; j += gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int i = 0; i < rows; ++i) acc += v[(long)i * cols + j];
+    out[j] = acc;
+  }
+}
+
+// Adam with bias correction (Kingma & Ba): bc1 = 1 - beta1^t, bc2 = 1 - beta2^t.
+__global__ void adam_kernel(float* p, const float* g, float* mo, float* ve, long n, float lr, float beta1,
+                            float beta2, float eps, float bc1, float bc2) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const float gg = g[e];
+    const float m1 = beta1 * mo[e] + (1.f - beta1) * gg;
+    const float v1 = beta2 * ve[e] + (1.f - beta2) * gg * gg;
+    mo[e] = m1;
+    ve[e] = v1;
+    p[e] -= lr * (m1 / bc1) / (sqrtf(v1 / bc2) + eps);
+  }
+}
+
+// Packs one FP64 target TT into the zero-padded FP32 slot (d x ru x mmax x ru).
+__global__ void pack_core_kernel(float* slot, const double* core, int ra, int m, int rb, int ru, int mmax) {
+  const long n = (long)ru * mmax * ru;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / ((long)mmax * ru)), rem = (int)(e % ((long)mmax * ru)), i = rem / ru, c2 = rem % ru;
+    slot[e] = (c < ra && i < m && c2 < rb) ? (float)core[((long)c * m + i) * rb + c2] : 0.f;
+  }
+}
+
+// TT cores of y (one sample) to FP64 cores.
+__global__ void unpack_core_kernel(double* core, const float* y, long n) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    core[e] = (double)y[e];
+}
+
+int ew_blocks(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, 8L * kNumSMs)); }
+
+t2s2_status mm(t2s2_mlp net, int M, int N, int K, bool tA, bool tB, const float* A, long lda, const float* B,
+               long ldb, float* C, long ldc, cudaStream_t st) {
+  Gemm<float> g;
+  g.M = M; g.N = N; g.K = K; g.tA = tA; g.tB = tB; g.alpha = 1.f; g.beta = 0.f;
+  g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc; g.batch = 1;
+  const size_t need = gemm_tc_workspace_bytes(g, T2S2_BF16_REFINE);
+  if (need > net->ws_bytes) {
+    T2S2_CUDA_TRY(cudaStreamSynchronize(st));  // earlier launches may still read the old buffer
+    if (net->ws) cudaFree(net->ws);
+    net->ws = nullptr;
+    net->ws_bytes = 0;
+    T2S2_CUDA_TRY(cudaMalloc(&net->ws, need));
+    net->ws_bytes = need;
+  }
+  return gemm_tc(g, T2S2_BF16_REFINE, net->ws, net->ws_bytes, net->dstat, st);
+}
+
+t2s2_status ensure_batch(t2s2_mlp net, int batch) {
+  if (batch <= net->bcap) return T2S2_OK;
+  float** bufs[] = {&net->z1, &net->h1, &net->z2, &net->h2, &net->dh, &net->dz, &net->y, &net->dy, &net->loss};
+  for (auto b : bufs)
+    if (*b) cudaFree(*b), *b = nullptr;
+  if (net->hbuf) cudaFreeHost(net->hbuf), net->hbuf = nullptr;
+  const size_t H = (size_t)batch * net->hidden, Y = (size_t)batch * net->odim;
+  const size_t sizes[] = {H, H, H, H, H, H, Y, Y, (size_t)batch};
+  for (int i = 0; i < 9; ++i) T2S2_CUDA_TRY(cudaMalloc(bufs[i], sizes[i] * sizeof(float)));
+  T2S2_CUDA_TRY(cudaMallocHost(&net->hbuf, (size_t)batch * sizeof(float)));
+  net->bcap = batch;
+  return T2S2_OK;
+}
+
+t2s2_status forward(t2s2_mlp net, const float* P, int B, cudaStream_t st) {
+  const int h = net->hidden;
+  float* w = net->params;
+  T2S2_TRY(mm(net, B, h, net->in_dim, false, true, P, net->in_dim, w + net->oW1, net->in_dim, net->z1, h, st));
+  {
+    TraceScope ts(kTrMlp, st, 2.0 * B * h, 8.0 * B * h);
+    bias_act_kernel<<<ew_blocks((long)B * h), 256, 0, st>>>(net->z1, net->h1, w + net->ob1, B, h);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  T2S2_TRY(mm(net, B, h, h, false, true, net->h1, h, w + net->oW2, h, net->z2, h, st));
+  {
+    TraceScope ts(kTrMlp, st, 2.0 * B * h, 8.0 * B * h);
+    bias_act_kernel<<<ew_blocks((long)B * h), 256, 0, st>>>(net->z2, net->h2, w + net->ob2, B, h);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  T2S2_TRY(mm(net, B, net->odim, h, false, true, net->h2, h, w + net->oW3, h, net->y, net->odim, st));
+  {
+    TraceScope ts(kTrMlp, st, 1.0 * B * net->odim, 8.0 * B * net->odim);
+    bias_act_kernel<<<ew_blocks((long)B * net->odim), 256, 0, st>>>(net->y, nullptr, w + net->ob3, B, net->odim);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  return T2S2_OK;
+}
+
+t2s2_status loss_grad(t2s2_mlp net, const float* P, int B, const float* targets, const float* uu, cudaStream_t st) {
+  T2S2_TRY(forward(net, P, B, st));
+  LossArgs a;
+  a.y = net->y;
+  a.targets = targets;
+  a.uu = uu;
+  a.dy = net->dy;
+  a.loss = net->loss;
+  a.batch = B;
+  a.odim = net->odim;
+  a.d = net->d;
+  a.r = net->r;
+  a.ru = net->ru;
+  a.mmax = net->mmax;
+  for (int k = 0; k < net->d; ++k) a.m[k] = net->m[k];
+  for (int k = 0; k <= net->d; ++k) a.off[k] = net->off[k];
+  a.inv_batch = 1.f / (float)B;
+  const size_t smem = loss_smem_floats(a) * sizeof(float);
+  {
+    double fl = 0.0;
+    for (int k = 0; k < net->d; ++k) {
+      const double mk = net->m[k], r = net->r, ru = net->ru;
+      fl += 2.0 * (2 * r * mk * r * r + 2 * ru * mk * r * r + 2 * ru * mk * r * ru) * 1.5;
+    }
+    TraceScope ts(kTrMlp, st, fl * B, 4.0 * B * ((double)net->odim * 2 + (double)net->d * net->ru * net->mmax * net->ru));
+    T2S2_CUDA_TRY(cudaFuncSetAttribute(tt_loss_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tt_loss_grad_kernel<<<B, kLossThreads, smem, st>>>(a);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  // backward through the layers
+  const int h = net->hidden, od = net->odim;
+  float* w = net->params;
+  float* g = net->grads;
+  T2S2_TRY(mm(net, od, h, B, true, false, net->dy, od, net->h2, h, g + net->oW3, h, st));  // dW3 = dy^T h2
+  {
+    TraceScope ts(kTrMlp, st, 1.0 * B * od, 4.0 * B * od);
+    colsum_kernel<<<ew_blocks(od), 256, 0, st>>>(g + net->ob3, net->dy, B, od);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  T2S2_TRY(mm(net, B, h, od, false, false, net->dy, od, w + net->oW3, h, net->dh, h, st));  // dh2 = dy W3
+  {
+    TraceScope ts(kTrMlp, st, 2.0 * B * h, 12.0 * B * h);
+    relu_back_kernel<<<ew_blocks((long)B * h), 256, 0, st>>>(net->dz, net->dh, net->z2, (long)B * h);
+    colsum_kernel<<<ew_blocks(h), 256, 0, st>>>(g + net->ob2, net->dz, B, h);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  T2S2_TRY(mm(net, h, h, B, true, false, net->dz, h, net->h1, h, g + net->oW2, h, st));  // dW2 = dz2^T h1
+  T2S2_TRY(mm(net, B, h, h, false, false, net->dz, h, w + net->oW2, h, net->dh, h, st));  // dh1 = dz2 W2
+  {
+    TraceScope ts(kTrMlp, st, 2.0 * B * h, 12.0 * B * h);
+    relu_back_kernel<<<ew_blocks((long)B * h), 256, 0, st>>>(net->dz, net->dh, net->z1, (long)B * h);
+    colsum_kernel<<<ew_blocks(h), 256, 0, st>>>(g + net->ob1, net->dz, B, h);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  T2S2_TRY(mm(net, h, net->in_dim, B, true, false, net->dz, h, P, net->in_dim, g + net->oW1, net->in_dim, st));
+  return T2S2_OK;
+}
+
+t2s2_status check_status(t2s2_mlp net, cudaStream_t st) {
+  int h = 0;
+  T2S2_CUDA_TRY(cudaMemcpyAsync(&h, net->dstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(st));
+  return h ? T2S2_ETIMEOUT : T2S2_OK;
+}
+
+t2s2_status mean_loss(t2s2_mlp net, int B, float* out, cudaStream_t st) {
+  T2S2_CUDA_TRY(cudaMemcpyAsync(net->hbuf, net->loss, sizeof(float) * B, cudaMemcpyDeviceToHost, st));
+  T2S2_TRY(check_status(net, st));
+  double s = 0.0;
+  for (int i = 0; i < B; ++i) s += net->hbuf[i];
+  *out = (float)(s / B);
+  return T2S2_OK;
+}
+
+}  // namespace
+}  // namespace t2s2
+
+using namespace t2s2;
+
+extern "C" {
+
+t2s2_status t2s2_mlp_create(int in_dim, int hidden, int d, const int* m, int r, int ru, unsigned long long seed,
+                            t2s2_mlp* out) {
+  if (!out || !m || in_dim < 1 || hidden < 1 || d < 2 || d > T2S2_MAX_D) return T2S2_EINVAL;
+  if (r < 1 || r > kMlpMaxRank || ru < 1 || ru > kMlpMaxTargetRank) return T2S2_EINVAL;
+  *out = nullptr;
+  t2s2_mlp net = new t2s2_mlp_s;
+  cudaGetDevice(&net->device);
+  net->in_dim = in_dim;
+  net->hidden = hidden;
+  net->d = d;
+  net->r = r;
+  net->ru = ru;
+  int o = 0;
+  for (int k = 0; k < d; ++k) {
+    if (m[k] < 1 || m[k] > kMlpMaxM) {
+      delete net;
+      return T2S2_EINVAL;
+    }
+    net->m[k] = m[k];
+    net->mmax = std::max(net->mmax, m[k]);
+    net->off[k] = o;
+    o += (k == 0 ? 1 : r) * m[k] * (k == d - 1 ? 1 : r);
+  }
+  net->off[d] = o;
+  net->odim = o;
+  {
+    LossArgs a{};
+    a.odim = o; a.d = d; a.r = r; a.ru = ru; a.mmax = net->mmax;
+    if (loss_smem_floats(a) * sizeof(float) > 200 * 1024) {
+      delete net;
+      return T2S2_EINVAL;
+    }
+  }
+  const long long h = hidden;
+  net->oW1 = 0;
+  net->ob1 = h * in_dim;
+  net->oW2 = net->ob1 + h;
+  net->ob2 = net->oW2 + h * h;
+  net->oW3 = net->ob2 + h;
+  net->ob3 = net->oW3 + (long long)o * h;
+  net->nparams = net->ob3 + o;
+  // He-normal weights (std sqrt(2 / fan_in); sqrt(1 / fan_in) for the linear
+  // output layer), zero biases, from a seeded host generator
+  std::vector<float> p(net->nparams, 0.f);
+  std::mt19937_64 gen(seed);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  for (long long i = 0; i < h * in_dim; ++i) p[net->oW1 + i] = (float)(nd(gen) * std::sqrt(2.0 / in_dim));
+  for (long long i = 0; i < h * h; ++i) p[net->oW2 + i] = (float)(nd(gen) * std::sqrt(2.0 / h));
+  for (long long i = 0; i < (long long)o * h; ++i) p[net->oW3 + i] = (float)(nd(gen) * std::sqrt(1.0 / h));
+  const size_t bytes = sizeof(float) * net->nparams;
+  cudaError_t e = cudaMalloc(&net->params, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&net->grads, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&net->adam_m, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&net->adam_v, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&net->dstat, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&net->pbuf, sizeof(float) * in_dim);
+  if (e == cudaSuccess) e = cudaMemcpy(net->params, p.data(), bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(net->grads, 0, bytes);
+  if (e == cudaSuccess) e = cudaMemset(net->adam_m, 0, bytes);
+  if (e == cudaSuccess) e = cudaMemset(net->adam_v, 0, bytes);
+  if (e == cudaSuccess) e = cudaMemset(net->dstat, 0, sizeof(int) * 4);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "t2s2_mlp_create", __FILE__, __LINE__);
+    t2s2_mlp_destroy(net);
+    return e == cudaErrorMemoryAllocation ? T2S2_ENOMEM : T2S2_ECUDA;
+  }
+  *out = net;
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_mlp_destroy(t2s2_mlp net) {
+  if (!net) return T2S2_OK;
+  void* bufs[] = {net->params, net->grads, net->adam_m, net->adam_v, net->z1, net->h1, net->z2, net->h2,
+                  net->y,      net->dy,    net->dh,     net->dz,     net->loss, net->ws, net->dstat,
+                  net->pbuf};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (net->hbuf) cudaFreeHost(net->hbuf);
+  delete net;
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_mlp_info(t2s2_mlp net, long long* nparams, int* out_dim) {
+  if (!net) return T2S2_EINVAL;
+  if (nparams) *nparams = net->nparams;
+  if (out_dim) *out_dim = net->odim;
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_mlp_get_params(t2s2_mlp net, float* params, float* grads, void* stream) {
+  if (!net) return T2S2_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = sizeof(float) * net->nparams;
+  if (params) T2S2_CUDA_TRY(cudaMemcpyAsync(params, net->params, bytes, cudaMemcpyDefault, st));
+  if (grads) T2S2_CUDA_TRY(cudaMemcpyAsync(grads, net->grads, bytes, cudaMemcpyDefault, st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(st));
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_mlp_set_params(t2s2_mlp net, const float* params, void* stream) {
+  if (!net || !params) return T2S2_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  T2S2_CUDA_TRY(cudaMemcpyAsync(net->params, params, sizeof(float) * net->nparams, cudaMemcpyDefault, st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(st));
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_mlp_pack_target(t2s2_mlp net, t2s2_op op, const t2s2_tt* u, float* slot, float* uu,
+                                 void* stream) {
+  if (!net || !op || !u || !slot || !uu || u->d != net->d || u->loc != T2S2_DEVICE) return T2S2_EINVAL;
+  T2S2_TRY(check_tt(op, u));
+  for (int k = 0; k < net->d; ++k) {
+    if (u->m[k] != net->m[k]) return T2S2_EINVAL;
+    if (u->r[k + 1] > net->ru) return T2S2_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long per = (long)net->ru * net->mmax * net->ru;
+  for (int k = 0; k < net->d; ++k) {
+    pack_core_kernel<<<ew_blocks(per), 256, 0, st>>>(slot + k * per, static_cast<const double*>(u->cores[k]),
+                                                     u->r[k], u->m[k], u->r[k + 1], net->ru, net->mmax);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  double nrm = 0.0;
+  T2S2_TRY(t2s2_norm(op, u, &nrm, stream));
+  const float v = (float)(nrm * nrm);
+  T2S2_CUDA_TRY(cudaMemcpyAsync(uu, &v, sizeof(float), cudaMemcpyHostToDevice, st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(st));
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_mlp_loss_grad(t2s2_mlp net, const float* P, int batch, const float* targets, const float* uu,
+                               float* loss, void* stream) {
+  if (!net || !P || !targets || !uu || batch < 1) return T2S2_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  T2S2_TRY(ensure_batch(net, batch));
+  T2S2_CUDA_TRY(cudaMemsetAsync(net->dstat, 0, sizeof(int), st));
+  T2S2_TRY(loss_grad(net, P, batch, targets, uu, st));
+  float l = 0.f;
+  T2S2_TRY(mean_loss(net, batch, &l, st));
+  if (loss) *loss = l;
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_mlp_train_step(t2s2_mlp net, const float* P, int batch, const float* targets, const float* uu,
+                                float lr, float* loss, void* stream) {
+  if (!net || !P || !targets || !uu || batch < 1 || !(lr > 0.f)) return T2S2_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  T2S2_TRY(ensure_batch(net, batch));
+  T2S2_CUDA_TRY(cudaMemsetAsync(net->dstat, 0, sizeof(int), st));
+  T2S2_TRY(loss_grad(net, P, batch, targets, uu, st));
+  net->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float bc1 = 1.f - (float)std::pow(0.9, (double)net->step);
+  const float bc2 = 1.f - (float)std::pow(0.999, (double)net->step);
+  {
+    TraceScope ts(kTrMlp, st, 10.0 * net->nparams, 4.0 * 7 * net->nparams);
+    adam_kernel<<<ew_blocks(net->nparams), 256, 0, st>>>(net->params, net->grads, net->adam_m, net->adam_v,
+                                                       net->nparams, lr, b1, b2, 1e-8f, bc1, bc2);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  if (loss) {
+    float l = 0.f;
+    T2S2_TRY(mean_loss(net, batch, &l, st));
+    *loss = l;
+  }
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_mlp_predict(t2s2_mlp net, const float* p, t2s2_tt* x, void* stream) {
+  if (!net || !p || !x || x->d != net->d || !x->r || !x->cores || !x->cap) return T2S2_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  T2S2_TRY(ensure_batch(net, 1));
+  float* dp = net->pbuf;
+  T2S2_CUDA_TRY(cudaMemcpyAsync(dp, p, sizeof(float) * net->in_dim, cudaMemcpyDefault, st));
+  T2S2_CUDA_TRY(cudaMemsetAsync(net->dstat, 0, sizeof(int), st));
+  T2S2_TRY(forward(net, dp, 1, st));
+  for (int k = 0; k < net->d; ++k) {
+    const int ra = k == 0 ? 1 : net->r, rb = k == net->d - 1 ? 1 : net->r;
+    const long n = (long)ra * net->m[k] * rb;
+    if ((size_t)n > x->cap[k] || (x->m && x->m[k] != net->m[k])) return T2S2_EINVAL;
+    if (x->loc == T2S2_DEVICE) {
+      unpack_core_kernel<<<ew_blocks(n), 256, 0, st>>>(static_cast<double*>(x->cores[k]), net->y + net->off[k], n);
+      T2S2_CUDA_TRY(cudaGetLastError());
+    } else {
+      std::vector<float> hv(n);
+      T2S2_CUDA_TRY(cudaMemcpyAsync(hv.data(), net->y + net->off[k], sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+      T2S2_CUDA_TRY(cudaStreamSynchronize(st));
+      double* dst = static_cast<double*>(x->cores[k]);
+      for (long i = 0; i < n; ++i) dst[i] = hv[i];
+    }
+  }
+  x->r[0] = 1;
+  for (int k = 1; k < net->d; ++k) x->r[k] = net->r;
+  x->r[net->d] = 1;
+  return check_status(net, st);
+}
+
+}  // extern "C"

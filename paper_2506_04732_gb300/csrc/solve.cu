@@ -202,9 +202,14 @@ struct Amen {
       T2S2_TRY(dev_axpy(c, Bp[k], op->dI[k], (size_t)m * m, c_mass / d));
     }
     // transformed right-hand side f = M^{-1} b (mode-k products with Rt_k^{-1})
+    // (always FP64: the right-hand side fixes what the inner solve converges to)
     T2S2_TRY(tt_alloc(c, f, d, op->m, b.r, 0));
-    for (int k = 0; k < d; ++k)
-      T2S2_TRY(mode2(c, op->dRinv[k], op->m[k], b.c[k], b.r[k], b.r[k + 1], f.c[k]));
+    {
+      Ctx c64 = c;
+      c64.contract_prec = T2S2_FP64;
+      for (int k = 0; k < d; ++k)
+        T2S2_TRY(mode2(c64, op->dRinv[k], op->m[k], b.c[k], b.r[k], b.r[k + 1], f.c[k]));
+    }
     // x: copy of the initial guess with capacity rcap
     int rx[T2S2_MAX_D + 1];
     for (int k = 0; k <= d; ++k) rx[k] = x0.r[k];
@@ -403,6 +408,12 @@ struct Amen {
     P.mr = gm_restart;
     P.iters_out = gm_iters;
     P.res_out = gm_res;
+    P.fls = use_fls ? 1 : 0;
+    P.team = op->team;
+    P.eigL = eig_buf;
+    P.eigR = eig_buf + (size_t)R + 2 * (size_t)R * R;
+    P.eig_status = eig_status;
+    P.ybuf = ybuf;
     T2S2_TRY(local_gmres<float>(P, c.st));
     return dev_f2d(c, X, fx, N);
   }
@@ -522,7 +533,10 @@ struct Amen {
         T2S2_TRY(gemm_ex<double>(c, rn, rk, rows, true, false, 1.0, Q, rn, U, rk, 0.0, C, rk));
         T2S2_TRY(gemm_ex<double>(c, rn, rb, rk, false, false, 1.0, C, rk, SV, rb, 0.0, CS, rb));
         if ((size_t)rn * mn * rnn > x.cap[k + 1] || (size_t)ra * m * rn > x.cap[k]) return T2S2_ENOMEM;
-        T2S2_TRY(mode1(c, CS, rn, rb, x.c[k + 1], mn, rnn, P));
+        // the iterate itself is carried in FP64 whatever the contraction arithmetic
+        Ctx c64 = c;
+        c64.contract_prec = T2S2_FP64;
+        T2S2_TRY(mode1(c64, CS, rn, rb, x.c[k + 1], mn, rnn, P));
         T2S2_TRY(d2d(c, x.c[k + 1], P, (size_t)rn * mn * rnn));
         T2S2_TRY(d2d(c, x.c[k], Q, (size_t)rows * rn));
         x.r[k + 1] = rn;
@@ -552,9 +566,12 @@ struct Amen {
   }
 };
 
+t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c_mass, double c_op,
+                        double tol, int rmax, int max_sweeps, t2s2_precision prec, t2s2_solve_info* info);
+
 t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c_mass, double c_op,
                        double tol, int rmax, int max_sweeps, t2s2_precision prec, t2s2_solve_info* info) {
-  (void)prec;
+  if (prec != T2S2_FP64) return refine_impl(op, cx, b, xio, c_mass, c_op, tol, rmax, max_sweeps, prec, info);
   Amen am;
   PhaseTimer pt;
   pt.start(cx.st);
@@ -612,6 +629,206 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
   return res <= tol ? T2S2_OK : T2S2_ENOCONV;
 }
 
+// Mixed precision with iterative refinement.  The outer loop is FP64:
+//     r = b - (c_mass M + c_op A) x                (FP64 apply and TT sum),
+//     r <- rndg(r) at a tenth of the inner tolerance,
+//     delta ~ (c_mass M + c_op A)^{-1} r           (inner AMEn, loose tolerance),
+//     x <- rndg(x + delta) at tol / 10, rank cap rmax,
+// until the FP64 residual ||b - A x|| / ||b|| <= tol.  The inner AMEn runs
+// its local solves in binary32 and, for TF32 / BF16, its core contractions
+// (mode products and interface updates) on the tensor cores; its QR / SVD,
+// the residual and every rounding stay FP64.
+//
+// The contraction arithmetic puts a floor under what one inner solve can
+// reach (about 2u: near 1e-3 for TF32, 1e-2 for BF16), so the inner target is
+// set above it per precision, and an inner solve that stops improving ends
+// early.  A correction computed with rounded contractions also carries
+// rounding noise of relative size ~u ||delta||, spread over many TT ranks;
+// once ||delta|| is small that noise can no longer be represented under the
+// rank cap and refinement stalls (near 5e-6 for TF32 on the d = 6, n = 32
+// problem).  So the tensor-core contractions serve a first stage only: an
+// inner solve of the whole system down to their floor, whose result is not
+// added to x but becomes the initial guess of the next inner solve of the
+// whole system, with FP64 contractions and binary32 local solves (the
+// alternating sweeps re-solve every core and so discard the noise); then the
+// corrections proceed as usual.  When the caller's x0 is worse than zero
+// (residual above 1) the loop starts from x = 0, so that the first inner
+// solve is the original system and takes x0 as its initial guess (a warm
+// start acts there); each later correction starts from the previous one,
+// whose ranks already fit the error's.
+double inner_tol_for(t2s2_precision prec) {
+  switch (prec) {
+    case T2S2_BF16_REFINE: return 3e-2;
+    case T2S2_TF32_REFINE: return 3e-3;
+    default: return 1e-4;
+  }
+}
+
+t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c_mass, double c_op,
+                        double tol, int rmax, int max_sweeps, t2s2_precision prec, t2s2_solve_info* info) {
+  const double kInnerTol = inner_tol_for(prec);
+  constexpr int kMaxRefinements = 40;
+  const int d = op->d;
+  const int kick = 4, rcap = rmax + kick;
+  const char* ev = std::getenv("T2S2_VERBOSE");
+  const bool verbose = ev && ev[0] == '1';
+  // persistent state: the iterate x, the caller's guess g and the previous
+  // correction dprev (capacity rcap each)
+  DevTT x, g, ones, dprev;
+  int rx[T2S2_MAX_D + 1];
+  for (int k = 0; k <= d; ++k) rx[k] = std::min(xio.r[k], rcap);
+  rx[0] = rx[d] = 1;
+  T2S2_TRY(tt_alloc(cx, x, d, op->m, rx, rcap));
+  T2S2_TRY(tt_alloc(cx, g, d, op->m, rx, rcap));
+  {
+    int r1[T2S2_MAX_D + 1];
+    for (int k = 0; k <= d; ++k) r1[k] = 1;
+    T2S2_TRY(tt_alloc(cx, ones, d, op->m, r1, 1));
+    for (int k = 0; k < d; ++k) T2S2_TRY(dev_fill(cx, ones.c[k], op->m[k], 1.0));
+    T2S2_TRY(tt_alloc(cx, dprev, d, op->m, r1, rcap));
+    T2S2_TRY(tt_copy(cx, ones, dprev));
+  }
+  {
+    const size_t mk = cx.ar->mark();
+    DevTT t;
+    T2S2_TRY(tt_alloc(cx, t, d, op->m, xio.r, 0));
+    T2S2_TRY(tt_copy(cx, xio, t));
+    T2S2_TRY(tt_round(cx, t, 0.0, rcap));
+    for (int k = 0; k <= d; ++k) x.r[k] = g.r[k] = t.r[k];
+    T2S2_TRY(tt_copy(cx, t, x));
+    T2S2_TRY(tt_copy(cx, t, g));
+    cx.ar->release(mk);
+  }
+  double bnorm = -1.0, res = 0.0;
+  T2S2_TRY(residual_impl(op, cx, b, x, c_mass, c_op, false, &res, &bnorm));
+  bool x_zero = false;
+  if (res >= 1.0) {  // x0 is worse than x = 0
+    x_zero = true;
+    res = 1.0;
+  }
+  if (verbose)
+    fprintf(stderr, "[t2s2] refine d=%d prec=%d tol=%g initial residual %.3e%s\n", d, (int)prec, tol, res,
+            x_zero ? " (starting from x = 0)" : "");
+  const bool tc = prec == T2S2_BF16_REFINE || prec == T2S2_TF32_REFINE;
+  if (tc) T2S2_CUDA_TRY(cudaMemsetAsync(cx.dstat + kStatTensorCore, 0, sizeof(int), cx.st));
+  bool tc_stage = tc;  // the tensor-core stage: a guess for the whole system
+  if (tc_stage && !x_zero) {
+    // start that stage from the caller's iterate: solve the whole system
+    x_zero = true;
+    res = 1.0;
+  }
+  int sweeps = 0, refinements = 0, stall = 0;
+  long long local_iters = 0;
+  while (res > tol && sweeps < max_sweeps && refinements < kMaxRefinements) {
+    const size_t mk = cx.ar->mark();
+    const double tin = std::max(kInnerTol, 0.5 * tol / res);
+    // r = b - A x in FP64, rounded (r = b while x = 0)
+    DevTT r;
+    const DevTT* rhs = &b;
+    if (!x_zero) {
+      DevTT y;
+      int r2[T2S2_MAX_D + 1];
+      for (int k = 0; k <= d; ++k) r2[k] = (k == 0 || k == d) ? 1 : 2 * x.r[k];
+      T2S2_TRY(tt_alloc(cx, y, d, op->m, r2, 0));
+      T2S2_TRY(apply_op(op, cx, x, y, c_mass, c_op, false));
+      T2S2_TRY(tt_axpby(cx, 1.0, b, -1.0, y, r));
+      T2S2_TRY(tt_round(cx, r, 0.1 * tin, std::min(kSmallMax, 2 * rcap)));
+      rhs = &r;
+    }
+    // inner solve: tensor-core contractions in the first stage only
+    Ctx cl = cx;
+    cl.contract_prec = tc_stage ? (int)prec : (int)T2S2_FP64;
+    Amen am;
+    am.fp32_local = true;
+    T2S2_TRY(am.init(op, cl, *rhs, x_zero ? g : dprev, c_mass, c_op, tin, rmax));
+    T2S2_TRY(tt_orth_right(cl, am.x));
+    double rnorm = -1.0;
+    T2S2_TRY(tt_norm(cx, *rhs, &rnorm));
+    double est = 1.0, est_prev2 = 1e300, est_prev = 1e300;
+    int inner = 0;
+    while (sweeps < max_sweeps) {
+      T2S2_TRY(am.sweep());
+      ++sweeps;
+      ++inner;
+      T2S2_TRY(residual_estimate(op, cx, *rhs, am.x, c_mass, c_op, rnorm * rnorm, &est));
+      if (verbose) {
+        fprintf(stderr, "[t2s2]   inner sweep %d est %.3e ranks", inner, est);
+        for (int k = 0; k <= d; ++k) fprintf(stderr, " %d", am.x.r[k]);
+        fprintf(stderr, " local_iters %lld\n", am.local_iters);
+      }
+      if (est <= tin) break;
+      if (inner >= 3 && est > 0.7 * est_prev2) break;  // at the precision floor
+      est_prev2 = est_prev;
+      est_prev = est;
+      T2S2_TRY(tt_orth_right(cl, am.x));
+    }
+    local_iters += am.local_iters;
+    if (tc_stage) {
+      // its result seeds the next solve of the whole system (x stays 0)
+      for (int k = 0; k < d; ++k)
+        if (am.x.core_elems(k) > g.cap[k]) return T2S2_ENOMEM;
+      T2S2_TRY(tt_copy(cx, am.x, g));
+      cx.ar->release(mk);
+      tc_stage = false;
+      ++refinements;
+      if (verbose) {
+        double rg = 0.0;
+        T2S2_TRY(residual_impl(op, cx, b, g, c_mass, c_op, false, &rg, &bnorm));
+        fprintf(stderr, "[t2s2] tensor-core stage: inner sweeps %d est %.2e residual %.3e\n", inner, est, rg);
+      }
+      continue;
+    }
+    if (am.x.core_elems(0) > 0) {
+      bool fits = true;
+      for (int k = 0; k < d; ++k) fits = fits && am.x.core_elems(k) <= dprev.cap[k];
+      if (fits) T2S2_TRY(tt_copy(cx, am.x, dprev));
+    }
+    // x <- rndg(x + delta)  (x <- delta while x = 0)
+    DevTT z;
+    if (x_zero) {
+      int rz[T2S2_MAX_D + 1];
+      for (int k = 0; k <= d; ++k) rz[k] = am.x.r[k];
+      T2S2_TRY(tt_alloc(cx, z, d, op->m, rz, 0));
+      T2S2_TRY(tt_copy(cx, am.x, z));
+    } else {
+      T2S2_TRY(tt_axpby(cx, 1.0, x, 1.0, am.x, z));
+    }
+    T2S2_TRY(tt_round(cx, z, 0.1 * tol, rmax));
+    for (int k = 0; k < d; ++k)
+      if (z.core_elems(k) > x.cap[k]) return T2S2_ENOMEM;
+    for (int k = 0; k <= d; ++k) x.r[k] = z.r[k];
+    T2S2_TRY(tt_copy(cx, z, x));
+    cx.ar->release(mk);
+    x_zero = false;
+    ++refinements;
+    const double prev = res;
+    T2S2_TRY(residual_impl(op, cx, b, x, c_mass, c_op, false, &res, &bnorm));
+    if (verbose) {
+      fprintf(stderr, "[t2s2] refinement %d: inner sweeps %d est %.2e (target %.1e) residual %.3e ranks", refinements,
+              inner, est, tin, res);
+      for (int k = 0; k <= d; ++k) fprintf(stderr, " %d", x.r[k]);
+      fprintf(stderr, "\n");
+    }
+    stall = (res > 0.5 * prev) ? stall + 1 : 0;
+    if (stall >= 3) break;  // no longer contracting (rank cap or precision floor)
+  }
+  if (tc) T2S2_TRY(tensor_core_status(cx));
+  for (int k = 0; k < d; ++k)
+    if (x.core_elems(k) > xio.cap[k]) return T2S2_ENOMEM;
+  for (int k = 0; k <= d; ++k) xio.r[k] = x.r[k];
+  T2S2_TRY(tt_copy(cx, x, xio));
+  if (info) {
+    info->residual = res;
+    info->sweeps = sweeps;
+    int mr = 1;
+    for (int k = 0; k <= d; ++k) mr = std::max(mr, x.r[k]);
+    info->max_rank = mr;
+    info->refinements = refinements;
+    info->local_iters = local_iters;
+  }
+  return res <= tol ? T2S2_OK : T2S2_ENOCONV;
+}
+
 }  // namespace
 
 // The public apply: FP64 and FP32_REFINE take the FP64 kernel; BF16 / TF32
@@ -629,6 +846,17 @@ t2s2_status apply_dispatch(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double
   return apply_fp64(b, cx.st);
 }
 
+// Arena bytes the refinement loop needs beyond one FP64 solve: the iterate,
+// A x, the residual train and x + delta (all at most rank rf + 2 rcap), and
+// the inner solver's workspace for a right-hand side of rank 2 rcap.
+static size_t refine_extra_bytes(t2s2_op op, int rcap, int rf) {
+  size_t mm = 0;
+  for (int k = 0; k < op->d; ++k) mm = std::max<size_t>(mm, op->m[k]);
+  const size_t R = (size_t)rf + 2 * rcap;
+  const size_t train = (size_t)op->d * R * mm * R * sizeof(double);
+  return 6 * train + Amen::bytes_needed(op->d, op->m, rcap, std::min(kSmallMax, 2 * rcap), 4, 40);
+}
+
 static t2s2_status solve_entry(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double c_mass, double c_op,
                                double tol, int rmax, int max_sweeps, t2s2_precision prec, void* stream,
                                t2s2_solve_info* info) {
@@ -640,6 +868,7 @@ static t2s2_status solve_entry(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double 
   int rfmax = 1;
   for (int k = 0; k <= op->d; ++k) rfmax = std::max(rfmax, b->r[k]);
   size_t need = Amen::bytes_needed(op->d, op->m, rmax + 4, rfmax, 4, 40) + 2 * (tt_bytes(b) + tt_bytes(x));
+  if (prec != T2S2_FP64) need += refine_extra_bytes(op, rmax + 4, rfmax);
   T2S2_TRY(ensure_arena(op, need));
   Ctx cx = make_ctx(op, stream);
   DevTT db, dx;
@@ -657,6 +886,7 @@ static t2s2_status step_entry(t2s2_op op, t2s2_tt* u, double dt, double tol, int
   T2S2_TRY(check_tt(op, u));
   const int d = op->d;
   size_t need = Amen::bytes_needed(d, op->m, rmax + 4, 2 * (rmax + 4), 4, 40) + 8 * tt_bytes(u);
+  if (prec != T2S2_FP64) need += refine_extra_bytes(op, rmax + 4, 2 * (rmax + 4));
   T2S2_TRY(ensure_arena(op, need));
   Ctx cx = make_ctx(op, stream);
   DevTT du;

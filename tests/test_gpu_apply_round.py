@@ -183,3 +183,19 @@ def test_rank_deficient_orthogonalisation_is_finite(T):
     b = OT.matvec(O.ttm_cores(ops, 1.0, 0.3), x)
     r = T.t2s2_residual(op, T.TT.from_cores(b), T.TT.from_cores(x), c_mass=1.0, c_op=0.3)
     assert np.isfinite(r) and r <= 1e-13
+
+
+def test_diff_norm_resolves_tiny_differences(T):
+    # x and y agree to ~1e-10 relative: the TT difference still gives the
+    # distance to a few digits (the dot-product formula would return noise)
+    from paper_2506_04732_gb300 import problem as P
+    p = W.config1(d=4, n=12)
+    op = P.build_operator(p)
+    x = W.random_tt(4, 10, [1, 3, 4, 2, 1], seed=11)
+    y = [c.copy() for c in x]
+    y[2] = y[2] + 1e-10 * np.random.default_rng(3).standard_normal(y[2].shape)
+    d_gpu = T.t2s2_diff_norm(op, T.TT.from_cores(x), T.TT.from_cores(y))
+    d_or = OT.diff_norm(x, y)
+    assert d_or > 0
+    assert abs(d_gpu - d_or) <= 1e-5 * d_or
+    assert T.t2s2_diff_norm(op, T.TT.from_cores(x), T.TT.from_cores(x)) <= 1e-14 * OT.norm(x)

@@ -140,3 +140,35 @@ def test_gemm_within_rounding_bound(T, fmt, M, N, K, tA, tB, batch):
     assert np.all(err <= bound * 1.0001 + 1e-300), float(np.max(err / (bound + 1e-300)))
     if K > 1:
         assert float(np.max(err)) > 0  # the operands really were rounded
+
+
+@pytest.mark.parametrize("fmt", ["fp64", "bf16", "tf32"])
+def test_grouped_apply_matches_per_instance_products(T, fmt):
+    """Many instances of uneven n and ranks in one persistent launch."""
+    from paper_2506_04732_gb300 import problem as P
+    probs = [W.config3(i) for i in range(12)]
+    ops, xs, ys, refs, bounds = [], [], [], [], []
+    for i, p in enumerate(probs):
+        m = p.n[0] - 2
+        r = [1] + [int(v) for v in np.random.default_rng(i).integers(1, 17, p.d - 1)] + [1]
+        x = W.random_tt(p.d, m, r, seed=500 + i)
+        ops.append(P.build_operator(p))
+        xs.append(T.TT.from_cores(x))
+        ys.append(T.TT.empty([m] * p.d, 2 * max(r)))
+        A = O.ttm_cores(O.build(p), 0.5, 1.0)
+        refs.append(OT.matvec(A, x))
+        bounds.append(OT.matvec([np.abs(a) for a in A], [np.abs(c) for c in x]))
+    prec = {"fp64": T.FP64, "bf16": T.BF16_REFINE, "tf32": T.TF32_REFINE}[fmt]
+    T.t2s2_apply_batched(ops, xs, ys, c_mass=0.5, c_op=1.0, prec=prec)
+    T.t2s2_apply_batched(ops, xs, ys, c_mass=0.5, c_op=1.0, prec=prec)  # tuned launch shape
+    for y, ref, bnd, p in zip(ys, refs, bounds, probs):
+        m = p.n[0] - 2
+        for a, b, s in zip(y.cores(), ref, bnd):
+            assert a.shape == b.shape
+            if fmt == "fp64":
+                assert np.max(np.abs(a - b)) <= 1e-12 * max(1.0, np.abs(b).max())
+            else:
+                u = U[fmt]
+                gamma = 2 * u + u * u + 2 * m * 2.0 ** -24
+                assert np.all(np.abs(a - b) <= gamma * s * 1.0001 + 1e-300)
+    assert "apply" in T.t2s2_autotune_report()

@@ -1,0 +1,139 @@
+"""GPU parity of the warm-start network (t2s2_mlp_*) against oracle/mlp.py,
+and what the trained network gains over a cold start.
+
+Bounds: the six layer products round their operands to BF16 (unit roundoff
+2^-8) and accumulate in FP32; through three layers and the TT loss gradient
+the Frobenius-relative error of each gradient tensor stays below 3e-2 and
+that of the loss below 1e-2 (random-sign rounding errors add in quadrature:
+about 2^-8 per product, a few products deep).  Adam runs in FP32 and is
+checked against its closed-form first step to 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2506_04732_gb300 as pkg
+    torch.cuda.set_device(0)
+    return pkg
+
+
+def _flat(params):
+    return np.concatenate([params[k].ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+
+def _unflat(flat, ref):
+    out, o = {}, 0
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        n = ref[k].size
+        out[k] = flat[o:o + n].reshape(ref[k].shape)
+        o += n
+    return out
+
+
+def _setup(T, hidden=32, d=4, m=6, r=3, ru=5, batch=8, seed=0):
+    from paper_2506_04732_gb300 import problem as P
+    net = T.WarmStartNet(15, hidden, [m] * d, r, ru, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    params = M.init_params(15, hidden, net.out_dim, seed)
+    for k in ("b1", "b2", "b3"):
+        params[k] = 0.1 * rng.standard_normal(params[k].shape)
+    params = {k: v.astype(np.float32).astype(np.float64) for k, v in params.items()}
+    net.set_params(torch.tensor(_flat(params), dtype=torch.float32))
+    Pm = rng.standard_normal((batch, 15)).astype(np.float32)
+    ranks = [1] + [int(rng.integers(1, ru + 1)) for _ in range(d - 1)] + [1]
+    targets = [W.random_tt(d, m, ranks, seed=seed * 100 + s) for s in range(batch)]
+    op = P.build_operator(W.config1(d=d, n=m + 2))
+    tg, uu = net.pack_targets(op, [T.TT.from_cores(t) for t in targets])
+    return net, params, Pm, targets, tg, uu, (d, [m] * d, r)
+
+
+def test_loss_and_gradients_match_oracle(T):
+    net, params, Pm, targets, tg, uu, (d, m, r) = _setup(T)
+    P = torch.tensor(Pm, device="cuda")
+    loss = net.loss_grad(P, tg, uu)
+    g = _unflat(net.grads().cpu().numpy().astype(np.float64), params)
+    loss_or, g_or = M.loss_and_grads(params, Pm.astype(np.float64), targets, d, m, r)
+    assert abs(loss - loss_or) <= 1e-2 * loss_or
+    for k in g_or:
+        rel = np.linalg.norm(g[k] - g_or[k]) / np.linalg.norm(g_or[k])
+        assert rel <= 3e-2, (k, rel)
+
+
+def test_adam_first_step_closed_form(T):
+    net, params, Pm, targets, tg, uu, _ = _setup(T, seed=3)
+    P = torch.tensor(Pm, device="cuda")
+    p0 = net.params().cpu().numpy().astype(np.float64)
+    lr = 1e-3
+    net.train_step(P, tg, uu, lr)
+    g = net.grads().cpu().numpy().astype(np.float64)
+    p1 = net.params().cpu().numpy().astype(np.float64)
+    expect = p0 - lr * g / (np.abs(g) + 1e-8)
+    assert np.allclose(p1, expect, rtol=1e-6, atol=1e-5 * lr)
+
+
+def test_training_reduces_the_loss(T):
+    net, params, Pm, targets, tg, uu, _ = _setup(T, hidden=64, batch=32, seed=5)
+    P = torch.tensor(Pm, device="cuda")
+    first = net.loss_grad(P, tg, uu)
+    for _ in range(300):
+        last = net.train_step(P, tg, uu, 3e-3)
+    assert last <= 0.1 * first, (first, last)
+
+
+def test_warm_start_saves_sweeps_and_keeps_the_answer(T):
+    """Train on solutions the solver itself produced; on held-out problems the
+    warm-started solve reaches the same tolerance in fewer sweeps in total."""
+    from paper_2506_04732_gb300 import problem as P
+    d, n = 4, 16
+    m = n - 2
+    rmax, tol = 20, 1e-8
+
+    def solve(p, x0=None, net=None):
+        op = P.build_operator(p)
+        b = T.TT.from_cores(P.source_cores(p, op))
+        x = T.TT.from_cores([np.ones((1, m, 1))] * d, rcap=rmax + 4)
+        if net is not None:
+            net.predict(W.warm_features(p), x)
+        info = T.t2s2_solve(op, b, x, tol, rmax, 40, allow_noconv=True)
+        return op, x, info
+
+    def family(seed):
+        # the config-4 family at d = 4, n = 16 with diffusion ratios in
+        # [1e-2, 1e-1], which that grid resolves (sharper layers need n = 32)
+        p = W.config4(seed, d=d, n=n)
+        p.eps = float(10.0 ** np.random.default_rng(seed).uniform(-2.0, -1.0)) * W.EDGE_LENGTH
+        return p
+
+    train = [family(10000 + i) for i in range(96)]
+    sols = [solve(p) for p in train]
+    net = T.WarmStartNet(W.WARM_IN_DIM, 128, [m] * d, 6, rmax + 4, seed=1)
+    tg, uu = net.pack_targets(sols[0][0], [s[1] for s in sols])
+    Pf = torch.tensor(np.stack([W.warm_features(p) for p in train]), device="cuda")
+    for it in range(600):
+        lo = (it * 32) % 96
+        net.train_step(Pf, tg, uu, 2e-3 if it < 400 else 5e-4, lo=lo, hi=lo + 32)
+    test = [family(90000 + i) for i in range(8)]
+    cold = warm = 0
+    for p in test:
+        _, xc, ic = solve(p)
+        if ic.residual > tol:
+            continue  # the cold solve itself is rank-limited here: no reference
+        _, xw, iw = solve(p, net=net)
+        assert iw.residual <= tol
+        a, b = xc.cores(), xw.cores()
+        from oracle import tt as OT
+        assert OT.diff_norm(a, b) <= 1e-5 * OT.norm(a)
+        cold += ic.sweeps
+        warm += iw.sweeps
+    print(f"held-out sweeps: cold {cold} warm {warm}")
+    assert cold > 0 and warm < cold

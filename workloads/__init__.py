@@ -204,6 +204,24 @@ def config4(seed: int, d: int = 6, n: int = 32) -> Problem:
                    terms, tol=1e-8, rmax=20, max_sweeps=50, seed=seed, params=p)
 
 
+WARM_IN_DIM = 15
+
+
+def warm_features(p: Problem) -> np.ndarray:
+    """Input vector of the warm-start network for a config4-style problem.
+
+    15 values, each scaled to about [-1, 1]: log10(eps / (|beta| L)) + 3, the
+    6 components of beta, the 4 amplitudes (a - 0.75) * 4, the 2 frequencies
+    w - 2 and the 2 centres 2 mu.  (An input width of 11 cannot hold beta,
+    the diffusion ratio and 8 source parameters; 15 can.)
+    """
+    beta = np.asarray(p.beta, dtype=np.float64)
+    ratio = p.eps / (EDGE_LENGTH * float(np.linalg.norm(beta)))
+    a, w, mu = p.params[:4], p.params[4:6], p.params[6:8]
+    f = np.concatenate([[math.log10(ratio) + 3.0], beta, (a - 0.75) * 4.0, w - 2.0, 2.0 * mu])
+    return f.astype(np.float32)
+
+
 def sine_problem(d: int, n: int, ratio: float, seed: int = 5, tol: float = 1e-8,
                  rmax: int = 12) -> Problem:
     """Small well-resolved steady problem: u* = prod sin(pi(x+1)/2) + 0.5 prod sin(pi(x+1))."""
