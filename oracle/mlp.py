@@ -9,23 +9,31 @@ supplies that guess:
 
     h1 = relu(W1 p + b1),  h2 = relu(W2 h1 + b2),  y = W3 h2 + b3,
 
-with y read as the TT cores of a tensor X(p) (core 0 of shape (1, m_1, r),
-middle cores (r, m_k, r), last core (r, m_d, 1), each row-major, concatenated
-in order).  The loss of one sample with target tensor U (a TT of any ranks)
-is the gauge-invariant relative error
+with y read as raw TT cores Y_k (core 0 of shape (1, m_1, r), middle cores
+(r, m_k, r), last core (r, m_d, 1), each row-major, concatenated in order)
+followed by one log-scale sigma.  The tensor X(p) has the cores
+X_k = Y_k / ||Y_k||_F, with core 0 also multiplied by exp(sigma): each core
+enters through its direction only and the overall size through sigma.  (The
+loss is a polynomial of degree 2d in raw cores; normalised cores keep it well
+conditioned, and the alternating solver that consumes X(p) does not depend on
+the scale of its initial guess anyway.)  The loss of one sample with target
+tensor U (a TT of any ranks) is the gauge-invariant relative error
 
     L = ||X - U||_F^2 / ||U||_F^2 = (<X,X> - 2 <X,U> + <U,U>) / <U,U>,
 
 evaluated with TT inner products, and averaged over the batch.  Gradients
 are by hand: dL/dX_k from the left and right environments of <X,X> and
-<X,U>, then ordinary backpropagation through the three layers (relu'(0) = 0).
+<X,U>, then through the normalisation (dL/dY = (g - <g, Yhat> Yhat) / ||Y||
+with g = dL/dYhat, and dL/dsigma = <dL/dX_0, X_0>), then ordinary
+backpropagation through the three layers (relu'(0) = 0).
 Adam follows Kingma & Ba with bias correction (beta1 0.9, beta2 0.999,
 epsilon 1e-8).
 
 Weights are row-major (out x in).  Pins (tests/test_oracle_mlp.py): central
 finite differences of the loss in FP64 on a small network, loss against the
-dense tensors, gauge invariance, zero loss at X = U, and Adam's first steps in
-closed form.
+dense tensors, gauge invariance, zero loss at X = U, invariance under scaling
+of a raw core, the exp(sigma) norm law, and Adam's first steps in closed
+form.
 """
 from __future__ import annotations
 
@@ -34,15 +42,20 @@ import numpy as np
 from . import tt as OT
 
 
-def out_dim(d, m, r):
-    """Length of y for d cores of mode sizes m (list) and rank r."""
+def core_dim(d, m, r):
+    """Number of raw core entries for d cores of mode sizes m (list) and rank r."""
     if d == 1:
         return m[0]
     return m[0] * r + sum(r * m[k] * r for k in range(1, d - 1)) + r * m[d - 1]
 
 
-def split_cores(y, d, m, r):
-    """TT cores read from the flat vector y (see module docstring)."""
+def out_dim(d, m, r):
+    """Length of y: the raw cores and the log-scale."""
+    return core_dim(d, m, r) + 1
+
+
+def raw_cores(y, d, m, r):
+    """The raw cores Y_k of y (see module docstring)."""
     cores, o = [], 0
     for k in range(d):
         a = 1 if k == 0 else r
@@ -50,7 +63,14 @@ def split_cores(y, d, m, r):
         n = a * m[k] * b
         cores.append(np.asarray(y[o:o + n]).reshape(a, m[k], b))
         o += n
-    assert o == len(y)
+    assert o + 1 == len(y)
+    return cores
+
+
+def split_cores(y, d, m, r):
+    """TT cores of X(p): normalised raw cores, core 0 scaled by exp(sigma)."""
+    cores = [c / np.linalg.norm(c) for c in raw_cores(y, d, m, r)]
+    cores[0] = cores[0] * np.exp(y[-1])
     return cores
 
 
@@ -126,10 +146,19 @@ def loss_and_grads(params, P, targets, d, m, r):
     dy = np.zeros_like(y)
     total = 0.0
     for s in range(B):
+        raw = raw_cores(y[s], d, m, r)
         x = split_cores(y[s], d, m, r)
         loss, g = tt_loss_grad(x, targets[s])
         total += loss
-        dy[s] = np.concatenate([gk.ravel() for gk in g]) / B
+        sig = y[s, -1]
+        parts = []
+        for k in range(d):
+            nk = np.linalg.norm(raw[k])
+            yhat = raw[k] / nk
+            gh = g[k] * np.exp(sig) if k == 0 else g[k]  # dL/dYhat_k
+            parts.append(((gh - np.sum(gh * yhat) * yhat) / nk).ravel())
+        parts.append(np.array([np.sum(g[0] * x[0])]))    # dL/dsigma
+        dy[s] = np.concatenate(parts) / B
     grads = {}
     grads["W3"] = dy.T @ h2
     grads["b3"] = dy.sum(axis=0)

@@ -27,11 +27,30 @@ def _setup(seed=0, batch=3):
 
 def test_out_dim_and_split():
     odim = M.out_dim(D, MM, R)
-    assert odim == 4 * 2 + 2 * 5 * 2 + 2 * 3
-    y = np.arange(odim, dtype=float)
+    assert odim == 4 * 2 + 2 * 5 * 2 + 2 * 3 + 1
+    y = np.arange(odim, dtype=float) / odim
+    raw = M.raw_cores(y, D, MM, R)
+    assert [c.shape for c in raw] == [(1, 4, 2), (2, 5, 2), (2, 3, 1)]
+    assert raw[1][0, 0, 0] == y[8] and raw[2][1, 2, 0] == y[odim - 2]
     cores = M.split_cores(y, D, MM, R)
-    assert [c.shape for c in cores] == [(1, 4, 2), (2, 5, 2), (2, 3, 1)]
-    assert cores[1][0, 0, 0] == 8 and cores[2][1, 2, 0] == odim - 1
+    # unit-norm cores, the first scaled by exp(sigma)
+    assert abs(np.linalg.norm(cores[0]) - np.exp(y[-1])) <= 1e-12 * np.exp(y[-1])
+    assert all(abs(np.linalg.norm(c) - 1.0) <= 1e-14 for c in cores[1:])
+
+
+def test_loss_ignores_the_scale_of_each_raw_core():
+    params, P, targets = _setup()
+    y, _ = M.forward(params, P)
+    x0 = M.split_cores(y[0], D, MM, R)
+    # scaling one raw core leaves X (and so the loss) unchanged
+    y2 = y[0].copy()
+    y2[8:28] *= 3.7
+    x2 = M.split_cores(y2, D, MM, R)
+    assert all(np.allclose(a, b, rtol=1e-14, atol=0) for a, b in zip(x0, x2))
+    # sigma moves the norm of X exactly by exp(sigma)
+    y3 = y[0].copy()
+    y3[-1] += 0.5
+    assert abs(OT.norm(M.split_cores(y3, D, MM, R)) / OT.norm(x0) - np.exp(0.5)) <= 1e-13
 
 
 def test_tt_loss_matches_dense():
