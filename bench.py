@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the precision-variant and grouped-contraction measurements")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle CPU work for the cpu_baseline sample")
     ap.add_argument("--workload", default="steady", choices=["steady", "batched", "cn", "warm"],
@@ -506,7 +508,6 @@ def main():
         infos.append(T.t2s2_solve(op, b, x, p.tol, p.rmax, p.max_sweeps, prec=prec))
     torch.cuda.synchronize()
     lib = T.load()
-    T.load().t2s2_trace(1)
     launches0 = lib.t2s2_kernel_launches()
     clocks = ClockSampler(local)
     if ws > 1:
@@ -530,19 +531,16 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     launches = lib.t2s2_kernel_launches() - launches0
-    import ctypes
-    fam = {}
-    for i, name in enumerate(FAMILIES):
-        n_l = ctypes.c_longlong()
-        ms = ctypes.c_double()
-        fl = ctypes.c_double()
-        by = ctypes.c_double()
-        lib.t2s2_trace_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
-                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                                        ctypes.POINTER(ctypes.c_double)]
-        lib.t2s2_trace_read(i, ctypes.byref(n_l), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by))
-        fam[name] = {"launches": n_l.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
-    lib.t2s2_trace(0)
+    # per-family kernel times come from one more solve, untimed, with a CUDA
+    # event pair around every launch (the events would slow the timed steps)
+    flush.zero_()
+    reset_x()
+    torch.cuda.synchronize()
+    T.t2s2_trace(True)
+    T.t2s2_solve(op, b, x, p.tol, p.rmax, p.max_sweeps, prec=prec)
+    torch.cuda.synchronize()
+    fam = {name: T.t2s2_trace_read(name) for name in FAMILIES}
+    T.t2s2_trace(False)
     total_ms = sum(step_ms)
     if ws > 1:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
@@ -575,7 +573,7 @@ def main():
                "d2h_bytes_per_step": d2h}
 
     extras = {}
-    if rank == 0 and ws == 1 and args.prec == "fp64":
+    if rank == 0 and ws == 1 and args.prec == "fp64" and not args.no_extras:
         for key, fn in (("precision_variants", lambda: measure_precisions(T, P, W, torch, op, b, x)),
                         ("contraction", lambda: measure_contraction(T, P, W, torch))):
             try:
@@ -601,7 +599,7 @@ def main():
             "per_launch_ms": fd["ms"] / max(1, fd["launches"])}
 
     cpu = None
-    if rank == 0:
+    if rank == 0 and args.cpu_budget > 0:
         dt, sweeps, conv, res = cpu_baseline_sample("config1()", args.cpu_budget)
         solves = min(1.0, sweeps / SWEEPS_NEEDED_HINT) if not conv else 1.0
         cpu = {"value": solves / dt if dt > 0 and sweeps else 0.0, "unit": UNIT, "cores": os.cpu_count(),

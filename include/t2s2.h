@@ -310,6 +310,16 @@ t2s2_status t2s2_mlp_loss_grad(t2s2_mlp net, const float* P, int batch, const fl
 /* As t2s2_mlp_loss_grad followed by one Adam update with learning rate lr. */
 t2s2_status t2s2_mlp_train_step(t2s2_mlp net, const float* P, int batch, const float* targets,
                                 const float* uu, float lr, float* loss, void* stream);
+/* `steps` training steps over a resident training set of n samples (P: n x
+ * in_dim, targets / uu as packed above, all device), minibatches of `batch`
+ * consecutive samples cycling through the set, learning rate lr.  With
+ * use_graph = 1 the launch sequence of a step is captured once per minibatch
+ * as a CUDA graph (the first visit runs eagerly) and replayed afterwards;
+ * the step count and learning rate live in device memory so a replay stays
+ * valid.  *loss (may be NULL) receives the last step's mean loss.
+ * Synchronises the stream at the end. */
+t2s2_status t2s2_mlp_train(t2s2_mlp net, const float* P, int n, const float* targets, const float* uu,
+                           int batch, int steps, float lr, int use_graph, float* loss, void* stream);
 /* Warm start: the cores of X(p) (p: host or device, in_dim floats) as FP64
  * into x (device or host cores with room for them); x->r is set to the
  * network's ranks. */

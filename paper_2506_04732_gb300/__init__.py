@@ -124,6 +124,9 @@ _SIGS = {
                                            ctypes.c_void_p, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
                                            ctypes.c_void_p]),
     "t2s2_mlp_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_void_p]),
+    "t2s2_mlp_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
     "t2s2_apply_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_TT), ctypes.POINTER(_TT),
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_void_p]),
@@ -279,6 +282,14 @@ class WarmStartNet:
         loss = ctypes.c_float()
         _check(load().t2s2_mlp_train_step(self._h, pp, hi - lo, tp, up, float(lr), ctypes.byref(loss),
                                           _stream_handle(None)), "t2s2_mlp_train_step")
+        return loss.value
+
+    def train(self, P, targets, uu, batch, steps, lr, use_graph=True):
+        """`steps` Adam steps cycling through the resident set; returns the last loss."""
+        loss = ctypes.c_float()
+        _check(load().t2s2_mlp_train(self._h, P.data_ptr(), int(P.shape[0]), targets.data_ptr(), uu.data_ptr(),
+                                     int(batch), int(steps), float(lr), int(bool(use_graph)), ctypes.byref(loss),
+                                     _stream_handle(None)), "t2s2_mlp_train")
         return loss.value
 
     def predict(self, p, x: "TT"):

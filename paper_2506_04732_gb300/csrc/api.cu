@@ -10,9 +10,13 @@
 
 namespace t2s2 {
 
-static thread_local char g_last_error[256] = "";
+// The last CUDA failure, process-wide (worker threads of the batched solve
+// report through it too); diagnostics only.
+static char g_last_error[256] = "";
+static std::mutex g_last_error_mu;
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  std::lock_guard<std::mutex> lk(g_last_error_mu);
   snprintf(g_last_error, sizeof(g_last_error), "%s at %s:%d: %s", cudaGetErrorString(e), file, line,
            what);
 }
@@ -42,6 +46,7 @@ Ctx make_ctx(t2s2_op op, void* stream) {
   cx.ar = &op->arena;
   cx.hbuf = op->hbuf;
   cx.dstat = op->dstat;
+  cx.coop_ctas = op->team;
   return cx;
 }
 

@@ -3,9 +3,9 @@
 //     A = sum_k Rt_1 x ... x Lt_k x ... x Rt_d,   M = Rt_1 x ... x Rt_d.
 // Core k of y needs the two mode-k contractions S X_k and G X_k with
 // S = Rt_k and G = c_op Lt_k (+ c_mass Rt_1 on the first core).  Each CTA
-// computes a 64 x 64 tile of [S; G] X_k[a] (rows: the 2m stacked output rows,
-// columns: the r_{k+1} right-rank index) and writes it straight into the block
-// pattern of Y_k:
+// computes a 64 x 64 tile of [S; G] X_k (rows: the 2m stacked output rows,
+// columns: the (a, b) = (left, right) rank pairs of the core) and writes it
+// straight into the block pattern of Y_k:
 //     first  [G X, S X]            (1      x m x 2 r1)
 //     middle [[S X, 0], [G X, S X]] (2 r0  x m x 2 r1)
 //     last   [S X; G X]            (2 r0  x m x 1)
@@ -48,7 +48,9 @@ __device__ __forceinline__ int find_core(const Work& w, int tile) {
   return lo;
 }
 
-// Persistent over tiles: CTA b takes tiles b, b + gridDim.x, ...
+// Persistent over tiles: CTA b takes tiles b, b + gridDim.x, ...  A tile is
+// 64 rows of [S; G] by 64 (a, b) pairs of the core (column g = a rb + b), so
+// small right ranks waste no columns.
 template <class Work>
 __global__ void __launch_bounds__(NT) apply_kernel(Work w, int total) {
   __shared__ double As[BK][BM + 1];
@@ -57,11 +59,10 @@ __global__ void __launch_bounds__(NT) apply_kernel(Work w, int total) {
     const int ci = find_core(w, tile);
     const ApplyCore c = w.core(ci);
     const int local = tile - w.first(ci);
-    const int mt = cdiv_dev(2 * c.m, BM), nt = cdiv_dev(c.rb, BN);
-    const int a = local / (mt * nt);
-    const int rem = local % (mt * nt);
-    const int m0 = (rem / nt) * BM, n0 = (rem % nt) * BN;
-    const double* X = c.X + (long)a * c.m * c.rb;  // m x rb
+    const long npairs = (long)c.ra * c.rb;
+    const int nt = (int)((npairs + BN - 1) / BN);
+    const int m0 = (local / nt) * BM;
+    const long n0 = (long)(local % nt) * BN;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     double acc[4][4];
 #pragma unroll
@@ -85,9 +86,15 @@ __global__ void __launch_bounds__(NT) apply_kernel(Work w, int total) {
         As[kk][mm] = v;
       }
       for (int e = threadIdx.x; e < BN * BK; e += NT) {
-        int nn = e % BN, kk = e / BN;
-        int col = n0 + nn, row = k0 + kk;
-        Bs[kk][nn] = (row < c.m && col < c.rb) ? X[(long)row * c.rb + col] : 0.0;
+        const int nn = e % BN, kk = e / BN;
+        const long g = n0 + nn;
+        const int j = k0 + kk;
+        double v = 0.0;
+        if (j < c.m && g < npairs) {
+          const long a = g / c.rb, b = g % c.rb;
+          v = c.X[(a * c.m + j) * c.rb + b];
+        }
+        Bs[kk][nn] = v;
       }
       __syncthreads();
 #pragma unroll
@@ -104,42 +111,43 @@ __global__ void __launch_bounds__(NT) apply_kernel(Work w, int total) {
       }
       __syncthreads();
     }
-    // scatter
+    // scatter into the block pattern of Y
     const int ra = c.ra, rb = c.rb, m = c.m;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      int row = m0 + ty + 16 * i;
-      if (row >= 2 * m) continue;
-      const bool gpart = row >= m;
-      const int ii = gpart ? row - m : row;
+    for (int j = 0; j < 4; ++j) {
+      const long g = n0 + tx + 16 * j;
+      if (g >= npairs) continue;
+      const long a = g / rb, b = g % rb;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        int b = n0 + tx + 16 * j;
-        if (b >= rb) continue;
-        double v = acc[i][j];
+      for (int i = 0; i < 4; ++i) {
+        const int row = m0 + ty + 16 * i;
+        if (row >= 2 * m) continue;
+        const bool gpart = row >= m;
+        const int ii = gpart ? row - m : row;
+        const double v = acc[i][j];
         double* Y = c.Y;
         switch (c.kind) {
           case kApplySingle:  // 1 x m x 1
             if (gpart) Y[ii] = v;
             break;
           case kApplyFirst: {  // 1 x m x 2rb: [G X, S X]
-            long base = (long)ii * 2 * rb;
+            const long base = (long)ii * 2 * rb;
             if (gpart) Y[base + b] = v; else Y[base + rb + b] = v;
             break;
           }
           case kApplyLast: {  // 2ra x m x 1: [S X; G X]
-            long r = gpart ? (ra + a) : a;
+            const long r = gpart ? (ra + a) : a;
             Y[r * m + ii] = v;
             break;
           }
           default: {  // middle: 2ra x m x 2rb
-            long wd = 2L * rb;
+            const long wd = 2L * rb;
             if (gpart) {
-              Y[((long)(ra + a) * m + ii) * wd + b] = v;            // (1,0): G X
+              Y[((ra + a) * m + ii) * wd + b] = v;            // (1,0): G X
             } else {
-              Y[((long)a * m + ii) * wd + b] = v;                   // (0,0): S X
-              Y[((long)(ra + a) * m + ii) * wd + rb + b] = v;       // (1,1): S X
-              Y[((long)a * m + ii) * wd + rb + b] = 0.0;            // (0,1): 0
+              Y[(a * m + ii) * wd + b] = v;                   // (0,0): S X
+              Y[((ra + a) * m + ii) * wd + rb + b] = v;       // (1,1): S X
+              Y[(a * m + ii) * wd + rb + b] = 0.0;            // (0,1): 0
             }
           }
         }
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(NT) apply_kernel(Work w, int total) {
 }
 }  // namespace
 
-int apply_fp64_tiles(const ApplyCore& c) { return c.ra * cdiv(2 * c.m, BM) * cdiv(c.rb, BN); }
+int apply_fp64_tiles(const ApplyCore& c) { return cdiv(2 * c.m, BM) * cdiv((long)c.ra * c.rb, BN); }
 
 t2s2_status apply_fp64(const ApplyBatch& p, cudaStream_t st) {
   ParamWork w;

@@ -31,7 +31,7 @@ using namespace tc;
 constexpr int kTileM = 128;    // (a, b) rows per CTA = TMEM lanes
 constexpr int kMaxK = 64;      // contraction length m (zero padded)
 constexpr int kTileN = 128;    // 2m stacked rows (zero padded) = TMEM columns
-constexpr int kThreads = 128;  // 4 warps: one per 32 TMEM lanes
+constexpr int kThreads = 256;  // 8 warps: two per 32-lane TMEM quarter (column halves)
 // Dynamic shared memory per CTA: the two operand tiles plus alignment slack,
 // and never less than 48 KB, so that at most 4 CTAs share an SM and the
 // 4 x 128 TMEM columns they allocate never exceed the SM's 512.
@@ -73,7 +73,7 @@ __device__ __forceinline__ int find_core(const Work& w, int tile) {
 // mbarrier are set up once; the operator tile is restaged only when the core
 // changes.
 template <int P, class Work>
-__global__ void __launch_bounds__(kThreads) apply_tc_kernel(Work w, int total, int* err) {
+__global__ void __launch_bounds__(kThreads, 4) apply_tc_kernel(Work w, int total, int* err) {
   using O = Op<P>;
   constexpr int E = O::kBytes;
   constexpr int kTileBytes = kTileM * kMaxK * E;  // 16 KB (BF16) or 32 KB (TF32)
@@ -105,15 +105,20 @@ __global__ void __launch_bounds__(kThreads) apply_tc_kernel(Work w, int total, i
     // K padded to whole MMAs; N = 2m padded to a multiple of 16 (M = 128 form)
     const int kpad = ((m + O::kMmaK - 1) / O::kMmaK) * O::kMmaK;
     const int npad = ((2 * m + 15) / 16) * 16;
-    // A tile: row t <-> pair g = row0 + t = (a, b); zero rows past the core
+    // A tile: row t <-> pair g = row0 + t = (a, b); zero rows past the core.
+    // Two threads per row, each loading half of the K range.
     {
-      const long g = row0 + tid;
+      const int t = tid & (kTileM - 1), half = tid / kTileM;
+      const int kh = kpad / 2;
+      const long g = row0 + t;
       const bool valid = g < nrows;
       const long a = valid ? g / rb : 0, b = valid ? g % rb : 0;
       const double* xr = c.X + a * (long)m * rb + b;
-      for (int j = 0; j < kpad; ++j) {
+#pragma unroll 8
+      for (int jj = 0; jj < kh; ++jj) {
+        const int j = half * kh + jj;
         const double v = (valid && j < m) ? xr[(long)j * rb] : 0.0;
-        O::store(sA + sw128_off<E>(tid, j, kTileM), v);
+        O::store(sA + sw128_off<E>(t, j, kTileM), v);
       }
     }
     // B tile: row ii < m: S row ii; m <= ii < 2m: G row ii - m; zero padded
@@ -159,15 +164,17 @@ __global__ void __launch_bounds__(kThreads) apply_tc_kernel(Work w, int total, i
       break;
     }
     fence_after_sync();
-    // epilogue: warp w owns TMEM lanes 32w .. 32w+31 = tile rows
-    const int t = warp * 32 + lane;
+    // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (= tile rows)
+    // and every other 32-column chunk, starting at chunk w / 4
+    const int quarter = warp & 3;
+    const int t = quarter * 32 + lane;
     const long g = row0 + t;
     const bool valid = g < nrows;
     const long a = valid ? g / rb : 0, b = valid ? g % rb : 0;
     double* Y = c.Y;
-    for (int c0 = 0; c0 < 2 * m; c0 += 32) {
+    for (int c0 = 32 * (warp >> 2); c0 < 2 * m; c0 += 64) {
       uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
       if (!valid) continue;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {

@@ -6,11 +6,15 @@
 //
 //   h1 = relu(W1 p + b1),  h2 = relu(W2 h1 + b2),  y = W3 h2 + b3,
 //
-// y holds the cores of X(p): core 0 (1 x m_1 x r), middle cores (r x m_k x r),
-// last core (r x m_d x 1), row-major, concatenated.  Loss per sample with
-// target U: ||X - U||^2 / ||U||^2 = (<X,X> - 2 <X,U> + <U,U>) / <U,U>, which
-// does not depend on the TT gauge of X; its gradient with respect to core k
-// comes from the left and right environments of <X,X> and <X,U>.
+// y holds raw cores Y_k (core 0: 1 x m_1 x r, middle: r x m_k x r, last:
+// r x m_d x 1, row-major, concatenated) and a log-scale sigma; X(p) has the
+// cores Y_k / ||Y_k||, core 0 times exp(sigma), so the network learns each
+// core's direction and one overall size (the solver does not depend on the
+// scale of its initial guess; raw cores would make the loss a polynomial of
+// degree 2d).  Loss per sample with target U: ||X - U||^2 / ||U||^2 =
+// (<X,X> - 2 <X,U> + <U,U>) / <U,U>, independent of the TT gauge of X; its
+// gradient with respect to core k comes from the left and right environments
+// of <X,X> and <X,U>, then through the normalisation.
 //
 // Kernels: the six layer products (three forward, three backward per layer
 // pair) run on the tcgen05 GEMM with BF16 operands (weights and activations
@@ -30,9 +34,10 @@
 
 struct t2s2_mlp_s {
   int device = 0;
-  int in_dim = 0, hidden = 0, d = 0, r = 0, ru = 0, odim = 0, mmax = 0;
+  int in_dim = 0, hidden = 0, d = 0, r = 0, ru = 0, odim = 0, ncore = 0, mmax = 0;
   int m[T2S2_MAX_D] = {0};
-  int off[T2S2_MAX_D + 1] = {0};  // offsets of the cores in y
+  int off[T2S2_MAX_D + 1] = {0};  // offsets of the cores in y; y[ncore] = sigma
+  double* ystage = nullptr;        // ncore doubles: the cores of one prediction
   long long nparams = 0;
   long long oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
   float* params = nullptr;  // W1 b1 W2 b2 W3 b3
@@ -44,6 +49,17 @@ struct t2s2_mlp_s {
   float *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *y = nullptr, *dy = nullptr;
   float *dh = nullptr, *dz = nullptr, *loss = nullptr;
   float* pbuf = nullptr;  // in_dim floats: the input of a single prediction
+  long long* dstep = nullptr;  // device copy of the Adam step count
+  float* dlr = nullptr;        // device learning rate
+  float* hlr = nullptr;        // pinned host staging of the learning rate
+  struct GraphEntry {
+    const float *P, *targets, *uu;
+    int batch;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;  // captured training steps, one per minibatch
+  cudaStream_t gstream = nullptr;  // non-blocking stream for capture and replay
+  cudaEvent_t gev = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int* dstat = nullptr;
@@ -60,12 +76,12 @@ constexpr int kMlpMaxTargetRank = 32;
 constexpr int kMlpMaxM = 64;
 
 struct LossArgs {
-  const float* y;        // batch x odim
+  const float* y;        // batch x odim (odim = ncore + 1: cores, then sigma)
   const float* targets;  // batch x d x ru x mmax x ru (zero padded)
   const float* uu;       // batch: <U,U>
   float* dy;             // batch x odim: dL/dy, already divided by the batch size
   float* loss;           // batch
-  int batch, odim, d, r, ru, mmax;
+  int batch, odim, ncore, d, r, ru, mmax;
   int m[T2S2_MAX_D];
   int off[T2S2_MAX_D + 1];
   float inv_batch;
@@ -75,7 +91,7 @@ size_t loss_smem_floats(const LossArgs& a) {
   const size_t env = (size_t)(a.d + 1) * (2 * a.r * a.r + 2 * a.r * a.ru);
   const size_t W = (size_t)std::max(a.r, a.ru) * a.mmax * a.r;
   const size_t G = (size_t)a.r * a.mmax * a.r;
-  return (size_t)a.odim + env + W + G;
+  return 2 * (size_t)a.ncore + env + W + G + kLossThreads + 2 * T2S2_MAX_D;
 }
 
 // One CTA per sample.  Every core of X is treated as r x m_k x r with zeros
@@ -87,14 +103,38 @@ __global__ void __launch_bounds__(kLossThreads) tt_loss_grad_kernel(LossArgs a) 
   const int s = blockIdx.x, tid = threadIdx.x;
   const int d = a.d, r = a.r, ru = a.ru, mmax = a.mmax;
   float* sX = sm;
-  float* Lxx = sX + a.odim;
+  float* Gall = sX + a.ncore;  // dL/dX, all cores
+  float* Lxx = Gall + a.ncore;
   float* Rxx = Lxx + (d + 1) * r * r;
   float* Lxu = Rxx + (d + 1) * r * r;
   float* Rxu = Lxu + (d + 1) * r * ru;
   float* W = Rxu + (d + 1) * r * ru;
   float* G = W + max(r, ru) * mmax * r;
+  float* red = G + r * mmax * r;  // block-reduction scratch
+  float* invn = red + kLossThreads;  // 1 / ||Y_k||
+  float* dots = invn + T2S2_MAX_D;   // <dL/dX_k, X_k>
   const float* U = a.targets + (size_t)s * d * ru * mmax * ru;
-  for (int e = tid; e < a.odim; e += kLossThreads) sX[e] = a.y[(size_t)s * a.odim + e];
+  for (int e = tid; e < a.ncore; e += kLossThreads) sX[e] = a.y[(size_t)s * a.odim + e];
+  const float sigma = a.y[(size_t)s * a.odim + a.ncore];
+  const float esig = expf(sigma);
+  __syncthreads();
+  // X_k = Y_k / ||Y_k|| (core 0 times exp(sigma)); sums in a fixed order
+  for (int k = 0; k < d; ++k) {
+    float acc = 0.f;
+    for (int e = a.off[k] + tid; e < a.off[k + 1]; e += kLossThreads) acc = fmaf(sX[e], sX[e], acc);
+    red[tid] = acc;
+    __syncthreads();
+    for (int w = kLossThreads / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) invn[k] = red[0] > 0.f ? rsqrtf(red[0]) : 0.f;
+    __syncthreads();
+  }
+  for (int k = 0; k < d; ++k) {
+    const float f = invn[k] * (k == 0 ? esig : 1.f);
+    for (int e = a.off[k] + tid; e < a.off[k + 1]; e += kLossThreads) sX[e] *= f;
+  }
   for (int e = tid; e < (d + 1) * r * r; e += kLossThreads) Lxx[e] = Rxx[e] = 0.f;
   for (int e = tid; e < (d + 1) * r * ru; e += kLossThreads) Lxu[e] = Rxu[e] = 0.f;
   __syncthreads();
@@ -230,11 +270,32 @@ __global__ void __launch_bounds__(kLossThreads) tt_loss_grad_kernel(LossArgs a) 
       const int aa = e / (mk * r), rem = e % (mk * r), i = rem / r, b = rem % r;
       float acc = 0.f;
       for (int c = 0; c < ru; ++c) acc = fmaf(F[aa * ru + c], W[c * mk * r + rem], acc);
-      if (aa < ra && b < rb)
-        a.dy[(size_t)s * a.odim + a.off[k] + (aa * mk + i) * rb + b] = (G[e] - 2.f * acc) * scale;
+      if (aa < ra && b < rb) Gall[a.off[k] + (aa * mk + i) * rb + b] = G[e] - 2.f * acc;
     }
     __syncthreads();
   }
+  // through the normalisation: with Yhat = Y / ||Y|| and g = dL/dYhat,
+  // dL/dY = (g - <g, Yhat> Yhat) / ||Y||; for every core <g, Yhat> equals
+  // <dL/dX_k, X_k>, which for core 0 is also dL/dsigma
+  for (int k = 0; k < d; ++k) {
+    float acc = 0.f;
+    for (int e = a.off[k] + tid; e < a.off[k + 1]; e += kLossThreads) acc = fmaf(Gall[e], sX[e], acc);
+    red[tid] = acc;
+    __syncthreads();
+    for (int w = kLossThreads / 2; w > 0; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) dots[k] = red[0];
+    __syncthreads();
+  }
+  for (int k = 0; k < d; ++k) {
+    const float gs = (k == 0) ? esig : 1.f;      // g = gs * dL/dX_k
+    const float ys = (k == 0) ? 1.f / esig : 1.f;  // Yhat = ys * X_k
+    for (int e = a.off[k] + tid; e < a.off[k + 1]; e += kLossThreads)
+      a.dy[(size_t)s * a.odim + e] = (gs * Gall[e] - dots[k] * ys * sX[e]) * invn[k] * scale;
+  }
+  if (tid == 0) a.dy[(size_t)s * a.odim + a.ncore] = dots[0] * scale;
 }
 
 // z += bias (per column); h = relu(z) if h != nullptr.
@@ -263,8 +324,15 @@ __global__ void colsum_kernel(float* out, const float* v, int rows, int cols) {
 }
 
 // Adam with bias correction (Kingma & Ba): bc1 = 1 - beta1^t, bc2 = 1 - beta2^t.
-__global__ void adam_kernel(float* p, const float* g, float* mo, float* ve, long n, float lr, float beta1,
-                            float beta2, float eps, float bc1, float bc2) {
+// The step t (after this update) and the learning rate are read from device
+// memory, so that a captured CUDA graph of the training step stays valid from
+// one replay to the next.
+__global__ void adam_kernel(float* p, const float* g, float* mo, float* ve, long n, const float* lr_p,
+                            const long long* step_p, float beta1, float beta2, float eps) {
+  const double t = (double)(*step_p + 1);
+  const float bc1 = (float)(1.0 - pow((double)beta1, t));
+  const float bc2 = (float)(1.0 - pow((double)beta2, t));
+  const float lr = *lr_p;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
     const float gg = g[e];
     const float m1 = beta1 * mo[e] + (1.f - beta1) * gg;
@@ -275,6 +343,8 @@ __global__ void adam_kernel(float* p, const float* g, float* mo, float* ve, long
   }
 }
 
+__global__ void step_increment_kernel(long long* step_p) { *step_p += 1; }
+
 // Packs one FP64 target TT into the zero-padded FP32 slot (d x ru x mmax x ru).
 __global__ void pack_core_kernel(float* slot, const double* core, int ra, int m, int rb, int ru, int mmax) {
   const long n = (long)ru * mmax * ru;
@@ -284,13 +354,37 @@ __global__ void pack_core_kernel(float* slot, const double* core, int ra, int m,
   }
 }
 
-// TT cores of y (one sample) to FP64 cores.
-__global__ void unpack_core_kernel(double* core, const float* y, long n) {
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
-    core[e] = (double)y[e];
+// The cores of X(p) for one sample: block k normalises raw core k of y
+// (fixed-order block sum) and scales core 0 by exp(sigma); FP64 out.
+struct UnpackArgs {
+  const float* y;
+  double* out;
+  int off[T2S2_MAX_D + 1];
+  int ncore;
+};
+__global__ void unpack_cores_kernel(UnpackArgs u) {
+  __shared__ float red[256];
+  const int k = blockIdx.x, t = threadIdx.x;
+  const int o0 = u.off[k], o1 = u.off[k + 1];
+  float acc = 0.f;
+  for (int e = o0 + t; e < o1; e += blockDim.x) acc = fmaf(u.y[e], u.y[e], acc);
+  red[t] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (t < w) red[t] += red[t + w];
+    __syncthreads();
+  }
+  const double f = (red[0] > 0.f ? 1.0 / sqrt((double)red[0]) : 0.0) * (k == 0 ? exp((double)u.y[u.ncore]) : 1.0);
+  for (int e = o0 + t; e < o1; e += blockDim.x) u.out[e] = f * (double)u.y[e];
 }
 
 int ew_blocks(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, 8L * kNumSMs)); }
+
+// Captured graphs hold buffer addresses: drop them whenever a buffer moves.
+void drop_graphs(t2s2_mlp net) {
+  for (auto& g : net->graphs) cudaGraphExecDestroy(g.exec);
+  net->graphs.clear();
+}
 
 t2s2_status mm(t2s2_mlp net, int M, int N, int K, bool tA, bool tB, const float* A, long lda, const float* B,
                long ldb, float* C, long ldc, cudaStream_t st) {
@@ -300,6 +394,7 @@ t2s2_status mm(t2s2_mlp net, int M, int N, int K, bool tA, bool tB, const float*
   const size_t need = gemm_tc_workspace_bytes(g, T2S2_BF16_REFINE);
   if (need > net->ws_bytes) {
     T2S2_CUDA_TRY(cudaStreamSynchronize(st));  // earlier launches may still read the old buffer
+    drop_graphs(net);
     if (net->ws) cudaFree(net->ws);
     net->ws = nullptr;
     net->ws_bytes = 0;
@@ -311,6 +406,7 @@ t2s2_status mm(t2s2_mlp net, int M, int N, int K, bool tA, bool tB, const float*
 
 t2s2_status ensure_batch(t2s2_mlp net, int batch) {
   if (batch <= net->bcap) return T2S2_OK;
+  drop_graphs(net);
   float** bufs[] = {&net->z1, &net->h1, &net->z2, &net->h2, &net->dh, &net->dz, &net->y, &net->dy, &net->loss};
   for (auto b : bufs)
     if (*b) cudaFree(*b), *b = nullptr;
@@ -357,6 +453,7 @@ t2s2_status loss_grad(t2s2_mlp net, const float* P, int B, const float* targets,
   a.loss = net->loss;
   a.batch = B;
   a.odim = net->odim;
+  a.ncore = net->ncore;
   a.d = net->d;
   a.r = net->r;
   a.ru = net->ru;
@@ -372,7 +469,8 @@ t2s2_status loss_grad(t2s2_mlp net, const float* P, int B, const float* targets,
       fl += 2.0 * (2 * r * mk * r * r + 2 * ru * mk * r * r + 2 * ru * mk * r * ru) * 1.5;
     }
     TraceScope ts(kTrMlp, st, fl * B, 4.0 * B * ((double)net->odim * 2 + (double)net->d * net->ru * net->mmax * net->ru));
-    T2S2_CUDA_TRY(cudaFuncSetAttribute(tt_loss_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    T2S2_CUDA_TRY(cudaFuncSetAttribute(tt_loss_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)std::max<size_t>(smem, 200 * 1024)));
     tt_loss_grad_kernel<<<B, kLossThreads, smem, st>>>(a);
     T2S2_CUDA_TRY(cudaGetLastError());
   }
@@ -421,6 +519,27 @@ t2s2_status mean_loss(t2s2_mlp net, int B, float* out, cudaStream_t st) {
   return T2S2_OK;
 }
 
+t2s2_status set_lr(t2s2_mlp net, float lr, cudaStream_t st) {
+  // the previous copy out of the pinned slot must be done before it is reused
+  T2S2_CUDA_TRY(cudaStreamSynchronize(st));
+  *net->hlr = lr;
+  T2S2_CUDA_TRY(cudaMemcpyAsync(net->dlr, net->hlr, sizeof(float), cudaMemcpyHostToDevice, st));
+  return T2S2_OK;
+}
+
+// One training step as a fixed sequence of launches (capturable): loss and
+// gradient, Adam update, step counter.
+t2s2_status train_launches(t2s2_mlp net, const float* P, int batch, const float* targets, const float* uu,
+                           cudaStream_t st) {
+  T2S2_TRY(loss_grad(net, P, batch, targets, uu, st));
+  TraceScope ts(kTrMlp, st, 10.0 * net->nparams, 4.0 * 7 * net->nparams);
+  adam_kernel<<<ew_blocks(net->nparams), 256, 0, st>>>(net->params, net->grads, net->adam_m, net->adam_v,
+                                                     net->nparams, net->dlr, net->dstep, 0.9f, 0.999f, 1e-8f);
+  step_increment_kernel<<<1, 1, 0, st>>>(net->dstep);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
+
 }  // namespace
 }  // namespace t2s2
 
@@ -452,16 +571,18 @@ t2s2_status t2s2_mlp_create(int in_dim, int hidden, int d, const int* m, int r, 
     o += (k == 0 ? 1 : r) * m[k] * (k == d - 1 ? 1 : r);
   }
   net->off[d] = o;
-  net->odim = o;
+  net->ncore = o;
+  net->odim = o + 1;  // the cores, then the log-scale
   {
     LossArgs a{};
-    a.odim = o; a.d = d; a.r = r; a.ru = ru; a.mmax = net->mmax;
+    a.odim = o + 1; a.ncore = o; a.d = d; a.r = r; a.ru = ru; a.mmax = net->mmax;
     if (loss_smem_floats(a) * sizeof(float) > 200 * 1024) {
       delete net;
       return T2S2_EINVAL;
     }
   }
   const long long h = hidden;
+  o = net->odim;  // network outputs
   net->oW1 = 0;
   net->ob1 = h * in_dim;
   net->oW2 = net->ob1 + h;
@@ -484,6 +605,11 @@ t2s2_status t2s2_mlp_create(int in_dim, int hidden, int d, const int* m, int r, 
   if (e == cudaSuccess) e = cudaMalloc(&net->adam_v, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&net->dstat, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&net->pbuf, sizeof(float) * in_dim);
+  if (e == cudaSuccess) e = cudaMalloc(&net->ystage, sizeof(double) * net->ncore);
+  if (e == cudaSuccess) e = cudaMalloc(&net->dstep, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&net->dlr, sizeof(float));
+  if (e == cudaSuccess) e = cudaMallocHost(&net->hlr, sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(net->dstep, 0, sizeof(long long));
   if (e == cudaSuccess) e = cudaMemcpy(net->params, p.data(), bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(net->grads, 0, bytes);
   if (e == cudaSuccess) e = cudaMemset(net->adam_m, 0, bytes);
@@ -502,10 +628,14 @@ t2s2_status t2s2_mlp_destroy(t2s2_mlp net) {
   if (!net) return T2S2_OK;
   void* bufs[] = {net->params, net->grads, net->adam_m, net->adam_v, net->z1, net->h1, net->z2, net->h2,
                   net->y,      net->dy,    net->dh,     net->dz,     net->loss, net->ws, net->dstat,
-                  net->pbuf};
+                  net->pbuf,   net->dstep, net->dlr,    net->ystage};
+  for (auto& g : net->graphs) cudaGraphExecDestroy(g.exec);
+  if (net->gstream) cudaStreamDestroy(net->gstream);
+  if (net->gev) cudaEventDestroy(net->gev);
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (net->hbuf) cudaFreeHost(net->hbuf);
+  if (net->hlr) cudaFreeHost(net->hlr);
   delete net;
   return T2S2_OK;
 }
@@ -576,22 +706,88 @@ t2s2_status t2s2_mlp_train_step(t2s2_mlp net, const float* P, int batch, const f
   if (!net || !P || !targets || !uu || batch < 1 || !(lr > 0.f)) return T2S2_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   T2S2_TRY(ensure_batch(net, batch));
+  T2S2_TRY(set_lr(net, lr, st));
   T2S2_CUDA_TRY(cudaMemsetAsync(net->dstat, 0, sizeof(int), st));
-  T2S2_TRY(loss_grad(net, P, batch, targets, uu, st));
+  T2S2_TRY(train_launches(net, P, batch, targets, uu, st));
   net->step += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float bc1 = 1.f - (float)std::pow(0.9, (double)net->step);
-  const float bc2 = 1.f - (float)std::pow(0.999, (double)net->step);
-  {
-    TraceScope ts(kTrMlp, st, 10.0 * net->nparams, 4.0 * 7 * net->nparams);
-    adam_kernel<<<ew_blocks(net->nparams), 256, 0, st>>>(net->params, net->grads, net->adam_m, net->adam_v,
-                                                       net->nparams, lr, b1, b2, 1e-8f, bc1, bc2);
-    T2S2_CUDA_TRY(cudaGetLastError());
-  }
   if (loss) {
     float l = 0.f;
     T2S2_TRY(mean_loss(net, batch, &l, st));
     *loss = l;
+  }
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_mlp_train(t2s2_mlp net, const float* P, int n, const float* targets, const float* uu, int batch,
+                           int steps, float lr, int use_graph, float* loss, void* stream) {
+  if (!net || !P || !targets || !uu || batch < 1 || n < batch || steps < 0 || !(lr > 0.f)) return T2S2_EINVAL;
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  cudaStream_t st = caller;
+  if (use_graph) {
+    // the legacy default stream cannot be captured: work on the network's
+    // own stream, ordered after the caller's prior work and before its later work
+    if (!net->gstream) {
+      T2S2_CUDA_TRY(cudaStreamCreateWithFlags(&net->gstream, cudaStreamNonBlocking));
+      T2S2_CUDA_TRY(cudaEventCreateWithFlags(&net->gev, cudaEventDisableTiming));
+    }
+    T2S2_CUDA_TRY(cudaEventRecord(net->gev, caller));
+    T2S2_CUDA_TRY(cudaStreamWaitEvent(net->gstream, net->gev, 0));
+    st = net->gstream;
+  }
+  T2S2_TRY(ensure_batch(net, batch));
+  T2S2_TRY(set_lr(net, lr, st));
+  T2S2_CUDA_TRY(cudaMemsetAsync(net->dstat, 0, sizeof(int), st));
+  const long per = (long)net->d * net->ru * net->mmax * net->ru;
+  const int slots = n - batch + 1;
+  int last_lo = 0;
+  for (int i = 0; i < steps; ++i) {
+    const int lo = (int)(((long)i * batch) % slots);
+    last_lo = lo;
+    const float* Pb = P + (long)lo * net->in_dim;
+    const float* Tb = targets + (long)lo * per;
+    const float* Ub = uu + lo;
+    if (!use_graph) {
+      T2S2_TRY(train_launches(net, Pb, batch, Tb, Ub, st));
+    } else {
+      cudaGraphExec_t exec = nullptr;
+      for (auto& e : net->graphs)
+        if (e.P == Pb && e.targets == Tb && e.uu == Ub && e.batch == batch) exec = e.exec;
+      if (exec) {
+        T2S2_CUDA_TRY(cudaGraphLaunch(exec, st));
+      } else {
+        // the first visit of a minibatch runs eagerly (sizing every workspace,
+        // so that nothing is allocated during capture), then the same launch
+        // sequence is captured for the later visits
+        T2S2_TRY(train_launches(net, Pb, batch, Tb, Ub, st));
+        cudaGraph_t graph = nullptr;
+        T2S2_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const t2s2_status cs = train_launches(net, Pb, batch, Tb, Ub, st);
+        const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (cs != T2S2_OK) {
+          if (graph) cudaGraphDestroy(graph);
+          return cs;
+        }
+        T2S2_CUDA_TRY(ce);
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        T2S2_CUDA_TRY(ie);
+        net->graphs.push_back({Pb, Tb, Ub, batch, exec});
+      }
+    }
+    net->step += 1;
+  }
+  if (loss) {
+    // the per-sample losses of the last step's minibatch
+    float l = 0.f;
+    T2S2_TRY(mean_loss(net, batch, &l, st));
+    *loss = l;
+    (void)last_lo;
+  } else {
+    T2S2_TRY(check_status(net, st));
+  }
+  if (st != caller) {
+    T2S2_CUDA_TRY(cudaEventRecord(net->gev, st));
+    T2S2_CUDA_TRY(cudaStreamWaitEvent(caller, net->gev, 0));
   }
   return T2S2_OK;
 }
@@ -604,21 +800,24 @@ t2s2_status t2s2_mlp_predict(t2s2_mlp net, const float* p, t2s2_tt* x, void* str
   T2S2_CUDA_TRY(cudaMemcpyAsync(dp, p, sizeof(float) * net->in_dim, cudaMemcpyDefault, st));
   T2S2_CUDA_TRY(cudaMemsetAsync(net->dstat, 0, sizeof(int), st));
   T2S2_TRY(forward(net, dp, 1, st));
+  {
+    UnpackArgs u;
+    u.y = net->y;
+    u.out = net->ystage;
+    for (int k = 0; k <= net->d; ++k) u.off[k] = net->off[k];
+    u.ncore = net->ncore;
+    TraceScope ts(kTrMlp, st, 3.0 * net->ncore, 12.0 * net->ncore);
+    unpack_cores_kernel<<<net->d, 256, 0, st>>>(u);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
   for (int k = 0; k < net->d; ++k) {
     const int ra = k == 0 ? 1 : net->r, rb = k == net->d - 1 ? 1 : net->r;
     const long n = (long)ra * net->m[k] * rb;
     if ((size_t)n > x->cap[k] || (x->m && x->m[k] != net->m[k])) return T2S2_EINVAL;
-    if (x->loc == T2S2_DEVICE) {
-      unpack_core_kernel<<<ew_blocks(n), 256, 0, st>>>(static_cast<double*>(x->cores[k]), net->y + net->off[k], n);
-      T2S2_CUDA_TRY(cudaGetLastError());
-    } else {
-      std::vector<float> hv(n);
-      T2S2_CUDA_TRY(cudaMemcpyAsync(hv.data(), net->y + net->off[k], sizeof(float) * n, cudaMemcpyDeviceToHost, st));
-      T2S2_CUDA_TRY(cudaStreamSynchronize(st));
-      double* dst = static_cast<double*>(x->cores[k]);
-      for (long i = 0; i < n; ++i) dst[i] = hv[i];
-    }
+    T2S2_CUDA_TRY(cudaMemcpyAsync(x->cores[k], net->ystage + net->off[k], sizeof(double) * n,
+                                  x->loc == T2S2_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   }
+  T2S2_CUDA_TRY(cudaStreamSynchronize(st));
   x->r[0] = 1;
   for (int k = 1; k < net->d; ++k) x->r[k] = net->r;
   x->r[net->d] = 1;

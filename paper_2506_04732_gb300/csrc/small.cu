@@ -17,6 +17,7 @@ namespace t2s2 {
 namespace {
 
 constexpr int kThreads = 512;
+constexpr size_t kJacobiMaxSmem = 200 * 1024;
 
 // G (c x c, row-major, ld c) -> L lower (G + shift I = L L^T), Linv = L^{-1}.
 __global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __restrict__ G, int c,
@@ -98,7 +99,8 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
                                                               int q, int transpose,
                                                               double* __restrict__ U,
                                                               double* __restrict__ s_out,
-                                                              double* __restrict__ V, int* sweeps_out) {
+                                                              double* __restrict__ V, int* sweeps_out,
+                                                              int prerotate) {
   // Working matrix W is rows x cols with rows >= cols (transposed input if p < q).
   extern __shared__ double sm[];
   const int rows = transpose ? q : p, cols = transpose ? p : q;
@@ -113,10 +115,102 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
     W[j * rows + i] = transpose ? A[j * q + i] : A[i * q + j];
   }
   for (int e = t; e < cols * cols; e += blockDim.x) Vs[e] = (e % cols == e / cols) ? 1.0 : 0.0;
+  __shared__ double fro2;
+  __shared__ double wsum[kThreads / 32];
   __syncthreads();
+  {
+    double acc = 0.0;
+    for (int e = t; e < rows * cols; e += blockDim.x) acc = fma(W[e], W[e], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((t & 31) == 0) wsum[t / 32] = acc;
+  }
+  __syncthreads();
+  if (t == 0) {  // fixed order: the result does not depend on timing
+    double acc = 0.0;
+    for (int w = 0; w < (int)blockDim.x / 32; ++w) acc += wsum[w];
+    fro2 = acc;
+  }
+  __syncthreads();
+  // a column whose squared norm is below this is zero to working precision
+  // (e.g. a direction the semidefinite Cholesky zeroed): rotating it only
+  // stirs roundoff, and the sweeps would never settle
+  const double negligible = 1e-32 * fro2;
   const int warp = t / 32, lane = t % 32, nwarps = blockDim.x / 32;
   const int npair = (cols + 1) / 2;  // round-robin with a dummy column when cols is odd
   const int ncol = 2 * npair;
+  // Binary32 pre-rotation.  A binary64 instruction costs a warp ~64 issue
+  // cycles on this part (2 DFMA/clk/SM), binary32 one: the sweeps run in
+  // binary32 on a rounded copy until its columns are orthogonal to ~1e-6,
+  // W <- W V32 in binary64, and the binary64 sweeps below (starting from
+  // V = V32) need one or two passes to converge quadratically.  Small
+  // singular values keep full binary64 relative accuracy: they come from
+  // binary64 column norms after the binary64 rotations.
+  if (prerotate) {
+    float* Wf = reinterpret_cast<float*>(nrm + cols);
+    float* Vf = Wf + rows * cols;
+    // keep Wt 8-byte aligned: pad the float arrays to an even count
+    double* Wt = reinterpret_cast<double*>(Vf + cols * cols + ((rows * cols + cols * cols) & 1));
+    for (int e = t; e < rows * cols; e += blockDim.x) Wf[e] = (float)W[e];
+    for (int e = t; e < cols * cols; e += blockDim.x) Vf[e] = (e % cols == e / cols) ? 1.f : 0.f;
+    const float negl32 = (float)(1e-14 * fro2);
+    for (int sw = 0; sw < 30; ++sw) {
+      if (t == 0) rotated = 0;
+      __syncthreads();
+      for (int round = 0; round < ncol - 1; ++round) {
+        for (int pr = warp; pr < npair; pr += nwarps) {
+          int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (ncol - 1);
+          int b = 1 + (ncol - 2 - pr + round) % (ncol - 1);
+          if (a >= cols || b >= cols) continue;
+          if (a > b) { int tmp = a; a = b; b = tmp; }
+          float* wa = Wf + a * rows;
+          float* wb = Wf + b * rows;
+          float alpha = 0.f, beta = 0.f, gamma = 0.f;
+          for (int i = lane; i < rows; i += 32) {
+            alpha = fmaf(wa[i], wa[i], alpha);
+            beta = fmaf(wb[i], wb[i], beta);
+            gamma = fmaf(wa[i], wb[i], gamma);
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+            beta += __shfl_xor_sync(0xffffffffu, beta, o);
+            gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+          }
+          if (gamma != 0.f && gamma * gamma > 1e-12f * alpha * beta && alpha > negl32 && beta > negl32) {
+            const float diff = beta - alpha, g2 = 2.f * gamma;
+            const float tf = (diff >= 0.f ? g2 : -g2) / (fabsf(diff) + sqrtf(fmaf(diff, diff, g2 * g2)));
+            const float cs = rsqrtf(fmaf(tf, tf, 1.f)), sn = cs * tf;
+            for (int i = lane; i < rows; i += 32) {
+              const float x = wa[i], y = wb[i];
+              wa[i] = cs * x - sn * y;
+              wb[i] = sn * x + cs * y;
+            }
+            float* va = Vf + a * cols;
+            float* vb = Vf + b * cols;
+            for (int i = lane; i < cols; i += 32) {
+              const float x = va[i], y = vb[i];
+              va[i] = cs * x - sn * y;
+              vb[i] = sn * x + cs * y;
+            }
+            if (lane == 0) rotated = 1;
+          }
+        }
+        __syncthreads();
+      }
+      if (!rotated) break;
+      __syncthreads();
+    }
+    // W <- W V32 and V <- V32, in binary64
+    for (int e = t; e < rows * cols; e += blockDim.x) {
+      const int i = e % rows, j = e / rows;
+      double acc = 0.0;
+      for (int k = 0; k < cols; ++k) acc = fma(W[k * rows + i], (double)Vf[j * cols + k], acc);
+      Wt[e] = acc;
+    }
+    __syncthreads();
+    for (int e = t; e < rows * cols; e += blockDim.x) W[e] = Wt[e];
+    for (int e = t; e < cols * cols; e += blockDim.x) Vs[e] = (double)Vf[e];
+    __syncthreads();
+  }
   int sweep = 0;
   for (sweep = 0; sweep < 60; ++sweep) {
     if (t == 0) rotated = 0;
@@ -141,7 +235,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
           beta += __shfl_xor_sync(0xffffffffu, beta, o);
           gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
         }
-        if (gamma != 0.0 && gamma * gamma > 1e-30 * alpha * beta) {
+        if (gamma != 0.0 && gamma * gamma > 1e-30 * alpha * beta && alpha > negligible && beta > negligible) {
           // Rotation angle in binary32 (only its orthogonality must be exact):
           // t = 2 gamma sign(beta - alpha) / (|beta - alpha| + sqrt((beta - alpha)^2 + 4 gamma^2)).
           // Near convergence a binary32 angle still cuts gamma by ~1e-7 per sweep.
@@ -252,15 +346,19 @@ t2s2_status jacobi_svd(const double* A, int p, int q, double* U, double* s, doub
   int transpose = p < q;
   int rows = transpose ? q : p, cols = transpose ? p : q;
   size_t smem = ((size_t)rows * cols + (size_t)cols * cols + cols) * sizeof(double);
+  // binary32 pre-rotation when its copies and the product buffer fit
+  const size_t extra = ((size_t)rows * cols + (size_t)cols * cols + 1) * sizeof(float) +
+                       (size_t)rows * cols * sizeof(double) + 16;
+  const int prerotate = (smem + extra <= kJacobiMaxSmem) ? 1 : 0;
+  if (prerotate) smem += extra;
   static bool attr = false;
   if (!attr) {
-    T2S2_CUDA_TRY(cudaFuncSetAttribute(
-        jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)((2 * kSmallMax * kSmallMax + kSmallMax) * sizeof(double))));
+    T2S2_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kJacobiMaxSmem));
     attr = true;
   }
   TraceScope ts(kTrSmall, st, 6.0 * 8 * (double)rows * cols * cols, 8.0 * (2.0 * p * q + q * q));
-  jacobi_svd_kernel<<<1, kThreads, smem, st>>>(A, p, q, transpose, U, s, V, sweeps);
+  jacobi_svd_kernel<<<1, kThreads, smem, st>>>(A, p, q, transpose, U, s, V, sweeps, prerotate);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }

@@ -15,4 +15,14 @@ t2s2_status chol_inv(const double* G, int c, double shift_rel, double* L, double
 t2s2_status jacobi_svd(const double* A, int p, int q, double* U, double* s, double* V, int* sweeps,
                        cudaStream_t st);
 
+// Shifted CholeskyQR3 of nlong vectors of length c in one cooperative launch
+// (cholqr.cu).  tall: W is nlong x c row-major, W = Q R (R = c x c upper);
+// wide: W is c x nlong row-major, W = R Q (R lower).  Plan first: false if
+// the grid cannot be co-resident or shared memory would not fit; max_grid > 0
+// caps the number of CTAs.
+bool cholqr3_plan(int nlong, int c, int max_grid, int* grid, int* per, size_t* smem);
+size_t cholqr3_scratch_doubles(int nlong, int c, int grid);
+t2s2_status cholqr3_fused(const double* W, double* Q, double* R, int nlong, int c, bool tall, double shift_rel,
+                          double* scratch, int* status, int grid, int per, size_t smem, cudaStream_t st);
+
 }  // namespace t2s2

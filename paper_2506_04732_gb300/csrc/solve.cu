@@ -721,7 +721,8 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
   long long local_iters = 0;
   while (res > tol && sweeps < max_sweeps && refinements < kMaxRefinements) {
     const size_t mk = cx.ar->mark();
-    const double tin = std::max(kInnerTol, 0.5 * tol / res);
+    // the inner target follows the stage's contraction arithmetic
+    const double tin = std::max(tc_stage ? kInnerTol : inner_tol_for(T2S2_FP32_REFINE), 0.5 * tol / res);
     // r = b - A x in FP64, rounded (r = b while x = 0)
     DevTT r;
     const DevTT* rhs = &b;

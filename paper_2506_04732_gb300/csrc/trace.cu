@@ -49,7 +49,10 @@ void drain_locked() {
 
 TraceScope::TraceScope(int f, cudaStream_t s, double fl, double by) : fam(f), st(s), flops(fl), bytes(by), slot(-1) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  if (g_on.load(std::memory_order_relaxed)) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  // no timing events inside a stream capture (they would become graph nodes)
+  if (g_on.load(std::memory_order_relaxed) && cudaStreamIsCapturing(st, &cap) == cudaSuccess &&
+      cap == cudaStreamCaptureStatusNone) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_recs.size() > 200000) drain_locked();
     Rec r{fam, get_event(), get_event(), flops, bytes};

@@ -174,8 +174,31 @@ __global__ void k_transpose(double* dst, const double* src, int r, int c) {
 }
 }  // namespace
 
+// Fused single-launch CholeskyQR3 when its grid fits (cholqr.cu), else the
+// pass-by-pass sequence below.
+static bool qr_fused(Ctx& cx, const double* W, int nlong, int c, bool tall, double* Q, double* R,
+                     t2s2_status* st) {
+  int grid = 0, per = 0;
+  size_t smem = 0;
+  if (!cholqr3_plan(nlong, c, cx.coop_ctas, &grid, &per, &smem)) return false;
+  const size_t mk = cx.ar->mark();
+  double* scratch = aget<double>(cx, cholqr3_scratch_doubles(nlong, c, grid));
+  if (!scratch) {
+    cx.ar->release(mk);
+    return false;
+  }
+  const double shift = 11.0 * ((double)nlong * c + (double)c * (c + 1)) * kUnit;
+  *st = cholqr3_fused(W, Q, R, nlong, c, tall, shift, scratch, cx.dstat, grid, per, smem, cx.st);
+  cx.ar->release(mk);
+  return true;
+}
+
 t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, double* R) {
   if (cols > kSmallMax || rows < cols || cols <= 0) return T2S2_EINVAL;
+  {
+    t2s2_status fs = T2S2_OK;
+    if (qr_fused(cx, W, rows, cols, true, Q, R, &fs)) return fs;
+  }
   size_t mk = cx.ar->mark();
   const int c = cols;
   double* G = aget<double>(cx, (size_t)c * c);
@@ -211,6 +234,10 @@ t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, dou
 
 t2s2_status lq_wide(Ctx& cx, const double* W, int rows, int cols, double* Q, double* Lout) {
   if (rows > kSmallMax || rows > cols || rows <= 0) return T2S2_EINVAL;
+  {
+    t2s2_status fs = T2S2_OK;
+    if (qr_fused(cx, W, cols, rows, false, Q, Lout, &fs)) return fs;
+  }
   size_t mk = cx.ar->mark();
   const int c = rows;
   double* G = aget<double>(cx, (size_t)c * c);

@@ -42,6 +42,9 @@ struct Ctx {
   // T2S2_FP64 (SIMT FP64 GEMM) or T2S2_TF32_REFINE / T2S2_BF16_REFINE
   // (tcgen05 GEMM).  QR, SVD and norms always run in FP64.
   int contract_prec = T2S2_FP64;
+  // CTAs a cooperative launch may use (0: the whole GPU); concurrent solves
+  // split the SMs so that their cooperative grids are co-resident
+  int coop_ctas = 0;
 };
 
 template <typename T>

@@ -40,7 +40,7 @@ def _unflat(flat, ref):
     return out
 
 
-def _setup(T, hidden=32, d=4, m=6, r=3, ru=5, batch=8, seed=0):
+def _setup(T, hidden=32, d=4, m=6, r=3, ru=5, batch=8, seed=0, target_rank=None):
     from paper_2506_04732_gb300 import problem as P
     net = T.WarmStartNet(15, hidden, [m] * d, r, ru, seed=seed)
     rng = np.random.default_rng(seed + 1)
@@ -50,7 +50,8 @@ def _setup(T, hidden=32, d=4, m=6, r=3, ru=5, batch=8, seed=0):
     params = {k: v.astype(np.float32).astype(np.float64) for k, v in params.items()}
     net.set_params(torch.tensor(_flat(params), dtype=torch.float32))
     Pm = rng.standard_normal((batch, 15)).astype(np.float32)
-    ranks = [1] + [int(rng.integers(1, ru + 1)) for _ in range(d - 1)] + [1]
+    top = ru if target_rank is None else target_rank
+    ranks = [1] + [int(rng.integers(1, top + 1)) for _ in range(d - 1)] + [1]
     targets = [W.random_tt(d, m, ranks, seed=seed * 100 + s) for s in range(batch)]
     op = P.build_operator(W.config1(d=d, n=m + 2))
     tg, uu = net.pack_targets(op, [T.TT.from_cores(t) for t in targets])
@@ -82,7 +83,8 @@ def test_adam_first_step_closed_form(T):
 
 
 def test_training_reduces_the_loss(T):
-    net, params, Pm, targets, tg, uu, _ = _setup(T, hidden=64, batch=32, seed=5)
+    # targets of rank <= 3, which the rank-3 output can represent
+    net, params, Pm, targets, tg, uu, _ = _setup(T, hidden=64, batch=32, seed=5, target_rank=3)
     P = torch.tensor(Pm, device="cuda")
     first = net.loss_grad(P, tg, uu)
     for _ in range(300):
@@ -94,9 +96,11 @@ def test_warm_start_saves_sweeps_and_keeps_the_answer(T):
     """Train on solutions the solver itself produced; on held-out problems the
     warm-started solve reaches the same tolerance in fewer sweeps in total."""
     from paper_2506_04732_gb300 import problem as P
+    # at d = 4, n = 16 this family needs ranks above 20 below ~3e-8 (the
+    # oracle's AMEn stalls at 2.5e-8 too), so the comparison runs to 1e-6
     d, n = 4, 16
     m = n - 2
-    rmax, tol = 20, 1e-8
+    rmax, tol = 20, 1e-6
 
     def solve(p, x0=None, net=None):
         op = P.build_operator(p)
@@ -137,3 +141,16 @@ def test_warm_start_saves_sweeps_and_keeps_the_answer(T):
         warm += iw.sweeps
     print(f"held-out sweeps: cold {cold} warm {warm}")
     assert cold > 0 and warm < cold
+
+
+def test_graph_replayed_training_matches_eager(T):
+    """CUDA-graph replays of the training step give the same parameters as eager launches."""
+    nets = []
+    for use_graph in (False, True):
+        net, params, Pm, targets, tg, uu, _ = _setup(T, hidden=32, batch=24, seed=9)
+        P = torch.tensor(Pm, device="cuda")
+        loss = net.train(P, tg, uu, batch=8, steps=12, lr=2e-3, use_graph=use_graph)
+        nets.append((net.params().cpu().numpy(), loss))
+    (pe, le), (pg, lg) = nets
+    assert np.array_equal(pe, pg)
+    assert le == lg
