@@ -44,10 +44,11 @@ def parse():
                     help="skip the precision-variant and grouped-contraction measurements")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle CPU work for the cpu_baseline sample")
-    ap.add_argument("--workload", default="steady", choices=["steady", "batched", "cn", "warm"],
+    ap.add_argument("--workload", default="steady", choices=["steady", "batched", "cn", "warm", "contract"],
                     help="steady: d=6 n=32 solve (headline); batched: 256 d=5 instances; "
                          "cn: Crank-Nicolson steps at d=7 n=64; warm: learned warm start "
-                         "(--instances training solves)")
+                         "(--instances training solves); contract: grouped core contractions of "
+                         "--instances d=5 problems in one launch")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--workers", type=int, default=8)
     return ap.parse_args()
@@ -378,6 +379,19 @@ def run_warm(args, T, P, W, torch):
     return 0
 
 
+def run_contract(args, T, P, W, torch):
+    """Grouped core contractions alone: BF16 / TF32 tensor-core and FP64 applies
+    of every core of --instances d=5 problems, one persistent launch each."""
+    c = measure_contraction(T, P, W, torch, instances=args.instances, reps=max(1, args.steps))
+    line = {"metric": "core-contraction TFLOP/s (grouped TT apply, BF16 tensor cores)",
+            "value": c["bf16"]["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": c["bf16"]["ms_per_launch"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 operands, fp32 accumulate, fp64 storage",
+            "data": "synthetic", "config": {"workload": c["workload"]}, "contraction": c}
+    print(json.dumps(line))
+    return 0
+
+
 def measure_contraction(T, P, W, torch, instances=256, reps=10):
     """Grouped core contractions (t2s2_apply_batched): every core of `instances`
     d=5 problems (n in {16,24,32,48}, TT ranks 16) in one persistent launch.
@@ -463,7 +477,7 @@ def main():
         import paper_2506_04732_gb300 as T
         from paper_2506_04732_gb300 import problem as P
         import workloads as W
-        fn = {"batched": run_batched, "cn": run_cn, "warm": run_warm}[args.workload]
+        fn = {"batched": run_batched, "cn": run_cn, "warm": run_warm, "contract": run_contract}[args.workload]
         return fn(args, T, P, W, torch)
     ws, rank, local = dist_env()
     import torch

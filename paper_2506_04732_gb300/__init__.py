@@ -266,6 +266,11 @@ class WarmStartNet:
 
     def _batch_ptrs(self, P, targets, uu, lo, hi):
         per = self.d * self.ru * self.mmax * self.ru
+        n = P.shape[0]
+        if P.dim() != 2 or P.shape[1] != self.in_dim or P.dtype != self._torch.float32 or not P.is_contiguous():
+            raise ValueError(f"P must be a contiguous float32 (N, {self.in_dim}) tensor")
+        if not (0 <= lo < hi <= n) or targets.numel() < n * per or uu.numel() < n:
+            raise ValueError("minibatch outside the training set")
         return (P.data_ptr() + 4 * lo * self.in_dim, targets.data_ptr() + 4 * lo * per, uu.data_ptr() + 4 * lo)
 
     def loss_grad(self, P, targets, uu, lo=0, hi=None):
@@ -286,6 +291,7 @@ class WarmStartNet:
 
     def train(self, P, targets, uu, batch, steps, lr, use_graph=True):
         """`steps` Adam steps cycling through the resident set; returns the last loss."""
+        self._batch_ptrs(P, targets, uu, 0, int(batch))  # shape checks
         loss = ctypes.c_float()
         _check(load().t2s2_mlp_train(self._h, P.data_ptr(), int(P.shape[0]), targets.data_ptr(), uu.data_ptr(),
                                      int(batch), int(steps), float(lr), int(bool(use_graph)), ctypes.byref(loss),
@@ -295,6 +301,8 @@ class WarmStartNet:
     def predict(self, p, x: "TT"):
         """Write the network's guess for parameter vector p (in_dim floats) into x."""
         v = self._torch.as_tensor(np.asarray(p, dtype=np.float32)).contiguous()
+        if v.numel() != self.in_dim:
+            raise ValueError(f"expected {self.in_dim} parameters, got {v.numel()}")
         s = x._struct()
         _check(load().t2s2_mlp_predict(self._h, v.data_ptr(), ctypes.byref(s), _stream_handle(None)),
                "t2s2_mlp_predict")

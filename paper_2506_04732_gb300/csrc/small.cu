@@ -199,16 +199,39 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
       if (!rotated) break;
       __syncthreads();
     }
-    // W <- W V32 and V <- V32, in binary64
+    // V32 is orthogonal only to ~1e-7: make it orthogonal in binary64 with
+    // two Newton-Schulz steps V <- V (3 I - V^T V) / 2 (quadratic: 1e-7 ->
+    // 1e-14 -> roundoff), so that W0 = W V^T stays exact for the caller
+    double* V2 = Wt + rows * cols;  // cols x cols
+    for (int e = t; e < cols * cols; e += blockDim.x) Vs[e] = (double)Vf[e];
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
+      for (int e = t; e < cols * cols; e += blockDim.x) {  // Wt <- V^T V
+        const int i = e % cols, j = e / cols;
+        double acc = 0.0;
+        for (int k = 0; k < cols; ++k) acc = fma(Vs[i * cols + k], Vs[j * cols + k], acc);
+        Wt[e] = acc;
+      }
+      __syncthreads();
+      for (int e = t; e < cols * cols; e += blockDim.x) {  // V2 <- V (3 I - V^T V) / 2
+        const int k = e % cols, j = e / cols;
+        double acc = 0.0;
+        for (int i = 0; i < cols; ++i) acc = fma(Vs[i * cols + k], ((i == j) ? 3.0 : 0.0) - Wt[j * cols + i], acc);
+        V2[e] = 0.5 * acc;
+      }
+      __syncthreads();
+      for (int e = t; e < cols * cols; e += blockDim.x) Vs[e] = V2[e];
+      __syncthreads();
+    }
+    // W <- W V, in binary64
     for (int e = t; e < rows * cols; e += blockDim.x) {
       const int i = e % rows, j = e / rows;
       double acc = 0.0;
-      for (int k = 0; k < cols; ++k) acc = fma(W[k * rows + i], (double)Vf[j * cols + k], acc);
+      for (int k = 0; k < cols; ++k) acc = fma(W[k * rows + i], Vs[j * cols + k], acc);
       Wt[e] = acc;
     }
     __syncthreads();
     for (int e = t; e < rows * cols; e += blockDim.x) W[e] = Wt[e];
-    for (int e = t; e < cols * cols; e += blockDim.x) Vs[e] = (double)Vf[e];
     __syncthreads();
   }
   int sweep = 0;
@@ -275,7 +298,9 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
             va[i] = cs * x - sn * y;
             vb[i] = sn * x + cs * y;
           }
-          if (lane == 0) rotated = 1;
+          // a sweep whose rotations were all below 1e-8 (relative) leaves
+          // off-diagonals of ~1e-16 (quadratic convergence): it is the last
+          if (lane == 0 && gamma * gamma > 1e-16 * alpha * beta) rotated = 1;
         }
       }
       __syncthreads();
@@ -348,7 +373,7 @@ t2s2_status jacobi_svd(const double* A, int p, int q, double* U, double* s, doub
   size_t smem = ((size_t)rows * cols + (size_t)cols * cols + cols) * sizeof(double);
   // binary32 pre-rotation when its copies and the product buffer fit
   const size_t extra = ((size_t)rows * cols + (size_t)cols * cols + 1) * sizeof(float) +
-                       (size_t)rows * cols * sizeof(double) + 16;
+                       ((size_t)rows * cols + (size_t)cols * cols) * sizeof(double) + 16;
   const int prerotate = (smem + extra <= kJacobiMaxSmem) ? 1 : 0;
   if (prerotate) smem += extra;
   static bool attr = false;

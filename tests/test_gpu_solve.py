@@ -155,8 +155,11 @@ def test_solve_batched_matches_sequential(T):
     for i, p in enumerate(probs):
         assert infos[i].status == 0 and infos[i].residual <= 1e-8
         seq = T.t2s2_solve(ops[i], bs[i], xs_seq[i], 1e-8, 16, 50)
-        # identical arithmetic on each instance: same iterates
-        assert abs(seq.residual - infos[i].residual) <= 1e-12
+        # the batched solve gives each instance a share of the SMs, which
+        # changes the grid (and so the summation order) of its cooperative
+        # kernels: the same iterates up to rounding, the same tolerance
+        assert seq.residual <= 1e-8 and abs(seq.sweeps - infos[i].sweeps) <= 1
+        assert T.t2s2_diff_norm(ops[i], xs[i], xs_seq[i]) <= 1e-6 * T.t2s2_norm(ops[i], xs_seq[i])
         ops_o = O.build(p)
         r = OS.residual(O.ttm_cores(ops_o), O.source_tt(p, ops_o), xs[i].cores())
         assert r <= 1.01e-8

@@ -211,14 +211,18 @@ def warm_features(p: Problem) -> np.ndarray:
     """Input vector of the warm-start network for a config4-style problem.
 
     15 values, each scaled to about [-1, 1]: log10(eps / (|beta| L)) + 3, the
-    6 components of beta, the 4 amplitudes (a - 0.75) * 4, the 2 frequencies
-    w - 2 and the 2 centres 2 mu.  (An input width of 11 cannot hold beta,
-    the diffusion ratio and 8 source parameters; 15 can.)
+    components of beta (zero-padded or cut to 6), the 4 amplitudes
+    (a - 0.75) * 4, the 2 frequencies w - 2 and the 2 centres 2 mu.  (An input
+    width of 11 cannot hold beta, the diffusion ratio and 8 source parameters
+    at d = 6; 15 can.)
     """
     beta = np.asarray(p.beta, dtype=np.float64)
     ratio = p.eps / (EDGE_LENGTH * float(np.linalg.norm(beta)))
+    b6 = np.zeros(6)
+    b6[:min(6, beta.size)] = beta[:6]
     a, w, mu = p.params[:4], p.params[4:6], p.params[6:8]
-    f = np.concatenate([[math.log10(ratio) + 3.0], beta, (a - 0.75) * 4.0, w - 2.0, 2.0 * mu])
+    f = np.concatenate([[math.log10(ratio) + 3.0], b6, (a - 0.75) * 4.0, w - 2.0, 2.0 * mu])
+    assert f.size == WARM_IN_DIM
     return f.astype(np.float32)
 
 
