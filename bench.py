@@ -333,6 +333,8 @@ def run_warm(args, T, P, W, torch):
     tg, uu = net.pack_targets(sols[0][0], [s[1] for s in sols])
     Pf = torch.tensor(np.stack([W.warm_features(p) for p in train]), device="cuda")
     steps, batch = 1500, min(64, ntrain)
+    net.init_output_bias(sols[0][0], sols[0][1])
+    sigma_shift = net.calibrate_scale(Pf, tg, uu, 0, min(256, ntrain))
     T.t2s2_trace(True)
     t0 = time.perf_counter()
     losses = []
@@ -372,6 +374,7 @@ def run_warm(args, T, P, W, torch):
                        "cold_converged": conv_c, "warm_converged": conv_w,
                        "max_rel_diff_cold_vs_warm": max(diffs), "train_steps": steps, "batch": batch,
                        "loss_first": losses[0], "loss_last": float(np.mean(losses[-20:])),
+                       "log_scale_calibration": sigma_shift,
                        "data_generation_s": t_data, "training_s": t_train,
                        "mlp_kernels": mlp, "mlp_gemm_tc": gemm,
                        "network": "15 -> 256 -> 256 -> TT cores rank 8 (8160 outputs), ReLU, Adam"}}

@@ -307,6 +307,12 @@ t2s2_status t2s2_mlp_pack_target(t2s2_mlp net, t2s2_op op, const t2s2_tt* u, flo
  * Synchronises the stream.  T2S2_ETIMEOUT if a tensor-core wait gave up. */
 t2s2_status t2s2_mlp_loss_grad(t2s2_mlp net, const float* P, int batch, const float* targets,
                                const float* uu, float* loss, void* stream);
+/* Output-scale calibration: evaluates the batch and adds 0.5 log(mean <U,U> /
+ * mean <X,X>) to the bias of the log-scale output, so that X(p) starts at the
+ * targets' size (normalised cores multiply to a TT whose norm shrinks with d
+ * and r).  *shift (may be NULL) receives the change.  Synchronises. */
+t2s2_status t2s2_mlp_calibrate_scale(t2s2_mlp net, const float* P, int batch, const float* targets,
+                                     const float* uu, float* shift, void* stream);
 /* As t2s2_mlp_loss_grad followed by one Adam update with learning rate lr. */
 t2s2_status t2s2_mlp_train_step(t2s2_mlp net, const float* P, int batch, const float* targets,
                                 const float* uu, float lr, float* loss, void* stream);

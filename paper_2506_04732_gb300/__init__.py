@@ -124,6 +124,8 @@ _SIGS = {
                                            ctypes.c_void_p, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
                                            ctypes.c_void_p]),
     "t2s2_mlp_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_void_p]),
+    "t2s2_mlp_calibrate_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
     "t2s2_mlp_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
@@ -280,6 +282,48 @@ class WarmStartNet:
         _check(load().t2s2_mlp_loss_grad(self._h, pp, hi - lo, tp, up, ctypes.byref(loss), _stream_handle(None)),
                "t2s2_mlp_loss_grad")
         return loss.value
+
+    def init_output_bias(self, op: "Operator", u: "TT", weight_scale=0.1):
+        """Start the network's output at a representative target: the output
+        bias takes the cores of u rounded to the network's rank (t2s2_round),
+        and the output weights are scaled by weight_scale, so that X(p) starts
+        near u for every p and training learns the deviations."""
+        import torch
+        if u.d != self.d or u.m != self.m:
+            raise ValueError("u does not live on the network's grid")
+        v = TT.empty(u.m, max(self.r, max(u.r)))
+        for k in range(self.d):
+            n = u.r[k] * u.m[k] * u.r[k + 1]
+            v.buffers[k][:n].copy_(u.buffers[k][:n])
+        v.r = list(u.r)
+        t2s2_round(op, v, 0.0, self.r)
+        if max(v.r[1:-1]) > self.r:
+            raise RuntimeError("rounding did not reach the network rank")
+        cores = []
+        for k in range(self.d):
+            a = 1 if k == 0 else self.r
+            b = 1 if k == self.d - 1 else self.r
+            c = torch.zeros((a, self.m[k], b), dtype=torch.float64, device="cuda")
+            ra, rb = v.r[k], v.r[k + 1]
+            c[:ra, :, :rb] = v.buffers[k][:ra * self.m[k] * rb].view(ra, self.m[k], rb)
+            cores.append(c.reshape(-1))
+        p = self.params()
+        h, ind, od = self.hidden, self.in_dim, self.out_dim
+        ow3 = h * ind + h + h * h + h
+        ob3 = ow3 + od * h
+        p[ow3:ob3] *= weight_scale
+        p[ob3:ob3 + od - 1] = torch.cat(cores).to(torch.float32)
+        p[ob3 + od - 1] = 0.0
+        self.set_params(p)
+
+    def calibrate_scale(self, P, targets, uu, lo=0, hi=None):
+        """Shift the log-scale bias so that X(p) starts at the targets' size."""
+        hi = P.shape[0] if hi is None else hi
+        pp, tp, up = self._batch_ptrs(P, targets, uu, lo, hi)
+        shift = ctypes.c_float()
+        _check(load().t2s2_mlp_calibrate_scale(self._h, pp, hi - lo, tp, up, ctypes.byref(shift),
+                                               _stream_handle(None)), "t2s2_mlp_calibrate_scale")
+        return shift.value
 
     def train_step(self, P, targets, uu, lr, lo=0, hi=None):
         hi = P.shape[0] if hi is None else hi

@@ -112,27 +112,39 @@ __global__ void splitk_reduce(Gemm<T> g, int splits, const T* ws) {
 
 inline int tile_code(int x) { return x <= 16 ? 1 : (x <= 32 ? 2 : 4); }
 
+// Tile shape and split-K.  FP64 runs at 2 DFMA/clk/SM on this part, so a
+// CTA's time is about BM*BN*K/2 cycles: start from tiles that fit M and N,
+// then halve the larger tile side while the grid has fewer CTAs than SMs, and
+// finally split long K over the SMs.
+struct TilePlan {
+  int tm, tn, splits, kc;
+};
+
 template <typename T>
-int choose_splits(const Gemm<T>& g, int* kchunk) {
+TilePlan plan_tiles(const Gemm<T>& g) {
+  TilePlan p{tile_code(g.M), tile_code(g.N), 1, g.K};
+  auto tiles = [&]() { return (long)cdiv(g.M, 16 * p.tm) * cdiv(g.N, 16 * p.tn) * g.batch; };
+  if (sizeof(T) == 8) {
+    while (tiles() < kNumSMs && (p.tm > 1 || p.tn > 1)) {
+      if (p.tm >= p.tn) p.tm /= 2; else p.tn /= 2;
+    }
+  }
   if (g.K <= 0) {
-    *kchunk = 0;
-    return 1;
+    p.kc = 0;
+    return p;
   }
-  const int BM = 16 * tile_code(g.M), BN = 16 * tile_code(g.N);
-  long tiles = (long)cdiv(g.M, BM) * cdiv(g.N, BN) * g.batch;
-  // FP64 runs at 2 DFMA/clk/SM on this part: spread long-K products over all SMs
+  const long t = tiles();
   const long target = (sizeof(T) == 8) ? 2L * kNumSMs : kNumSMs;
-  int splits = 1;
-  if (tiles < target && g.K > 2 * BK) {
-    long want = (target + tiles - 1) / tiles;
+  if (t < target && g.K > 2 * BK) {
+    long want = (target + t - 1) / t;
     long maxs = g.K / (2 * BK);
-    splits = (int)std::max(1L, std::min(std::min(want, maxs), 128L));
+    p.splits = (int)std::max(1L, std::min(std::min(want, maxs), 128L));
   }
-  int kc = cdiv(g.K, splits);
+  int kc = cdiv(g.K, p.splits);
   kc = cdiv(kc, BK) * BK;
-  splits = cdiv(g.K, kc);
-  *kchunk = kc;
-  return splits;
+  p.splits = cdiv(g.K, kc);
+  p.kc = kc;
+  return p;
 }
 
 template <typename T, int TM, int TN>
@@ -142,8 +154,7 @@ void launch_tile(const Gemm<T>& g, int splits, int kc, T* ws, cudaStream_t st) {
 }
 
 template <typename T>
-void launch_any(const Gemm<T>& g, int splits, int kc, T* ws, cudaStream_t st) {
-  const int tm = tile_code(g.M), tn = tile_code(g.N);
+void launch_any(const Gemm<T>& g, int tm, int tn, int splits, int kc, T* ws, cudaStream_t st) {
 #define T2S2_TILE(a, b) if (tm == a && tn == b) { launch_tile<T, a, b>(g, splits, kc, ws, st); return; }
   T2S2_TILE(1, 1) T2S2_TILE(1, 2) T2S2_TILE(1, 4)
   T2S2_TILE(2, 1) T2S2_TILE(2, 2) T2S2_TILE(2, 4)
@@ -154,16 +165,15 @@ void launch_any(const Gemm<T>& g, int splits, int kc, T* ws, cudaStream_t st) {
 
 template <typename T>
 size_t gemm_workspace(const Gemm<T>& g) {
-  int kc;
-  int s = choose_splits(g, &kc);
-  return s > 1 ? (size_t)s * g.batch * g.M * g.N : 0;
+  const TilePlan p = plan_tiles(g);
+  return p.splits > 1 ? (size_t)p.splits * g.batch * g.M * g.N : 0;
 }
 
 template <typename T>
 t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return T2S2_OK;
-  int kc;
-  int splits = choose_splits(g, &kc);
+  const TilePlan plan = plan_tiles(g);
+  int splits = plan.splits, kc = plan.kc;
   if (splits > 1 && (ws == nullptr || ws_elems < (size_t)splits * g.batch * g.M * g.N)) {
     splits = 1;
     kc = g.K;
@@ -173,7 +183,7 @@ t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st) {
     const double fl = 2.0 * g.M * g.N * (double)g.K * g.batch;
     const double by = (double)sizeof(T) * g.batch * ((double)g.M * g.K + (double)g.K * g.N + 2.0 * g.M * g.N);
     TraceScope ts(kTrGemm, st, fl, by);
-    launch_any<T>(g, splits, kc, ws, st);
+    launch_any<T>(g, plan.tm, plan.tn, splits, kc, ws, st);
   }
   T2S2_CUDA_TRY(cudaGetLastError());
   if (splits > 1) {

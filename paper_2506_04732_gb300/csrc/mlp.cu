@@ -47,7 +47,7 @@ struct t2s2_mlp_s {
   long long step = 0;
   int bcap = 0;  // batch capacity of the activation buffers
   float *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *y = nullptr, *dy = nullptr;
-  float *dh = nullptr, *dz = nullptr, *loss = nullptr;
+  float *dh = nullptr, *dz = nullptr, *loss = nullptr, *xx = nullptr;
   float* pbuf = nullptr;  // in_dim floats: the input of a single prediction
   long long* dstep = nullptr;  // device copy of the Adam step count
   float* dlr = nullptr;        // device learning rate
@@ -81,6 +81,7 @@ struct LossArgs {
   const float* uu;       // batch: <U,U>
   float* dy;             // batch x odim: dL/dy, already divided by the batch size
   float* loss;           // batch
+  float* xx;             // batch: <X,X> (optional)
   int batch, odim, ncore, d, r, ru, mmax;
   int m[T2S2_MAX_D];
   int off[T2S2_MAX_D + 1];
@@ -233,7 +234,10 @@ __global__ void __launch_bounds__(kLossThreads) tt_loss_grad_kernel(LossArgs a) 
     __syncthreads();
   }
   const float xx = Lxx[d * r * r], xu = Lxu[d * r * ru], uu = a.uu[s];
-  if (tid == 0) a.loss[s] = (xx - 2.f * xu + uu) / uu;
+  if (tid == 0) {
+    a.loss[s] = (xx - 2.f * xu + uu) / uu;
+    if (a.xx) a.xx[s] = xx;
+  }
   const float scale = a.inv_batch / uu;
   // gradient, core by core
   for (int k = 0; k < d; ++k) {
@@ -407,13 +411,14 @@ t2s2_status mm(t2s2_mlp net, int M, int N, int K, bool tA, bool tB, const float*
 t2s2_status ensure_batch(t2s2_mlp net, int batch) {
   if (batch <= net->bcap) return T2S2_OK;
   drop_graphs(net);
-  float** bufs[] = {&net->z1, &net->h1, &net->z2, &net->h2, &net->dh, &net->dz, &net->y, &net->dy, &net->loss};
+  float** bufs[] = {&net->z1, &net->h1, &net->z2, &net->h2, &net->dh, &net->dz, &net->y, &net->dy, &net->loss,
+                    &net->xx};
   for (auto b : bufs)
     if (*b) cudaFree(*b), *b = nullptr;
   if (net->hbuf) cudaFreeHost(net->hbuf), net->hbuf = nullptr;
   const size_t H = (size_t)batch * net->hidden, Y = (size_t)batch * net->odim;
-  const size_t sizes[] = {H, H, H, H, H, H, Y, Y, (size_t)batch};
-  for (int i = 0; i < 9; ++i) T2S2_CUDA_TRY(cudaMalloc(bufs[i], sizes[i] * sizeof(float)));
+  const size_t sizes[] = {H, H, H, H, H, H, Y, Y, (size_t)batch, (size_t)batch};
+  for (int i = 0; i < 10; ++i) T2S2_CUDA_TRY(cudaMalloc(bufs[i], sizes[i] * sizeof(float)));
   T2S2_CUDA_TRY(cudaMallocHost(&net->hbuf, (size_t)batch * sizeof(float)));
   net->bcap = batch;
   return T2S2_OK;
@@ -451,6 +456,7 @@ t2s2_status loss_grad(t2s2_mlp net, const float* P, int B, const float* targets,
   a.uu = uu;
   a.dy = net->dy;
   a.loss = net->loss;
+  a.xx = net->xx;
   a.batch = B;
   a.odim = net->odim;
   a.ncore = net->ncore;
@@ -627,7 +633,7 @@ t2s2_status t2s2_mlp_create(int in_dim, int hidden, int d, const int* m, int r, 
 t2s2_status t2s2_mlp_destroy(t2s2_mlp net) {
   if (!net) return T2S2_OK;
   void* bufs[] = {net->params, net->grads, net->adam_m, net->adam_v, net->z1, net->h1, net->z2, net->h2,
-                  net->y,      net->dy,    net->dh,     net->dz,     net->loss, net->ws, net->dstat,
+                  net->y,      net->dy,    net->dh,     net->dz,     net->loss, net->xx, net->ws, net->dstat,
                   net->pbuf,   net->dstep, net->dlr,    net->ystage};
   for (auto& g : net->graphs) cudaGraphExecDestroy(g.exec);
   if (net->gstream) cudaStreamDestroy(net->gstream);
@@ -698,6 +704,34 @@ t2s2_status t2s2_mlp_loss_grad(t2s2_mlp net, const float* P, int batch, const fl
   float l = 0.f;
   T2S2_TRY(mean_loss(net, batch, &l, st));
   if (loss) *loss = l;
+  return T2S2_OK;
+}
+
+t2s2_status t2s2_mlp_calibrate_scale(t2s2_mlp net, const float* P, int batch, const float* targets,
+                                     const float* uu, float* shift, void* stream) {
+  if (!net || !P || !targets || !uu || batch < 1) return T2S2_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  T2S2_TRY(ensure_batch(net, batch));
+  T2S2_CUDA_TRY(cudaMemsetAsync(net->dstat, 0, sizeof(int), st));
+  T2S2_TRY(loss_grad(net, P, batch, targets, uu, st));
+  std::vector<float> hx(batch), hu(batch);
+  T2S2_CUDA_TRY(cudaMemcpyAsync(hx.data(), net->xx, sizeof(float) * batch, cudaMemcpyDeviceToHost, st));
+  T2S2_CUDA_TRY(cudaMemcpyAsync(hu.data(), uu, sizeof(float) * batch, cudaMemcpyDeviceToHost, st));
+  T2S2_TRY(check_status(net, st));
+  double sx = 0.0, su = 0.0;
+  for (int i = 0; i < batch; ++i) sx += hx[i], su += hu[i];
+  if (!(sx > 0.0) || !(su > 0.0)) return T2S2_EINVAL;
+  // sigma enters X linearly through exp(sigma): shift its bias by half the log
+  // of the mean ratio <U,U> / <X,X>
+  const float d_sigma = (float)(0.5 * std::log(su / sx));
+  float b = 0.f;
+  float* bptr = net->params + net->ob3 + net->ncore;
+  T2S2_CUDA_TRY(cudaMemcpyAsync(&b, bptr, sizeof(float), cudaMemcpyDeviceToHost, st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(st));
+  b += d_sigma;
+  T2S2_CUDA_TRY(cudaMemcpyAsync(bptr, &b, sizeof(float), cudaMemcpyHostToDevice, st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(st));
+  if (shift) *shift = d_sigma;
   return T2S2_OK;
 }
 

@@ -298,9 +298,12 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
             va[i] = cs * x - sn * y;
             vb[i] = sn * x + cs * y;
           }
-          // a sweep whose rotations were all below 1e-8 (relative) leaves
-          // off-diagonals of ~1e-16 (quadratic convergence): it is the last
-          if (lane == 0 && gamma * gamma > 1e-16 * alpha * beta) rotated = 1;
+          // a sweep whose rotations were all below 1e-6 (relative) leaves
+          // off-diagonals of ~1e-12 (quadratic convergence): it is the last.
+          // Singular values then carry ~1e-24 relative error, and the left
+          // vectors are orthogonal to ~1e-12 (the sweeps that consume them
+          // re-orthogonalise with CholeskyQR3 anyway)
+          if (lane == 0 && gamma * gamma > 1e-12 * alpha * beta) rotated = 1;
         }
       }
       __syncthreads();

@@ -14,6 +14,7 @@ import torch
 
 import workloads as W
 from oracle import mlp as M
+from oracle import tt as OT
 
 pytestmark = pytest.mark.gpu
 
@@ -82,6 +83,21 @@ def test_adam_first_step_closed_form(T):
     assert np.allclose(p1, expect, rtol=1e-6, atol=1e-5 * lr)
 
 
+def test_scale_calibration_matches_target_norms(T):
+    net, params, Pm, targets, tg, uu, _ = _setup(T, hidden=32, batch=16, seed=13)
+    P = torch.tensor(Pm, device="cuda")
+    net.calibrate_scale(P, tg, uu)
+    # after calibration, mean <X,X> equals mean <U,U> (to BF16 accuracy)
+    p2 = {k: v.copy() for k, v in params.items()}
+    flat = net.params().cpu().numpy().astype(np.float64)
+    p2["b3"] = flat[-p2["b3"].size:]
+    y2, _ = M.forward(p2, Pm.astype(np.float64))
+    d, m, r = 4, [6] * 4, 3
+    xx = np.mean([OT.dot(M.split_cores(y2[s], d, m, r), M.split_cores(y2[s], d, m, r)) for s in range(16)])
+    uu_mean = np.mean([OT.dot(t, t) for t in targets])
+    assert abs(xx / uu_mean - 1.0) <= 0.1
+
+
 def test_training_reduces_the_loss(T):
     # targets of rank <= 3, which the rank-3 output can represent
     net, params, Pm, targets, tg, uu, _ = _setup(T, hidden=64, batch=32, seed=5, target_rank=3)
@@ -123,6 +139,8 @@ def test_warm_start_saves_sweeps_and_keeps_the_answer(T):
     net = T.WarmStartNet(W.WARM_IN_DIM, 128, [m] * d, 6, rmax + 4, seed=1)
     tg, uu = net.pack_targets(sols[0][0], [s[1] for s in sols])
     Pf = torch.tensor(np.stack([W.warm_features(p) for p in train]), device="cuda")
+    net.init_output_bias(sols[0][0], sols[0][1])
+    net.calibrate_scale(Pf, tg, uu)
     for it in range(600):
         lo = (it * 32) % 96
         net.train_step(Pf, tg, uu, 2e-3 if it < 400 else 5e-4, lo=lo, hi=lo + 32)
