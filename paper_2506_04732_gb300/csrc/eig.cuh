@@ -138,7 +138,11 @@ __device__ bool warp_eig(const TA* A, int lda, int r, EigSmem& s, cf* lam, cf* V
     while (l > 0) {
       const float sub = cabsf(t(l, l - 1));
       const float dg = cabsf(t(l - 1, l - 1)) + cabsf(t(l, l));
-      if (sub <= eps * (dg > 0.f ? dg : tnorm)) break;
+      // deflate when the subdiagonal is negligible relative to its diagonal
+      // neighbours or, norm-wise, to the matrix (a backward-stable
+      // perturbation of eps ||T||; tiny eigenvalues otherwise wait for a
+      // relative test that binary32 noise never lets them pass)
+      if (sub <= eps * fmaxf(dg, tnorm)) break;
       --l;
     }
     __syncwarp();
