@@ -80,7 +80,7 @@ def _vec_right(Psi, U, F):
     return np.einsum("aib,bh,gih->ag", U, Psi, F)
 
 
-def amen_solve(A, b, x0, tol, rmax, max_sweeps=50, kick=4, seed=0, dense_max=4096,
+def amen_solve(A, b, x0, tol, rmax, max_sweeps=50, kick=8, seed=0, dense_max=4096,
                verbose=False, history=None):
     """Solve A x = b in TT format (A: TT-matrix cores, b and x0: TT cores).
 
