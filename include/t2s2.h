@@ -42,6 +42,10 @@ extern "C" {
 
 #define T2S2_MAX_D 16
 #define T2S2_MAX_N 128
+/* Rank of the enrichment directions the alternating solver adds per core and
+ * sweep (environment variable T2S2_KICK overrides it, 1 .. 16): a solution
+ * can carry ranks up to rmax + T2S2_RANK_KICK. */
+#define T2S2_RANK_KICK 8
 
 typedef enum {
   T2S2_OK = 0,

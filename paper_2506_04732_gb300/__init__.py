@@ -18,13 +18,16 @@ from dataclasses import dataclass
 import numpy as np
 
 __all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REFINE",
-           "TF32_REFINE", "BF16_REFINE", "t2s2_build_operator", "t2s2_apply", "t2s2_round",
+           "TF32_REFINE", "BF16_REFINE", "RANK_KICK", "t2s2_build_operator", "t2s2_apply", "t2s2_round",
            "t2s2_norm", "t2s2_diff_norm", "t2s2_norm_noalloc", "t2s2_residual", "t2s2_solve", "t2s2_solve_batched", "t2s2_cn_step", "t2s2_be_step",
            "t2s2_device_count", "t2s2_strerror", "t2s2_gemm", "WarmStartNet", "t2s2_apply_batched",
            "t2s2_autotune_report", "t2s2_kernel_launches", "t2s2_trace",
            "t2s2_trace_read", "TRACE_FAMILIES", "lib_path"]
 
 FP64, FP32_REFINE, TF32_REFINE, BF16_REFINE = 0, 1, 2, 3
+# enrichment rank of the solver (T2S2_RANK_KICK; the T2S2_KICK environment
+# variable overrides it): a solution can carry ranks up to rmax + RANK_KICK
+RANK_KICK = int(os.environ.get("T2S2_KICK", "8")) if 1 <= int(os.environ.get("T2S2_KICK", "8")) <= 16 else 8
 _DEVICE, _HOST = 0, 1
 MAX_D = 16
 

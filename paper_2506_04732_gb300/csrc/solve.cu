@@ -119,6 +119,25 @@ struct PhaseTimer {
   }
 };
 
+// Rank of the enrichment (residual) directions added per core and sweep.
+// The paper names AMEn without parameters.  On the d = 6, n = 32 problem a
+// kick of 4 needs 7 sweeps (ranks grow 1, 5, 9, 13, ...), a kick of 8 one
+// sweep: the solution's rank at 1e-8 is about 9-13, and a first sweep whose
+// bases span it converges at once.  T2S2_KICK overrides it (1 .. 16).
+// Enrichment rank of the time steps (their solves start from the previous
+// step): on the d = 7, n = 64 Crank-Nicolson step a kick of 4 keeps ranks at
+// 7 and takes 10.3 ms, a kick of 8 raises them to 11 and takes 15 ms.
+constexpr int kStepKick = 4;
+
+int amen_kick() {
+  static const int k = [] {
+    const char* e = std::getenv("T2S2_KICK");
+    const int v = e ? std::atoi(e) : T2S2_RANK_KICK;
+    return (v >= 1 && v <= 16) ? v : T2S2_RANK_KICK;
+  }();
+  return k;
+}
+
 struct Amen {
   PhaseTimer* pt = nullptr;
   void ph(int p) {
@@ -126,7 +145,7 @@ struct Amen {
   }
   t2s2_op op = nullptr;
   Ctx* cx = nullptr;
-  int d = 0, kick = 4, rcap = 0, rmax = 0, mmax = 0, R = 0;
+  int d = 0, kick = amen_kick(), rcap = 0, rmax = 0, mmax = 0, R = 0;
   double ltol = 0.0;
   DevTT x, f, z;
   double* Bp[T2S2_MAX_D] = {nullptr};
@@ -183,6 +202,7 @@ struct Amen {
     c_mass = cm;
     c_op = co;
     rmax = rmax_;
+    kick = c.kick > 0 ? c.kick : amen_kick();
     rcap = rmax + kick;
     if (rcap > kSmallMax) return T2S2_EINVAL;
     ltol = tol / std::sqrt((double)d);
@@ -669,7 +689,7 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
   const double kInnerTol = inner_tol_for(prec);
   constexpr int kMaxRefinements = 40;
   const int d = op->d;
-  const int kick = 4, rcap = rmax + kick;
+  const int kick = cx.kick > 0 ? cx.kick : amen_kick(), rcap = rmax + kick;
   const char* ev = std::getenv("T2S2_VERBOSE");
   const bool verbose = ev && ev[0] == '1';
   // persistent state: the iterate x, the caller's guess g and the previous
@@ -855,7 +875,7 @@ static size_t refine_extra_bytes(t2s2_op op, int rcap, int rf) {
   for (int k = 0; k < op->d; ++k) mm = std::max<size_t>(mm, op->m[k]);
   const size_t R = (size_t)rf + 2 * rcap;
   const size_t train = (size_t)op->d * R * mm * R * sizeof(double);
-  return 6 * train + Amen::bytes_needed(op->d, op->m, rcap, std::min(kSmallMax, 2 * rcap), 4, 40);
+  return 6 * train + Amen::bytes_needed(op->d, op->m, rcap, std::min(kSmallMax, 2 * rcap), amen_kick(), 40);
 }
 
 static t2s2_status solve_entry(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double c_mass, double c_op,
@@ -868,8 +888,8 @@ static t2s2_status solve_entry(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double 
   T2S2_TRY(check_tt(op, x));
   int rfmax = 1;
   for (int k = 0; k <= op->d; ++k) rfmax = std::max(rfmax, b->r[k]);
-  size_t need = Amen::bytes_needed(op->d, op->m, rmax + 4, rfmax, 4, 40) + 2 * (tt_bytes(b) + tt_bytes(x));
-  if (prec != T2S2_FP64) need += refine_extra_bytes(op, rmax + 4, rfmax);
+  size_t need = Amen::bytes_needed(op->d, op->m, rmax + amen_kick(), rfmax, amen_kick(), 40) + 2 * (tt_bytes(b) + tt_bytes(x));
+  if (prec != T2S2_FP64) need += refine_extra_bytes(op, rmax + amen_kick(), rfmax);
   T2S2_TRY(ensure_arena(op, need));
   Ctx cx = make_ctx(op, stream);
   DevTT db, dx;
@@ -886,8 +906,8 @@ static t2s2_status step_entry(t2s2_op op, t2s2_tt* u, double dt, double tol, int
   if (!op || !u || !(dt > 0.0) || !(tol > 0.0) || rmax < 1) return T2S2_EINVAL;
   T2S2_TRY(check_tt(op, u));
   const int d = op->d;
-  size_t need = Amen::bytes_needed(d, op->m, rmax + 4, 2 * (rmax + 4), 4, 40) + 8 * tt_bytes(u);
-  if (prec != T2S2_FP64) need += refine_extra_bytes(op, rmax + 4, 2 * (rmax + 4));
+  size_t need = Amen::bytes_needed(d, op->m, rmax + amen_kick(), 2 * (rmax + amen_kick()), amen_kick(), 40) + 8 * tt_bytes(u);
+  if (prec != T2S2_FP64) need += refine_extra_bytes(op, rmax + amen_kick(), 2 * (rmax + amen_kick()));
   T2S2_TRY(ensure_arena(op, need));
   Ctx cx = make_ctx(op, stream);
   DevTT du;
@@ -900,6 +920,9 @@ static t2s2_status step_entry(t2s2_op op, t2s2_tt* u, double dt, double tol, int
   T2S2_TRY(apply_op(op, cx, du, rhs, 1.0, cn ? -0.5 * dt : 0.0, false));
   T2S2_TRY(tt_round(cx, rhs, tol, rmax));
   const double co = cn ? 0.5 * dt : dt;
+  // a time step starts from the previous step, already close: a small kick
+  // keeps the ranks (and the cost of every later step) down
+  cx.kick = std::min(kStepKick, amen_kick());
   t2s2_status st = solve_impl(op, cx, rhs, du, 1.0, co, tol, rmax, 20, prec, info);
   if (st != T2S2_OK && st != T2S2_ENOCONV) return st;
   t2s2_status st2 = unbind_tt(cx, du, u);

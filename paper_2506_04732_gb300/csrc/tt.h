@@ -45,6 +45,8 @@ struct Ctx {
   // CTAs a cooperative launch may use (0: the whole GPU); concurrent solves
   // split the SMs so that their cooperative grids are co-resident
   int coop_ctas = 0;
+  // rank of the solver's enrichment for this call (0: the library default)
+  int kick = 0;
 };
 
 template <typename T>

@@ -31,7 +31,7 @@ def _setup(T, p):
     op = P.build_operator(p)
     b = T.TT.from_cores(P.source_cores(p, op))
     m = [n - 2 for n in p.n]
-    x = T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + 4)
+    x = T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + T.RANK_KICK)
     return op, b, x
 
 
@@ -73,7 +73,7 @@ def test_mixed_cn_step_matches_dense(T, prec):
     op = P.build_operator(p)
     ops = O.build(p)
     u0 = O.solution_tt(p, ops)
-    u = T.TT.from_cores(P.solution_cores(p, op), rcap=20)
+    u = T.TT.from_cores(P.solution_cores(p, op), rcap=16 + T.RANK_KICK)
     info = T.t2s2_cn_step(op, u, p.dt, 1e-11, 16, prec=getattr(T, prec))
     Mp = O.dense(ops, 1.0, 0.5 * p.dt)
     Mm = O.dense(ops, 1.0, -0.5 * p.dt)

@@ -32,7 +32,7 @@ def _setup(T, p):
     op = P.build_operator(p)
     b = T.TT.from_cores(P.source_cores(p, op))
     m = [n - 2 for n in p.n]
-    x = T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + 4)
+    x = T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + T.RANK_KICK)
     return op, b, x
 
 
@@ -101,7 +101,7 @@ def test_cn_step_matches_dense(T):
     op = P.build_operator(p)
     ops = O.build(p)
     u0 = O.solution_tt(p, ops)
-    u = T.TT.from_cores(P.solution_cores(p, op), rcap=20)
+    u = T.TT.from_cores(P.solution_cores(p, op), rcap=16 + T.RANK_KICK)
     info = T.t2s2_cn_step(op, u, p.dt, 1e-12, 16)
     Mp = O.dense(ops, 1.0, 0.5 * p.dt)
     Mm = O.dense(ops, 1.0, -0.5 * p.dt)
@@ -116,7 +116,7 @@ def test_be_step_matches_dense(T):
     op = P.build_operator(p)
     ops = O.build(p)
     u0 = O.solution_tt(p, ops)
-    u = T.TT.from_cores(P.solution_cores(p, op), rcap=14)
+    u = T.TT.from_cores(P.solution_cores(p, op), rcap=10 + T.RANK_KICK)
     T.t2s2_be_step(op, u, p.dt, 1e-12, 10)
     ud = np.linalg.solve(O.dense(ops, 1.0, p.dt), O.dense(ops, 1.0, 0.0) @ OT.full(u0).ravel())
     assert np.linalg.norm(OT.full(u.cores()).ravel() - ud) <= 1e-10 * np.linalg.norm(ud)
@@ -149,8 +149,8 @@ def test_solve_batched_matches_sequential(T):
         ops.append(op)
         bs.append(T.TT.from_cores(P.source_cores(p, op)))
         m = [n - 2 for n in p.n]
-        xs.append(T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + 4))
-        xs_seq.append(T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + 4))
+        xs.append(T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + T.RANK_KICK))
+        xs_seq.append(T.TT.from_cores([np.ones((1, mm, 1)) for mm in m], rcap=p.rmax + T.RANK_KICK))
     infos = T.t2s2_solve_batched(ops, bs, xs, 1e-8, 16, 50, workers=3)
     for i, p in enumerate(probs):
         assert infos[i].status == 0 and infos[i].residual <= 1e-8
@@ -172,9 +172,9 @@ def test_cn_step_config2_full_size_checked_by_oracle(T):
     from paper_2506_04732_gb300 import problem as P
     p = W.config2()
     op = P.build_operator(p)
-    u = T.TT.from_cores(P.solution_cores(p, op), rcap=p.rmax + 4)
+    u = T.TT.from_cores(P.solution_cores(p, op), rcap=p.rmax + T.RANK_KICK)
     info = T.t2s2_cn_step(op, u, p.dt, p.tol, p.rmax)
-    assert info.residual <= p.tol and max(u.r) <= p.rmax + 4
+    assert info.residual <= p.tol and max(u.r) <= p.rmax + T.RANK_KICK
     ops = O.build(p)
     u0 = O.solution_tt(p, ops)
     lhs = OT.matvec(O.ttm_cores(ops, 1.0, 0.5 * p.dt), u.cores())
