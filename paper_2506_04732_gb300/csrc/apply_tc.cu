@@ -106,19 +106,27 @@ __global__ void __launch_bounds__(kThreads, 4) apply_tc_kernel(Work w, int total
     const int kpad = ((m + O::kMmaK - 1) / O::kMmaK) * O::kMmaK;
     const int npad = ((2 * m + 15) / 16) * 16;
     // A tile: row t <-> pair g = row0 + t = (a, b); zero rows past the core.
-    // Two threads per row, each loading half of the K range.
+    // Work items are 16-byte chunks of one row (8 BF16 / 4 TF32 values): a
+    // warp takes 32 consecutive rows of one chunk, so each of its loads reads
+    // 32 consecutive b (coalesced), each thread keeps a chunk's loads in
+    // flight together, and one 16-byte shared store lands the chunk in its
+    // swizzled slot.
     {
-      const int t = tid & (kTileM - 1), half = tid / kTileM;
-      const int kh = kpad / 2;
-      const long g = row0 + t;
-      const bool valid = g < nrows;
-      const long a = valid ? g / rb : 0, b = valid ? g % rb : 0;
-      const double* xr = c.X + a * (long)m * rb + b;
-#pragma unroll 8
-      for (int jj = 0; jj < kh; ++jj) {
-        const int j = half * kh + jj;
-        const double v = (valid && j < m) ? xr[(long)j * rb] : 0.0;
-        O::store(sA + sw128_off<E>(t, j, kTileM), v);
+      constexpr int kPer = 16 / E;
+      const int nch = kpad / kPer;
+      for (int it = tid; it < kTileM * nch; it += kThreads) {
+        const int t = it % kTileM, ch = it / kTileM;
+        const long g = row0 + t;
+        const bool valid = g < nrows;
+        const long a = valid ? g / rb : 0, b = valid ? g % rb : 0;
+        const double* xr = c.X + a * (long)m * rb + b;
+        double v[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+          const int j = ch * kPer + q;
+          v[q] = (valid && j < m) ? xr[(long)j * rb] : 0.0;
+        }
+        *reinterpret_cast<uint4*>(sA + sw128_off<E>(t, ch * kPer, kTileM)) = O::pack16(v);
       }
     }
     // B tile: row ii < m: S row ii; m <= ii < 2m: G row ii - m; zero padded

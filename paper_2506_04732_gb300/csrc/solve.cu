@@ -599,8 +599,18 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
   am.ph(0);
   T2S2_TRY(am.init(op, cx, b, xio, c_mass, c_op, tol, rmax));
   T2S2_TRY(tt_orth_right(cx, am.x));
-  double bnorm = -1.0, res = 0.0;
-  T2S2_TRY(residual_impl(op, cx, b, am.x, c_mass, c_op, false, &res, &bnorm));
+  // |b| from <b, b> (a sum of squares: no cancellation), and the same screen
+  // as after every sweep for the initial guess
+  double bb = 0.0, res = 0.0;
+  T2S2_TRY(tt_dot(cx, b, b, &bb));
+  double bnorm = std::sqrt(bb);
+  double est = 0.0;
+  if (tol < 1e-6) T2S2_TRY(residual_estimate(op, cx, b, am.x, c_mass, c_op, bb, &est));
+  if (tol < 1e-6 && est > 1e-5) {
+    res = est;
+  } else {
+    T2S2_TRY(residual_impl(op, cx, b, am.x, c_mass, c_op, false, &res, &bnorm));
+  }
   int sweeps = 0;
   const char* ev = std::getenv("T2S2_VERBOSE");
   const bool verbose = ev && ev[0] == '1';
@@ -613,8 +623,8 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
     // Screen with the dot-product residual while it is far above tolerance
     // (there its cancellation error, ~sqrt(eps), is irrelevant); the
     // accurate orthogonalised residual alone decides convergence.
-    double est = 0.0;
-    if (tol < 1e-6) T2S2_TRY(residual_estimate(op, cx, b, am.x, c_mass, c_op, bnorm * bnorm, &est));
+    est = 0.0;
+    if (tol < 1e-6) T2S2_TRY(residual_estimate(op, cx, b, am.x, c_mass, c_op, bb, &est));
     if (tol < 1e-6 && est > 1e-5) {
       res = est;
     } else {

@@ -24,6 +24,17 @@ struct Op<T2S2_BF16_REFINE> {
   __device__ static void store(unsigned char* p, double v) {
     *reinterpret_cast<__nv_bfloat16*>(p) = __double2bfloat16(v);
   }
+  // eight values rounded and packed into one 16-byte chunk, in K order
+  __device__ static uint4 pack16(const double (&v)[8]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t lo = __bfloat16_as_ushort(__double2bfloat16(v[2 * i]));
+      const uint32_t hi = __bfloat16_as_ushort(__double2bfloat16(v[2 * i + 1]));
+      w[i] = lo | (hi << 16);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+  }
 };
 template <>
 struct Op<T2S2_TF32_REFINE> {
@@ -32,6 +43,13 @@ struct Op<T2S2_TF32_REFINE> {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)v));
     *reinterpret_cast<uint32_t*>(p) = r;
+  }
+  // four values rounded into one 16-byte chunk, in K order
+  __device__ static uint4 pack16(const double (&v)[4]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[i]) : "f"((float)v[i]));
+    return make_uint4(w[0], w[1], w[2], w[3]);
   }
 };
 
