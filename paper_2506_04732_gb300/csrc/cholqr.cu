@@ -1,24 +1,38 @@
-// Shifted CholeskyQR3 in ONE cooperative launch.
+// Shifted CholeskyQR (up to three passes) in ONE cooperative launch.
 //
 // The orthogonalisations of the TT sweeps (Methods: QR of the unfoldings
 // before every truncation) factor tall-skinny blocks of nlong vectors of
-// length c <= 96.  As separate launches each of the three CholeskyQR passes
-// needs a Gram GEMM (plus split-K sum), a one-CTA Cholesky, the triangular
-// product and the factor update: about sixteen launches per QR, each a few
-// microseconds of mostly idle GPU.  Here one grid does all three passes:
+// length c <= 96.  One grid does every pass:
 //
-//   for pass = 1..3:
-//     every CTA:  partial Gram of its own vectors             (grid sync)
-//     every CTA:  Gram = sum of all partials in CTA order, then
-//                 (Gram + shift I) = L L^T (semidefinite; pivots below
-//                 64 u max diag zeroed), L^{-1}, Lacc <- Lacc L -- the same
-//                 numbers in every CTA, so no second barrier is needed
-//     every CTA:  v <- L^{-1} v for its own vectors (kept in shared memory)
+//   pass p = 0, 1, 2:
+//     every CTA:  partial Gram of its own vectors (compact lower triangle)
+//                                                             (grid sync)
+//     CTA b:      sums its slice of the Gram over all partials (grid sync)
+//     every CTA:  loads the Gram; if it is within kOrthDev of the identity
+//                 this pass is the last one (and pass 0 runs unshifted);
+//                 (Gram + shift I) = L D L^T, semidefinite (pivots below
+//                 64 u max diag zeroed), with L^{-1} built in the same
+//                 elimination steps; v <- D^{-1/2} L^{-1} v for its own
+//                 vectors; its own rows of Lacc <- Lacc L D^{1/2}
 //
-// with the shift of the first pass as in Fukaya et al.'s shifted CholeskyQR3.
-// "Vectors" are the rows of a row-major rows x c block (tall: W = Q R with
-// R = Lacc^T) or the columns of a row-major c x cols block (wide: W = L Q with
-// L = Lacc).  Sums run in a fixed order, so results do not depend on timing.
+// with the shift of the first pass as in Fukaya et al.'s shifted
+// CholeskyQR3.  The stopping test is the CholeskyQR2 argument: a Gram close
+// to the identity means a condition number close to 1, for which one more
+// CholeskyQR pass yields Q orthonormal to working precision; blocks with one
+// column need a single unshifted pass.  "Vectors" are the rows of a row-major
+// rows x c block (tall: W = Q R with R = Lacc^T) or the columns of a
+// row-major c x cols block (wide: W = L Q with L = Lacc).  Sums run in a
+// fixed order, so results do not depend on timing.
+//
+// Binary64 on this part issues one warp instruction per ~64 cycles per SM
+// sub-partition, so the small c x c work is shaped around that: one barrier
+// per elimination step, the next pivot's reciprocal computed by one thread
+// while the others update (binary32 seed, one Newton step in binary64 -- the
+// pivots are exact binary64 values and decide zeroing; a reciprocal good to
+// 2^-46 only perturbs L's off-diagonal entries, which are O(1e-3) or smaller
+// in the final pass), exact power-of-4 scaling of the Gram so that binary32
+// comparisons and seeds stay in range, and maxima taken as integer
+// reductions of bit patterns.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -36,163 +50,252 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kCholQrMaxSmem = 200 * 1024;
+constexpr int kMaxGrid = 128;    // CTAs of one factorisation
+constexpr int kPerTarget = 8;    // vectors per CTA
+constexpr float kOrthDev = 1e-3f;
+constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
 
 struct CholQrArgs {
   const double* W;
   double* Q;
   double* R;     // c x c output (R = Lacc^T for tall, L = Lacc for wide)
-  double* part;  // 2 x grid x c x c partial Grams (alternating by pass)
+  double* part;  // grid x T partial Grams (T = c (c + 1) / 2)
+  double* gsum;  // T: the summed Gram
   int* status;   // set to 1 when a pivot was zeroed (rank deficiency)
   int nlong, c, per;  // vectors, their length, vectors per CTA
   int tall;
   double shift_rel;
 };
 
+__host__ __device__ inline int tri_count(int c) { return c * (c + 1) / 2; }
+
+__host__ __device__ inline size_t smem_bytes(int per, int c, int grid) {
+  const int rpc = (c + grid - 1) / grid;
+  return sizeof(double) * (2 * (size_t)per * c + 2 * (size_t)c * c + 2 * (size_t)rpc * c + 4 * (size_t)c) +
+         sizeof(int) * ((tri_count(c) + 1) & ~1);
+}
+
 // element j of vector i in a tall (i-th row) or wide (i-th column) block
 __device__ __forceinline__ long vidx(const CholQrArgs& a, int i, int j) {
   return a.tall ? (long)i * a.c + j : (long)j * a.nlong + i;
 }
 
+// binary32 seed and one binary64 Newton step: 1/v to about 2^-46
+__device__ __forceinline__ double pivot_rcp(double v, float f) {
+  double y = (double)__frcp_rn(f);
+  return y * fma(-v, y, 2.0);
+}
+
 __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ double sm[];
-  const int c = a.c, cc = c * c;
-  const int b = blockIdx.x, t = threadIdx.x, G = gridDim.x;
+  const int c = a.c, T = tri_count(c);
+  const int b = blockIdx.x, t = threadIdx.x, G = gridDim.x, lane = t & 31, warp = t >> 5;
   const int i0 = b * a.per, cnt = max(0, min(a.per, a.nlong - i0));
-  double* V = sm;                 // per x c: own vectors
-  double* V2 = V + a.per * c;     // per x c
-  double* A = V2 + a.per * c;     // c x c: Gram, then L
-  double* Iv = A + cc;            // c x c: L^{-1}
-  double* Lacc = Iv + cc;         // c x c (kept by every CTA; CTA 0 writes it out)
-  __shared__ double shift, tau;
-  __shared__ int bad;
-  // own vectors of W
+  const int rpc = (c + G - 1) / G;
+  const int nrow = b < c ? (c - 1 - b) / G + 1 : 0;  // own rows b, b + G, ... of Lacc
+  double* V = sm;                // per x c: own vectors
+  double* V2 = V + a.per * c;    // per x c
+  double* A = V2 + a.per * c;    // c x c lower: scaled Gram, LDL^T work, then L D^{1/2}
+  double* B = A + c * c;         // c x c lower: unit L^{-1}
+  double* Lr = B + c * c;        // rpc x c: own rows of Lacc
+  double* Lr2 = Lr + rpc * c;    // rpc x c
+  double* rv = Lr2 + rpc * c;    // 1/d_j (0 for a zeroed pivot), scaled units
+  double* dv = rv + c;           // d_j (0 for a zeroed pivot), scaled units
+  double* sdn = dv + c;          // sqrt(d_j), scaled units
+  double* isdn = sdn + c;        // 1/sqrt(d_j), scaled units
+  int* tri = reinterpret_cast<int*>(isdn + c);  // (row << 8) | col, lower triangle row by row
+  __shared__ unsigned ired[2][kThreads / 32];
+  __shared__ double shift, sc, isc;
+  __shared__ float tauf;
+  __shared__ int bad, last;
   for (int e = t; e < cnt * c; e += kThreads) {
     const int r = a.tall ? e / c : e % cnt, j = a.tall ? e % c : e / cnt;
     V[r * c + j] = a.W[vidx(a, i0 + r, j)];
   }
+  for (int ia = t; ia < c; ia += kThreads)
+    for (int ib = 0; ib <= ia; ++ib) tri[ia * (ia + 1) / 2 + ib] = (ia << 8) | ib;
   if (t == 0) bad = 0;
   __syncthreads();
-  for (int pass = 0; pass < 3; ++pass) {
-    // partials alternate between two buffers: a CTA may still be reading the
-    // previous pass's partials while a faster one writes this pass's
-    double* part = a.part + (size_t)(pass & 1) * G * cc;
-    // (1) partial Gram of own vectors (upper triangle)
-    for (int e = t; e < cc; e += kThreads) {
-      const int j = e / c, k = e % c;
+  const int sl = (T + G - 1) / G;  // Gram entries summed by each CTA
+  int pass = 0;
+  for (;; ++pass) {
+    // (1) partial Gram of own vectors, entries (k, j) with j <= k
+    for (int e = t; e < T; e += kThreads) {
+      const int rc = tri[e], k = rc >> 8, j = rc & 255;
       double s = 0.0;
-      if (k >= j)
-        for (int r = 0; r < cnt; ++r) s = fma(V[r * c + j], V[r * c + k], s);
-      part[(long)b * cc + e] = s;
+      for (int r = 0; r < cnt; ++r) s = fma(V[r * c + j], V[r * c + k], s);
+      a.part[(long)b * T + e] = s;
     }
     grid.sync();
-    // (2) every CTA: Gram = sum of the partials in CTA order, then the same
-    // shifted semidefinite Cholesky and inverse (identical in all CTAs)
-    for (int e = t; e < cc; e += kThreads) {
-      const int j = e / c, k = e % c;
+    // (2) this CTA's slice of the Gram: lanes over the partials, then a fixed
+    // shuffle tree
+    for (int e = b * sl + warp; e < min(T, (b + 1) * sl); e += kThreads / 32) {
       double s = 0.0;
-      if (k <= j) {
-#pragma unroll 8
-        for (int p = 0; p < G; ++p) s += part[(long)p * cc + k * c + j];
+      for (int p = lane; p < G; p += 32) s += a.part[(long)p * T + e];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) a.gsum[e] = s;
+    }
+    grid.sync();
+    // (3) load the Gram; the largest diagonal and the distance from the
+    // identity as integer maxima of bit patterns (non-negative values order
+    // like their bits); exactly zero columns, left by zeroed pivots, do not
+    // count against the identity
+    {
+      unsigned mxh = 0, devb = 0;
+      for (int e = t; e < T; e += kThreads) {
+        const int rc = tri[e], k = rc >> 8, j = rc & 255;
+        const double g = a.gsum[e];
+        A[k * c + j] = g;
+        B[k * c + j] = (k == j) ? 1.0 : 0.0;
+        const float gf = (float)g;
+        if (k == j) {
+          mxh = max(mxh, (unsigned)max(__double2hiint(g), 0));
+          if ((__double_as_longlong(g) << 1) != 0) devb = max(devb, __float_as_uint(fabsf(gf - 1.0f)));
+        } else {
+          devb = max(devb, __float_as_uint(fabsf(gf)));
+        }
       }
-      A[e] = s;  // lower triangle (row j >= column k) from the upper partials
+      mxh = __reduce_max_sync(0xffffffffu, mxh);
+      devb = __reduce_max_sync(0xffffffffu, devb);
+      if (lane == 0) ired[0][warp] = mxh, ired[1][warp] = devb;
     }
     __syncthreads();
     if (t == 0) {
-      double tr = 0.0, mx = 0.0;
-      for (int i = 0; i < c; ++i) {
-        tr += A[i * c + i];
-        mx = fmax(mx, A[i * c + i]);
-      }
-      shift = (pass == 0) ? a.shift_rel * tr : 0.0;
-      tau = 64.0 * 1.1102230246251565e-16 * (mx + shift);
+      unsigned M = 0, D = 0;
+      for (int w = 0; w < kThreads / 32; ++w) M = max(M, ired[0][w]), D = max(D, ired[1][w]);
+      const bool fin = (__uint_as_float(D) <= kOrthDev) || c == 1 || pass == 2;
+      const double mx = __hiloint2double((int)M, 0);
+      // shift of the first pass, with c * (largest diagonal) >= trace
+      const double sh = (pass == 0 && !fin) ? a.shift_rel * c * mx : 0.0;
+      shift = sh;
+      last = fin;
+      // exact power-of-4 scaling: the largest diagonal lands in [1, 4)
+      const int ex = (int)((M >> 20) & 0x7FF);
+      const int k2 = (ex > 0 && ex < 0x7FF) ? ((ex - 1023) >> 1) : 0;
+      sc = __longlong_as_double((long long)(1023 + k2) << 52);
+      isc = __longlong_as_double((long long)(1023 - k2) << 52);
+      const double s2 = __longlong_as_double((long long)(1023 - 2 * k2) << 52);
+      tauf = (float)(64.0 * kUnitRoundoff * (mx + sh) * s2);
     }
     __syncthreads();
-    for (int i = t; i < c; i += kThreads) A[i * c + i] += shift;
-    __syncthreads();
-    for (int j = 0; j < c; ++j) {
-      const double v = A[j * c + j];
-      const bool zero = !(v > tau);
-      __syncthreads();
-      if (zero) {
-        for (int i = j + t; i < c; i += kThreads) A[i * c + j] = 0.0;
-        if (t == 0) bad = 1;
-        __syncthreads();
-        continue;
-      }
-      const double rinv = drsqrt(v);
-      for (int i = j + 1 + t; i < c; i += kThreads) A[i * c + j] *= rinv;
-      if (t == 0) A[j * c + j] = v * rinv;
-      __syncthreads();
-      const int rem = c - j - 1;
-      for (int e = t; e < rem * rem; e += kThreads) {
-        const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-        if (k <= i) A[i * c + k] -= A[i * c + j] * A[k * c + j];
-      }
-      __syncthreads();
-    }
-    // pseudo-inverse of lower-triangular L (x_i = 0 where L_ii = 0)
-    for (int e = t; e < cc; e += kThreads) Iv[e] = 0.0;
-    __syncthreads();
-    for (int k = t; k < c; k += kThreads) {
-      for (int i = k; i < c; ++i) {
-        const double dii = A[i * c + i];
-        if (dii == 0.0) continue;
-        double s = (i == k) ? 1.0 : 0.0;
-        for (int l = k; l < i; ++l) s -= A[i * c + l] * Iv[l * c + k];
-        Iv[i * c + k] = s * drcp(dii);
+    {
+      const double s2 = isc * isc, sh = shift;
+      for (int e = t; e < T; e += kThreads) {
+        const int rc = tri[e], k = rc >> 8, j = rc & 255;
+        const double v = (A[k * c + j] + (k == j ? sh : 0.0)) * s2;
+        A[k * c + j] = v;
+        if (e == 0) {  // tri[0] is (0, 0): the first pivot
+          const float f = (float)v;
+          const bool z = !(f > tauf);
+          rv[0] = z ? 0.0 : pivot_rcp(v, f);
+          dv[0] = z ? 0.0 : v;
+          if (z) bad = 1;
+        }
       }
     }
     __syncthreads();
-    // (3) v <- L^{-1} v for own vectors
-    for (int e = t; e < cnt * c; e += kThreads) {
-      const int r = e / c, j = e % c;
+    // (4) L D L^T: step j takes column j out of the trailing block and out of
+    // the rows of L^{-1} below j.  Thread 0 updates the next pivot and takes
+    // its reciprocal; the other threads do the rest.
+    for (int j = 0; j + 1 < c; ++j) {
+      const int rem = c - 1 - j, nt = rem * (rem + 1) / 2, ni = rem * (j + 1);
+      const double r = rv[j];
+      if (t == 0) {
+        const int i = j + 1;
+        const double l = A[i * c + j];
+        const double v = fma(-(l * r), l, A[i * c + i]);
+        A[i * c + i] = v;
+        const float f = (float)v;
+        const bool z = !(f > tauf);
+        rv[i] = z ? 0.0 : pivot_rcp(v, z ? 1.0f : f);
+        dv[i] = z ? 0.0 : v;
+        if (z) bad = 1;
+      } else {
+        for (int e = t; e < nt + ni; e += kThreads - 1) {
+          if (e < nt) {
+            const int rc = tri[e], i = j + 1 + (rc >> 8), k = j + 1 + (rc & 255);
+            A[i * c + k] = fma(-(A[i * c + j] * r), A[k * c + j], A[i * c + k]);
+          } else {
+            const int q = e - nt, i = j + 1 + q / (j + 1), l = q % (j + 1);
+            B[i * c + l] = fma(-(A[i * c + j] * r), B[j * c + l], B[i * c + l]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (int i = t; i < c; i += kThreads) {
+      const double d = dv[i];
+      const double is = d > 0.0 ? drsqrt(d) : 0.0;
+      isdn[i] = is;
+      sdn[i] = d * is;
+    }
+    __syncthreads();
+    // (5) v <- D^{-1/2} L^{-1} v for own vectors; rows i and c-1-i together,
+    // so that every thread runs c + 1 products
+    {
+      const int h = (c + 1) / 2;
+      const double sci = isc;
+      for (int e = t; e < cnt * h; e += kThreads) {
+        const int r = e / h, i1 = e % h, i2 = c - 1 - i1;
+        const double* vr = V + r * c;
+        double s1 = 0.0;
+        for (int l = 0; l <= i1; ++l) s1 = fma(B[i1 * c + l], vr[l], s1);
+        V2[r * c + i1] = s1 * isdn[i1] * sci;
+        if (i2 != i1) {
+          double s2 = 0.0;
+          for (int l = 0; l <= i2; ++l) s2 = fma(B[i2 * c + l], vr[l], s2);
+          V2[r * c + i2] = s2 * isdn[i2] * sci;
+        }
+      }
+    }
+    // the factor L D^{1/2} in unscaled units into A's lower part
+    for (int e = t; e < T; e += kThreads) {
+      const int rc = tri[e], i = rc >> 8, j = rc & 255;
+      A[i * c + j] = (i == j) ? sdn[j] * sc : A[i * c + j] * isdn[j] * sc;
+    }
+    __syncthreads();
+    // (6) own rows of Lacc <- Lacc L D^{1/2}
+    for (int e = t; e < nrow * c; e += kThreads) {
+      const int q = e / c, k = e % c, i = b + q * G;
       double s = 0.0;
-      for (int k = 0; k <= j; ++k) s = fma(Iv[j * c + k], V[r * c + k], s);
-      V2[e] = s;
-    }
-    __syncthreads();
-    // Lacc <- Lacc L (lower triangular product), staged in Iv (now free)
-    if (pass == 0) {
-      for (int e = t; e < cc; e += kThreads) Lacc[e] = (e % c <= e / c) ? A[e] : 0.0;
-    } else {
-      for (int e = t; e < cc; e += kThreads) {
-        const int i = e / c, k = e % c;
-        double s = 0.0;
-        if (k <= i)
-          for (int l = k; l <= i; ++l) s = fma(Lacc[i * c + l], A[l * c + k], s);
-        Iv[e] = s;
+      if (pass == 0) {
+        s = (k <= i) ? A[i * c + k] : 0.0;
+      } else if (k <= i) {
+        for (int l = k; l <= i; ++l) s = fma(Lr[q * c + l], A[l * c + k], s);
       }
-      __syncthreads();
-      for (int e = t; e < cc; e += kThreads) Lacc[e] = Iv[e];
+      Lr2[q * c + k] = s;
     }
     __syncthreads();
-    double* tmp = V;
+    double* tmp = Lr;
+    Lr = Lr2;
+    Lr2 = tmp;
+    tmp = V;
     V = V2;
     V2 = tmp;
+    if (last) break;  // the same decision in every CTA: same Gram, same code
   }
-  // own vectors of Q
   for (int e = t; e < cnt * c; e += kThreads) {
     const int r = a.tall ? e / c : e % cnt, j = a.tall ? e % c : e / cnt;
     a.Q[vidx(a, i0 + r, j)] = V[r * c + j];
   }
-  if (b == 0) {
-    for (int e = t; e < cc; e += kThreads) {
-      const int i = e / c, k = e % c;
-      a.R[e] = a.tall ? Lacc[k * c + i] : Lacc[e];
-    }
-    if (t == 0 && a.status) *a.status = bad;
+  for (int e = t; e < nrow * c; e += kThreads) {
+    const int q = e / c, k = e % c, i = b + q * G;
+    if (a.tall) a.R[k * c + i] = Lr[q * c + k];
+    else a.R[i * c + k] = Lr[q * c + k];
   }
+  if (b == 0 && t == 0 && a.status) *a.status = bad;
 }
 
 }  // namespace
 
 size_t cholqr3_scratch_doubles(int nlong, int c, int grid) {
   (void)nlong;
-  return 2 * (size_t)grid * c * c;  // two alternating sets of partial Grams
+  return (size_t)(grid + 1) * tri_count(c);  // partial Grams and their sum
 }
 
-// Grid size and shared memory for a fused CholeskyQR3 of nlong vectors of
+// Grid size and shared memory for a fused CholeskyQR of nlong vectors of
 // length c; returns false if no co-resident grid fits.
 bool cholqr3_plan(int nlong, int c, int max_grid, int* grid_out, int* per_out, size_t* smem_out) {
   if (c < 1 || c > kSmallMax || nlong < c) return false;
@@ -200,13 +303,13 @@ bool cholqr3_plan(int nlong, int c, int max_grid, int* grid_out, int* per_out, s
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // about 16 vectors per CTA and at most 64 CTAs: the Gram reduction reads one
-  // partial per CTA for every entry, so a wider grid costs more than it saves
-  const int cap = std::min(64, max_grid > 0 ? std::min(sms, max_grid) : sms);
-  int grid = std::max(1, std::min(cap, (nlong + 15) / 16));
+  // about kPerTarget vectors per CTA: the Gram and the triangular product
+  // scale with the vectors per CTA, the Gram sums are spread over the CTAs
+  const int cap = std::min(kMaxGrid, max_grid > 0 ? std::min(sms, max_grid) : sms);
+  int grid = std::max(1, std::min(cap, (nlong + kPerTarget - 1) / kPerTarget));
   const int per = (nlong + grid - 1) / grid;
   grid = (nlong + per - 1) / per;
-  const size_t smem = sizeof(double) * (2 * (size_t)per * c + 3 * (size_t)c * c);
+  const size_t smem = smem_bytes(per, c, grid);
   if (smem > kCholQrMaxSmem) return false;
   // the attribute is set once per device to the largest size ever used: a
   // per-call value would race with concurrent solves on other host threads
@@ -239,13 +342,16 @@ t2s2_status cholqr3_fused(const double* W, double* Q, double* R, int nlong, int 
   a.Q = Q;
   a.R = R;
   a.part = scratch;
+  a.gsum = scratch + (size_t)grid * tri_count(c);
   a.status = status;
   a.nlong = nlong;
   a.c = c;
   a.per = per;
   a.tall = tall ? 1 : 0;
   a.shift_rel = shift_rel;
-  const double fl = 3.0 * (4.0 * nlong * (double)c * c) + 3.0 * (double)c * c * c;
+  // work of two passes (the common case): Gram and triangular product
+  // 2 n c^2 each, the L D L^T with its inverse 2 c^3 / 3
+  const double fl = 2.0 * (4.0 * nlong * (double)c * c) + 2.0 * (2.0 * (double)c * c * c / 3.0);
   TraceScope ts(kTrSmall, st, fl, 16.0 * nlong * c);
   void* args[] = {&a};
   T2S2_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)cholqr3_kernel, dim3(grid), dim3(kThreads), args, smem, st));

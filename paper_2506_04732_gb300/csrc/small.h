@@ -15,8 +15,9 @@ t2s2_status chol_inv(const double* G, int c, double shift_rel, double* L, double
 t2s2_status jacobi_svd(const double* A, int p, int q, double* U, double* s, double* V, int* sweeps,
                        cudaStream_t st);
 
-// Shifted CholeskyQR3 of nlong vectors of length c in one cooperative launch
-// (cholqr.cu).  tall: W is nlong x c row-major, W = Q R (R = c x c upper);
+// Shifted CholeskyQR of nlong vectors of length c in one cooperative launch
+// (cholqr.cu): up to three passes, fewer when a pass's Gram certifies that
+// the next one finishes.  tall: W is nlong x c row-major, W = Q R (R = c x c upper);
 // wide: W is c x nlong row-major, W = R Q (R lower).  Plan first: false if
 // the grid cannot be co-resident or shared memory would not fit; max_grid > 0
 // caps the number of CTAs.
