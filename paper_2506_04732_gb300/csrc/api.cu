@@ -46,6 +46,7 @@ Ctx make_ctx(t2s2_op op, void* stream) {
   cx.ar = &op->arena;
   cx.hbuf = op->hbuf;
   cx.dstat = op->dstat;
+  cx.gcnt = op->gcnt;
   cx.coop_ctas = op->team;
   return cx;
 }
@@ -160,7 +161,7 @@ t2s2_status contract_gemm(Ctx& cx, const Gemm<double>& g) {
   const size_t mk = cx.ar->mark();
   double* ws = need ? aget<double>(cx, need) : nullptr;
   if (need && !ws) return T2S2_ENOMEM;
-  const t2s2_status s = gemm(g, ws, need, cx.st);
+  const t2s2_status s = gemm(g, ws, need, cx.st, cx.gcnt, cx.gcnt ? kGemmCounters : 0);
   cx.ar->release(mk);
   return s;
 }
@@ -343,6 +344,8 @@ t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op*
     e = cudaMemcpyAsync(op->fmat, hostf.data(), sizeof(float) * total, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMallocHost(&op->hbuf, sizeof(double) * 4096);
   if (e == cudaSuccess) e = cudaMalloc(&op->dstat, sizeof(int) * 64);
+  if (e == cudaSuccess) e = cudaMalloc(&op->gcnt, sizeof(int) * kGemmCounters);
+  if (e == cudaSuccess) e = cudaMemsetAsync(op->gcnt, 0, sizeof(int) * kGemmCounters, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     set_last_cuda_error(e, "operator upload", __FILE__, __LINE__);
@@ -374,6 +377,7 @@ t2s2_status t2s2_op_destroy(t2s2_op op) {
   if (op->arena.base) cudaFree(op->arena.base);
   if (op->hbuf) cudaFreeHost(op->hbuf);
   if (op->dstat) cudaFree(op->dstat);
+  if (op->gcnt) cudaFree(op->gcnt);
   op->free_solver_buffers();
   delete op;
   return T2S2_OK;

@@ -30,6 +30,7 @@ struct t2s2_op_s {
   int team = 0;            // CTAs per cooperative local solve (0: whole GPU)
   double* hbuf = nullptr;  // pinned host scratch
   int* dstat = nullptr;    // device status words
+  int* gcnt = nullptr;     // kGemmCounters split-K tile counters (zero between launches)
   void free_solver_buffers();
 };
 

@@ -1,7 +1,18 @@
 // Tiled SIMT GEMM for the small dense contractions of the TT sweeps.
-// 64x64 output tile per CTA, 256 threads with a 4x4 register micro-tile,
-// K staged through shared memory in slices of 16.  Used for FP64 work, whose
-// throughput on sm_103 is bounded by the DFMA pipe rather than by memory.
+//
+// Two kernels.  gemm_kernel: up to 64x64 outputs per CTA, 256 threads with a
+// register micro-tile, K staged through shared memory in slices of 16; for
+// larger products and for FP32.  small_kernel: the FP64 contractions of the
+// sweeps (M, N of a few tens to a few hundreds, K from ~10 to ~1000) cost
+// ~0.3 MFLOP each -- a quarter of a microsecond of the whole GPU's binary64
+// rate -- so their time is latency: one output per thread, 8x8 to 16x16
+// thread tiles chosen so that the grid covers the SMs, K in slices of 32,
+// and long K split over CTAs with the partial sums added, in split order, by
+// the last CTA of each tile to arrive (a per-tile counter that the adding CTA
+// resets), so no second launch is needed and the result does not depend on
+// timing.
+#include <type_traits>
+
 #include "gemm.h"
 #include "trace.h"
 
@@ -110,6 +121,107 @@ __global__ void splitk_reduce(Gemm<T> g, int splits, const T* ws) {
   }
 }
 
+// 256 threads on a BM x BN output tile: KG = 256 / (BM BN) threads share an
+// output, each taking every KG-th k of a slice of SBK with two accumulators,
+// so that the dependent chain per thread is SBK / (2 KG) binary64 FMAs (each
+// ~150 cycles of latency on this part).  The KG partial sums are added in a
+// fixed order.  With splits > 1 the CTA of split s writes its partial tile to
+// ws[s], and the last CTA of the tile to finish (counter cnt[tile]) adds the
+// partials in split order.
+constexpr int SBK = 64, SNT = 256;
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(SNT) small_kernel(Gemm<double> g, int splits, int kchunk, double* ws,
+                                                    int* cnt) {
+  constexpr int NO = BM * BN, KG = SNT / NO;
+  static_assert(NO * KG == SNT, "tile must divide the CTA");
+  __shared__ double As[SBK][BM + 1];
+  __shared__ double Bs[SBK][BN + 1];
+  __shared__ double red[KG][NO];
+  __shared__ int last;
+  const int bz = blockIdx.z;
+  const int b = bz / splits, sidx = bz % splits;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int k_begin = sidx * kchunk;
+  const int k_end = min(g.K, k_begin + kchunk);
+  const double* A = g.A + (long)b * g.sA;
+  const double* B = g.B + (long)b * g.sB;
+  const int t = threadIdx.x, o = t % NO, kg = t / NO, tx = o % BN, ty = o / BN;
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int k0 = k_begin; k0 < k_end; k0 += SBK) {
+    const int kn = min(SBK, k_end - k0);
+    for (int e = t; e < BM * kn; e += SNT) {
+      int mm, kk;
+      if (g.tA) { mm = e % BM; kk = e / BM; } else { kk = e % kn; mm = e / kn; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      double v = 0.0;
+      if (gm < g.M) v = g.tA ? A[(long)gk * g.lda + gm] : A[(long)gm * g.lda + gk];
+      As[kk][mm] = v;
+    }
+    for (int e = t; e < BN * kn; e += SNT) {
+      int nn, kk;
+      if (g.tB) { kk = e % kn; nn = e / kn; } else { nn = e % BN; kk = e / BN; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      double v = 0.0;
+      if (gn < g.N) v = g.tB ? B[(long)gn * g.ldb + gk] : B[(long)gk * g.ldb + gn];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+    int kk = kg;
+    for (; kk + KG < kn; kk += 2 * KG) {
+      acc0 = fma(As[kk][ty], Bs[kk][tx], acc0);
+      acc1 = fma(As[kk + KG][ty], Bs[kk + KG][tx], acc1);
+    }
+    if (kk < kn) acc0 = fma(As[kk][ty], Bs[kk][tx], acc0);
+    __syncthreads();
+  }
+  red[kg][o] = acc0 + acc1;
+  __syncthreads();
+  const int gm = m0 + ty, gn = n0 + tx;
+  const bool in = kg == 0 && gm < g.M && gn < g.N;
+  double acc = 0.0;
+  if (kg == 0)
+#pragma unroll
+    for (int q = 0; q < KG; ++q) acc += red[q][o];
+  const long mn = (long)g.M * g.N;
+  if (splits == 1) {
+    if (in) {
+      double* c = g.C + (long)b * g.sC + (long)gm * g.ldc + gn;
+      double v = g.alpha * acc;
+      if (g.beta != 0.0) v = fma(g.beta, *c, v);
+      *c = v;
+    }
+    return;
+  }
+  if (in) ws[((long)sidx * g.batch + b) * mn + (long)gm * g.N + gn] = acc;
+  if (!cnt) return;  // the caller adds the partials with splitk_reduce
+  __threadfence();
+  __syncthreads();
+  const long tile = ((long)b * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  if (t == 0) last = (atomicAdd(cnt + tile, 1) == splits - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // partials q = kg, kg + KG, ... per thread, then the KG sums in order
+  double s = 0.0;
+  if (gm < g.M && gn < g.N) {
+    const volatile double* p = ws + (long)b * mn + (long)gm * g.N + gn;
+    for (int q = kg; q < splits; q += KG) s += p[(long)q * g.batch * mn];
+  }
+  red[kg][o] = s;
+  __syncthreads();
+  if (in) {
+    double tot = 0.0;
+#pragma unroll
+    for (int q = 0; q < KG; ++q) tot += red[q][o];
+    double* c = g.C + (long)b * g.sC + (long)gm * g.ldc + gn;
+    double v = g.alpha * tot;
+    if (g.beta != 0.0) v = fma(g.beta, *c, v);
+    *c = v;
+  }
+  if (t == 0) cnt[tile] = 0;  // ready for the next launch on this stream
+}
+
 inline int tile_code(int x) { return x <= 16 ? 1 : (x <= 32 ? 2 : 4); }
 
 // Tile shape and split-K.  FP64 runs at 2 DFMA/clk/SM on this part, so a
@@ -147,6 +259,63 @@ TilePlan plan_tiles(const Gemm<T>& g) {
   return p;
 }
 
+// Plan of the small FP64 kernel from a latency model (cycles on one SM):
+// the dependent FMA chain of a thread (~150 cycles per binary64 FMA), one
+// global-load round trip per K slice (~800), the cross-CTA addition when K is
+// split, and the binary64 issue limit of the busiest SM (2 FMAs per cycle).
+struct SmallPlan {
+  bool use;
+  int bm, bn, splits, kc;
+};
+constexpr double kSmallMaxFmas = 16e6;
+constexpr int kShapes[][2] = {{16, 16}, {8, 16}, {16, 8}, {8, 8}, {4, 16}, {16, 4},
+                              {1, 64},  {64, 1}, {4, 4}};
+
+SmallPlan plan_small(const Gemm<double>& g) {
+  SmallPlan best{false, 8, 8, 1, g.K};
+  if ((double)g.M * g.N * (double)std::max(g.K, 1) * g.batch > kSmallMaxFmas) return best;
+  best.use = true;
+  if (g.K <= 0) {
+    best.kc = 0;
+    return best;
+  }
+  double best_cost = 1e300;
+  for (auto& sh : kShapes) {
+    const int bm = sh[0], bn = sh[1], kgr = SNT / (bm * bn);
+    const long tiles = (long)cdiv(g.M, bm) * cdiv(g.N, bn) * g.batch;
+    const int maxs = (int)std::min<long>(64, std::max(1, cdiv(g.K, 32)));
+    for (int s = 1; s <= maxs; s = (s < 4 ? s + 1 : s * 2)) {
+      if ((long)g.batch * s > 65535L) break;
+      int kc = cdiv(cdiv(g.K, s), 8) * 8;
+      const int sp = cdiv(g.K, kc);
+      const double chain = 150.0 * ((double)kc / (2.0 * kgr) + kgr);
+      const double loads = 800.0 * cdiv(kc, SBK);
+      const double reduce = sp > 1 ? 900.0 + 150.0 * ((double)sp / kgr + kgr) : 0.0;
+      const long ctas = tiles * sp;
+      const double issue = (double)((ctas + kNumSMs - 1) / kNumSMs) * bm * bn * (double)kc / 2.0;
+      const double cost = std::max(chain + loads, issue) + reduce;
+      if (cost < best_cost * 0.98) {
+        best_cost = cost;
+        best.bm = bm;
+        best.bn = bn;
+        best.splits = sp;
+        best.kc = kc;
+      }
+    }
+  }
+  return best;
+}
+
+void launch_small(const Gemm<double>& g, const SmallPlan& p, double* ws, int* cnt, cudaStream_t st) {
+  dim3 grid(cdiv(g.N, p.bn), cdiv(g.M, p.bm), g.batch * p.splits);
+  const int kc = std::max(p.kc, 1);
+#define T2S2_SMALL(a, b) \
+  if (p.bm == a && p.bn == b) { small_kernel<a, b><<<grid, SNT, 0, st>>>(g, p.splits, kc, ws, cnt); return; }
+  T2S2_SMALL(16, 16) T2S2_SMALL(8, 16) T2S2_SMALL(16, 8) T2S2_SMALL(8, 8) T2S2_SMALL(4, 16)
+  T2S2_SMALL(16, 4) T2S2_SMALL(1, 64) T2S2_SMALL(64, 1) T2S2_SMALL(4, 4)
+#undef T2S2_SMALL
+}
+
 template <typename T, int TM, int TN>
 void launch_tile(const Gemm<T>& g, int splits, int kc, T* ws, cudaStream_t st) {
   dim3 grid(cdiv(g.N, 16 * TN), cdiv(g.M, 16 * TM), g.batch * splits);
@@ -165,13 +334,44 @@ void launch_any(const Gemm<T>& g, int tm, int tn, int splits, int kc, T* ws, cud
 
 template <typename T>
 size_t gemm_workspace(const Gemm<T>& g) {
+  if constexpr (std::is_same<T, double>::value) {
+    const SmallPlan sp = plan_small(g);
+    if (sp.use) return sp.splits > 1 ? (size_t)sp.splits * g.batch * g.M * g.N : 0;
+  }
   const TilePlan p = plan_tiles(g);
   return p.splits > 1 ? (size_t)p.splits * g.batch * g.M * g.N : 0;
 }
 
 template <typename T>
-t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st) {
+t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st, int* cnt, long ncnt) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return T2S2_OK;
+  const double fl = 2.0 * g.M * g.N * (double)g.K * g.batch;
+  const double by = (double)sizeof(T) * g.batch * ((double)g.M * g.K + (double)g.K * g.N + 2.0 * g.M * g.N);
+  if constexpr (std::is_same<T, double>::value) {
+    SmallPlan sp = plan_small(g);
+    if (sp.use) {
+      if (sp.splits > 1 && (ws == nullptr || ws_elems < (size_t)sp.splits * g.batch * g.M * g.N)) {
+        sp.splits = 1;
+        sp.kc = g.K;
+      }
+      if (g.batch * (long)sp.splits > 65535L) return T2S2_EINVAL;
+      const long tiles = (long)cdiv(g.M, sp.bm) * cdiv(g.N, sp.bn) * g.batch;
+      int* c = (sp.splits > 1 && cnt && tiles <= ncnt) ? cnt : nullptr;
+      {
+        TraceScope ts(kTrGemm, st, fl, by);
+        launch_small(g, sp, ws, c, st);
+      }
+      T2S2_CUDA_TRY(cudaGetLastError());
+      if (sp.splits > 1 && !c) {
+        const long total = (long)g.batch * g.M * g.N;
+        const int blocks = (int)std::min<long>(cdiv(total, 256), 4L * kNumSMs);
+        TraceScope ts(kTrElem, st, 0.0, (double)sizeof(T) * total * (sp.splits + 2));
+        splitk_reduce<T><<<blocks, 256, 0, st>>>(g, sp.splits, ws);
+        T2S2_CUDA_TRY(cudaGetLastError());
+      }
+      return T2S2_OK;
+    }
+  }
   const TilePlan plan = plan_tiles(g);
   int splits = plan.splits, kc = plan.kc;
   if (splits > 1 && (ws == nullptr || ws_elems < (size_t)splits * g.batch * g.M * g.N)) {
@@ -180,8 +380,6 @@ t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st) {
   }
   if (g.batch * (long)splits > 65535L) return T2S2_EINVAL;
   {
-    const double fl = 2.0 * g.M * g.N * (double)g.K * g.batch;
-    const double by = (double)sizeof(T) * g.batch * ((double)g.M * g.K + (double)g.K * g.N + 2.0 * g.M * g.N);
     TraceScope ts(kTrGemm, st, fl, by);
     launch_any<T>(g, plan.tm, plan.tn, splits, kc, ws, st);
   }
@@ -198,7 +396,7 @@ t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st) {
 
 template size_t gemm_workspace<double>(const Gemm<double>&);
 template size_t gemm_workspace<float>(const Gemm<float>&);
-template t2s2_status gemm<double>(const Gemm<double>&, double*, size_t, cudaStream_t);
-template t2s2_status gemm<float>(const Gemm<float>&, float*, size_t, cudaStream_t);
+template t2s2_status gemm<double>(const Gemm<double>&, double*, size_t, cudaStream_t, int*, long);
+template t2s2_status gemm<float>(const Gemm<float>&, float*, size_t, cudaStream_t, int*, long);
 
 }  // namespace t2s2

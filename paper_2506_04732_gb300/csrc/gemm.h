@@ -23,7 +23,10 @@ struct Gemm {
 template <typename T>
 size_t gemm_workspace(const Gemm<T>& g);
 
+// cnt (ncnt ints, all zero, owned by the caller's stream) lets FP64 split-K
+// products add their partials inside the same launch; the counters are left
+// at zero.  Without it a second launch adds them.
 template <typename T>
-t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st);
+t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st, int* cnt = nullptr, long ncnt = 0);
 
 }  // namespace t2s2

@@ -47,7 +47,11 @@ struct Ctx {
   int coop_ctas = 0;
   // rank of the solver's enrichment for this call (0: the library default)
   int kick = 0;
+  // split-K tile counters of the FP64 GEMM on this context's stream (null:
+  // partial sums are added by a second launch)
+  int* gcnt = nullptr;
 };
+constexpr long kGemmCounters = 16384;
 
 template <typename T>
 inline T* aget(Ctx& cx, size_t n) {
@@ -89,7 +93,7 @@ inline t2s2_status gemm_ex(Ctx& cx, int M, int N, int K, bool tA, bool tB, T alp
   size_t need = gemm_workspace(g);
   size_t mk = cx.ar->mark();
   T* ws = need ? aget<T>(cx, need) : nullptr;
-  t2s2_status s = gemm(g, ws, ws ? need : 0, cx.st);
+  t2s2_status s = gemm(g, ws, ws ? need : 0, cx.st, cx.gcnt, cx.gcnt ? kGemmCounters : 0);
   cx.ar->release(mk);
   return s;
 }

@@ -108,6 +108,8 @@ GEMMS = [
     (5, 3, 0, False, False, 1),        # empty K: C = beta C
     (129, 257, 65, False, False, 1),   # one past every tile edge
     (2000, 40, 4000, True, True, 1),   # long K, many row tiles
+    (17, 9, 700, True, False, 4),      # batched split K added inside the launch
+    (8, 8, 33, False, False, 1),       # K one past a slice
 ]
 
 
