@@ -203,52 +203,34 @@ t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
   return T2S2_OK;
 }
 
-// <u, v> by left-to-right contraction of the interface matrices (GEMMs only).
-// Accurate for the value itself; differences of such dots cancel, so this is
-// used only to screen residuals far above the solver tolerance.
+// <u, v> by left-to-right contraction of the interface matrices (one fused
+// launch, ttdot.cu).  Accurate for the value itself; differences of such dots
+// cancel, so they serve only to screen residuals far above the tolerance.
 t2s2_status tt_dot(Ctx& cx, const DevTT& u, const DevTT& v, double* out) {
-  const int d = u.d;
-  size_t mark = cx.ar->mark();
-  int rmaxu = 1, rmaxv = 1, mm = 1;
-  for (int k = 0; k <= d; ++k) {
-    rmaxu = std::max(rmaxu, u.r[k]);
-    rmaxv = std::max(rmaxv, v.r[k]);
-  }
-  for (int k = 0; k < d; ++k) mm = std::max(mm, u.m[k]);
-  double* phi = aget<double>(cx, (size_t)rmaxu * rmaxv);
-  double* phi2 = aget<double>(cx, (size_t)rmaxu * rmaxv);
-  double* T = aget<double>(cx, (size_t)rmaxv * mm * rmaxu);
-  if (!phi || !phi2 || !T) return T2S2_ENOMEM;
-  T2S2_TRY(dev_fill(cx, phi, 1, 1.0));
-  for (int k = 0; k < d; ++k) {
-    const int ra = u.r[k], rb = u.r[k + 1], sa = v.r[k], sb = v.r[k + 1], m = u.m[k];
-    // T[a', i, b] = sum_a phi[a, a'] U[a, i, b]
-    T2S2_TRY(gemm_ex<double>(cx, sa, m * rb, ra, true, false, 1.0, phi, sa, u.c[k], (long)m * rb, 0.0, T,
-                             (long)m * rb));
-    // phi2[b, b'] = sum_{a', i} T[a', i, b] V[a', i, b']
-    T2S2_TRY(gemm_ex<double>(cx, rb, sb, sa * m, true, false, 1.0, T, rb, v.c[k], sb, 0.0, phi2, sb));
-    std::swap(phi, phi2);
-  }
-  T2S2_CUDA_TRY(cudaMemcpyAsync(cx.hbuf, phi, sizeof(double), cudaMemcpyDeviceToHost, cx.st));
-  T2S2_CUDA_TRY(cudaStreamSynchronize(cx.st));
-  *out = cx.hbuf[0];
-  cx.ar->release(mark);
-  return T2S2_OK;
+  const DevTT* pu[1] = {&u};
+  const DevTT* pv[1] = {&v};
+  return tt_dots(cx, 1, pu, pv, out);
 }
 
-// Residual screen sqrt(|b|^2 - 2<b, A x> + |A x|^2) / |b| (see tt_dot).
+// Residual screen sqrt(|b|^2 - 2<b, A x> + |A x|^2) / |b|, with y = A x and
+// the two (three, when *bb_io < 0: then |b|^2 is returned in *bb_io) inner
+// products in one launch.
 t2s2_status residual_estimate(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
-                              double c_op, double bb, double* out) {
+                              double c_op, double* bb_io, double* out) {
   size_t mark = cx.ar->mark();
   DevTT y;
   int r2[T2S2_MAX_D + 1];
   for (int k = 0; k <= op->d; ++k) r2[k] = (k == 0 || k == op->d) ? 1 : 2 * x.r[k];
   T2S2_TRY(tt_alloc(cx, y, op->d, x.m, r2, 0));
   T2S2_TRY(apply_op(op, cx, x, y, c_mass, c_op, false));
-  double by = 0.0, yy = 0.0;
-  T2S2_TRY(tt_dot(cx, b, y, &by));
-  T2S2_TRY(tt_dot(cx, y, y, &yy));
-  const double r2v = bb - 2.0 * by + yy;
+  const bool with_bb = *bb_io < 0.0;
+  const DevTT* pu[3] = {&b, &y, &b};
+  const DevTT* pv[3] = {&y, &y, &b};
+  double dots[3] = {0.0, 0.0, 0.0};
+  T2S2_TRY(tt_dots(cx, with_bb ? 3 : 2, pu, pv, dots));
+  if (with_bb) *bb_io = dots[2];
+  const double bb = *bb_io;
+  const double r2v = bb - 2.0 * dots[0] + dots[1];
   *out = (bb > 0) ? std::sqrt(std::max(r2v, 0.0) / bb) : std::sqrt(std::max(r2v, 0.0));
   cx.ar->release(mark);
   return T2S2_OK;
@@ -378,6 +360,7 @@ t2s2_status t2s2_op_destroy(t2s2_op op) {
   if (op->hbuf) cudaFreeHost(op->hbuf);
   if (op->dstat) cudaFree(op->dstat);
   if (op->gcnt) cudaFree(op->gcnt);
+  if (op->zcache) cudaFree(op->zcache);
   op->free_solver_buffers();
   delete op;
   return T2S2_OK;

@@ -31,6 +31,10 @@ struct t2s2_op_s {
   double* hbuf = nullptr;  // pinned host scratch
   int* dstat = nullptr;    // device status words
   int* gcnt = nullptr;     // kGemmCounters split-K tile counters (zero between launches)
+  // the solver's right-orthogonalised random start of z for one kick
+  double* zcache = nullptr;
+  size_t zcache_elems = 0;
+  int zcache_kick = 0;
   void free_solver_buffers();
 };
 
@@ -56,8 +60,11 @@ t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mas
 t2s2_status apply_dispatch(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass,
                            double c_op, t2s2_precision prec);
 t2s2_status tt_dot(Ctx& cx, const DevTT& u, const DevTT& v, double* out);
+// Up to four TT inner products <u_p, v_p> in one launch (ttdot.cu); reads
+// the values back (synchronising).
+t2s2_status tt_dots(Ctx& cx, int n, const DevTT* const* u, const DevTT* const* v, double* out);
 t2s2_status residual_estimate(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
-                              double c_op, double bb, double* out);
+                              double c_op, double* bb_io, double* out);
 t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
                           double c_op, bool transformed, double* out, double* bnorm_io);
 }  // namespace t2s2

@@ -167,6 +167,20 @@ struct Amen {
   float* fbuf = nullptr;     // FP32 rhs / x / GMRES basis for the mixed-precision local solves
   bool fp32_local = false;
   long long local_iters = 0;
+  // GMRES count of the sweep's last local solve, copied without a wait
+  static constexpr int kIterSlot = kSmallMax + 16;
+  bool pending_iters = false;
+  int pend_ra = 0, pend_m = 0, pend_rb = 0;
+  t2s2_status collect_iters() {
+    if (!pending_iters) return T2S2_OK;
+    T2S2_CUDA_TRY(cudaStreamSynchronize(cx->st));
+    int it;
+    std::memcpy(&it, cx->hbuf + kIterSlot, sizeof(int));
+    local_iters += it;
+    trace_add_work(kTrLocal, local_flops(pend_ra, pend_m, pend_rb, it, gm_restart), 0.0);
+    pending_iters = false;
+    return T2S2_OK;
+  }
   double c_op = 1.0, c_mass = 0.0;
   int gm_restart = 40, gm_maxit = 600;
   bool tstamp_req = false, tstamp_done = false;
@@ -248,18 +262,43 @@ struct Amen {
       rz[k] = (int)std::min<double>(kick, std::min(left, right));
     }
     T2S2_TRY(tt_alloc(c, z, d, op->m, rz, kick));
-    {
+    size_t zel = 0;
+    for (int k = 0; k < d; ++k) zel += z.core_elems(k);
+    if (op->zcache && op->zcache_kick == kick && op->zcache_elems == zel) {
+      // the right-orthogonalised start of z depends only on the mode sizes
+      // and the kick: kept with the operator after its first use
+      size_t o = 0;
+      for (int k = 0; k < d; ++k) {
+        T2S2_TRY(d2d(c, z.c[k], op->zcache + o, z.core_elems(k)));
+        o += z.core_elems(k);
+      }
+    } else {
       std::mt19937_64 gen(0x5eedULL + d);
       std::normal_distribution<double> nd(0.0, 1.0);
+      std::vector<double> h(zel);
+      for (auto& v : h) v = nd(gen);
+      size_t o = 0;
       for (int k = 0; k < d; ++k) {
-        std::vector<double> h(z.core_elems(k));
-        for (auto& v : h) v = nd(gen);
-        T2S2_CUDA_TRY(cudaMemcpyAsync(z.c[k], h.data(), h.size() * sizeof(double),
+        T2S2_CUDA_TRY(cudaMemcpyAsync(z.c[k], h.data() + o, z.core_elems(k) * sizeof(double),
                                       cudaMemcpyHostToDevice, c.st));
-        T2S2_CUDA_TRY(cudaStreamSynchronize(c.st));
+        o += z.core_elems(k);
       }
+      T2S2_CUDA_TRY(cudaStreamSynchronize(c.st));
+      T2S2_TRY(tt_orth_right(c, z));
+      if (op->zcache_elems < zel) {
+        if (op->zcache) cudaFree(op->zcache);
+        op->zcache = nullptr;
+        op->zcache_elems = 0;
+        T2S2_CUDA_TRY(cudaMalloc(&op->zcache, zel * sizeof(double)));
+      }
+      o = 0;
+      for (int k = 0; k < d; ++k) {
+        T2S2_TRY(d2d(c, op->zcache + o, z.c[k], z.core_elems(k)));
+        o += z.core_elems(k);
+      }
+      op->zcache_elems = zel;
+      op->zcache_kick = kick;
     }
-    T2S2_TRY(tt_orth_right(c, z));
     for (int k = 0; k <= d; ++k) {
       double** arrs[10] = {PL, FL, ZIL, ZBL, ZFL, PR, FR, ZIR, ZBR, ZFR};
       for (auto a : arrs) {
@@ -459,12 +498,10 @@ struct Amen {
       ph(4);
       if (k == d - 1) {
         T2S2_TRY(d2d(c, x.c[k], X, (size_t)ra * m * rb));
-        T2S2_CUDA_TRY(cudaMemcpyAsync(c.hbuf + 8, gm_iters, sizeof(int), cudaMemcpyDeviceToHost, c.st));
-        T2S2_CUDA_TRY(cudaStreamSynchronize(c.st));
-        int it;
-        std::memcpy(&it, c.hbuf + 8, sizeof(int));
-        local_iters += it;
-        trace_add_work(kTrLocal, local_flops(ra, m, rb, it, gm_restart), 0.0);
+        // the count is read after the solver's next synchronisation
+        T2S2_CUDA_TRY(cudaMemcpyAsync(c.hbuf + kIterSlot, gm_iters, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+        pending_iters = true;
+        pend_ra = ra, pend_m = m, pend_rb = rb;
         break;
       }
       // --- truncation: X (rows x rb) = U S V^T
@@ -601,11 +638,10 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
   T2S2_TRY(tt_orth_right(cx, am.x));
   // |b| from <b, b> (a sum of squares: no cancellation), and the same screen
   // as after every sweep for the initial guess
-  double bb = 0.0, res = 0.0;
-  T2S2_TRY(tt_dot(cx, b, b, &bb));
+  double bb = -1.0, res = 0.0, est = 0.0;
+  if (tol < 1e-6) T2S2_TRY(residual_estimate(op, cx, b, am.x, c_mass, c_op, &bb, &est));
+  else T2S2_TRY(tt_dot(cx, b, b, &bb));
   double bnorm = std::sqrt(bb);
-  double est = 0.0;
-  if (tol < 1e-6) T2S2_TRY(residual_estimate(op, cx, b, am.x, c_mass, c_op, bb, &est));
   if (tol < 1e-6 && est > 1e-5) {
     res = est;
   } else {
@@ -624,12 +660,13 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
     // (there its cancellation error, ~sqrt(eps), is irrelevant); the
     // accurate orthogonalised residual alone decides convergence.
     est = 0.0;
-    if (tol < 1e-6) T2S2_TRY(residual_estimate(op, cx, b, am.x, c_mass, c_op, bb, &est));
+    if (tol < 1e-6) T2S2_TRY(residual_estimate(op, cx, b, am.x, c_mass, c_op, &bb, &est));
     if (tol < 1e-6 && est > 1e-5) {
       res = est;
     } else {
       T2S2_TRY(residual_impl(op, cx, b, am.x, c_mass, c_op, false, &res, &bnorm));
     }
+    T2S2_TRY(am.collect_iters());
     if (verbose) {
       double rt = 0.0;
       T2S2_TRY(residual_impl(op, cx, am.f, am.x, c_mass, c_op, true, &rt, nullptr));
@@ -781,7 +818,9 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
       T2S2_TRY(am.sweep());
       ++sweeps;
       ++inner;
-      T2S2_TRY(residual_estimate(op, cx, *rhs, am.x, c_mass, c_op, rnorm * rnorm, &est));
+      double rr = rnorm * rnorm;
+      T2S2_TRY(residual_estimate(op, cx, *rhs, am.x, c_mass, c_op, &rr, &est));
+      T2S2_TRY(am.collect_iters());
       if (verbose) {
         fprintf(stderr, "[t2s2]   inner sweep %d est %.3e ranks", inner, est);
         for (int k = 0; k <= d; ++k) fprintf(stderr, " %d", am.x.r[k]);

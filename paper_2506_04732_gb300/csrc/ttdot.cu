@@ -1,0 +1,171 @@
+// TT inner products <u_p, v_p> (up to kMaxDots of them) in ONE cooperative
+// launch.
+//
+// The residual screens of the solver need <b, y>, <y, y> and <b, b> (y = A x)
+// at once.  As separate GEMM chains they cost two launches per core and
+// product plus a host read-back each; here every product's left-to-right
+// contraction (Methods: TT inner products through the interface matrices)
+// runs in the same grid, with two grid barriers per core:
+//
+//   stage 1:  W_p[a', i, b]  = sum_a        phi_p[a, a'] U_p[a, i, b]
+//   stage 2:  phi_p[b, b']   = sum_{a', i}  W_p[a', i, b] V_p[a', i, b']
+//
+// starting from phi_p = 1 and ending with the 1 x 1 phi_p = <u_p, v_p>.
+// Stage 1 gives each W entry to one thread (two accumulators), stage 2 each
+// phi entry to one warp (lanes over (a', i), then a fixed shuffle tree), so
+// the sums are taken in an order that does not depend on timing.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "api_internal.h"
+#include "trace.h"
+
+namespace cg = cooperative_groups;
+
+namespace t2s2 {
+
+namespace {
+
+constexpr int kDotThreads = 256;
+constexpr int kMaxDots = 4;
+
+struct DotArgs {
+  int n, d;
+  int m[T2S2_MAX_D];
+  int ru[kMaxDots][T2S2_MAX_D + 1], rv[kMaxDots][T2S2_MAX_D + 1];
+  const double* u[kMaxDots][T2S2_MAX_D];
+  const double* v[kMaxDots][T2S2_MAX_D];
+  double* phi[kMaxDots];  // ru_k x rv_k
+  double* w[kMaxDots];    // rv_k x m_k x ru_{k+1}
+  double* out;            // n values
+};
+
+__global__ void __launch_bounds__(kDotThreads) tt_dots_kernel(DotArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  const long nthreads = (long)gridDim.x * kDotThreads;
+  const long gt = (long)blockIdx.x * kDotThreads + threadIdx.x;
+  const long gw = gt >> 5, nwarps = nthreads >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < a.d; ++k) {
+    const int m = a.m[k];
+    long tot = 0;
+    for (int p = 0; p < a.n; ++p) tot += (long)a.rv[p][k] * m * a.ru[p][k + 1];
+    for (long e = gt; e < tot; e += nthreads) {
+      int p = 0;
+      long q = e;
+      while (q >= (long)a.rv[p][k] * m * a.ru[p][k + 1]) q -= (long)a.rv[p][k] * m * a.ru[p][k + 1], ++p;
+      const int ra = a.ru[p][k], rb = a.ru[p][k + 1], sa = a.rv[p][k];
+      const int b = (int)(q % rb);
+      const long ai = q / rb;  // a' * m + i
+      const int i = (int)(ai % m), ap = (int)(ai / m);
+      const double* U = a.u[p][k];
+      double s0 = 0.0, s1 = 0.0;
+      if (k == 0) {
+        s0 = U[(long)i * rb + b];  // phi = 1, ra = sa = 1
+      } else {
+        const double* ph = a.phi[p];
+        int x = 0;
+        for (; x + 1 < ra; x += 2) {
+          s0 = fma(ph[(long)x * sa + ap], U[((long)x * m + i) * rb + b], s0);
+          s1 = fma(ph[(long)(x + 1) * sa + ap], U[((long)(x + 1) * m + i) * rb + b], s1);
+        }
+        if (x < ra) s0 = fma(ph[(long)x * sa + ap], U[((long)x * m + i) * rb + b], s0);
+      }
+      a.w[p][q] = s0 + s1;
+    }
+    grid.sync();
+    long tot2 = 0;
+    for (int p = 0; p < a.n; ++p) tot2 += (long)a.ru[p][k + 1] * a.rv[p][k + 1];
+    for (long it = gw; it < tot2; it += nwarps) {
+      int p = 0;
+      long q = it;
+      while (q >= (long)a.ru[p][k + 1] * a.rv[p][k + 1]) q -= (long)a.ru[p][k + 1] * a.rv[p][k + 1], ++p;
+      const int rb = a.ru[p][k + 1], sb = a.rv[p][k + 1], sa = a.rv[p][k];
+      const int b = (int)(q / sb), bp = (int)(q % sb);
+      const double* W = a.w[p];
+      const double* V = a.v[p][k];
+      const int K = sa * m;
+      double s0 = 0.0, s1 = 0.0;
+      int x = lane;
+      for (; x + 32 < K; x += 64) {
+        s0 = fma(W[(long)x * rb + b], V[(long)x * sb + bp], s0);
+        s1 = fma(W[(long)(x + 32) * rb + b], V[(long)(x + 32) * sb + bp], s1);
+      }
+      if (x < K) s0 = fma(W[(long)x * rb + b], V[(long)x * sb + bp], s0);
+      double s = s0 + s1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) a.phi[p][q] = s;
+    }
+    grid.sync();
+  }
+  if (gt < a.n) a.out[gt] = a.phi[gt][0];
+}
+
+}  // namespace
+
+t2s2_status tt_dots(Ctx& cx, int n, const DevTT* const* u, const DevTT* const* v, double* out) {
+  if (n < 1 || n > kMaxDots) return T2S2_EINVAL;
+  const int d = u[0]->d;
+  DotArgs a;
+  a.n = n;
+  a.d = d;
+  for (int k = 0; k < d; ++k) a.m[k] = u[0]->m[k];
+  size_t mark = cx.ar->mark();
+  long st1 = 0, st2 = 0;
+  double fl = 0.0;
+  for (int p = 0; p < n; ++p) {
+    if (u[p]->d != d || v[p]->d != d) return T2S2_EINVAL;
+    size_t phi_n = 1, w_n = 1;
+    for (int k = 0; k < d; ++k) {
+      if (u[p]->m[k] != a.m[k] || v[p]->m[k] != a.m[k]) return T2S2_EINVAL;
+      a.u[p][k] = u[p]->c[k];
+      a.v[p][k] = v[p]->c[k];
+      phi_n = std::max(phi_n, (size_t)u[p]->r[k + 1] * v[p]->r[k + 1]);
+      w_n = std::max(w_n, (size_t)v[p]->r[k] * a.m[k] * u[p]->r[k + 1]);
+      fl += 2.0 * v[p]->r[k] * a.m[k] * (double)u[p]->r[k + 1] * (u[p]->r[k] + v[p]->r[k + 1]);
+    }
+    for (int k = 0; k <= d; ++k) {
+      a.ru[p][k] = u[p]->r[k];
+      a.rv[p][k] = v[p]->r[k];
+    }
+    a.phi[p] = aget<double>(cx, phi_n);
+    a.w[p] = aget<double>(cx, w_n);
+    if (!a.phi[p] || !a.w[p]) return T2S2_ENOMEM;
+  }
+  for (int k = 0; k < d; ++k) {
+    long s1 = 0, s2 = 0;
+    for (int p = 0; p < n; ++p) {
+      s1 += (long)a.rv[p][k] * a.m[k] * a.ru[p][k + 1];
+      s2 += (long)a.ru[p][k + 1] * a.rv[p][k + 1];
+    }
+    st1 = std::max(st1, s1);
+    st2 = std::max(st2, s2);
+  }
+  a.out = aget<double>(cx, n);
+  if (!a.out) return T2S2_ENOMEM;
+  int dev = 0, sms = 0, per_sm = 0;
+  T2S2_CUDA_TRY(cudaGetDevice(&dev));
+  T2S2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  T2S2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tt_dots_kernel, kDotThreads, 0));
+  long cap = (long)std::max(1, per_sm) * sms;
+  cap = std::min<long>(cap, sms);
+  if (cx.coop_ctas > 0) cap = std::min<long>(cap, cx.coop_ctas);
+  const long want = std::max((st1 + kDotThreads - 1) / kDotThreads, (32 * st2 + kDotThreads - 1) / kDotThreads);
+  const int G = (int)std::max(1L, std::min(cap, want));
+  {
+    TraceScope ts(kTrGemm, cx.st, fl, 0.0);
+    void* args[] = {&a};
+    T2S2_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tt_dots_kernel, dim3(G), dim3(kDotThreads), args, 0,
+                                              cx.st));
+  }
+  T2S2_CUDA_TRY(cudaMemcpyAsync(cx.hbuf, a.out, sizeof(double) * n, cudaMemcpyDeviceToHost, cx.st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(cx.st));
+  for (int p = 0; p < n; ++p) out[p] = cx.hbuf[p];
+  cx.ar->release(mark);
+  return T2S2_OK;
+}
+
+}  // namespace t2s2
