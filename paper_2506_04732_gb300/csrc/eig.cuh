@@ -134,16 +134,22 @@ __device__ bool warp_eig(const TA* A, int lda, int r, EigSmem& s, cf* lam, cf* V
   int hi = r - 1, iter = 0, total = 0;
   bool ok = true;
   while (hi > 0) {
-    int l = hi;
-    while (l > 0) {
-      const float sub = cabsf(t(l, l - 1));
-      const float dg = cabsf(t(l - 1, l - 1)) + cabsf(t(l, l));
-      // deflate when the subdiagonal is negligible relative to its diagonal
-      // neighbours or, norm-wise, to the matrix (a backward-stable
-      // perturbation of eps ||T||; tiny eigenvalues otherwise wait for a
-      // relative test that binary32 noise never lets them pass)
-      if (sub <= eps * fmaxf(dg, tnorm)) break;
-      --l;
+    // the largest l <= hi whose subdiagonal is negligible relative to its
+    // diagonal neighbours or, norm-wise, to the matrix (a backward-stable
+    // perturbation of eps ||T||; tiny eigenvalues otherwise wait for a
+    // relative test that binary32 noise never lets them pass); 0 if none.
+    // Lanes test l = lane + 1 + 32 c in parallel, a ballot picks the largest.
+    int l = 0;
+    for (int c0 = ((hi - 1) / 32) * 32; c0 >= 0 && l == 0; c0 -= 32) {
+      const int li = c0 + lane + 1;
+      bool neg = false;
+      if (li <= hi) {
+        const float sub = sqrtf(cabs2(t(li, li - 1)));
+        const float dg = sqrtf(cabs2(t(li - 1, li - 1))) + sqrtf(cabs2(t(li, li)));
+        neg = sub <= eps * fmaxf(dg, tnorm);
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, neg);
+      if (mask) l = c0 + 32 - __clz(mask);
     }
     __syncwarp();
     if (l > 0 && lane == 0) t(l, l - 1) = cmk(0.f, 0.f);
@@ -171,19 +177,21 @@ __device__ bool warp_eig(const TA* A, int lda, int r, EigSmem& s, cf* lam, cf* V
     }
     cf xx = csub(t(l, l), mu), yy = t(l + 1, l);
     for (int k = l; k < hi; ++k) {
-      const float ax = cabsf(xx), ay = cabsf(yy);
-      const float rr = hypotf(ax, ay);
+      // rotation [c, s; -conj(s), c] with c = |x| / r, s = (x / |x|) conj(y) / r,
+      // r = sqrt(|x|^2 + |y|^2), from binary32 reciprocal square roots
+      const float nx = cabs2(xx), ny = cabs2(yy), n2 = nx + ny;
       float c;
       cf sn;
-      if (rr == 0.f) {
+      if (n2 == 0.f) {
         c = 1.f;
         sn = cmk(0.f, 0.f);
-      } else if (ax == 0.f) {
+      } else if (nx == 0.f) {
         c = 0.f;
-        sn = cscale(cconj(yy), 1.f / ay);
+        sn = cscale(cconj(yy), rsqrtf(ny));
       } else {
-        c = ax / rr;
-        sn = cscale(cmul(cscale(xx, 1.f / ax), cconj(yy)), 1.f / rr);
+        const float ix = rsqrtf(nx), ir = rsqrtf(n2);
+        c = nx * ix * ir;
+        sn = cscale(cmul(cscale(xx, ix), cconj(yy)), ir);
       }
       const cf sbar = cconj(sn);
       for (int j = (k - 1 > l ? k - 1 : l) + lane; j < r; j += 32) {
