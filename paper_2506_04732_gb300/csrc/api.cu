@@ -166,6 +166,20 @@ t2s2_status contract_gemm(Ctx& cx, const Gemm<double>& g) {
   return s;
 }
 
+t2s2_status contract_group(Ctx& cx, const Gemm<double>* gs, int n) {
+  if (cx.contract_prec == T2S2_BF16_REFINE || cx.contract_prec == T2S2_TF32_REFINE || !cx.gcnt || n == 1) {
+    for (int i = 0; i < n; ++i) T2S2_TRY(contract_gemm(cx, gs[i]));
+    return T2S2_OK;
+  }
+  const size_t need = gemm_group_workspace(gs, n);
+  const size_t mk = cx.ar->mark();
+  double* ws = need ? aget<double>(cx, need) : nullptr;
+  if (need && !ws) return T2S2_ENOMEM;
+  const t2s2_status s = gemm_group(gs, n, ws, need, cx.st, cx.gcnt, kGemmCounters);
+  cx.ar->release(mk);
+  return s;
+}
+
 t2s2_status tensor_core_status(Ctx& cx) {
   int h = 0;
   T2S2_CUDA_TRY(cudaMemcpyAsync(cx.hbuf, cx.dstat + kStatTensorCore, sizeof(int), cudaMemcpyDeviceToHost, cx.st));

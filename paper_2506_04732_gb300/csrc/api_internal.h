@@ -51,6 +51,9 @@ t2s2_status unbind_tt(Ctx& cx, const DevTT& dv, t2s2_tt* t);
 constexpr int kStatTensorCore = 16;
 // GEMM of the sweep's contractions in the context's contraction arithmetic.
 t2s2_status contract_gemm(Ctx& cx, const Gemm<double>& g);
+// Independent contractions (no output read or written by another) in one
+// launch where the arithmetic allows, else one after another.
+t2s2_status contract_group(Ctx& cx, const Gemm<double>* gs, int n);
 // Reads (synchronising) and reports the tensor-core wait status word.
 t2s2_status tensor_core_status(Ctx& cx);
 t2s2_status apply_batch(t2s2_op op, const DevTT& x, DevTT& y, double c_mass, double c_op, bool transformed,

@@ -130,18 +130,19 @@ __global__ void splitk_reduce(Gemm<T> g, int splits, const T* ws) {
 // partials in split order.
 constexpr int SBK = 64, SNT = 256;
 
+// One BM x BN tile (column tile nt, row tile mt) of batch entry / split bz;
+// tiles_m x tiles_n tiles per batch entry (the counter index of the tile).
 template <int BM, int BN>
-__global__ void __launch_bounds__(SNT) small_kernel(Gemm<double> g, int splits, int kchunk, double* ws,
-                                                    int* cnt) {
+__device__ __forceinline__ void small_tile(const Gemm<double>& g, int splits, int kchunk, double* ws, int* cnt,
+                                           int nt, int mt, int bz, int tiles_m, int tiles_n) {
   constexpr int NO = BM * BN, KG = SNT / NO;
   static_assert(NO * KG == SNT, "tile must divide the CTA");
   __shared__ double As[SBK][BM + 1];
   __shared__ double Bs[SBK][BN + 1];
   __shared__ double red[KG][NO];
   __shared__ int last;
-  const int bz = blockIdx.z;
   const int b = bz / splits, sidx = bz % splits;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m0 = mt * BM, n0 = nt * BN;
   const int k_begin = sidx * kchunk;
   const int k_end = min(g.K, k_begin + kchunk);
   const double* A = g.A + (long)b * g.sA;
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(SNT) small_kernel(Gemm<double> g, int splits, 
   if (!cnt) return;  // the caller adds the partials with splitk_reduce
   __threadfence();
   __syncthreads();
-  const long tile = ((long)b * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  const long tile = ((long)b * tiles_m + mt) * tiles_n + nt;
   if (t == 0) last = (atomicAdd(cnt + tile, 1) == splits - 1);
   __syncthreads();
   if (!last) return;
@@ -220,6 +221,39 @@ __global__ void __launch_bounds__(SNT) small_kernel(Gemm<double> g, int splits, 
     *c = v;
   }
   if (t == 0) cnt[tile] = 0;  // ready for the next launch on this stream
+}
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(SNT) small_kernel(Gemm<double> g, int splits, int kchunk, double* ws,
+                                                    int* cnt) {
+  small_tile<BM, BN>(g, splits, kchunk, ws, cnt, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.y, gridDim.x);
+}
+
+// Independent GEMMs of one group in one launch: CTA ranges start[i] ..
+// start[i+1] belong to GEMM i, each with its own split plan, workspace and
+// counter range.
+struct GroupArgs {
+  int n;
+  Gemm<double> g[kMaxGroup];
+  int splits[kMaxGroup], kc[kMaxGroup], tm[kMaxGroup], tn[kMaxGroup];
+  long start[kMaxGroup + 1];
+  long wsoff[kMaxGroup], cntoff[kMaxGroup];
+  double* ws;
+  int* cnt;
+};
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(SNT) small_group_kernel(GroupArgs a) {
+  const long bid = blockIdx.x;
+  int i = 0;
+  while (i + 1 < a.n && bid >= a.start[i + 1]) ++i;
+  long q = bid - a.start[i];
+  const int nt = (int)(q % a.tn[i]);
+  q /= a.tn[i];
+  const int mt = (int)(q % a.tm[i]);
+  const int bz = (int)(q / a.tm[i]);
+  small_tile<BM, BN>(a.g[i], a.splits[i], a.kc[i], a.ws + a.wsoff[i], a.cnt + a.cntoff[i], nt, mt, bz, a.tm[i],
+                     a.tn[i]);
 }
 
 inline int tile_code(int x) { return x <= 16 ? 1 : (x <= 32 ? 2 : 4); }
@@ -271,36 +305,51 @@ constexpr double kSmallMaxFmas = 16e6;
 constexpr int kShapes[][2] = {{16, 16}, {8, 16}, {16, 8}, {8, 8}, {4, 16}, {16, 4},
                               {1, 64},  {64, 1}, {4, 4}};
 
+// Best split of g for tile shape bm x bn under the latency model; returns
+// its cost (cycles) and fills splits / kc.
+double plan_shape(const Gemm<double>& g, int bm, int bn, int* splits, int* kcout) {
+  const int kgr = SNT / (bm * bn);
+  const long tiles = (long)cdiv(g.M, bm) * cdiv(g.N, bn) * g.batch;
+  if (g.K <= 0) {
+    *splits = 1;
+    *kcout = 0;
+    return 900.0;
+  }
+  double best = 1e300;
+  const int maxs = (int)std::min<long>(64, std::max(1, cdiv(g.K, 32)));
+  for (int s = 1; s <= maxs; s = (s < 4 ? s + 1 : s * 2)) {
+    if ((long)g.batch * s > 65535L) break;
+    const int kc = cdiv(cdiv(g.K, s), 8) * 8;
+    const int sp = cdiv(g.K, kc);
+    const double chain = 150.0 * ((double)kc / (2.0 * kgr) + kgr);
+    const double loads = 800.0 * cdiv(kc, SBK);
+    const double reduce = sp > 1 ? 900.0 + 150.0 * ((double)sp / kgr + kgr) : 0.0;
+    const long ctas = tiles * sp;
+    const double issue = (double)((ctas + kNumSMs - 1) / kNumSMs) * bm * bn * (double)kc / 2.0;
+    const double cost = std::max(chain + loads, issue) + reduce;
+    if (cost < best * 0.98) {
+      best = cost;
+      *splits = sp;
+      *kcout = kc;
+    }
+  }
+  return best;
+}
+
 SmallPlan plan_small(const Gemm<double>& g) {
   SmallPlan best{false, 8, 8, 1, g.K};
   if ((double)g.M * g.N * (double)std::max(g.K, 1) * g.batch > kSmallMaxFmas) return best;
   best.use = true;
-  if (g.K <= 0) {
-    best.kc = 0;
-    return best;
-  }
   double best_cost = 1e300;
   for (auto& sh : kShapes) {
-    const int bm = sh[0], bn = sh[1], kgr = SNT / (bm * bn);
-    const long tiles = (long)cdiv(g.M, bm) * cdiv(g.N, bn) * g.batch;
-    const int maxs = (int)std::min<long>(64, std::max(1, cdiv(g.K, 32)));
-    for (int s = 1; s <= maxs; s = (s < 4 ? s + 1 : s * 2)) {
-      if ((long)g.batch * s > 65535L) break;
-      int kc = cdiv(cdiv(g.K, s), 8) * 8;
-      const int sp = cdiv(g.K, kc);
-      const double chain = 150.0 * ((double)kc / (2.0 * kgr) + kgr);
-      const double loads = 800.0 * cdiv(kc, SBK);
-      const double reduce = sp > 1 ? 900.0 + 150.0 * ((double)sp / kgr + kgr) : 0.0;
-      const long ctas = tiles * sp;
-      const double issue = (double)((ctas + kNumSMs - 1) / kNumSMs) * bm * bn * (double)kc / 2.0;
-      const double cost = std::max(chain + loads, issue) + reduce;
-      if (cost < best_cost * 0.98) {
-        best_cost = cost;
-        best.bm = bm;
-        best.bn = bn;
-        best.splits = sp;
-        best.kc = kc;
-      }
+    int sp = 1, kc = 0;
+    const double cost = plan_shape(g, sh[0], sh[1], &sp, &kc);
+    if (cost < best_cost * 0.98) {
+      best_cost = cost;
+      best.bm = sh[0];
+      best.bn = sh[1];
+      best.splits = sp;
+      best.kc = kc;
     }
   }
   return best;
@@ -314,6 +363,44 @@ void launch_small(const Gemm<double>& g, const SmallPlan& p, double* ws, int* cn
   T2S2_SMALL(16, 16) T2S2_SMALL(8, 16) T2S2_SMALL(16, 8) T2S2_SMALL(8, 8) T2S2_SMALL(4, 16)
   T2S2_SMALL(16, 4) T2S2_SMALL(1, 64) T2S2_SMALL(64, 1) T2S2_SMALL(4, 4)
 #undef T2S2_SMALL
+}
+
+void launch_group(const GroupArgs& a, int bm, int bn, cudaStream_t st) {
+  const long ctas = a.start[a.n];
+#define T2S2_GROUP(x, y) \
+  if (bm == x && bn == y) { small_group_kernel<x, y><<<(unsigned)ctas, SNT, 0, st>>>(a); return; }
+  T2S2_GROUP(16, 16) T2S2_GROUP(8, 16) T2S2_GROUP(16, 8) T2S2_GROUP(8, 8) T2S2_GROUP(4, 16)
+  T2S2_GROUP(16, 4) T2S2_GROUP(1, 64) T2S2_GROUP(64, 1) T2S2_GROUP(4, 4)
+#undef T2S2_GROUP
+}
+
+// Shape of a group: the tile shape whose worst member cost is least.
+struct GroupPlan {
+  bool ok;
+  int bm, bn;
+  int splits[kMaxGroup], kc[kMaxGroup];
+};
+
+GroupPlan plan_group(const Gemm<double>* gs, int n) {
+  GroupPlan gp;
+  gp.ok = false;
+  gp.bm = gp.bn = 8;
+  for (int i = 0; i < n; ++i)
+    if ((double)gs[i].M * gs[i].N * (double)std::max(gs[i].K, 1) * gs[i].batch > kSmallMaxFmas) return gp;
+  double best = 1e300;
+  for (auto& sh : kShapes) {
+    double worst = 0.0;
+    int sp[kMaxGroup], kc[kMaxGroup];
+    for (int i = 0; i < n; ++i) worst = std::max(worst, plan_shape(gs[i], sh[0], sh[1], &sp[i], &kc[i]));
+    if (worst < best * 0.98) {
+      best = worst;
+      gp.bm = sh[0];
+      gp.bn = sh[1];
+      for (int i = 0; i < n; ++i) gp.splits[i] = sp[i], gp.kc[i] = kc[i];
+    }
+  }
+  gp.ok = true;
+  return gp;
 }
 
 template <typename T, int TM, int TN>
@@ -391,6 +478,68 @@ t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st, int*
     splitk_reduce<T><<<blocks, 256, 0, st>>>(g, splits, ws);
     T2S2_CUDA_TRY(cudaGetLastError());
   }
+  return T2S2_OK;
+}
+
+size_t gemm_group_workspace(const Gemm<double>* gs, int n) {
+  if (n < 1 || n > kMaxGroup) return 0;
+  const GroupPlan gp = plan_group(gs, n);
+  if (!gp.ok) return 0;
+  size_t w = 0;
+  for (int i = 0; i < n; ++i)
+    if (gp.splits[i] > 1) w += (size_t)gp.splits[i] * gs[i].batch * gs[i].M * gs[i].N;
+  return w;
+}
+
+t2s2_status gemm_group(const Gemm<double>* gs, int n, double* ws, size_t ws_elems, cudaStream_t st, int* cnt,
+                       long ncnt) {
+  if (n < 1 || n > kMaxGroup) return T2S2_EINVAL;
+  const GroupPlan gp = plan_group(gs, n);
+  bool fallback = !gp.ok || !cnt;
+  GroupArgs a;
+  a.n = 0;
+  long ctas = 0, wso = 0, cno = 0;
+  double fl = 0.0, by = 0.0;
+  if (!fallback) {
+    for (int i = 0; i < n; ++i) {
+      const Gemm<double>& g = gs[i];
+      if (g.M <= 0 || g.N <= 0 || g.batch <= 0) continue;
+      const int j = a.n++;
+      a.g[j] = g;
+      a.splits[j] = gp.splits[i];
+      a.kc[j] = std::max(gp.kc[i], 1);
+      a.tm[j] = cdiv(g.M, gp.bm);
+      a.tn[j] = cdiv(g.N, gp.bn);
+      a.start[j] = ctas;
+      const long tiles = (long)a.tm[j] * a.tn[j] * g.batch;
+      ctas += tiles * a.splits[j];
+      a.wsoff[j] = wso;
+      a.cntoff[j] = cno;
+      if (a.splits[j] > 1) {
+        wso += (long)a.splits[j] * g.batch * g.M * g.N;
+        cno += tiles;
+      }
+      if ((long)g.batch * a.splits[j] > 65535L) fallback = true;
+      fl += 2.0 * g.M * g.N * (double)g.K * g.batch;
+      by += 8.0 * g.batch * ((double)g.M * g.K + (double)g.K * g.N + 2.0 * g.M * g.N);
+    }
+    a.start[a.n] = ctas;
+    if ((size_t)wso > ws_elems || (wso > 0 && !ws) || cno > ncnt || ctas > (1L << 30)) fallback = true;
+  }
+  if (fallback) {
+    // one launch per product, in stream order, each reusing the workspace
+    // (a product whose split does not fit runs unsplit)
+    for (int i = 0; i < n; ++i) T2S2_TRY(gemm(gs[i], ws, ws ? ws_elems : 0, st, cnt, ncnt));
+    return T2S2_OK;
+  }
+  if (a.n == 0) return T2S2_OK;
+  a.ws = ws;
+  a.cnt = cnt;
+  {
+    TraceScope ts(kTrGemm, st, fl, by);
+    launch_group(a, gp.bm, gp.bn, st);
+  }
+  T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 

@@ -29,4 +29,13 @@ size_t gemm_workspace(const Gemm<T>& g);
 template <typename T>
 t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st, int* cnt = nullptr, long ncnt = 0);
 
+// Up to kMaxGroup independent FP64 products (no output shared with another's
+// input or output) in one launch; each keeps its own split of K, whose
+// partials are added inside the launch (cnt required, else one launch per
+// product).  Workspace: gemm_group_workspace elements.
+constexpr int kMaxGroup = 8;
+size_t gemm_group_workspace(const Gemm<double>* gs, int n);
+t2s2_status gemm_group(const Gemm<double>* gs, int n, double* ws, size_t ws_elems, cudaStream_t st, int* cnt,
+                       long ncnt);
+
 }  // namespace t2s2

@@ -44,34 +44,54 @@ Gemm<double> gdesc(int M, int N, int K, bool tA, bool tB, double alpha, const do
   return g;
 }
 // Mode products of a core X (ra x m x rb) and the interface contractions, in
-// the context's contraction arithmetic.
+// the context's contraction arithmetic: descriptors (for grouped launches)
+// and single calls.
 // Y[c,i,b] = sum_a P[c,a] X[a,i,b]
-t2s2_status mode1(Ctx& cx, const double* P, int rn, int ro, const double* X, int m, int rb, double* Y,
-                  double alpha = 1.0, double beta = 0.0) {
-  return contract_gemm(cx, gdesc(rn, m * rb, ro, false, false, alpha, P, ro, X, (long)m * rb, beta, Y,
-                                 (long)m * rb));
+Gemm<double> g_mode1(const double* P, int rn, int ro, const double* X, int m, int rb, double* Y,
+                     double alpha = 1.0, double beta = 0.0) {
+  return gdesc(rn, m * rb, ro, false, false, alpha, P, ro, X, (long)m * rb, beta, Y, (long)m * rb);
 }
 // Y[a,i,b] = sum_j B[i,j] X[a,j,b]
-t2s2_status mode2(Ctx& cx, const double* B, int m, const double* X, int ra, int rb, double* Y,
-                  double alpha = 1.0, double beta = 0.0) {
-  return contract_gemm(cx, gdesc(m, rb, m, false, false, alpha, B, m, X, rb, beta, Y, rb, ra, 0,
-                                 (long)m * rb, (long)m * rb));
+Gemm<double> g_mode2(const double* B, int m, const double* X, int ra, int rb, double* Y, double alpha = 1.0,
+                     double beta = 0.0) {
+  return gdesc(m, rb, m, false, false, alpha, B, m, X, rb, beta, Y, rb, ra, 0, (long)m * rb, (long)m * rb);
 }
 // Y[a,i,c] = sum_b X[a,i,b] Q[c,b]
-t2s2_status mode3(Ctx& cx, const double* X, int ra, int m, int ro, const double* Q, int rn, double* Y,
-                  double alpha = 1.0, double beta = 0.0) {
-  return contract_gemm(cx, gdesc(ra * m, rn, ro, false, true, alpha, X, ro, Q, ro, beta, Y, rn));
+Gemm<double> g_mode3(const double* X, int ra, int m, int ro, const double* Q, int rn, double* Y,
+                     double alpha = 1.0, double beta = 0.0) {
+  return gdesc(ra * m, rn, ro, false, true, alpha, X, ro, Q, ro, beta, Y, rn);
 }
 // out[b][c] = sum_{a,i} U[a,i,b] T[a,i,c]
-t2s2_status contract_left(Ctx& cx, const double* U, int ra, int m, int rb, const double* T, int rc,
-                          double* out) {
-  return contract_gemm(cx, gdesc(rb, rc, ra * m, true, false, 1.0, U, rb, T, rc, 0.0, out, rc));
+Gemm<double> g_cleft(const double* U, int ra, int m, int rb, const double* T, int rc, double* out) {
+  return gdesc(rb, rc, ra * m, true, false, 1.0, U, rb, T, rc, 0.0, out, rc);
 }
 // out[a][c] = sum_{i,b} U[a,i,b] T[c,i,b]
+Gemm<double> g_cright(const double* U, int ra, int m, int rb, const double* T, int rc, double* out) {
+  return gdesc(ra, rc, m * rb, false, true, 1.0, U, (long)m * rb, T, (long)m * rb, 0.0, out, rc);
+}
+t2s2_status mode1(Ctx& cx, const double* P, int rn, int ro, const double* X, int m, int rb, double* Y,
+                  double alpha = 1.0, double beta = 0.0) {
+  return contract_gemm(cx, g_mode1(P, rn, ro, X, m, rb, Y, alpha, beta));
+}
+t2s2_status mode2(Ctx& cx, const double* B, int m, const double* X, int ra, int rb, double* Y,
+                  double alpha = 1.0, double beta = 0.0) {
+  return contract_gemm(cx, g_mode2(B, m, X, ra, rb, Y, alpha, beta));
+}
+t2s2_status mode3(Ctx& cx, const double* X, int ra, int m, int ro, const double* Q, int rn, double* Y,
+                  double alpha = 1.0, double beta = 0.0) {
+  return contract_gemm(cx, g_mode3(X, ra, m, ro, Q, rn, Y, alpha, beta));
+}
+t2s2_status contract_left(Ctx& cx, const double* U, int ra, int m, int rb, const double* T, int rc,
+                          double* out) {
+  return contract_gemm(cx, g_cleft(U, ra, m, rb, T, rc, out));
+}
 t2s2_status contract_right(Ctx& cx, const double* U, int ra, int m, int rb, const double* T, int rc,
                            double* out) {
-  return contract_gemm(cx, gdesc(ra, rc, m * rb, false, true, 1.0, U, (long)m * rb, T, (long)m * rb, 0.0,
-                                 out, rc));
+  return contract_gemm(cx, g_cright(U, ra, m, rb, T, rc, out));
+}
+template <int N>
+t2s2_status group(Ctx& cx, const Gemm<double> (&gs)[N]) {
+  return contract_group(cx, gs, N);
 }
 t2s2_status d2d(Ctx& cx, double* dst, const double* src, size_t n) {
   if (n == 0) return T2S2_OK;
@@ -355,25 +375,26 @@ struct Amen {
       const int m = op->m[k];
       const int ra = x.r[k], rb = x.r[k + 1], fa = f.r[k], fb = f.r[k + 1], za = z.r[k], zb = z.r[k + 1];
       const double *X = x.c[k], *F = f.c[k], *Z = z.c[k];
-      double *T1 = tmp[0], *T2 = tmp[1], *BX = tmp[2];
-      // PR[k] = X (X x_3 PR[k+1] + B' x_2 X)
-      T2S2_TRY(mode2(c, Bp[k], m, X, ra, rb, BX));
-      T2S2_TRY(d2d(c, T1, BX, (size_t)ra * m * rb));
-      T2S2_TRY(mode3(c, X, ra, m, rb, PR[k + 1], rb, T1, 1.0, 1.0));
-      T2S2_TRY(contract_right(c, X, ra, m, rb, T1, ra, PR[k]));
-      // FR[k] = X (F x_3 FR[k+1])
-      T2S2_TRY(mode3(c, F, fa, m, fb, FR[k + 1], rb, T2));
-      T2S2_TRY(contract_right(c, X, ra, m, rb, T2, fa, FR[k]));
-      // ZIR[k] = Z (X x_3 ZIR[k+1])
-      T2S2_TRY(mode3(c, X, ra, m, rb, ZIR[k + 1], zb, T1));
-      T2S2_TRY(contract_right(c, Z, za, m, zb, T1, ra, ZIR[k]));
-      // ZBR[k] = Z (X x_3 ZBR[k+1] + (B' X) x_3 ZIR[k+1])
-      T2S2_TRY(mode3(c, X, ra, m, rb, ZBR[k + 1], zb, T1));
-      T2S2_TRY(mode3(c, BX, ra, m, rb, ZIR[k + 1], zb, T1, 1.0, 1.0));
-      T2S2_TRY(contract_right(c, Z, za, m, zb, T1, ra, ZBR[k]));
-      // ZFR[k] = Z (F x_3 ZFR[k+1])
-      T2S2_TRY(mode3(c, F, fa, m, fb, ZFR[k + 1], zb, T2));
-      T2S2_TRY(contract_right(c, Z, za, m, zb, T2, fa, ZFR[k]));
+      double *BX = tmp[0], *A1 = tmp[1], *A2 = tmp[2], *A3 = tmp[3], *A4 = tmp[4], *A5 = tmp[5];
+      // PR[k] = X (X x_3 PR[k+1] + B' x_2 X),  FR[k] = X (F x_3 FR[k+1]),
+      // ZIR[k] = Z (X x_3 ZIR[k+1]),  ZBR[k] = Z (X x_3 ZBR[k+1] + (B' X) x_3 ZIR[k+1]),
+      // ZFR[k] = Z (F x_3 ZFR[k+1]): three launches of independent products
+      const Gemm<double> s1[] = {g_mode2(Bp[k], m, X, ra, rb, BX),
+                                 g_mode2(Bp[k], m, X, ra, rb, A1),
+                                 g_mode3(F, fa, m, fb, FR[k + 1], rb, A2),
+                                 g_mode3(X, ra, m, rb, ZIR[k + 1], zb, A3),
+                                 g_mode3(X, ra, m, rb, ZBR[k + 1], zb, A4),
+                                 g_mode3(F, fa, m, fb, ZFR[k + 1], zb, A5)};
+      T2S2_TRY(group(c, s1));
+      const Gemm<double> s2[] = {g_mode3(X, ra, m, rb, PR[k + 1], rb, A1, 1.0, 1.0),
+                                 g_mode3(BX, ra, m, rb, ZIR[k + 1], zb, A4, 1.0, 1.0)};
+      T2S2_TRY(group(c, s2));
+      const Gemm<double> s3[] = {g_cright(X, ra, m, rb, A1, ra, PR[k]),
+                                 g_cright(X, ra, m, rb, A2, fa, FR[k]),
+                                 g_cright(Z, za, m, zb, A3, ra, ZIR[k]),
+                                 g_cright(Z, za, m, zb, A4, ra, ZBR[k]),
+                                 g_cright(Z, za, m, zb, A5, fa, ZFR[k])};
+      T2S2_TRY(group(c, s3));
     }
     return T2S2_OK;
   }
@@ -539,24 +560,34 @@ struct Amen {
       T2S2_TRY(dev_sv_t(c, SV, svals, Vx, rk, rb, kk));
       T2S2_TRY(gemm_ex<double>(c, rows, rb, rk, false, false, 1.0, U, rk, SV, rb, 0.0, Xt, rb));
       ph(5);
-      // --- enrichment directions: residual on (x-left) x m x (z-right)
+      // --- enrichment directions: residual on (x-left) x m x (z-right),
+      //   res  = (FL F) x_3 ZFR - (B' Xt + PL Xt) x_3 ZIR - Xt x_3 ZBR,
+      // --- z update: residual on (z-left) x m x (z-right),
+      //   zres = (ZFL F) x_3 ZFR - (ZBL Xt + ZIL B' Xt) x_3 ZIR - (ZIL Xt) x_3 ZBR;
+      // four launches of independent products.  tmp[0] still holds FL[k] x_1 F
+      // from the local right-hand side.
+      double *Tz = tmp[2], *T2b = tmp[3];  // T1 = tmp[0], T2 = tmp[1]
       double *BX = tmp[5], *Y1 = tmp[6], *res = tmp[7], *zres = tmp[8];
-      T2S2_TRY(mode2(c, Bp[k], m, Xt, ra, rb, BX));
-      T2S2_TRY(d2d(c, Y1, BX, (size_t)ra * m * rb));
-      T2S2_TRY(mode1(c, PL[k], ra, ra, Xt, m, rb, Y1, 1.0, 1.0));
-      T2S2_TRY(mode1(c, FL[k], ra, fa, F, m, fb, T1));
-      T2S2_TRY(mode3(c, T1, ra, m, fb, ZFR[k + 1], zb, res));
-      T2S2_TRY(mode3(c, Y1, ra, m, rb, ZIR[k + 1], zb, res, -1.0, 1.0));
-      T2S2_TRY(mode3(c, Xt, ra, m, rb, ZBR[k + 1], zb, res, -1.0, 1.0));
+      {
+        const Gemm<double> s1[] = {g_mode2(Bp[k], m, Xt, ra, rb, BX),
+                                   g_mode2(Bp[k], m, Xt, ra, rb, Y1),
+                                   g_mode1(ZFL[k], za, fa, F, m, fb, Tz),
+                                   g_mode1(ZBL[k], za, ra, Xt, m, rb, T2),
+                                   g_mode1(ZIL[k], za, ra, Xt, m, rb, T2b)};
+        T2S2_TRY(group(c, s1));
+        const Gemm<double> s2[] = {g_mode1(PL[k], ra, ra, Xt, m, rb, Y1, 1.0, 1.0),
+                                   g_mode1(ZIL[k], za, ra, BX, m, rb, T2, 1.0, 1.0),
+                                   g_mode3(T1, ra, m, fb, ZFR[k + 1], zb, res),
+                                   g_mode3(Tz, za, m, fb, ZFR[k + 1], zb, zres)};
+        T2S2_TRY(group(c, s2));
+        const Gemm<double> s3[] = {g_mode3(Y1, ra, m, rb, ZIR[k + 1], zb, res, -1.0, 1.0),
+                                   g_mode3(T2, za, m, rb, ZIR[k + 1], zb, zres, -1.0, 1.0)};
+        T2S2_TRY(group(c, s3));
+        const Gemm<double> s4[] = {g_mode3(Xt, ra, m, rb, ZBR[k + 1], zb, res, -1.0, 1.0),
+                                   g_mode3(T2b, za, m, rb, ZBR[k + 1], zb, zres, -1.0, 1.0)};
+        T2S2_TRY(group(c, s4));
+      }
       ph(6);
-      // --- z update: residual on (z-left) x m x (z-right)
-      T2S2_TRY(mode1(c, ZFL[k], za, fa, F, m, fb, T1));
-      T2S2_TRY(mode3(c, T1, za, m, fb, ZFR[k + 1], zb, zres));
-      T2S2_TRY(mode1(c, ZBL[k], za, ra, Xt, m, rb, T2));
-      T2S2_TRY(mode1(c, ZIL[k], za, ra, BX, m, rb, T2, 1.0, 1.0));
-      T2S2_TRY(mode3(c, T2, za, m, rb, ZIR[k + 1], zb, zres, -1.0, 1.0));
-      T2S2_TRY(mode1(c, ZIL[k], za, ra, Xt, m, rb, T2));
-      T2S2_TRY(mode3(c, T2, za, m, rb, ZBR[k + 1], zb, zres, -1.0, 1.0));
       {
         double* Rz = tmp[1];
         double* Qz = tmp[0];
@@ -599,24 +630,30 @@ struct Amen {
         x.r[k + 1] = rn;
       }
       ph(8);
-      // --- left interfaces for bond k+1
+      // --- left interfaces for bond k+1:
+      //   PL' = Qc^T (PL Qc + B' Qc),  FL' = Qc^T (FL F),  ZIL' = Z^T (ZIL Qc),
+      //   ZBL' = Z^T (ZBL Qc + ZIL B' Qc),  ZFL' = Z^T (ZFL F)
+      // in three launches of independent products
       {
         const double* Qc = x.c[k];
         const double* Z = z.c[k];
-        double *T3 = tmp[3], *BQ = tmp[4];
-        T2S2_TRY(mode2(c, Bp[k], m, Qc, ra, rn, BQ));
-        T2S2_TRY(d2d(c, T3, BQ, (size_t)ra * m * rn));
-        T2S2_TRY(mode1(c, PL[k], ra, ra, Qc, m, rn, T3, 1.0, 1.0));
-        T2S2_TRY(contract_left(c, Qc, ra, m, rn, T3, rn, PL[k + 1]));
-        T2S2_TRY(mode1(c, FL[k], ra, fa, F, m, fb, T3));
-        T2S2_TRY(contract_left(c, Qc, ra, m, rn, T3, fb, FL[k + 1]));
-        T2S2_TRY(mode1(c, ZIL[k], za, ra, Qc, m, rn, T3));
-        T2S2_TRY(contract_left(c, Z, za, m, zb, T3, rn, ZIL[k + 1]));
-        T2S2_TRY(mode1(c, ZBL[k], za, ra, Qc, m, rn, T3));
-        T2S2_TRY(mode1(c, ZIL[k], za, ra, BQ, m, rn, T3, 1.0, 1.0));
-        T2S2_TRY(contract_left(c, Z, za, m, zb, T3, rn, ZBL[k + 1]));
-        T2S2_TRY(mode1(c, ZFL[k], za, fa, F, m, fb, T3));
-        T2S2_TRY(contract_left(c, Z, za, m, zb, T3, fb, ZFL[k + 1]));
+        double *BQ = tmp[3], *A1 = tmp[4], *A2 = tmp[5], *A3 = tmp[6], *A4 = tmp[7], *A5 = tmp[8];
+        const Gemm<double> s1[] = {g_mode2(Bp[k], m, Qc, ra, rn, BQ),
+                                   g_mode2(Bp[k], m, Qc, ra, rn, A1),
+                                   g_mode1(FL[k], ra, fa, F, m, fb, A2),
+                                   g_mode1(ZIL[k], za, ra, Qc, m, rn, A3),
+                                   g_mode1(ZBL[k], za, ra, Qc, m, rn, A4),
+                                   g_mode1(ZFL[k], za, fa, F, m, fb, A5)};
+        T2S2_TRY(group(c, s1));
+        const Gemm<double> s2[] = {g_mode1(PL[k], ra, ra, Qc, m, rn, A1, 1.0, 1.0),
+                                   g_mode1(ZIL[k], za, ra, BQ, m, rn, A4, 1.0, 1.0)};
+        T2S2_TRY(group(c, s2));
+        const Gemm<double> s3[] = {g_cleft(Qc, ra, m, rn, A1, rn, PL[k + 1]),
+                                   g_cleft(Qc, ra, m, rn, A2, fb, FL[k + 1]),
+                                   g_cleft(Z, za, m, zb, A3, rn, ZIL[k + 1]),
+                                   g_cleft(Z, za, m, zb, A4, rn, ZBL[k + 1]),
+                                   g_cleft(Z, za, m, zb, A5, fb, ZFL[k + 1])};
+        T2S2_TRY(group(c, s3));
       }
     }
     return T2S2_OK;
