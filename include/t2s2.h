@@ -207,7 +207,10 @@ t2s2_status t2s2_norm_noalloc(const t2s2_tt* x, double* out, void* stream);
  * Errors: T2S2_EINVAL for mismatched shapes. */
 t2s2_status t2s2_diff_norm(t2s2_op op, const t2s2_tt* x, const t2s2_tt* y, double* out, void* stream);
 
-/* ||b - (c_mass M + c_op A) x||_F / ||b||_F, accurate difference norm, FP64. */
+/* ||b - (c_mass M + c_op A) x||_F / ||b||_F in FP64, accurate even where A x
+ * agrees with b to many digits: z = b - A x is formed as a TT and <z, z> is
+ * accumulated in double-double (error-free products and sums); a result below
+ * 1e-11 is recomputed as the norm of the right-orthogonalised z. */
 t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double c_mass,
                           double c_op, double* out, void* stream);
 
@@ -218,7 +221,7 @@ t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double
  * tol/sqrt(d), residual-based rank enrichment, until the true relative
  * residual ||b - (c_mass M + c_op A) x||_F / ||b||_F <= tol or max_sweeps.
  * b is the right-hand side sampled on the collocation grid; x holds the
- * initial guess on input and the solution on output (ranks <= rmax + 4).
+ * initial guess on input and the solution on output (ranks <= rmax + T2S2_RANK_KICK).
  * Returns T2S2_ENOCONV (with x and info filled) if the sweep cap is hit.
  * The plain solve is c_mass = 0, c_op = 1.
  */

@@ -217,6 +217,37 @@ t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
   return T2S2_OK;
 }
 
+// ||b - (c_mass M + c_op A) x|| / ||b|| through <z, z> in double-double
+// (ttdot.cu), z = b - A x as a TT sum: no orthogonalisation of z.  Where the
+// result falls below kDDFloor (relative), the double-double noise (~1e-14
+// relative in the norm) could matter, and the orthogonalised norm of
+// residual_impl is taken instead.
+constexpr double kDDFloor = 1e-11;
+
+t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,
+                          double* out, double* bnorm_io) {
+  size_t mark = cx.ar->mark();
+  DevTT y;
+  int r2[T2S2_MAX_D + 1];
+  for (int k = 0; k <= op->d; ++k) r2[k] = (k == 0 || k == op->d) ? 1 : 2 * x.r[k];
+  T2S2_TRY(tt_alloc(cx, y, op->d, x.m, r2, 0));
+  T2S2_TRY(apply_op(op, cx, x, y, c_mass, c_op, false));
+  DevTT z;
+  T2S2_TRY(tt_axpby(cx, 1.0, b, -1.0, y, z));
+  const bool with_b = *bnorm_io < 0.0;
+  const DevTT* pu[2] = {&z, &b};
+  double hi[2] = {0.0, 0.0}, lo[2] = {0.0, 0.0};
+  T2S2_TRY(tt_norm2_dd(cx, with_b ? 2 : 1, pu, hi, lo));
+  if (with_b) *bnorm_io = std::sqrt(std::max(hi[1] + lo[1], 0.0));
+  const double bn = *bnorm_io;
+  const double zn = std::sqrt(std::max(hi[0] + lo[0], 0.0));
+  double res = (bn > 0) ? zn / bn : zn;
+  cx.ar->release(mark);
+  if (res < kDDFloor) T2S2_TRY(residual_impl(op, cx, b, x, c_mass, c_op, false, &res, bnorm_io));
+  *out = res;
+  return T2S2_OK;
+}
+
 // <u, v> by left-to-right contraction of the interface matrices (one fused
 // launch, ttdot.cu).  Accurate for the value itself; differences of such dots
 // cancel, so they serve only to screen residuals far above the tolerance.
@@ -485,7 +516,8 @@ t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double
   DevTT db, dx;
   T2S2_TRY(bind_tt(cx, b, db, true));
   T2S2_TRY(bind_tt(cx, x, dx, true));
-  return residual_impl(op, cx, db, dx, c_mass, c_op, false, out, nullptr);
+  double bnorm = -1.0;
+  return residual_fast(op, cx, db, dx, c_mass, c_op, out, &bnorm);
 }
 
 }  // extern "C"

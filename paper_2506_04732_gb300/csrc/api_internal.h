@@ -68,6 +68,12 @@ t2s2_status tt_dot(Ctx& cx, const DevTT& u, const DevTT& v, double* out);
 t2s2_status tt_dots(Ctx& cx, int n, const DevTT* const* u, const DevTT* const* v, double* out);
 t2s2_status residual_estimate(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
                               double c_op, double* bb_io, double* out);
+// <u_p, u_p> in double-double for p < n <= 4 (ttdot.cu), as hi + lo pairs.
+t2s2_status tt_norm2_dd(Ctx& cx, int n, const DevTT* const* u, double* hi, double* lo);
+// The residual of the original system from <z, z> in double-double, falling
+// back to residual_impl's orthogonalised norm for residuals below 1e-11.
+t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,
+                          double* out, double* bnorm_io);
 t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
                           double c_op, bool transformed, double* out, double* bnorm_io);
 }  // namespace t2s2

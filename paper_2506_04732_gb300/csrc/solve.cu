@@ -673,17 +673,9 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
   am.ph(0);
   T2S2_TRY(am.init(op, cx, b, xio, c_mass, c_op, tol, rmax));
   T2S2_TRY(tt_orth_right(cx, am.x));
-  // |b| from <b, b> (a sum of squares: no cancellation), and the same screen
-  // as after every sweep for the initial guess
-  double bb = -1.0, res = 0.0, est = 0.0;
-  if (tol < 1e-6) T2S2_TRY(residual_estimate(op, cx, b, am.x, c_mass, c_op, &bb, &est));
-  else T2S2_TRY(tt_dot(cx, b, b, &bb));
-  double bnorm = std::sqrt(bb);
-  if (tol < 1e-6 && est > 1e-5) {
-    res = est;
-  } else {
-    T2S2_TRY(residual_impl(op, cx, b, am.x, c_mass, c_op, false, &res, &bnorm));
-  }
+  // the residual of the original system, before and after every sweep
+  double bnorm = -1.0, res = 0.0;
+  T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &bnorm));
   int sweeps = 0;
   const char* ev = std::getenv("T2S2_VERBOSE");
   const bool verbose = ev && ev[0] == '1';
@@ -693,16 +685,7 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
     T2S2_TRY(am.sweep());
     ++sweeps;
     am.ph(9);
-    // Screen with the dot-product residual while it is far above tolerance
-    // (there its cancellation error, ~sqrt(eps), is irrelevant); the
-    // accurate orthogonalised residual alone decides convergence.
-    est = 0.0;
-    if (tol < 1e-6) T2S2_TRY(residual_estimate(op, cx, b, am.x, c_mass, c_op, &bb, &est));
-    if (tol < 1e-6 && est > 1e-5) {
-      res = est;
-    } else {
-      T2S2_TRY(residual_impl(op, cx, b, am.x, c_mass, c_op, false, &res, &bnorm));
-    }
+    T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &bnorm));
     T2S2_TRY(am.collect_iters());
     if (verbose) {
       double rt = 0.0;
@@ -804,7 +787,7 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
     cx.ar->release(mk);
   }
   double bnorm = -1.0, res = 0.0;
-  T2S2_TRY(residual_impl(op, cx, b, x, c_mass, c_op, false, &res, &bnorm));
+  T2S2_TRY(residual_fast(op, cx, b, x, c_mass, c_op, &res, &bnorm));
   bool x_zero = false;
   if (res >= 1.0) {  // x0 is worse than x = 0
     x_zero = true;
@@ -880,7 +863,7 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
       ++refinements;
       if (verbose) {
         double rg = 0.0;
-        T2S2_TRY(residual_impl(op, cx, b, g, c_mass, c_op, false, &rg, &bnorm));
+        T2S2_TRY(residual_fast(op, cx, b, g, c_mass, c_op, &rg, &bnorm));
         fprintf(stderr, "[t2s2] tensor-core stage: inner sweeps %d est %.2e residual %.3e\n", inner, est, rg);
       }
       continue;
@@ -909,7 +892,7 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
     x_zero = false;
     ++refinements;
     const double prev = res;
-    T2S2_TRY(residual_impl(op, cx, b, x, c_mass, c_op, false, &res, &bnorm));
+    T2S2_TRY(residual_fast(op, cx, b, x, c_mass, c_op, &res, &bnorm));
     if (verbose) {
       fprintf(stderr, "[t2s2] refinement %d: inner sweeps %d est %.2e (target %.1e) residual %.3e ranks", refinements,
               inner, est, tin, res);

@@ -104,7 +104,186 @@ __global__ void __launch_bounds__(kDotThreads) tt_dots_kernel(DotArgs a) {
   if (gt < a.n) a.out[gt] = a.phi[gt][0];
 }
 
+// ---------------------------------------------------------------------------
+// <u, u> in double-double arithmetic: every product of binary64 inputs is
+// split exactly (p + e = a b through an FMA) and every sum is an error-free
+// two-sum, so the environments carry ~2^-104 relative precision.  For a
+// residual z = b - A x the terms of <z, z> are of the size |b|^2 while the
+// result is |b - A x|^2, many orders smaller; in binary64 the cancellation
+// leaves noise of ~1e-16 |b|^2, in double-double ~1e-28 |b|^2, so the
+// norm of a residual down to ~1e-11 |b| comes out to three or more digits
+// without orthogonalising z.
+
+struct DDArgs {
+  int n, d;
+  int m[T2S2_MAX_D];
+  int r[kMaxDots][T2S2_MAX_D + 1];
+  const double* u[kMaxDots][T2S2_MAX_D];
+  double* phh[kMaxDots];  // phi, high and low parts (r_k x r_k)
+  double* phl[kMaxDots];
+  double* wh[kMaxDots];   // W, high and low parts (r_k x m_k x r_{k+1})
+  double* wl[kMaxDots];
+  double* out;            // n (hi, lo) pairs
+};
+
+// The error-free steps use explicitly rounded operations, which the compiler
+// never fuses into an FMA (a fused a*b + c would break the exact splits).
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// (hi, lo) += (xh + xl) y
+__device__ __forceinline__ void dd_fma(double& hi, double& lo, double xh, double xl, double y) {
+  const double p = __dmul_rn(xh, y);
+  double pe = fma(xh, y, -p);
+  pe = fma(xl, y, pe);
+  double s, e;
+  two_sum(hi, p, s, e);
+  hi = s;
+  lo = __dadd_rn(lo, __dadd_rn(e, pe));
+}
+
+__device__ __forceinline__ void dd_add(double& hi, double& lo, double h2, double l2) {
+  double s, e;
+  two_sum(hi, h2, s, e);
+  hi = s;
+  lo = __dadd_rn(lo, __dadd_rn(l2, e));
+}
+
+__global__ void __launch_bounds__(kDotThreads) tt_norm2_dd_kernel(DDArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  const long nthreads = (long)gridDim.x * kDotThreads;
+  const long gt = (long)blockIdx.x * kDotThreads + threadIdx.x;
+  const long gw = gt >> 5, nwarps = nthreads >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < a.d; ++k) {
+    const int m = a.m[k];
+    long tot = 0;
+    for (int p = 0; p < a.n; ++p) tot += (long)a.r[p][k] * m * a.r[p][k + 1];
+    // W[a', i, b] = sum_a phi[a, a'] U[a, i, b]
+    for (long e = gt; e < tot; e += nthreads) {
+      int p = 0;
+      long q = e;
+      while (q >= (long)a.r[p][k] * m * a.r[p][k + 1]) q -= (long)a.r[p][k] * m * a.r[p][k + 1], ++p;
+      const int ra = a.r[p][k], rb = a.r[p][k + 1];
+      const int b = (int)(q % rb);
+      const long ai = q / rb;
+      const int i = (int)(ai % m), ap = (int)(ai / m);
+      const double* U = a.u[p][k];
+      double h0 = 0.0, l0 = 0.0, h1 = 0.0, l1 = 0.0;
+      if (k == 0) {
+        h0 = U[(long)i * rb + b];
+      } else {
+        const double *ph = a.phh[p], *pl = a.phl[p];
+        int x = 0;
+        for (; x + 1 < ra; x += 2) {
+          dd_fma(h0, l0, ph[(long)x * ra + ap], pl[(long)x * ra + ap], U[((long)x * m + i) * rb + b]);
+          dd_fma(h1, l1, ph[(long)(x + 1) * ra + ap], pl[(long)(x + 1) * ra + ap],
+                 U[((long)(x + 1) * m + i) * rb + b]);
+        }
+        if (x < ra) dd_fma(h0, l0, ph[(long)x * ra + ap], pl[(long)x * ra + ap], U[((long)x * m + i) * rb + b]);
+        dd_add(h0, l0, h1, l1);
+      }
+      a.wh[p][q] = h0;
+      a.wl[p][q] = l0;
+    }
+    grid.sync();
+    // phi[b, b'] = sum_{a', i} W[a', i, b] U[a', i, b']
+    long tot2 = 0;
+    for (int p = 0; p < a.n; ++p) tot2 += (long)a.r[p][k + 1] * a.r[p][k + 1];
+    for (long it = gw; it < tot2; it += nwarps) {
+      int p = 0;
+      long q = it;
+      while (q >= (long)a.r[p][k + 1] * a.r[p][k + 1]) q -= (long)a.r[p][k + 1] * a.r[p][k + 1], ++p;
+      const int rb = a.r[p][k + 1], ra = a.r[p][k];
+      const int b = (int)(q / rb), bp = (int)(q % rb);
+      const double *Wh = a.wh[p], *Wl = a.wl[p];
+      const double* U = a.u[p][k];
+      const int K = ra * m;
+      double h0 = 0.0, l0 = 0.0, h1 = 0.0, l1 = 0.0;
+      int x = lane;
+      for (; x + 32 < K; x += 64) {
+        dd_fma(h0, l0, Wh[(long)x * rb + b], Wl[(long)x * rb + b], U[(long)x * rb + bp]);
+        dd_fma(h1, l1, Wh[(long)(x + 32) * rb + b], Wl[(long)(x + 32) * rb + b], U[(long)(x + 32) * rb + bp]);
+      }
+      if (x < K) dd_fma(h0, l0, Wh[(long)x * rb + b], Wl[(long)x * rb + b], U[(long)x * rb + bp]);
+      dd_add(h0, l0, h1, l1);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double h2 = __shfl_xor_sync(0xffffffffu, h0, o), l2 = __shfl_xor_sync(0xffffffffu, l0, o);
+        dd_add(h0, l0, h2, l2);
+      }
+      if (lane == 0) {
+        double s, e;
+        two_sum(h0, l0, s, e);  // renormalise
+        a.phh[p][q] = s;
+        a.phl[p][q] = e;
+      }
+    }
+    grid.sync();
+  }
+  if (gt < a.n) {
+    a.out[2 * gt] = a.phh[gt][0];
+    a.out[2 * gt + 1] = a.phl[gt][0];
+  }
+}
+
 }  // namespace
+
+t2s2_status tt_norm2_dd(Ctx& cx, int n, const DevTT* const* u, double* hi, double* lo) {
+  if (n < 1 || n > kMaxDots) return T2S2_EINVAL;
+  const int d = u[0]->d;
+  DDArgs a;
+  a.n = n;
+  a.d = d;
+  for (int k = 0; k < d; ++k) a.m[k] = u[0]->m[k];
+  size_t mark = cx.ar->mark();
+  double fl = 0.0;
+  for (int p = 0; p < n; ++p) {
+    if (u[p]->d != d) return T2S2_EINVAL;
+    size_t phi_n = 1, w_n = 1;
+    for (int k = 0; k < d; ++k) {
+      if (u[p]->m[k] != a.m[k]) return T2S2_EINVAL;
+      a.u[p][k] = u[p]->c[k];
+      phi_n = std::max(phi_n, (size_t)u[p]->r[k + 1] * u[p]->r[k + 1]);
+      w_n = std::max(w_n, (size_t)u[p]->r[k] * a.m[k] * u[p]->r[k + 1]);
+      fl += 2.0 * u[p]->r[k] * a.m[k] * (double)u[p]->r[k + 1] * (u[p]->r[k] + u[p]->r[k + 1]);
+    }
+    for (int k = 0; k <= d; ++k) a.r[p][k] = u[p]->r[k];
+    a.phh[p] = aget<double>(cx, phi_n);
+    a.phl[p] = aget<double>(cx, phi_n);
+    a.wh[p] = aget<double>(cx, w_n);
+    a.wl[p] = aget<double>(cx, w_n);
+    if (!a.phh[p] || !a.phl[p] || !a.wh[p] || !a.wl[p]) return T2S2_ENOMEM;
+  }
+  a.out = aget<double>(cx, 2 * (size_t)n);
+  if (!a.out) return T2S2_ENOMEM;
+  int dev = 0, sms = 0, per_sm = 0;
+  T2S2_CUDA_TRY(cudaGetDevice(&dev));
+  T2S2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  T2S2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tt_norm2_dd_kernel, kDotThreads, 0));
+  long cap = std::min<long>((long)std::max(1, per_sm) * sms, sms);
+  if (cx.coop_ctas > 0) cap = std::min<long>(cap, cx.coop_ctas);
+  // ~11 binary64 operations per product term: binary64 issue, not the item
+  // count, sets the time, so every SM takes a share
+  const int G = (int)std::max(1L, cap);
+  {
+    TraceScope ts(kTrGemm, cx.st, 11.0 * fl, 0.0);
+    void* args[] = {&a};
+    T2S2_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tt_norm2_dd_kernel, dim3(G), dim3(kDotThreads), args, 0,
+                                              cx.st));
+  }
+  T2S2_CUDA_TRY(cudaMemcpyAsync(cx.hbuf, a.out, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, cx.st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(cx.st));
+  for (int p = 0; p < n; ++p) {
+    hi[p] = cx.hbuf[2 * p];
+    lo[p] = cx.hbuf[2 * p + 1];
+  }
+  cx.ar->release(mark);
+  return T2S2_OK;
+}
 
 t2s2_status tt_dots(Ctx& cx, int n, const DevTT* const* u, const DevTT* const* v, double* out) {
   if (n < 1 || n > kMaxDots) return T2S2_EINVAL;

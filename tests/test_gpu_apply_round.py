@@ -199,3 +199,20 @@ def test_diff_norm_resolves_tiny_differences(T):
     assert d_or > 0
     assert abs(d_gpu - d_or) <= 1e-5 * d_or
     assert T.t2s2_diff_norm(op, T.TT.from_cores(x), T.TT.from_cores(x)) <= 1e-14 * OT.norm(x)
+
+
+@pytest.mark.parametrize("scale", [1e-3, 1e-7, 1e-9])
+def test_residual_resolves_small_residuals(T, scale):
+    # b = A x + scale * e: the residual is ~scale, many orders below |b|; the
+    # library's double-double <z, z> must still give it to five digits (FP64
+    # dot products would return noise below ~1e-8)
+    p = W.config1(d=4, n=14)
+    op, ops = _op(T, p)
+    x = W.random_tt(4, 12, [1, 3, 5, 2, 1], seed=31)
+    e = W.random_tt(4, 12, [1, 2, 2, 2, 1], seed=32)
+    A = O.ttm_cores(ops, 1.0, 0.3)
+    ax = OT.matvec(A, x)
+    b = OT.add(ax, OT.scale(e, scale * OT.norm(ax) / OT.norm(e)))
+    got = T.t2s2_residual(op, T.TT.from_cores(b), T.TT.from_cores(x), c_mass=1.0, c_op=0.3)
+    ref = np.linalg.norm(OT.full(b) - OT.full(ax)) / np.linalg.norm(OT.full(b))
+    assert abs(got - ref) <= 1e-5 * ref
