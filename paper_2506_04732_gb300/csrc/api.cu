@@ -223,15 +223,34 @@ t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
 // relative in the norm) could matter, and the orthogonalised norm of
 // residual_impl is taken instead.
 constexpr double kDDFloor = 1e-11;
+constexpr double kScreen = 1e-5;
 
 t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,
-                          double* out, double* bnorm_io) {
+                          double* out, double* bnorm_io, bool screen) {
   size_t mark = cx.ar->mark();
   DevTT y;
   int r2[T2S2_MAX_D + 1];
   for (int k = 0; k <= op->d; ++k) r2[k] = (k == 0 || k == op->d) ? 1 : 2 * x.r[k];
   T2S2_TRY(tt_alloc(cx, y, op->d, x.m, r2, 0));
   T2S2_TRY(apply_op(op, cx, x, y, c_mass, c_op, false));
+  if (screen) {
+    // binary64 |b|^2 - 2<b, y> + |y|^2: its cancellation noise (~1e-8
+    // relative in the norm) is irrelevant for a residual far above kScreen
+    const bool with_bb = *bnorm_io < 0.0;
+    const DevTT* pu[3] = {&b, &y, &b};
+    const DevTT* pv[3] = {&y, &y, &b};
+    double dots[3] = {0.0, 0.0, 0.0};
+    T2S2_TRY(tt_dots(cx, with_bb ? 3 : 2, pu, pv, dots));
+    const double bb = with_bb ? dots[2] : (*bnorm_io) * (*bnorm_io);
+    const double r2v = std::max(bb - 2.0 * dots[0] + dots[1], 0.0);
+    const double est = (bb > 0) ? std::sqrt(r2v / bb) : std::sqrt(r2v);
+    if (est > kScreen) {
+      if (with_bb) *bnorm_io = std::sqrt(bb);
+      *out = est;
+      cx.ar->release(mark);
+      return T2S2_OK;
+    }
+  }
   DevTT z;
   T2S2_TRY(tt_axpby(cx, 1.0, b, -1.0, y, z));
   const bool with_b = *bnorm_io < 0.0;
@@ -517,7 +536,7 @@ t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double
   T2S2_TRY(bind_tt(cx, b, db, true));
   T2S2_TRY(bind_tt(cx, x, dx, true));
   double bnorm = -1.0;
-  return residual_fast(op, cx, db, dx, c_mass, c_op, out, &bnorm);
+  return residual_fast(op, cx, db, dx, c_mass, c_op, out, &bnorm, false);
 }
 
 }  // extern "C"

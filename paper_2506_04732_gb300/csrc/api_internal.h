@@ -72,8 +72,10 @@ t2s2_status residual_estimate(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& 
 t2s2_status tt_norm2_dd(Ctx& cx, int n, const DevTT* const* u, double* hi, double* lo);
 // The residual of the original system from <z, z> in double-double, falling
 // back to residual_impl's orthogonalised norm for residuals below 1e-11.
+// screen: first try binary64 inner products, and return their value when it
+// is above 1e-5 (a guess far from converged).
 t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,
-                          double* out, double* bnorm_io);
+                          double* out, double* bnorm_io, bool screen);
 t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
                           double c_op, bool transformed, double* out, double* bnorm_io);
 }  // namespace t2s2

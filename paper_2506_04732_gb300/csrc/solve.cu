@@ -675,7 +675,7 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
   T2S2_TRY(tt_orth_right(cx, am.x));
   // the residual of the original system, before and after every sweep
   double bnorm = -1.0, res = 0.0;
-  T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &bnorm));
+  T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &bnorm, true));
   int sweeps = 0;
   const char* ev = std::getenv("T2S2_VERBOSE");
   const bool verbose = ev && ev[0] == '1';
@@ -685,7 +685,7 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
     T2S2_TRY(am.sweep());
     ++sweeps;
     am.ph(9);
-    T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &bnorm));
+    T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &bnorm, false));
     T2S2_TRY(am.collect_iters());
     if (verbose) {
       double rt = 0.0;
@@ -787,7 +787,7 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
     cx.ar->release(mk);
   }
   double bnorm = -1.0, res = 0.0;
-  T2S2_TRY(residual_fast(op, cx, b, x, c_mass, c_op, &res, &bnorm));
+  T2S2_TRY(residual_fast(op, cx, b, x, c_mass, c_op, &res, &bnorm, true));
   bool x_zero = false;
   if (res >= 1.0) {  // x0 is worse than x = 0
     x_zero = true;
@@ -863,7 +863,7 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
       ++refinements;
       if (verbose) {
         double rg = 0.0;
-        T2S2_TRY(residual_fast(op, cx, b, g, c_mass, c_op, &rg, &bnorm));
+        T2S2_TRY(residual_fast(op, cx, b, g, c_mass, c_op, &rg, &bnorm, true));
         fprintf(stderr, "[t2s2] tensor-core stage: inner sweeps %d est %.2e residual %.3e\n", inner, est, rg);
       }
       continue;
@@ -892,7 +892,7 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
     x_zero = false;
     ++refinements;
     const double prev = res;
-    T2S2_TRY(residual_fast(op, cx, b, x, c_mass, c_op, &res, &bnorm));
+    T2S2_TRY(residual_fast(op, cx, b, x, c_mass, c_op, &res, &bnorm, true));
     if (verbose) {
       fprintf(stderr, "[t2s2] refinement %d: inner sweeps %d est %.2e (target %.1e) residual %.3e ranks", refinements,
               inner, est, tin, res);

@@ -44,15 +44,15 @@ struct DotArgs {
 
 __global__ void __launch_bounds__(kDotThreads) tt_dots_kernel(DotArgs a) {
   cg::grid_group grid = cg::this_grid();
-  const long nthreads = (long)gridDim.x * kDotThreads;
   const long gt = (long)blockIdx.x * kDotThreads + threadIdx.x;
-  const long gw = gt >> 5, nwarps = nthreads >> 5;
   const int lane = threadIdx.x & 31;
   for (int k = 0; k < a.d; ++k) {
     const int m = a.m[k];
     long tot = 0;
     for (int p = 0; p < a.n; ++p) tot += (long)a.rv[p][k] * m * a.ru[p][k + 1];
-    for (long e = gt; e < tot; e += nthreads) {
+    for (long slot = threadIdx.x;; slot += kDotThreads) {
+      const long e = slot * gridDim.x + blockIdx.x;  // item j on CTA j mod G
+      if (e >= tot) break;
       int p = 0;
       long q = e;
       while (q >= (long)a.rv[p][k] * m * a.ru[p][k + 1]) q -= (long)a.rv[p][k] * m * a.ru[p][k + 1], ++p;
@@ -78,7 +78,9 @@ __global__ void __launch_bounds__(kDotThreads) tt_dots_kernel(DotArgs a) {
     grid.sync();
     long tot2 = 0;
     for (int p = 0; p < a.n; ++p) tot2 += (long)a.ru[p][k + 1] * a.rv[p][k + 1];
-    for (long it = gw; it < tot2; it += nwarps) {
+    for (long slot = threadIdx.x >> 5;; slot += kDotThreads / 32) {
+      const long it = slot * gridDim.x + blockIdx.x;
+      if (it >= tot2) break;
       int p = 0;
       long q = it;
       while (q >= (long)a.ru[p][k + 1] * a.rv[p][k + 1]) q -= (long)a.ru[p][k + 1] * a.rv[p][k + 1], ++p;
@@ -152,25 +154,29 @@ __device__ __forceinline__ void dd_add(double& hi, double& lo, double h2, double
   lo = __dadd_rn(lo, __dadd_rn(l2, e));
 }
 
+// Item j of a stage goes to CTA j mod G: the binary64 work of the items
+// spreads over every SM instead of filling the first CTAs.
+__device__ __forceinline__ long spread_item(long slot, int G, int g) { return slot * G + g; }
+
 __global__ void __launch_bounds__(kDotThreads) tt_norm2_dd_kernel(DDArgs a) {
   cg::grid_group grid = cg::this_grid();
-  const long nthreads = (long)gridDim.x * kDotThreads;
-  const long gt = (long)blockIdx.x * kDotThreads + threadIdx.x;
-  const long gw = gt >> 5, nwarps = nthreads >> 5;
-  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x, g = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = 0; k < a.d; ++k) {
     const int m = a.m[k];
     long tot = 0;
     for (int p = 0; p < a.n; ++p) tot += (long)a.r[p][k] * m * a.r[p][k + 1];
     // W[a', i, b] = sum_a phi[a, a'] U[a, i, b]
-    for (long e = gt; e < tot; e += nthreads) {
+    for (long slot = threadIdx.x;; slot += kDotThreads) {
+      const long e = spread_item(slot, G, g);
+      if (e >= tot) break;
       int p = 0;
       long q = e;
       while (q >= (long)a.r[p][k] * m * a.r[p][k + 1]) q -= (long)a.r[p][k] * m * a.r[p][k + 1], ++p;
       const int ra = a.r[p][k], rb = a.r[p][k + 1];
       const int b = (int)(q % rb);
-      const long ai = q / rb;
-      const int i = (int)(ai % m), ap = (int)(ai / m);
+      const int ai = (int)(q / rb);
+      const int i = ai % m, ap = ai / m;
       const double* U = a.u[p][k];
       double h0 = 0.0, l0 = 0.0, h1 = 0.0, l1 = 0.0;
       if (k == 0) {
@@ -190,15 +196,23 @@ __global__ void __launch_bounds__(kDotThreads) tt_norm2_dd_kernel(DDArgs a) {
       a.wl[p][q] = l0;
     }
     grid.sync();
-    // phi[b, b'] = sum_{a', i} W[a', i, b] U[a', i, b']
+    // phi[b, b'] = sum_{a', i} W[a', i, b] U[a', i, b'], b <= b' (phi is
+    // symmetric; both halves are written)
     long tot2 = 0;
-    for (int p = 0; p < a.n; ++p) tot2 += (long)a.r[p][k + 1] * a.r[p][k + 1];
-    for (long it = gw; it < tot2; it += nwarps) {
+    for (int p = 0; p < a.n; ++p) tot2 += (long)a.r[p][k + 1] * (a.r[p][k + 1] + 1) / 2;
+    for (long slot = warp;; slot += kDotThreads / 32) {
+      const long it = spread_item(slot, G, g);
+      if (it >= tot2) break;
       int p = 0;
       long q = it;
-      while (q >= (long)a.r[p][k + 1] * a.r[p][k + 1]) q -= (long)a.r[p][k + 1] * a.r[p][k + 1], ++p;
+      while (q >= (long)a.r[p][k + 1] * (a.r[p][k + 1] + 1) / 2) q -= (long)a.r[p][k + 1] * (a.r[p][k + 1] + 1) / 2, ++p;
       const int rb = a.r[p][k + 1], ra = a.r[p][k];
-      const int b = (int)(q / rb), bp = (int)(q % rb);
+      // q -> (b, b') with b <= b', row-major over the upper triangle
+      int b = (int)((2.0f * rb + 1.0f - sqrtf((2.0f * rb + 1.0f) * (2.0f * rb + 1.0f) - 8.0f * (float)q)) * 0.5f);
+      b = max(0, min(rb - 1, b));
+      while (b > 0 && (long)b * (2 * rb - b + 1) / 2 > q) --b;
+      while ((long)(b + 1) * (2 * rb - b) / 2 <= q) ++b;
+      const int bp = b + (int)(q - (long)b * (2 * rb - b + 1) / 2);
       const double *Wh = a.wh[p], *Wl = a.wl[p];
       const double* U = a.u[p][k];
       const int K = ra * m;
@@ -216,17 +230,19 @@ __global__ void __launch_bounds__(kDotThreads) tt_norm2_dd_kernel(DDArgs a) {
         dd_add(h0, l0, h2, l2);
       }
       if (lane == 0) {
-        double s, e;
-        two_sum(h0, l0, s, e);  // renormalise
-        a.phh[p][q] = s;
-        a.phl[p][q] = e;
+        double sh, se;
+        two_sum(h0, l0, sh, se);  // renormalise
+        a.phh[p][(long)b * rb + bp] = sh;
+        a.phl[p][(long)b * rb + bp] = se;
+        a.phh[p][(long)bp * rb + b] = sh;
+        a.phl[p][(long)bp * rb + b] = se;
       }
     }
     grid.sync();
   }
-  if (gt < a.n) {
-    a.out[2 * gt] = a.phh[gt][0];
-    a.out[2 * gt + 1] = a.phl[gt][0];
+  if (g == 0 && threadIdx.x < a.n) {
+    a.out[2 * threadIdx.x] = a.phh[threadIdx.x][0];
+    a.out[2 * threadIdx.x + 1] = a.phl[threadIdx.x][0];
   }
 }
 
