@@ -462,24 +462,45 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
   };
 
   // ||rhs||
-  own_dots(P.rhs, 0, true);
-  tm.sync();
-  gather(1);
-  const double rhs_norm = sqrt(hcol[0]);
-  const double tol_abs = P.tol_rel * rhs_norm;
+  double rhs_norm = 0.0, tol_abs = 0.0;
   int its = 0;
   double resid = 0.0;
   for (int cycle = 0;; ++cycle) {
-    // r = rhs - K x -> Wv (own elements) ; beta = ||r||   (x complete)
+    // r = rhs - K x -> Wv (own elements) ; beta = ||r||   (x complete); the
+    // first cycle also takes ||rhs|| in the same reduction
     tm.matvec(P.x, Wv);
     for (long k = threadIdx.x; k < tm.nown; k += NT) {
       const long e = E(k);
       Wv[e] = (T)((double)P.rhs[e] - (double)Wv[e]);
     }
     __syncthreads();
-    own_dots(Wv, 0, true);
-    tm.sync();
-    gather(1);
+    if (cycle == 0) {
+      for (int v = wid; v < 2; v += NW) {
+        const T* a = (v == 0) ? Wv : P.rhs;
+        double s0 = 0.0, s1 = 0.0;
+        long k = lane;
+        for (; k + 32 < tm.nown; k += 64) {
+          const long e0 = E(k), e1 = E(k + 32);
+          s0 = fma((double)a[e0], (double)a[e0], s0);
+          s1 = fma((double)a[e1], (double)a[e1], s1);
+        }
+        if (k < tm.nown) {
+          const long e0 = E(k);
+          s0 = fma((double)a[e0], (double)a[e0], s0);
+        }
+        double sv = s0 + s1;
+        for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        if (lane == 0) partial(pbuf, g, v) = sv;
+      }
+      tm.sync();
+      gather(2);
+      rhs_norm = sqrt(hcol[1]);
+      tol_abs = P.tol_rel * rhs_norm;
+    } else {
+      own_dots(Wv, 0, true);
+      tm.sync();
+      gather(1);
+    }
     const double beta = sqrt(hcol[0]);
     resid = beta;
     if (beta <= tol_abs || its >= P.maxit || beta == 0.0) break;
@@ -655,11 +676,21 @@ t2s2_status local_gmres(const LocalProblem<T>& P, cudaStream_t st) {
   int dev0 = 0, sms0 = 0;
   T2S2_CUDA_TRY(cudaGetDevice(&dev0));
   T2S2_CUDA_TRY(cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0));
+  // Team size: one CTA per fibre (the preconditioner gives each fibre a
+  // warp, and fibres of one CTA that differ in a are done one after another)
+  // and at least one element per thread, at most the GPU (or the caller's
+  // share of it).  Every grid barrier and reduction costs more with more
+  // CTAs, so a small local system gets a small team.
+  const long nf = (long)P.ra * P.rb;
+  int G_target = sms0;
+  if (sizeof(T) == 8) G_target = (int)std::min<long>(sms0, std::max(nf, (N + NT - 1) / NT));
+  else G_target = (int)std::min<long>(sms0, std::max((N + NT * 4 - 1) / (NT * 4), (nf + NW - 1) / NW));
+  if (P.team > 0) G_target = std::min(G_target, P.team);
+  G_target = std::max(1, G_target);
   {
-    // own-element list sized for the smallest team this launch may use
-    const long nf = (long)P.ra * P.rb;
-    const int gmin = (P.team > 0) ? std::min(P.team, sms0) : sms0;  // larger than the team only if occupancy-limited: then indices are recomputed
-    const long per = ((nf + gmin - 1) / gmin) * P.m;
+    // own-element list sized for that team (a smaller, occupancy-limited
+    // grid recomputes indices instead)
+    const long per = ((nf + G_target - 1) / G_target) * P.m;
     Q.own_cap = (int)std::min<long>(per, kLocalOwnMax);
   }
   Q.smem_mats = local_smem_bytes(P.m, true, Q.own_cap) <= kLocalSmemCap;
@@ -692,13 +723,7 @@ t2s2_status local_gmres(const LocalProblem<T>& P, cudaStream_t st) {
   T2S2_CUDA_TRY(cudaGetDevice(&dev));
   T2S2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const long resident = (long)std::max(1, per_sm) * sms;
-  // FP64 runs at 2 DFMA/clk/SM: spread the team over every SM.  FP32 is
-  // latency bound: size the team by the work (fibres per warp, elements).
-  long want = (sizeof(T) == 8)
-                  ? (long)sms
-                  : std::max((N + NT * 4 - 1) / (NT * 4), ((long)P.ra * P.rb + NW - 1) / NW);
-  int G = (int)std::max(1L, std::min<long>(want, std::min<long>(resident, sms)));
-  if (P.team > 0) G = std::min(G, P.team);
+  int G = (int)std::max(1L, std::min<long>(G_target, std::min<long>(resident, sms)));
   void* args[] = {&Q};
   {
     TraceScope ts(kTrLocal, st, 0.0, 0.0);
