@@ -30,6 +30,7 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int NW = NT / 32;
+constexpr int kRichardsonSteps = 3;  // before GMRES, with the exact preconditioner
 
 // Vectors written during the kernel (basis, preconditioned vector, iterate)
 // are read with coherent loads; only launch-constant data may use __ldg.
@@ -465,7 +466,69 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
   double rhs_norm = 0.0, tol_abs = 0.0;
   int its = 0;
   double resid = 0.0;
-  for (int cycle = 0;; ++cycle) {
+  bool done = false;
+  if (fls_on) {
+    // Preconditioned Richardson steps x <- x + M^{-1} r while each one cuts
+    // the residual at least tenfold.  With the exact Kronecker-sum
+    // preconditioner ||I - K M^{-1}|| is of the order of the binary32
+    // eigendecompositions' accuracy, so one or two steps usually reach the
+    // tolerance with no Arnoldi basis; otherwise GMRES continues from x.
+    T* zr = Zs;  // scratch: the first preconditioned-basis slot
+    double beta = -1.0;
+    for (int step = 0; step <= kRichardsonSteps; ++step) {
+      // r = rhs - K x -> Wv (own elements), ||r|| (and ||rhs|| at first)
+      tm.matvec(P.x, Wv);
+      for (long k = threadIdx.x; k < tm.nown; k += NT) {
+        const long e = E(k);
+        Wv[e] = (T)((double)P.rhs[e] - (double)Wv[e]);
+      }
+      __syncthreads();
+      const int nv = (step == 0) ? 2 : 1;
+      for (int v = wid; v < nv; v += NW) {
+        const T* a = (v == 0) ? Wv : P.rhs;
+        double s0 = 0.0, s1 = 0.0;
+        long k = lane;
+        for (; k + 32 < tm.nown; k += 64) {
+          const long e0 = E(k), e1 = E(k + 32);
+          s0 = fma((double)a[e0], (double)a[e0], s0);
+          s1 = fma((double)a[e1], (double)a[e1], s1);
+        }
+        if (k < tm.nown) {
+          const long e0 = E(k);
+          s0 = fma((double)a[e0], (double)a[e0], s0);
+        }
+        double sv = s0 + s1;
+        for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        if (lane == 0) partial(pbuf, g, v) = sv;
+      }
+      tm.sync();
+      gather(nv);
+      if (step == 0) {
+        rhs_norm = sqrt(hcol[1]);
+        tol_abs = P.tol_rel * rhs_norm;
+      }
+      const double bn = sqrt(hcol[0]);
+      resid = bn;
+      if (bn <= tol_abs || bn == 0.0) {
+        done = true;
+        break;
+      }
+      // the last step did not pay: hand the current x to GMRES
+      if ((beta >= 0.0 && bn > 0.1 * beta) || step == kRichardsonSteps || its >= P.maxit) break;
+      beta = bn;
+      tm.sync();  // Wv complete for the preconditioner
+      fls_phase_a(tm, Wv, Ybuf, F, Ttr, Tti, Zr, Zi, ld);
+      tm.sync();  // Y complete
+      fls_phase_b(tm, Ybuf, zr, F);
+      for (long k = threadIdx.x; k < tm.nown; k += NT) {
+        const long e = E(k);
+        P.x[e] = (T)((double)P.x[e] + (double)zr[e]);
+      }
+      ++its;
+      tm.sync();  // x complete before the next residual
+    }
+  }
+  for (int cycle = 0; !done; ++cycle) {
     // r = rhs - K x -> Wv (own elements) ; beta = ||r||   (x complete); the
     // first cycle also takes ||rhs|| in the same reduction
     tm.matvec(P.x, Wv);
@@ -474,7 +537,7 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
       Wv[e] = (T)((double)P.rhs[e] - (double)Wv[e]);
     }
     __syncthreads();
-    if (cycle == 0) {
+    if (cycle == 0 && !fls_on) {
       for (int v = wid; v < 2; v += NW) {
         const T* a = (v == 0) ? Wv : P.rhs;
         double s0 = 0.0, s1 = 0.0;
