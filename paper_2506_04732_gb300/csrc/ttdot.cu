@@ -286,7 +286,7 @@ t2s2_status tt_norm2_dd(Ctx& cx, int n, const DevTT* const* u, double* hi, doubl
   // count, sets the time, so every SM takes a share
   const int G = (int)std::max(1L, cap);
   {
-    TraceScope ts(kTrGemm, cx.st, 11.0 * fl, 0.0);
+    TraceScope ts(kTrGemm, cx.st, fl, 0.0);  // algorithmic: 2 per product term
     void* args[] = {&a};
     T2S2_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tt_norm2_dd_kernel, dim3(G), dim3(kDotThreads), args, 0,
                                               cx.st));
