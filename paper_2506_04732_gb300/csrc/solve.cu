@@ -261,8 +261,9 @@ struct Amen {
     {
       Ctx c64 = c;
       c64.contract_prec = T2S2_FP64;
-      for (int k = 0; k < d; ++k)
-        T2S2_TRY(mode2(c64, op->dRinv[k], op->m[k], b.c[k], b.r[k], b.r[k + 1], f.c[k]));
+      Gemm<double> gs[T2S2_MAX_D];
+      for (int k = 0; k < d; ++k) gs[k] = g_mode2(op->dRinv[k], op->m[k], b.c[k], b.r[k], b.r[k + 1], f.c[k]);
+      for (int k0 = 0; k0 < d; k0 += kMaxGroup) T2S2_TRY(contract_group(c64, gs + k0, std::min(kMaxGroup, d - k0)));
     }
     // x: copy of the initial guess with capacity rcap
     int rx[T2S2_MAX_D + 1];

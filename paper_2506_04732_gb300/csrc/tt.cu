@@ -297,6 +297,57 @@ t2s2_status tt_copy(Ctx& cx, const DevTT& src, DevTT& dst) {
   return T2S2_OK;
 }
 
+namespace {
+struct OrthArgs1 {
+  int d;
+  int m[T2S2_MAX_D];
+  double* c[T2S2_MAX_D];
+};
+}  // namespace
+
+namespace {
+// Cores of z = alpha x + beta y (block structure: first core [alpha X | beta Y],
+// middle cores diag(X, Y), last core [X; Y]) for all cores in one launch.
+struct SumArgs {
+  int d;
+  int m[T2S2_MAX_D];
+  int rx[T2S2_MAX_D + 1], ry[T2S2_MAX_D + 1], rz[T2S2_MAX_D + 1];
+  const double* x[T2S2_MAX_D];
+  const double* y[T2S2_MAX_D];
+  double* z[T2S2_MAX_D];
+  long off[T2S2_MAX_D + 1];
+  double alpha, beta;
+};
+
+__global__ void k_tt_sum(SumArgs a) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < a.off[a.d]; e += (long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (e >= a.off[k + 1]) ++k;
+    const long q = e - a.off[k];
+    const int m = a.m[k];
+    double v;
+    if (a.d == 1) {
+      v = a.alpha * a.x[0][q] + a.beta * a.y[0][q];
+    } else {
+      const int rz1 = a.rz[k + 1];
+      const int b = (int)(q % rz1);
+      const long t = q / rz1;
+      const int i = (int)(t % m), aa = (int)(t / m);
+      const double ax = (k == 0) ? a.alpha : 1.0, by = (k == 0) ? a.beta : 1.0;
+      const int a0y = (k == 0) ? 0 : a.rx[k];
+      const int b0y = (k == a.d - 1) ? 0 : a.rx[k + 1];
+      const int ya = aa - a0y, yb = b - b0y;
+      v = 0.0;
+      if (aa < a.rx[k] && b < a.rx[k + 1])
+        v = ax * a.x[k][((long)aa * m + i) * a.rx[k + 1] + b];
+      else if (ya >= 0 && ya < a.ry[k] && yb >= 0 && yb < a.ry[k + 1])
+        v = by * a.y[k][((long)ya * m + i) * a.ry[k + 1] + yb];
+    }
+    a.z[k][q] = v;
+  }
+}
+}  // namespace
+
 t2s2_status tt_axpby(Ctx& cx, double alpha, const DevTT& x, double beta, const DevTT& y, DevTT& z) {
   const int d = x.d;
   if (y.d != d) return T2S2_EINVAL;
@@ -305,25 +356,91 @@ t2s2_status tt_axpby(Ctx& cx, double alpha, const DevTT& x, double beta, const D
   r[d] = 1;
   for (int k = 1; k < d; ++k) r[k] = x.r[k] + y.r[k];
   T2S2_TRY(tt_alloc(cx, z, d, x.m, r, 0));
-  for (int k = 0; k < d; ++k) {
-    const int m = x.m[k];
-    T2S2_TRY(dev_fill(cx, z.c[k], z.core_elems(k), 0.0));
-    if (d == 1) {  // single core: alpha X + beta Y
-      T2S2_TRY(dev_scale_copy(cx, z.c[k], x.c[k], m, alpha));
-      T2S2_TRY(dev_axpy(cx, z.c[k], y.c[k], m, beta));
-      continue;
-    }
-    const double ax = (k == 0) ? alpha : 1.0, by = (k == 0) ? beta : 1.0;
-    const int a0y = (k == 0) ? 0 : x.r[k];
-    const int b0y = (k == d - 1) ? 0 : x.r[k + 1];
-    T2S2_TRY(dev_copy_block(cx, z.c[k], z.r[k], z.r[k + 1], 0, 0, x.c[k], x.r[k], m, x.r[k + 1], ax));
-    T2S2_TRY(dev_copy_block(cx, z.c[k], z.r[k], z.r[k + 1], a0y, b0y, y.c[k], y.r[k], m, y.r[k + 1], by));
+  SumArgs a;
+  a.d = d;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.off[0] = 0;
+  for (int k = 0; k <= d; ++k) {
+    a.rx[k] = x.r[k];
+    a.ry[k] = y.r[k];
+    a.rz[k] = z.r[k];
   }
+  for (int k = 0; k < d; ++k) {
+    if (y.m[k] != x.m[k]) return T2S2_EINVAL;
+    a.m[k] = x.m[k];
+    a.x[k] = x.c[k];
+    a.y[k] = y.c[k];
+    a.z[k] = z.c[k];
+    a.off[k + 1] = a.off[k] + (long)z.core_elems(k);
+  }
+  {
+    TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * a.off[d]);
+    k_tt_sum<<<blocks_for((size_t)a.off[d]), 256, 0, cx.st>>>(a);
+  }
+  T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 
+namespace {
+// Right orthogonalisation of a TT whose interior ranks are all 1: core k
+// (k >= 1) becomes x_k / |x_k| and core 0 takes the product of the norms
+// (the LQ factor of a single row is its norm).  One CTA; sums in a fixed
+// order.
+__global__ void k_orth_rank1(OrthArgs1 a) {
+  __shared__ double red[8];
+  __shared__ double scale_s;
+  double prod = 1.0;
+  for (int k = a.d - 1; k >= 0; --k) {
+    double* c = a.c[k];
+    const int m = a.m[k];
+    double s;
+    if (k > 0) {
+      double p = 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) p = fma(c[i], c[i], p);
+      for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = p;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        const double nrm = sqrt(t);
+        scale_s = nrm > 0.0 ? 1.0 / nrm : 0.0;
+        red[0] = nrm;
+      }
+      __syncthreads();
+      s = scale_s;
+      prod *= red[0];
+      __syncthreads();
+    } else {
+      s = prod;
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) c[i] *= s;
+    __syncthreads();
+  }
+}
+}  // namespace
+
 t2s2_status tt_orth_right(Ctx& cx, DevTT& x) {
   const int d = x.d;
+  {
+    bool rank1 = true;
+    for (int k = 1; k < d; ++k) rank1 = rank1 && x.r[k] == 1;
+    if (rank1 && d > 1) {
+      OrthArgs1 a;
+      a.d = d;
+      for (int k = 0; k < d; ++k) {
+        a.m[k] = x.m[k];
+        a.c[k] = x.c[k];
+      }
+      {
+        TraceScope ts_(kTrSmall, cx.st, 2.0 * d * 64, 16.0 * d * 64);
+        k_orth_rank1<<<1, 256, 0, cx.st>>>(a);
+      }
+      T2S2_CUDA_TRY(cudaGetLastError());
+      return T2S2_OK;
+    }
+  }
   for (int k = d - 1; k >= 1; --k) {
     const int rk = x.r[k], mk_ = x.m[k], rk1 = x.r[k + 1];
     const int cols = mk_ * rk1;
