@@ -100,6 +100,30 @@ t2s2_status d2d(Ctx& cx, double* dst, const double* src, size_t n) {
 }
 t2s2_status set_scalar(Ctx& cx, double* dst, double v) { return dev_fill(cx, dst, 1, v); }
 
+// SVD of one column x (n entries): u = x / |x| (0 for x = 0), s v^T = |x|,
+// and the truncated product u s v^T = x.  One CTA, fixed-order sum.
+__global__ void k_col_split(const double* x, int n, double* u, double* sv, double* xt) {
+  __shared__ double red[32];
+  double p = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p = fma(x[i], x[i], p);
+  for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = p;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    red[0] = sqrt(t);
+    sv[0] = red[0];
+  }
+  __syncthreads();
+  const double nrm = red[0];
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    u[i] = x[i] * inv;
+    xt[i] = x[i];
+  }
+}
+
 // Optional per-phase timing of the solver (T2S2_PHASES=1): CUDA events at the
 // phase boundaries on the solver's stream, summed and printed per solve.
 struct PhaseTimer {
@@ -187,18 +211,31 @@ struct Amen {
   float* fbuf = nullptr;     // FP32 rhs / x / GMRES basis for the mixed-precision local solves
   bool fp32_local = false;
   long long local_iters = 0;
-  // GMRES count of the sweep's last local solve, copied without a wait
+  // GMRES counts of local solves that no synchronisation followed, copied
+  // without a wait into pinned slots and read at the next collect_iters()
   static constexpr int kIterSlot = kSmallMax + 16;
-  bool pending_iters = false;
-  int pend_ra = 0, pend_m = 0, pend_rb = 0;
+  static constexpr int kMaxPending = 2 * T2S2_MAX_D;
+  int npending = 0;
+  int pend_shape[kMaxPending][3];
+  t2s2_status defer_iters(int ra, int m, int rb) {
+    if (npending == kMaxPending) T2S2_TRY(collect_iters());
+    T2S2_CUDA_TRY(cudaMemcpyAsync(cx->hbuf + kIterSlot + npending, gm_iters, sizeof(int), cudaMemcpyDeviceToHost,
+                                  cx->st));
+    pend_shape[npending][0] = ra, pend_shape[npending][1] = m, pend_shape[npending][2] = rb;
+    ++npending;
+    return T2S2_OK;
+  }
   t2s2_status collect_iters() {
-    if (!pending_iters) return T2S2_OK;
+    if (npending == 0) return T2S2_OK;
     T2S2_CUDA_TRY(cudaStreamSynchronize(cx->st));
-    int it;
-    std::memcpy(&it, cx->hbuf + kIterSlot, sizeof(int));
-    local_iters += it;
-    trace_add_work(kTrLocal, local_flops(pend_ra, pend_m, pend_rb, it, gm_restart), 0.0);
-    pending_iters = false;
+    for (int j = 0; j < npending; ++j) {
+      int it;
+      std::memcpy(&it, cx->hbuf + kIterSlot + j, sizeof(int));
+      local_iters += it;
+      trace_add_work(kTrLocal, local_flops(pend_shape[j][0], pend_shape[j][1], pend_shape[j][2], it, gm_restart),
+                     0.0);
+    }
+    npending = 0;
     return T2S2_OK;
   }
   double c_op = 1.0, c_mass = 0.0;
@@ -521,15 +558,25 @@ struct Amen {
       if (k == d - 1) {
         T2S2_TRY(d2d(c, x.c[k], X, (size_t)ra * m * rb));
         // the count is read after the solver's next synchronisation
-        T2S2_CUDA_TRY(cudaMemcpyAsync(c.hbuf + kIterSlot, gm_iters, sizeof(int), cudaMemcpyDeviceToHost, c.st));
-        pending_iters = true;
-        pend_ra = ra, pend_m = m, pend_rb = rb;
+        T2S2_TRY(defer_iters(ra, m, rb));
         break;
       }
       // --- truncation: X (rows x rb) = U S V^T
       const int rows = ra * m;
       double *Qx = tmp[5], *Ux = tmp[6], *Vx = tmp[7], *Rx = tmp[8];
-      int kk;
+      double *U = tmp[9], *SV = tmp[10], *Xt = tmp[11];
+      int kk, rk;
+      if (rb == 1) {
+        // a single column: U = X / |X|, S V^T = |X|, rank 1 -- no
+        // factorisation and no read-back
+        {
+          TraceScope ts(kTrSmall, c.st, 3.0 * rows, 24.0 * rows);
+          k_col_split<<<1, 256, 0, c.st>>>(X, rows, U, SV, Xt);
+        }
+        T2S2_CUDA_TRY(cudaGetLastError());
+        T2S2_TRY(defer_iters(ra, m, rb));
+        rk = 1;
+      } else {
       if (rows >= rb) {
         T2S2_TRY(qr_tall(c, X, rows, rb, Qx, Rx));
         T2S2_TRY(jacobi_svd(Rx, rb, rb, Ux, svals, Vx, nullptr, c.st));
@@ -550,8 +597,7 @@ struct Amen {
       double snorm = 0.0;
       for (int j = 0; j < kk; ++j) snorm += c.hbuf[j] * c.hbuf[j];
       snorm = std::sqrt(snorm);
-      const int rk = trunc_rank(c.hbuf, kk, ltol * snorm, rmax);
-      double *U = tmp[9], *SV = tmp[10], *Xt = tmp[11];
+      rk = trunc_rank(c.hbuf, kk, ltol * snorm, rmax);
       if (rows >= rb) {
         T2S2_TRY(gemm_ex<double>(c, rows, rk, rb, false, false, 1.0, Qx, rb, Ux, kk, 0.0, U, rk));
       } else {
@@ -560,6 +606,7 @@ struct Amen {
       }
       T2S2_TRY(dev_sv_t(c, SV, svals, Vx, rk, rb, kk));
       T2S2_TRY(gemm_ex<double>(c, rows, rb, rk, false, false, 1.0, U, rk, SV, rb, 0.0, Xt, rb));
+      }
       ph(5);
       // --- enrichment directions: residual on (x-left) x m x (z-right),
       //   res  = (FL F) x_3 ZFR - (B' Xt + PL Xt) x_3 ZIR - Xt x_3 ZBR,
