@@ -209,8 +209,9 @@ t2s2_status t2s2_diff_norm(t2s2_op op, const t2s2_tt* x, const t2s2_tt* y, doubl
 
 /* ||b - (c_mass M + c_op A) x||_F / ||b||_F in FP64, accurate even where A x
  * agrees with b to many digits: z = b - A x is formed as a TT and <z, z> is
- * accumulated in double-double (error-free products and sums); a result below
- * 1e-11 is recomputed as the norm of the right-orthogonalised z. */
+ * accumulated in double-double (error-free products and sums), ~1e-4 relative
+ * at a residual of 1e-12; a result below 1e-13 is recomputed as the norm of the
+ * right-orthogonalised z. */
 t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double c_mass,
                           double c_op, double* out, void* stream);
 

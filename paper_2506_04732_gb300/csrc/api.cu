@@ -218,11 +218,13 @@ t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
 }
 
 // ||b - (c_mass M + c_op A) x|| / ||b|| through <z, z> in double-double
-// (ttdot.cu), z = b - A x as a TT sum: no orthogonalisation of z.  Where the
-// result falls below kDDFloor (relative), the double-double noise (~1e-14
-// relative in the norm) could matter, and the orthogonalised norm of
-// residual_impl is taken instead.
-constexpr double kDDFloor = 1e-11;
+// (ttdot.cu), z = b - A x as a TT sum: no orthogonalisation of z.  The
+// double-double sums carry ~1e-28 |b|^2 of error, i.e. ~1e-4 relative in a
+// residual of 1e-12 |b|; a CholeskyQR-orthogonalised z (residual_impl) would
+// drop directions below ~2e-13 of its largest singular value in its unshifted
+// passes, so it is only the last resort, below kDDFloor, where neither
+// resolves the residual.
+constexpr double kDDFloor = 1e-13;
 constexpr double kScreen = 1e-5;
 
 t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,

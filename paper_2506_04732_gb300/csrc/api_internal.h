@@ -71,7 +71,7 @@ t2s2_status residual_estimate(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& 
 // <u_p, u_p> in double-double for p < n <= 4 (ttdot.cu), as hi + lo pairs.
 t2s2_status tt_norm2_dd(Ctx& cx, int n, const DevTT* const* u, double* hi, double* lo);
 // The residual of the original system from <z, z> in double-double, falling
-// back to residual_impl's orthogonalised norm for residuals below 1e-11.
+// back to residual_impl's orthogonalised norm for residuals below 1e-13.
 // screen: first try binary64 inner products, and return their value when it
 // is above 1e-5 (a guess far from converged).
 t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,

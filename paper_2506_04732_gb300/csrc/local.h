@@ -34,7 +34,28 @@ struct LocalProblem {
   unsigned long long* tstamp = nullptr;  // optional phase timestamps (diagnostics)
   int* iters_out = nullptr;            // total GMRES iterations
   double* res_out = nullptr;           // [final residual norm, ||rhs||]
+  const int* skip = nullptr;           // device word: 0 = solved already, return at once
 };
+
+// Local solve with rb = 1 in one CTA (sylv.cu): binary64 refinement around
+// the Schur-basis Sylvester solver in binary32.  *status = 0 when ||rhs - K x||
+// <= tol_rel ||rhs||, else 1 with the iterate left in x.
+struct SylvProblem {
+  int ra = 0, m = 0;
+  const double* PL = nullptr;          // ra x ra
+  const double* PR = nullptr;          // 1 x 1
+  const double* Bp = nullptr;          // m x m  B' = c_op B + shift I
+  const float *Tr = nullptr, *Ti = nullptr, *Zr = nullptr, *Zi = nullptr;  // Schur B = Z T Z^H
+  double c_op = 1.0, shift = 0.0;
+  const double* rhs = nullptr;         // ra x m
+  double* x = nullptr;                 // ra x m, initial guess in, iterate out
+  double tol_rel = 1e-10;
+  int* status = nullptr;
+  int* iters_out = nullptr;
+  double* res_out = nullptr;
+};
+bool sylv_rb1_fits(int ra, int m);
+t2s2_status sylv_rb1(const SylvProblem& P, cudaStream_t st);
 
 template <typename T>
 size_t local_work_elems(long N, int mr);

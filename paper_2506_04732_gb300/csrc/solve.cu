@@ -206,6 +206,7 @@ struct Amen {
   double* svals = nullptr;
   double* eig_buf = nullptr;  // complex binary32 eigen data of both interfaces
   double* ybuf = nullptr;     // complex binary32 intermediate of the exact preconditioner
+  int* sylv_status = nullptr; // status word of the rb = 1 local solver
   int* eig_status = nullptr;
   bool use_fls = true;
   float* fbuf = nullptr;     // FP32 rhs / x / GMRES basis for the mixed-precision local solves
@@ -385,6 +386,8 @@ struct Amen {
       eig_buf = aget<double>(c, 2 * side);                 // 8 bytes per complex binary32
       ybuf = aget<double>(c, (size_t)rcap * mmax * rcap);
       eig_status = reinterpret_cast<int*>(aget<double>(c, 1));
+      sylv_status = reinterpret_cast<int*>(aget<double>(c, 1));
+      if (!sylv_status) return T2S2_ENOMEM;
       if (!eig_buf || !ybuf || !eig_status) return T2S2_ENOMEM;
     }
     {
@@ -481,6 +484,30 @@ struct Amen {
     const bool stamp_this = tstamp_req && !tstamp_done && local_count == tstamp_target;
     ++local_count;
     if (stamp_this) P.tstamp = tstamp_dev;
+    if (P.rb == 1 && use_fls && sylv_rb1_fits(P.ra, P.m)) {
+      // rb = 1: the Schur-basis Sylvester solver first; the general solver
+      // below runs only if it leaves status 1
+      SylvProblem S;
+      S.ra = P.ra;
+      S.m = P.m;
+      S.PL = P.PL;
+      S.PR = P.PR;
+      S.Bp = P.Bp;
+      S.Tr = P.Tr;
+      S.Ti = P.Ti;
+      S.Zr = P.Zr;
+      S.Zi = P.Zi;
+      S.c_op = P.c_op;
+      S.shift = P.shift;
+      S.rhs = P.rhs;
+      S.x = P.x;
+      S.tol_rel = P.tol_rel;
+      S.status = sylv_status;
+      S.iters_out = P.iters_out;
+      S.res_out = P.res_out;
+      T2S2_TRY(sylv_rb1(S, c.st));
+      P.skip = sylv_status;
+    }
     T2S2_TRY(local_gmres<double>(P, c.st));
     if (stamp_this) {
       tstamp_done = true;

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kDotThreads) tt_dots_kernel(DotArgs a) {
 // residual z = b - A x the terms of <z, z> are of the size |b|^2 while the
 // result is |b - A x|^2, many orders smaller; in binary64 the cancellation
 // leaves noise of ~1e-16 |b|^2, in double-double ~1e-28 |b|^2, so the
-// norm of a residual down to ~1e-11 |b| comes out to three or more digits
+// norm of a residual of 1e-12 |b| comes out to about four digits
 // without orthogonalising z.
 
 struct DDArgs {

@@ -216,3 +216,18 @@ def test_residual_resolves_small_residuals(T, scale):
     got = T.t2s2_residual(op, T.TT.from_cores(b), T.TT.from_cores(x), c_mass=1.0, c_op=0.3)
     ref = np.linalg.norm(OT.full(b) - OT.full(ax)) / np.linalg.norm(OT.full(b))
     assert abs(got - ref) <= 1e-5 * ref
+
+
+def test_residual_near_the_rounding_floor(T):
+    # a residual of ~1e-12 |b|: the double-double norm must still resolve it
+    # (the binary64 evaluation of A x itself is good to ~4e-15 here)
+    p = W.config1(d=4, n=14)
+    op, ops = _op(T, p)
+    x = W.random_tt(4, 12, [1, 3, 5, 2, 1], seed=41)
+    e = W.random_tt(4, 12, [1, 2, 2, 2, 1], seed=42)
+    A = O.ttm_cores(ops, 1.0, 0.3)
+    ax = OT.matvec(A, x)
+    b = OT.add(ax, OT.scale(e, 1e-12 * OT.norm(ax) / OT.norm(e)))
+    got = T.t2s2_residual(op, T.TT.from_cores(b), T.TT.from_cores(x), c_mass=1.0, c_op=0.3)
+    ref = np.linalg.norm(OT.full(b) - OT.full(ax)) / np.linalg.norm(OT.full(b))
+    assert abs(got - ref) <= 1e-2 * ref
