@@ -90,17 +90,12 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
     bool bad = false;
     for (int p = 0; p < ra; ++p) {
       // pivot: largest |a_qp| over q >= p (ties: smallest q)
-      float best = -1.f;
-      int arg = p;
-      if (lane >= p && lane < ra) {
-        best = cabs2(A[lane * ra + p]);
-        arg = lane;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float b2 = __shfl_xor_sync(0xffffffffu, best, o);
-        const int a2 = __shfl_xor_sync(0xffffffffu, arg, o);
-        if (b2 > best || (b2 == best && a2 < arg)) best = b2, arg = a2;
-      }
+      // (non-negative binary32 values order like their bit patterns)
+      const unsigned mine = (lane >= p && lane < ra) ? __float_as_uint(cabs2(A[lane * ra + p])) : 0u;
+      const unsigned top = __reduce_max_sync(0xffffffffu, mine);
+      const unsigned who = __ballot_sync(0xffffffffu, lane >= p && lane < ra && mine == top);
+      const int arg = __ffs(who) - 1;
+      const float best = __uint_as_float(top);
       perm[p] = arg;
       if (!(best > 1e-24f * amax)) bad = true;
       if (arg != p)
@@ -143,10 +138,16 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
     double pr = 0.0, pf = 0.0;
     for (int e = t; e < ra * m; e += kSylvThreads) {
       const int a = e / m, i = e % m;
-      double s0 = pi * X[e], s1 = 0.0;
+      double s0 = pi * X[e], s1 = 0.0, s2 = 0.0, s3 = 0.0;
       for (int p = 0; p < ra; ++p) s0 = fma(PL[a * ra + p], X[p * m + i], s0);
-      for (int j = 0; j < m; ++j) s1 = fma(Bp[i * m + j], X[a * m + j], s1);
-      const double r = F[e] - (s0 + s1);
+      int j = 0;
+      for (; j + 2 < m; j += 3) {
+        s1 = fma(Bp[i * m + j], X[a * m + j], s1);
+        s2 = fma(Bp[i * m + j + 1], X[a * m + j + 1], s2);
+        s3 = fma(Bp[i * m + j + 2], X[a * m + j + 2], s3);
+      }
+      for (; j < m; ++j) s1 = fma(Bp[i * m + j], X[a * m + j], s1);
+      const double r = F[e] - ((s0 + s1) + (s2 + s3));
       R[e] = r;
       pr = fma(r, r, pr);
       if (step == 0) pf = fma(F[e], F[e], pf);
