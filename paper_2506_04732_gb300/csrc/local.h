@@ -53,7 +53,9 @@ struct SylvProblem {
   int* status = nullptr;
   int* iters_out = nullptr;
   double* res_out = nullptr;
+  unsigned long long* tstamp = nullptr;  // optional phase timestamps (diagnostics), kSylvStamps slots
 };
+constexpr int kSylvStamps = 48;
 bool sylv_rb1_fits(int ra, int m);
 t2s2_status sylv_rb1(const SylvProblem& P, cudaStream_t st);
 

@@ -505,8 +505,21 @@ struct Amen {
       S.status = sylv_status;
       S.iters_out = P.iters_out;
       S.res_out = P.res_out;
+      if (stamp_this) {
+        T2S2_CUDA_TRY(cudaMemsetAsync(tstamp_dev, 0, sizeof(unsigned long long) * kSylvStamps, c.st));
+        S.tstamp = tstamp_dev;
+      }
       T2S2_TRY(sylv_rb1(S, c.st));
       P.skip = sylv_status;
+      if (stamp_this) {
+        unsigned long long h[kSylvStamps];
+        T2S2_CUDA_TRY(cudaMemcpyAsync(h, tstamp_dev, sizeof(h), cudaMemcpyDeviceToHost, c.st));
+        T2S2_CUDA_TRY(cudaStreamSynchronize(c.st));
+        fprintf(stderr, "[t2s2] rb=1 local solve phase times (ns) ra=%d m=%d:", P.ra, P.m);
+        for (int i = 1; i < kSylvStamps && h[i]; ++i) fprintf(stderr, " %lld", (long long)(h[i] - h[i - 1]));
+        fprintf(stderr, "\n");
+        P.tstamp = nullptr;
+      }
     }
     T2S2_TRY(local_gmres<double>(P, c.st));
     if (stamp_this) {

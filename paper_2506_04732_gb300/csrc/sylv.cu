@@ -31,12 +31,25 @@ namespace {
 constexpr int kSylvThreads = 256;
 constexpr int kSylvMaxRa = 32;
 constexpr int kSylvMaxSteps = 6;
+constexpr int kSylvBlock = 8;  // columns of the backward substitution per serial block
 constexpr size_t kSylvMaxSmem = 160 * 1024;
 
+// Leading dimensions: odd counts of 8-byte words per row, so that lanes
+// walking down a column hit different shared-memory banks.
+__host__ __device__ inline int sylv_ld(int n) { return n | 1; }
+
 size_t sylv_smem_bytes(int ra, int m) {
-  const size_t dbl = (size_t)ra * ra + (size_t)m * m + 3 * (size_t)ra * m;
-  const size_t cpx = 2 * (size_t)m * m + (size_t)m * ra * ra + (size_t)ra * m + kSylvMaxRa;
+  const size_t lm = sylv_ld(m), la = sylv_ld(ra);
+  const size_t dbl = (size_t)ra * ra + (size_t)m * lm + 3 * (size_t)ra * m;
+  const size_t cpx = 2 * (size_t)m * lm + (size_t)m * ra * la + (size_t)ra * lm + kSylvMaxRa +
+                     (size_t)(kSylvThreads / 32) * kSylvMaxRa;
   return sizeof(double) * dbl + sizeof(cf) * cpx;
+}
+
+__device__ __forceinline__ unsigned long long sylv_clock() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
 }
 
 __device__ __forceinline__ cf cinv(cf a) {
@@ -47,26 +60,33 @@ __device__ __forceinline__ cf cinv(cf a) {
 __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ra = P.ra, m = P.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int lm = sylv_ld(m), la = sylv_ld(ra);
   double* PL = reinterpret_cast<double*>(smem);  // ra x ra
-  double* Bp = PL + ra * ra;                      // m x m
-  double* X = Bp + m * m;                         // ra x m
+  double* Bp = PL + ra * ra;                      // m x lm
+  double* X = Bp + m * lm;                        // ra x m
   double* R = X + ra * m;                         // ra x m
   double* F = R + ra * m;                         // ra x m
-  cf* Ts = reinterpret_cast<cf*>(F + ra * m);     // m x m (upper triangle)
-  cf* Z = Ts + m * m;                             // m x m
-  cf* Inv = Z + m * m;                            // m matrices ra x ra
-  cf* G = Inv + (size_t)m * ra * ra;              // ra x m: G, then Y in place
-  cf* tv = G + ra * m;                            // kSylvMaxRa: one right-hand side
+  cf* Ts = reinterpret_cast<cf*>(F + ra * m);     // m x lm (upper triangle)
+  cf* Z = Ts + m * lm;                            // m x lm
+  cf* Inv = Z + m * lm;                           // m matrices ra x la
+  cf* G = Inv + (size_t)m * ra * la;              // ra x lm: G, then Y in place
+  cf* tv = G + ra * lm;                           // kSylvMaxRa: one right-hand side
+  cf* prow = tv + kSylvMaxRa;                     // per warp: the pivot row
   __shared__ double red[kSylvThreads / 32];
   __shared__ int fail;
+  int nst = 0;
+  auto stamp = [&]() {
+    if (P.tstamp && t == 0 && nst < kSylvStamps) P.tstamp[nst++] = sylv_clock();
+  };
+  stamp();
   const double pi = P.PR[0];
   const float cop = (float)P.c_op, sh = (float)P.shift;
   for (int e = t; e < ra * ra; e += kSylvThreads) PL[e] = P.PL[e];
   for (int e = t; e < m * m; e += kSylvThreads) {
-    Bp[e] = P.Bp[e];
     const int i = e / m, j = e % m;
-    Ts[e] = cmk(cop * P.Tr[e] + (i == j ? sh : 0.f), cop * P.Ti[e]);
-    Z[e] = cmk(P.Zr[e], P.Zi[e]);
+    Bp[i * lm + j] = P.Bp[e];
+    Ts[i * lm + j] = cmk(cop * P.Tr[e] + (i == j ? sh : 0.f), cop * P.Ti[e]);
+    Z[i * lm + j] = cmk(P.Zr[e], P.Zi[e]);
   }
   for (int e = t; e < ra * m; e += kSylvThreads) {
     X[e] = P.x[e];
@@ -74,99 +94,117 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
   }
   if (t == 0) fail = 0;
   __syncthreads();
-  // inverses of A_i = P_L + (Ts_ii + pi) I, one warp each; lane = row
+  stamp();
+  // inverses of A_i = P_L + (Ts_ii + pi) I by Gauss-Jordan, one warp each;
+  // lane = row (lane = column for the pivot-row steps)
+  cf* pr = prow + warp * kSylvMaxRa;
   for (int i = warp; i < m; i += kSylvThreads / 32) {
-    cf* A = Inv + (size_t)i * ra * ra;
-    const cf s = cadd(Ts[i * m + i], cmk((float)pi, 0.f));
+    cf* A = Inv + (size_t)i * ra * la;
+    const cf s = cadd(Ts[i * lm + i], cmk((float)pi, 0.f));
+    float amax = 0.f;
     for (int e = lane; e < ra * ra; e += 32) {
       const int p = e / ra, q = e % ra;
-      A[e] = cadd(cmk((float)PL[e], 0.f), p == q ? s : cmk(0.f, 0.f));
+      const cf v = cadd(cmk((float)PL[e], 0.f), p == q ? s : cmk(0.f, 0.f));
+      A[p * la + q] = v;
+      amax = fmaxf(amax, cabs2(v));
     }
-    __syncwarp();
-    float amax = 0.f;
-    for (int e = lane; e < ra * ra; e += 32) amax = fmaxf(amax, cabs2(A[e]));
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    __syncwarp();
     int perm[kSylvMaxRa];
     bool bad = false;
     for (int p = 0; p < ra; ++p) {
-      // pivot: largest |a_qp| over q >= p (ties: smallest q)
+      // pivot: largest |a_qp| over q >= p, ties to the smallest q
       // (non-negative binary32 values order like their bit patterns)
-      const unsigned mine = (lane >= p && lane < ra) ? __float_as_uint(cabs2(A[lane * ra + p])) : 0u;
+      const unsigned mine = (lane >= p && lane < ra) ? __float_as_uint(cabs2(A[lane * la + p])) : 0u;
       const unsigned top = __reduce_max_sync(0xffffffffu, mine);
       const unsigned who = __ballot_sync(0xffffffffu, lane >= p && lane < ra && mine == top);
       const int arg = __ffs(who) - 1;
-      const float best = __uint_as_float(top);
       perm[p] = arg;
-      if (!(best > 1e-24f * amax)) bad = true;
-      if (arg != p)
-        for (int c = lane; c < ra; c += 32) {
-          const cf u = A[p * ra + c];
-          A[p * ra + c] = A[arg * ra + c];
-          A[arg * ra + c] = u;
+      if (!(__uint_as_float(top) > 1e-24f * amax)) bad = true;
+      // row arg -> pivot row (scaled by 1 / pivot, the pivot slot set to 1),
+      // row p -> row arg
+      const cf piv = A[arg * la + p];
+      const cf ip = bad ? cmk(0.f, 0.f) : cinv(piv);
+      if (lane < ra) {
+        const cf vp = A[arg * la + lane], vq = A[p * la + lane];
+        pr[lane] = cmul(lane == p ? cmk(1.f, 0.f) : vp, ip);
+        if (arg != p) A[arg * la + lane] = vq;
+      }
+      __syncwarp();
+      if (lane < ra) {
+        cf* __restrict__ row = A + lane * la;
+        const cf* __restrict__ prr = pr;
+        if (lane == p) {
+          for (int c = 0; c < ra; ++c) row[c] = prr[c];
+        } else {
+          const cf f = row[p];
+          for (int c = 0; c < ra; ++c) {
+            const cf base = (c == p) ? cmk(0.f, 0.f) : row[c];
+            row[c] = csub(base, cmul(f, prr[c]));
+          }
         }
-      __syncwarp();
-      const cf ip = bad ? cmk(0.f, 0.f) : cinv(A[p * ra + p]);
-      __syncwarp();
-      for (int c = lane; c < ra; c += 32) A[p * ra + c] = cmul(c == p ? cmk(1.f, 0.f) : A[p * ra + c], ip);
-      __syncwarp();
-      if (lane < ra && lane != p) {
-        const cf f = A[lane * ra + p];
-        A[lane * ra + p] = cmk(0.f, 0.f);
-        for (int c = 0; c < ra; ++c) A[lane * ra + c] = csub(A[lane * ra + c], cmul(f, A[p * ra + c]));
       }
       __syncwarp();
     }
     // undo the row swaps as column swaps, last first
     for (int p = ra - 1; p >= 0; --p) {
       const int q = perm[p];
-      if (q != p)
-        for (int r = lane; r < ra; r += 32) {
-          const cf u = A[r * ra + p];
-          A[r * ra + p] = A[r * ra + q];
-          A[r * ra + q] = u;
-        }
+      if (q != p && lane < ra) {
+        const cf u = A[lane * la + p];
+        A[lane * la + p] = A[lane * la + q];
+        A[lane * la + q] = u;
+      }
       __syncwarp();
     }
     if (bad && lane == 0) fail = 1;
   }
   __syncthreads();
+  stamp();
   int status = fail ? 1 : 0;
   double rr = 0.0, ff = 0.0, rr_prev = -1.0;
   int its = 0;
   for (int step = 0; status == 0; ++step) {
     // R = F - K X in binary64, ||R||^2 (and ||F||^2 at first)
-    double pr = 0.0, pf = 0.0;
-    for (int e = t; e < ra * m; e += kSylvThreads) {
-      const int a = e / m, i = e % m;
-      double s0 = pi * X[e], s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      for (int p = 0; p < ra; ++p) s0 = fma(PL[a * ra + p], X[p * m + i], s0);
-      int j = 0;
-      for (; j + 2 < m; j += 3) {
-        s1 = fma(Bp[i * m + j], X[a * m + j], s1);
-        s2 = fma(Bp[i * m + j + 1], X[a * m + j + 1], s2);
-        s3 = fma(Bp[i * m + j + 2], X[a * m + j + 2], s3);
+    double prs = 0.0, pfs = 0.0;
+    {
+      const double* __restrict__ Xr = X;
+      const double* __restrict__ Br = Bp;
+      const double* __restrict__ Pr = PL;
+      const double* __restrict__ Fr = F;
+      double* __restrict__ Rw = R;
+      for (int e = t; e < ra * m; e += kSylvThreads) {
+        const int a = e / m, i = e % m;
+        double s0 = pi * Xr[e], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        for (int p = 0; p < ra; ++p) s0 = fma(Pr[a * ra + p], Xr[p * m + i], s0);
+        int j = 0;
+        for (; j + 2 < m; j += 3) {
+          s1 = fma(Br[i * lm + j], Xr[a * m + j], s1);
+          s2 = fma(Br[i * lm + j + 1], Xr[a * m + j + 1], s2);
+          s3 = fma(Br[i * lm + j + 2], Xr[a * m + j + 2], s3);
+        }
+        for (; j < m; ++j) s1 = fma(Br[i * lm + j], Xr[a * m + j], s1);
+        const double r = Fr[e] - ((s0 + s1) + (s2 + s3));
+        Rw[e] = r;
+        prs = fma(r, r, prs);
+        if (step == 0) pfs = fma(Fr[e], Fr[e], pfs);
       }
-      for (; j < m; ++j) s1 = fma(Bp[i * m + j], X[a * m + j], s1);
-      const double r = F[e] - ((s0 + s1) + (s2 + s3));
-      R[e] = r;
-      pr = fma(r, r, pr);
-      if (step == 0) pf = fma(F[e], F[e], pf);
     }
     for (int o = 16; o > 0; o >>= 1) {
-      pr += __shfl_xor_sync(0xffffffffu, pr, o);
-      pf += __shfl_xor_sync(0xffffffffu, pf, o);
+      prs += __shfl_xor_sync(0xffffffffu, prs, o);
+      pfs += __shfl_xor_sync(0xffffffffu, pfs, o);
     }
-    if (lane == 0) red[warp] = pr;
+    if (lane == 0) red[warp] = prs;
     __syncthreads();
     rr = 0.0;
     for (int w = 0; w < kSylvThreads / 32; ++w) rr += red[w];
     __syncthreads();
     if (step == 0) {
-      if (lane == 0) red[warp] = pf;
+      if (lane == 0) red[warp] = pfs;
       __syncthreads();
       for (int w = 0; w < kSylvThreads / 32; ++w) ff += red[w];
       __syncthreads();
     }
+    stamp();
     if (rr <= P.tol_rel * P.tol_rel * ff || rr == 0.0) break;  // converged
     if ((rr_prev >= 0.0 && rr > 0.01 * rr_prev) || step == kSylvMaxSteps) {
       status = 1;  // not paying off: the general solver takes over
@@ -174,50 +212,100 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
     }
     rr_prev = rr;
     // G = R conj(Z)
-    for (int e = t; e < ra * m; e += kSylvThreads) {
-      const int a = e / m, i = e % m;
-      float gr = 0.f, gi = 0.f;
-      for (int j = 0; j < m; ++j) {
-        const float rv = (float)R[a * m + j];
-        const cf z = Z[j * m + i];
-        gr = fmaf(rv, z.x, gr);
-        gi = fmaf(-rv, z.y, gi);
-      }
-      G[e] = cmk(gr, gi);
-    }
-    __syncthreads();
-    // y_i = A_i^{-1} (g_i - sum_{j > i} Ts_ij y_j), i = m-1 .. 0 (warp 0;
-    // lane = row a), Y over G in place
-    if (warp == 0) {
-      for (int i = m - 1; i >= 0; --i) {
-        if (lane < ra) {
-          cf s = G[lane * m + i];
-          for (int j = i + 1; j < m; ++j) s = csub(s, cmul(Ts[i * m + j], G[lane * m + j]));
-          tv[lane] = s;
+    {
+      const double* __restrict__ Rr = R;
+      const cf* __restrict__ Zr = Z;
+      cf* __restrict__ Gw = G;
+      for (int e = t; e < ra * m; e += kSylvThreads) {
+        const int a = e / m, i = e % m;
+        float gr = 0.f, gi = 0.f, hr = 0.f, hi = 0.f;
+        int j = 0;
+        for (; j + 1 < m; j += 2) {
+          const float rv = (float)Rr[a * m + j], rw = (float)Rr[a * m + j + 1];
+          const cf z = Zr[j * lm + i], w = Zr[(j + 1) * lm + i];
+          gr = fmaf(rv, z.x, gr);
+          gi = fmaf(-rv, z.y, gi);
+          hr = fmaf(rw, w.x, hr);
+          hi = fmaf(-rw, w.y, hi);
         }
-        __syncwarp();
-        if (lane < ra) {
-          const cf* A = Inv + (size_t)i * ra * ra + lane * ra;
-          cf y = cmk(0.f, 0.f);
-          for (int q = 0; q < ra; ++q) y = cadd(y, cmul(A[q], tv[q]));
-          G[lane * m + i] = y;
+        if (j < m) {
+          const float rv = (float)Rr[a * m + j];
+          const cf z = Zr[j * lm + i];
+          gr = fmaf(rv, z.x, gr);
+          gi = fmaf(-rv, z.y, gi);
         }
-        __syncwarp();
+        Gw[a * lm + i] = cmk(gr + hr, gi + hi);
       }
     }
     __syncthreads();
+    stamp();
+    // y_i = A_i^{-1} (g_i - sum_{j > i} Ts_ij y_j), i = m-1 .. 0, Y over G in
+    // place: blocks of kSylvBlock columns from the last; one warp solves a
+    // block step by step with the in-block terms only, then all threads take
+    // the block's contribution out of the earlier right-hand sides at once
+    for (int hi = m - 1; hi >= 0; hi -= kSylvBlock) {
+      const int lo = max(0, hi - kSylvBlock + 1);
+      if (warp == 0) {
+        const cf* __restrict__ Tr = Ts;
+        for (int i = hi; i >= lo; --i) {
+          if (lane < ra) {
+            cf s = G[lane * lm + i];
+            for (int j = i + 1; j <= hi; ++j) s = csub(s, cmul(Tr[i * lm + j], G[lane * lm + j]));
+            tv[lane] = s;
+          }
+          __syncwarp();
+          if (lane < ra) {
+            const cf* __restrict__ A = Inv + (size_t)i * ra * la + lane * la;
+            const cf* __restrict__ v = tv;
+            cf y0 = cmk(0.f, 0.f), y1 = cmk(0.f, 0.f);
+            int q = 0;
+            for (; q + 1 < ra; q += 2) {
+              y0 = cadd(y0, cmul(A[q], v[q]));
+              y1 = cadd(y1, cmul(A[q + 1], v[q + 1]));
+            }
+            if (q < ra) y0 = cadd(y0, cmul(A[q], v[q]));
+            G[lane * lm + i] = cadd(y0, y1);
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      {
+        const cf* __restrict__ Tr = Ts;
+        for (int e = t; e < ra * lo; e += kSylvThreads) {
+          const int a = e / lo, j = e % lo;
+          cf s = G[a * lm + j];
+          for (int i = lo; i <= hi; ++i) s = csub(s, cmul(Tr[j * lm + i], G[a * lm + i]));
+          G[a * lm + j] = s;
+        }
+      }
+      __syncthreads();
+    }
+    stamp();
     // X += Re(Y Z^T)
-    for (int e = t; e < ra * m; e += kSylvThreads) {
-      const int a = e / m, i = e % m;
-      float d = 0.f;
-      for (int j = 0; j < m; ++j) {
-        const cf y = G[a * m + j], z = Z[i * m + j];
-        d = fmaf(y.x, z.x, fmaf(-y.y, z.y, d));
+    {
+      const cf* __restrict__ Yr = G;
+      const cf* __restrict__ Zr = Z;
+      double* __restrict__ Xw = X;
+      for (int e = t; e < ra * m; e += kSylvThreads) {
+        const int a = e / m, i = e % m;
+        float d0 = 0.f, d1 = 0.f;
+        int j = 0;
+        for (; j + 1 < m; j += 2) {
+          const cf y = Yr[a * lm + j], z = Zr[i * lm + j], y2 = Yr[a * lm + j + 1], z2 = Zr[i * lm + j + 1];
+          d0 = fmaf(y.x, z.x, fmaf(-y.y, z.y, d0));
+          d1 = fmaf(y2.x, z2.x, fmaf(-y2.y, z2.y, d1));
+        }
+        if (j < m) {
+          const cf y = Yr[a * lm + j], z = Zr[i * lm + j];
+          d0 = fmaf(y.x, z.x, fmaf(-y.y, z.y, d0));
+        }
+        Xw[e] += (double)(d0 + d1);
       }
-      X[e] += (double)d;
     }
     ++its;
     __syncthreads();
+    stamp();
   }
   for (int e = t; e < ra * m; e += kSylvThreads) P.x[e] = X[e];
   if (t == 0) {
