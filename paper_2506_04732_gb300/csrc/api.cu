@@ -227,8 +227,17 @@ t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
 constexpr double kDDFloor = 1e-13;
 constexpr double kScreen = 1e-5;
 
+namespace {
+// s + e = a + b exactly (no multiplication, so nothing can be fused)
+void host_two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+}  // namespace
+
 t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,
-                          double* out, double* bnorm_io, bool screen) {
+                          double* out, ResidualCache* rc, bool screen) {
   size_t mark = cx.ar->mark();
   DevTT y;
   int r2[T2S2_MAX_D + 1];
@@ -238,33 +247,43 @@ t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
   if (screen) {
     // binary64 |b|^2 - 2<b, y> + |y|^2: its cancellation noise (~1e-8
     // relative in the norm) is irrelevant for a residual far above kScreen
-    const bool with_bb = *bnorm_io < 0.0;
+    const bool with_bb = rc->bnorm < 0.0;
     const DevTT* pu[3] = {&b, &y, &b};
     const DevTT* pv[3] = {&y, &y, &b};
     double dots[3] = {0.0, 0.0, 0.0};
     T2S2_TRY(tt_dots(cx, with_bb ? 3 : 2, pu, pv, dots));
-    const double bb = with_bb ? dots[2] : (*bnorm_io) * (*bnorm_io);
+    const double bb = with_bb ? dots[2] : rc->bnorm * rc->bnorm;
     const double r2v = std::max(bb - 2.0 * dots[0] + dots[1], 0.0);
     const double est = (bb > 0) ? std::sqrt(r2v / bb) : std::sqrt(r2v);
     if (est > kScreen) {
-      if (with_bb) *bnorm_io = std::sqrt(bb);
+      if (with_bb) rc->bnorm = std::sqrt(bb);
       *out = est;
       cx.ar->release(mark);
       return T2S2_OK;
     }
   }
-  DevTT z;
-  T2S2_TRY(tt_axpby(cx, 1.0, b, -1.0, y, z));
-  const bool with_b = *bnorm_io < 0.0;
-  const DevTT* pu[2] = {&z, &b};
-  double hi[2] = {0.0, 0.0}, lo[2] = {0.0, 0.0};
-  T2S2_TRY(tt_norm2_dd(cx, with_b ? 2 : 1, pu, hi, lo));
-  if (with_b) *bnorm_io = std::sqrt(std::max(hi[1] + lo[1], 0.0));
-  const double bn = *bnorm_io;
-  const double zn = std::sqrt(std::max(hi[0] + lo[0], 0.0));
+  // |b|^2 - 2<b, y> + |y|^2 with every inner product in double-double (|b|^2
+  // once per right-hand side), combined with error-free sums
+  const bool with_bb = rc->bb_hi < 0.0;
+  const DevTT* pu[3] = {&b, &y, &b};
+  const DevTT* pv[3] = {&y, &y, &b};
+  double hi[3] = {0.0, 0.0, 0.0}, lo[3] = {0.0, 0.0, 0.0};
+  T2S2_TRY(tt_dots_dd(cx, with_bb ? 3 : 2, pu, pv, hi, lo));
+  if (with_bb) {
+    rc->bb_hi = hi[2];
+    rc->bb_lo = lo[2];
+  }
+  double s1, e1, s2, e2;
+  host_two_sum(rc->bb_hi, -2.0 * hi[0], s1, e1);
+  host_two_sum(s1, hi[1], s2, e2);
+  const double r2v = s2 + (((rc->bb_lo - 2.0 * lo[0]) + lo[1]) + (e1 + e2));
+  const double bb = rc->bb_hi + rc->bb_lo;
+  if (rc->bnorm < 0.0) rc->bnorm = std::sqrt(std::max(bb, 0.0));
+  const double bn = rc->bnorm;
+  const double zn = std::sqrt(std::max(r2v, 0.0));
   double res = (bn > 0) ? zn / bn : zn;
   cx.ar->release(mark);
-  if (res < kDDFloor) T2S2_TRY(residual_impl(op, cx, b, x, c_mass, c_op, false, &res, bnorm_io));
+  if (res < kDDFloor) T2S2_TRY(residual_impl(op, cx, b, x, c_mass, c_op, false, &res, &rc->bnorm));
   *out = res;
   return T2S2_OK;
 }
@@ -537,8 +556,8 @@ t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double
   DevTT db, dx;
   T2S2_TRY(bind_tt(cx, b, db, true));
   T2S2_TRY(bind_tt(cx, x, dx, true));
-  double bnorm = -1.0;
-  return residual_fast(op, cx, db, dx, c_mass, c_op, out, &bnorm, false);
+  ResidualCache rc;
+  return residual_fast(op, cx, db, dx, c_mass, c_op, out, &rc, false);
 }
 
 }  // extern "C"

@@ -68,14 +68,21 @@ t2s2_status tt_dot(Ctx& cx, const DevTT& u, const DevTT& v, double* out);
 t2s2_status tt_dots(Ctx& cx, int n, const DevTT* const* u, const DevTT* const* v, double* out);
 t2s2_status residual_estimate(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
                               double c_op, double* bb_io, double* out);
-// <u_p, u_p> in double-double for p < n <= 4 (ttdot.cu), as hi + lo pairs.
-t2s2_status tt_norm2_dd(Ctx& cx, int n, const DevTT* const* u, double* hi, double* lo);
-// The residual of the original system from <z, z> in double-double, falling
-// back to residual_impl's orthogonalised norm for residuals below 1e-13.
-// screen: first try binary64 inner products, and return their value when it
-// is above 1e-5 (a guess far from converged).
+// <u_p, v_p> in double-double for p < n <= 4 (ttdot.cu), as hi + lo pairs.
+t2s2_status tt_dots_dd(Ctx& cx, int n, const DevTT* const* u, const DevTT* const* v, double* hi, double* lo);
+// What the residual of one right-hand side b keeps between calls: |b| and
+// |b|^2 in double-double (negative: not known yet).
+struct ResidualCache {
+  double bnorm = -1.0;
+  double bb_hi = -1.0, bb_lo = 0.0;
+};
+// The residual of the original system: |b|^2 - 2<b, A x> + |A x|^2 with the
+// inner products in double-double, falling back to residual_impl's
+// orthogonalised norm for residuals below 1e-13.  screen: first try binary64
+// inner products, and return their value when it is above 1e-5 (a guess far
+// from converged).
 t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,
-                          double* out, double* bnorm_io, bool screen);
+                          double* out, ResidualCache* rc, bool screen);
 t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
                           double c_op, bool transformed, double* out, double* bnorm_io);
 }  // namespace t2s2

@@ -57,6 +57,8 @@ constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
 
 struct CholQrArgs {
   const double* W;
+  const double* W2;  // tall only: columns c1 .. c-1 in a second block (null: one block)
+  int c1;
   double* Q;
   double* R;     // c x c output (R = Lacc^T for tall, L = Lacc for wide)
   double* part;  // grid x T partial Grams (T = c (c + 1) / 2)
@@ -78,6 +80,12 @@ __host__ __device__ inline size_t smem_bytes(int per, int c, int grid) {
 // element j of vector i in a tall (i-th row) or wide (i-th column) block
 __device__ __forceinline__ long vidx(const CholQrArgs& a, int i, int j) {
   return a.tall ? (long)i * a.c + j : (long)j * a.nlong + i;
+}
+
+// element j of input vector i (a tall input may come in two column blocks)
+__device__ __forceinline__ double win(const CholQrArgs& a, int i, int j) {
+  if (a.W2) return j < a.c1 ? a.W[(long)i * a.c1 + j] : a.W2[(long)i * (a.c - a.c1) + (j - a.c1)];
+  return a.W[vidx(a, i, j)];
 }
 
 // binary32 seed and one binary64 Newton step: 1/v to about 2^-46
@@ -111,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
   __shared__ int bad, last;
   for (int e = t; e < cnt * c; e += kThreads) {
     const int r = a.tall ? e / c : e % cnt, j = a.tall ? e % c : e / cnt;
-    V[r * c + j] = a.W[vidx(a, i0 + r, j)];
+    V[r * c + j] = win(a, i0 + r, j);
   }
   for (int ia = t; ia < c; ia += kThreads)
     for (int ib = 0; ib <= ia; ++ib) tri[ia * (ia + 1) / 2 + ib] = (ia << 8) | ib;
@@ -336,9 +344,12 @@ bool cholqr3_plan(int nlong, int c, int max_grid, int* grid_out, int* per_out, s
 }
 
 t2s2_status cholqr3_fused(const double* W, double* Q, double* R, int nlong, int c, bool tall, double shift_rel,
-                          double* scratch, int* status, int grid, int per, size_t smem, cudaStream_t st) {
+                          double* scratch, int* status, int grid, int per, size_t smem, cudaStream_t st,
+                          const double* W2, int c1) {
   CholQrArgs a;
   a.W = W;
+  a.W2 = (tall && W2) ? W2 : nullptr;
+  a.c1 = c1;
   a.Q = Q;
   a.R = R;
   a.part = scratch;

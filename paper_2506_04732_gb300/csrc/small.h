@@ -23,7 +23,10 @@ t2s2_status jacobi_svd(const double* A, int p, int q, double* U, double* s, doub
 // caps the number of CTAs.
 bool cholqr3_plan(int nlong, int c, int max_grid, int* grid, int* per, size_t* smem);
 size_t cholqr3_scratch_doubles(int nlong, int c, int grid);
+// W2 (tall only): the input as two row-major blocks, columns 0 .. c1-1 in W
+// (nlong x c1) and c1 .. c-1 in W2 (nlong x (c - c1)).
 t2s2_status cholqr3_fused(const double* W, double* Q, double* R, int nlong, int c, bool tall, double shift_rel,
-                          double* scratch, int* status, int grid, int per, size_t smem, cudaStream_t st);
+                          double* scratch, int* status, int grid, int per, size_t smem, cudaStream_t st,
+                          const double* W2 = nullptr, int c1 = 0);
 
 }  // namespace t2s2

@@ -100,6 +100,51 @@ t2s2_status d2d(Ctx& cx, double* dst, const double* src, size_t n) {
 }
 t2s2_status set_scalar(Ctx& cx, double* dst, double v) { return dev_fill(cx, dst, 1, v); }
 
+// The next core of the sweep, (Q^T U S V^T) x_1 X1, in one CTA when X1 fits
+// in shared memory: C = Q^T U (one warp per entry, lanes over the rows, fixed
+// shuffle tree), CS = C S V^T, then X1 <- CS x_1 X1 in place (X1 is staged
+// in shared memory first).
+constexpr size_t kNextCoreSmem = 40 * 1024;
+
+__global__ void k_next_core(const double* Q, const double* U, const double* SV, int rows, int rn, int rk, int rb,
+                            double* X1, int mn, int rnn) {
+  extern __shared__ double nsm[];
+  double* xs = nsm;                     // rb x mn x rnn
+  double* C = xs + (size_t)rb * mn * rnn;  // rn x rk
+  double* CS = C + rn * rk;             // rn x rb
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  const int nx = rb * mn * rnn;
+  for (int e = t; e < nx; e += blockDim.x) xs[e] = X1[e];
+  for (int q = warp; q < rn * rk; q += nw) {
+    const int cc = q / rk, a = q % rk;
+    double s0 = 0.0, s1 = 0.0;
+    int r = lane;
+    for (; r + 32 < rows; r += 64) {
+      s0 = fma(Q[(long)r * rn + cc], U[(long)r * rk + a], s0);
+      s1 = fma(Q[(long)(r + 32) * rn + cc], U[(long)(r + 32) * rk + a], s1);
+    }
+    if (r < rows) s0 = fma(Q[(long)r * rn + cc], U[(long)r * rk + a], s0);
+    double s = s0 + s1;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) C[q] = s;
+  }
+  __syncthreads();
+  for (int e = t; e < rn * rb; e += blockDim.x) {
+    const int cc = e / rb, b = e % rb;
+    double s = 0.0;
+    for (int a = 0; a < rk; ++a) s = fma(C[cc * rk + a], SV[a * rb + b], s);
+    CS[e] = s;
+  }
+  __syncthreads();
+  const int inner = mn * rnn;
+  for (int e = t; e < rn * inner; e += blockDim.x) {
+    const int cc = e / inner, ie = e % inner;
+    double s = 0.0;
+    for (int b = 0; b < rb; ++b) s = fma(CS[cc * rb + b], xs[b * inner + ie], s);
+    X1[e] = s;
+  }
+}
+
 // SVD of one column x (n entries): u = x / |x| (0 for x = 0), s v^T = |x|,
 // and the truncated product u s v^T = x.  One CTA, fixed-order sum.
 __global__ void k_col_split(const double* x, int n, double* u, double* sv, double* xt) {
@@ -683,38 +728,39 @@ struct Amen {
         T2S2_TRY(d2d(c, z.c[k], Qz, (size_t)za * m * zb));
       }
       ph(7);
-      // --- new core: orthonormal basis of [U | res]
-      int cols = rk + zb;
-      double* Q = tmp[2];
-      int rn;
+      // --- new core: orthonormal basis of [U | res], written over core k
+      // (whose old content the local solve has consumed)
+      const int cols = rk + zb;
+      const int mn = op->m[k + 1], rnn = x.r[k + 2];
+      const int rn = (rows >= cols) ? cols : rows;
+      if ((size_t)rn * mn * rnn > x.cap[k + 1] || (size_t)rows * rn > x.cap[k]) return T2S2_ENOMEM;
+      double* Q = x.c[k];
       if (rows >= cols) {
-        double* cat = tmp[1];
-        T2S2_CUDA_TRY(cudaMemcpy2DAsync(cat, sizeof(double) * cols, U, sizeof(double) * rk,
-                                        sizeof(double) * rk, rows, cudaMemcpyDeviceToDevice, c.st));
-        T2S2_CUDA_TRY(cudaMemcpy2DAsync(cat + rk, sizeof(double) * cols, res, sizeof(double) * zb,
-                                        sizeof(double) * zb, rows, cudaMemcpyDeviceToDevice, c.st));
         double* Rq = tmp[8];
-        T2S2_TRY(qr_tall(c, cat, rows, cols, Q, Rq));
-        rn = cols;
+        T2S2_TRY(qr_tall2(c, U, rk, res, zb, rows, Q, Rq, tmp[1]));
       } else {
         T2S2_TRY(dev_identity(c, Q, rows));
-        rn = rows;
       }
-      // next core: (Q^T U SV) x_1 x[k+1]
+      // next core: (Q^T U SV) x_1 x[k+1], carried in FP64 whatever the
+      // contraction arithmetic
       {
-        const int mn = op->m[k + 1], rnn = x.r[k + 2];
-        double* C = tmp[6];
-        double* CS = tmp[7];
-        double* P = tmp[0];
-        T2S2_TRY(gemm_ex<double>(c, rn, rk, rows, true, false, 1.0, Q, rn, U, rk, 0.0, C, rk));
-        T2S2_TRY(gemm_ex<double>(c, rn, rb, rk, false, false, 1.0, C, rk, SV, rb, 0.0, CS, rb));
-        if ((size_t)rn * mn * rnn > x.cap[k + 1] || (size_t)ra * m * rn > x.cap[k]) return T2S2_ENOMEM;
-        // the iterate itself is carried in FP64 whatever the contraction arithmetic
-        Ctx c64 = c;
-        c64.contract_prec = T2S2_FP64;
-        T2S2_TRY(mode1(c64, CS, rn, rb, x.c[k + 1], mn, rnn, P));
-        T2S2_TRY(d2d(c, x.c[k + 1], P, (size_t)rn * mn * rnn));
-        T2S2_TRY(d2d(c, x.c[k], Q, (size_t)rows * rn));
+        const size_t nx = (size_t)rb * mn * rnn;
+        const size_t sm = sizeof(double) * (nx + (size_t)rn * (rk + rb));
+        if (sm <= kNextCoreSmem) {
+          TraceScope ts(kTrGemm, c.st, 2.0 * rows * rn * rk + 2.0 * rn * rk * rb + 2.0 * rn * (double)nx, 0.0);
+          k_next_core<<<1, 256, sm, c.st>>>(Q, U, SV, rows, rn, rk, rb, x.c[k + 1], mn, rnn);
+          T2S2_CUDA_TRY(cudaGetLastError());
+        } else {
+          double* C = tmp[6];
+          double* CS = tmp[7];
+          double* P = tmp[0];
+          T2S2_TRY(gemm_ex<double>(c, rn, rk, rows, true, false, 1.0, Q, rn, U, rk, 0.0, C, rk));
+          T2S2_TRY(gemm_ex<double>(c, rn, rb, rk, false, false, 1.0, C, rk, SV, rb, 0.0, CS, rb));
+          Ctx c64 = c;
+          c64.contract_prec = T2S2_FP64;
+          T2S2_TRY(mode1(c64, CS, rn, rb, x.c[k + 1], mn, rnn, P));
+          T2S2_TRY(d2d(c, x.c[k + 1], P, nx / rb * rn));
+        }
         x.r[k + 1] = rn;
       }
       ph(8);
@@ -762,8 +808,9 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
   T2S2_TRY(am.init(op, cx, b, xio, c_mass, c_op, tol, rmax));
   T2S2_TRY(tt_orth_right(cx, am.x));
   // the residual of the original system, before and after every sweep
-  double bnorm = -1.0, res = 0.0;
-  T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &bnorm, true));
+  ResidualCache rcache;
+  double res = 0.0;
+  T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &rcache, true));
   int sweeps = 0;
   const char* ev = std::getenv("T2S2_VERBOSE");
   const bool verbose = ev && ev[0] == '1';
@@ -773,7 +820,7 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
     T2S2_TRY(am.sweep());
     ++sweeps;
     am.ph(9);
-    T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &bnorm, false));
+    T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &rcache, false));
     T2S2_TRY(am.collect_iters());
     if (verbose) {
       double rt = 0.0;
@@ -874,8 +921,9 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
     T2S2_TRY(tt_copy(cx, t, g));
     cx.ar->release(mk);
   }
-  double bnorm = -1.0, res = 0.0;
-  T2S2_TRY(residual_fast(op, cx, b, x, c_mass, c_op, &res, &bnorm, true));
+  ResidualCache rcache;
+  double res = 0.0;
+  T2S2_TRY(residual_fast(op, cx, b, x, c_mass, c_op, &res, &rcache, true));
   bool x_zero = false;
   if (res >= 1.0) {  // x0 is worse than x = 0
     x_zero = true;
@@ -951,7 +999,7 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
       ++refinements;
       if (verbose) {
         double rg = 0.0;
-        T2S2_TRY(residual_fast(op, cx, b, g, c_mass, c_op, &rg, &bnorm, true));
+        T2S2_TRY(residual_fast(op, cx, b, g, c_mass, c_op, &rg, &rcache, true));
         fprintf(stderr, "[t2s2] tensor-core stage: inner sweeps %d est %.2e residual %.3e\n", inner, est, rg);
       }
       continue;
@@ -980,7 +1028,7 @@ t2s2_status refine_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double 
     x_zero = false;
     ++refinements;
     const double prev = res;
-    T2S2_TRY(residual_fast(op, cx, b, x, c_mass, c_op, &res, &bnorm, true));
+    T2S2_TRY(residual_fast(op, cx, b, x, c_mass, c_op, &res, &rcache, true));
     if (verbose) {
       fprintf(stderr, "[t2s2] refinement %d: inner sweeps %d est %.2e (target %.1e) residual %.3e ranks", refinements,
               inner, est, tin, res);

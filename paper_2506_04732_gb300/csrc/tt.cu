@@ -177,7 +177,7 @@ __global__ void k_transpose(double* dst, const double* src, int r, int c) {
 // Fused single-launch CholeskyQR3 when its grid fits (cholqr.cu), else the
 // pass-by-pass sequence below.
 static bool qr_fused(Ctx& cx, const double* W, int nlong, int c, bool tall, double* Q, double* R,
-                     t2s2_status* st) {
+                     t2s2_status* st, const double* W2 = nullptr, int c1 = 0) {
   int grid = 0, per = 0;
   size_t smem = 0;
   if (!cholqr3_plan(nlong, c, cx.coop_ctas, &grid, &per, &smem)) return false;
@@ -188,7 +188,7 @@ static bool qr_fused(Ctx& cx, const double* W, int nlong, int c, bool tall, doub
     return false;
   }
   const double shift = 11.0 * ((double)nlong * c + (double)c * (c + 1)) * kUnit;
-  *st = cholqr3_fused(W, Q, R, nlong, c, tall, shift, scratch, cx.dstat, grid, per, smem, cx.st);
+  *st = cholqr3_fused(W, Q, R, nlong, c, tall, shift, scratch, cx.dstat, grid, per, smem, cx.st, W2, c1);
   cx.ar->release(mk);
   return true;
 }
@@ -230,6 +230,22 @@ t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, dou
   T2S2_CUDA_TRY(cudaGetLastError());
   cx.ar->release(mk);
   return T2S2_OK;
+}
+
+t2s2_status qr_tall2(Ctx& cx, const double* U, int c1, const double* W2, int c2, int rows, double* Q, double* R,
+                     double* scratch) {
+  const int cols = c1 + c2;
+  if (cols > kSmallMax || rows < cols || c1 <= 0 || c2 <= 0) return T2S2_EINVAL;
+  {
+    t2s2_status fs = T2S2_OK;
+    if (qr_fused(cx, U, rows, cols, true, Q, R, &fs, W2, c1)) return fs;
+  }
+  // the pass-by-pass path wants one block
+  T2S2_CUDA_TRY(cudaMemcpy2DAsync(scratch, sizeof(double) * cols, U, sizeof(double) * c1, sizeof(double) * c1, rows,
+                                  cudaMemcpyDeviceToDevice, cx.st));
+  T2S2_CUDA_TRY(cudaMemcpy2DAsync(scratch + c1, sizeof(double) * cols, W2, sizeof(double) * c2, sizeof(double) * c2,
+                                  rows, cudaMemcpyDeviceToDevice, cx.st));
+  return qr_tall(cx, scratch, rows, cols, Q, R);
 }
 
 t2s2_status lq_wide(Ctx& cx, const double* W, int rows, int cols, double* Q, double* Lout) {

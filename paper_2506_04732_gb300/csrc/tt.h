@@ -77,6 +77,10 @@ t2s2_status tt_norm(Ctx& cx, const DevTT& x, double* out);
 // Dense helpers used by the solver.
 // W (rows x cols, rows >= cols) = Q R, Q orthonormal columns (shifted CholeskyQR3).
 t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, double* R);
+// [U | W2] (rows x (c1 + c2), two row-major blocks) = Q R; scratch holds
+// rows x (c1 + c2) for the unfused path.
+t2s2_status qr_tall2(Ctx& cx, const double* U, int c1, const double* W2, int c2, int rows, double* Q, double* R,
+                     double* scratch);
 // W (rows x cols, rows <= cols) = L Q, Q orthonormal rows.
 t2s2_status lq_wide(Ctx& cx, const double* W, int rows, int cols, double* Q, double* L);
 // Smallest r >= 1 with sqrt(sum_{j >= r} s_j^2) <= delta, capped by rmax (> 0).

@@ -107,23 +107,26 @@ __global__ void __launch_bounds__(kDotThreads) tt_dots_kernel(DotArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// <u, u> in double-double arithmetic: every product of binary64 inputs is
+// <u, v> in double-double arithmetic: every product of binary64 inputs is
 // split exactly (p + e = a b through an FMA) and every sum is an error-free
-// two-sum, so the environments carry ~2^-104 relative precision.  For a
-// residual z = b - A x the terms of <z, z> are of the size |b|^2 while the
-// result is |b - A x|^2, many orders smaller; in binary64 the cancellation
-// leaves noise of ~1e-16 |b|^2, in double-double ~1e-28 |b|^2, so the
-// norm of a residual of 1e-12 |b| comes out to about four digits
-// without orthogonalising z.
+// two-sum, so the environments carry ~2^-104 relative precision.  The
+// residual |b - A x|^2 = |b|^2 - 2<b, A x> + |A x|^2 has terms of the size
+// |b|^2 while the result is many orders smaller; in binary64 the cancellation
+// leaves noise of ~1e-16 |b|^2, in double-double ~1e-28 |b|^2, so a residual
+// of 1e-12 |b| comes out to about four digits.  When v is u the environments
+// are symmetric and only their upper triangles are computed.
 
 struct DDArgs {
   int n, d;
   int m[T2S2_MAX_D];
-  int r[kMaxDots][T2S2_MAX_D + 1];
+  int r[kMaxDots][T2S2_MAX_D + 1];   // ranks of u_p
+  int s[kMaxDots][T2S2_MAX_D + 1];   // ranks of v_p
+  int sym[kMaxDots];                 // 1: v_p is u_p (phi symmetric)
   const double* u[kMaxDots][T2S2_MAX_D];
-  double* phh[kMaxDots];  // phi, high and low parts (r_k x r_k)
+  const double* v[kMaxDots][T2S2_MAX_D];
+  double* phh[kMaxDots];  // phi, high and low parts (r_k x s_k)
   double* phl[kMaxDots];
-  double* wh[kMaxDots];   // W, high and low parts (r_k x m_k x r_{k+1})
+  double* wh[kMaxDots];   // W, high and low parts (s_k x m_k x r_{k+1})
   double* wl[kMaxDots];
   double* out;            // n (hi, lo) pairs
 };
@@ -158,6 +161,13 @@ __device__ __forceinline__ void dd_add(double& hi, double& lo, double h2, double
 // spreads over every SM instead of filling the first CTAs.
 __device__ __forceinline__ long spread_item(long slot, int G, int g) { return slot * G + g; }
 
+// number of phi entries computed for product p at bond k+1: the upper
+// triangle when phi is symmetric
+__device__ __forceinline__ long dd_phi_items(const DDArgs& a, int p, int k) {
+  const long r1 = a.r[p][k + 1], s1 = a.s[p][k + 1];
+  return a.sym[p] ? r1 * (r1 + 1) / 2 : r1 * s1;
+}
+
 __global__ void __launch_bounds__(kDotThreads) tt_norm2_dd_kernel(DDArgs a) {
   cg::grid_group grid = cg::this_grid();
   const int G = gridDim.x, g = blockIdx.x;
@@ -165,15 +175,15 @@ __global__ void __launch_bounds__(kDotThreads) tt_norm2_dd_kernel(DDArgs a) {
   for (int k = 0; k < a.d; ++k) {
     const int m = a.m[k];
     long tot = 0;
-    for (int p = 0; p < a.n; ++p) tot += (long)a.r[p][k] * m * a.r[p][k + 1];
+    for (int p = 0; p < a.n; ++p) tot += (long)a.s[p][k] * m * a.r[p][k + 1];
     // W[a', i, b] = sum_a phi[a, a'] U[a, i, b]
     for (long slot = threadIdx.x;; slot += kDotThreads) {
       const long e = spread_item(slot, G, g);
       if (e >= tot) break;
       int p = 0;
       long q = e;
-      while (q >= (long)a.r[p][k] * m * a.r[p][k + 1]) q -= (long)a.r[p][k] * m * a.r[p][k + 1], ++p;
-      const int ra = a.r[p][k], rb = a.r[p][k + 1];
+      while (q >= (long)a.s[p][k] * m * a.r[p][k + 1]) q -= (long)a.s[p][k] * m * a.r[p][k + 1], ++p;
+      const int ra = a.r[p][k], rb = a.r[p][k + 1], sa = a.s[p][k];
       const int b = (int)(q % rb);
       const int ai = (int)(q / rb);
       const int i = ai % m, ap = ai / m;
@@ -185,44 +195,50 @@ __global__ void __launch_bounds__(kDotThreads) tt_norm2_dd_kernel(DDArgs a) {
         const double *ph = a.phh[p], *pl = a.phl[p];
         int x = 0;
         for (; x + 1 < ra; x += 2) {
-          dd_fma(h0, l0, ph[(long)x * ra + ap], pl[(long)x * ra + ap], U[((long)x * m + i) * rb + b]);
-          dd_fma(h1, l1, ph[(long)(x + 1) * ra + ap], pl[(long)(x + 1) * ra + ap],
+          dd_fma(h0, l0, ph[(long)x * sa + ap], pl[(long)x * sa + ap], U[((long)x * m + i) * rb + b]);
+          dd_fma(h1, l1, ph[(long)(x + 1) * sa + ap], pl[(long)(x + 1) * sa + ap],
                  U[((long)(x + 1) * m + i) * rb + b]);
         }
-        if (x < ra) dd_fma(h0, l0, ph[(long)x * ra + ap], pl[(long)x * ra + ap], U[((long)x * m + i) * rb + b]);
+        if (x < ra) dd_fma(h0, l0, ph[(long)x * sa + ap], pl[(long)x * sa + ap], U[((long)x * m + i) * rb + b]);
         dd_add(h0, l0, h1, l1);
       }
       a.wh[p][q] = h0;
       a.wl[p][q] = l0;
     }
     grid.sync();
-    // phi[b, b'] = sum_{a', i} W[a', i, b] U[a', i, b'], b <= b' (phi is
-    // symmetric; both halves are written)
+    // phi[b, b'] = sum_{a', i} W[a', i, b] V[a', i, b'] (upper triangle only
+    // when V is U; both halves are written)
     long tot2 = 0;
-    for (int p = 0; p < a.n; ++p) tot2 += (long)a.r[p][k + 1] * (a.r[p][k + 1] + 1) / 2;
+    for (int p = 0; p < a.n; ++p) tot2 += dd_phi_items(a, p, k);
     for (long slot = warp;; slot += kDotThreads / 32) {
       const long it = spread_item(slot, G, g);
       if (it >= tot2) break;
       int p = 0;
       long q = it;
-      while (q >= (long)a.r[p][k + 1] * (a.r[p][k + 1] + 1) / 2) q -= (long)a.r[p][k + 1] * (a.r[p][k + 1] + 1) / 2, ++p;
-      const int rb = a.r[p][k + 1], ra = a.r[p][k];
-      // q -> (b, b') with b <= b', row-major over the upper triangle
-      int b = (int)((2.0f * rb + 1.0f - sqrtf((2.0f * rb + 1.0f) * (2.0f * rb + 1.0f) - 8.0f * (float)q)) * 0.5f);
-      b = max(0, min(rb - 1, b));
-      while (b > 0 && (long)b * (2 * rb - b + 1) / 2 > q) --b;
-      while ((long)(b + 1) * (2 * rb - b) / 2 <= q) ++b;
-      const int bp = b + (int)(q - (long)b * (2 * rb - b + 1) / 2);
+      while (q >= dd_phi_items(a, p, k)) q -= dd_phi_items(a, p, k), ++p;
+      const int rb = a.r[p][k + 1], sb = a.s[p][k + 1], sa = a.s[p][k];
+      int b, bp;
+      if (a.sym[p]) {
+        // q -> (b, b') with b <= b', row-major over the upper triangle
+        b = (int)((2.0f * rb + 1.0f - sqrtf((2.0f * rb + 1.0f) * (2.0f * rb + 1.0f) - 8.0f * (float)q)) * 0.5f);
+        b = max(0, min(rb - 1, b));
+        while (b > 0 && (long)b * (2 * rb - b + 1) / 2 > q) --b;
+        while ((long)(b + 1) * (2 * rb - b) / 2 <= q) ++b;
+        bp = b + (int)(q - (long)b * (2 * rb - b + 1) / 2);
+      } else {
+        b = (int)(q / sb);
+        bp = (int)(q % sb);
+      }
       const double *Wh = a.wh[p], *Wl = a.wl[p];
-      const double* U = a.u[p][k];
-      const int K = ra * m;
+      const double* V = a.v[p][k];
+      const int K = sa * m;
       double h0 = 0.0, l0 = 0.0, h1 = 0.0, l1 = 0.0;
       int x = lane;
       for (; x + 32 < K; x += 64) {
-        dd_fma(h0, l0, Wh[(long)x * rb + b], Wl[(long)x * rb + b], U[(long)x * rb + bp]);
-        dd_fma(h1, l1, Wh[(long)(x + 32) * rb + b], Wl[(long)(x + 32) * rb + b], U[(long)(x + 32) * rb + bp]);
+        dd_fma(h0, l0, Wh[(long)x * rb + b], Wl[(long)x * rb + b], V[(long)x * sb + bp]);
+        dd_fma(h1, l1, Wh[(long)(x + 32) * rb + b], Wl[(long)(x + 32) * rb + b], V[(long)(x + 32) * sb + bp]);
       }
-      if (x < K) dd_fma(h0, l0, Wh[(long)x * rb + b], Wl[(long)x * rb + b], U[(long)x * rb + bp]);
+      if (x < K) dd_fma(h0, l0, Wh[(long)x * rb + b], Wl[(long)x * rb + b], V[(long)x * sb + bp]);
       dd_add(h0, l0, h1, l1);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -232,10 +248,12 @@ __global__ void __launch_bounds__(kDotThreads) tt_norm2_dd_kernel(DDArgs a) {
       if (lane == 0) {
         double sh, se;
         two_sum(h0, l0, sh, se);  // renormalise
-        a.phh[p][(long)b * rb + bp] = sh;
-        a.phl[p][(long)b * rb + bp] = se;
-        a.phh[p][(long)bp * rb + b] = sh;
-        a.phl[p][(long)bp * rb + b] = se;
+        a.phh[p][(long)b * sb + bp] = sh;
+        a.phl[p][(long)b * sb + bp] = se;
+        if (a.sym[p]) {
+          a.phh[p][(long)bp * sb + b] = sh;
+          a.phl[p][(long)bp * sb + b] = se;
+        }
       }
     }
     grid.sync();
@@ -248,7 +266,7 @@ __global__ void __launch_bounds__(kDotThreads) tt_norm2_dd_kernel(DDArgs a) {
 
 }  // namespace
 
-t2s2_status tt_norm2_dd(Ctx& cx, int n, const DevTT* const* u, double* hi, double* lo) {
+t2s2_status tt_dots_dd(Ctx& cx, int n, const DevTT* const* u, const DevTT* const* v, double* hi, double* lo) {
   if (n < 1 || n > kMaxDots) return T2S2_EINVAL;
   const int d = u[0]->d;
   DDArgs a;
@@ -258,16 +276,21 @@ t2s2_status tt_norm2_dd(Ctx& cx, int n, const DevTT* const* u, double* hi, doubl
   size_t mark = cx.ar->mark();
   double fl = 0.0;
   for (int p = 0; p < n; ++p) {
-    if (u[p]->d != d) return T2S2_EINVAL;
+    if (u[p]->d != d || v[p]->d != d) return T2S2_EINVAL;
+    a.sym[p] = (u[p] == v[p]) ? 1 : 0;
     size_t phi_n = 1, w_n = 1;
     for (int k = 0; k < d; ++k) {
-      if (u[p]->m[k] != a.m[k]) return T2S2_EINVAL;
+      if (u[p]->m[k] != a.m[k] || v[p]->m[k] != a.m[k]) return T2S2_EINVAL;
       a.u[p][k] = u[p]->c[k];
-      phi_n = std::max(phi_n, (size_t)u[p]->r[k + 1] * u[p]->r[k + 1]);
-      w_n = std::max(w_n, (size_t)u[p]->r[k] * a.m[k] * u[p]->r[k + 1]);
-      fl += 2.0 * u[p]->r[k] * a.m[k] * (double)u[p]->r[k + 1] * (u[p]->r[k] + u[p]->r[k + 1]);
+      a.v[p][k] = v[p]->c[k];
+      phi_n = std::max(phi_n, (size_t)u[p]->r[k + 1] * v[p]->r[k + 1]);
+      w_n = std::max(w_n, (size_t)v[p]->r[k] * a.m[k] * u[p]->r[k + 1]);
+      fl += 2.0 * v[p]->r[k] * a.m[k] * (double)u[p]->r[k + 1] * (u[p]->r[k] + v[p]->r[k + 1]);
     }
-    for (int k = 0; k <= d; ++k) a.r[p][k] = u[p]->r[k];
+    for (int k = 0; k <= d; ++k) {
+      a.r[p][k] = u[p]->r[k];
+      a.s[p][k] = v[p]->r[k];
+    }
     a.phh[p] = aget<double>(cx, phi_n);
     a.phl[p] = aget<double>(cx, phi_n);
     a.wh[p] = aget<double>(cx, w_n);
@@ -348,6 +371,8 @@ t2s2_status tt_dots(Ctx& cx, int n, const DevTT* const* u, const DevTT* const* v
   long cap = (long)std::max(1, per_sm) * sms;
   cap = std::min<long>(cap, sms);
   if (cx.coop_ctas > 0) cap = std::min<long>(cap, cx.coop_ctas);
+  // sized by the work (one item per thread, one phi entry per warp): every
+  // grid barrier costs more with more CTAs
   const long want = std::max((st1 + kDotThreads - 1) / kDotThreads, (32 * st2 + kDotThreads - 1) / kDotThreads);
   const int G = (int)std::max(1L, std::min(cap, want));
   {
