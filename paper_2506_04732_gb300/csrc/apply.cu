@@ -21,6 +21,9 @@ namespace t2s2 {
 
 namespace {
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+// small trains: 16 x 16 tiles, one output per thread, so that the few
+// tiles of a small problem still spread over the SMs
+constexpr int BMS = 16, BNS = 16;
 
 struct ParamWork {
   ApplyBatch p;
@@ -51,26 +54,27 @@ __device__ __forceinline__ int find_core(const Work& w, int tile) {
 // Persistent over tiles: CTA b takes tiles b, b + gridDim.x, ...  A tile is
 // 64 rows of [S; G] by 64 (a, b) pairs of the core (column g = a rb + b), so
 // small right ranks waste no columns.
-template <class Work>
+template <class Work, int TBM, int TBN>
 __global__ void __launch_bounds__(NT) apply_kernel(Work w, int total) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  constexpr int TM = TBM / 16, TN = TBN / 16;
+  __shared__ double As[BK][TBM + 1];
+  __shared__ double Bs[BK][TBN + 1];
   for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
     const int ci = find_core(w, tile);
     const ApplyCore c = w.core(ci);
     const int local = tile - w.first(ci);
     const long npairs = (long)c.ra * c.rb;
-    const int nt = (int)((npairs + BN - 1) / BN);
-    const int m0 = (local / nt) * BM;
-    const long n0 = (long)(local % nt) * BN;
+    const int nt = (int)((npairs + TBN - 1) / TBN);
+    const int m0 = (local / nt) * TBM;
+    const long n0 = (long)(local % nt) * TBN;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    double acc[4][4];
+    double acc[TM][TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
     for (int k0 = 0; k0 < c.m; k0 += BK) {
-      for (int e = threadIdx.x; e < BM * BK; e += NT) {
+      for (int e = threadIdx.x; e < TBM * BK; e += NT) {
         int kk = e % BK, mm = e / BK;
         int row = m0 + mm, col = k0 + kk;
         double v = 0.0;
@@ -85,8 +89,8 @@ __global__ void __launch_bounds__(NT) apply_kernel(Work w, int total) {
         }
         As[kk][mm] = v;
       }
-      for (int e = threadIdx.x; e < BN * BK; e += NT) {
-        const int nn = e % BN, kk = e / BN;
+      for (int e = threadIdx.x; e < TBN * BK; e += NT) {
+        const int nn = e % TBN, kk = e / TBN;
         const long g = n0 + nn;
         const int j = k0 + kk;
         double v = 0.0;
@@ -99,27 +103,27 @@ __global__ void __launch_bounds__(NT) apply_kernel(Work w, int total) {
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        double av[4], bv[4];
+        double av[TM], bv[TN];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+        for (int i = 0; i < TM; ++i) av[i] = As[kk][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+        for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
       }
       __syncthreads();
     }
     // scatter into the block pattern of Y
     const int ra = c.ra, rb = c.rb, m = c.m;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const long g = n0 + tx + 16 * j;
       if (g >= npairs) continue;
       const long a = g / rb, b = g % rb;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < TM; ++i) {
         const int row = m0 + ty + 16 * i;
         if (row >= 2 * m) continue;
         const bool gpart = row >= m;
@@ -165,15 +169,24 @@ t2s2_status apply_fp64(const ApplyBatch& p, cudaStream_t st) {
   int total = 0;
   double fl = 0.0, by = 0.0;
   for (int k = 0; k < p.ncores; ++k) {
+    total += apply_fp64_tiles(p.c[k]);
+    apply_work_totals(p.c[k], &fl, &by);
+  }
+  if (total == 0) return T2S2_OK;
+  // fewer 64 x 64 tiles than SMs: take 16 x 16 tiles instead (a 64 x 64
+  // tile of K = m costs its SM 64 x 64 x m / 2 cycles of binary64 issue)
+  const bool small = total < kNumSMs;
+  const int tbm = small ? BMS : BM, tbn = small ? BNS : BN;
+  total = 0;
+  for (int k = 0; k < p.ncores; ++k) {
     w.start[k] = total;
     const ApplyCore& c = p.c[k];
-    total += apply_fp64_tiles(c);
-    apply_work_totals(c, &fl, &by);
+    total += cdiv(2 * c.m, tbm) * cdiv((long)c.ra * c.rb, tbn);
   }
   w.start[p.ncores] = total;
-  if (total == 0) return T2S2_OK;
   TraceScope ts(kTrApply, st, fl, by);
-  apply_kernel<ParamWork><<<total, NT, 0, st>>>(w, total);
+  if (small) apply_kernel<ParamWork, BMS, BNS><<<total, NT, 0, st>>>(w, total);
+  else apply_kernel<ParamWork, BM, BN><<<total, NT, 0, st>>>(w, total);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
@@ -184,7 +197,7 @@ t2s2_status apply_fp64_grouped(const ApplyCore* dcores, const int* dstart, int n
   if (total == 0) return T2S2_OK;
   GlobalWork w{dcores, dstart, ncores};
   TraceScope ts(kTrApply, st, flops, bytes);
-  apply_kernel<GlobalWork><<<std::min(grid, total), NT, 0, st>>>(w, total);
+  apply_kernel<GlobalWork, BM, BN><<<std::min(grid, total), NT, 0, st>>>(w, total);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }

@@ -722,10 +722,9 @@ struct Amen {
       }
       ph(6);
       {
+        // the orthonormal factor goes straight into z's core k (same shape)
         double* Rz = tmp[1];
-        double* Qz = tmp[0];
-        T2S2_TRY(qr_tall(c, zres, za * m, zb, Qz, Rz));
-        T2S2_TRY(d2d(c, z.c[k], Qz, (size_t)za * m * zb));
+        T2S2_TRY(qr_tall(c, zres, za * m, zb, z.c[k], Rz));
       }
       ph(7);
       // --- new core: orthonormal basis of [U | res], written over core k

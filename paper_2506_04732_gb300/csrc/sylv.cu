@@ -28,7 +28,7 @@ namespace t2s2 {
 
 namespace {
 
-constexpr int kSylvThreads = 256;
+constexpr int kSylvThreads = 512;
 constexpr int kSylvMaxRa = 32;
 constexpr int kSylvMaxSteps = 6;
 constexpr int kSylvBlock = 8;  // columns of the backward substitution per serial block
