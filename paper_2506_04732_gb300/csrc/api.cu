@@ -446,6 +446,9 @@ t2s2_status t2s2_op_destroy(t2s2_op op) {
   if (op->dstat) cudaFree(op->dstat);
   if (op->gcnt) cudaFree(op->gcnt);
   if (op->zcache) cudaFree(op->zcache);
+  if (op->ev_fork) cudaEventDestroy(op->ev_fork);
+  if (op->ev_join) cudaEventDestroy(op->ev_join);
+  if (op->side) cudaStreamDestroy(op->side);
   op->free_solver_buffers();
   delete op;
   return T2S2_OK;

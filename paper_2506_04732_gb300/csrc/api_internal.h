@@ -31,6 +31,10 @@ struct t2s2_op_s {
   double* hbuf = nullptr;  // pinned host scratch
   int* dstat = nullptr;    // device status words
   int* gcnt = nullptr;     // kGemmCounters split-K tile counters (zero between launches)
+  // a second stream for work that overlaps the main one, with its fork and
+  // join events (created on first use)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // the solver's right-orthogonalised random start of z for one kick
   double* zcache = nullptr;
   size_t zcache_elems = 0;

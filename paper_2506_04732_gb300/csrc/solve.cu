@@ -271,6 +271,24 @@ struct Amen {
     ++npending;
     return T2S2_OK;
   }
+  // the operator's side stream (created on first use; false if that fails)
+  bool side_ready() {
+    if (op->side && op->ev_fork && op->ev_join) return true;
+    if (!op->side && cudaStreamCreateWithFlags(&op->side, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      op->side = nullptr;
+      return false;
+    }
+    if (!op->ev_fork && cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (!op->ev_join && cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  }
   t2s2_status collect_iters() {
     if (npending == 0) return T2S2_OK;
     T2S2_CUDA_TRY(cudaStreamSynchronize(cx->st));
@@ -721,10 +739,22 @@ struct Amen {
         T2S2_TRY(group(c, s4));
       }
       ph(6);
+      // the orthonormal factor goes straight into z's core k (same shape); on
+      // the operator's side stream it overlaps the new core's QR below and
+      // joins before the left interfaces read z's core k
+      const size_t zmark = c.ar->mark();
+      bool zside = false;
       {
-        // the orthonormal factor goes straight into z's core k (same shape)
-        double* Rz = tmp[1];
-        T2S2_TRY(qr_tall(c, zres, za * m, zb, z.c[k], Rz));
+        double* Rz = tmp[3];
+        t2s2_status zs = T2S2_OK;
+        if (side_ready()) {
+          T2S2_CUDA_TRY(cudaEventRecord(op->ev_fork, c.st));
+          T2S2_CUDA_TRY(cudaStreamWaitEvent(op->side, op->ev_fork, 0));
+          zside = qr_tall_async(c, zres, za * m, zb, z.c[k], Rz, op->side, &zs);
+          T2S2_TRY(zs);
+          if (zside) T2S2_CUDA_TRY(cudaEventRecord(op->ev_join, op->side));
+        }
+        if (!zside) T2S2_TRY(qr_tall(c, zres, za * m, zb, z.c[k], Rz));
       }
       ph(7);
       // --- new core: orthonormal basis of [U | res], written over core k
@@ -735,7 +765,7 @@ struct Amen {
       if ((size_t)rn * mn * rnn > x.cap[k + 1] || (size_t)rows * rn > x.cap[k]) return T2S2_ENOMEM;
       double* Q = x.c[k];
       if (rows >= cols) {
-        double* Rq = tmp[8];
+        double* Rq = tmp[5];  // tmp[8] holds zres, which the side stream may still read
         T2S2_TRY(qr_tall2(c, U, rk, res, zb, rows, Q, Rq, tmp[1]));
       } else {
         T2S2_TRY(dev_identity(c, Q, rows));
@@ -763,6 +793,8 @@ struct Amen {
         x.r[k + 1] = rn;
       }
       ph(8);
+      if (zside) T2S2_CUDA_TRY(cudaStreamWaitEvent(c.st, op->ev_join, 0));
+      c.ar->release(zmark);
       // --- left interfaces for bond k+1:
       //   PL' = Qc^T (PL Qc + B' Qc),  FL' = Qc^T (FL F),  ZIL' = Z^T (ZIL Qc),
       //   ZBL' = Z^T (ZBL Qc + ZIL B' Qc),  ZFL' = Z^T (ZFL F)

@@ -193,6 +193,20 @@ static bool qr_fused(Ctx& cx, const double* W, int nlong, int c, bool tall, doub
   return true;
 }
 
+bool qr_tall_async(Ctx& cx, const double* W, int rows, int cols, double* Q, double* R, cudaStream_t side,
+                   t2s2_status* st) {
+  int grid = 0, per = 0;
+  size_t smem = 0;
+  if (cols < 1 || cols > kSmallMax || rows < cols) return false;
+  if (!cholqr3_plan(rows, cols, cx.coop_ctas, &grid, &per, &smem)) return false;
+  // held (not released) until the caller joins the side stream
+  double* scratch = aget<double>(cx, cholqr3_scratch_doubles(rows, cols, grid));
+  if (!scratch) return false;
+  const double shift = 11.0 * ((double)rows * cols + (double)cols * (cols + 1)) * kUnit;
+  *st = cholqr3_fused(W, Q, R, rows, cols, true, shift, scratch, cx.dstat, grid, per, smem, side);
+  return true;
+}
+
 t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, double* R) {
   if (cols > kSmallMax || rows < cols || cols <= 0) return T2S2_EINVAL;
   {

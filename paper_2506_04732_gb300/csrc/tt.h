@@ -77,6 +77,11 @@ t2s2_status tt_norm(Ctx& cx, const DevTT& x, double* out);
 // Dense helpers used by the solver.
 // W (rows x cols, rows >= cols) = Q R, Q orthonormal columns (shifted CholeskyQR3).
 t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, double* R);
+// The fused CholeskyQR of a tall block on stream `side` (false, with nothing
+// queued, if it does not fit).  Its scratch comes from the arena and stays
+// allocated: release the arena mark only after joining `side`.
+bool qr_tall_async(Ctx& cx, const double* W, int rows, int cols, double* Q, double* R, cudaStream_t side,
+                   t2s2_status* st);
 // [U | W2] (rows x (c1 + c2), two row-major blocks) = Q R; scratch holds
 // rows x (c1 + c2) for the unfused path.
 t2s2_status qr_tall2(Ctx& cx, const double* U, int c1, const double* W2, int c2, int rows, double* Q, double* R,
