@@ -57,6 +57,86 @@ __device__ __forceinline__ cf cinv(cf a) {
   return cmk(a.x * d, -a.y * d);
 }
 
+// Gauss-Jordan inverses (partial pivoting) of A_i = P_L + (Ts_ii + pi) I for
+// i < m, 32 / W matrices per warp, each on W lanes: lane = row (lane =
+// column for the pivot-row steps); segment-local maxima by shuffles within
+// the W lanes.  A vanishing pivot sets *fail.
+template <int W>
+__device__ void sylv_invert(cf* Inv, const cf* Ts, const double* PL, double pi, int ra, int la, int lm, int m,
+                            cf* prow_w, int warp, int nwarps, int lane, int* fail) {
+  constexpr int S = 32 / W;
+  const int seg = lane / W, sl = lane % W;
+  cf* pr = prow_w + seg * W;
+  for (int i0 = warp * S; i0 < m; i0 += nwarps * S) {
+    const int i = i0 + seg;
+    const bool act = i < m;
+    cf* A = Inv + (size_t)(act ? i : 0) * ra * la;
+    float amax = 0.f;
+    if (act) {
+      const cf s = cadd(Ts[i * lm + i], cmk((float)pi, 0.f));
+      for (int e = sl; e < ra * ra; e += W) {
+        const int p = e / ra, q = e % ra;
+        const cf v = cadd(cmk((float)PL[e], 0.f), p == q ? s : cmk(0.f, 0.f));
+        A[p * la + q] = v;
+        amax = fmaxf(amax, cabs2(v));
+      }
+    }
+    for (int o = W / 2; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    __syncwarp();
+    int perm[kSylvMaxRa];
+    bool bad = false;
+    for (int p = 0; p < ra; ++p) {
+      // pivot: largest |a_qp| over q >= p, ties to the smallest q
+      // (non-negative binary32 values order like their bit patterns)
+      const bool cand = act && sl >= p && sl < ra;
+      const unsigned mine = cand ? __float_as_uint(cabs2(A[sl * la + p])) : 0u;
+      unsigned top = mine;
+      for (int o = W / 2; o > 0; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+      const unsigned who = __ballot_sync(0xffffffffu, cand && mine == top);
+      unsigned segbits = who;
+      if constexpr (W < 32) segbits = (who >> (seg * W)) & ((1u << W) - 1u);
+      const int arg = segbits ? __ffs(segbits) - 1 : p;
+      perm[p] = arg;
+      if (act && !(__uint_as_float(top) > 1e-24f * amax)) bad = true;
+      // row arg -> pivot row (scaled by 1 / pivot, the pivot slot set to 1),
+      // row p -> row arg
+      if (act && sl < ra) {
+        const cf piv = A[arg * la + p];
+        const cf ip = bad ? cmk(0.f, 0.f) : cinv(piv);
+        const cf vp = A[arg * la + sl], vq = A[p * la + sl];
+        pr[sl] = cmul(sl == p ? cmk(1.f, 0.f) : vp, ip);
+        if (arg != p) A[arg * la + sl] = vq;
+      }
+      __syncwarp();
+      if (act && sl < ra) {
+        cf* __restrict__ row = A + sl * la;
+        const cf* __restrict__ prr = pr;
+        if (sl == p) {
+          for (int c = 0; c < ra; ++c) row[c] = prr[c];
+        } else {
+          const cf f = row[p];
+          for (int c = 0; c < ra; ++c) {
+            const cf base = (c == p) ? cmk(0.f, 0.f) : row[c];
+            row[c] = csub(base, cmul(f, prr[c]));
+          }
+        }
+      }
+      __syncwarp();
+    }
+    // undo the row swaps as column swaps, last first
+    for (int p = ra - 1; p >= 0; --p) {
+      const int q = perm[p];
+      if (act && q != p && sl < ra) {
+        const cf u = A[sl * la + p];
+        A[sl * la + p] = A[sl * la + q];
+        A[sl * la + q] = u;
+      }
+      __syncwarp();
+    }
+    if (act && bad && sl == 0) *fail = 1;
+  }
+}
+
 __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ra = P.ra, m = P.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -95,69 +175,12 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
   if (t == 0) fail = 0;
   __syncthreads();
   stamp();
-  // inverses of A_i = P_L + (Ts_ii + pi) I by Gauss-Jordan, one warp each;
-  // lane = row (lane = column for the pivot-row steps)
-  cf* pr = prow + warp * kSylvMaxRa;
-  for (int i = warp; i < m; i += kSylvThreads / 32) {
-    cf* A = Inv + (size_t)i * ra * la;
-    const cf s = cadd(Ts[i * lm + i], cmk((float)pi, 0.f));
-    float amax = 0.f;
-    for (int e = lane; e < ra * ra; e += 32) {
-      const int p = e / ra, q = e % ra;
-      const cf v = cadd(cmk((float)PL[e], 0.f), p == q ? s : cmk(0.f, 0.f));
-      A[p * la + q] = v;
-      amax = fmaxf(amax, cabs2(v));
-    }
-    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    __syncwarp();
-    int perm[kSylvMaxRa];
-    bool bad = false;
-    for (int p = 0; p < ra; ++p) {
-      // pivot: largest |a_qp| over q >= p, ties to the smallest q
-      // (non-negative binary32 values order like their bit patterns)
-      const unsigned mine = (lane >= p && lane < ra) ? __float_as_uint(cabs2(A[lane * la + p])) : 0u;
-      const unsigned top = __reduce_max_sync(0xffffffffu, mine);
-      const unsigned who = __ballot_sync(0xffffffffu, lane >= p && lane < ra && mine == top);
-      const int arg = __ffs(who) - 1;
-      perm[p] = arg;
-      if (!(__uint_as_float(top) > 1e-24f * amax)) bad = true;
-      // row arg -> pivot row (scaled by 1 / pivot, the pivot slot set to 1),
-      // row p -> row arg
-      const cf piv = A[arg * la + p];
-      const cf ip = bad ? cmk(0.f, 0.f) : cinv(piv);
-      if (lane < ra) {
-        const cf vp = A[arg * la + lane], vq = A[p * la + lane];
-        pr[lane] = cmul(lane == p ? cmk(1.f, 0.f) : vp, ip);
-        if (arg != p) A[arg * la + lane] = vq;
-      }
-      __syncwarp();
-      if (lane < ra) {
-        cf* __restrict__ row = A + lane * la;
-        const cf* __restrict__ prr = pr;
-        if (lane == p) {
-          for (int c = 0; c < ra; ++c) row[c] = prr[c];
-        } else {
-          const cf f = row[p];
-          for (int c = 0; c < ra; ++c) {
-            const cf base = (c == p) ? cmk(0.f, 0.f) : row[c];
-            row[c] = csub(base, cmul(f, prr[c]));
-          }
-        }
-      }
-      __syncwarp();
-    }
-    // undo the row swaps as column swaps, last first
-    for (int p = ra - 1; p >= 0; --p) {
-      const int q = perm[p];
-      if (q != p && lane < ra) {
-        const cf u = A[lane * la + p];
-        A[lane * la + p] = A[lane * la + q];
-        A[lane * la + q] = u;
-      }
-      __syncwarp();
-    }
-    if (bad && lane == 0) fail = 1;
-  }
+  // inverses of A_i = P_L + (Ts_ii + pi) I by Gauss-Jordan: two matrices per
+  // warp (16-lane halves) when ra <= 16, else one
+  if (ra <= 16)
+    sylv_invert<16>(Inv, Ts, PL, pi, ra, la, lm, m, prow + warp * kSylvMaxRa, warp, kSylvThreads / 32, lane, &fail);
+  else
+    sylv_invert<32>(Inv, Ts, PL, pi, ra, la, lm, m, prow + warp * kSylvMaxRa, warp, kSylvThreads / 32, lane, &fail);
   __syncthreads();
   stamp();
   int status = fail ? 1 : 0;
