@@ -35,7 +35,9 @@ FAMILIES = ["gemm", "apply", "local_solve", "small_factor", "elementwise", "appl
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 200 for the headline solve, whose timed region then spans "
+                         "several clock samples; 5 for the other workloads and the reference arm)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"])
@@ -72,17 +74,25 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.skip = 0
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
             self.proc = None
+            return
+        # the timed region starts once the sampler is live; the sample taken
+        # before it is dropped
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.skip = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -91,6 +101,13 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        inside = len(self.lines) - self.skip
+        if inside <= 0:
+            # a region shorter than the interval: take the next sample, which
+            # the nvidia-smi loop writes within about 100 ms of its end
+            t0 = time.time()
+            while len(self.lines) <= self.skip and time.time() - t0 < 1.0 and self.proc.poll() is None:
+                time.sleep(0.005)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -98,7 +115,7 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.skip:]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -113,7 +130,7 @@ class ClockSampler:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2] if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_in_region": max(0, inside)}
 
 
 def peaks():
@@ -192,6 +209,11 @@ def cpu_baseline_sample(problem_expr, budget_s):
     return (last["t"] if conv else max(last["t"], time.perf_counter() - t0)), last["sweeps"], conv, last["res"]
 
 
+REF_STEP_FLOOR_S = 60.0   # per timed reference step, when the run stays bounded
+REF_TOTAL_S = 330.0       # bound on the timed reference steps together
+REF_WARMUP_S = 1.0        # per untimed reference step
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -200,8 +222,14 @@ def run_reference(args):
     p = W.config1()
     times = []
     info = None
+    # A fresh oracle process per step has nothing to warm up, so warm-up steps
+    # get a short sample.  A timed step is given a minute (the oracle's first
+    # sweep takes about 20 s on 16 Arm cores) while the timed steps together
+    # stay within about five and a half minutes.
+    step_budget = max(args.cpu_budget / max(1, args.steps), min(REF_STEP_FLOOR_S, REF_TOTAL_S / max(1, args.steps)))
     for i in range(args.warmup + args.steps):
-        dt, sweeps, conv, res = cpu_baseline_sample("config1()", args.cpu_budget / max(1, args.steps))
+        budget = step_budget if i >= args.warmup else min(step_budget, REF_WARMUP_S)
+        dt, sweeps, conv, res = cpu_baseline_sample("config1()", budget)
         if i >= args.warmup:
             times.append((dt, sweeps, conv, res))
         info = (dt, sweeps, conv, res)
@@ -217,8 +245,8 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": p.name, "d": p.d, "n": p.n[0], "tol": p.tol,
                                              "rmax": p.rmax},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"oracle AMEn sweeps within {args.cpu_budget / max(1, args.steps):.0f} s "
-                                       f"per step, scaled by {need} sweeps per solve"},
+                             "sample": f"oracle AMEn sweeps within {step_budget:.0f} s per step, "
+                                       f"scaled by {need} sweeps per solve"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -480,6 +508,8 @@ def measure_precisions(T, P, W, torch, op, b, x_ref, steps=3):
 
 def main():
     args = parse()
+    if args.steps is None:
+        args.steps = 200 if args.impl == "ours" and args.workload == "steady" else 5
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "steady":

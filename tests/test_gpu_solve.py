@@ -79,6 +79,30 @@ def test_solve_d5_residual_checked_by_oracle(T):
     assert OT.diff_norm(x.cores(), us) <= 1e-5 * OT.norm(us)
 
 
+def test_solve_from_random_high_rank_guess(T):
+    # a random rank-20 initial guess: the last core's local solves (right rank
+    # 1) then see left ranks of 17 and more, beyond the 16-lane Gauss-Jordan
+    # halves of the rank-1-right solver, while the first cores go through GMRES
+    p = W.config1(d=4, n=24, ratio=1e-2, rmax=24, tol=1e-9)
+    from paper_2506_04732_gb300 import problem as P
+    op = P.build_operator(p)
+    b = T.TT.from_cores(P.source_cores(p, op))
+    m = [n - 2 for n in p.n]
+    rng = np.random.default_rng(2506)
+    r = [1, 20, 20, 20, 1]
+    x0 = [rng.standard_normal((r[k], m[k], r[k + 1])) / np.sqrt(r[k] * m[k]) for k in range(p.d)]
+    x = T.TT.from_cores(x0, rcap=p.rmax + T.RANK_KICK)
+    info = T.t2s2_solve(op, b, x, p.tol, p.rmax, 30)
+    assert info.status == 0 and info.residual <= p.tol
+    ops = O.build(p)
+    ob = O.source_tt(p, ops)
+    r_or = OS.residual(O.ttm_cores(ops), ob, x.cores())
+    assert r_or <= p.tol * 1.01
+    assert abs(r_or - info.residual) <= 1e-3 * p.tol + 1e-6 * info.residual
+    us = O.solution_tt(p, ops)
+    assert OT.diff_norm(x.cores(), us) <= 1e-5 * OT.norm(us)
+
+
 def test_solve_matches_oracle_amen(T):
     # two different iterates of the same solver family: both reach tol in the
     # oracle's residual, and they differ by at most a condition-style factor
