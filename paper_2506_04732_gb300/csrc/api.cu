@@ -2,6 +2,7 @@
 // rounding, norms and residuals.  The solver entry points live in solve.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -19,6 +20,14 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
   std::lock_guard<std::mutex> lk(g_last_error_mu);
   snprintf(g_last_error, sizeof(g_last_error), "%s at %s:%d: %s", cudaGetErrorString(e), file, line,
            what);
+}
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("T2S2_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
 }
 
 t2s2_status ensure_arena(t2s2_op op, size_t bytes) {

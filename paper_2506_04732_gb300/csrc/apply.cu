@@ -56,6 +56,8 @@ __device__ __forceinline__ int find_core(const Work& w, int tile) {
 // small right ranks waste no columns.
 template <class Work, int TBM, int TBN>
 __global__ void __launch_bounds__(NT) apply_kernel(Work w, int total) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int TM = TBM / 16, TN = TBN / 16;
   __shared__ double As[BK][TBM + 1];
   __shared__ double Bs[BK][TBN + 1];
@@ -185,8 +187,8 @@ t2s2_status apply_fp64(const ApplyBatch& p, cudaStream_t st) {
   }
   w.start[p.ncores] = total;
   TraceScope ts(kTrApply, st, fl, by);
-  if (small) apply_kernel<ParamWork, BMS, BNS><<<total, NT, 0, st>>>(w, total);
-  else apply_kernel<ParamWork, BM, BN><<<total, NT, 0, st>>>(w, total);
+  if (small) (void)launch_pdl(apply_kernel<ParamWork, BMS, BNS>, total, NT, 0, st, w, total);
+  else (void)launch_pdl(apply_kernel<ParamWork, BM, BN>, total, NT, 0, st, w, total);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
@@ -197,7 +199,7 @@ t2s2_status apply_fp64_grouped(const ApplyCore* dcores, const int* dstart, int n
   if (total == 0) return T2S2_OK;
   GlobalWork w{dcores, dstart, ncores};
   TraceScope ts(kTrApply, st, flops, bytes);
-  apply_kernel<GlobalWork, BM, BN><<<std::min(grid, total), NT, 0, st>>>(w, total);
+  (void)launch_pdl(apply_kernel<GlobalWork, BM, BN>, std::min(grid, total), NT, 0, st, w, total);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }

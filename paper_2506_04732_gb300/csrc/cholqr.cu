@@ -95,6 +95,7 @@ __device__ __forceinline__ double pivot_rcp(double v, float f) {
 }
 
 __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
+  pdl_trigger();
   cg::grid_group grid = cg::this_grid();
   extern __shared__ double sm[];
   const int c = a.c, T = tri_count(c);

@@ -24,6 +24,8 @@ constexpr int BK = 16, NT = 256;
 // Tile of (16*TM) x (16*TN) outputs; 16 x 16 threads, each a TM x TN micro-tile.
 template <typename T, int TM, int TN>
 __global__ void __launch_bounds__(NT) gemm_kernel(Gemm<T> g, int splits, int kchunk, T* ws) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int BM = 16 * TM, BN = 16 * TN;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
@@ -106,6 +108,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(Gemm<T> g, int splits, int kch
 
 template <typename T>
 __global__ void splitk_reduce(Gemm<T> g, int splits, const T* ws) {
+  pdl_wait();
+  pdl_trigger();
   long total = (long)g.batch * g.M * g.N;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
@@ -226,6 +230,8 @@ __device__ __forceinline__ void small_tile(const Gemm<double>& g, int splits, in
 template <int BM, int BN>
 __global__ void __launch_bounds__(SNT) small_kernel(Gemm<double> g, int splits, int kchunk, double* ws,
                                                     int* cnt) {
+  pdl_wait();
+  pdl_trigger();
   small_tile<BM, BN>(g, splits, kchunk, ws, cnt, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.y, gridDim.x);
 }
 
@@ -244,6 +250,8 @@ struct GroupArgs {
 
 template <int BM, int BN>
 __global__ void __launch_bounds__(SNT) small_group_kernel(GroupArgs a) {
+  pdl_wait();
+  pdl_trigger();
   const long bid = blockIdx.x;
   int i = 0;
   while (i + 1 < a.n && bid >= a.start[i + 1]) ++i;
@@ -359,7 +367,7 @@ void launch_small(const Gemm<double>& g, const SmallPlan& p, double* ws, int* cn
   dim3 grid(cdiv(g.N, p.bn), cdiv(g.M, p.bm), g.batch * p.splits);
   const int kc = std::max(p.kc, 1);
 #define T2S2_SMALL(a, b) \
-  if (p.bm == a && p.bn == b) { small_kernel<a, b><<<grid, SNT, 0, st>>>(g, p.splits, kc, ws, cnt); return; }
+  if (p.bm == a && p.bn == b) { (void)launch_pdl(small_kernel<a, b>, grid, SNT, 0, st, g, p.splits, kc, ws, cnt); return; }
   T2S2_SMALL(16, 16) T2S2_SMALL(8, 16) T2S2_SMALL(16, 8) T2S2_SMALL(8, 8) T2S2_SMALL(4, 16)
   T2S2_SMALL(16, 4) T2S2_SMALL(1, 64) T2S2_SMALL(64, 1) T2S2_SMALL(4, 4)
 #undef T2S2_SMALL
@@ -368,7 +376,7 @@ void launch_small(const Gemm<double>& g, const SmallPlan& p, double* ws, int* cn
 void launch_group(const GroupArgs& a, int bm, int bn, cudaStream_t st) {
   const long ctas = a.start[a.n];
 #define T2S2_GROUP(x, y) \
-  if (bm == x && bn == y) { small_group_kernel<x, y><<<(unsigned)ctas, SNT, 0, st>>>(a); return; }
+  if (bm == x && bn == y) { (void)launch_pdl(small_group_kernel<x, y>, (unsigned)ctas, SNT, 0, st, a); return; }
   T2S2_GROUP(16, 16) T2S2_GROUP(8, 16) T2S2_GROUP(16, 8) T2S2_GROUP(8, 8) T2S2_GROUP(4, 16)
   T2S2_GROUP(16, 4) T2S2_GROUP(1, 64) T2S2_GROUP(64, 1) T2S2_GROUP(4, 4)
 #undef T2S2_GROUP
@@ -406,7 +414,7 @@ GroupPlan plan_group(const Gemm<double>* gs, int n) {
 template <typename T, int TM, int TN>
 void launch_tile(const Gemm<T>& g, int splits, int kc, T* ws, cudaStream_t st) {
   dim3 grid(cdiv(g.N, 16 * TN), cdiv(g.M, 16 * TM), g.batch * splits);
-  gemm_kernel<T, TM, TN><<<grid, NT, 0, st>>>(g, splits, std::max(kc, 1), ws);
+  (void)launch_pdl(gemm_kernel<T, TM, TN>, grid, NT, 0, st, g, splits, std::max(kc, 1), ws);
 }
 
 template <typename T>
@@ -453,7 +461,7 @@ t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st, int*
         const long total = (long)g.batch * g.M * g.N;
         const int blocks = (int)std::min<long>(cdiv(total, 256), 4L * kNumSMs);
         TraceScope ts(kTrElem, st, 0.0, (double)sizeof(T) * total * (sp.splits + 2));
-        splitk_reduce<T><<<blocks, 256, 0, st>>>(g, sp.splits, ws);
+        (void)launch_pdl(splitk_reduce<T>, blocks, 256, 0, st, g, sp.splits, ws);
         T2S2_CUDA_TRY(cudaGetLastError());
       }
       return T2S2_OK;
@@ -475,7 +483,7 @@ t2s2_status gemm(const Gemm<T>& g, T* ws, size_t ws_elems, cudaStream_t st, int*
     long total = (long)g.batch * g.M * g.N;
     int blocks = (int)std::min<long>(cdiv(total, 256), 4L * kNumSMs);
     TraceScope ts(kTrElem, st, 0.0, (double)sizeof(T) * total * (splits + 2));
-    splitk_reduce<T><<<blocks, 256, 0, st>>>(g, splits, ws);
+    (void)launch_pdl(splitk_reduce<T>, blocks, 256, 0, st, g, splits, ws);
     T2S2_CUDA_TRY(cudaGetLastError());
   }
   return T2S2_OK;

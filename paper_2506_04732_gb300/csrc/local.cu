@@ -341,6 +341,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
 
 template <typename T>
 __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
+  pdl_trigger();
   if (P.skip && *P.skip == 0) return;  // solved already (every CTA reads the same word)
   Team<T> tm(P);
   // optional phase timestamps (CTA 0, thread 0): slot 0 start, then 8 per
@@ -707,6 +708,8 @@ __global__ void __launch_bounds__(NT) gmres_team_kernel(LocalProblem<T> P) {
 // layout per side: lam[r], V[r*r], Vinv[r*r] (complex binary32).
 __global__ void local_eig_kernel(const double* PL, int ra, const double* PR, int rb, cf* outL, cf* outR,
                                  int* status, const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (skip && *skip == 0) return;  // the local system is solved already
   extern __shared__ __align__(16) unsigned char esm[];
   const int w = threadIdx.x / 32;
@@ -772,7 +775,7 @@ t2s2_status local_gmres(const LocalProblem<T>& P, cudaStream_t st) {
       eattr = true;
     }
     TraceScope ts(kTrSmall, st, 40.0 * ((double)P.ra * P.ra * P.ra + (double)P.rb * P.rb * P.rb), 0.0);
-    local_eig_kernel<<<1, 64, esm, st>>>(P.PL, P.ra, P.PR, P.rb, reinterpret_cast<cf*>(P.eigL),
+    (void)launch_pdl(local_eig_kernel, 1, 64, esm, st, P.PL, P.ra, P.PR, P.rb, reinterpret_cast<cf*>(P.eigL),
                                           reinterpret_cast<cf*>(P.eigR), P.eig_status, P.skip);
     T2S2_CUDA_TRY(cudaGetLastError());
   }

@@ -23,6 +23,8 @@ constexpr size_t kJacobiMaxSmem = 200 * 1024;
 __global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __restrict__ G, int c,
                                                             double shift_rel, double* __restrict__ L,
                                                             double* __restrict__ Linv, int* status) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ double sm[];
   double* A = sm;           // c x c
   double* Iv = sm + c * c;  // c x c
@@ -101,6 +103,8 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
                                                               double* __restrict__ s_out,
                                                               double* __restrict__ V, int* sweeps_out,
                                                               int prerotate) {
+  pdl_wait();
+  pdl_trigger();
   // Working matrix W is rows x cols with rows >= cols (transposed input if p < q).
   extern __shared__ double sm[];
   const int rows = transpose ? q : p, cols = transpose ? p : q;
@@ -363,7 +367,7 @@ t2s2_status chol_inv(const double* G, int c, double shift_rel, double* L, double
   }
   TraceScope ts(kTrSmall, st, (double)c * c * c, 8.0 * 3 * c * c);
   const int nt = c <= 32 ? 32 : (c <= 64 ? 128 : 256);
-  chol_inv_kernel<<<1, nt, smem, st>>>(G, c, shift_rel, L, Linv, status);
+  (void)launch_pdl(chol_inv_kernel, 1, nt, smem, st, G, c, shift_rel, L, Linv, status);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
@@ -386,7 +390,7 @@ t2s2_status jacobi_svd(const double* A, int p, int q, double* U, double* s, doub
     attr = true;
   }
   TraceScope ts(kTrSmall, st, 6.0 * 8 * (double)rows * cols * cols, 8.0 * (2.0 * p * q + q * q));
-  jacobi_svd_kernel<<<1, kThreads, smem, st>>>(A, p, q, transpose, U, s, V, sweeps, prerotate);
+  (void)launch_pdl(jacobi_svd_kernel, 1, kThreads, smem, st, A, p, q, transpose, U, s, V, sweeps, prerotate);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }

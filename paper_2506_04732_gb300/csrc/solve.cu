@@ -108,6 +108,8 @@ constexpr size_t kNextCoreSmem = 40 * 1024;
 
 __global__ void k_next_core(const double* Q, const double* U, const double* SV, int rows, int rn, int rk, int rb,
                             double* X1, int mn, int rnn) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ double nsm[];
   double* xs = nsm;                     // rb x mn x rnn
   double* C = xs + (size_t)rb * mn * rnn;  // rn x rk
@@ -148,6 +150,8 @@ __global__ void k_next_core(const double* Q, const double* U, const double* SV, 
 // SVD of one column x (n entries): u = x / |x| (0 for x = 0), s v^T = |x|,
 // and the truncated product u s v^T = x.  One CTA, fixed-order sum.
 __global__ void k_col_split(const double* x, int n, double* u, double* sv, double* xt) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[32];
   double p = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) p = fma(x[i], x[i], p);
@@ -674,7 +678,7 @@ struct Amen {
         // factorisation and no read-back
         {
           TraceScope ts(kTrSmall, c.st, 3.0 * rows, 24.0 * rows);
-          k_col_split<<<1, 256, 0, c.st>>>(X, rows, U, SV, Xt);
+          (void)launch_pdl(k_col_split, 1, 256, 0, c.st, X, rows, U, SV, Xt);
         }
         T2S2_CUDA_TRY(cudaGetLastError());
         T2S2_TRY(defer_iters(ra, m, rb));
@@ -777,7 +781,7 @@ struct Amen {
         const size_t sm = sizeof(double) * (nx + (size_t)rn * (rk + rb));
         if (sm <= kNextCoreSmem) {
           TraceScope ts(kTrGemm, c.st, 2.0 * rows * rn * rk + 2.0 * rn * rk * rb + 2.0 * rn * (double)nx, 0.0);
-          k_next_core<<<1, 256, sm, c.st>>>(Q, U, SV, rows, rn, rk, rb, x.c[k + 1], mn, rnn);
+          (void)launch_pdl(k_next_core, 1, 256, sm, c.st, Q, U, SV, rows, rn, rk, rb, x.c[k + 1], mn, rnn);
           T2S2_CUDA_TRY(cudaGetLastError());
         } else {
           double* C = tmp[6];

@@ -138,6 +138,8 @@ __device__ void sylv_invert(cf* Inv, const cf* Ts, const double* PL, double pi, 
 }
 
 __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   const int ra = P.ra, m = P.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int lm = sylv_ld(m), la = sylv_ld(ra);
@@ -358,7 +360,7 @@ t2s2_status sylv_rb1(const SylvProblem& P, cudaStream_t st) {
   const size_t smem = sylv_smem_bytes(P.ra, P.m);
   const double N = (double)P.ra * P.m;
   TraceScope ts(kTrLocal, st, 2.0 * N * (P.ra + P.m) * 3.0, 0.0);
-  sylv_rb1_kernel<<<1, kSylvThreads, smem, st>>>(P);
+  (void)launch_pdl(sylv_rb1_kernel, 1, kSylvThreads, smem, st, P);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }

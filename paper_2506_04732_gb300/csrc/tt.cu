@@ -19,21 +19,29 @@ namespace t2s2 {
 namespace {
 
 __global__ void k_scale_copy(double* dst, const double* src, size_t n, double alpha) {
+  pdl_wait();
+  pdl_trigger();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x)
     dst[e] = alpha * src[e];
 }
 __global__ void k_axpy(double* dst, const double* src, size_t n, double beta) {
+  pdl_wait();
+  pdl_trigger();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x)
     dst[e] += beta * src[e];
 }
 __global__ void k_fill(double* dst, size_t n, double v) {
+  pdl_wait();
+  pdl_trigger();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x)
     dst[e] = v;
 }
 __global__ void k_identity(double* dst, int n) {
+  pdl_wait();
+  pdl_trigger();
   size_t nn = (size_t)n * n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn;
        e += (size_t)gridDim.x * blockDim.x)
@@ -41,6 +49,8 @@ __global__ void k_identity(double* dst, int n) {
 }
 __global__ void k_copy_block(double* dst, int rd0, int rd1, int a0, int b0, const double* src, int ra,
                              int m, int rb, double alpha) {
+  pdl_wait();
+  pdl_trigger();
   size_t n = (size_t)ra * m * rb;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -52,6 +62,8 @@ __global__ void k_copy_block(double* dst, int rd0, int rd1, int a0, int b0, cons
   }
 }
 __global__ void k_sv_t(double* M, const double* s, const double* V, int r, int q, int ldv) {
+  pdl_wait();
+  pdl_trigger();
   int n = r * q;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int i = e / q, j = e % q;
@@ -59,17 +71,23 @@ __global__ void k_sv_t(double* M, const double* s, const double* V, int r, int q
   }
 }
 __global__ void k_d2f(float* dst, const double* src, size_t n) {
+  pdl_wait();
+  pdl_trigger();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x)
     dst[e] = (float)src[e];
 }
 __global__ void k_f2d(double* dst, const float* src, size_t n) {
+  pdl_wait();
+  pdl_trigger();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x)
     dst[e] = (double)src[e];
 }
 // sum of squares, one block, fixed order per thread then tree (deterministic)
 __global__ void k_sumsq(const double* v, size_t n, double* out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[1024];
   double s = 0.0;
   for (size_t e = threadIdx.x; e < n; e += blockDim.x) s += v[e] * v[e];
@@ -88,24 +106,24 @@ inline int blocks_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_
 
 t2s2_status dev_scale_copy(Ctx& cx, double* dst, const double* src, size_t n, double alpha) {
   if (n == 0) return T2S2_OK;
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * n); k_scale_copy<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n, alpha); }
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * n); (void)launch_pdl(k_scale_copy, blocks_for(n), 256, 0, cx.st, dst, src, n, alpha); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 t2s2_status dev_axpy(Ctx& cx, double* dst, const double* src, size_t n, double beta) {
   if (n == 0) return T2S2_OK;
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 24.0 * n); k_axpy<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n, beta); }
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 24.0 * n); (void)launch_pdl(k_axpy, blocks_for(n), 256, 0, cx.st, dst, src, n, beta); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 t2s2_status dev_fill(Ctx& cx, double* dst, size_t n, double v) {
   if (n == 0) return T2S2_OK;
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 8.0 * n); k_fill<<<blocks_for(n), 256, 0, cx.st>>>(dst, n, v); }
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 8.0 * n); (void)launch_pdl(k_fill, blocks_for(n), 256, 0, cx.st, dst, n, v); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 t2s2_status dev_identity(Ctx& cx, double* dst, int n) {
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 8.0 * n * n); k_identity<<<blocks_for((size_t)n * n), 256, 0, cx.st>>>(dst, n); }
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 8.0 * n * n); (void)launch_pdl(k_identity, blocks_for((size_t)n * n), 256, 0, cx.st, dst, n); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
@@ -114,26 +132,26 @@ t2s2_status dev_copy_block(Ctx& cx, double* dst, int rd0, int rd1, int a0, int b
   (void)rd0;
   size_t n = (size_t)ra * m * rb;
   if (n == 0) return T2S2_OK;
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * n); k_copy_block<<<blocks_for(n), 256, 0, cx.st>>>(dst, rd0, rd1, a0, b0, src, ra, m, rb, alpha); }
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * n); (void)launch_pdl(k_copy_block, blocks_for(n), 256, 0, cx.st, dst, rd0, rd1, a0, b0, src, ra, m, rb, alpha); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 t2s2_status dev_sv_t(Ctx& cx, double* M, const double* s, const double* V, int r, int q, int ldv) {
   if (r * q == 0) return T2S2_OK;
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * r * q); k_sv_t<<<blocks_for((size_t)r * q), 256, 0, cx.st>>>(M, s, V, r, q, ldv); }
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * r * q); (void)launch_pdl(k_sv_t, blocks_for((size_t)r * q), 256, 0, cx.st, M, s, V, r, q, ldv); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 
 t2s2_status dev_d2f(Ctx& cx, float* dst, const double* src, size_t n) {
   if (n == 0) return T2S2_OK;
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 12.0 * n); k_d2f<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n); }
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 12.0 * n); (void)launch_pdl(k_d2f, blocks_for(n), 256, 0, cx.st, dst, src, n); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
 t2s2_status dev_f2d(Ctx& cx, double* dst, const float* src, size_t n) {
   if (n == 0) return T2S2_OK;
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 12.0 * n); k_f2d<<<blocks_for(n), 256, 0, cx.st>>>(dst, src, n); }
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 12.0 * n); (void)launch_pdl(k_f2d, blocks_for(n), 256, 0, cx.st, dst, src, n); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
@@ -142,7 +160,7 @@ t2s2_status core_norm(Ctx& cx, const double* v, size_t n, double* out) {
   size_t mk = cx.ar->mark();
   double* d = aget<double>(cx, 1);
   if (!d) return T2S2_ENOMEM;
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 8.0 * n); k_sumsq<<<1, 1024, 0, cx.st>>>(v, n, d); }
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 8.0 * n); (void)launch_pdl(k_sumsq, 1, 1024, 0, cx.st, v, n, d); }
   T2S2_CUDA_TRY(cudaGetLastError());
   T2S2_CUDA_TRY(cudaMemcpyAsync(cx.hbuf, d, sizeof(double), cudaMemcpyDeviceToHost, cx.st));
   T2S2_CUDA_TRY(cudaStreamSynchronize(cx.st));
@@ -166,6 +184,8 @@ static constexpr double kUnit = 1.1102230246251565e-16;
 
 namespace {
 __global__ void k_transpose(double* dst, const double* src, int r, int c) {
+  pdl_wait();
+  pdl_trigger();
   int n = r * c;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int i = e / c, j = e % c;
@@ -240,7 +260,7 @@ t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, dou
     cur = outs[pass];
   }
   // W = Q (L1 L2 L3)^T  ->  R = Lacc^T
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * c * c); k_transpose<<<blocks_for((size_t)c * c), 256, 0, cx.st>>>(R, Lacc, c, c); }
+  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * c * c); (void)launch_pdl(k_transpose, blocks_for((size_t)c * c), 256, 0, cx.st, R, Lacc, c, c); }
   T2S2_CUDA_TRY(cudaGetLastError());
   cx.ar->release(mk);
   return T2S2_OK;
@@ -350,6 +370,8 @@ struct SumArgs {
 };
 
 __global__ void k_tt_sum(SumArgs a) {
+  pdl_wait();
+  pdl_trigger();
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < a.off[a.d]; e += (long)gridDim.x * blockDim.x) {
     int k = 0;
     while (e >= a.off[k + 1]) ++k;
@@ -406,7 +428,7 @@ t2s2_status tt_axpby(Ctx& cx, double alpha, const DevTT& x, double beta, const D
   }
   {
     TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * a.off[d]);
-    k_tt_sum<<<blocks_for((size_t)a.off[d]), 256, 0, cx.st>>>(a);
+    (void)launch_pdl(k_tt_sum, blocks_for((size_t)a.off[d]), 256, 0, cx.st, a);
   }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
@@ -418,6 +440,8 @@ namespace {
 // (the LQ factor of a single row is its norm).  One CTA; sums in a fixed
 // order.
 __global__ void k_orth_rank1(OrthArgs1 a) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[8];
   __shared__ double scale_s;
   double prod = 1.0;
@@ -465,7 +489,7 @@ t2s2_status tt_orth_right(Ctx& cx, DevTT& x) {
       }
       {
         TraceScope ts_(kTrSmall, cx.st, 2.0 * d * 64, 16.0 * d * 64);
-        k_orth_rank1<<<1, 256, 0, cx.st>>>(a);
+        (void)launch_pdl(k_orth_rank1, 1, 256, 0, cx.st, a);
       }
       T2S2_CUDA_TRY(cudaGetLastError());
       return T2S2_OK;

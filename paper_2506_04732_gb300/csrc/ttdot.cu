@@ -43,6 +43,7 @@ struct DotArgs {
 };
 
 __global__ void __launch_bounds__(kDotThreads) tt_dots_kernel(DotArgs a) {
+  pdl_trigger();
   cg::grid_group grid = cg::this_grid();
   const long gt = (long)blockIdx.x * kDotThreads + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -169,6 +170,7 @@ __device__ __forceinline__ long dd_phi_items(const DDArgs& a, int p, int k) {
 }
 
 __global__ void __launch_bounds__(kDotThreads) tt_norm2_dd_kernel(DDArgs a) {
+  pdl_trigger();
   cg::grid_group grid = cg::this_grid();
   const int G = gridDim.x, g = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
