@@ -30,6 +30,11 @@
  * - Every entry point returns a status; nothing aborts the process.
  * - An operator handle owns its device matrices and its workspace; calls that
  *   share one handle must not run concurrently (they share the workspace).
+ * - Kernels of one call are queued with programmatic dependent launch: a
+ *   kernel may become resident while its predecessor in the stream runs, but
+ *   touches memory only after that predecessor has completed, so results
+ *   equal those of plain stream order.  Environment variable T2S2_PDL=0
+ *   launches them plainly.
  */
 #ifndef T2S2_H
 #define T2S2_H
