@@ -56,6 +56,25 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over the ranks of the default process group (x itself
+    when no group is initialised or it has one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(ws: int, steps: int, seconds: float) -> float:
+    """Whole-job rate of ws independent replicas that each ran `steps` units,
+    timed by the slowest rank's `seconds`."""
+    return ws * steps / seconds if seconds > 0 else 0.0
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -604,11 +623,8 @@ def main():
     fam = {name: T.t2s2_trace_read(name) for name in FAMILIES}
     T.t2s2_trace(False)
     total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms)
+    value = replica_rate(ws, args.steps, total_ms / 1e3)
     last = infos[-1]
 
     # end to end through the C ABI with host buffers (copies inside the call)
@@ -631,7 +647,8 @@ def main():
             torch.cuda.synchronize()
             tt += time.perf_counter() - t0
             d2h = sum(8 * xh.r[k] * xh.m[k] * xh.r[k + 1] for k in range(xh.d))
-        e2e = {"value": ws * args.steps / tt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        tt = max_over_ranks(tt)
+        e2e = {"value": replica_rate(ws, args.steps, tt), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
     extras = {}
