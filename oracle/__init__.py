@@ -19,6 +19,9 @@ Everything here is plain, slow, FP64 numpy written from the paper:
 * ``solve``        - dense direct solve for tiny grids, an AMEn-style
                      alternating solver, Crank-Nicolson / backward-Euler steps
                      (eq. ttss-Crank-Nicolson, eq. ttss-backward-Euler).
+* ``spacetime``    - the unified space-time formulation: time as one more
+                     collocated dimension, the initial condition lifted into
+                     the right-hand side.
 
 Pinning status of each function is listed in its module header.  The
 superconsistent node rule follows a reading of the paper (the formula itself

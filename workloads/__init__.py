@@ -40,11 +40,14 @@ class Factor:
     kind == "wgauss": phi(x) = (1 - x^2) * exp(-(x - mu)^2 / (2 s^2))
     kind == "gauss":  phi(x) = exp(-(x - mu)^2 / (2 s^2))
     kind == "wsine":  phi(x) = (1 - x^2) * sin(m * pi * x)
+    kind == "exp":    phi(x) = exp(m * x)
+    kind == "poly":   phi(x) = sum_i c[i] x^i
     """
     kind: str
     m: float = 1.0
     mu: float = 0.0
     s: float = 1.0
+    c: tuple = ()
 
     def __call__(self, x, deriv: int = 0):
         x = np.asarray(x, dtype=np.float64)
@@ -81,6 +84,13 @@ class Factor:
                 return w1 * g + w * g1
             if deriv == 2:
                 return w2 * g + 2.0 * w1 * g1 + w * g2
+        elif self.kind == "exp":
+            if deriv in (0, 1, 2):
+                return self.m ** deriv * np.exp(self.m * x)
+        elif self.kind == "poly":
+            if deriv in (0, 1, 2):
+                c = np.polynomial.polynomial.polyder(np.asarray(self.c, dtype=np.float64), deriv)
+                return np.polynomial.polynomial.polyval(x, c) + 0.0 * x
         raise ValueError(f"bad factor {self.kind} / deriv {deriv}")
 
 
