@@ -118,8 +118,8 @@ int t2s2_device_count(void);
  * Build the d-dimensional collocation operator (Overview (ii)-(iii)).
  * Per dimension, on the host in FP64: GLL nodes, superconsistent collocation
  * points eta (roots in (-1,1) of eps P_N' - beta_k P_N, dropping the root
- * nearest the outflow end when N of them fall inside, N = n-1; see the design doc
- * for this reading of the paper), Lagrange matrices Rt = l_i(eta_j),
+ * nearest the outflow end when N of them fall inside, N = n-1; a reading of
+ * Overview (ii), which does not print the rule), Lagrange matrices Rt = l_i(eta_j),
  * D, D2 on the interior nodes, Lt = beta_k D - eps D2, the interpolation
  * inverse and B_k = Rt^{-1} Lt.  The collocation operator is the rank-2
  * TT-matrix (eq. tt-matrix-format)

@@ -6,7 +6,7 @@ from the representation points.  For the 1D model beta u' - eps u'' = 1
 zeros of P_N when convection dominates, with an intermediate set in between
 that depends only on eps/|beta| and N (Fig. 1).  The paper does not print the
 formula (its Methods section covers only the tensor-train part), so this module
-follows a reading, recorded in the design doc:
+follows a reading of Overview (ii):
 
     eta = roots in (-1, 1) of q(x) = eps P_N'(x) - beta P_N(x).
 

@@ -18,8 +18,8 @@ The time operator (2/T) d/ds is pure transport towards s = +1.  The
 superconsistent points of a transport operator (eps -> 0 in Overview (ii))
 are the zeros of P_N; with only the inflow end constrained there is no
 outflow root to drop, so the N collocation times are the N Gauss points g_i.
-This choice is a reading (the paper does not print the time nodes of its
-space-time runs) and is recorded with the other readings.
+This choice is a reading: the paper does not print the time nodes of its
+space-time runs.
 
 With the unknowns ordered time first, then x_1 .. x_d, the discrete operator is
 the Kronecker sum over d + 1 dimensions,
