@@ -134,6 +134,38 @@ t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op*
 /* Free an operator and its workspace.  NULL is accepted. */
 t2s2_status t2s2_op_destroy(t2s2_op op);
 
+/* Kinds of a dimension for t2s2_dim_matrices. */
+#define T2S2_DIM_SPACE 0       /* both ends Dirichlet, superconsistent points */
+#define T2S2_DIM_SPACE_PLAIN 1 /* both ends Dirichlet, interior GLL points (Plain-SC) */
+#define T2S2_DIM_TIME 2        /* time of the space-time form: value given at s = -1 only */
+
+/*
+ * One dimension's 1D collocation matrices, computed on the host in FP64 with
+ * no device involved (the per-dimension part of t2s2_build_operator).
+ * n GLL nodes x_0 = -1 < ... < x_N = 1 (N = n-1, 3 <= n <= T2S2_MAX_N):
+ *   space kinds: m = n-2 unknowns x_1..x_{N-1}; collocation points as in
+ *                t2s2_build_operator (superconsistent, or interior GLL for
+ *                T2S2_DIM_SPACE_PLAIN); boundary columns x_0 and x_N (nb = 2);
+ *   T2S2_DIM_TIME: the unified space-time formulation (time mapped onto
+ *                [-1, 1], the initial condition a boundary condition at
+ *                s = -1, none at s = 1): m = n-1 unknowns x_1..x_N,
+ *                collocation at the N zeros of P_N (the eps -> 0
+ *                superconsistent points of transport with only the inflow
+ *                end constrained; a reading, the paper prints no time
+ *                nodes); boundary column x_0 (nb = 1).  Pass beta = 2/T for
+ *                a time interval of length T and eps = 0.
+ * Outputs (host arrays; any may be NULL): x (n), eta (m collocation
+ * points), Rt and Lt (m x m, row-major, row = collocation point, column =
+ * unknown node), Rb and Lb (m x nb, the boundary columns, for lifting
+ * boundary or initial data), with R = l_i(eta_j) and L = beta l_i'(eta_j) -
+ * eps l_i''(eta_j).
+ * Errors: T2S2_EINVAL for n outside [3, T2S2_MAX_N], an unknown kind,
+ * non-finite eps or beta, eps <= 0 on a space kind (as t2s2_build_operator)
+ * or eps < 0 on the time kind.
+ */
+t2s2_status t2s2_dim_matrices(int n, double eps, double beta, int kind, double* x, double* eta, double* Rt,
+                              double* Lt, double* Rb, double* Lb);
+
 /* Copy dimension k's GLL nodes x (n values) and collocation points eta
  * (n-2 values) into host arrays; either pointer may be NULL. */
 t2s2_status t2s2_op_nodes(t2s2_op op, int k, double* x, double* eta);

@@ -22,9 +22,11 @@ __all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REF
            "t2s2_norm", "t2s2_diff_norm", "t2s2_norm_noalloc", "t2s2_residual", "t2s2_solve", "t2s2_solve_batched", "t2s2_cn_step", "t2s2_be_step",
            "t2s2_device_count", "t2s2_strerror", "t2s2_gemm", "WarmStartNet", "t2s2_apply_batched",
            "t2s2_autotune_report", "t2s2_kernel_launches", "t2s2_trace",
-           "t2s2_trace_read", "TRACE_FAMILIES", "lib_path"]
+           "t2s2_trace_read", "TRACE_FAMILIES", "lib_path", "t2s2_dim_matrices", "DIM_SPACE",
+           "DIM_SPACE_PLAIN", "DIM_TIME"]
 
 FP64, FP32_REFINE, TF32_REFINE, BF16_REFINE = 0, 1, 2, 3
+DIM_SPACE, DIM_SPACE_PLAIN, DIM_TIME = 0, 1, 2
 # enrichment rank of the solver (T2S2_RANK_KICK; the T2S2_KICK environment
 # variable overrides it): a solution can carry ranks up to rmax + RANK_KICK
 RANK_KICK = int(os.environ.get("T2S2_KICK", "8")) if 1 <= int(os.environ.get("T2S2_KICK", "8")) <= 16 else 8
@@ -77,6 +79,8 @@ _SIGS = {
     "t2s2_build_operator": (ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.c_void_p,
                                            ctypes.POINTER(ctypes.c_void_p)]),
     "t2s2_op_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "t2s2_dim_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+                          + [ctypes.c_void_p] * 6),
     "t2s2_op_nodes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                      ctypes.c_void_p]),
     "t2s2_op_matrices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
@@ -375,6 +379,21 @@ def t2s2_trace_read(family) -> dict:
     _check(load().t2s2_trace_read(idx, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
                                   ctypes.byref(by)), "t2s2_trace_read")
     return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
+
+
+def t2s2_dim_matrices(n: int, eps: float, beta: float, kind: int = DIM_SPACE):
+    """One dimension's 1D collocation matrices, computed on the host (no
+    device): returns dict x (n), eta (m), Rt, Lt (m x m), Rb, Lb (m x nb) with
+    m = n-2, nb = 2 for the space kinds and m = n-1, nb = 1 for DIM_TIME."""
+    time = kind == DIM_TIME
+    m, nb = (n - 1, 1) if time else (n - 2, 2)
+    out = {"x": np.zeros(n), "eta": np.zeros(max(m, 0)), "Rt": np.zeros((max(m, 0), max(m, 0))),
+           "Lt": np.zeros((max(m, 0), max(m, 0))), "Rb": np.zeros((max(m, 0), nb)),
+           "Lb": np.zeros((max(m, 0), nb))}
+    _check(load().t2s2_dim_matrices(int(n), float(eps), float(beta), int(kind),
+                                    *[out[k].ctypes.data for k in ("x", "eta", "Rt", "Lt", "Rb", "Lb")]),
+           "t2s2_dim_matrices")
+    return out
 
 
 def _check(status: int, what: str, ok=(0,)):

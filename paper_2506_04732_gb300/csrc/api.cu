@@ -463,6 +463,41 @@ t2s2_status t2s2_op_destroy(t2s2_op op) {
   return T2S2_OK;
 }
 
+t2s2_status t2s2_dim_matrices(int n, double eps, double beta, int kind, double* x, double* eta, double* Rt,
+                              double* Lt, double* Rb, double* Lb) {
+  if (n < 3 || n > T2S2_MAX_N) return T2S2_EINVAL;
+  if (kind != T2S2_DIM_SPACE && kind != T2S2_DIM_SPACE_PLAIN && kind != T2S2_DIM_TIME) return T2S2_EINVAL;
+  if (!std::isfinite(eps) || !std::isfinite(beta)) return T2S2_EINVAL;
+  const bool time = kind == T2S2_DIM_TIME;
+  if (time ? eps < 0.0 : !(eps > 0.0)) return T2S2_EINVAL;
+  const int N = n - 1, m = time ? n - 1 : n - 2, nb = time ? 1 : 2;
+  std::vector<double> xs(n), pts(m);
+  gll_points(N, xs.data());
+  if (time) {
+    gauss_points(N, pts.data());
+  } else {
+    collocation_points(N, eps, beta, kind == T2S2_DIM_SPACE_PLAIN, pts.data());
+  }
+  std::vector<double> R((size_t)m * n), D((size_t)m * n), D2((size_t)m * n);
+  lagrange_matrices(N, xs.data(), m, pts.data(), R.data(), D.data(), D2.data());
+  auto L = [&](size_t e) { return beta * D[e] - eps * D2[e]; };
+  for (int j = 0; j < m; ++j) {
+    for (int i = 0; i < m; ++i) {
+      const size_t e = (size_t)j * n + i + 1;  // unknown i is node i + 1
+      if (Rt) Rt[(size_t)j * m + i] = R[e];
+      if (Lt) Lt[(size_t)j * m + i] = L(e);
+    }
+    for (int q = 0; q < nb; ++q) {
+      const size_t e = (size_t)j * n + (q == 0 ? 0 : N);
+      if (Rb) Rb[(size_t)j * nb + q] = R[e];
+      if (Lb) Lb[(size_t)j * nb + q] = L(e);
+    }
+  }
+  if (x) std::copy(xs.begin(), xs.end(), x);
+  if (eta) std::copy(pts.begin(), pts.end(), eta);
+  return T2S2_OK;
+}
+
 t2s2_status t2s2_op_nodes(t2s2_op op, int k, double* x, double* eta) {
   if (!op || k < 0 || k >= op->d) return T2S2_EINVAL;
   const Dim1D& D = op->dims[k];
