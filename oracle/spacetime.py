@@ -110,11 +110,6 @@ def ttm_cores(top: TimeOp1D, ops):
     return O.ttm_cores([top] + list(ops), 0.0, 1.0)
 
 
-def _space_factor_values(st, ops, pts_of):
-    """Per term: list over k of factor values at pts_of(ops[k])."""
-    return [[t.factors[k](pts_of(ops[k])) for k in range(st.space.d)] for t in st.space.terms]
-
-
 def solution_tt(st: SpaceTimeProblem, top: TimeOp1D, ops):
     """u* at the unknowns: time nodes s_1..s_N, interior spatial GLL nodes."""
     vecs = []
