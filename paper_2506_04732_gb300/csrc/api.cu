@@ -297,15 +297,6 @@ t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
   return T2S2_OK;
 }
 
-// <u, v> by left-to-right contraction of the interface matrices (one fused
-// launch, ttdot.cu).  Accurate for the value itself; differences of such dots
-// cancel, so they serve only to screen residuals far above the tolerance.
-t2s2_status tt_dot(Ctx& cx, const DevTT& u, const DevTT& v, double* out) {
-  const DevTT* pu[1] = {&u};
-  const DevTT* pv[1] = {&v};
-  return tt_dots(cx, 1, pu, pv, out);
-}
-
 // Residual screen sqrt(|b|^2 - 2<b, A x> + |A x|^2) / |b|, with y = A x and
 // the two (three, when *bb_io < 0: then |b|^2 is returned in *bb_io) inner
 // products in one launch.

@@ -66,7 +66,6 @@ t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mas
                      bool transformed);
 t2s2_status apply_dispatch(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass,
                            double c_op, t2s2_precision prec);
-t2s2_status tt_dot(Ctx& cx, const DevTT& u, const DevTT& v, double* out);
 // Up to four TT inner products <u_p, v_p> in one launch (ttdot.cu); reads
 // the values back (synchronising).
 t2s2_status tt_dots(Ctx& cx, int n, const DevTT* const* u, const DevTT* const* v, double* out);

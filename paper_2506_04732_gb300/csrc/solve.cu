@@ -73,21 +73,9 @@ t2s2_status mode1(Ctx& cx, const double* P, int rn, int ro, const double* X, int
                   double alpha = 1.0, double beta = 0.0) {
   return contract_gemm(cx, g_mode1(P, rn, ro, X, m, rb, Y, alpha, beta));
 }
-t2s2_status mode2(Ctx& cx, const double* B, int m, const double* X, int ra, int rb, double* Y,
-                  double alpha = 1.0, double beta = 0.0) {
-  return contract_gemm(cx, g_mode2(B, m, X, ra, rb, Y, alpha, beta));
-}
 t2s2_status mode3(Ctx& cx, const double* X, int ra, int m, int ro, const double* Q, int rn, double* Y,
                   double alpha = 1.0, double beta = 0.0) {
   return contract_gemm(cx, g_mode3(X, ra, m, ro, Q, rn, Y, alpha, beta));
-}
-t2s2_status contract_left(Ctx& cx, const double* U, int ra, int m, int rb, const double* T, int rc,
-                          double* out) {
-  return contract_gemm(cx, g_cleft(U, ra, m, rb, T, rc, out));
-}
-t2s2_status contract_right(Ctx& cx, const double* U, int ra, int m, int rb, const double* T, int rc,
-                           double* out) {
-  return contract_gemm(cx, g_cright(U, ra, m, rb, T, rc, out));
 }
 template <int N>
 t2s2_status group(Ctx& cx, const Gemm<double> (&gs)[N]) {

@@ -47,20 +47,6 @@ __global__ void k_identity(double* dst, int n) {
        e += (size_t)gridDim.x * blockDim.x)
     dst[e] = (e / n == e % n) ? 1.0 : 0.0;
 }
-__global__ void k_copy_block(double* dst, int rd0, int rd1, int a0, int b0, const double* src, int ra,
-                             int m, int rb, double alpha) {
-  pdl_wait();
-  pdl_trigger();
-  size_t n = (size_t)ra * m * rb;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
-       e += (size_t)gridDim.x * blockDim.x) {
-    int b = (int)(e % rb);
-    size_t t = e / rb;
-    int i = (int)(t % m);
-    int a = (int)(t / m);
-    dst[((size_t)(a0 + a) * m + i) * rd1 + b0 + b] = alpha * src[e];
-  }
-}
 __global__ void k_sv_t(double* M, const double* s, const double* V, int r, int q, int ldv) {
   pdl_wait();
   pdl_trigger();
@@ -124,15 +110,6 @@ t2s2_status dev_fill(Ctx& cx, double* dst, size_t n, double v) {
 }
 t2s2_status dev_identity(Ctx& cx, double* dst, int n) {
   { TraceScope ts_(kTrElem, cx.st, 0.0, 8.0 * n * n); (void)launch_pdl(k_identity, blocks_for((size_t)n * n), 256, 0, cx.st, dst, n); }
-  T2S2_CUDA_TRY(cudaGetLastError());
-  return T2S2_OK;
-}
-t2s2_status dev_copy_block(Ctx& cx, double* dst, int rd0, int rd1, int a0, int b0, const double* src,
-                           int ra, int m, int rb, double alpha) {
-  (void)rd0;
-  size_t n = (size_t)ra * m * rb;
-  if (n == 0) return T2S2_OK;
-  { TraceScope ts_(kTrElem, cx.st, 0.0, 16.0 * n); (void)launch_pdl(k_copy_block, blocks_for(n), 256, 0, cx.st, dst, rd0, rd1, a0, b0, src, ra, m, rb, alpha); }
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
@@ -520,37 +497,6 @@ t2s2_status tt_orth_right(Ctx& cx, DevTT& x) {
       T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k - 1], P, sizeof(double) * rp * mp * cols, cudaMemcpyDeviceToDevice, cx.st));
       T2S2_TRY(dev_identity(cx, x.c[k], cols));
       x.r[k] = cols;
-    }
-    cx.ar->release(mark);
-  }
-  return T2S2_OK;
-}
-
-t2s2_status tt_orth_left(Ctx& cx, DevTT& x) {
-  const int d = x.d;
-  for (int k = 0; k + 1 < d; ++k) {
-    const int rk = x.r[k], mk_ = x.m[k], rk1 = x.r[k + 1];
-    const int rows = rk * mk_;
-    const int mn = x.m[k + 1], rn = x.r[k + 2];
-    size_t mark = cx.ar->mark();
-    if (rows >= rk1) {
-      if (rk1 > kSmallMax) return T2S2_EINVAL;
-      double* Q = aget<double>(cx, (size_t)rows * rk1);
-      double* R = aget<double>(cx, (size_t)rk1 * rk1);
-      double* P = aget<double>(cx, (size_t)rk1 * mn * rn);
-      if (!Q || !R || !P) return T2S2_ENOMEM;
-      T2S2_TRY(qr_tall(cx, x.c[k], rows, rk1, Q, R));
-      T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k], Q, sizeof(double) * rows * rk1, cudaMemcpyDeviceToDevice, cx.st));
-      T2S2_TRY(gemm_ex<double>(cx, rk1, mn * rn, rk1, false, false, 1.0, R, rk1, x.c[k + 1], mn * rn, 0.0, P, mn * rn));
-      T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k + 1], P, sizeof(double) * rk1 * mn * rn, cudaMemcpyDeviceToDevice, cx.st));
-    } else {
-      if ((size_t)rows * mn * rn > x.cap[k + 1] || (size_t)rows * rows > x.cap[k]) return T2S2_ENOMEM;
-      double* P = aget<double>(cx, (size_t)rows * mn * rn);
-      if (!P) return T2S2_ENOMEM;
-      T2S2_TRY(gemm_ex<double>(cx, rows, mn * rn, rk1, false, false, 1.0, x.c[k], rk1, x.c[k + 1], mn * rn, 0.0, P, mn * rn));
-      T2S2_CUDA_TRY(cudaMemcpyAsync(x.c[k + 1], P, sizeof(double) * rows * mn * rn, cudaMemcpyDeviceToDevice, cx.st));
-      T2S2_TRY(dev_identity(cx, x.c[k], rows));
-      x.r[k + 1] = rows;
     }
     cx.ar->release(mark);
   }

@@ -66,7 +66,6 @@ t2s2_status tt_axpby(Ctx& cx, double alpha, const DevTT& x, double beta, const D
 // In place: cores 1..d-1 right-orthonormal (rows), weight in core 0.
 t2s2_status tt_orth_right(Ctx& cx, DevTT& x);
 // In place: cores 0..d-2 left-orthonormal (columns), weight in core d-1.
-t2s2_status tt_orth_left(Ctx& cx, DevTT& x);
 // In place rounding with ||x - rndg(x)|| <= tol ||x|| (cap rmax <= 0: none).
 t2s2_status tt_round(Ctx& cx, DevTT& x, double tol, int rmax);
 // ||x||_F of a TT already right-orthogonalised (norm of core 0).
@@ -114,9 +113,6 @@ t2s2_status dev_axpy(Ctx& cx, double* dst, const double* src, size_t n, double b
 t2s2_status dev_d2f(Ctx& cx, float* dst, const double* src, size_t n);
 t2s2_status dev_f2d(Ctx& cx, double* dst, const float* src, size_t n);
 t2s2_status dev_identity(Ctx& cx, double* dst, int n);
-// dst (rd0 x m x rd1) block at (a0, b0) = alpha * src (ra x m x rb)
-t2s2_status dev_copy_block(Ctx& cx, double* dst, int rd0, int rd1, int a0, int b0,
-                           const double* src, int ra, int m, int rb, double alpha);
 // M[i][j] = s[i] * V[j][i] for i < r, j < q (V: q x ldv)
 t2s2_status dev_sv_t(Ctx& cx, double* M, const double* s, const double* V, int r, int q, int ldv);
 
