@@ -31,7 +31,7 @@ def driver(tmp_path_factory):
 
 
 def _plans(exe, shapes):
-    inp = "".join(f"{M} {N} {K} {b}\n" for M, N, K, b in shapes)
+    inp = "".join(f"s {M} {N} {K} {b}\n" for M, N, K, b in shapes)
     out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
     return [tuple(int(v) for v in ln.split()) for ln in out if ln.strip()]
 
@@ -50,13 +50,38 @@ def test_plans_keep_the_kernel_invariants(driver):
     for (M, N, K, b), (use, bm, bn, splits, kc) in zip(shapes, plans):
         small = M * N * max(K, 1) * b <= SMALL_MAX_FMAS
         assert bool(use) == small, (M, N, K, b)
-        if not use:
+        if use:
+            assert (bm, bn) in SHAPES and 256 % (bm * bn) == 0
+            _check_split(K, b, splits, kc)
+
+
+def _check_split(K, b, splits, kc):
+    if K == 0:
+        assert splits == 1 and kc == 0
+        return
+    assert kc >= 8 and kc % 8 == 0
+    assert splits == math.ceil(K / kc)          # every split has work ...
+    assert (splits - 1) * kc < K <= splits * kc  # ... and together they cover K
+    assert 1 <= splits <= 64 and b * splits <= 65535
+
+
+def test_group_plans_keep_the_kernel_invariants(driver):
+    rng = np.random.default_rng(1)
+    groups = []
+    for _ in range(400):
+        n = int(rng.integers(1, 9))
+        groups.append([(int(rng.integers(1, 300)), int(rng.integers(1, 300)), int(rng.integers(0, 3000)),
+                        1 if rng.random() < 0.8 else int(rng.integers(1, 16))) for _ in range(n)])
+    inp = "".join("g %d %s\n" % (len(g), " ".join(f"{M} {N} {K} {b}" for M, N, K, b in g)) for g in groups)
+    out = subprocess.run([driver], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    rows = [[int(v) for v in ln.split()] for ln in out if ln.strip()]
+    assert len(rows) == len(groups)
+    for g, row in zip(groups, rows):
+        ok, bm, bn = row[:3]
+        small = all(M * N * max(K, 1) * b <= SMALL_MAX_FMAS for M, N, K, b in g)
+        assert bool(ok) == small
+        if not ok:
             continue
-        assert (bm, bn) in SHAPES and 256 % (bm * bn) == 0
-        if K == 0:
-            assert splits == 1 and kc == 0
-            continue
-        assert kc >= 8 and kc % 8 == 0
-        assert splits == math.ceil(K / kc)          # every split has work ...
-        assert (splits - 1) * kc < K <= splits * kc  # ... and together they cover K
-        assert 1 <= splits <= 64 and b * splits <= 65535
+        assert (bm, bn) in SHAPES   # one tile shape for the whole launch
+        for i, (M, N, K, b) in enumerate(g):
+            _check_split(K, b, row[3 + 2 * i], row[4 + 2 * i])
