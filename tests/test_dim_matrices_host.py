@@ -23,7 +23,10 @@ def _close(a, b, rel):
 
 @pytest.mark.parametrize("n,eps,beta,plain", [
     (5, 0.3, 1.0, False), (16, 1e-2, 0.8, False), (16, 1e-2, -0.8, False),
-    (33, 1e-4, 0.57, False), (33, 1e-3, 0.57, True), (12, 0.05, 0.0, False)])
+    (33, 1e-4, 0.57, False), (33, 1e-3, 0.57, True), (12, 0.05, 0.0, False),
+    # the extremes of n: one unknown, and the largest operator the library takes
+    (3, 0.1, 1.0, False), (3, 1e-6, -1.0, False), (4, 1e-8, 1.0, False),
+    (128, 1e-2, 0.7, False), (128, 1e-5, 0.7, False), (128, 1e-3, -0.3, True)])
 def test_space_dimension_matches_oracle(n, eps, beta, plain):
     kind = T.DIM_SPACE_PLAIN if plain else T.DIM_SPACE
     got = T.t2s2_dim_matrices(n, eps, beta, kind)
@@ -38,7 +41,7 @@ def test_space_dimension_matches_oracle(n, eps, beta, plain):
     assert _close(got["Lb"], beta * o.D[:, cols] - eps * o.D2[:, cols], 1e-11)
 
 
-@pytest.mark.parametrize("n,T_len", [(3, 1.0), (9, 2.5), (24, 0.4)])
+@pytest.mark.parametrize("n,T_len", [(3, 1.0), (9, 2.5), (24, 0.4), (128, 0.5)])
 def test_time_dimension_matches_oracle(n, T_len):
     got = T.t2s2_dim_matrices(n, 0.0, 2.0 / T_len, T.DIM_TIME)
     o = ST.time_op1d(n, T_len)

@@ -36,8 +36,9 @@ def _run(exe, n, eps, beta, plain):
     return {k: np.array(v).reshape(m, m) for k, v in d.items()}
 
 
-@pytest.mark.parametrize("n,eps,beta,plain", [(6, 1e-2, 0.8, False), (12, 1e-3, -0.6, False),
-                                              (20, 0.05, 0.3, True), (33, 1e-4, 0.57, False)])
+@pytest.mark.parametrize("n,eps,beta,plain", [(3, 0.1, 1.0, False), (6, 1e-2, 0.8, False),
+                                              (12, 1e-3, -0.6, False), (20, 0.05, 0.3, True),
+                                              (33, 1e-4, 0.57, False), (128, 1e-3, 0.7, False)])
 def test_dimension_data_and_schur_form(driver, n, eps, beta, plain):
     h = _run(driver, n, eps, beta, plain)
     o = C.op1d(n, eps, beta, plain)
