@@ -116,6 +116,20 @@ def test_sc_nodes_interlace_gauss_and_gll(N):
         assert np.all(eta > g[:-1] - 1e-14) and np.all(eta < x[1:-1] + 1e-14)
 
 
+@pytest.mark.parametrize("N", [3, 7, 20])
+def test_sc_nodes_shift_monotonically_as_diffusion_falls(N):
+    # Overview (ii), Fig. 1: with n fixed, lowering eps moves the points steadily
+    # from the zeros of P_N' towards the zeros of P_N (for beta > 0: every
+    # eta_j decreases monotonically with eps, from x_j towards g_j)
+    x, _ = gll_nodes(N)
+    g = np.sort(npleg.leggauss(N)[0])
+    eps = np.logspace(2, -6, 33)
+    etas = np.array([sc_nodes(N, e, 1.0) for e in eps])
+    assert np.all(np.diff(etas, axis=0) <= 1e-15)                      # decreasing with eps
+    assert np.max(np.abs(etas[0] - x[1:-1])) < 1e-2 * np.max(np.diff(x))   # near P_N' zeros
+    assert np.max(np.abs(etas[-1] - g[:-1])) < 1e-2 * np.max(np.diff(x))   # near P_N zeros
+
+
 def _poly_eval(coef, x, deriv=0):
     return nppoly.polyval(x, nppoly.polyder(coef, deriv) if deriv else coef)
 
