@@ -8,8 +8,13 @@ Samples a workload's analytic factors at the nodes the library reports
   analytic solutions, Results "Global Accuracy"); one rank-2 block per term.
 * ``solution_cores``: u* (or an initial condition) on the interior GLL grid,
   one rank-1 block per term.
+* ``spacetime_*``: the same for the unified space-time form (time as one
+  more collocated dimension, first): the source before the initial
+  condition is lifted, and the initial condition itself.
 """
 from __future__ import annotations
+
+import dataclasses
 
 import numpy as np
 
@@ -82,3 +87,53 @@ def build_operator(problem, stream=None):
     from . import t2s2_build_operator
     return t2s2_build_operator(problem.d, problem.n, problem.beta, problem.eps,
                                problem.plain_sc, stream)
+
+
+def spacetime_dims(st):
+    """The per-dimension node data of a space-time workload, time first, from
+    the library's host-side t2s2_dim_matrices (no device involved)."""
+    from . import DIM_SPACE, DIM_SPACE_PLAIN, DIM_TIME, t2s2_dim_matrices
+    sp = st.space
+    dims = [t2s2_dim_matrices(st.n_t, 0.0, 2.0 / st.T, DIM_TIME)]
+    kind = DIM_SPACE_PLAIN if sp.plain_sc else DIM_SPACE
+    dims += [t2s2_dim_matrices(sp.n[k], sp.eps, float(sp.beta[k]), kind) for k in range(sp.d)]
+    return dims
+
+
+def spacetime_source_cores(st, dims):
+    """b = (2/T) du*/ds - eps Laplace u* + beta . grad u* on the space-time
+    collocation grid (Gauss times, superconsistent points), before the
+    initial condition is lifted: per separable term, the spatial source times
+    phi_t at the collocation times plus (2/T) phi_t' times the spatial values.
+    ``dims`` is ``spacetime_dims(st)``."""
+    sp = st.space
+    scale = 2.0 / st.T
+    g = dims[0]["eta"]
+    blocks = []
+    for t, ft in zip(sp.terms, st.time_factors):
+        one = dataclasses.replace(sp, terms=[t])
+        spatial = _sampled_source(one, [dims[k + 1]["eta"] for k in range(sp.d)])
+        mass = [t.factors[k](dims[k + 1]["eta"]).reshape(1, -1, 1) for k in range(sp.d)]
+        mass[0] = mass[0] * t.coef
+        blocks.append([ft(g).reshape(1, -1, 1)] + spatial)
+        blocks.append([(scale * ft(g, 1)).reshape(1, -1, 1)] + mass)
+    return _block_tt(blocks)
+
+
+def spacetime_initial_cores(st, dims):
+    """u0 = u*(x, s = -1) at the interior spatial GLL nodes (d cores)."""
+    sp = st.space
+    blocks = []
+    for t, ft in zip(sp.terms, st.time_factors):
+        cores = [t.factors[k](dims[k + 1]["x"][1:-1]).reshape(1, -1, 1) for k in range(sp.d)]
+        cores[0] = cores[0] * (t.coef * float(ft(np.array([-1.0]))[0]))
+        blocks.append(cores)
+    return _block_tt(blocks)
+
+
+def _sampled_source(problem, etas):
+    """source_cores of ``problem`` at the given collocation points per dimension."""
+    class _Nodes:
+        def nodes(self, k):
+            return None, etas[k]
+    return source_cores(problem, _Nodes())
