@@ -131,6 +131,22 @@ int t2s2_device_count(void);
  */
 t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op* out);
 
+/*
+ * Operator of the unified space-time form (Methods overview; Results,
+ * "Global Accuracy"): time is one more collocated dimension, placed first,
+ * with the time interval [0, t_len] mapped onto [-1, 1].  Dimension 0 has n_t
+ * GLL nodes, n_t - 1 unknowns (every node but s = -1, which carries the
+ * initial condition) and collocation at the n_t - 1 Gauss points (see
+ * t2s2_dim_matrices, T2S2_DIM_TIME); its Lt is (2 / t_len) D.  Dimensions
+ * 1..d are those of t2s2_build_operator(space).  The operator is the rank-2
+ * TT-matrix Lt_t x M_x + Rt_t x A_x over d + 1 dimensions; solve it with
+ * c_mass = 0, c_op = 1 and a right-hand side that carries the lifted initial
+ * condition.  Errors as t2s2_build_operator, and T2S2_EINVAL for n_t outside
+ * [3, T2S2_MAX_N], t_len <= 0 or space->d + 1 > T2S2_MAX_D.
+ */
+t2s2_status t2s2_build_spacetime_operator(const t2s2_problem* space, int n_t, double t_len, void* stream,
+                                          t2s2_op* out);
+
 /* Free an operator and its workspace.  NULL is accepted. */
 t2s2_status t2s2_op_destroy(t2s2_op op);
 
@@ -167,11 +183,12 @@ t2s2_status t2s2_dim_matrices(int n, double eps, double beta, int kind, double* 
                               double* Lt, double* Rb, double* Lb);
 
 /* Copy dimension k's GLL nodes x (n values) and collocation points eta
- * (n-2 values) into host arrays; either pointer may be NULL. */
+ * (m values: n-2, or n-1 for the time dimension of a space-time operator)
+ * into host arrays; either pointer may be NULL. */
 t2s2_status t2s2_op_nodes(t2s2_op op, int k, double* x, double* eta);
 
-/* Copy dimension k's interior matrices Rt and Lt ((n-2)^2 doubles each,
- * row-major, row = collocation point, column = interior GLL node) to host
+/* Copy dimension k's matrices Rt and Lt (m^2 doubles each, m as above,
+ * row-major, row = collocation point, column = unknown GLL node) to host
  * arrays; either pointer may be NULL. */
 t2s2_status t2s2_op_matrices(t2s2_op op, int k, double* Rt, double* Lt);
 

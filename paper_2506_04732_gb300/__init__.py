@@ -23,6 +23,7 @@ __all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REF
            "t2s2_device_count", "t2s2_strerror", "t2s2_gemm", "WarmStartNet", "t2s2_apply_batched",
            "t2s2_autotune_report", "t2s2_kernel_launches", "t2s2_trace",
            "t2s2_trace_read", "TRACE_FAMILIES", "lib_path", "t2s2_dim_matrices", "DIM_SPACE",
+           "t2s2_build_spacetime_operator",
            "DIM_SPACE_PLAIN", "DIM_TIME"]
 
 FP64, FP32_REFINE, TF32_REFINE, BF16_REFINE = 0, 1, 2, 3
@@ -78,6 +79,8 @@ _SIGS = {
     "t2s2_device_count": (ctypes.c_int, []),
     "t2s2_build_operator": (ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.c_void_p,
                                            ctypes.POINTER(ctypes.c_void_p)]),
+    "t2s2_build_spacetime_operator": (ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.c_int, ctypes.c_double,
+                                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "t2s2_op_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "t2s2_dim_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
                           + [ctypes.c_void_p] * 6),
@@ -412,10 +415,10 @@ def _stream_handle(stream):
 class Operator:
     """Handle on the library's operator (t2s2_build_operator / t2s2_op_destroy)."""
 
-    def __init__(self, handle, d, n, beta, eps, plain_sc):
+    def __init__(self, handle, d, n, beta, eps, plain_sc, m=None):
         self._h = handle
         self.d, self.n, self.beta, self.eps, self.plain_sc = d, tuple(n), tuple(beta), eps, plain_sc
-        self.m = tuple(v - 2 for v in self.n)
+        self.m = tuple(v - 2 for v in self.n) if m is None else tuple(int(v) for v in m)
 
     @property
     def handle(self):
@@ -460,6 +463,23 @@ def t2s2_build_operator(d, n, beta, eps, plain_sc=False, stream=None) -> Operato
     _check(lib.t2s2_build_operator(ctypes.byref(prob), _stream_handle(stream), ctypes.byref(h)),
            "t2s2_build_operator")
     return Operator(h, d, n, beta, float(eps), bool(plain_sc))
+
+
+def t2s2_build_spacetime_operator(d, n, beta, eps, n_t, t_len, plain_sc=False, stream=None) -> Operator:
+    """Operator of the unified space-time form: time (n_t nodes, n_t - 1
+    unknowns, interval length t_len) as dimension 0, then the d spatial
+    dimensions of t2s2_build_operator."""
+    lib = load()
+    n = [int(v) for v in (n if np.ndim(n) else [n] * d)]
+    beta = [float(v) for v in beta]
+    na = (ctypes.c_int * d)(*n)
+    ba = (ctypes.c_double * d)(*beta)
+    prob = _Problem(d, na, ba, float(eps), int(bool(plain_sc)))
+    h = ctypes.c_void_p()
+    _check(lib.t2s2_build_spacetime_operator(ctypes.byref(prob), int(n_t), float(t_len), _stream_handle(stream),
+                                             ctypes.byref(h)), "t2s2_build_spacetime_operator")
+    return Operator(h, d + 1, [int(n_t)] + n, [2.0 / float(t_len)] + beta, float(eps), bool(plain_sc),
+                    m=[int(n_t) - 1] + [v - 2 for v in n])
 
 
 class TT:

@@ -352,36 +352,12 @@ int t2s2_device_count(void) {
   return good;
 }
 
-t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op* out) {
-  if (!prob || !out || !prob->n || !prob->beta) return T2S2_EINVAL;
-  *out = nullptr;
-  if (prob->d < 1 || prob->d > T2S2_MAX_D || !(prob->eps > 0.0) || !std::isfinite(prob->eps))
-    return T2S2_EINVAL;
-  for (int k = 0; k < prob->d; ++k) {
-    if (prob->n[k] < 3 || prob->n[k] > T2S2_MAX_N || !std::isfinite(prob->beta[k])) return T2S2_EINVAL;
-  }
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return T2S2_ENODEV;
-  cudaDeviceProp p;
-  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess || p.major != 10 || p.minor != 3) return T2S2_ENODEV;
-  t2s2_op op = new t2s2_op_s();
-  op->device = dev;
-  op->d = prob->d;
-  op->eps = prob->eps;
-  op->plain = prob->plain_sc;
-  op->dims.resize(op->d);
+// Device copies of every dimension's matrices (FP64 and FP32) and the
+// per-operator buffers, for an operator whose host dimensions are built.
+// Frees the operator on failure.
+static t2s2_status upload_operator(t2s2_op op, cudaStream_t st, t2s2_op* out) {
   size_t total = 0;
-  for (int k = 0; k < op->d; ++k) {
-    op->n[k] = prob->n[k];
-    op->m[k] = prob->n[k] - 2;
-    op->beta[k] = prob->beta[k];
-    if (!build_dimension(op->n[k], op->eps, op->beta[k], op->plain, &op->dims[k])) {
-      delete op;
-      return T2S2_EINVAL;
-    }
-    total += (size_t)kMatsPerDim * op->m[k] * op->m[k];
-  }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < op->d; ++k) total += (size_t)kMatsPerDim * op->m[k] * op->m[k];
   std::vector<double> host(total, 0.0);
   size_t off = 0;
   std::vector<size_t> offs(op->d);
@@ -435,6 +411,76 @@ t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op*
   }
   *out = op;
   return T2S2_OK;
+}
+
+t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op* out) {
+  if (!prob || !out || !prob->n || !prob->beta) return T2S2_EINVAL;
+  *out = nullptr;
+  if (prob->d < 1 || prob->d > T2S2_MAX_D || !(prob->eps > 0.0) || !std::isfinite(prob->eps))
+    return T2S2_EINVAL;
+  for (int k = 0; k < prob->d; ++k) {
+    if (prob->n[k] < 3 || prob->n[k] > T2S2_MAX_N || !std::isfinite(prob->beta[k])) return T2S2_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return T2S2_ENODEV;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess || p.major != 10 || p.minor != 3) return T2S2_ENODEV;
+  t2s2_op op = new t2s2_op_s();
+  op->device = dev;
+  op->d = prob->d;
+  op->eps = prob->eps;
+  op->plain = prob->plain_sc;
+  op->dims.resize(op->d);
+  for (int k = 0; k < op->d; ++k) {
+    op->n[k] = prob->n[k];
+    op->m[k] = prob->n[k] - 2;
+    op->beta[k] = prob->beta[k];
+    if (!build_dimension(op->n[k], op->eps, op->beta[k], op->plain, &op->dims[k])) {
+      delete op;
+      return T2S2_EINVAL;
+    }
+  }
+  return upload_operator(op, static_cast<cudaStream_t>(stream), out);
+}
+
+t2s2_status t2s2_build_spacetime_operator(const t2s2_problem* space, int n_t, double t_len, void* stream,
+                                          t2s2_op* out) {
+  if (!space || !out || !space->n || !space->beta) return T2S2_EINVAL;
+  *out = nullptr;
+  if (space->d < 1 || space->d + 1 > T2S2_MAX_D || !(space->eps > 0.0) || !std::isfinite(space->eps))
+    return T2S2_EINVAL;
+  if (n_t < 3 || n_t > T2S2_MAX_N || !(t_len > 0.0) || !std::isfinite(t_len)) return T2S2_EINVAL;
+  for (int k = 0; k < space->d; ++k) {
+    if (space->n[k] < 3 || space->n[k] > T2S2_MAX_N || !std::isfinite(space->beta[k])) return T2S2_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return T2S2_ENODEV;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess || p.major != 10 || p.minor != 3) return T2S2_ENODEV;
+  t2s2_op op = new t2s2_op_s();
+  op->device = dev;
+  op->d = space->d + 1;
+  op->eps = space->eps;
+  op->plain = space->plain_sc;
+  op->dims.resize(op->d);
+  // dimension 0: time on [0, t_len] mapped onto [-1, 1]
+  op->n[0] = n_t;
+  op->m[0] = n_t - 1;
+  op->beta[0] = 2.0 / t_len;
+  if (!build_time_dimension(n_t, op->beta[0], &op->dims[0])) {
+    delete op;
+    return T2S2_EINVAL;
+  }
+  for (int k = 1; k < op->d; ++k) {
+    op->n[k] = space->n[k - 1];
+    op->m[k] = space->n[k - 1] - 2;
+    op->beta[k] = space->beta[k - 1];
+    if (!build_dimension(op->n[k], op->eps, op->beta[k], op->plain, &op->dims[k])) {
+      delete op;
+      return T2S2_EINVAL;
+    }
+  }
+  return upload_operator(op, static_cast<cudaStream_t>(stream), out);
 }
 
 t2s2_status t2s2_op_destroy(t2s2_op op) {

@@ -324,22 +324,9 @@ bool complex_schur(int m, const double* A, std::complex<double>* T, std::complex
   return true;
 }
 
-bool build_dimension(int n, double eps, double beta, int plain, Dim1D* out) {
-  const int N = n - 1, m = n - 2;
-  out->n = n;
-  out->x.assign(n, 0.0);
-  out->eta.assign(m, 0.0);
-  gll_points(N, out->x.data());
-  collocation_points(N, eps, beta, plain, out->eta.data());
-  std::vector<double> R((size_t)m * n), D((size_t)m * n), D2((size_t)m * n);
-  lagrange_matrices(N, out->x.data(), m, out->eta.data(), R.data(), D.data(), D2.data());
-  out->Rt.assign((size_t)m * m, 0.0);
-  out->Lt.assign((size_t)m * m, 0.0);
-  for (int j = 0; j < m; ++j)
-    for (int i = 0; i < m; ++i) {
-      out->Rt[(size_t)j * m + i] = R[(size_t)j * n + i + 1];
-      out->Lt[(size_t)j * m + i] = beta * D[(size_t)j * n + i + 1] - eps * D2[(size_t)j * n + i + 1];
-    }
+// Interpolation inverse, B = Rt^{-1} Lt and B's complex Schur form, from the
+// m x m matrices Rt and Lt already in *out.
+static bool finish_dimension(int m, Dim1D* out) {
   out->Rinv = out->Rt;
   if (!invert(m, out->Rinv.data())) return false;
   out->B.assign((size_t)m * m, 0.0);
@@ -362,6 +349,49 @@ bool build_dimension(int n, double eps, double beta, int plain, Dim1D* out) {
     out->Zi[e] = Z[e].imag();
   }
   return true;
+}
+
+bool build_dimension(int n, double eps, double beta, int plain, Dim1D* out) {
+  const int N = n - 1, m = n - 2;
+  out->n = n;
+  out->x.assign(n, 0.0);
+  out->eta.assign(m, 0.0);
+  gll_points(N, out->x.data());
+  collocation_points(N, eps, beta, plain, out->eta.data());
+  std::vector<double> R((size_t)m * n), D((size_t)m * n), D2((size_t)m * n);
+  lagrange_matrices(N, out->x.data(), m, out->eta.data(), R.data(), D.data(), D2.data());
+  out->Rt.assign((size_t)m * m, 0.0);
+  out->Lt.assign((size_t)m * m, 0.0);
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < m; ++i) {
+      out->Rt[(size_t)j * m + i] = R[(size_t)j * n + i + 1];
+      out->Lt[(size_t)j * m + i] = beta * D[(size_t)j * n + i + 1] - eps * D2[(size_t)j * n + i + 1];
+    }
+  return finish_dimension(m, out);
+}
+
+bool build_time_dimension(int n, double scale, Dim1D* out) {
+  const int N = n - 1, m = n - 1;
+  out->n = n;
+  out->x.assign(n, 0.0);
+  out->eta.assign(m, 0.0);
+  gll_points(N, out->x.data());
+  gauss_points(N, out->eta.data());
+  std::vector<double> R((size_t)m * n), D((size_t)m * n), D2((size_t)m * n);
+  lagrange_matrices(N, out->x.data(), m, out->eta.data(), R.data(), D.data(), D2.data());
+  out->Rt.assign((size_t)m * m, 0.0);
+  out->Lt.assign((size_t)m * m, 0.0);
+  out->R0.assign(m, 0.0);
+  out->L0.assign(m, 0.0);
+  for (int j = 0; j < m; ++j) {
+    for (int i = 0; i < m; ++i) {
+      out->Rt[(size_t)j * m + i] = R[(size_t)j * n + i + 1];
+      out->Lt[(size_t)j * m + i] = scale * D[(size_t)j * n + i + 1];
+    }
+    out->R0[j] = R[(size_t)j * n];
+    out->L0[j] = scale * D[(size_t)j * n];
+  }
+  return finish_dimension(m, out);
 }
 
 }  // namespace t2s2

@@ -6,7 +6,7 @@
 namespace t2s2 {
 
 struct Dim1D {
-  int n = 0;                 // GLL nodes (polynomial degree n-1); m = n-2 interior unknowns
+  int n = 0;                 // GLL nodes (polynomial degree n-1); m = n-2 interior unknowns (n-1 for time)
   std::vector<double> x;     // n GLL points
   std::vector<double> eta;   // m collocation points
   std::vector<double> Rt;    // m x m: l_i(eta_j), interior i
@@ -15,6 +15,7 @@ struct Dim1D {
   std::vector<double> B;     // Rt^{-1} Lt
   std::vector<double> Tr, Ti;  // complex Schur form of B: B = Z T Z^H, T upper triangular
   std::vector<double> Zr, Zi;  // unitary Schur basis
+  std::vector<double> R0, L0;  // time dimension only: the columns of the initial node s = -1
 };
 
 void gll_points(int N, double* x);
@@ -26,5 +27,8 @@ bool invert(int m, double* A);
 void hessenberg(int m, double* B, double* W);
 bool complex_schur(int m, const double* A, std::complex<double>* T, std::complex<double>* Z);
 bool build_dimension(int n, double eps, double beta, int plain, Dim1D* out);
+// The time dimension of the space-time form: m = n-1 unknowns (all GLL nodes
+// but s = -1), collocation at the n-1 Gauss points, Lt = scale * D.
+bool build_time_dimension(int n, double scale, Dim1D* out);
 
 }  // namespace t2s2

@@ -31,9 +31,23 @@ def driver(tmp_path_factory):
 def _run(exe, n, eps, beta, plain):
     out = subprocess.run([exe, str(n), repr(eps), repr(beta), str(int(plain))], check=True,
                          capture_output=True, text=True).stdout
-    d = json.loads(out)
-    m = n - 2
-    return {k: np.array(v).reshape(m, m) for k, v in d.items()}
+    return _shape(json.loads(out), n - 2)
+
+
+def _shape(d, m):
+    return {k: (np.array(v) if k in ("x", "eta", "R0", "L0") else np.array(v).reshape(m, m))
+            for k, v in d.items()}
+
+
+def _check_schur(h, m):
+    T = h["Tr"] + 1j * h["Ti"]
+    Z = h["Zr"] + 1j * h["Zi"]
+    assert np.linalg.norm(Z.conj().T @ Z - np.eye(m)) <= 1e-13 * m
+    assert np.max(np.abs(np.tril(T, -1))) <= 1e-14 * np.linalg.norm(T)
+    assert np.linalg.norm(Z @ T @ Z.conj().T - h["B"]) <= 1e-12 * np.linalg.norm(h["B"])
+    lam = np.diag(T)
+    assert abs(lam.sum() - np.trace(h["B"])) <= 1e-11 * np.linalg.norm(h["B"]) * m
+    assert abs((lam ** 2).sum() - np.trace(h["B"] @ h["B"])) <= 1e-10 * np.linalg.norm(h["B"]) ** 2 * m
 
 
 @pytest.mark.parametrize("n,eps,beta,plain", [(3, 0.1, 1.0, False), (6, 1e-2, 0.8, False),
@@ -50,15 +64,29 @@ def test_dimension_data_and_schur_form(driver, n, eps, beta, plain):
     assert np.max(np.abs(h["Rinv"] @ h["Rt"] - np.eye(m))) <= 1e-11
     B_ref = np.linalg.solve(o.Rt, o.Lt)
     assert np.linalg.norm(h["B"] - B_ref) <= 1e-10 * np.linalg.norm(B_ref)
-    # complex Schur form: Z unitary, T upper triangular, Z T Z^H = B
-    T = h["Tr"] + 1j * h["Ti"]
-    Z = h["Zr"] + 1j * h["Zi"]
-    assert np.linalg.norm(Z.conj().T @ Z - np.eye(m)) <= 1e-13 * m
-    assert np.max(np.abs(np.tril(T, -1))) <= 1e-14 * np.linalg.norm(T)
-    assert np.linalg.norm(Z @ T @ Z.conj().T - h["B"]) <= 1e-12 * np.linalg.norm(h["B"])
-    # the diagonal of T carries B's spectrum: the trace and the sum of squares
-    # of the eigenvalues (trace of B^2) are well conditioned even where single
-    # eigenvalues are not
-    lam = np.diag(T)
-    assert abs(lam.sum() - np.trace(h["B"])) <= 1e-11 * np.linalg.norm(h["B"]) * m
-    assert abs((lam ** 2).sum() - np.trace(h["B"] @ h["B"])) <= 1e-10 * np.linalg.norm(h["B"]) ** 2 * m
+    # complex Schur form: Z unitary, T upper triangular, Z T Z^H = B; the
+    # diagonal of T carries B's spectrum (its trace and the trace of B^2 are
+    # well conditioned even where single eigenvalues are not)
+    _check_schur(h, m)
+
+
+@pytest.mark.parametrize("n,T_len", [(3, 1.0), (7, 2.0), (16, 0.25), (64, 1.0)])
+def test_time_dimension_data_and_schur_form(driver, n, T_len):
+    from oracle import spacetime as ST
+    out = subprocess.run([driver, "time", str(n), repr(2.0 / T_len)], check=True, capture_output=True,
+                         text=True).stdout
+    m = n - 1
+    h = _shape(json.loads(out), m)
+    o = ST.time_op1d(n, T_len)
+    scale = lambda A: max(1.0, np.max(np.abs(A)))
+    assert np.max(np.abs(h["x"] - o.x)) <= 1e-15 and np.max(np.abs(h["eta"] - o.g)) <= 1e-14
+    assert np.max(np.abs(h["Rt"] - o.Rt)) <= 1e-12 * scale(o.Rt)
+    assert np.max(np.abs(h["Lt"] - o.Lt)) <= 1e-11 * scale(o.Lt)
+    assert np.max(np.abs(h["R0"] - o.r0)) <= 1e-12 * scale(o.r0)
+    assert np.max(np.abs(h["L0"] - o.l0)) <= 1e-11 * scale(o.l0)
+    B_ref = np.linalg.solve(o.Rt, o.Lt)
+    assert np.linalg.norm(h["B"] - B_ref) <= 1e-10 * np.linalg.norm(B_ref)
+    _check_schur(h, m)
+    # the inflow-constrained transport operator is stable: its spectrum lies
+    # in the right half plane
+    assert np.min(np.diag(h["Tr"])) > 0.0
