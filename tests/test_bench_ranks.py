@@ -63,3 +63,33 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     args = argparse.Namespace(steps=5, warmup=3, cpu_budget=20.0, gpus=2, impl="reference")
     assert bench.run_reference(args) == 0
+
+
+def test_clock_lines_median_max_and_reasons():
+    ok = "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    cap = "0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active"
+    hot = "0, 1500, 2070, 1300.0, 0x8, Active, Not Active, Not Active, Not Active"
+    r = bench.parse_clock_lines([ok, cap, ok])
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    r = bench.parse_clock_lines([ok, hot, "garbage", "0, [N/A], 2070, 1, 0, a, b, c, d"])
+    assert r["reasons"] == ["hw_slowdown"] and r["samples"] == 2 and r["sm_mhz"] == 2070.0
+    assert bench.parse_clock_lines([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_clock_sampler_flow_with_a_fake_nvidia_smi(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi that prints one sample every 20 ms: the sampler
+    # drops the sample taken before the region and parses the rest
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\nwhile true; do\n"
+                    "echo '0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "sleep 0.02\ndone\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    import time
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.skip >= 1          # the region starts once the sampler is live
+    time.sleep(0.2)
+    r = s.stop()
+    assert r["sm_mhz"] == 2070.0 and r["reasons"] == [] and r["samples"] >= 3
+    assert r["samples_in_region"] >= 3
