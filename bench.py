@@ -241,6 +241,13 @@ REF_TOTAL_S = 330.0       # bound on the timed reference steps together
 REF_WARMUP_S = 1.0        # per untimed reference step
 
 
+def reference_budgets(cpu_budget: float, steps: int):
+    """Seconds of oracle work per timed and per warm-up reference step."""
+    k = max(1, steps)
+    step = max(cpu_budget / k, min(REF_STEP_FLOOR_S, REF_TOTAL_S / k))
+    return step, min(step, REF_WARMUP_S)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -253,9 +260,9 @@ def run_reference(args):
     # get a short sample.  A timed step is given a minute (the oracle's first
     # sweep takes about 20 s on 16 Arm cores) while the timed steps together
     # stay within about five and a half minutes.
-    step_budget = max(args.cpu_budget / max(1, args.steps), min(REF_STEP_FLOOR_S, REF_TOTAL_S / max(1, args.steps)))
+    step_budget, warm_budget = reference_budgets(args.cpu_budget, args.steps)
     for i in range(args.warmup + args.steps):
-        budget = step_budget if i >= args.warmup else min(step_budget, REF_WARMUP_S)
+        budget = step_budget if i >= args.warmup else warm_budget
         dt, sweeps, conv, res = cpu_baseline_sample("config1()", budget)
         if i >= args.warmup:
             times.append((dt, sweeps, conv, res))

@@ -93,3 +93,14 @@ def test_clock_sampler_flow_with_a_fake_nvidia_smi(tmp_path, monkeypatch):
     r = s.stop()
     assert r["sm_mhz"] == 2070.0 and r["reasons"] == [] and r["samples"] >= 3
     assert r["samples_in_region"] >= 3
+
+
+def test_reference_budgets_stay_bounded():
+    # default K = 5: a minute per timed step, five minutes in all
+    assert bench.reference_budgets(20.0, 5) == (60.0, 1.0)
+    # many steps: the timed steps together stay within REF_TOTAL_S
+    for k in (10, 50, 200, 1000):
+        step, warm = bench.reference_budgets(20.0, k)
+        assert step * k <= max(bench.REF_TOTAL_S, 20.0) + 1e-9 and warm <= 1.0
+    # a larger --cpu-budget is honoured
+    assert bench.reference_budgets(600.0, 5)[0] == 120.0
