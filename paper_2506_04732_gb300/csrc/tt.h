@@ -65,7 +65,6 @@ t2s2_status tt_copy(Ctx& cx, const DevTT& src, DevTT& dst);
 t2s2_status tt_axpby(Ctx& cx, double alpha, const DevTT& x, double beta, const DevTT& y, DevTT& z);
 // In place: cores 1..d-1 right-orthonormal (rows), weight in core 0.
 t2s2_status tt_orth_right(Ctx& cx, DevTT& x);
-// In place: cores 0..d-2 left-orthonormal (columns), weight in core d-1.
 // In place rounding with ||x - rndg(x)|| <= tol ||x|| (cap rmax <= 0: none).
 t2s2_status tt_round(Ctx& cx, DevTT& x, double tol, int rmax);
 // ||x||_F of a TT already right-orthogonalised (norm of core 0).
