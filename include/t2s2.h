@@ -147,6 +147,19 @@ t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op*
 t2s2_status t2s2_build_spacetime_operator(const t2s2_problem* space, int n_t, double t_len, void* stream,
                                           t2s2_op* out);
 
+/*
+ * Right-hand side of a space-time solve with the initial condition lifted:
+ *     out = round(b - L0 x (M_x u0) - R0 x (A_x u0), tol, rmax),
+ * where b is the source on the space-time collocation grid (d + 1 cores,
+ * time first), u0 the initial condition on the spatial interior GLL grid (d
+ * cores), M_x and A_x the spatial mass matrix and operator, and L0, R0 the
+ * columns of the time matrices at the initial node s = -1.  op must come from
+ * t2s2_build_spacetime_operator.  Errors: T2S2_EINVAL for another operator or
+ * mismatched shapes; T2S2_ENOMEM if out is too small.
+ */
+t2s2_status t2s2_spacetime_rhs(t2s2_op op, const t2s2_tt* b, const t2s2_tt* u0, t2s2_tt* out, double tol,
+                               int rmax, void* stream);
+
 /* Free an operator and its workspace.  NULL is accepted. */
 t2s2_status t2s2_op_destroy(t2s2_op op);
 

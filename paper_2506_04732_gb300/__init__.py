@@ -23,7 +23,7 @@ __all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REF
            "t2s2_device_count", "t2s2_strerror", "t2s2_gemm", "WarmStartNet", "t2s2_apply_batched",
            "t2s2_autotune_report", "t2s2_kernel_launches", "t2s2_trace",
            "t2s2_trace_read", "TRACE_FAMILIES", "lib_path", "t2s2_dim_matrices", "DIM_SPACE",
-           "t2s2_build_spacetime_operator",
+           "t2s2_build_spacetime_operator", "t2s2_spacetime_rhs",
            "DIM_SPACE_PLAIN", "DIM_TIME"]
 
 FP64, FP32_REFINE, TF32_REFINE, BF16_REFINE = 0, 1, 2, 3
@@ -81,6 +81,8 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_void_p)]),
     "t2s2_build_spacetime_operator": (ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.c_int, ctypes.c_double,
                                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "t2s2_spacetime_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.POINTER(_TT),
+                                          ctypes.POINTER(_TT), ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
     "t2s2_op_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "t2s2_dim_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
                           + [ctypes.c_void_p] * 6),
@@ -480,6 +482,17 @@ def t2s2_build_spacetime_operator(d, n, beta, eps, n_t, t_len, plain_sc=False, s
                                              ctypes.byref(h)), "t2s2_build_spacetime_operator")
     return Operator(h, d + 1, [int(n_t)] + n, [2.0 / float(t_len)] + beta, float(eps), bool(plain_sc),
                     m=[int(n_t) - 1] + [v - 2 for v in n])
+
+
+def t2s2_spacetime_rhs(op: Operator, b: "TT", u0: "TT", out: "TT", tol: float, rmax: int, stream=None):
+    """out = round(b - L0 (x) M_x u0 - R0 (x) A_x u0): the space-time right-hand
+    side with the initial condition u0 lifted (op from
+    t2s2_build_spacetime_operator)."""
+    sb, su, so = b._struct(), u0._struct(), out._struct()
+    _check(load().t2s2_spacetime_rhs(op.handle, ctypes.byref(sb), ctypes.byref(su), ctypes.byref(so),
+                                     float(tol), int(rmax), _stream_handle(stream)), "t2s2_spacetime_rhs")
+    out._sync_ranks()
+    return out
 
 
 class TT:

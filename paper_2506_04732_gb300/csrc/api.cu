@@ -568,6 +568,79 @@ t2s2_status t2s2_apply(t2s2_op op, const t2s2_tt* x, t2s2_tt* y, double c_mass, 
   return unbind_tt(cx, dy, y);
 }
 
+t2s2_status t2s2_spacetime_rhs(t2s2_op op, const t2s2_tt* b, const t2s2_tt* u0, t2s2_tt* out, double tol,
+                               int rmax, void* stream) {
+  if (!op || !b || !u0 || !out || !(tol >= 0.0)) return T2S2_EINVAL;
+  if (op->d < 2 || op->dims[0].R0.empty()) return T2S2_EINVAL;  // not a space-time operator
+  T2S2_TRY(check_tt(op, b));
+  if (!out->r || !out->cores || !out->cap || out->d != op->d) return T2S2_EINVAL;
+  const int ds = op->d - 1, mt = op->m[0];
+  if (!u0->r || !u0->cores || !u0->cap || !u0->m || u0->d != ds || u0->r[0] != 1 || u0->r[ds] != 1)
+    return T2S2_EINVAL;
+  if (u0->loc != T2S2_DEVICE && u0->loc != T2S2_HOST) return T2S2_EINVAL;
+  for (int k = 0; k < ds; ++k) {
+    if (u0->m[k] != op->m[k + 1] || u0->r[k + 1] < 1 || !u0->cores[k]) return T2S2_EINVAL;
+    if ((size_t)u0->r[k] * u0->m[k] * u0->r[k + 1] > u0->cap[k]) return T2S2_ENOMEM;
+  }
+  size_t mc = max_core(b);
+  T2S2_TRY(ensure_arena(op, tt_bytes(b) * 4 + tt_bytes(u0) * 16 + tt_bytes(out) + 2 * mt * sizeof(double) +
+                                12 * mc * sizeof(double) + ((size_t)16 << 20)));
+  Ctx cx = make_ctx(op, stream);
+  DevTT db, du;
+  T2S2_TRY(bind_tt(cx, b, db, true));
+  T2S2_TRY(bind_tt(cx, u0, du, true));
+  // M_x u0 (v = 0) and A_x u0 (v = 1): the rank-2 apply over dimensions 1..d
+  DevTT y[2];
+  int ry[T2S2_MAX_D + 1];
+  for (int k = 0; k <= ds; ++k) ry[k] = (k == 0 || k == ds) ? 1 : 2 * du.r[k];
+  for (int v = 0; v < 2; ++v) {
+    T2S2_TRY(tt_alloc(cx, y[v], ds, du.m, ry, 0));
+    ApplyBatch ab;
+    ab.ncores = ds;
+    for (int k = 0; k < ds; ++k) {
+      ApplyCore& c = ab.c[k];
+      c.S = op->dRt[k + 1];
+      c.L = op->dLt[k + 1];
+      c.X = du.c[k];
+      c.Y = y[v].c[k];
+      c.ra = du.r[k];
+      c.m = du.m[k];
+      c.rb = du.r[k + 1];
+      c.kind = (ds == 1) ? kApplySingle : (k == 0 ? kApplyFirst : (k == ds - 1 ? kApplyLast : kApplyMiddle));
+      c.g_op = (v == 0) ? 0.0 : 1.0;
+      c.g_mass = (k == 0 && v == 0) ? 1.0 : 0.0;
+    }
+    T2S2_TRY(apply_fp64(ab, cx.st));
+  }
+  // the columns of the initial node s = -1 as rank-1 time cores in front
+  double* cols = aget<double>(cx, 2 * (size_t)mt);
+  if (!cols) return T2S2_ENOMEM;
+  T2S2_CUDA_TRY(cudaMemcpyAsync(cols, op->dims[0].L0.data(), sizeof(double) * mt, cudaMemcpyHostToDevice, cx.st));
+  T2S2_CUDA_TRY(cudaMemcpyAsync(cols + mt, op->dims[0].R0.data(), sizeof(double) * mt, cudaMemcpyHostToDevice,
+                                cx.st));
+  DevTT t[2];
+  for (int v = 0; v < 2; ++v) {
+    t[v].d = op->d;
+    t[v].r[0] = 1;
+    t[v].m[0] = mt;
+    t[v].c[0] = cols + v * (size_t)mt;
+    t[v].cap[0] = mt;
+    for (int k = 0; k < ds; ++k) {
+      t[v].r[k + 1] = y[v].r[k];
+      t[v].m[k + 1] = y[v].m[k];
+      t[v].c[k + 1] = y[v].c[k];
+      t[v].cap[k + 1] = y[v].cap[k];
+    }
+    t[v].r[op->d] = 1;
+  }
+  // b_st = b - L0 (x) M_x u0 - R0 (x) A_x u0, rounded
+  DevTT s1, s2;
+  T2S2_TRY(tt_axpby(cx, 1.0, db, -1.0, t[0], s1));
+  T2S2_TRY(tt_axpby(cx, 1.0, s1, -1.0, t[1], s2));
+  T2S2_TRY(tt_round(cx, s2, tol, rmax));
+  return unbind_tt(cx, s2, out);
+}
+
 t2s2_status t2s2_gemm(t2s2_op op, int M, int N, int K, int tA, int tB, double alpha, const double* A,
                       long lda, long sA, const double* B, long ldb, long sB, double beta, double* C,
                       long ldc, long sC, int batch, t2s2_precision prec, void* stream) {
