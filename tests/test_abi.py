@@ -41,3 +41,35 @@ def test_no_device_reports_cleanly():
         pytest.skip("a GPU is present")
     import paper_2506_04732_gb300 as T
     assert T.t2s2_device_count() == 0
+
+
+def test_operator_builders_validate_before_touching_a_device():
+    # bad arguments are rejected up front; good ones reach the device check,
+    # which fails cleanly here (no device, no CPU fallback).  The C entry
+    # points are called directly with a NULL stream.
+    import ctypes
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2506_04732_gb300 as T
+    lib = T.load()
+    EINVAL, ENODEV = 1, 7
+
+    def build(d, n, beta, eps, n_t=None, t_len=None):
+        prob = T._Problem(d, (ctypes.c_int * d)(*n), (ctypes.c_double * d)(*beta), float(eps), 0)
+        h = ctypes.c_void_p()
+        if n_t is None:
+            return lib.t2s2_build_operator(ctypes.byref(prob), None, ctypes.byref(h))
+        return lib.t2s2_build_spacetime_operator(ctypes.byref(prob), int(n_t), float(t_len), None,
+                                                 ctypes.byref(h))
+
+    good = dict(d=2, n=[8, 8], beta=[0.6, 0.8], eps=1e-2)
+    for kw in [dict(n=[2, 8]), dict(n=[8, 129]), dict(eps=0.0), dict(beta=[1.0, float("nan")])]:
+        args = {**good, **kw}
+        assert build(**args) == EINVAL, kw
+        assert build(**args, n_t=6, t_len=1.0) == EINVAL, kw
+    for n_t, t_len in [(2, 1.0), (129, 1.0), (6, 0.0), (6, -1.0), (6, float("inf"))]:
+        assert build(**good, n_t=n_t, t_len=t_len) == EINVAL, (n_t, t_len)
+    assert build(16, [8] * 16, [0.25] * 16, 1e-2, n_t=6, t_len=1.0) == EINVAL   # 17 dimensions
+    assert build(**good) == ENODEV
+    assert build(**good, n_t=6, t_len=1.0) == ENODEV
