@@ -50,6 +50,8 @@ from functools import reduce
 
 import numpy as np
 
+from workloads import SpaceTimeProblem  # noqa: F401  (parameters only)
+
 from . import operator as O
 from . import tt as T
 from .collocation import lagrange_matrices
@@ -79,17 +81,6 @@ def time_op1d(n: int, T_len: float) -> TimeOp1D:
     R, D, _ = lagrange_matrices(x, g)
     scale = 2.0 / T_len
     return TimeOp1D(n, x, g, R[:, 1:].copy(), scale * D[:, 1:], R[:, 0].copy(), scale * D[:, 0], T_len)
-
-
-@dataclass
-class SpaceTimeProblem:
-    """A space-time workload: the spatial problem (its ``terms`` give the
-    spatial factors), one time factor per term, n_t time nodes and the length
-    T of the time interval.  u*(x, s) = sum_t coef_t phi_t(s) prod_k phi_{t,k}(x_k)."""
-    space: object
-    time_factors: tuple
-    n_t: int
-    T: float
 
 
 def build(st: SpaceTimeProblem):

@@ -135,3 +135,19 @@ def test_amen_on_the_space_time_operator_reaches_the_dense_solution():
     assert res <= 1e-12
     ud = ST.dense_solve(st, top, ops)
     assert np.linalg.norm(T.full(x) - ud) <= 1e-10 * np.linalg.norm(ud)
+
+
+def test_spacetime_workload_is_seeded_and_resolved():
+    a, b = W.config_spacetime(), W.config_spacetime()
+    assert np.array_equal(a.space.beta, b.space.beta) and a.space.terms == b.space.terms
+    assert not np.array_equal(W.config_spacetime(seed=7).space.beta, a.space.beta)
+    # a reduced instance of the same recipe: the discrete space-time solution
+    # approaches the manufactured one as the grids grow (spectral accuracy)
+    errs = []
+    for n, n_t in ((8, 6), (16, 12)):
+        st = W.config_spacetime(d=2, n=n, n_t=n_t, ratio=0.05)
+        top, ops = ST.build(st)
+        u = ST.dense_solve(st, top, ops)
+        want = T.full(ST.solution_tt(st, top, ops))
+        errs.append(np.max(np.abs(u - want)) / np.max(np.abs(want)))
+    assert errs[1] < 1e-5 * errs[0] and errs[1] < 1e-7

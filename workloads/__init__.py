@@ -24,8 +24,8 @@ import math
 
 import numpy as np
 
-__all__ = ["Factor", "Term", "Problem", "config0", "config1", "config2",
-           "config3", "config4", "random_tt", "sine_problem", "random_unit_vector",
+__all__ = ["Factor", "Term", "Problem", "SpaceTimeProblem", "config0", "config1", "config2",
+           "config3", "config4", "config_spacetime", "random_tt", "sine_problem", "random_unit_vector",
            "EDGE_LENGTH"]
 
 EDGE_LENGTH = 2.0
@@ -234,6 +234,31 @@ def warm_features(p: Problem) -> np.ndarray:
     f = np.concatenate([[math.log10(ratio) + 3.0], b6, (a - 0.75) * 4.0, w - 2.0, 2.0 * mu])
     assert f.size == WARM_IN_DIM
     return f.astype(np.float32)
+
+
+@dataclass
+class SpaceTimeProblem:
+    """A workload of the unified space-time form: the spatial problem (its
+    ``terms`` give the spatial factors), one time factor per term, n_t time
+    nodes and the length T of the time interval.
+    u*(x, s) = sum_t coef_t phi_t(s) prod_k phi_{t,k}(x_k), s in [-1, 1]."""
+    space: Problem
+    time_factors: tuple
+    n_t: int
+    T: float
+
+
+def config_spacetime(seed: int = 6, d: int = 5, n: int = 32, n_t: int = 24, T: float = 1.0,
+                     ratio: float = 1e-3, tol: float = 1e-8, rmax: int = 20) -> SpaceTimeProblem:
+    """Space-time workload (time as the first collocated dimension): two
+    separable sine terms in space, growing and decaying exponentials in time."""
+    rng = np.random.default_rng(seed)
+    beta = random_unit_vector(d, rng)
+    terms = [Term(1.0, tuple(Factor("sine", m=int(rng.integers(1, 4))) for _ in range(d))),
+             Term(0.5, tuple(Factor("sine", m=int(rng.integers(1, 4))) for _ in range(d)))]
+    sp = Problem(f"space-time d={d}+1 n={n} n_t={n_t} ratio={ratio:g}", d, (n,) * d, beta,
+                 ratio * EDGE_LENGTH, terms, tol=tol, rmax=rmax, max_sweeps=30, seed=seed)
+    return SpaceTimeProblem(sp, (Factor("exp", m=1.0), Factor("exp", m=-0.7)), n_t, T)
 
 
 def sine_problem(d: int, n: int, ratio: float, seed: int = 5, tol: float = 1e-8,
