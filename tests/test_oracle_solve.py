@@ -52,6 +52,56 @@ def test_amen_uses_gmres_path_for_large_local_systems():
     assert np.linalg.norm(T.full(x) - xd) <= 1e-6 * np.linalg.norm(xd)
 
 
+@pytest.mark.parametrize("plain", [False, True])
+def test_node_form_matches_dense_lu(plain):
+    # AMEn in the node-to-node form M^-1 A reaches the dense LU solution of the
+    # original collocation system, and reports that system's residual
+    p = W.config1(d=3, n=10, ratio=0.01)
+    p.plain_sc = plain
+    ops = O.build(p)
+    b = O.source_tt(p, ops)
+    x, res, _ = S.solve_collocation(ops, b, _ones(ops), 1e-11, 20)
+    xd = S.dense_solve(ops, b)
+    assert res <= 1e-11
+    assert np.linalg.norm(T.full(x) - xd) <= 1e-8 * np.linalg.norm(xd)
+    r = O.dense(ops) @ T.full(x).ravel() - T.full(b).ravel()
+    assert abs(np.linalg.norm(r) / np.linalg.norm(T.full(b)) - res) < 1e-13
+
+
+def test_node_form_with_mass_term_matches_dense():
+    p = W.config0()
+    ops = O.build(p)
+    b = O.source_tt(p, ops)
+    x, res, _ = S.solve_collocation(ops, b, _ones(ops), 1e-12, 16, c_mass=2.5, c_op=0.3)
+    xd = S.dense_solve(ops, b, 2.5, 0.3)
+    assert res <= 1e-12
+    assert np.linalg.norm(T.full(x) - xd) <= 1e-10 * np.linalg.norm(xd)
+
+
+def test_node_form_operator_is_the_kronecker_sum_of_b():
+    # M^-1 A = sum_k I (x) B_k (x) I with B_k = Rt_k^-1 Lt_k, densely
+    p = W.config1(d=3, n=6, ratio=0.02)
+    ops = O.build(p)
+    nops = [S._NodeOp(o) for o in ops]
+    M = O.dense(ops, 1.0, 0.0)
+    want = np.linalg.solve(M, O.dense(ops, 0.0, 1.0))
+    assert np.allclose(T.ttm_full(O.ttm_cores(nops)), want, rtol=0, atol=1e-10 * np.max(np.abs(want)))
+
+
+def test_headline_problem_completes_in_the_node_form():
+    # d = 6, n = 32 (the headline workload): one or two sweeps reach 1e-8 in the
+    # residual of the original collocation system, at ranks <= rmax + kick
+    p = W.config1()
+    ops = O.build(p)
+    b = O.source_tt(p, ops)
+    x, res, sweeps = S.solve_collocation(ops, b, _ones(ops), p.tol, p.rmax, max_sweeps=2)
+    assert res <= p.tol and sweeps <= 2
+    assert max(T.ranks(x)) <= p.rmax + 8
+    # the discrete solution is the spectrally accurate one
+    us = O.solution_tt(p, ops)
+    assert T.diff_norm(x, us) <= 1e-6 * T.norm(us)
+
+
 def test_cn_step_matches_dense():
     p = W.config2(d=2, n=10, dt=0.02)
     ops = O.build(p)

@@ -137,6 +137,19 @@ def test_amen_on_the_space_time_operator_reaches_the_dense_solution():
     assert np.linalg.norm(T.full(x) - ud) <= 1e-10 * np.linalg.norm(ud)
 
 
+def test_node_form_amen_on_the_space_time_operator_reaches_the_dense_solution():
+    fx = W.Factor("sine", m=1)
+    sp = _space(2, 7, 0.01, [W.Term(1.0, (fx, W.Factor("sine", m=2)))])
+    st = ST.SpaceTimeProblem(sp, (W.Factor("exp", m=-0.5),), 6, 2.0)
+    top, ops = ST.build(st)
+    b = ST.lifted_source_tt(st, top, ops)
+    x0 = [np.ones((1, c.shape[1], 1)) for c in b]
+    x, res, _ = S.solve_collocation([top] + list(ops), b, x0, 1e-12, 20)
+    assert res <= 1e-12
+    ud = ST.dense_solve(st, top, ops)
+    assert np.linalg.norm(T.full(x) - ud) <= 1e-10 * np.linalg.norm(ud)
+
+
 def test_spacetime_workload_is_seeded_and_resolved():
     a, b = W.config_spacetime(), W.config_spacetime()
     assert np.array_equal(a.space.beta, b.space.beta) and a.space.terms == b.space.terms
