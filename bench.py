@@ -185,32 +185,28 @@ from oracle import operator as O
 from oracle import solve as S
 p = W.{cfg}
 ops = O.build(p)
-A = O.ttm_cores(ops)
 b = O.source_tt(p, ops)
-x = [np.ones((1, n - 2, 1)) for n in p.n]
-t0 = time.perf_counter()
-for k in range(p.max_sweeps):
-    x, res, _ = S.amen_solve(A, b, x, p.tol, p.rmax, max_sweeps=1)
-    print(json.dumps({{"sweeps": k + 1, "t": time.perf_counter() - t0, "res": res}}), flush=True)
-    if res <= p.tol:
-        break
+for i in range({count}):
+    x0 = [np.ones((1, n - 2, 1)) for n in p.n]
+    t0 = time.perf_counter()
+    x, res, sweeps = S.solve_collocation(ops, b, x0, p.tol, p.rmax, max_sweeps=p.max_sweeps)
+    t = time.perf_counter() - t0
+    print(json.dumps({{"i": i, "t": t, "res": res, "sweeps": sweeps}}), flush=True)
 """
 
 
-def cpu_baseline_sample(problem_expr, budget_s):
-    """Time the FP64 oracle's solve on the host cores, bounded by a hard budget.
+def oracle_solves(problem_expr, count, budget_s):
+    """Complete FP64 oracle solves of a workload on the host cores.
 
-    The oracle runs sweep by sweep in a child process that is stopped once the
-    budget is spent; the sample is the sweeps completed by then.  The rate per
-    solve scales completed sweeps by the sweeps a solve needs -- optimistic for
-    the oracle, whose later sweeps (higher ranks) are its most expensive.
-    Returns (seconds, sweeps done, converged, last residual).
+    A child process builds the oracle's operator and source once and then runs
+    up to `count` complete solves from the rank-1 start (oracle.solve.
+    solve_collocation: AMEn to the workload's tolerance), each timed on its
+    own; it is stopped once `budget_s` seconds have passed.  Returns one
+    record per finished solve: {"t": seconds, "res": residual, "sweeps": n}.
     """
     import subprocess as sp
-    code = _ORACLE_CHILD.format(root=ROOT, cfg=problem_expr)
-    t0 = time.perf_counter()
+    code = _ORACLE_CHILD.format(root=ROOT, cfg=problem_expr, count=int(count))
     proc = sp.Popen([sys.executable, "-c", code], stdout=sp.PIPE, stderr=sp.DEVNULL, text=True)
-    last = None
     lines = []
 
     def reader():
@@ -225,29 +221,32 @@ def cpu_baseline_sample(problem_expr, budget_s):
         proc.kill()
         proc.wait()
     th.join(timeout=5)
+    out = []
     for ln in lines:
         try:
-            last = json.loads(ln)
+            out.append(json.loads(ln))
         except ValueError:
             pass
-    if not last:
-        return time.perf_counter() - t0, 0, False, None
-    conv = last["res"] <= 1e-8
-    # an unfinished solve is charged the whole time it ran, not the time of its
-    # last completed sweep (the next sweep may cost far more)
-    return (last["t"] if conv else max(last["t"], time.perf_counter() - t0)), last["sweeps"], conv, last["res"]
+    return out
 
 
-REF_STEP_FLOOR_S = 60.0   # per timed reference step, when the run stays bounded
-REF_TOTAL_S = 330.0       # bound on the timed reference steps together
-REF_WARMUP_S = 1.0        # per untimed reference step
+def cpu_baseline_sample(problem_expr, budget_s, tol):
+    """The oracle's rate on a bounded sample: complete solves within budget_s
+    (the first, which pays the process's warm-up, is left out when others
+    finished).  Returns (solves/s or 0, description)."""
+    recs = oracle_solves(problem_expr, 1000, budget_s)
+    timed = recs[1:] if len(recs) > 1 else recs
+    conv = [r for r in timed if r["res"] <= tol]
+    tot = sum(r["t"] for r in timed)
+    if not conv or tot <= 0:
+        return 0.0, f"no complete oracle solve within {budget_s:.0f} s"
+    return len(conv) / tot, (f"{len(conv)} complete oracle solves to {tol:g} (AMEn in the node-to-node form, "
+                             f"{max(r['sweeps'] for r in conv)} sweep(s), residual <= "
+                             f"{max(r['res'] for r in conv):.1e}), {tot / len(timed):.2f} s each, "
+                             f"within a {budget_s:.0f} s budget; the process's first solve is untimed")
 
 
-def reference_budgets(cpu_budget: float, steps: int):
-    """Seconds of oracle work per timed and per warm-up reference step."""
-    k = max(1, steps)
-    step = max(cpu_budget / k, min(REF_STEP_FLOOR_S, REF_TOTAL_S / k))
-    return step, min(step, REF_WARMUP_S)
+REF_TOTAL_S = 600.0       # bound on the whole reference run
 
 
 def run_reference(args):
@@ -256,46 +255,28 @@ def run_reference(args):
         return 0
     import workloads as W
     p = W.config1()
-    times = []
-    info = None
-    # A fresh oracle process per step has nothing to warm up, so warm-up steps
-    # get a short sample.  A timed step is given a minute (the oracle's first
-    # sweep takes about 20 s on 16 Arm cores) while the timed steps together
-    # stay within about five and a half minutes.
-    step_budget, warm_budget = reference_budgets(args.cpu_budget, args.steps)
-    for i in range(args.warmup + args.steps):
-        budget = step_budget if i >= args.warmup else warm_budget
-        dt, sweeps, conv, res = cpu_baseline_sample("config1()", budget)
-        if i >= args.warmup:
-            times.append((dt, sweeps, conv, res))
-        info = (dt, sweeps, conv, res)
-    # rate: solves/sec, a partial solve counted as sweeps_done / sweeps_needed
-    need = SWEEPS_NEEDED_HINT
-    tot = sum(t[0] for t in times)
-    solves = sum(min(1.0, t[1] / need) for t in times)
-    value = solves / tot if tot > 0 else 0.0
+    # one child process runs the warm-up solves and then the K timed ones, each
+    # step one complete oracle solve of the headline workload
+    recs = oracle_solves("config1()", args.warmup + args.steps, REF_TOTAL_S)
+    timed = recs[args.warmup:]
+    conv = [r for r in timed if r["res"] <= p.tol]
+    tot = sum(r["t"] for r in timed)
+    value = len(conv) / tot if tot > 0 else 0.0
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value if value else None,
+            "steps": len(timed), "warmup": min(args.warmup, len(recs)),
+            "ms_per_step": 1e3 * tot / len(timed) if timed else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": p.name, "d": p.d, "n": p.n[0], "tol": p.tol,
-                                             "rmax": p.rmax},
+                                             "rmax": p.rmax, "steps_requested": args.steps,
+                                             "sweeps": [r["sweeps"] for r in timed],
+                                             "residuals": [r["res"] for r in timed]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"oracle AMEn sweeps within {step_budget:.0f} s per step, "
-                                       f"scaled by {need} sweeps per solve: an upper bound on the oracle's "
-                                       f"rate (it needs more sweeps, the later ones minutes each)"},
+                             "sample": f"{len(timed)} timed complete oracle solves (FP64 numpy, AMEn in the "
+                                       f"node-to-node form to {p.tol:g}) after {args.warmup} untimed ones"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
-
-
-# A lower bound on the sweeps the oracle's alternating solver needs on the
-# d=6, n=32 problem to reach 1e-8, used to scale a partial sample: on 8 x86
-# cores its residual was 0.48 after one sweep (1.2 s) and 1.6e-2 after two
-# (475 s; local systems above 4096 unknowns go to unpreconditioned GMRES).
-# Crediting each completed sweep with half a solve therefore makes the rate
-# reported for the oracle an upper bound on its real rate.
-SWEEPS_NEEDED_HINT = 2
 
 
 def run_batched(args, T, P, W, torch):
@@ -315,7 +296,7 @@ def run_batched(args, T, P, W, torch):
     for _ in range(max(1, args.warmup)):
         T.t2s2_solve_batched(ops, bs, fresh(), 1e-8, 16, 50, workers=args.workers, allow_noconv=True)
     torch.cuda.synchronize()
-    times, infos = [], None
+    times, infos, solved = [], None, 0
     for _ in range(args.steps):
         xs = fresh()
         torch.cuda.synchronize()
@@ -323,7 +304,9 @@ def run_batched(args, T, P, W, torch):
         infos = T.t2s2_solve_batched(ops, bs, xs, 1e-8, 16, 50, workers=args.workers, allow_noconv=True)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
-    batched = args.instances * len(times) / sum(times)
+        solved += sum(1 for inf in infos if inf.residual <= 1e-8)
+    # only solves that reached the tolerance count towards the rate
+    batched = solved / sum(times)
     # sequential plain solves of a subset, one instance after the other
     nseq = min(32, args.instances)
     xs = fresh()
@@ -339,7 +322,8 @@ def run_batched(args, T, P, W, torch):
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.instances} instances d=5 n in {{16,24,32,48}}",
-                       "workers": args.workers, "converged": conv,
+                       "workers": args.workers, "converged": conv, "instances": args.instances,
+                       "unconverged": [i for i, inf in enumerate(infos) if inf.residual > 1e-8],
                        "max_sweeps": max(inf.sweeps for inf in infos),
                        "sequential_solves_per_s": seq, "sequential_sample": nseq}}
     print(json.dumps(line))
@@ -406,6 +390,7 @@ def run_spacetime(args, T, P, W, torch):
     clocks = ClockSampler(0)
     clocks.start()
     total = 0.0
+    infos = []
     for _ in range(args.steps):
         reset_x()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -418,11 +403,14 @@ def run_spacetime(args, T, P, W, torch):
     clk = clocks.stop()
     ms = total / args.steps
     last = infos[-1]
+    # only timed solves that reached the tolerance count towards the rate
+    solved = sum(1 for inf in infos if inf.residual <= sp.tol)
     line = {"metric": "space-time solves/sec to rel. residual 1e-8 (d=5+t, n=32, n_t=24)",
-            "value": 1e3 / ms, "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "value": 1e3 * solved / total if total > 0 else 0.0, "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": sp.name, "residual": last.residual, "sweeps": last.sweeps,
+            "config": {"workload": sp.name, "converged": solved, "timed_solves": len(infos),
+                       "residual": last.residual, "sweeps": last.sweeps,
                        "max_rank": last.max_rank, "status": last.status, "rhs_ranks": rhs.r},
             "clocks": clk}
     print(json.dumps(line))
@@ -751,13 +739,8 @@ def main():
 
     cpu = None
     if rank == 0 and args.cpu_budget > 0:
-        dt, sweeps, conv, res = cpu_baseline_sample("config1()", args.cpu_budget)
-        solves = min(1.0, sweeps / SWEEPS_NEEDED_HINT) if not conv else 1.0
-        cpu = {"value": solves / dt if dt > 0 and sweeps else 0.0, "unit": UNIT, "cores": os.cpu_count(),
-               "kind": "oracle",
-               "sample": f"{sweeps} oracle AMEn sweeps completed within a {args.cpu_budget:.0f} s budget "
-                         f"({dt:.1f} s)"
-                         f"{' (converged)' if conv else f'; rate scaled by {SWEEPS_NEEDED_HINT} sweeps per solve, an upper bound (the oracle needs more)'}"}
+        rate, sample = cpu_baseline_sample("config1()", args.cpu_budget, p.tol)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

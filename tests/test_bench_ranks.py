@@ -95,12 +95,15 @@ def test_clock_sampler_flow_with_a_fake_nvidia_smi(tmp_path, monkeypatch):
     assert r["samples_in_region"] >= 3
 
 
-def test_reference_budgets_stay_bounded():
-    # default K = 5: a minute per timed step, five minutes in all
-    assert bench.reference_budgets(20.0, 5) == (60.0, 1.0)
-    # many steps: the timed steps together stay within REF_TOTAL_S
-    for k in (10, 50, 200, 1000):
-        step, warm = bench.reference_budgets(20.0, k)
-        assert step * k <= max(bench.REF_TOTAL_S, 20.0) + 1e-9 and warm <= 1.0
-    # a larger --cpu-budget is honoured
-    assert bench.reference_budgets(600.0, 5)[0] == 120.0
+def test_oracle_solves_are_complete_and_timed_one_by_one():
+    # the reference arm's steps: whole oracle solves in a child process, each
+    # timed on its own and reaching the workload's tolerance
+    recs = bench.oracle_solves("config0()", 2, 120.0)
+    assert len(recs) == 2
+    for r in recs:
+        assert r["res"] <= 1e-12 and r["sweeps"] >= 1 and r["t"] > 0
+
+
+def test_oracle_solves_stop_at_the_budget():
+    # a budget shorter than one solve ends the child with nothing finished
+    assert bench.oracle_solves("config1()", 5, 0.5) == []
