@@ -79,6 +79,17 @@ t2s2_status check_tt(t2s2_op op, const t2s2_tt* t) {
   return T2S2_OK;
 }
 
+// An output TT: pointers present, the operator's d and mode sizes, a known
+// location.  Its ranks are written, not read.
+t2s2_status check_out_tt(t2s2_op op, const t2s2_tt* t) {
+  if (!t || !t->r || !t->cores || !t->cap || !t->m) return T2S2_EINVAL;
+  if (t->d != op->d) return T2S2_EINVAL;
+  if (t->loc != T2S2_DEVICE && t->loc != T2S2_HOST) return T2S2_EINVAL;
+  for (int k = 0; k < t->d; ++k)
+    if (t->m[k] != op->m[k] || !t->cores[k]) return T2S2_EINVAL;
+  return T2S2_OK;
+}
+
 // Bind a user TT to a DevTT; host TTs get device staging in the arena and,
 // if `upload`, their contents copied in.
 t2s2_status bind_tt(Ctx& cx, const t2s2_tt* t, DevTT& dv, bool upload) {
@@ -556,7 +567,7 @@ t2s2_status t2s2_apply(t2s2_op op, const t2s2_tt* x, t2s2_tt* y, double c_mass, 
   if (!op || !x || !y) return T2S2_EINVAL;
   if (prec < T2S2_FP64 || prec > T2S2_BF16_REFINE) return T2S2_EINVAL;
   T2S2_TRY(check_tt(op, x));
-  if (!y->r || !y->cores || !y->cap || y->d != op->d) return T2S2_EINVAL;
+  T2S2_TRY(check_out_tt(op, y));
   for (int k = 0; k < op->d; ++k)
     if (y->cores[k] == x->cores[k]) return T2S2_EINVAL;
   T2S2_TRY(ensure_arena(op, tt_bytes(x) + tt_bytes(y) + ((size_t)1 << 20)));
@@ -573,7 +584,7 @@ t2s2_status t2s2_spacetime_rhs(t2s2_op op, const t2s2_tt* b, const t2s2_tt* u0, 
   if (!op || !b || !u0 || !out || !(tol >= 0.0)) return T2S2_EINVAL;
   if (op->d < 2 || op->dims[0].R0.empty()) return T2S2_EINVAL;  // not a space-time operator
   T2S2_TRY(check_tt(op, b));
-  if (!out->r || !out->cores || !out->cap || out->d != op->d) return T2S2_EINVAL;
+  T2S2_TRY(check_out_tt(op, out));
   const int ds = op->d - 1, mt = op->m[0];
   if (!u0->r || !u0->cores || !u0->cap || !u0->m || u0->d != ds || u0->r[0] != 1 || u0->r[ds] != 1)
     return T2S2_EINVAL;

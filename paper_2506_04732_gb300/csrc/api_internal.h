@@ -48,6 +48,7 @@ Ctx make_ctx(t2s2_op op, void* stream);
 size_t tt_bytes(const t2s2_tt* t);
 size_t max_core(const t2s2_tt* t);
 t2s2_status check_tt(t2s2_op op, const t2s2_tt* t);
+t2s2_status check_out_tt(t2s2_op op, const t2s2_tt* t);
 t2s2_status bind_tt(Ctx& cx, const t2s2_tt* t, DevTT& dv, bool upload);
 t2s2_status unbind_tt(Ctx& cx, const DevTT& dv, t2s2_tt* t);
 // Status words in op->dstat: word 0 for the small factorisations, word
