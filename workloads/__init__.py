@@ -25,7 +25,7 @@ import math
 import numpy as np
 
 __all__ = ["Factor", "Term", "Problem", "SpaceTimeProblem", "config0", "config1", "config2",
-           "config3", "config4", "config_spacetime", "random_tt", "sine_problem", "random_unit_vector",
+           "config3", "config4", "config_spacetime", "config_dirichlet", "random_tt", "sine_problem", "random_unit_vector",
            "EDGE_LENGTH"]
 
 EDGE_LENGTH = 2.0
@@ -259,6 +259,21 @@ def config_spacetime(seed: int = 6, d: int = 5, n: int = 32, n_t: int = 24, T: f
     sp = Problem(f"space-time d={d}+1 n={n} n_t={n_t} ratio={ratio:g}", d, (n,) * d, beta,
                  ratio * EDGE_LENGTH, terms, tol=tol, rmax=rmax, max_sweeps=30, seed=seed)
     return SpaceTimeProblem(sp, (Factor("exp", m=1.0), Factor("exp", m=-0.7)), n_t, T)
+
+
+def config_dirichlet(seed: int = 8, d: int = 5, n: int = 24, ratio: float = 1e-2, tol: float = 1e-8,
+                     rmax: int = 20) -> Problem:
+    """Non-zero Dirichlet data (u = g on the boundary, g = u* there): u* is a
+    sum of two separable terms that do not vanish at +-1, exponentials
+    exp(a x) with a in [-1, 1] and Gaussians of width 0.6 centred in
+    [-0.5, 0.5].  The source b = -eps Laplace u* + beta . grad u* as for the
+    other workloads."""
+    rng = np.random.default_rng(seed)
+    beta = random_unit_vector(d, rng)
+    terms = [Term(1.0, tuple(Factor("exp", m=float(rng.uniform(-1.0, 1.0))) for _ in range(d))),
+             Term(0.5, tuple(Factor("gauss", mu=float(rng.uniform(-0.5, 0.5)), s=0.6) for _ in range(d)))]
+    return Problem(f"dirichlet d={d} n={n} ratio={ratio:g}", d, (n,) * d, beta, ratio * EDGE_LENGTH,
+                   terms, tol=tol, rmax=rmax, max_sweeps=30, seed=seed)
 
 
 def sine_problem(d: int, n: int, ratio: float, seed: int = 5, tol: float = 1e-8,
