@@ -25,7 +25,7 @@ import math
 import numpy as np
 
 __all__ = ["Factor", "Term", "Problem", "SpaceTimeProblem", "config0", "config1", "config2",
-           "config3", "config4", "config_spacetime", "config_dirichlet", "random_tt", "sine_problem", "random_unit_vector",
+           "config3", "config4", "config_spacetime", "config_dirichlet", "config_varcoef", "VarCoefProblem", "random_tt", "sine_problem", "random_unit_vector",
            "EDGE_LENGTH"]
 
 EDGE_LENGTH = 2.0
@@ -274,6 +274,36 @@ def config_dirichlet(seed: int = 8, d: int = 5, n: int = 24, ratio: float = 1e-2
              Term(0.5, tuple(Factor("gauss", mu=float(rng.uniform(-0.5, 0.5)), s=0.6) for _ in range(d)))]
     return Problem(f"dirichlet d={d} n={n} ratio={ratio:g}", d, (n,) * d, beta, ratio * EDGE_LENGTH,
                    terms, tol=tol, rmax=rmax, max_sweeps=30, seed=seed)
+
+
+@dataclass
+class VarCoefProblem:
+    """Variable coefficients for a Problem: beta_k(x) = beta_ref[k] (1 + a_k
+    sin(pi x)) and rho(x) = rho0 + sum_k c_k (1 + x_k^2); beta_ref[k] (the
+    problem's beta) is the speed that picks the superconsistent points."""
+    problem: Problem
+    amp: np.ndarray
+    rho_c: np.ndarray
+    rho0: float
+
+    def beta_fn(self, k):
+        b, a = float(self.problem.beta[k]), float(self.amp[k])
+        return lambda x: b * (1.0 + a * np.sin(np.pi * np.asarray(x, dtype=np.float64)))
+
+    def rho_fn(self, k):
+        c = float(self.rho_c[k])
+        return lambda x: c * (1.0 + np.asarray(x, dtype=np.float64) ** 2)
+
+
+def config_varcoef(seed: int = 9, d: int = 6, n: int = 32, ratio: float = 1e-3, tol: float = 1e-8,
+                   rmax: int = 20) -> VarCoefProblem:
+    """Variable convection beta_k(x_k) (amplitudes a_k in [0.2, 0.5] around a
+    seeded unit vector) and reaction rho0 + sum_k c_k (1 + x_k^2) (rho0 = 0.5,
+    c_k in [0, 0.3]); u* the rank-4 recipe of config1 with the same seed."""
+    base = config1(seed_beta=seed, seed_terms=seed + 1, d=d, n=n, ratio=ratio, rmax=rmax, tol=tol)
+    base.name = f"varcoef d={d} n={n} ratio={ratio:g}"
+    rng = np.random.default_rng(seed + 2)
+    return VarCoefProblem(base, rng.uniform(0.2, 0.5, d), rng.uniform(0.0, 0.3, d), 0.5)
 
 
 def sine_problem(d: int, n: int, ratio: float, seed: int = 5, tol: float = 1e-8,
