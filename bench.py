@@ -29,7 +29,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solves/sec to rel. residual 1e-8 (d=6,n=32)"
 UNIT = "solves/s"
-FAMILIES = ["gemm", "apply", "local_solve", "small_factor", "elementwise", "apply_tc", "gemm_tc", "mlp"]
+FAMILIES = ["gemm", "apply", "local_solve", "small_factor", "elementwise", "apply_tc", "gemm_tc", "mlp", "cholqr",
+            "sylvester", "dots"]
 
 
 def parse():
@@ -47,13 +48,17 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle CPU work for the cpu_baseline sample")
     ap.add_argument("--workload", default="steady",
-                    choices=["steady", "batched", "cn", "warm", "contract", "spacetime"],
+                    choices=["steady", "batched", "cn", "warm", "contract", "spacetime", "stability"],
                     help="steady: d=6 n=32 solve (headline); batched: 256 d=5 instances; "
                          "cn: Crank-Nicolson steps at d=7 n=64; warm: learned warm start "
                          "(--instances training solves); contract: grouped core contractions of "
                          "--instances d=5 problems in one launch; spacetime: d=5 space plus time "
-                         "(n=32, n_t=24) solved as one collocation system")
+                         "(n=32, n_t=24) solved as one collocation system; stability: the Plain-SC / "
+                         "superconsistent stability map (d=6) through the batched solve")
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--holdout", type=int, default=1000, help="held-out problems of --workload warm")
+    ap.add_argument("--warm-rank", type=int, default=1, help="TT rank of the warm-start network's output")
+    ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of --workload warm")
     ap.add_argument("--workers", type=int, default=8)
     return ap.parse_args()
 
@@ -174,6 +179,50 @@ def peaks():
 # FP64 ALU peak of GB300: 2 DFMA per clock per SM (4 FLOP) x 152 SMs at the
 # 1965 MHz clock this part sustains under FP64 load.
 FP64_ALU_PEAK_GFLOPS = 4 * 152 * 1.965
+
+
+# Kernel families that the FP64 ALU bounds (the rest: memory).
+ALU_FAMILIES = ("gemm", "apply", "local_solve", "small_factor", "cholqr", "sylvester", "dots")
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# family's dominant kernel from an ncu capture of the current build, with the
+# summary it comes from; a family without a current capture is left out.
+KERNEL_DRAM_BYTES = {}
+
+
+def kernel_family(name: str) -> str:
+    """Trace family of a kernel, by its (demangled) name."""
+    table = (("cholqr3_kernel", "cholqr"), ("sylv_rb1_kernel", "sylvester"), ("tt_norm2_dd_kernel", "dots"),
+             ("tt_dots_kernel", "dots"), ("small_group_kernel", "gemm"), ("small_kernel", "gemm"),
+             ("gemm_tc_kernel", "gemm_tc"), ("gemm_kernel", "gemm"), ("splitk", "gemm"),
+             ("apply_tc_kernel", "apply_tc"), ("apply_kernel", "apply"), ("gmres_team_kernel", "local_solve"),
+             ("local_eig_kernel", "local_solve"), ("jacobi_svd_kernel", "small_factor"),
+             ("chol_inv_kernel", "small_factor"), ("t2s2::", "elementwise"))
+    for key, famname in table:
+        if key in name:
+            return famname
+    return "other"
+
+
+def kernel_device_times(fn, torch):
+    """{kernel name: (launches, device microseconds)} of one call of fn, from
+    CUPTI activity records through torch.profiler; {} if unavailable.  Used to
+    rank kernels by device time only: no reported rate comes from it."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        out = {}
+        for ev in prof.key_averages():
+            us = getattr(ev, "device_time_total", None)
+            if us is None:
+                us = getattr(ev, "cuda_time_total", 0.0)
+            if us and us > 0 and "Memcpy" not in ev.key and "Memset" not in ev.key:
+                out[ev.key] = (int(ev.count), float(us))
+        return out
+    except Exception as exc:  # recorded by the caller
+        return {"__error__": (0, 0.0, repr(exc))}
 
 
 _ORACLE_CHILD = r"""
@@ -330,31 +379,113 @@ def run_batched(args, T, P, W, torch):
     return 0
 
 
+_ORACLE_CN_CHILD = r"""
+import sys, time, json
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import operator as O
+from oracle import solve as S
+p = W.config2()
+ops = O.build(p)
+u = O.solution_tt(p, ops)
+for i in range({count}):
+    t0 = time.perf_counter()
+    u, res, sweeps = S.cn_step(ops, u, p.dt, p.tol, p.rmax)
+    print(json.dumps({{"i": i, "t": time.perf_counter() - t0, "res": res, "sweeps": sweeps}}), flush=True)
+"""
+
+
+def oracle_cn_steps(budget_s):
+    """Crank-Nicolson steps of the FP64 oracle on the d=7, n=64 workload in a
+    child process, each timed on its own, until budget_s has passed."""
+    import subprocess as sp
+    code = _ORACLE_CN_CHILD.format(root=ROOT, count=100)
+    proc = sp.Popen([sys.executable, "-c", code], stdout=sp.PIPE, stderr=sp.DEVNULL, text=True)
+    lines = []
+    th = threading.Thread(target=lambda: lines.extend(proc.stdout), daemon=True)
+    th.start()
+    try:
+        proc.wait(timeout=budget_s)
+    except sp.TimeoutExpired:
+        proc.kill()
+        proc.wait()
+    th.join(timeout=5)
+    out = []
+    for ln in lines:
+        try:
+            out.append(json.loads(ln))
+        except ValueError:
+            pass
+    return out
+
+
 def run_cn(args, T, P, W, torch):
-    """Crank-Nicolson steps of the d=7, n=64 Gaussian pulse (dt = 1e-3, rmax 40, tol 1e-8)."""
+    """Crank-Nicolson run of the d=7, n=64 Gaussian pulse: the workload's 100
+    steps of dt = 1e-3 (rmax 40, tol 1e-8), FP64, timed with device events;
+    then the same trajectory with TF32 / BF16 tensor-core contractions under
+    FP64 refinement, with their distance to the FP64 states after 10 and 100
+    steps (t2s2_diff_norm)."""
     p = W.config2()
+    nsteps = args.steps
     op = P.build_operator(p)
-    u = T.TT.from_cores(P.solution_cores(p, op), rcap=p.rmax + T.RANK_KICK)
-    infos = []
-    for _ in range(args.warmup):
-        infos.append(T.t2s2_cn_step(op, u, p.dt, p.tol, p.rmax))
-    torch.cuda.synchronize()
+    u0 = P.solution_cores(p, op)
+    rcap = p.rmax + T.RANK_KICK
     stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        infos.append(T.t2s2_cn_step(op, u, p.dt, p.tol, p.rmax))
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    line = {"metric": "Crank-Nicolson steps/sec (d=7, n=64, dt=1e-3, tol 1e-8)", "value": 1e3 / ms,
-            "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+    # warm-up steps on a scratch copy: the measured trajectory starts at u0
+    uw = T.TT.from_cores(u0, rcap=rcap)
+    for _ in range(args.warmup):
+        T.t2s2_cn_step(op, uw, p.dt, p.tol, p.rmax)
+    torch.cuda.synchronize()
+
+    def trajectory(prec):
+        u = T.TT.from_cores(u0, rcap=rcap)
+        infos, keep = [], {}
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        for k in range(1, nsteps + 1):
+            e0.record(stream)
+            infos.append(T.t2s2_cn_step(op, u, p.dt, p.tol, p.rmax, prec=prec))
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            if k in (10, nsteps):   # states kept outside the timed spans
+                keep[k] = T.TT(u.m, list(u.r), [b.clone() for b in u.buffers], u.loc)
+        return u, infos, keep, ms
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    u, infos, keep64, ms = trajectory(T.FP64)
+    clk = clocks.stop()
+    variants = {}
+    for name, prec in (("tf32_refine", T.TF32_REFINE), ("bf16_refine", T.BF16_REFINE)):
+        try:
+            uv, iv, keepv, msv = trajectory(prec)
+            variants[name] = {"steps_per_s": 1e3 * nsteps / msv,
+                              "max_step_residual": max(i.residual for i in iv),
+                              "rel_diff_vs_fp64": {str(k): T.t2s2_diff_norm(op, keepv[k], keep64[k]) /
+                                                   T.t2s2_norm(op, keep64[k]) for k in keep64}}
+        except Exception as exc:  # recorded, never hides the FP64 number
+            variants[name] = {"error": repr(exc)}
+    cpu = None
+    if args.cpu_budget > 0:
+        recs = oracle_cn_steps(max(60.0, args.cpu_budget))
+        if recs:
+            tot = sum(r["t"] for r in recs)
+            cpu = {"value": len(recs) / tot, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"the oracle's first {len(recs)} Crank-Nicolson steps of the same trajectory "
+                             f"(FP64 numpy, {tot / len(recs):.1f} s each)"}
+    line = {"metric": "Crank-Nicolson steps/sec (d=7, n=64, dt=1e-3, tol 1e-8)", "value": 1e3 * nsteps / ms,
+            "unit": "steps/s", "n_gpus": 1, "steps": nsteps, "warmup": args.warmup, "ms_per_step": ms / nsteps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": p.name, "rmax": p.rmax, "ranks": u.r,
-                       "step_residuals": [inf.residual for inf in infos],
-                       "sweeps": [inf.sweeps for inf in infos]}}
+            "config": {"workload": p.name, "rmax": p.rmax, "final_ranks": u.r,
+                       "step_residuals_max": max(i.residual for i in infos),
+                       "all_steps_converged": all(i.residual <= p.tol for i in infos),
+                       "sweeps_per_step": [i.sweeps for i in infos],
+                       "max_rank": max(i.max_rank for i in infos)},
+            "precision_variants": variants, "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line))
     return 0
 
@@ -418,12 +549,17 @@ def run_spacetime(args, T, P, W, torch):
 
 
 def run_warm(args, T, P, W, torch):
-    """Learned warm start on the d=6, n=32 parameter family: generate solutions
-    with the solver itself, train the network on the GPU (forward, backward and
-    Adam kernels of the library), then solve held-out problems cold and warm
-    to the same tolerance."""
+    """Learned warm start on the d=6, n=32 parameter family (ratio log-uniform
+    in [1e-4, 1e-2], rank-4 source from 8 parameters, tol 1e-8, rmax 20):
+    generate --instances training solutions with the solver itself (seeds
+    10000+i), train the network on the GPU (the library's forward, backward
+    and Adam kernels), then solve --holdout held-out problems (seeds 90000+i)
+    cold and warm to the same tolerance.  The network outputs TT cores of
+    rank --warm-rank (1 by default: a rank-1 guess keeps the first sweep's
+    rank-1 right interfaces, the path on which a cold solve of this family
+    converges in one sweep)."""
     import numpy as np
-    ntrain, nhold = args.instances, 16
+    ntrain, nhold, rw = args.instances, args.holdout, args.warm_rank
     d, n, rmax, tol = 6, 32, 20, 1e-8
     m = n - 2
 
@@ -433,8 +569,10 @@ def run_warm(args, T, P, W, torch):
         x = T.TT.from_cores([np.ones((1, m, 1))] * d, rcap=rmax + T.RANK_KICK)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        t_inf = 0.0
         if net is not None:
             net.predict(W.warm_features(p), x)
+            t_inf = time.perf_counter() - t0
         if r0 is not None:  # initial residual, outside the solve's timing
             torch.cuda.synchronize()
             t1 = time.perf_counter()
@@ -442,17 +580,30 @@ def run_warm(args, T, P, W, torch):
             t0 += time.perf_counter() - t1
         info = T.t2s2_solve(op, b, x, tol, rmax, 50, allow_noconv=True)
         torch.cuda.synchronize()
-        return op, x, info, time.perf_counter() - t0
+        return op, x, info, time.perf_counter() - t0, t_inf
 
     t0 = time.perf_counter()
     train = [W.config4(10000 + i, d=d, n=n) for i in range(ntrain)]
-    sols = [solve(p) for p in train]
+    net = T.WarmStartNet(W.WARM_IN_DIM, 256, [m] * d, rw, rmax + T.RANK_KICK, seed=1)
+    per = net.d * net.ru * net.mmax * net.ru
+    tg = torch.zeros(ntrain * per, dtype=torch.float32, device="cuda")
+    uu = torch.zeros(ntrain, dtype=torch.float32, device="cuda")
+    train_sweeps, op0, x0 = [], None, None
+    for i, p in enumerate(train):
+        op, x, info, _, _ = solve(p)
+        train_sweeps.append(info.sweeps)
+        # each solution goes straight into its packed slot; one operator and
+        # solution are kept for the output initialisation
+        net.pack_target_into(op, x, tg, uu, i)
+        if i == 0:
+            op0, x0 = op, x
+        else:
+            op.destroy()
     t_data = time.perf_counter() - t0
-    net = T.WarmStartNet(W.WARM_IN_DIM, 256, [m] * d, 8, rmax + T.RANK_KICK, seed=1)
-    tg, uu = net.pack_targets(sols[0][0], [s[1] for s in sols])
+    train_sweeps = np.bincount(train_sweeps).tolist()
     Pf = torch.tensor(np.stack([W.warm_features(p) for p in train]), device="cuda")
-    steps, batch = 1500, min(64, ntrain)
-    net.init_output_bias(sols[0][0], sols[0][1])
+    steps, batch = args.train_steps, min(64, ntrain)
+    net.init_output_bias(op0, x0)
     sigma_shift = net.calibrate_scale(Pf, tg, uu, 0, min(256, ntrain))
     T.t2s2_trace(True)
     t0 = time.perf_counter()
@@ -466,39 +617,85 @@ def run_warm(args, T, P, W, torch):
     mlp = T.t2s2_trace_read("mlp")
     gemm = T.t2s2_trace_read("gemm_tc")
     T.t2s2_trace(False)
+    del tg, uu
     hold = [W.config4(90000 + i, d=d, n=n) for i in range(nhold)]
     for p in hold[:2]:  # warm-up
         solve(p)
         solve(p, net)
-    cold_t = warm_t = 0.0
-    cold_sw = warm_sw = 0
+    cold_t = warm_t = inf_t = 0.0
+    sw_c, sw_w = [], []
     conv_c = conv_w = 0
     diffs, r0c, r0w = [], [], []
     for p in hold:
-        op, xc, ic, tc = solve(p, r0=r0c)
-        _, xw, iw, tw = solve(p, net, r0=r0w)
+        op, xc, ic, tc, _ = solve(p, r0=r0c)
+        _, xw, iw, tw, ti = solve(p, net, r0=r0w)
         cold_t += tc
         warm_t += tw
-        cold_sw += ic.sweeps
-        warm_sw += iw.sweeps
+        inf_t += ti
+        sw_c.append(ic.sweeps)
+        sw_w.append(iw.sweeps)
         conv_c += ic.residual <= tol
         conv_w += iw.residual <= tol
         diffs.append(T.t2s2_diff_norm(op, xc, xw) / T.t2s2_norm(op, xc))
+        op.destroy()
+    sw_c, sw_w = np.array(sw_c), np.array(sw_w)
     line = {"metric": "solves/sec to rel. residual 1e-8 with the learned warm start (d=6,n=32 family)",
-            "value": nhold / warm_t, "unit": "solves/s", "n_gpus": 1, "steps": nhold, "warmup": 2,
+            "value": conv_w / warm_t, "unit": "solves/s", "n_gpus": 1, "steps": nhold, "warmup": 2,
             "ms_per_step": 1e3 * warm_t / nhold, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 solve, bf16/fp32 network", "data": "synthetic",
             "config": {"workload": f"config-4 family d={d} n={n}: {ntrain} training solves, {nhold} held-out",
-                       "cold_solves_per_s": nhold / cold_t, "cold_sweeps": cold_sw, "warm_sweeps": warm_sw,
+                       "cold_solves_per_s": conv_c / cold_t, "warm_rank": rw,
+                       "cold_sweeps": int(sw_c.sum()), "warm_sweeps": int(sw_w.sum()),
+                       "cold_sweep_histogram": np.bincount(sw_c).tolist(),
+                       "warm_sweep_histogram": np.bincount(sw_w).tolist(),
+                       "instances_warm_fewer_sweeps": int((sw_w < sw_c).sum()),
+                       "instances_warm_more_sweeps": int((sw_w > sw_c).sum()),
+                       "inference_ms_per_solve": 1e3 * inf_t / nhold,
                        "cold_converged": conv_c, "warm_converged": conv_w,
                        "initial_residual_median_cold": float(np.median(r0c)),
                        "initial_residual_median_warm": float(np.median(r0w)),
                        "max_rel_diff_cold_vs_warm": max(diffs), "train_steps": steps, "batch": batch,
+                       "training_sweep_histogram": train_sweeps,
                        "loss_first": losses[0], "loss_last": float(np.mean(losses[-20:])),
                        "log_scale_calibration": sigma_shift,
                        "data_generation_s": t_data, "training_s": t_train,
                        "mlp_kernels": mlp, "mlp_gemm_tc": gemm,
-                       "network": "15 -> 256 -> 256 -> TT cores rank 8 (8160 outputs), ReLU, Adam"}}
+                       "network": f"15 -> 256 -> 256 -> TT cores rank {rw}, ReLU, Adam"}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_stability(args, T, P, W, torch):
+    """Stability map of the paper's figure (d=6, beta of ones, b = 1, zero
+    data): degrees 8..40 by ratios 1e-1..1e-5, each pixel solved with Plain-SC
+    and with superconsistent collocation, all 50 solves in one batched call;
+    each pixel classified on its mid-axis line (derivative sign changes,
+    total-variation excess)."""
+    from paper_2506_04732_gb300 import stability as S
+    d, degrees, ratios = 6, (8, 16, 24, 32, 40), (1e-1, 1e-2, 1e-3, 1e-4, 1e-5)
+    S.solve_map(T, d, (8,), (1e-1,), workers=args.workers)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pixels, infos = S.solve_map(T, d, degrees, ratios, workers=args.workers)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rows = {}
+    for plain in (True, False):
+        name = "plain_sc" if plain else "superconsistent"
+        rows[name] = {f"N={N}": [f"{pixels[(N, r, plain)]['sign_changes']}:{pixels[(N, r, plain)]['tv_excess']:.2f}"
+                                 for r in ratios] for N in degrees}
+    macro = {("plain_sc" if pl else "superconsistent"): sum(1 for (N, r, p_), px in pixels.items()
+                                                               if p_ == pl and px["tv_excess"] > 0.1)
+             for pl in (True, False)}
+    conv = sum(1 for inf in infos if inf.residual <= 1e-8)
+    line = {"metric": "stability-map pixels/sec (d=6, 25 (degree, ratio) pixels x 2 schemes, one batched call)",
+            "value": len(pixels) / dt, "unit": "pixels/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * dt, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "beta=(1,..,1), b=1, zero Dirichlet data, tol 1e-8, rmax 30",
+                       "ratios": list(ratios), "degrees": list(degrees),
+                       "map_sign_changes_tv_excess": rows, "macroscopic_pixels": macro,
+                       "converged": conv, "solves": len(infos)}}
     print(json.dumps(line))
     return 0
 
@@ -592,7 +789,12 @@ def measure_precisions(T, P, W, torch, op, b, x_ref, steps=3):
 def main():
     args = parse()
     if args.steps is None:
-        args.steps = 200 if args.impl == "ours" and args.workload == "steady" else 5
+        if args.impl == "ours" and args.workload == "steady":
+            args.steps = 200
+        elif args.impl == "ours" and args.workload == "cn":
+            args.steps = 100   # the workload's trajectory
+        else:
+            args.steps = 5
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "steady":
@@ -604,7 +806,7 @@ def main():
         from paper_2506_04732_gb300 import problem as P
         import workloads as W
         fn = {"batched": run_batched, "cn": run_cn, "warm": run_warm, "contract": run_contract,
-              "spacetime": run_spacetime}[args.workload]
+              "spacetime": run_spacetime, "stability": run_stability}[args.workload]
         return fn(args, T, P, W, torch)
     ws, rank, local = dist_env()
     import torch
@@ -720,21 +922,45 @@ def main():
             except Exception as exc:  # recorded, never hides the headline number
                 extras[key] = {"error": repr(exc)}
 
-    # roofline of the dominant kernel family (largest share of traced time)
+    # The dominant kernel by device time: per-kernel device durations of one
+    # more solve from CUPTI activity records (no events between launches);
+    # the event trace above then gives that family's time per launch (events
+    # around each launch include its launch gap, so `achieved` is a lower bound)
+    flush.zero_()
+    reset_x()
+    torch.cuda.synchronize()
+    dev = kernel_device_times(lambda: T.t2s2_solve(op, b, x, p.tol, p.rmax, p.max_sweeps, prec=prec), torch)
+    cupti_error = dev.pop("__error__", (0, 0.0, None))[2] if dev else "no kernel records"
     pk, src = peaks()
-    dom = max(fam, key=lambda k: fam[k]["ms"])
+    if dev:
+        by_fam = {}
+        for name, (cnt, us) in dev.items():
+            by_fam[kernel_family(name)] = by_fam.get(kernel_family(name), 0.0) + us
+        by_fam.pop("other", None)
+        total_us = sum(by_fam.values())
+        dom = max(by_fam, key=by_fam.get)
+        share = {k: round(v / total_us, 4) for k, v in sorted(by_fam.items(), key=lambda kv: -kv[1])}
+        dom_src = "device time per kernel family of one solve (CUPTI activity records)"
+    else:
+        dom = max(fam, key=lambda k: fam[k]["ms"])
+        share, dom_src = None, f"event-traced time per family (CUPTI records unavailable: {cupti_error})"
     fd = fam[dom]
-    if dom in ("gemm", "apply", "local_solve", "small_factor"):
+    if dom in ALU_FAMILIES:
         bound, peak, unit = "alu", FP64_ALU_PEAK_GFLOPS / 1e3, "TFLOP/s"
         achieved = fd["flops"] / (fd["ms"] / 1e3) / 1e12 if fd["ms"] > 0 else 0.0
-        peak_src = "derived: 2 DFMA/clk/SM x 152 SMs x 1.965 GHz"
+        peak_src = "derived: 2 DFMA/clk/SM x 152 SMs x 1.965 GHz (FP64 ALU)"
     else:
         bound, peak, unit = "hbm", pk["hbm_gbs"], "GB/s"
         achieved = fd["bytes"] / (fd["ms"] / 1e3) / 1e9 if fd["ms"] > 0 else 0.0
         peak_src = f"{src} hbm_gbs"
+    traffic = KERNEL_DRAM_BYTES.get(dom)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak if peak else None, "traffic": None, "kernel": dom,
+            "frac": achieved / peak if peak else None,
+            "traffic": traffic[0] if traffic else None,
+            "traffic_source": traffic[1] if traffic else None,
+            "kernel": dom, "kernel_choice": dom_src, "device_time_share": share,
             "peak_source": peak_src,
+            "flops_per_launch": fd["flops"] / max(1, fd["launches"]),
             "per_launch_ms": fd["ms"] / max(1, fd["launches"])}
 
     cpu = None

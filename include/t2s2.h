@@ -59,7 +59,7 @@ typedef enum {
   T2S2_ECUDA = 3,      /* a CUDA call or kernel launch failed */
   T2S2_ENOCONV = 4,    /* the solver hit its sweep cap; best iterate and residual written */
   T2S2_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
-  T2S2_ENOTIMPL = 6,   /* feature not provided (e.g. non-zero Dirichlet data) */
+  T2S2_ENOTIMPL = 6,   /* feature not provided */
   T2S2_ENODEV = 7      /* no usable sm_103 device */
 } t2s2_status;
 
@@ -90,6 +90,26 @@ typedef struct {
 } t2s2_problem;
 
 typedef struct t2s2_op_s* t2s2_op;
+
+/* A coefficient function of one coordinate: value at x of dimension k's
+ * function; ctx is passed through. */
+typedef double (*t2s2_coef_fn)(int k, double x, void* ctx);
+
+/* Variable coefficients of eq. pblm:time:A in the form the paper's
+ * six-dimensional test uses for beta: beta_k(x_k) per dimension, and a
+ * reaction rho(x) = rho0 + sum_k rho_k(x_k).  base.beta[k] is the reference
+ * speed of dimension k that picks its superconsistent points (a reading: the
+ * paper does not say which speed picks them with a variable beta).
+ * beta_fn NULL: constant base.beta[k]; rho_fn NULL: rho = rho0.  A reaction
+ * that is a product of one-coordinate functions needs a rank-3 TT-matrix and
+ * is not provided. */
+typedef struct {
+  t2s2_problem base;
+  t2s2_coef_fn beta_fn;
+  t2s2_coef_fn rho_fn;
+  double rho0;
+  void* ctx;
+} t2s2_problem_var;
 
 typedef struct {
   int d;
@@ -132,6 +152,18 @@ int t2s2_device_count(void);
 t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op* out);
 
 /*
+ * t2s2_build_operator with variable coefficients (t2s2_problem_var): at the
+ * collocation point eta_j of dimension k the rows of the 1D derivative are
+ * scaled by beta_k(eta_j) and rho_k(eta_j) Rt_k is added (rho0 Rt in the
+ * first dimension), Lt_k = diag(beta_k(eta)) D - eps D2 + diag(rho_k(eta))
+ * Rt_k: the same rank-2 TT-matrix, so every entry point that takes an
+ * operator works unchanged.  The functions are called on the host during the
+ * build, n[k] - 2 times per dimension.  Errors as t2s2_build_operator, and
+ * T2S2_EINVAL if a coefficient value is not finite.
+ */
+t2s2_status t2s2_build_operator_var(const t2s2_problem_var* prob, void* stream, t2s2_op* out);
+
+/*
  * Operator of the unified space-time form (Methods overview; Results,
  * "Global Accuracy"): time is one more collocated dimension, placed first,
  * with the time interval [0, t_len] mapped onto [-1, 1].  Dimension 0 has n_t
@@ -159,6 +191,39 @@ t2s2_status t2s2_build_spacetime_operator(const t2s2_problem* space, int n_t, do
  */
 t2s2_status t2s2_spacetime_rhs(t2s2_op op, const t2s2_tt* b, const t2s2_tt* u0, t2s2_tt* out, double tol,
                                int rmax, void* stream);
+
+/*
+ * Non-zero Dirichlet data (eq. pblm:time:B, u = g on the boundary) by TT
+ * lifting.  g is a TT on the FULL GLL grid of a spatial operator: mode sizes
+ * n[k] (not n[k] - 2), cores [r[k]][n[k]][r[k+1]]; only its values at
+ * boundary nodes matter (any extension inside gives the same solution).
+ * With the full (n-2) x n 1D matrices Rf, Lf (every GLL node a column),
+ *     out = round(b - (c_mass M_full + c_op A_full) g, tol, rmax),
+ * the source of the zero-data system for the correction w = u - g:
+ * (c_mass M + c_op A) w = out, after which u = w + g on the interior nodes.
+ * b is the source on the collocation grid as for t2s2_solve; out has the
+ * interior mode sizes.  Errors: T2S2_EINVAL for a g off the full grid, a
+ * space-time operator or non-finite coefficients; T2S2_ENOMEM if out is too
+ * small.
+ */
+t2s2_status t2s2_dirichlet_rhs(t2s2_op op, const t2s2_tt* b, const t2s2_tt* g, double c_mass, double c_op,
+                               t2s2_tt* out, double tol, int rmax, void* stream);
+
+/*
+ * t2s2_solve with Dirichlet data g (a full-grid TT as in t2s2_dirichlet_rhs;
+ * NULL means zero data and gives exactly t2s2_solve).  The lifted source is
+ * rounded at tol / 100, the correction w solved from the initial guess in x
+ * (any interior-grid TT, e.g. all ones), and x receives u = w + g on the
+ * interior nodes as the exact TT sum, not recompressed (ranks of w plus those
+ * of g, so x needs room for ranks up to rmax + T2S2_RANK_KICK + max rank of
+ * g; recompressing it would lose the small directions of w next to g and the
+ * operator would amplify that loss).
+ * info->residual is the relative residual of the solved system,
+ * ||b_g - (c_mass M + c_op A) w|| / ||b_g||, b_g the lifted source.
+ */
+t2s2_status t2s2_solve_dirichlet(t2s2_op op, const t2s2_tt* b, const t2s2_tt* g, t2s2_tt* x, double c_mass,
+                                 double c_op, double tol, int rmax, int max_sweeps, t2s2_precision prec,
+                                 void* stream, t2s2_solve_info* info);
 
 /* Free an operator and its workspace.  NULL is accepted. */
 t2s2_status t2s2_op_destroy(t2s2_op op);
@@ -246,24 +311,36 @@ int t2s2_autotune_report(char* buf, int len);
  */
 t2s2_status t2s2_round(t2s2_op op, t2s2_tt* x, double tol, int rmax, void* stream);
 
+/* The values of x along mode `mode` with the other indices fixed (eq.
+ * TT-format:elementwise, the product of the core slices): out[t] =
+ * x(idx[0], .., t, .., idx[d-1]) for t < m[mode]; idx has d entries (the one
+ * at `mode` is ignored); out is a host array of m[mode] doubles.  Used to read
+ * a solution along a grid line (the mid-axis lines of the stability map).
+ * Synchronises.  Errors: T2S2_EINVAL for a mode or index out of range or
+ * ranks above 8192. */
+t2s2_status t2s2_tt_fibre(t2s2_op op, const t2s2_tt* x, int mode, const int* idx, double* out, void* stream);
+
 /* ||x||_F (accurate: orthogonalise and take the norm of the first core). */
 t2s2_status t2s2_norm(t2s2_op op, const t2s2_tt* x, double* out, void* stream);
 
 /*
  * ||x||_F exactly as t2s2_norm computes it, but without allocating anything.
  * The paper has no counterpart; this entry point exists for callers that may
- * not allocate device memory at the time they need the norm: for example, code
- * recording work into a CUDA graph, real-time or embedded loops whose memory
- * is fixed at start-up, or hosts whose framework allocator already owns the
- * device memory.  It takes no operator handle (no workspace).  Every
- * temporary lives in one 32 MiB array that the library reserves as a static
- * device variable on each GPU that loads it, kept until the process exits.
- * x must be device-resident (loc == T2S2_DEVICE) with ranks <= 96.  A train
- * whose temporaries would exceed the 32 MiB array is rejected with
- * T2S2_ENOMEM before any work is queued.  The first call on a device looks up
- * that device's array address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the one array, so calls whose
- * GPU work overlaps race on it: serialise them.  Synchronises with `stream`.
+ * not allocate device memory at the time they need the norm: real-time or
+ * embedded loops whose memory is fixed at start-up (a cudaMalloc there can
+ * stall or fail), or hosts whose framework allocator already owns the device
+ * memory.  It takes no operator handle (no workspace).  Every temporary
+ * lives in one 32 MiB array that the library reserves as a static device
+ * variable on each GPU that loads it, kept until the process exits.  x must
+ * be device-resident (loc == T2S2_DEVICE) with ranks <= 96.  A train whose
+ * temporaries would exceed the 32 MiB array is rejected with T2S2_ENOMEM
+ * before any work is queued; if an error occurs after work was queued, the
+ * call waits for that work before it returns.  The first call on a device
+ * looks up that device's array address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls whose GPU work overlaps race on it: serialise them.  The call
+ * synchronises with `stream` and reads the result back into host memory
+ * before it returns.
  */
 t2s2_status t2s2_norm_noalloc(const t2s2_tt* x, double* out, void* stream);
 
@@ -290,7 +367,11 @@ t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double
  * residual ||b - (c_mass M + c_op A) x||_F / ||b||_F <= tol or max_sweeps.
  * b is the right-hand side sampled on the collocation grid; x holds the
  * initial guess on input and the solution on output (ranks <= rmax + T2S2_RANK_KICK).
- * Returns T2S2_ENOCONV (with x and info filled) if the sweep cap is hit.
+ * Returns T2S2_ENOCONV (with x and info filled) if the sweep cap is hit, or
+ * earlier once some TT rank of x sits at rmax + T2S2_RANK_KICK and the
+ * residual has not halved over 8 sweeps (the rank cap, not the sweep count,
+ * then limits the solution; environment variable T2S2_STALL sets the number
+ * of sweeps, 0 turns this stop off).
  * The plain solve is c_mass = 0, c_op = 1.
  */
 t2s2_status t2s2_solve(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double c_mass, double c_op,
@@ -376,6 +457,15 @@ t2s2_status t2s2_mlp_set_params(t2s2_mlp net, const float* params, void* stream)
  * ru x mmax x ru, uu (device, 1 float) its squared norm (FP64 TT norm). */
 t2s2_status t2s2_mlp_pack_target(t2s2_mlp net, t2s2_op op, const t2s2_tt* u, float* slot, float* uu,
                                  void* stream);
+/* Start the network's output at a representative solution u (a device or
+ * host TT on the network's grid): the output bias takes the cores of u
+ * rounded to the network's rank r (FP64 rounding with no tolerance, then
+ * stored as FP32, zero-padded to the output's core shapes), the output
+ * weights W3 are multiplied by weight_scale, and the log-scale bias is set to
+ * zero.  X(p) then starts near u for every p and training learns the
+ * deviations.  Uses op's workspace.  Synchronises.  Errors: T2S2_EINVAL for
+ * a TT off the network's grid or a non-finite weight_scale. */
+t2s2_status t2s2_mlp_init_output(t2s2_mlp net, t2s2_op op, const t2s2_tt* u, float weight_scale, void* stream);
 /* Loss and gradient of a batch: P (device, batch x in_dim), targets and uu
  * (device, as packed above).  The gradient stays in the network (see
  * t2s2_mlp_get_params); *loss (may be NULL) receives the mean loss.
@@ -403,14 +493,29 @@ t2s2_status t2s2_mlp_train(t2s2_mlp net, const float* P, int n, const float* tar
                            int batch, int steps, float lr, int use_graph, float* loss, void* stream);
 /* Warm start: the cores of X(p) (p: host or device, in_dim floats) as FP64
  * into x (device or host cores with room for them); x->r is set to the
- * network's ranks. */
+ * network's ranks.  For a device x whose layers fit one CTA's shared memory
+ * (in_dim + 2 hidden + outputs <= 24k floats) the prediction is a single
+ * launch (layers with BF16 operands and FP32 sums, as the batched layers)
+ * queued on `stream` without synchronising; otherwise the batched layers run
+ * and the call synchronises. */
 t2s2_status t2s2_mlp_predict(t2s2_mlp net, const float* p, t2s2_tt* x, void* stream);
+
+/* The FP64 reciprocal square root and reciprocal that the small
+ * factorisations use (binary32 hardware seed refined by two binary64 Newton
+ * steps, y <- y (3 - x y^2) / 2 and y <- y (2 - x y); IEEE division and
+ * square root for |x| outside (1e-36, 1e36)), applied elementwise to the
+ * device array x (n doubles) so that they can be checked against correctly
+ * rounded results.  rsqrt_out / rcp_out: device arrays of n doubles, either
+ * may be NULL.  Synchronises.  The paper has no such call. */
+t2s2_status t2s2_fastmath(const double* x, double* rsqrt_out, double* rcp_out, long n, void* stream);
 
 /* ---- diagnostics ---------------------------------------------------------
  * Kernel families for tracing: 0 GEMM (SIMT contractions), 1 TT apply
- * (FP64), 2 local solve, 3 small factorisations (Cholesky, Jacobi SVD),
- * 4 elementwise, 5 TT apply on tensor cores (BF16/TF32), 6 GEMM on tensor
- * cores (BF16/TF32), 7 warm-start network (forward, backward, Adam).
+ * (FP64), 2 local solve (Krylov team and its eigendecompositions), 3 small
+ * factorisations (Cholesky, Jacobi SVD), 4 elementwise, 5 TT apply on tensor
+ * cores (BF16/TF32), 6 GEMM on tensor cores (BF16/TF32), 7 warm-start network
+ * (forward, backward, Adam), 8 fused CholeskyQR, 9 rank-1-right local solves
+ * (Sylvester solver), 10 TT inner products (binary64 and double-double).
  */
 
 /* Number of CUDA kernels this library has launched in this process. */

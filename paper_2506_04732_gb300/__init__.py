@@ -22,8 +22,8 @@ __all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REF
            "t2s2_norm", "t2s2_diff_norm", "t2s2_norm_noalloc", "t2s2_residual", "t2s2_solve", "t2s2_solve_batched", "t2s2_cn_step", "t2s2_be_step",
            "t2s2_device_count", "t2s2_strerror", "t2s2_gemm", "WarmStartNet", "t2s2_apply_batched",
            "t2s2_autotune_report", "t2s2_kernel_launches", "t2s2_trace",
-           "t2s2_trace_read", "TRACE_FAMILIES", "lib_path", "t2s2_dim_matrices", "DIM_SPACE",
-           "t2s2_build_spacetime_operator", "t2s2_spacetime_rhs",
+           "t2s2_trace_read", "t2s2_fastmath", "t2s2_tt_fibre", "TRACE_FAMILIES", "lib_path", "t2s2_dim_matrices", "DIM_SPACE",
+           "t2s2_build_spacetime_operator", "t2s2_spacetime_rhs", "t2s2_build_operator_var", "t2s2_dirichlet_rhs", "t2s2_solve_dirichlet",
            "DIM_SPACE_PLAIN", "DIM_TIME"]
 
 FP64, FP32_REFINE, TF32_REFINE, BF16_REFINE = 0, 1, 2, 3
@@ -49,6 +49,14 @@ class _Problem(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("n", ctypes.POINTER(ctypes.c_int)),
                 ("beta", ctypes.POINTER(ctypes.c_double)), ("eps", ctypes.c_double),
                 ("plain_sc", ctypes.c_int)]
+
+
+_COEF_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_void_p)
+
+
+class _ProblemVar(ctypes.Structure):
+    _fields_ = [("base", _Problem), ("beta_fn", _COEF_FN), ("rho_fn", _COEF_FN), ("rho0", ctypes.c_double),
+                ("ctx", ctypes.c_void_p)]
 
 
 class _TT(ctypes.Structure):
@@ -79,10 +87,19 @@ _SIGS = {
     "t2s2_device_count": (ctypes.c_int, []),
     "t2s2_build_operator": (ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.c_void_p,
                                            ctypes.POINTER(ctypes.c_void_p)]),
+    "t2s2_build_operator_var": (ctypes.c_int, [ctypes.POINTER(_ProblemVar), ctypes.c_void_p,
+                                               ctypes.POINTER(ctypes.c_void_p)]),
     "t2s2_build_spacetime_operator": (ctypes.c_int, [ctypes.POINTER(_Problem), ctypes.c_int, ctypes.c_double,
                                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "t2s2_spacetime_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.POINTER(_TT),
                                           ctypes.POINTER(_TT), ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    "t2s2_dirichlet_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.POINTER(_TT), ctypes.c_double,
+                                          ctypes.c_double, ctypes.POINTER(_TT), ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_void_p]),
+    "t2s2_solve_dirichlet": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.POINTER(_TT),
+                                            ctypes.POINTER(_TT), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.POINTER(_Info)]),
     "t2s2_op_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "t2s2_dim_matrices": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
                           + [ctypes.c_void_p] * 6),
@@ -136,6 +153,8 @@ _SIGS = {
                                            ctypes.c_void_p, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
                                            ctypes.c_void_p]),
     "t2s2_mlp_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_void_p]),
+    "t2s2_mlp_init_output": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_float,
+                                            ctypes.c_void_p]),
     "t2s2_mlp_calibrate_scale": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
     "t2s2_mlp_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
@@ -147,6 +166,10 @@ _SIGS = {
     "t2s2_autotune_report": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "t2s2_diff_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.POINTER(_TT),
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "t2s2_tt_fibre": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_TT), ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "t2s2_fastmath": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long,
+                                     ctypes.c_void_p]),
     "t2s2_kernel_launches": (ctypes.c_longlong, []),
     "t2s2_trace": (ctypes.c_int, [ctypes.c_int]),
     "t2s2_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -156,7 +179,7 @@ _SIGS = {
 
 # Kernel families of t2s2_trace_read, in the library's order.
 TRACE_FAMILIES = ["gemm", "apply", "local_solve", "small_factor", "elementwise", "apply_tc", "gemm_tc",
-                  "mlp"]
+                  "mlp", "cholqr", "sylvester", "dots"]
 
 
 def load():
@@ -278,6 +301,16 @@ class WarmStartNet:
                                                _stream_handle(None)), "t2s2_mlp_pack_target")
         return targets, uu
 
+    def pack_target_into(self, op: "Operator", u: "TT", targets, uu, i):
+        """Pack one device TT into slot i of the arrays of pack_targets."""
+        per = self.d * self.ru * self.mmax * self.ru
+        if targets.numel() < (i + 1) * per or uu.numel() < i + 1:
+            raise ValueError("slot outside the target arrays")
+        s = u._struct()
+        _check(load().t2s2_mlp_pack_target(self._h, op.handle, ctypes.byref(s),
+                                           targets.data_ptr() + 4 * i * per, uu.data_ptr() + 4 * i,
+                                           _stream_handle(None)), "t2s2_mlp_pack_target")
+
     def _batch_ptrs(self, P, targets, uu, lo, hi):
         per = self.d * self.ru * self.mmax * self.ru
         n = P.shape[0]
@@ -296,37 +329,14 @@ class WarmStartNet:
         return loss.value
 
     def init_output_bias(self, op: "Operator", u: "TT", weight_scale=0.1):
-        """Start the network's output at a representative target: the output
-        bias takes the cores of u rounded to the network's rank (t2s2_round),
-        and the output weights are scaled by weight_scale, so that X(p) starts
-        near u for every p and training learns the deviations."""
-        import torch
+        """Start the network's output at a representative target u
+        (t2s2_mlp_init_output): the output bias takes the cores of u rounded to
+        the network's rank, the output weights are scaled by weight_scale."""
         if u.d != self.d or u.m != self.m:
             raise ValueError("u does not live on the network's grid")
-        v = TT.empty(u.m, max(self.r, max(u.r)))
-        for k in range(self.d):
-            n = u.r[k] * u.m[k] * u.r[k + 1]
-            v.buffers[k][:n].copy_(u.buffers[k][:n])
-        v.r = list(u.r)
-        t2s2_round(op, v, 0.0, self.r)
-        if max(v.r[1:-1]) > self.r:
-            raise RuntimeError("rounding did not reach the network rank")
-        cores = []
-        for k in range(self.d):
-            a = 1 if k == 0 else self.r
-            b = 1 if k == self.d - 1 else self.r
-            c = torch.zeros((a, self.m[k], b), dtype=torch.float64, device="cuda")
-            ra, rb = v.r[k], v.r[k + 1]
-            c[:ra, :, :rb] = v.buffers[k][:ra * self.m[k] * rb].view(ra, self.m[k], rb)
-            cores.append(c.reshape(-1))
-        p = self.params()
-        h, ind, od = self.hidden, self.in_dim, self.out_dim
-        ow3 = h * ind + h + h * h + h
-        ob3 = ow3 + od * h
-        p[ow3:ob3] *= weight_scale
-        p[ob3:ob3 + od - 1] = torch.cat(cores).to(torch.float32)
-        p[ob3 + od - 1] = 0.0
-        self.set_params(p)
+        s = u._struct()
+        _check(load().t2s2_mlp_init_output(self._h, op.handle, ctypes.byref(s), float(weight_scale),
+                                           _stream_handle(None)), "t2s2_mlp_init_output")
 
     def calibrate_scale(self, P, targets, uu, lo=0, hi=None):
         """Shift the log-scale bias so that X(p) starts at the targets' size."""
@@ -364,6 +374,17 @@ class WarmStartNet:
                "t2s2_mlp_predict")
         x._sync_ranks()
         return x
+
+
+def t2s2_fastmath(x):
+    """(rsqrt, rcp) of a float64 CUDA tensor by the library's Newton-refined
+    FP64 routines (t2s2_fastmath)."""
+    import torch
+    x = x.to(device="cuda", dtype=torch.float64).contiguous()
+    rs, rc = torch.empty_like(x), torch.empty_like(x)
+    _check(load().t2s2_fastmath(x.data_ptr(), rs.data_ptr(), rc.data_ptr(), x.numel(), _stream_handle(None)),
+           "t2s2_fastmath")
+    return rs, rc
 
 
 def t2s2_kernel_launches() -> int:
@@ -465,6 +486,35 @@ def t2s2_build_operator(d, n, beta, eps, plain_sc=False, stream=None) -> Operato
     _check(lib.t2s2_build_operator(ctypes.byref(prob), _stream_handle(stream), ctypes.byref(h)),
            "t2s2_build_operator")
     return Operator(h, d, n, beta, float(eps), bool(plain_sc))
+
+
+def t2s2_build_operator_var(d, n, beta_ref, eps, beta_fns=None, rho_fns=None, rho0=0.0, plain_sc=False,
+                            stream=None) -> Operator:
+    """Operator with variable coefficients: beta_fns[k](x) (vectorised over
+    numpy arrays or scalar; None: the constant beta_ref[k]) and the reaction
+    rho0 + sum_k rho_fns[k](x_k).  beta_ref[k] picks dimension k's
+    superconsistent points."""
+    lib = load()
+    n = [int(v) for v in (n if np.ndim(n) else [n] * d)]
+    beta_ref = [float(v) for v in beta_ref]
+    na = (ctypes.c_int * d)(*n)
+    ba = (ctypes.c_double * d)(*beta_ref)
+
+    def wrap(fns, default):
+        if fns is None:
+            return _COEF_FN()
+        def f(k, x, _ctx):
+            g = fns[k]
+            return float(default(k) if g is None else g(np.float64(x)))
+        return _COEF_FN(f)
+
+    bfn = wrap(beta_fns, lambda k: beta_ref[k])
+    rfn = wrap(rho_fns, lambda k: 0.0)
+    prob = _ProblemVar(_Problem(d, na, ba, float(eps), int(bool(plain_sc))), bfn, rfn, float(rho0), None)
+    h = ctypes.c_void_p()
+    _check(lib.t2s2_build_operator_var(ctypes.byref(prob), _stream_handle(stream), ctypes.byref(h)),
+           "t2s2_build_operator_var")
+    return Operator(h, d, n, beta_ref, float(eps), bool(plain_sc))
 
 
 def t2s2_build_spacetime_operator(d, n, beta, eps, n_t, t_len, plain_sc=False, stream=None) -> Operator:
@@ -596,6 +646,15 @@ def t2s2_round(op: Operator, x: TT, tol, rmax=0, stream=None):
     return x
 
 
+def t2s2_tt_fibre(op: Operator, x: TT, mode: int, idx, stream=None) -> np.ndarray:
+    """x along `mode` with the other indices fixed at idx (d entries)."""
+    ia = (ctypes.c_int * x.d)(*[int(v) for v in idx])
+    out = np.zeros(x.m[mode] if 0 <= mode < x.d else 1)
+    _check(load().t2s2_tt_fibre(op.handle, ctypes.byref(x._struct()), int(mode), ia, out.ctypes.data,
+                                _stream_handle(stream)), "t2s2_tt_fibre")
+    return out
+
+
 def t2s2_norm(op: Operator, x: TT, stream=None) -> float:
     out = ctypes.c_double()
     _check(load().t2s2_norm(op.handle, ctypes.byref(x._struct()), ctypes.byref(out),
@@ -660,6 +719,32 @@ def t2s2_solve_batched(ops, bs, xs, tol, rmax, max_sweeps=50, prec=FP64, workers
     for i, x in enumerate(xs):
         x.r = [int(xarr[i].r[k]) for k in range(x.d + 1)]
     return [_info(sts[i], infos[i]) for i in range(n)]
+
+
+def t2s2_dirichlet_rhs(op: Operator, b: TT, g: TT, out: TT, tol, rmax=0, c_mass=0.0, c_op=1.0, stream=None):
+    """out = round(b - (c_mass M_full + c_op A_full) g): the source of the
+    zero-data correction for Dirichlet data g (a TT on the full GLL grid)."""
+    sb, sg, so = b._struct(), g._struct(), out._struct()
+    _check(load().t2s2_dirichlet_rhs(op.handle, ctypes.byref(sb), ctypes.byref(sg), float(c_mass), float(c_op),
+                                     ctypes.byref(so), float(tol), int(rmax), _stream_handle(stream)),
+           "t2s2_dirichlet_rhs")
+    out._sync_ranks()
+    return out
+
+
+def t2s2_solve_dirichlet(op: Operator, b: TT, g, x: TT, tol, rmax, max_sweeps=50, prec=FP64, c_mass=0.0,
+                         c_op=1.0, stream=None, allow_noconv=False) -> SolveInfo:
+    """Solve with Dirichlet data g (a full-grid TT, or None for zero data);
+    x: initial guess in, interior values of u out."""
+    info = _Info()
+    sb, sx = b._struct(), x._struct()
+    gp = ctypes.byref(g._struct()) if g is not None else None
+    st = load().t2s2_solve_dirichlet(op.handle, ctypes.byref(sb), gp, ctypes.byref(sx), float(c_mass),
+                                     float(c_op), float(tol), int(rmax), int(max_sweeps), int(prec),
+                                     _stream_handle(stream), ctypes.byref(info))
+    _check(st, "t2s2_solve_dirichlet", ok=(0, 4) if allow_noconv else (0,))
+    x._sync_ranks()
+    return _info(st, info)
 
 
 def t2s2_cn_step(op: Operator, u: TT, dt, tol, rmax, prec=FP64, stream=None) -> SolveInfo:

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -396,6 +397,27 @@ static t2s2_status upload_operator(t2s2_op op, cudaStream_t st, t2s2_op* out) {
   e = cudaMemcpyAsync(op->dmat, host.data(), sizeof(double) * total, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(op->fmat, hostf.data(), sizeof(float) * total, cudaMemcpyHostToDevice, st);
+  // the full matrices of the space dimensions (boundary-data lifting)
+  size_t nfull = 0;
+  for (int k = 0; k < op->d; ++k) nfull += op->dims[k].Rf.size() + op->dims[k].Lf.size();
+  if (e == cudaSuccess && nfull > 0) {
+    std::vector<double> hf;
+    hf.reserve(nfull);
+    for (int k = 0; k < op->d; ++k) {
+      hf.insert(hf.end(), op->dims[k].Rf.begin(), op->dims[k].Rf.end());
+      hf.insert(hf.end(), op->dims[k].Lf.begin(), op->dims[k].Lf.end());
+    }
+    e = cudaMalloc(&op->dfull, sizeof(double) * nfull);
+    if (e == cudaSuccess) e = cudaMemcpy(op->dfull, hf.data(), sizeof(double) * nfull, cudaMemcpyHostToDevice);
+    size_t o = 0;
+    for (int k = 0; k < op->d && e == cudaSuccess; ++k) {
+      if (op->dims[k].Rf.empty()) continue;
+      op->dRf[k] = op->dfull + o;
+      o += op->dims[k].Rf.size();
+      op->dLf[k] = op->dfull + o;
+      o += op->dims[k].Lf.size();
+    }
+  }
   if (e == cudaSuccess) e = cudaMallocHost(&op->hbuf, sizeof(double) * 4096);
   if (e == cudaSuccess) e = cudaMalloc(&op->dstat, sizeof(int) * 64);
   if (e == cudaSuccess) e = cudaMalloc(&op->gcnt, sizeof(int) * kGemmCounters);
@@ -454,6 +476,46 @@ t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op*
   return upload_operator(op, static_cast<cudaStream_t>(stream), out);
 }
 
+t2s2_status t2s2_build_operator_var(const t2s2_problem_var* var, void* stream, t2s2_op* out) {
+  if (!var || !out) return T2S2_EINVAL;
+  const t2s2_problem* prob = &var->base;
+  if (!prob->n || !prob->beta || !std::isfinite(var->rho0)) return T2S2_EINVAL;
+  *out = nullptr;
+  if (prob->d < 1 || prob->d > T2S2_MAX_D || !(prob->eps > 0.0) || !std::isfinite(prob->eps))
+    return T2S2_EINVAL;
+  for (int k = 0; k < prob->d; ++k) {
+    if (prob->n[k] < 3 || prob->n[k] > T2S2_MAX_N || !std::isfinite(prob->beta[k])) return T2S2_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return T2S2_ENODEV;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess || p.major != 10 || p.minor != 3) return T2S2_ENODEV;
+  t2s2_op op = new t2s2_op_s();
+  op->device = dev;
+  op->d = prob->d;
+  op->eps = prob->eps;
+  op->plain = prob->plain_sc;
+  op->dims.resize(op->d);
+  for (int k = 0; k < op->d; ++k) {
+    op->n[k] = prob->n[k];
+    op->m[k] = prob->n[k] - 2;
+    op->beta[k] = prob->beta[k];
+    std::function<double(double)> b, r;
+    if (var->beta_fn) b = [var, k](double x) { return var->beta_fn(k, x, var->ctx); };
+    const double r0 = k == 0 ? var->rho0 : 0.0;
+    if (var->rho_fn) {
+      r = [var, k, r0](double x) { return var->rho_fn(k, x, var->ctx) + r0; };
+    } else if (r0 != 0.0) {
+      r = [r0](double) { return r0; };
+    }
+    if (!build_dimension_coef(op->n[k], op->eps, op->beta[k], op->plain, b, r, &op->dims[k])) {
+      delete op;
+      return T2S2_EINVAL;
+    }
+  }
+  return upload_operator(op, static_cast<cudaStream_t>(stream), out);
+}
+
 t2s2_status t2s2_build_spacetime_operator(const t2s2_problem* space, int n_t, double t_len, void* stream,
                                           t2s2_op* out) {
   if (!space || !out || !space->n || !space->beta) return T2S2_EINVAL;
@@ -498,6 +560,7 @@ t2s2_status t2s2_op_destroy(t2s2_op op) {
   if (!op) return T2S2_OK;
   if (op->dmat) cudaFree(op->dmat);
   if (op->fmat) cudaFree(op->fmat);
+  if (op->dfull) cudaFree(op->dfull);
   if (op->arena.base) cudaFree(op->arena.base);
   if (op->hbuf) cudaFreeHost(op->hbuf);
   if (op->dstat) cudaFree(op->dstat);

@@ -25,6 +25,10 @@ struct t2s2_op_s {
          *dB[T2S2_MAX_D] = {nullptr}, *dI[T2S2_MAX_D] = {nullptr}, *dTr[T2S2_MAX_D] = {nullptr},
          *dTi[T2S2_MAX_D] = {nullptr}, *dZr[T2S2_MAX_D] = {nullptr}, *dZi[T2S2_MAX_D] = {nullptr};
   float* fmat = nullptr;  // FP32 copies of all of the above, same layout
+  // space dimensions: the full m x n matrices Rf, Lf (every GLL node a
+  // column), for lifting boundary data; null for the time dimension
+  double* dfull = nullptr;
+  double *dRf[T2S2_MAX_D] = {nullptr}, *dLf[T2S2_MAX_D] = {nullptr};
   float* fptr[kMatsPerDim][T2S2_MAX_D] = {{nullptr}};
   t2s2::Arena arena;
   int team = 0;            // CTAs per cooperative local solve (0: whole GPU)
@@ -89,4 +93,9 @@ t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
                           double* out, ResidualCache* rc, bool screen);
 t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
                           double c_op, bool transformed, double* out, double* bnorm_io);
+// The alternating solve of (c_mass M + c_op A) x = b on bound TTs (solve.cu).
+t2s2_status solve_run(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c_mass, double c_op,
+                      double tol, int rmax, int max_sweeps, t2s2_precision prec, t2s2_solve_info* info);
+// Arena bytes of one alternating solve (solve.cu).
+size_t solve_bytes(t2s2_op op, int rmax, int rfmax, t2s2_precision prec);
 }  // namespace t2s2

@@ -364,7 +364,7 @@ t2s2_status cholqr3_fused(const double* W, double* Q, double* R, int nlong, int 
   // work of two passes (the common case): Gram and triangular product
   // 2 n c^2 each, the L D L^T with its inverse 2 c^3 / 3
   const double fl = 2.0 * (4.0 * nlong * (double)c * c) + 2.0 * (2.0 * (double)c * c * c / 3.0);
-  TraceScope ts(kTrSmall, st, fl, 16.0 * nlong * c);
+  TraceScope ts(kTrCholQR, st, fl, 16.0 * nlong * c);
   void* args[] = {&a};
   T2S2_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)cholqr3_kernel, dim3(grid), dim3(kThreads), args, smem, st));
   return T2S2_OK;

@@ -352,21 +352,37 @@ static bool finish_dimension(int m, Dim1D* out) {
 }
 
 bool build_dimension(int n, double eps, double beta, int plain, Dim1D* out) {
+  return build_dimension_coef(n, eps, beta, plain, {}, {}, out);
+}
+
+bool build_dimension_coef(int n, double eps, double beta_ref, int plain, const std::function<double(double)>& beta_at,
+                          const std::function<double(double)>& rho_at, Dim1D* out) {
   const int N = n - 1, m = n - 2;
   out->n = n;
   out->x.assign(n, 0.0);
   out->eta.assign(m, 0.0);
   gll_points(N, out->x.data());
-  collocation_points(N, eps, beta, plain, out->eta.data());
+  collocation_points(N, eps, beta_ref, plain, out->eta.data());
   std::vector<double> R((size_t)m * n), D((size_t)m * n), D2((size_t)m * n);
   lagrange_matrices(N, out->x.data(), m, out->eta.data(), R.data(), D.data(), D2.data());
   out->Rt.assign((size_t)m * m, 0.0);
   out->Lt.assign((size_t)m * m, 0.0);
-  for (int j = 0; j < m; ++j)
-    for (int i = 0; i < m; ++i) {
-      out->Rt[(size_t)j * m + i] = R[(size_t)j * n + i + 1];
-      out->Lt[(size_t)j * m + i] = beta * D[(size_t)j * n + i + 1] - eps * D2[(size_t)j * n + i + 1];
+  out->Rf.assign((size_t)m * n, 0.0);
+  out->Lf.assign((size_t)m * n, 0.0);
+  for (int j = 0; j < m; ++j) {
+    const double bj = beta_at ? beta_at(out->eta[j]) : beta_ref;
+    const double rj = rho_at ? rho_at(out->eta[j]) : 0.0;
+    if (!std::isfinite(bj) || !std::isfinite(rj)) return false;
+    for (int i = 0; i < n; ++i) {
+      const size_t e = (size_t)j * n + i;
+      out->Rf[e] = R[e];
+      out->Lf[e] = bj * D[e] - eps * D2[e] + rj * R[e];
     }
+    for (int i = 0; i < m; ++i) {
+      out->Rt[(size_t)j * m + i] = out->Rf[(size_t)j * n + i + 1];
+      out->Lt[(size_t)j * m + i] = out->Lf[(size_t)j * n + i + 1];
+    }
+  }
   return finish_dimension(m, out);
 }
 

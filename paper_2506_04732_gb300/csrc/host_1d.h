@@ -1,6 +1,7 @@
 // Host-side FP64 construction of the per-dimension collocation matrices.
 #pragma once
 #include <complex>
+#include <functional>
 #include <vector>
 
 namespace t2s2 {
@@ -16,6 +17,7 @@ struct Dim1D {
   std::vector<double> Tr, Ti;  // complex Schur form of B: B = Z T Z^H, T upper triangular
   std::vector<double> Zr, Zi;  // unitary Schur basis
   std::vector<double> R0, L0;  // time dimension only: the columns of the initial node s = -1
+  std::vector<double> Rf, Lf;  // space dimensions: m x n, every GLL node a column (boundary data)
 };
 
 void gll_points(int N, double* x);
@@ -27,6 +29,13 @@ bool invert(int m, double* A);
 void hessenberg(int m, double* B, double* W);
 bool complex_schur(int m, const double* A, std::complex<double>* T, std::complex<double>* Z);
 bool build_dimension(int n, double eps, double beta, int plain, Dim1D* out);
+// As build_dimension with variable coefficients: the collocation points are
+// those of the reference speed beta_ref; at collocation point eta_j the rows
+// of D are scaled by beta_at(eta_j) (empty: beta_ref) and rho_at(eta_j) Rt
+// (empty: zero) is added, Lt = diag(beta(eta)) D - eps D2 + diag(rho(eta)) Rt.
+// False if a coefficient is not finite.
+bool build_dimension_coef(int n, double eps, double beta_ref, int plain, const std::function<double(double)>& beta_at,
+                          const std::function<double(double)>& rho_at, Dim1D* out);
 // The time dimension of the space-time form: m = n-1 unknowns (all GLL nodes
 // but s = -1), collocation at the n-1 Gauss points, Lt = scale * D.
 bool build_time_dimension(int n, double scale, Dim1D* out);

@@ -28,6 +28,8 @@
 #include <random>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "api_internal.h"
 #include "gemm_tc.h"
 #include "trace.h"
@@ -358,6 +360,20 @@ __global__ void pack_core_kernel(float* slot, const double* core, int ra, int m,
   }
 }
 
+// Writes one rounded FP64 core (ra x m x rb) into the network's output bias
+// as an FP32 core of the network's shape (na x m x nb), zero outside it.
+__global__ void bias_core_kernel(float* bias, const double* core, int ra, int m, int rb, int na, int nb) {
+  const long n = (long)na * m * nb;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const int a = (int)(e / ((long)m * nb)), rem = (int)(e % ((long)m * nb)), i = rem / nb, b = rem % nb;
+    bias[e] = (a < ra && b < rb) ? (float)core[((long)a * m + i) * rb + b] : 0.f;
+  }
+}
+
+__global__ void scale_kernel(float* v, long n, float f) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) v[e] *= f;
+}
+
 // The cores of X(p) for one sample: block k normalises raw core k of y
 // (fixed-order block sum) and scales core 0 by exp(sigma); FP64 out.
 struct UnpackArgs {
@@ -383,6 +399,76 @@ __global__ void unpack_cores_kernel(UnpackArgs u) {
 }
 
 int ew_blocks(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, 8L * kNumSMs)); }
+
+// Prediction for one parameter vector in one CTA: the three layers as
+// warp-per-row products with the operands rounded to BF16 and FP32 sums (the
+// arithmetic of the batched tensor-core layers, summed in another order),
+// then the cores of X(p) normalised and written as FP64 straight into the
+// caller's cores.  One launch instead of the batched path's GEMM, bias and
+// unpack launches; used for warm starts, where the solve waits on it.
+struct PredictArgs {
+  const float* p;
+  const float* w;
+  long long oW1, ob1, oW2, ob2, oW3, ob3;
+  int in_dim, hidden, odim, ncore, d;
+  int off[T2S2_MAX_D + 1];
+  double* out[T2S2_MAX_D];
+};
+constexpr int kPredictThreads = 512;
+constexpr size_t kPredictMaxSmem = 96 * 1024;
+
+size_t predict_smem_bytes(int in_dim, int hidden, int odim) {
+  return sizeof(float) * ((size_t)in_dim + 2 * (size_t)hidden + (size_t)odim + 32);
+}
+
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// out[row] = act(sum_i bf16(W[row, i]) bf16(x[i]) + bias[row]) for row < rows.
+__device__ void gemv_rows(const float* W, const float* bias, const float* x, float* out, int rows, int K,
+                          bool relu) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int row = warp; row < rows; row += nw) {
+    const float* wr = W + (long)row * K;
+    float acc = 0.f;
+    for (int i = lane; i < K; i += 32) acc = fmaf(bf16r(wr[i]), bf16r(x[i]), acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const float v = acc + bias[row];
+      out[row] = relu ? fmaxf(v, 0.f) : v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPredictThreads) predict_kernel(PredictArgs a) {
+  extern __shared__ float sm[];
+  float* xin = sm;
+  float* h1 = xin + a.in_dim;
+  float* h2 = h1 + a.hidden;
+  float* y = h2 + a.hidden;
+  float* red = y + a.odim;
+  for (int i = threadIdx.x; i < a.in_dim; i += blockDim.x) xin[i] = a.p[i];
+  __syncthreads();
+  gemv_rows(a.w + a.oW1, a.w + a.ob1, xin, h1, a.hidden, a.in_dim, true);
+  __syncthreads();
+  gemv_rows(a.w + a.oW2, a.w + a.ob2, h1, h2, a.hidden, a.hidden, true);
+  __syncthreads();
+  gemv_rows(a.w + a.oW3, a.w + a.ob3, h2, y, a.odim, a.hidden, false);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < a.d; ++k) {
+    const int o0 = a.off[k], o1 = a.off[k + 1];
+    float acc = 0.f;
+    for (int e = o0 + threadIdx.x; e < o1; e += blockDim.x) acc = fmaf(y[e], y[e], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    float ss = 0.f;
+    for (int w = 0; w < nw; ++w) ss += red[w];  // fixed order
+    const double f = (ss > 0.f ? 1.0 / sqrt((double)ss) : 0.0) * (k == 0 ? exp((double)y[a.ncore]) : 1.0);
+    for (int e = o0 + threadIdx.x; e < o1; e += blockDim.x) a.out[k][e - o0] = f * (double)y[e];
+    __syncthreads();
+  }
+}
 
 // Captured graphs hold buffer addresses: drop them whenever a buffer moves.
 void drop_graphs(t2s2_mlp net) {
@@ -826,9 +912,77 @@ t2s2_status t2s2_mlp_train(t2s2_mlp net, const float* P, int n, const float* tar
   return T2S2_OK;
 }
 
+t2s2_status t2s2_mlp_init_output(t2s2_mlp net, t2s2_op op, const t2s2_tt* u, float weight_scale, void* stream) {
+  if (!net || !op || !u || u->d != net->d || !std::isfinite(weight_scale)) return T2S2_EINVAL;
+  T2S2_TRY(check_tt(op, u));
+  for (int k = 0; k < net->d; ++k)
+    if (u->m[k] != net->m[k]) return T2S2_EINVAL;
+  const size_t mc = max_core(u);
+  T2S2_TRY(ensure_arena(op, tt_bytes(u) * 3 + 10 * mc * sizeof(double) + ((size_t)8 << 20)));
+  Ctx cx = make_ctx(op, stream);
+  DevTT du, v;
+  T2S2_TRY(bind_tt(cx, u, du, true));
+  int rc = 1;
+  for (int k = 0; k <= u->d; ++k) rc = std::max(rc, u->r[k]);
+  T2S2_TRY(tt_alloc(cx, v, du.d, du.m, du.r, rc));
+  T2S2_TRY(tt_copy(cx, du, v));
+  // u rounded to the network's rank (FP64 rounding, no tolerance)
+  T2S2_TRY(tt_round(cx, v, 0.0, net->r));
+  for (int k = 1; k < net->d; ++k)
+    if (v.r[k] > net->r) return T2S2_EINVAL;
+  for (int k = 0; k < net->d; ++k) {
+    const int na = k == 0 ? 1 : net->r, nb = k == net->d - 1 ? 1 : net->r;
+    const long n = (long)na * net->m[k] * nb;
+    bias_core_kernel<<<ew_blocks(n), 256, 0, cx.st>>>(net->params + net->ob3 + net->off[k], v.c[k], v.r[k],
+                                                     net->m[k], v.r[k + 1], na, nb);
+    T2S2_CUDA_TRY(cudaGetLastError());
+  }
+  const long nw = (long)net->odim * net->hidden;
+  scale_kernel<<<ew_blocks(nw), 256, 0, cx.st>>>(net->params + net->oW3, nw, weight_scale);
+  T2S2_CUDA_TRY(cudaGetLastError());
+  // the log-scale output starts at zero (0.0f is all zero bits)
+  T2S2_CUDA_TRY(cudaMemsetAsync(net->params + net->ob3 + net->ncore, 0, sizeof(float), cx.st));
+  T2S2_CUDA_TRY(cudaStreamSynchronize(cx.st));
+  return T2S2_OK;
+}
+
 t2s2_status t2s2_mlp_predict(t2s2_mlp net, const float* p, t2s2_tt* x, void* stream) {
   if (!net || !p || !x || x->d != net->d || !x->r || !x->cores || !x->cap) return T2S2_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t psmem = predict_smem_bytes(net->in_dim, net->hidden, net->odim);
+  if (x->loc == T2S2_DEVICE && psmem <= kPredictMaxSmem) {
+    // one launch, written straight into the caller's device cores; stream
+    // ordered (no synchronisation)
+    PredictArgs a;
+    for (int k = 0; k < net->d; ++k) {
+      const int ra = k == 0 ? 1 : net->r, rb = k == net->d - 1 ? 1 : net->r;
+      if ((size_t)ra * net->m[k] * rb > x->cap[k] || (x->m && x->m[k] != net->m[k]) || !x->cores[k])
+        return T2S2_EINVAL;
+      a.out[k] = x->cores[k];
+    }
+    static bool attr = false;
+    if (!attr) {
+      T2S2_CUDA_TRY(cudaFuncSetAttribute(predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kPredictMaxSmem));
+      attr = true;
+    }
+    T2S2_CUDA_TRY(cudaMemcpyAsync(net->pbuf, p, sizeof(float) * net->in_dim, cudaMemcpyDefault, st));
+    a.p = net->pbuf;
+    a.w = net->params;
+    a.oW1 = net->oW1; a.ob1 = net->ob1; a.oW2 = net->oW2; a.ob2 = net->ob2; a.oW3 = net->oW3; a.ob3 = net->ob3;
+    a.in_dim = net->in_dim; a.hidden = net->hidden; a.odim = net->odim; a.ncore = net->ncore; a.d = net->d;
+    for (int k = 0; k <= net->d; ++k) a.off[k] = net->off[k];
+    {
+      const double h = net->hidden;
+      TraceScope ts(kTrMlp, st, 2.0 * h * (net->in_dim + h + net->odim), 4.0 * h * (net->in_dim + h + net->odim));
+      predict_kernel<<<1, kPredictThreads, psmem, st>>>(a);
+      T2S2_CUDA_TRY(cudaGetLastError());
+    }
+    x->r[0] = 1;
+    for (int k = 1; k < net->d; ++k) x->r[k] = net->r;
+    x->r[net->d] = 1;
+    return T2S2_OK;
+  }
   T2S2_TRY(ensure_batch(net, 1));
   float* dp = net->pbuf;
   T2S2_CUDA_TRY(cudaMemcpyAsync(dp, p, sizeof(float) * net->in_dim, cudaMemcpyDefault, st));

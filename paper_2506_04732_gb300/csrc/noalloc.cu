@@ -34,8 +34,10 @@ void* g_noalloc_addr[kMaxDevices] = {nullptr};
 double g_noalloc_host[8];  // pageable host landing slot for the reduction result
 
 // Upper bound of the scratch tt_norm needs for this train: a copy of the
-// cores plus the largest per-core orthogonalisation step (LQ factors, the
-// three CholeskyQR passes, the neighbour product and split-K partials).
+// cores, sized as tt_norm allocates it (every interior core padded to
+// max(r_k, rc) x m_k x max(r_{k+1}, rc), rc the largest rank), plus the
+// largest per-core orthogonalisation step (LQ factors, the three CholeskyQR
+// passes, the neighbour product and split-K partials).
 size_t splitk_elems(int M, int N, int K, bool tA, bool tB) {
   Gemm<double> g;
   g.M = M; g.N = N; g.K = K; g.tA = tA; g.tB = tB;
@@ -44,8 +46,14 @@ size_t splitk_elems(int M, int N, int K, bool tA, bool tB) {
 
 size_t norm_scratch_bytes(const DevTT& x) {
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  int rc = 0;
+  for (int k = 0; k <= x.d; ++k) rc = std::max(rc, x.r[k]);
   size_t copy = 0;
-  for (int k = 0; k < x.d; ++k) copy += al(x.core_elems(k) * sizeof(double));
+  for (int k = 0; k < x.d; ++k) {
+    const size_t r0 = (k == 0) ? 1 : std::max(x.r[k], rc);
+    const size_t r1 = (k == x.d - 1) ? 1 : std::max(x.r[k + 1], rc);
+    copy += al(r0 * x.m[k] * r1 * sizeof(double));
+  }
   size_t step = 0;
   for (int k = x.d - 1; k >= 1; --k) {
     const int rk = x.r[k], cols = x.m[k] * x.r[k + 1];
@@ -120,7 +128,11 @@ t2s2_status t2s2_norm_noalloc(const t2s2_tt* x, double* out, void* stream) {
   // the status word must start at zero on every call (the array keeps the
   // previous call's contents)
   T2S2_CUDA_TRY(cudaMemsetAsync(cx.dstat, 0, 64 * sizeof(int), cx.st));
-  return tt_norm(cx, dv, out);
+  const t2s2_status st = tt_norm(cx, dv, out);
+  // On an error part of the work may still be queued on the array: let it
+  // finish before the next caller can take the lock.
+  if (st != T2S2_OK) (void)cudaStreamSynchronize(cx.st);
+  return st;
 }
 
 }  // extern "C"

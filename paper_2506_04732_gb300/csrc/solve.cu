@@ -210,6 +210,17 @@ struct PhaseTimer {
 // 7 and takes 10.3 ms, a kick of 8 raises them to 11 and takes 15 ms.
 constexpr int kStepKick = 4;
 
+// Sweeps without a halving of the residual, at the rank cap, after which a
+// solve stops early (T2S2_STALL overrides it; 0 turns the stop off).
+int stall_sweeps() {
+  static const int v = [] {
+    const char* e = std::getenv("T2S2_STALL");
+    const int k = e ? std::atoi(e) : 8;
+    return k < 0 ? 8 : k;
+  }();
+  return v;
+}
+
 int amen_kick() {
   static const int k = [] {
     const char* e = std::getenv("T2S2_KICK");
@@ -839,20 +850,34 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
   const bool verbose = ev && ev[0] == '1';
   if (verbose) fprintf(stderr, "[t2s2] solve d=%d c_mass=%g c_op=%g tol=%g rmax=%d initial residual %.3e\n",
                        op->d, c_mass, c_op, tol, rmax, res);
+  // stagnation under the rank cap: once some bond carries rmax + kick and the
+  // residual has not halved in stall_sweeps() sweeps, more sweeps at that cap
+  // do not reach tol (the cap, not the sweep count, limits the solution)
+  const int kStallSweeps = stall_sweeps();
+  double mark = res;
+  int mark_sweep = 0;
   while (res > tol && sweeps < max_sweeps) {
     T2S2_TRY(am.sweep());
     ++sweeps;
     am.ph(9);
     T2S2_TRY(residual_fast(op, cx, b, am.x, c_mass, c_op, &res, &rcache, false));
+    if (res < 0.5 * mark) {
+      mark = res;
+      mark_sweep = sweeps;
+    }
+    int rx = 1;
+    for (int k = 0; k <= op->d; ++k) rx = std::max(rx, am.x.r[k]);
+    const bool stalled =
+        kStallSweeps > 0 && res > tol && rx >= am.rcap && sweeps - mark_sweep >= kStallSweeps;
     T2S2_TRY(am.collect_iters());
     if (verbose) {
       double rt = 0.0;
       T2S2_TRY(residual_impl(op, cx, am.f, am.x, c_mass, c_op, true, &rt, nullptr));
       fprintf(stderr, "[t2s2] sweep %d residual %.3e (transformed %.3e) ranks", sweeps, res, rt);
       for (int k = 0; k <= op->d; ++k) fprintf(stderr, " %d", am.x.r[k]);
-      fprintf(stderr, " local_iters %lld\n", am.local_iters);
+      fprintf(stderr, " local_iters %lld%s\n", am.local_iters, stalled ? " (stalled at the rank cap)" : "");
     }
-    if (res <= tol) break;
+    if (res <= tol || stalled) break;
     am.ph(10);
     T2S2_TRY(tt_orth_right(cx, am.x));
   }
@@ -1104,6 +1129,17 @@ static size_t refine_extra_bytes(t2s2_op op, int rcap, int rf) {
   const size_t R = (size_t)rf + 2 * rcap;
   const size_t train = (size_t)op->d * R * mm * R * sizeof(double);
   return 6 * train + Amen::bytes_needed(op->d, op->m, rcap, std::min(kSmallMax, 2 * rcap), amen_kick(), 40);
+}
+
+t2s2_status solve_run(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c_mass, double c_op,
+                      double tol, int rmax, int max_sweeps, t2s2_precision prec, t2s2_solve_info* info) {
+  return solve_impl(op, cx, b, xio, c_mass, c_op, tol, rmax, max_sweeps, prec, info);
+}
+
+size_t solve_bytes(t2s2_op op, int rmax, int rfmax, t2s2_precision prec) {
+  size_t need = Amen::bytes_needed(op->d, op->m, rmax + amen_kick(), rfmax, amen_kick(), 40);
+  if (prec != T2S2_FP64) need += refine_extra_bytes(op, rmax + amen_kick(), rfmax);
+  return need;
 }
 
 static t2s2_status solve_entry(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double c_mass, double c_op,

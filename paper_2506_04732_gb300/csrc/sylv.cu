@@ -359,7 +359,7 @@ t2s2_status sylv_rb1(const SylvProblem& P, cudaStream_t st) {
   }
   const size_t smem = sylv_smem_bytes(P.ra, P.m);
   const double N = (double)P.ra * P.m;
-  TraceScope ts(kTrLocal, st, 2.0 * N * (P.ra + P.m) * 3.0, 0.0);
+  TraceScope ts(kTrSylv, st, 2.0 * N * (P.ra + P.m) * 3.0, 0.0);
   (void)launch_pdl(sylv_rb1_kernel, 1, kSylvThreads, smem, st, P);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;

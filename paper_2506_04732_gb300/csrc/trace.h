@@ -13,7 +13,10 @@ enum TraceFamily {
   kTrApplyTc = 5,
   kTrGemmTc = 6,
   kTrMlp = 7,
-  kTrFamilies = 8
+  kTrCholQR = 8,  // the fused shifted CholeskyQR (one cooperative launch per QR)
+  kTrSylv = 9,    // the rank-1-right local solves (Schur-basis Sylvester solver)
+  kTrDots = 10,   // TT inner products (binary64 and double-double)
+  kTrFamilies = 11
 };
 
 // Count one launch of `fam` with its algorithmic FLOPs and DRAM-level bytes;

@@ -311,7 +311,7 @@ t2s2_status tt_dots_dd(Ctx& cx, int n, const DevTT* const* u, const DevTT* const
   // count, sets the time, so every SM takes a share
   const int G = (int)std::max(1L, cap);
   {
-    TraceScope ts(kTrGemm, cx.st, fl, 0.0);  // algorithmic: 2 per product term
+    TraceScope ts(kTrDots, cx.st, fl, 0.0);  // algorithmic: 2 per product term
     void* args[] = {&a};
     T2S2_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tt_norm2_dd_kernel, dim3(G), dim3(kDotThreads), args, 0,
                                               cx.st));
@@ -378,7 +378,7 @@ t2s2_status tt_dots(Ctx& cx, int n, const DevTT* const* u, const DevTT* const* v
   const long want = std::max((st1 + kDotThreads - 1) / kDotThreads, (32 * st2 + kDotThreads - 1) / kDotThreads);
   const int G = (int)std::max(1L, std::min(cap, want));
   {
-    TraceScope ts(kTrGemm, cx.st, fl, 0.0);
+    TraceScope ts(kTrDots, cx.st, fl, 0.0);
     void* args[] = {&a};
     T2S2_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tt_dots_kernel, dim3(G), dim3(kDotThreads), args, 0,
                                               cx.st));

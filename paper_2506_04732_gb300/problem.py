@@ -7,7 +7,8 @@ Samples a workload's analytic factors at the nodes the library reports
   grid, built exactly from separable terms (the paper derives sources from
   analytic solutions, Results "Global Accuracy"); one rank-2 block per term.
 * ``solution_cores``: u* (or an initial condition) on the interior GLL grid,
-  one rank-1 block per term.
+  one rank-1 block per term; ``full_solution_cores`` the same on every GLL
+  node (Dirichlet data).
 * ``spacetime_*``: the same for the unified space-time form (time as one
   more collocated dimension, first): the source before the initial
   condition is lifted, and the initial condition itself.
@@ -71,6 +72,47 @@ def source_cores(problem, op):
     return _block_tt(blocks)
 
 
+def varcoef_source_cores(vp, op):
+    """b = -eps Laplace u* + beta . grad u* + rho u* on the collocation grid
+    for a workloads.VarCoefProblem: per term and dimension the factor
+    beta_k(eta) phi' - eps phi'' + (rho_k(eta) [+ rho0 for k = 0]) phi."""
+    problem = vp.problem
+    d, eps = problem.d, problem.eps
+    blocks = []
+    for t in problem.terms:
+        cores = []
+        for k in range(d):
+            _, eta = op.nodes(k)
+            f = t.factors[k]
+            p = f(eta)
+            rho = vp.rho_fn(k)(eta) + (vp.rho0 if k == 0 else 0.0)
+            l = vp.beta_fn(k)(eta) * f(eta, 1) - eps * f(eta, 2) + rho * p
+            n = len(eta)
+            if d == 1:
+                c = l.reshape(1, n, 1)
+            elif k == 0:
+                c = np.stack([l, p], axis=1).reshape(1, n, 2)
+            elif k == d - 1:
+                c = np.stack([p, l], axis=0).reshape(2, n, 1)
+            else:
+                c = np.zeros((2, n, 2))
+                c[0, :, 0] = p
+                c[1, :, 0] = l
+                c[1, :, 1] = p
+            cores.append(c)
+        cores[0] = cores[0] * t.coef
+        blocks.append(cores)
+    return _block_tt(blocks)
+
+
+def build_operator_var(vp, stream=None):
+    """The library operator of a workloads.VarCoefProblem."""
+    from . import t2s2_build_operator_var
+    p = vp.problem
+    return t2s2_build_operator_var(p.d, p.n, p.beta, p.eps, [vp.beta_fn(k) for k in range(p.d)],
+                                   [vp.rho_fn(k) for k in range(p.d)], vp.rho0, p.plain_sc, stream)
+
+
 def solution_cores(problem, op):
     blocks = []
     for t in problem.terms:
@@ -78,6 +120,20 @@ def solution_cores(problem, op):
         for k in range(problem.d):
             x, _ = op.nodes(k)
             cores.append(t.factors[k](x[1:-1]).reshape(1, -1, 1))
+        cores[0] = cores[0] * t.coef
+        blocks.append(cores)
+    return _block_tt(blocks)
+
+
+def full_solution_cores(problem, op):
+    """u* at every GLL node (the full grid, n per dimension): Dirichlet data
+    g = u* on the boundary, extended by u* itself inside."""
+    blocks = []
+    for t in problem.terms:
+        cores = []
+        for k in range(problem.d):
+            x, _ = op.nodes(k)
+            cores.append(t.factors[k](x).reshape(1, -1, 1))
         cores[0] = cores[0] * t.coef
         blocks.append(cores)
     return _block_tt(blocks)

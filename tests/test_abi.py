@@ -73,3 +73,26 @@ def test_operator_builders_validate_before_touching_a_device():
     assert build(16, [8] * 16, [0.25] * 16, 1e-2, n_t=6, t_len=1.0) == EINVAL   # 17 dimensions
     assert build(**good) == ENODEV
     assert build(**good, n_t=6, t_len=1.0) == ENODEV
+
+
+def test_variable_coefficient_builder_validates_before_touching_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2506_04732_gb300 as T
+    lib = T.load()
+    EINVAL, ENODEV = 1, 7
+
+    def build(n=(8, 8), beta=(0.6, 0.8), eps=1e-2, rho0=0.0, fn=True):
+        base = T._Problem(2, (ctypes.c_int * 2)(*n), (ctypes.c_double * 2)(*beta), float(eps), 0)
+        f = T._COEF_FN(lambda k, x, c: 1.0) if fn else T._COEF_FN()
+        prob = T._ProblemVar(base, f, f, float(rho0), None)
+        h = ctypes.c_void_p()
+        return lib.t2s2_build_operator_var(ctypes.byref(prob), None, ctypes.byref(h))
+
+    assert build(n=(2, 8)) == EINVAL
+    assert build(eps=0.0) == EINVAL
+    assert build(rho0=float("nan")) == EINVAL
+    assert build() == ENODEV
+    assert build(fn=False) == ENODEV
+    assert lib.t2s2_build_operator_var(None, None, ctypes.byref(ctypes.c_void_p())) == EINVAL

@@ -107,3 +107,19 @@ def test_oracle_solves_are_complete_and_timed_one_by_one():
 def test_oracle_solves_stop_at_the_budget():
     # a budget shorter than one solve ends the child with nothing finished
     assert bench.oracle_solves("config1()", 5, 0.5) == []
+
+
+def test_kernel_names_map_to_trace_families():
+    # device-time ranking in bench.py groups kernels by the library's trace
+    # families; unknown kernels (torch's own) are "other"
+    kf = bench.kernel_family
+    assert kf("void t2s2::(anonymous namespace)::cholqr3_kernel<26>(t2s2::CqrArgs)") == "cholqr"
+    assert kf("t2s2::sylv_rb1_kernel(t2s2::SylvProblem)") == "sylvester"
+    assert kf("void t2s2::small_group_kernel<8, 16>(t2s2::GroupArgs)") == "gemm"
+    assert kf("void t2s2::small_kernel<4, 4>(t2s2::Gemm<double>)") == "gemm"
+    assert kf("t2s2::tt_norm2_dd_kernel(t2s2::DdArgs)") == "dots"
+    assert kf("void t2s2::apply_kernel<t2s2::ParamWork, 16, 16>(t2s2::ApplyBatch)") == "apply"
+    assert kf("void t2s2::apply_tc_kernel<2>(t2s2::TcArgs)") == "apply_tc"
+    assert kf("t2s2::(anonymous namespace)::k_sumsq(double const*, unsigned long, double*)") == "elementwise"
+    assert kf("void at::native::vectorized_elementwise_kernel<4, at::native::FillFunctor<unsigned char>>") == "other"
+    assert set(bench.ALU_FAMILIES) <= set(bench.FAMILIES)

@@ -185,3 +185,115 @@ def test_graph_replayed_training_matches_eager(T):
     (pe, le), (pg, lg) = nets
     assert np.array_equal(pe, pg)
     assert le == lg
+
+
+def test_config4_rank1_warm_start_keeps_sweeps_and_answer(T):
+    """The warm-start workload itself: d = 6, n = 32, diffusion ratio
+    log-uniform in [1e-4, 1e-2], rank-4 source from 8 parameters, tol 1e-8,
+    rank cap 20.  A rank-1 network output keeps the first sweep on rank-1
+    right interfaces, where a cold solve of this family usually converges in
+    one sweep: held-out solves started from the network's guess need no more
+    sweeps than cold ones, start from a smaller residual, and reach the same
+    answer."""
+    from paper_2506_04732_gb300 import problem as P
+    import time
+    d, n, rmax, tol = 6, 32, 20, 1e-8
+    m = n - 2
+
+    def solve(p, net=None):
+        op = P.build_operator(p)
+        b = T.TT.from_cores(P.source_cores(p, op))
+        x = T.TT.from_cores([np.ones((1, m, 1))] * d, rcap=rmax + T.RANK_KICK)
+        if net is not None:
+            net.predict(W.warm_features(p), x)
+        r0 = T.t2s2_residual(op, b, x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = T.t2s2_solve(op, b, x, tol, rmax, 50)
+        torch.cuda.synchronize()
+        return op, x, info, r0, time.perf_counter() - t0
+
+    ntrain = 128
+    net = T.WarmStartNet(W.WARM_IN_DIM, 256, [m] * d, 1, rmax + T.RANK_KICK, seed=1)
+    per = net.d * net.ru * net.mmax * net.ru
+    tg = torch.zeros(ntrain * per, dtype=torch.float32, device="cuda")
+    uu = torch.zeros(ntrain, dtype=torch.float32, device="cuda")
+    train = [W.config4(10000 + i, d=d, n=n) for i in range(ntrain)]
+    keep = None
+    for i, p in enumerate(train):
+        op, x, info, _, _ = solve(p)
+        assert info.residual <= tol
+        net.pack_target_into(op, x, tg, uu, i)
+        if i == 0:
+            keep = (op, x)
+    Pf = torch.tensor(np.stack([W.warm_features(p) for p in train]), device="cuda")
+    net.init_output_bias(*keep)
+    net.calibrate_scale(Pf, tg, uu)
+    for it in range(1500):
+        lo = (it * 64) % (ntrain - 64 + 1)
+        net.train_step(Pf, tg, uu, 2e-3 if it < 1000 else 4e-4, lo=lo, hi=lo + 64)
+    sw_c = sw_w = 0
+    t_c = t_w = 0.0
+    r_c, r_w = [], []
+    for i in range(16):
+        p = W.config4(90000 + i, d=d, n=n)
+        op, xc, ic, rc, tc = solve(p)
+        _, xw, iw, rw, tw = solve(p, net)
+        assert ic.residual <= tol and iw.residual <= tol
+        assert T.t2s2_diff_norm(op, xc, xw) <= 1e-6 * T.t2s2_norm(op, xc)
+        sw_c += ic.sweeps
+        sw_w += iw.sweeps
+        t_c += tc
+        t_w += tw
+        r_c.append(rc)
+        r_w.append(rw)
+    print(f"config 4, 16 held-out: sweeps cold {sw_c} warm {sw_w}; solve ms cold {1e3 * t_c / 16:.2f} "
+          f"warm {1e3 * t_w / 16:.2f}; initial residual median cold {np.median(r_c):.2e} warm {np.median(r_w):.2e}")
+    assert sw_w <= sw_c
+    assert np.median(r_w) < np.median(r_c)
+
+
+def test_init_output_starts_at_the_rounded_solution(T):
+    """t2s2_mlp_init_output: with the output weights scaled to zero, X(p) is
+    the target rounded to the network's rank (normalised cores times
+    exp(0)), for every p; the other output weights are scaled exactly."""
+    from paper_2506_04732_gb300 import problem as P
+    d, m, r = 4, 6, 3
+    net = T.WarmStartNet(15, 32, [m] * d, r, 8, seed=2)
+    op = P.build_operator(W.config1(d=d, n=m + 2))
+    u = W.random_tt(d, m, [1, 5, 6, 4, 1], seed=3)
+    before = net.params().cpu().numpy()
+    h, ind, od = net.hidden, net.in_dim, net.out_dim
+    ow3 = h * ind + h + h * h + h
+    ob3 = ow3 + od * h
+    net.init_output_bias(op, T.TT.from_cores(u), weight_scale=0.5)
+    after = net.params().cpu().numpy()
+    assert np.array_equal(after[:ow3], before[:ow3])
+    assert np.array_equal(after[ow3:ob3], 0.5 * before[ow3:ob3])
+    assert after[-1] == 0.0
+    net.init_output_bias(op, T.TT.from_cores(u), weight_scale=0.0)
+    want = OT.round_tt(u, 0.0, r)
+    for seed in (5, 6):
+        x = T.TT.empty([m] * d, r)
+        net.predict(np.random.default_rng(seed).standard_normal(15).astype(np.float32), x)
+        got = x.cores()
+        # the same direction as the rounded target, at unit-norm cores
+        cos = OT.dot(got, want) / (OT.norm(got) * OT.norm(want))
+        assert abs(cos - 1.0) <= 1e-6
+
+
+def test_single_launch_prediction_matches_batched_layers(T):
+    """The one-CTA prediction (device cores) and the batched tensor-core layers
+    (taken for host cores) compute the same BF16-operand products in another
+    summation order: their cores agree to FP32 rounding."""
+    for r in (1, 4):
+        net, params, Pm, targets, tg, uu, (d, m, _) = _setup(T, hidden=64, d=5, m=9, r=r, ru=6, seed=7)
+        for i in range(3):
+            xd = T.TT.empty(m, r)
+            xh = T.TT.empty(m, r, device="cpu")
+            net.predict(Pm[i], xd)
+            net.predict(Pm[i], xh)
+            torch.cuda.synchronize()
+            assert xd.r == xh.r == [1] + [r] * (d - 1) + [1]
+            for a, b in zip(xd.cores(), xh.cores()):
+                assert np.max(np.abs(a - b)) <= 2e-5 * np.max(np.abs(b)), (r, i)
