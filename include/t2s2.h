@@ -525,6 +525,12 @@ long long t2s2_kernel_launches(void);
  * While on, every launch is bracketed by two CUDA events on its stream. */
 t2s2_status t2s2_trace(int enable);
 
+/* Average time (ms) of an empty kernel launched as the library launches its
+ * kernels and bracketed by two CUDA events, over n launches on `stream`: the
+ * share of a traced launch's event time that is not the kernel's work.
+ * Synchronises. */
+t2s2_status t2s2_trace_overhead(int n, void* stream, double* ms);
+
 /* Totals since the last t2s2_trace call for one family: launches, summed
  * event time in ms, algorithmic FLOPs and algorithmic bytes (operands read
  * once, results written once).  Synchronises on the recorded events.

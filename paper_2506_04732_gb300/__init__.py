@@ -22,7 +22,7 @@ __all__ = ["load", "T2S2Error", "Operator", "TT", "SolveInfo", "FP64", "FP32_REF
            "t2s2_norm", "t2s2_diff_norm", "t2s2_norm_noalloc", "t2s2_residual", "t2s2_solve", "t2s2_solve_batched", "t2s2_cn_step", "t2s2_be_step",
            "t2s2_device_count", "t2s2_strerror", "t2s2_gemm", "WarmStartNet", "t2s2_apply_batched",
            "t2s2_autotune_report", "t2s2_kernel_launches", "t2s2_trace",
-           "t2s2_trace_read", "t2s2_fastmath", "t2s2_tt_fibre", "TRACE_FAMILIES", "lib_path", "t2s2_dim_matrices", "DIM_SPACE",
+           "t2s2_trace_read", "t2s2_trace_overhead", "t2s2_fastmath", "t2s2_tt_fibre", "TRACE_FAMILIES", "lib_path", "t2s2_dim_matrices", "DIM_SPACE",
            "t2s2_build_spacetime_operator", "t2s2_spacetime_rhs", "t2s2_build_operator_var", "t2s2_dirichlet_rhs", "t2s2_solve_dirichlet",
            "DIM_SPACE_PLAIN", "DIM_TIME"]
 
@@ -172,6 +172,7 @@ _SIGS = {
                                      ctypes.c_void_p]),
     "t2s2_kernel_launches": (ctypes.c_longlong, []),
     "t2s2_trace": (ctypes.c_int, [ctypes.c_int]),
+    "t2s2_trace_overhead": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "t2s2_trace_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
@@ -395,6 +396,13 @@ def t2s2_kernel_launches() -> int:
 def t2s2_trace(enable: bool):
     """Clear the per-family counters; turn CUDA-event timing on or off."""
     _check(load().t2s2_trace(1 if enable else 0), "t2s2_trace")
+
+
+def t2s2_trace_overhead(n=200, stream=None) -> float:
+    """Event-bracketed time (ms) of an empty library-style launch."""
+    out = ctypes.c_double()
+    _check(load().t2s2_trace_overhead(int(n), _stream_handle(stream), ctypes.byref(out)), "t2s2_trace_overhead")
+    return out.value
 
 
 def t2s2_trace_read(family) -> dict:

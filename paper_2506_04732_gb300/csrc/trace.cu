@@ -77,11 +77,49 @@ void trace_add_work(int fam, double flops, double bytes) {
 
 }  // namespace t2s2
 
+namespace t2s2 {
+namespace {
+// An empty kernel launched the way the library's kernels are, to measure what
+// a traced launch costs beyond its work.
+__global__ void k_trace_empty() {
+  pdl_wait();
+  pdl_trigger();
+}
+}  // namespace
+}  // namespace t2s2
+
 using namespace t2s2;
 
 extern "C" {
 
 long long t2s2_kernel_launches(void) { return g_launches.load(); }
+
+t2s2_status t2s2_trace_overhead(int n, void* stream, double* ms) {
+  if (n < 1 || !ms) return T2S2_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t a = nullptr, b = nullptr;
+  T2S2_CUDA_TRY(cudaEventCreate(&a));
+  T2S2_CUDA_TRY(cudaEventCreate(&b));
+  double tot = 0.0;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n + 1 && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(a, st);
+    if (e == cudaSuccess) e = launch_pdl(k_trace_empty, 1, 32, 0, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float f = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&f, a, b);
+    if (i > 0) tot += f;  // the first launch warms up
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "t2s2_trace_overhead", __FILE__, __LINE__);
+    return T2S2_ECUDA;
+  }
+  *ms = tot / n;
+  return T2S2_OK;
+}
 
 t2s2_status t2s2_trace(int enable) {
   std::lock_guard<std::mutex> lk(g_mu);
