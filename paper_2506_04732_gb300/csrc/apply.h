@@ -37,11 +37,18 @@ t2s2_status apply_tc(const ApplyBatch& p, int prec, int* err, cudaStream_t st);
 // tracing (apply_work_totals summed over the cores).
 int apply_fp64_tiles(const ApplyCore& c);
 int apply_tc_tiles(const ApplyCore& c);
-int apply_tc_max_ctas_per_sm(int prec);
+// CTAs per SM the tensor-core kernel can hold: the direct variant
+// (stage_elems = 0) or the staged one with a stage of stage_elems doubles.
+int apply_tc_max_ctas_per_sm(int prec, long stage_elems);
+// Doubles the staged variant needs for core c (the largest contiguous range a
+// tile reads), or -1 if the core is not 16-byte aligned.
+long apply_tc_stage_elems(const ApplyCore& c);
 void apply_work_totals(const ApplyCore& c, double* flops, double* bytes);
 t2s2_status apply_fp64_grouped(const ApplyCore* dcores, const int* dstart, int ncores, int total, int grid,
                                double flops, double bytes, cudaStream_t st);
+// stage_elems > 0: the staged (bulk TMA) variant with a stage of that many
+// doubles, at least apply_tc_stage_elems of every core; 0: direct loads.
 t2s2_status apply_tc_grouped(const ApplyCore* dcores, const int* dstart, int ncores, int total, int grid,
-                             double flops, double bytes, int prec, int* err, cudaStream_t st);
+                             double flops, double bytes, int prec, int* err, long stage_elems, cudaStream_t st);
 
 }  // namespace t2s2

@@ -13,9 +13,19 @@
 // the block pattern of Y (the same pattern as the FP64 kernel in apply.cu).
 // All cores of the train go in one launch.
 //
-// The wait on the mbarrier is bounded: on timeout the CTA sets *err, waits
-// once more (bounded) for its MMAs, frees its TMEM and returns without
-// writing Y.
+// Staged variant (kStage): the rows of X a tile needs form one contiguous
+// range of the core (whole r_b-blocks of the a it touches).  One thread copies
+// that range into a shared-memory stage with a one-dimensional bulk TMA copy
+// (cp.async.bulk, completion counted on an mbarrier) for the NEXT tile while
+// the CTA runs the current tile's MMAs and epilogue; the operand tile is then
+// converted from the stage instead of from global memory.  The copy starts at
+// the even element at or below the range (16-byte aligned, the cores being
+// 16-byte aligned) and covers an even number of elements; an odd last element
+// is read with a plain load.  Every byte copied lies inside the core.
+//
+// The waits on the mbarriers are bounded: on timeout the CTA sets *err, waits
+// once more (bounded) for its MMAs and for a bulk copy in flight, frees its
+// TMEM and returns without writing Y.
 #include <algorithm>
 
 #include "apply.h"
@@ -69,11 +79,37 @@ __device__ __forceinline__ int find_core(const Work& w, int tile) {
   return lo;
 }
 
+// The contiguous range of core elements [e0, e0 + n) that tile `tl` of core
+// c reads: whole r_b-blocks of the a its rows touch, e0 rounded down to even.
+__host__ __device__ inline void stage_range(const ApplyCore& c, long tl, long* e0, long* n) {
+  const long row0 = tl * kTileM;
+  const long a0 = row0 / c.rb;
+  const long last = (row0 + kTileM - 1) / c.rb;
+  const long a1 = last < c.ra - 1 ? last : (long)c.ra - 1;
+  const long s0 = a0 * c.m * c.rb, s1 = (a1 + 1) * c.m * c.rb;
+  *e0 = s0 & ~1L;
+  *n = s1 - *e0;
+}
+
+// Issue the staged copy of `tile` (thread 0 only): the even part by TMA, an
+// odd last element by a plain load; the arrive announces the TMA bytes.
+template <class Work>
+__device__ __forceinline__ void stage_issue(const Work& w, int tile, double* stage, uint32_t tbar) {
+  const int ci = find_core(w, tile);
+  const ApplyCore c = w.core(ci);
+  long e0, n;
+  stage_range(c, tile - w.first(ci), &e0, &n);
+  const uint32_t bytes = (uint32_t)((n & ~1L) * 8);
+  if (n & 1) stage[n - 1] = c.X[e0 + n - 1];
+  mbar_arrive_expect_tx(tbar, bytes);
+  if (bytes) bulk_g2s(smem_u32(stage), c.X + e0, bytes, tbar);
+}
+
 // Persistent: CTA b handles tiles b, b + gridDim.x, ...  TMEM and the
-// mbarrier are set up once; the operator tile is restaged only when the core
+// mbarriers are set up once; the operator tile is restaged only when the core
 // changes.
-template <int P, class Work>
-__global__ void __launch_bounds__(kThreads, 4) apply_tc_kernel(Work w, int total, int* err) {
+template <int P, class Work, bool kStage>
+__global__ void __launch_bounds__(kThreads, kStage ? 2 : 4) apply_tc_kernel(Work w, int total, int* err) {
   using O = Op<P>;
   constexpr int E = O::kBytes;
   constexpr int kTileBytes = kTileM * kMaxK * E;  // 16 KB (BF16) or 32 KB (TF32)
@@ -83,25 +119,49 @@ __global__ void __launch_bounds__(kThreads, 4) apply_tc_kernel(Work w, int total
   unsigned char* sA = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   unsigned char* sB = sA + kTileBytes;
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sB + kTileBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  unsigned long long* tbarp = mbar + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+  double* stage = reinterpret_cast<double*>(sB + kTileBytes + 128);  // 128-byte aligned
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
 
   if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kTileN);
-  if (tid == 0) mbar_init(smem_u32(mbar), 1);
+  if (tid == 0) {
+    mbar_init(smem_u32(mbar), 1);
+    if (kStage) mbar_init(smem_u32(tbarp), 1);
+  }
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const uint32_t bar = smem_u32(mbar);
+  const uint32_t tbar = smem_u32(tbarp);
+  if (kStage && tid == 0 && blockIdx.x < total) stage_issue(w, blockIdx.x, stage, tbar);
 
   int staged = -1;  // core whose operator tile sits in sB
-  uint32_t phase = 0;
+  uint32_t phase = 0, tphase = 0;
+  bool inflight = kStage && blockIdx.x < total;  // a staged copy not yet waited for
   for (int tile = blockIdx.x; tile < total; tile += gridDim.x, phase ^= 1u) {
     const int ci = find_core(w, tile);
     const ApplyCore c = w.core(ci);
     const int m = c.m, ra = c.ra, rb = c.rb;
     const long nrows = (long)ra * rb;
     const long row0 = (long)(tile - w.first(ci)) * kTileM;
+    long e0 = 0;
+    if (kStage) {
+      long n;
+      stage_range(c, tile - w.first(ci), &e0, &n);
+      const bool tok = __syncthreads_and(mbar_wait(tbar, tphase)) != 0;
+      tphase ^= 1u;
+      inflight = false;
+      if (!tok) {
+        if (tid == 0) atomicExch(err, 1);
+        mbar_wait(tbar, tphase ^ 1u);  // bounded second wait for the copy
+        break;
+      }
+    }
+    // element g of the core: xbase[g - xoff]
+    const double* xbase = kStage ? stage : c.X;
+    const long xoff = kStage ? e0 : 0;
     // K padded to whole MMAs; N = 2m padded to a multiple of 16 (M = 128 form)
     const int kpad = ((m + O::kMmaK - 1) / O::kMmaK) * O::kMmaK;
     const int npad = ((2 * m + 15) / 16) * 16;
@@ -119,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 4) apply_tc_kernel(Work w, int total
         const long g = row0 + t;
         const bool valid = g < nrows;
         const long a = valid ? g / rb : 0, b = valid ? g % rb : 0;
-        const double* xr = c.X + a * (long)m * rb + b;
+        const double* xr = xbase + (a * (long)m * rb + b - xoff);
         double v[kPer];
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
@@ -152,6 +212,12 @@ __global__ void __launch_bounds__(kThreads, 4) apply_tc_kernel(Work w, int total
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
+    // the stage has been read: bring in the next tile's rows while this
+    // tile's MMAs and epilogue run
+    if (kStage && tile + (int)gridDim.x < total) {
+      if (tid == 0) stage_issue(w, tile + gridDim.x, stage, tbar);
+      inflight = true;
+    }
     if (tid == 0) {
       const uint32_t idesc = make_idesc(O::kFmt, kTileM, npad);
       for (int k0 = 0; k0 < kpad; k0 += O::kMmaK) {
@@ -169,6 +235,7 @@ __global__ void __launch_bounds__(kThreads, 4) apply_tc_kernel(Work w, int total
     if (!ok) {
       if (tid == 0) atomicExch(err, 1);
       mbar_wait(bar, phase);  // bounded second wait for MMAs still in flight
+      if (inflight) mbar_wait(tbar, tphase);  // and for the next tile's copy
       break;
     }
     fence_after_sync();
@@ -225,12 +292,27 @@ __global__ void __launch_bounds__(kThreads, 4) apply_tc_kernel(Work w, int total
   if (warp == 0) tmem_dealloc(tmem, kTileN);
 }
 
+// Dynamic shared memory of the staged variant: the operand tiles, the
+// barriers and a stage of stage_elems doubles.
+size_t staged_smem_bytes(int elem_bytes, long stage_elems) {
+  return (size_t)2 * kTileM * kMaxK * elem_bytes + 1024 + 128 + (size_t)stage_elems * 8;
+}
+
 template <int P, class Work>
-t2s2_status launch_tc(const Work& w, int total, int grid, int* err, cudaStream_t st) {
+t2s2_status launch_tc(const Work& w, int total, int grid, int* err, long stage_elems, cudaStream_t st) {
+  if (stage_elems > 0) {
+    const size_t smem = staged_smem_bytes(Op<P>::kBytes, stage_elems);
+    T2S2_CUDA_TRY(cudaFuncSetAttribute(apply_tc_kernel<P, Work, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    apply_tc_kernel<P, Work, true><<<grid, kThreads, smem, st>>>(w, total, err);
+    T2S2_CUDA_TRY(cudaGetLastError());
+    return T2S2_OK;
+  }
   constexpr int kSmem = smem_bytes(Op<P>::kBytes);
   // the attribute is per function and device; setting it each call is cheap
-  T2S2_CUDA_TRY(cudaFuncSetAttribute(apply_tc_kernel<P, Work>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
-  apply_tc_kernel<P, Work><<<grid, kThreads, kSmem, st>>>(w, total, err);
+  T2S2_CUDA_TRY(
+      cudaFuncSetAttribute(apply_tc_kernel<P, Work, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  apply_tc_kernel<P, Work, false><<<grid, kThreads, kSmem, st>>>(w, total, err);
   T2S2_CUDA_TRY(cudaGetLastError());
   return T2S2_OK;
 }
@@ -251,9 +333,22 @@ bool apply_tc_supported(const ApplyBatch& p) {
 
 int apply_tc_tiles(const ApplyCore& c) { return (int)((((long)c.ra * c.rb) + kTileM - 1) / kTileM); }
 
-int apply_tc_max_ctas_per_sm(int prec) {
-  const int smem = smem_bytes(prec == T2S2_BF16_REFINE ? 2 : 4);
-  return std::min(512 / kTileN, (227 * 1024) / smem);
+int apply_tc_max_ctas_per_sm(int prec, long stage_elems) {
+  const int eb = prec == T2S2_BF16_REFINE ? 2 : 4;
+  const size_t smem = stage_elems > 0 ? staged_smem_bytes(eb, stage_elems) : (size_t)smem_bytes(eb);
+  return std::min<int>(std::min(512 / kTileN, stage_elems > 0 ? 2 : 4), (int)((227 * 1024) / smem));
+}
+
+long apply_tc_stage_elems(const ApplyCore& c) {
+  if (reinterpret_cast<uintptr_t>(c.X) % 16 != 0) return -1;  // the bulk copy needs 16-byte alignment
+  const long tiles = apply_tc_tiles(c);
+  long most = 0;
+  for (long tl = 0; tl < tiles; ++tl) {
+    long e0, n;
+    stage_range(c, tl, &e0, &n);
+    most = std::max(most, n);
+  }
+  return most;
 }
 
 t2s2_status apply_tc(const ApplyBatch& p, int prec, int* err, cudaStream_t st) {
@@ -271,19 +366,22 @@ t2s2_status apply_tc(const ApplyBatch& p, int prec, int* err, cudaStream_t st) {
   w.start[p.ncores] = total;
   if (total == 0) return T2S2_OK;
   TraceScope ts(kTrApplyTc, st, fl, by);
-  if (prec == T2S2_BF16_REFINE) return launch_tc<T2S2_BF16_REFINE>(w, total, total, err, st);
-  return launch_tc<T2S2_TF32_REFINE>(w, total, total, err, st);
+  if (prec == T2S2_BF16_REFINE) return launch_tc<T2S2_BF16_REFINE>(w, total, total, err, 0, st);
+  return launch_tc<T2S2_TF32_REFINE>(w, total, total, err, 0, st);
 }
 
 t2s2_status apply_tc_grouped(const ApplyCore* dcores, const int* dstart, int ncores, int total, int grid,
-                             double flops, double bytes, int prec, int* err, cudaStream_t st) {
+                             double flops, double bytes, int prec, int* err, long stage_elems, cudaStream_t st) {
   if (prec != T2S2_BF16_REFINE && prec != T2S2_TF32_REFINE) return T2S2_EINVAL;
   if (!err || ncores < 1 || total < 0 || grid < 1) return T2S2_EINVAL;
+  if (stage_elems > 0 && staged_smem_bytes(prec == T2S2_BF16_REFINE ? 2 : 4, stage_elems) > 227 * 1024)
+    return T2S2_EINVAL;
   if (total == 0) return T2S2_OK;
   GlobalWork w{dcores, dstart, ncores};
   TraceScope ts(kTrApplyTc, st, flops, bytes);
-  if (prec == T2S2_BF16_REFINE) return launch_tc<T2S2_BF16_REFINE>(w, total, std::min(grid, total), err, st);
-  return launch_tc<T2S2_TF32_REFINE>(w, total, std::min(grid, total), err, st);
+  if (prec == T2S2_BF16_REFINE)
+    return launch_tc<T2S2_BF16_REFINE>(w, total, std::min(grid, total), err, stage_elems, st);
+  return launch_tc<T2S2_TF32_REFINE>(w, total, std::min(grid, total), err, stage_elems, st);
 }
 
 void apply_work_totals(const ApplyCore& c, double* flops, double* bytes) { work_totals(c, *flops, *bytes); }

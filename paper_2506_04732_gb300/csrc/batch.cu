@@ -7,15 +7,19 @@
 // (apply.cu for FP64, apply_tc.cu for the tensor-core path), so instances of
 // uneven n and ranks share one launch with no per-instance launch overhead.
 //
-// Autotuner: the persistent grid is k CTAs per SM, k from the kernel's
-// residency limit.  The first call with a new shape class (precision, largest
-// m in steps of 16, largest rank as a power of two, tile count as a power of
-// two) times each k with CUDA events (one warm-up launch, then two timed) and
+// Autotuner: the tensor-core kernel comes in two variants, direct loads of
+// the operand rows or staged ones (a bulk TMA copy of the next tile's rows
+// into shared memory while the current tile runs, fewer CTAs per SM), and the
+// persistent grid is k CTAs per SM, k up to the variant's residency limit.
+// The first call with a new shape class (precision, largest m in steps of 16,
+// largest rank, tile count and stage size as powers of two) times every
+// (variant, k) with CUDA events (one warm-up launch, then two timed) and
 // keeps the fastest in a table that later calls reuse; t2s2_autotune_report
 // prints the table.  Re-running the product is harmless: it overwrites y
 // with the same values.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -32,13 +36,15 @@ namespace {
 
 struct TuneKey {
   int prec, mb, rb, tb;
+  long sb;
   bool operator<(const TuneKey& o) const {
-    return std::tie(prec, mb, rb, tb) < std::tie(o.prec, o.mb, o.rb, o.tb);
+    return std::tie(prec, mb, rb, tb, sb) < std::tie(o.prec, o.mb, o.rb, o.tb, o.sb);
   }
 };
 struct TuneVal {
   int ctas_per_sm;
-  std::vector<std::pair<int, float>> trials;  // (ctas per SM, ms per launch)
+  bool staged;  // the bulk-TMA staged variant of the tensor-core kernel
+  std::vector<std::tuple<bool, int, float>> trials;  // (staged, ctas per SM, ms per launch)
 };
 
 std::mutex g_mu;
@@ -115,6 +121,13 @@ t2s2_status t2s2_apply_batched(const t2s2_op* ops, const t2s2_tt* x, t2s2_tt* y,
   }
   const int n = (int)cores.size();
   bool tc = (prec == T2S2_BF16_REFINE || prec == T2S2_TF32_REFINE) && mmax <= 64;
+  // the stage the staged variant would need (-1: some core is not aligned)
+  long stage = tc ? 0 : -1;
+  for (int i = 0; i < n && stage >= 0; ++i) {
+    const long e = apply_tc_stage_elems(cores[i]);
+    stage = e < 0 ? -1 : std::max(stage, e);
+  }
+  if (stage > 0 && apply_tc_max_ctas_per_sm(prec, stage) < 1) stage = -1;
   std::vector<int> start(n + 1);
   double fl = 0.0, by = 0.0;
   int total = 0;
@@ -133,39 +146,60 @@ t2s2_status t2s2_apply_batched(const t2s2_op* ops, const t2s2_tt* x, t2s2_tt* y,
   const ApplyCore* dcores = reinterpret_cast<const ApplyCore*>(g_dev);
   const int* dstart = reinterpret_cast<const int*>(g_dev + cbytes);
   if (tc) T2S2_CUDA_TRY(cudaMemsetAsync(g_err, 0, sizeof(int), st));
-  auto launch = [&](int per_sm) -> t2s2_status {
+  auto launch = [&](bool staged, int per_sm) -> t2s2_status {
     const int grid = std::max(1, per_sm * kNumSMs);
-    if (tc) return apply_tc_grouped(dcores, dstart, n, total, grid, fl, by, prec, g_err, st);
+    if (tc) return apply_tc_grouped(dcores, dstart, n, total, grid, fl, by, prec, g_err, staged ? stage : 0, st);
     return apply_fp64_grouped(dcores, dstart, n, total, grid, fl, by, st);
   };
-  const TuneKey key{tc ? (int)prec : 0, (mmax + 15) / 16, pow2_ceil(rmax), pow2_ceil(total)};
+  // shape class: precision, largest m (steps of 16), largest rank and tile
+  // count (powers of two), and the stage size (powers of two; -1: none)
+  const TuneKey key{tc ? (int)prec : 0, (mmax + 15) / 16, pow2_ceil(rmax), pow2_ceil(total),
+                    stage > 0 ? pow2_ceil(stage) : -1};
+  // T2S2_APPLY_VARIANT=direct|staged forces one variant at its residency
+  // limit, without tuning (for tests of each variant)
+  const char* force = std::getenv("T2S2_APPLY_VARIANT");
+  if (tc && force && (std::strcmp(force, "direct") == 0 || std::strcmp(force, "staged") == 0)) {
+    const bool staged = std::strcmp(force, "staged") == 0;
+    if (staged && stage <= 0) return T2S2_EINVAL;
+    T2S2_TRY(launch(staged, apply_tc_max_ctas_per_sm(prec, staged ? stage : 0)));
+    int herr = 0;
+    T2S2_CUDA_TRY(cudaMemcpyAsync(&herr, g_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    T2S2_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < count; ++i)
+      for (int k = 0; k <= ys[i].d; ++k) y[i].r[k] = ys[i].r[k];
+    return herr ? T2S2_ETIMEOUT : T2S2_OK;
+  }
   auto it = g_table.find(key);
   if (it == g_table.end()) {
-    // tune: candidates up to the kernel's residency limit
-    const int kmax = tc ? apply_tc_max_ctas_per_sm(prec) : 3;
-    TuneVal tv{1, {}};
+    // tune: both variants, each up to its residency limit
+    TuneVal tv{1, false, {}};
     float best = 1e30f;
     cudaEvent_t e0, e1;
     T2S2_CUDA_TRY(cudaEventCreate(&e0));
     T2S2_CUDA_TRY(cudaEventCreate(&e1));
-    for (int k = 1; k <= kmax; ++k) {
-      T2S2_TRY(launch(k));  // warm-up (same result each time)
-      T2S2_CUDA_TRY(cudaEventRecord(e0, st));
-      T2S2_TRY(launch(k));
-      T2S2_TRY(launch(k));
-      T2S2_CUDA_TRY(cudaEventRecord(e1, st));
-      T2S2_CUDA_TRY(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      T2S2_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-      ms *= 0.5f;
-      tv.trials.push_back({k, ms});
-      if (ms < best) best = ms, tv.ctas_per_sm = k;
+    for (int variant = 0; variant < 2; ++variant) {
+      const bool staged = variant == 1;
+      if (staged && !(tc && stage > 0)) continue;
+      const int kmax = tc ? apply_tc_max_ctas_per_sm(prec, staged ? stage : 0) : 3;
+      for (int k = 1; k <= kmax; ++k) {
+        T2S2_TRY(launch(staged, k));  // warm-up (same result each time)
+        T2S2_CUDA_TRY(cudaEventRecord(e0, st));
+        T2S2_TRY(launch(staged, k));
+        T2S2_TRY(launch(staged, k));
+        T2S2_CUDA_TRY(cudaEventRecord(e1, st));
+        T2S2_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        T2S2_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        ms *= 0.5f;
+        tv.trials.emplace_back(staged, k, ms);
+        if (ms < best) best = ms, tv.ctas_per_sm = k, tv.staged = staged;
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     it = g_table.emplace(key, tv).first;
   } else {
-    T2S2_TRY(launch(it->second.ctas_per_sm));
+    T2S2_TRY(launch(it->second.staged, it->second.ctas_per_sm));
   }
   int herr = 0;
   if (tc) T2S2_CUDA_TRY(cudaMemcpyAsync(&herr, g_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -180,11 +214,13 @@ int t2s2_autotune_report(char* buf, int len) {
   std::string s;
   for (auto& kv : g_table) {
     char line[256];
-    int o = std::snprintf(line, sizeof(line), "apply prec=%d m<=%d r<=%d tiles<=%d: %d CTAs/SM [", kv.first.prec,
-                          kv.first.mb * 16, kv.first.rb, kv.first.tb, kv.second.ctas_per_sm);
+    int o = std::snprintf(line, sizeof(line), "apply prec=%d m<=%d r<=%d tiles<=%d stage<=%ld: %s %d CTAs/SM [",
+                          kv.first.prec, kv.first.mb * 16, kv.first.rb, kv.first.tb, kv.first.sb,
+                          kv.second.staged ? "staged" : "direct", kv.second.ctas_per_sm);
     s.append(line, std::min<int>(o, (int)sizeof(line) - 1));
     for (auto& t : kv.second.trials) {
-      o = std::snprintf(line, sizeof(line), " %d:%.4fms", t.first, t.second);
+      o = std::snprintf(line, sizeof(line), " %s%d:%.4fms", std::get<0>(t) ? "s" : "d", std::get<1>(t),
+                        std::get<2>(t));
       s.append(line, std::min<int>(o, (int)sizeof(line) - 1));
     }
     s += " ]\n";

@@ -166,6 +166,20 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
+// One-dimensional bulk copy (TMA, no tensor map) of `bytes` (a multiple of 16)
+// from global memory at `src` (16-byte aligned) into shared memory at `dst`
+// (16-byte aligned), completing `bytes` transactions on the mbarrier `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Arrive once on `bar` and announce `bytes` of transactions to wait for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void fence_smem_to_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

@@ -174,3 +174,37 @@ def test_grouped_apply_matches_per_instance_products(T, fmt):
                 gamma = 2 * u + u * u + 2 * m * 2.0 ** -24
                 assert np.all(np.abs(a - b) <= gamma * s * 1.0001 + 1e-300)
     assert "apply" in T.t2s2_autotune_report()
+
+
+@pytest.mark.parametrize("variant", ["direct", "staged"])
+@pytest.mark.parametrize("fmt", ["bf16", "tf32"])
+def test_grouped_apply_each_variant_within_rounding_bound(T, fmt, variant, monkeypatch):
+    """Both variants of the grouped tensor-core apply (operand rows loaded
+    directly, or staged in shared memory by a bulk TMA copy of the next
+    tile's rows) against the FP64 oracle product, at the per-element rounding
+    bound; instances of uneven n and ranks, including odd ranks (odd range
+    lengths and starts of the staged copies)."""
+    from paper_2506_04732_gb300 import problem as P
+    monkeypatch.setenv("T2S2_APPLY_VARIANT", variant)
+    probs = [W.config3(i) for i in range(10)]
+    ops, xs, ys, refs, bounds = [], [], [], [], []
+    for i, p in enumerate(probs):
+        m = p.n[0] - 2
+        r = [1] + [int(v) for v in np.random.default_rng(40 + i).integers(1, 24, p.d - 1)] + [1]
+        x = W.random_tt(p.d, m, r, seed=900 + i)
+        ops.append(P.build_operator(p))
+        xs.append(T.TT.from_cores(x))
+        ys.append(T.TT.empty([m] * p.d, 2 * max(r)))
+        A = O.ttm_cores(O.build(p), 0.25, 1.0)
+        refs.append(OT.matvec(A, x))
+        bounds.append(OT.matvec([np.abs(a) for a in A], [np.abs(c) for c in x]))
+    prec = {"bf16": T.BF16_REFINE, "tf32": T.TF32_REFINE}[fmt]
+    for _ in range(2):   # the second launch rewrites the same values
+        T.t2s2_apply_batched(ops, xs, ys, c_mass=0.25, c_op=1.0, prec=prec)
+    for y, ref, bnd, p in zip(ys, refs, bounds, probs):
+        m = p.n[0] - 2
+        for a, b, s in zip(y.cores(), ref, bnd):
+            assert a.shape == b.shape
+            u = U[fmt]
+            gamma = 2 * u + u * u + 2 * m * 2.0 ** -24
+            assert np.all(np.abs(a - b) <= gamma * s * 1.0001 + 1e-300)
