@@ -406,8 +406,10 @@ int ew_blocks(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) /
 // then the cores of X(p) normalised and written as FP64 straight into the
 // caller's cores.  One launch instead of the batched path's GEMM, bias and
 // unpack launches; used for warm starts, where the solve waits on it.
+constexpr int kPredictInline = 64;  // inputs passed inside the launch arguments
 struct PredictArgs {
-  const float* p;
+  const float* p;                 // device input, or null: pin holds it
+  float pin[kPredictInline];
   const float* w;
   long long oW1, ob1, oW2, ob2, oW3, ob3;
   int in_dim, hidden, odim, ncore, d;
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(kPredictThreads) predict_kernel(PredictArgs a)
   float* h2 = h1 + a.hidden;
   float* y = h2 + a.hidden;
   float* red = y + a.odim;
-  for (int i = threadIdx.x; i < a.in_dim; i += blockDim.x) xin[i] = a.p[i];
+  for (int i = threadIdx.x; i < a.in_dim; i += blockDim.x) xin[i] = a.p ? a.p[i] : a.pin[i];
   __syncthreads();
   gemv_rows(a.w + a.oW1, a.w + a.ob1, xin, h1, a.hidden, a.in_dim, true);
   __syncthreads();
@@ -966,8 +968,19 @@ t2s2_status t2s2_mlp_predict(t2s2_mlp net, const float* p, t2s2_tt* x, void* str
                                          (int)kPredictMaxSmem));
       attr = true;
     }
-    T2S2_CUDA_TRY(cudaMemcpyAsync(net->pbuf, p, sizeof(float) * net->in_dim, cudaMemcpyDefault, st));
-    a.p = net->pbuf;
+    // a host input travels inside the launch arguments (no copy); a device
+    // input is read where it is
+    cudaPointerAttributes pa;
+    const bool on_device = cudaPointerGetAttributes(&pa, p) == cudaSuccess &&
+                           (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+    (void)cudaGetLastError();  // a plain host pointer may leave an error behind on older runtimes
+    if (on_device || net->in_dim > kPredictInline) {
+      if (!on_device) T2S2_CUDA_TRY(cudaMemcpyAsync(net->pbuf, p, sizeof(float) * net->in_dim, cudaMemcpyDefault, st));
+      a.p = on_device ? p : net->pbuf;
+    } else {
+      a.p = nullptr;
+      std::memcpy(a.pin, p, sizeof(float) * net->in_dim);
+    }
     a.w = net->params;
     a.oW1 = net->oW1; a.ob1 = net->ob1; a.oW2 = net->oW2; a.ob2 = net->ob2; a.oW3 = net->oW3; a.ob3 = net->ob3;
     a.in_dim = net->in_dim; a.hidden = net->hidden; a.odim = net->odim; a.ncore = net->ncore; a.d = net->d;
