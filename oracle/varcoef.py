@@ -12,9 +12,12 @@ sum form with
 where the reaction is taken as a constant plus a sum of one-coordinate
 functions, rho(x) = rho_0 + sum_k rho_k(x_k) (the constant is folded into the
 first dimension).  Both keep the rank-2 TT-matrix of ``operator``.  A
-reaction that is a product of one-coordinate functions (the paper's
-six-dimensional test) adds a rank-1 Kronecker product instead, a rank-3
-TT-matrix; it is not covered here.
+reaction that is a product of one-coordinate functions, prod_k pi_k(x_k) (the
+paper's six-dimensional test), adds the Kronecker product
+(x)_k diag(pi_k(eta)) Rt_k: a rank-3 TT-matrix,
+
+    first [Lt_1  Rt_1  P_1],  middle [[Rt, 0, 0], [Lt, Rt, 0], [0, 0, P_k]],
+    last [Rt; Lt; P_d],   P_k = diag(pi_k(eta)) Rt_k.
 
 The superconsistent points of dimension k depend on one convection speed;
 with a variable beta_k they are chosen for a reference speed supplied with
@@ -22,9 +25,11 @@ the problem (a reading: the paper does not say which speed picks them).
 
 Pins (tests/test_oracle_varcoef.py): the operator applied to grid values of a
 tensor-product polynomial that vanishes on the boundary equals
--eps Laplace u + beta . grad u + rho u at the collocation grid exactly;
-constant coefficients give ``operator``'s matrices; the manufactured source
-is the PDE applied pointwise; the discrete solution converges spectrally.
+-eps Laplace u + beta . grad u + rho u at the collocation grid exactly (with
+and without the product term); constant coefficients give ``operator``'s
+matrices; the rank-3 TT-matrix contracts to the dense operator; the
+manufactured source is the PDE applied pointwise; the discrete solution
+converges spectrally.
 """
 from __future__ import annotations
 
@@ -40,11 +45,13 @@ from .gll import gll_nodes
 @dataclass
 class VarCoef:
     """beta_k(x) per dimension (None: the constant beta_ref[k]), rho_k(x) per
-    dimension (None: zero) and the constant rho0."""
+    dimension (None: zero), the constant rho0 and the factors pi_k(x) of a
+    product reaction prod_k pi_k(x_k) (None: no product term)."""
     beta_ref: np.ndarray
     beta_fns: list
     rho_fns: list
     rho0: float = 0.0
+    prod_fns: Optional[list] = None
 
 
 def op1d_var(n: int, eps: float, beta_ref: float, beta_fn: Optional[Callable], rho_fn: Optional[Callable],
@@ -67,9 +74,60 @@ def op1d_var(n: int, eps: float, beta_ref: float, beta_fn: Optional[Callable], r
 
 
 def build(problem, vc: VarCoef):
-    """Per-dimension pieces; rho0 goes to the first dimension."""
-    return [op1d_var(problem.n[k], problem.eps, float(vc.beta_ref[k]), vc.beta_fns[k], vc.rho_fns[k],
-                     vc.rho0 if k == 0 else 0.0, problem.plain_sc) for k in range(problem.d)]
+    """Per-dimension pieces; rho0 goes to the first dimension.  With a
+    product reaction each piece also carries P = diag(pi_k(eta)) Rt."""
+    ops = [op1d_var(problem.n[k], problem.eps, float(vc.beta_ref[k]), vc.beta_fns[k], vc.rho_fns[k],
+                    vc.rho0 if k == 0 else 0.0, problem.plain_sc) for k in range(problem.d)]
+    if vc.prod_fns is not None:
+        for o, f in zip(ops, vc.prod_fns):
+            o.pvals = np.asarray(f(o.eta), dtype=np.float64) * np.ones_like(o.eta)
+            o.P = o.pvals[:, None] * o.Rt
+    return ops
+
+
+def dense(ops, c_mass: float = 0.0, c_op: float = 1.0):
+    """c_mass M + c_op (A + the product reaction) as a dense matrix (tiny grids)."""
+    from functools import reduce
+    from .operator import dense as dense_sum
+    out = dense_sum(ops, c_mass, c_op)
+    if getattr(ops[0], "P", None) is not None:
+        out = out + c_op * reduce(np.kron, [o.P for o in ops])
+    return out
+
+
+def ttm_cores(ops, c_mass: float = 0.0, c_op: float = 1.0):
+    """TT-matrix cores of c_mass M + c_op (A + product reaction): the rank-2
+    cores of ``operator`` without a product term, the rank-3 pattern above
+    with one."""
+    from .operator import ttm_cores as ttm2
+    if getattr(ops[0], "P", None) is None:
+        return ttm2(ops, c_mass, c_op)
+    d = len(ops)
+    cores = []
+    for k, o in enumerate(ops):
+        R, L, Pk = o.Rt, c_op * o.Lt, o.P
+        m = R.shape[0]
+        if d == 1:
+            c = np.zeros((1, m, m, 1))
+            c[0, :, :, 0] = L + c_mass * R + c_op * Pk
+        elif k == 0:
+            c = np.zeros((1, m, m, 3))
+            c[0, :, :, 0] = L + c_mass * R
+            c[0, :, :, 1] = R
+            c[0, :, :, 2] = c_op * Pk
+        elif k == d - 1:
+            c = np.zeros((3, m, m, 1))
+            c[0, :, :, 0] = R
+            c[1, :, :, 0] = L
+            c[2, :, :, 0] = Pk
+        else:
+            c = np.zeros((3, m, m, 3))
+            c[0, :, :, 0] = R
+            c[1, :, :, 0] = L
+            c[1, :, :, 1] = R
+            c[2, :, :, 2] = Pk
+        cores.append(c)
+    return cores
 
 
 def source_tt(problem, ops):
@@ -97,6 +155,12 @@ def source_tt(problem, ops):
                 c = np.zeros((2, m, 2)); c[0, :, 0] = p; c[1, :, 0] = l; c[1, :, 1] = p
             cores.append(c)
         cores[0] = cores[0] * t.coef
+        if getattr(ops[0], "P", None) is not None:
+            # the product reaction of this term: prod_k pi_k(eta) phi_k(eta), rank 1
+            from .tt import add
+            prod = [(ops[k].pvals * t.factors[k](ops[k].eta)).reshape(1, -1, 1) for k in range(d)]
+            prod[0] = prod[0] * t.coef
+            cores = add(cores, prod)
         if total is None:
             total = cores
         else:

@@ -69,3 +69,19 @@ def test_rank_cap_16_is_what_stops_the_instance(T, i):
     x40, info = _solve(T, op, b, p, 1e-8, 40, 50)
     assert info.status == 0
     assert OS.residual(A, ob, x40.cores()) <= 1.01e-8
+
+
+def test_solve_stops_early_at_the_rank_cap(T):
+    """Under the cap of 16 a rank-capped instance stops once its ranks sit at
+    rmax + kick and its residual has not halved in 8 sweeps: T2S2_ENOCONV well
+    before the 50-sweep cap, with the last iterate and its residual."""
+    from paper_2506_04732_gb300 import problem as P
+    p = W.config3(13)
+    op = P.build_operator(p)
+    b = T.TT.from_cores(P.source_cores(p, op))
+    x, info = _solve(T, op, b, p, 1e-8, 16, 50)
+    assert info.status == 4 and info.residual > 1e-8
+    assert info.sweeps < 20 and info.max_rank == 16 + T.RANK_KICK
+    ops = O.build(p)
+    r = OS.residual(O.ttm_cores(ops), O.source_tt(p, ops), x.cores())
+    assert abs(r - info.residual) <= 1e-3 * info.residual

@@ -294,6 +294,15 @@ class VarCoefProblem:
         c = float(self.rho_c[k])
         return lambda x: c * (1.0 + np.asarray(x, dtype=np.float64) ** 2)
 
+    @staticmethod
+    def prod_fn(k):
+        """One factor of the paper's product reaction, the same in every
+        dimension: 1/2 - (x + 11/10)(x - 1/2)(x + 1/2)(x - 11/10)."""
+        def f(x):
+            x = np.asarray(x, dtype=np.float64)
+            return 0.5 - (x + 1.1) * (x - 0.5) * (x + 0.5) * (x - 1.1)
+        return f
+
 
 def config_varcoef(seed: int = 9, d: int = 6, n: int = 32, ratio: float = 1e-3, tol: float = 1e-8,
                    rmax: int = 20) -> VarCoefProblem:
