@@ -96,19 +96,19 @@ typedef struct t2s2_op_s* t2s2_op;
 typedef double (*t2s2_coef_fn)(int k, double x, void* ctx);
 
 /* Variable coefficients of eq. pblm:time:A in the form the paper's
- * six-dimensional test uses for beta: beta_k(x_k) per dimension, and a
- * reaction rho(x) = rho0 + sum_k rho_k(x_k).  base.beta[k] is the reference
- * speed of dimension k that picks its superconsistent points (a reading: the
- * paper does not say which speed picks them with a variable beta).
- * beta_fn NULL: constant base.beta[k]; rho_fn NULL: rho = rho0.  A reaction
- * that is a product of one-coordinate functions needs a rank-3 TT-matrix and
- * is not provided. */
+ * six-dimensional test uses: beta_k(x_k) per dimension, and a reaction
+ * rho(x) = rho0 + sum_k rho_k(x_k) + prod_k pi_k(x_k).  base.beta[k] is the
+ * reference speed of dimension k that picks its superconsistent points (a
+ * reading: the paper does not say which speed picks them with a variable
+ * beta).  beta_fn NULL: constant base.beta[k]; rho_fn NULL: no sum term;
+ * prod_fn NULL: no product term. */
 typedef struct {
   t2s2_problem base;
   t2s2_coef_fn beta_fn;
   t2s2_coef_fn rho_fn;
   double rho0;
   void* ctx;
+  t2s2_coef_fn prod_fn;
 } t2s2_problem_var;
 
 typedef struct {
@@ -157,9 +157,24 @@ t2s2_status t2s2_build_operator(const t2s2_problem* prob, void* stream, t2s2_op*
  * scaled by beta_k(eta_j) and rho_k(eta_j) Rt_k is added (rho0 Rt in the
  * first dimension), Lt_k = diag(beta_k(eta)) D - eps D2 + diag(rho_k(eta))
  * Rt_k: the same rank-2 TT-matrix, so every entry point that takes an
- * operator works unchanged.  The functions are called on the host during the
- * build, n[k] - 2 times per dimension.  Errors as t2s2_build_operator, and
- * T2S2_EINVAL if a coefficient value is not finite.
+ * operator works unchanged.  A product reaction prod_k pi_k(x_k) adds the
+ * Kronecker product (x)_k diag(pi_k(eta)) Rt_k, a rank-3 TT-matrix in all:
+ * then t2s2_apply returns ranks 3 r_x (FP64 only), t2s2_residual includes
+ * the term, and t2s2_solve (FP64 only; other precisions return
+ * T2S2_ENOTIMPL) lags the reaction: each outer step solves, with the
+ * alternating solver and from the current x, (c_mass M + c_op A + c_op
+ * rho_bar M) x+ = b - c_op (P - rho_bar M) x (rho_bar: the product of the
+ * factors' means over the collocation points, the part of the product term
+ * the solver sees), until the residual of the full operator is at most tol;
+ * the steps contract by ||(c_mass M + c_op (A + rho_bar M))^-1 c_op
+ * (P - rho_bar M)||.  info->refinements counts the outer steps; the
+ * residual is |b - A_full x| / |b| with its inner products in double-double.
+ * With a product reaction t2s2_solve wants 2 (rmax + 8) <= 96 (T2S2_EINVAL
+ * otherwise).
+ * t2s2_cn_step and t2s2_be_step return T2S2_ENOTIMPL for such an operator.
+ * The functions are called on the host during the build, n[k] - 2 times per
+ * dimension.  Errors as t2s2_build_operator, and T2S2_EINVAL if a
+ * coefficient value is not finite.
  */
 t2s2_status t2s2_build_operator_var(const t2s2_problem_var* prob, void* stream, t2s2_op* out);
 

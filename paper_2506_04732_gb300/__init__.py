@@ -56,7 +56,7 @@ _COEF_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int, ctypes.c_double, ctyp
 
 class _ProblemVar(ctypes.Structure):
     _fields_ = [("base", _Problem), ("beta_fn", _COEF_FN), ("rho_fn", _COEF_FN), ("rho0", ctypes.c_double),
-                ("ctx", ctypes.c_void_p)]
+                ("ctx", ctypes.c_void_p), ("prod_fn", _COEF_FN)]
 
 
 class _TT(ctypes.Structure):
@@ -497,11 +497,11 @@ def t2s2_build_operator(d, n, beta, eps, plain_sc=False, stream=None) -> Operato
 
 
 def t2s2_build_operator_var(d, n, beta_ref, eps, beta_fns=None, rho_fns=None, rho0=0.0, plain_sc=False,
-                            stream=None) -> Operator:
+                            stream=None, prod_fns=None) -> Operator:
     """Operator with variable coefficients: beta_fns[k](x) (vectorised over
     numpy arrays or scalar; None: the constant beta_ref[k]) and the reaction
-    rho0 + sum_k rho_fns[k](x_k).  beta_ref[k] picks dimension k's
-    superconsistent points."""
+    rho0 + sum_k rho_fns[k](x_k) + prod_k prod_fns[k](x_k).  beta_ref[k] picks
+    dimension k's superconsistent points."""
     lib = load()
     n = [int(v) for v in (n if np.ndim(n) else [n] * d)]
     beta_ref = [float(v) for v in beta_ref]
@@ -518,7 +518,8 @@ def t2s2_build_operator_var(d, n, beta_ref, eps, beta_fns=None, rho_fns=None, rh
 
     bfn = wrap(beta_fns, lambda k: beta_ref[k])
     rfn = wrap(rho_fns, lambda k: 0.0)
-    prob = _ProblemVar(_Problem(d, na, ba, float(eps), int(bool(plain_sc))), bfn, rfn, float(rho0), None)
+    pfn = wrap(prod_fns, lambda k: 1.0)
+    prob = _ProblemVar(_Problem(d, na, ba, float(eps), int(bool(plain_sc))), bfn, rfn, float(rho0), None, pfn)
     h = ctypes.c_void_p()
     _check(lib.t2s2_build_operator_var(ctypes.byref(prob), _stream_handle(stream), ctypes.byref(h)),
            "t2s2_build_operator_var")

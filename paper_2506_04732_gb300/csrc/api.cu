@@ -23,6 +23,16 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
            what);
 }
 
+void note_failure(int status, const char* what, const char* file, int line) {
+  static const bool on = [] {
+    const char* e = std::getenv("T2S2_VERBOSE");
+    return e && e[0] == '1';
+  }();
+  if (status == T2S2_ENOCONV || !on) return;
+  const char* f = std::strrchr(file, '/');
+  fprintf(stderr, "[t2s2] status %d from %s at %s:%d\n", status, what, f ? f + 1 : file, line);
+}
+
 bool pdl_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("T2S2_PDL");
@@ -168,6 +178,72 @@ t2s2_status apply_op(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mas
   return apply_fp64(b, cx.st);
 }
 
+t2s2_status apply_full(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass, double c_op) {
+  const int d = op->d;
+  int r2[T2S2_MAX_D + 1];
+  for (int k = 0; k <= d; ++k) r2[k] = (k == 0 || k == d) ? 1 : 2 * x.r[k];
+  if (!op->has_prod) {
+    T2S2_TRY(tt_alloc(cx, y, d, x.m, r2, 0));
+    return apply_op(op, cx, x, y, c_mass, c_op, false);
+  }
+  DevTT y2, yp;
+  T2S2_TRY(tt_alloc(cx, y2, d, x.m, r2, 0));
+  T2S2_TRY(apply_op(op, cx, x, y2, c_mass, c_op, false));
+  // the product term keeps the ranks: core k times P_k along its mode
+  T2S2_TRY(apply_kron(cx, x, op->dP, yp));
+  return tt_axpby(cx, 1.0, y2, c_op, yp, y);
+}
+
+t2s2_status apply_kron(Ctx& cx, const DevTT& x, double* const* mats, DevTT& y) {
+  const int d = x.d;
+  T2S2_TRY(tt_alloc(cx, y, d, x.m, x.r, 0));
+  Ctx c64 = cx;
+  c64.contract_prec = T2S2_FP64;
+  for (int k = 0; k < d; ++k) {
+    const int m = x.m[k], ra = x.r[k], rb = x.r[k + 1];
+    Gemm<double> g;
+    g.M = m; g.N = rb; g.K = m; g.tA = false; g.tB = false; g.alpha = 1.0; g.beta = 0.0;
+    g.A = mats[k]; g.lda = m; g.sA = 0;
+    g.B = x.c[k]; g.ldb = rb; g.sB = (long)m * rb;
+    g.C = y.c[k]; g.ldc = rb; g.sC = (long)m * rb;
+    g.batch = ra;
+    T2S2_TRY(contract_gemm(c64, g));
+  }
+  return T2S2_OK;
+}
+
+namespace {
+// s + e = a + b exactly (no multiplication, so nothing can be fused)
+void host_two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+}  // namespace
+
+t2s2_status residual_full(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,
+                          double* out) {
+  // |b|^2 - 2<b, y> + |y|^2 in double-double, y the full operator applied
+  // to x (ranks 3 r_x): z = b - y is never formed, so its ranks (r_b + 3 r_x)
+  // meet no limit of the orthogonalisation
+  const size_t mk = cx.ar->mark();
+  DevTT y;
+  T2S2_TRY(apply_full(op, cx, x, y, c_mass, c_op));
+  const DevTT* pu[3] = {&b, &y, &b};
+  const DevTT* pv[3] = {&y, &y, &b};
+  double hi[3] = {0.0, 0.0, 0.0}, lo[3] = {0.0, 0.0, 0.0};
+  T2S2_TRY(tt_dots_dd(cx, 3, pu, pv, hi, lo));
+  cx.ar->release(mk);
+  double s1, e1, s2, e2;
+  host_two_sum(hi[2], -2.0 * hi[0], s1, e1);
+  host_two_sum(s1, hi[1], s2, e2);
+  const double r2v = s2 + (((lo[2] - 2.0 * lo[0]) + lo[1]) + (e1 + e2));
+  const double bn = std::sqrt(std::max(hi[2] + lo[2], 0.0));
+  const double zn = std::sqrt(std::max(r2v, 0.0));
+  *out = bn > 0.0 ? zn / bn : zn;
+  return T2S2_OK;
+}
+
 t2s2_status contract_gemm(Ctx& cx, const Gemm<double>& g) {
   if (cx.contract_prec == T2S2_BF16_REFINE || cx.contract_prec == T2S2_TF32_REFINE) {
     const size_t need = gemm_tc_workspace_bytes(g, cx.contract_prec);
@@ -223,11 +299,26 @@ t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
   for (int k = 0; k <= op->d; ++k) r2[k] = (k == 0 || k == op->d) ? 1 : 2 * x.r[k];
   T2S2_TRY(tt_alloc(cx, y, op->d, x.m, r2, 0));
   T2S2_TRY(apply_op(op, cx, x, y, c_mass, c_op, transformed));
-  DevTT z;
-  T2S2_TRY(tt_axpby(cx, 1.0, b, -1.0, y, z));
-  T2S2_TRY(tt_orth_right(cx, z));
+  int rz = 1;
+  for (int k = 0; k <= op->d; ++k) rz = std::max(rz, b.r[k] + y.r[k]);
   double rn;
-  T2S2_TRY(core_norm(cx, z.c[0], z.core_elems(0), &rn));
+  if (rz > kSmallMax) {
+    // z = b - y is past the orthogonalisation's rank limit: |z|^2 from the
+    // double-double inner products instead
+    const DevTT* pu[3] = {&b, &y, &b};
+    const DevTT* pv[3] = {&y, &y, &b};
+    double hi[3] = {0.0, 0.0, 0.0}, lo[3] = {0.0, 0.0, 0.0};
+    T2S2_TRY(tt_dots_dd(cx, 3, pu, pv, hi, lo));
+    double s1, e1, s2, e2;
+    host_two_sum(hi[2], -2.0 * hi[0], s1, e1);
+    host_two_sum(s1, hi[1], s2, e2);
+    rn = std::sqrt(std::max(s2 + (((lo[2] - 2.0 * lo[0]) + lo[1]) + (e1 + e2)), 0.0));
+  } else {
+    DevTT z;
+    T2S2_TRY(tt_axpby(cx, 1.0, b, -1.0, y, z));
+    T2S2_TRY(tt_orth_right(cx, z));
+    T2S2_TRY(core_norm(cx, z.c[0], z.core_elems(0), &rn));
+  }
   double bn = bnorm_io ? *bnorm_io : -1.0;
   if (bn < 0) {
     T2S2_TRY(tt_norm(cx, b, &bn));
@@ -248,14 +339,6 @@ t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
 constexpr double kDDFloor = 1e-13;
 constexpr double kScreen = 1e-5;
 
-namespace {
-// s + e = a + b exactly (no multiplication, so nothing can be fused)
-void host_two_sum(double a, double b, double& s, double& e) {
-  s = a + b;
-  const double bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-}  // namespace
 
 t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,
                           double* out, ResidualCache* rc, bool screen) {
@@ -513,7 +596,42 @@ t2s2_status t2s2_build_operator_var(const t2s2_problem_var* var, void* stream, t
       return T2S2_EINVAL;
     }
   }
-  return upload_operator(op, static_cast<cudaStream_t>(stream), out);
+  // product reaction: P_k = diag(pi_k(eta)) Rt_k and the product of the means
+  std::vector<double> hp;
+  if (var->prod_fn) {
+    op->has_prod = 1;
+    op->rho_bar = 1.0;
+    for (int k = 0; k < op->d; ++k) {
+      const Dim1D& D = op->dims[k];
+      const int m = op->m[k];
+      double mean = 0.0;
+      for (int j = 0; j < m; ++j) {
+        const double pj = var->prod_fn(k, D.eta[j], var->ctx);
+        if (!std::isfinite(pj)) {
+          delete op;
+          return T2S2_EINVAL;
+        }
+        mean += pj / m;
+        for (int i = 0; i < m; ++i) hp.push_back(pj * D.Rt[(size_t)j * m + i]);
+      }
+      op->rho_bar *= mean;
+    }
+  }
+  t2s2_status st = upload_operator(op, static_cast<cudaStream_t>(stream), out);
+  if (st != T2S2_OK || hp.empty()) return st;
+  t2s2_op o = *out;
+  if (cudaMalloc(&o->dprod, sizeof(double) * hp.size()) != cudaSuccess ||
+      cudaMemcpy(o->dprod, hp.data(), sizeof(double) * hp.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    t2s2_op_destroy(o);
+    *out = nullptr;
+    return T2S2_ENOMEM;
+  }
+  size_t off = 0;
+  for (int k = 0; k < o->d; ++k) {
+    o->dP[k] = o->dprod + off;
+    off += (size_t)o->m[k] * o->m[k];
+  }
+  return T2S2_OK;
 }
 
 t2s2_status t2s2_build_spacetime_operator(const t2s2_problem* space, int n_t, double t_len, void* stream,
@@ -561,6 +679,7 @@ t2s2_status t2s2_op_destroy(t2s2_op op) {
   if (op->dmat) cudaFree(op->dmat);
   if (op->fmat) cudaFree(op->fmat);
   if (op->dfull) cudaFree(op->dfull);
+  if (op->dprod) cudaFree(op->dprod);
   if (op->arena.base) cudaFree(op->arena.base);
   if (op->hbuf) cudaFreeHost(op->hbuf);
   if (op->dstat) cudaFree(op->dstat);
@@ -633,6 +752,15 @@ t2s2_status t2s2_apply(t2s2_op op, const t2s2_tt* x, t2s2_tt* y, double c_mass, 
   T2S2_TRY(check_out_tt(op, y));
   for (int k = 0; k < op->d; ++k)
     if (y->cores[k] == x->cores[k]) return T2S2_EINVAL;
+  if (op->has_prod) {
+    // the rank-3 operator: FP64, ranks 3 r_x
+    T2S2_TRY(ensure_arena(op, 16 * tt_bytes(x) + ((size_t)4 << 20)));
+    Ctx cx = make_ctx(op, stream);
+    DevTT dx, dy;
+    T2S2_TRY(bind_tt(cx, x, dx, true));
+    T2S2_TRY(apply_full(op, cx, dx, dy, c_mass, c_op));
+    return unbind_tt(cx, dy, y);
+  }
   T2S2_TRY(ensure_arena(op, tt_bytes(x) + tt_bytes(y) + ((size_t)1 << 20)));
   Ctx cx = make_ctx(op, stream);
   DevTT dx, dy;
@@ -787,6 +915,7 @@ t2s2_status t2s2_residual(t2s2_op op, const t2s2_tt* b, const t2s2_tt* x, double
   DevTT db, dx;
   T2S2_TRY(bind_tt(cx, b, db, true));
   T2S2_TRY(bind_tt(cx, x, dx, true));
+  if (op->has_prod) return residual_full(op, cx, db, dx, c_mass, c_op, out);
   ResidualCache rc;
   return residual_fast(op, cx, db, dx, c_mass, c_op, out, &rc, false);
 }

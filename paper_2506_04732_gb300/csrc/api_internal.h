@@ -29,6 +29,12 @@ struct t2s2_op_s {
   // column), for lifting boundary data; null for the time dimension
   double* dfull = nullptr;
   double *dRf[T2S2_MAX_D] = {nullptr}, *dLf[T2S2_MAX_D] = {nullptr};
+  // a product reaction prod_k pi_k(x_k): P_k = diag(pi_k(eta)) Rt_k per
+  // dimension (m x m) and rho_bar = prod_k mean(pi_k(eta))
+  int has_prod = 0;
+  double* dprod = nullptr;
+  double* dP[T2S2_MAX_D] = {nullptr};
+  double rho_bar = 0.0;
   float* fptr[kMatsPerDim][T2S2_MAX_D] = {{nullptr}};
   t2s2::Arena arena;
   int team = 0;            // CTAs per cooperative local solve (0: whole GPU)
@@ -93,6 +99,17 @@ t2s2_status residual_fast(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, d
                           double* out, ResidualCache* rc, bool screen);
 t2s2_status residual_impl(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass,
                           double c_op, bool transformed, double* out, double* bnorm_io);
+// y = (c_mass M + c_op A) x, plus c_op times the product reaction when the
+// operator has one (ranks 3 r_x then, 2 r_x otherwise); y is allocated in
+// the arena.
+t2s2_status apply_full(t2s2_op op, Ctx& cx, const DevTT& x, DevTT& y, double c_mass, double c_op);
+// y = ((x)_k mats[k]) x: every core times its m x m matrix along its mode
+// (ranks kept); y is allocated in the arena.
+t2s2_status apply_kron(Ctx& cx, const DevTT& x, double* const* mats, DevTT& y);
+// ||b - (c_mass M + c_op A + c_op P) x|| / ||b|| through the orthogonalised
+// difference (operators with a product reaction).
+t2s2_status residual_full(t2s2_op op, Ctx& cx, const DevTT& b, const DevTT& x, double c_mass, double c_op,
+                          double* out);
 // The alternating solve of (c_mass M + c_op A) x = b on bound TTs (solve.cu).
 t2s2_status solve_run(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c_mass, double c_op,
                       double tol, int rmax, int max_sweeps, t2s2_precision prec, t2s2_solve_info* info);

@@ -15,14 +15,20 @@
     }                                                         \
   } while (0)
 
-#define T2S2_TRY(expr)                 \
-  do {                                 \
-    t2s2_status _s = (expr);           \
-    if (_s != T2S2_OK) return _s;      \
+// With T2S2_VERBOSE=1 every level a failure passes through is printed to
+// stderr (innermost first); the check costs nothing on the success path.
+#define T2S2_TRY(expr)                                      \
+  do {                                                      \
+    t2s2_status _s = (expr);                                \
+    if (_s != T2S2_OK) {                                    \
+      t2s2::note_failure(_s, #expr, __FILE__, __LINE__);    \
+      return _s;                                            \
+    }                                                       \
   } while (0)
 
 namespace t2s2 {
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void note_failure(int status, const char* what, const char* file, int line);
 
 // Programmatic dependent launch.  A kernel started by launch_pdl may begin
 // (its CTAs become resident) while the previous kernel of its stream is still

@@ -1136,6 +1136,95 @@ t2s2_status solve_run(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c_
   return solve_impl(op, cx, b, xio, c_mass, c_op, tol, rmax, max_sweeps, prec, info);
 }
 
+// Operators with a product reaction P: the reaction-free operator shifted by
+// the product's mean, K = c_mass M + c_op A + c_op rho_bar M, is solved by the
+// alternating solver with the rest of the reaction lagged,
+//     K x_{j+1} = b - c_op (P - rho_bar M) x_j,
+// each solve starting from x_j (its right-hand side is as smooth as b and
+// x_j, unlike a residual) at a tolerance that follows the full residual
+// ||b - (c_mass M + c_op A + c_op P) x_j|| / ||b||, until that is at most tol.
+// The steps contract by ||K^-1 c_op (P - rho_bar M)||.
+static t2s2_status prod_solve(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c_mass, double c_op,
+                              double tol, int rmax, int max_sweeps, t2s2_solve_info* info) {
+  constexpr int kMaxOuter = 60;
+  const int d = op->d;
+  const int rcap = rmax + amen_kick();
+  const double shift = c_op * op->rho_bar;
+  DevTT x;
+  int rx[T2S2_MAX_D + 1];
+  for (int k = 0; k <= d; ++k) rx[k] = std::min(xio.r[k], rcap);
+  rx[0] = rx[d] = 1;
+  T2S2_TRY(tt_alloc(cx, x, d, op->m, rx, rcap));
+  {
+    const size_t mk = cx.ar->mark();
+    DevTT t;
+    T2S2_TRY(tt_alloc(cx, t, d, op->m, xio.r, 0));
+    T2S2_TRY(tt_copy(cx, xio, t));
+    T2S2_TRY(tt_round(cx, t, 0.0, rcap));
+    T2S2_TRY(tt_copy(cx, t, x));
+    cx.ar->release(mk);
+  }
+  const char* ev = std::getenv("T2S2_VERBOSE");
+  const bool verbose = ev && ev[0] == '1';
+  double bn = 0.0;
+  T2S2_TRY(tt_norm(cx, b, &bn));
+  double res = 0.0;
+  int sweeps = 0, outer = 0;
+  for (;;) {
+    const size_t mk = cx.ar->mark();
+    T2S2_TRY(residual_full(op, cx, b, x, c_mass, c_op, &res));
+    if (verbose) {
+      fprintf(stderr, "[t2s2] lagged-reaction step %d: full residual %.3e, sweeps %d, ranks", outer, res, sweeps);
+      for (int k = 0; k <= d; ++k) fprintf(stderr, " %d", x.r[k]);
+      fprintf(stderr, "\n");
+    }
+    if (res <= tol || outer >= kMaxOuter || sweeps >= max_sweeps) {
+      cx.ar->release(mk);
+      break;
+    }
+    // rhs = b - c_op (P x - rho_bar M x)
+    DevTT px, mx, lag, rhs;
+    T2S2_TRY(apply_kron(cx, x, op->dP, px));
+    T2S2_TRY(apply_kron(cx, x, op->dRt, mx));
+    T2S2_TRY(tt_axpby(cx, c_op, px, -shift, mx, lag));
+    const double tin = std::max(0.3 * tol, 0.05 * res);
+    int rsum = 1, rbmax = 1;
+    for (int k = 0; k <= d; ++k) {
+      rsum = std::max(rsum, b.r[k] + lag.r[k]);
+      rbmax = std::max(rbmax, b.r[k]);
+    }
+    if (rsum > kSmallMax) {
+      // the sum would exceed the orthogonalisation's rank limit: compress the
+      // lagged term first, its error measured against |b|
+      double ln = 0.0;
+      T2S2_TRY(tt_norm(cx, lag, &ln));
+      T2S2_TRY(tt_round(cx, lag, ln > 0.0 ? 1e-3 * tin * bn / ln : 0.0, kSmallMax - rbmax));
+    }
+    T2S2_TRY(tt_axpby(cx, 1.0, b, -1.0, lag, rhs));
+    T2S2_TRY(tt_round(cx, rhs, 0.01 * tin, kSmallMax));
+    t2s2_solve_info ii{};
+    const t2s2_status st = solve_impl(op, cx, rhs, x, c_mass + shift, c_op, tin, rmax, max_sweeps - sweeps,
+                                      T2S2_FP64, &ii);
+    if (st != T2S2_OK && st != T2S2_ENOCONV) return st;
+    sweeps += std::max(1, ii.sweeps);
+    cx.ar->release(mk);
+    ++outer;
+  }
+  for (int k = 0; k < d; ++k)
+    if (x.core_elems(k) > xio.cap[k]) return T2S2_ENOMEM;
+  T2S2_TRY(tt_copy(cx, x, xio));
+  if (info) {
+    info->residual = res;
+    info->sweeps = sweeps;
+    int mr = 1;
+    for (int k = 0; k <= d; ++k) mr = std::max(mr, x.r[k]);
+    info->max_rank = mr;
+    info->refinements = outer;
+    info->local_iters = 0;
+  }
+  return res <= tol ? T2S2_OK : T2S2_ENOCONV;
+}
+
 size_t solve_bytes(t2s2_op op, int rmax, int rfmax, t2s2_precision prec) {
   size_t need = Amen::bytes_needed(op->d, op->m, rmax + amen_kick(), rfmax, amen_kick(), 40);
   if (prec != T2S2_FP64) need += refine_extra_bytes(op, rmax + amen_kick(), rfmax);
@@ -1154,12 +1243,24 @@ static t2s2_status solve_entry(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double 
   for (int k = 0; k <= op->d; ++k) rfmax = std::max(rfmax, b->r[k]);
   size_t need = Amen::bytes_needed(op->d, op->m, rmax + amen_kick(), rfmax, amen_kick(), 40) + 2 * (tt_bytes(b) + tt_bytes(x));
   if (prec != T2S2_FP64) need += refine_extra_bytes(op, rmax + amen_kick(), rfmax);
+  if (op->has_prod) {
+    if (prec != T2S2_FP64) return T2S2_ENOTIMPL;
+    // the lagged term P x - rho_bar M x (ranks 2 rcap) is rounded as one train
+    if (2 * (rmax + amen_kick()) > kSmallMax) return T2S2_EINVAL;
+    // the full operator's product and residual trains (ranks up to
+    // r_b + 3 rcap), their rounding temporaries, the correction and x + d
+    size_t mm = 1;
+    for (int k = 0; k < op->d; ++k) mm = std::max<size_t>(mm, op->m[k]);
+    const size_t r3 = (size_t)rfmax + 3 * (size_t)(rmax + amen_kick());
+    need += 12 * (size_t)op->d * r3 * r3 * mm * sizeof(double);
+  }
   T2S2_TRY(ensure_arena(op, need));
   Ctx cx = make_ctx(op, stream);
   DevTT db, dx;
   T2S2_TRY(bind_tt(cx, b, db, true));
   T2S2_TRY(bind_tt(cx, x, dx, true));
-  t2s2_status st = solve_impl(op, cx, db, dx, c_mass, c_op, tol, rmax, max_sweeps, prec, info);
+  t2s2_status st = op->has_prod ? prod_solve(op, cx, db, dx, c_mass, c_op, tol, rmax, max_sweeps, info)
+                                : solve_impl(op, cx, db, dx, c_mass, c_op, tol, rmax, max_sweeps, prec, info);
   if (st != T2S2_OK && st != T2S2_ENOCONV) return st;
   t2s2_status st2 = unbind_tt(cx, dx, x);
   return st2 != T2S2_OK ? st2 : st;
@@ -1168,6 +1269,7 @@ static t2s2_status solve_entry(t2s2_op op, const t2s2_tt* b, t2s2_tt* x, double 
 static t2s2_status step_entry(t2s2_op op, t2s2_tt* u, double dt, double tol, int rmax, bool cn,
                               t2s2_precision prec, void* stream, t2s2_solve_info* info) {
   if (!op || !u || !(dt > 0.0) || !(tol > 0.0) || rmax < 1) return T2S2_EINVAL;
+  if (op->has_prod) return T2S2_ENOTIMPL;
   T2S2_TRY(check_tt(op, u));
   const int d = op->d;
   size_t need = Amen::bytes_needed(d, op->m, rmax + amen_kick(), 2 * (rmax + amen_kick()), amen_kick(), 40) + 8 * tt_bytes(u);

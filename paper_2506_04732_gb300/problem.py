@@ -75,7 +75,8 @@ def source_cores(problem, op):
 def varcoef_source_cores(vp, op):
     """b = -eps Laplace u* + beta . grad u* + rho u* on the collocation grid
     for a workloads.VarCoefProblem: per term and dimension the factor
-    beta_k(eta) phi' - eps phi'' + (rho_k(eta) [+ rho0 for k = 0]) phi."""
+    beta_k(eta) phi' - eps phi'' + (rho_k(eta) [+ rho0 for k = 0]) phi, and
+    with a product reaction one more rank-1 block per term."""
     problem = vp.problem
     d, eps = problem.d, problem.eps
     blocks = []
@@ -102,6 +103,14 @@ def varcoef_source_cores(vp, op):
             cores.append(c)
         cores[0] = cores[0] * t.coef
         blocks.append(cores)
+        if vp.prod:
+            # the product reaction of this term, prod_k pi_k(eta) phi_k(eta)
+            prod = []
+            for k in range(d):
+                _, eta = op.nodes(k)
+                prod.append((vp.prod_fn(k)(eta) * t.factors[k](eta)).reshape(1, -1, 1))
+            prod[0] = prod[0] * t.coef
+            blocks.append(prod)
     return _block_tt(blocks)
 
 
@@ -110,7 +119,8 @@ def build_operator_var(vp, stream=None):
     from . import t2s2_build_operator_var
     p = vp.problem
     return t2s2_build_operator_var(p.d, p.n, p.beta, p.eps, [vp.beta_fn(k) for k in range(p.d)],
-                                   [vp.rho_fn(k) for k in range(p.d)], vp.rho0, p.plain_sc, stream)
+                                   [vp.rho_fn(k) for k in range(p.d)], vp.rho0, p.plain_sc, stream,
+                                   [vp.prod_fn(k) for k in range(p.d)] if vp.prod else None)
 
 
 def solution_cores(problem, op):

@@ -17,6 +17,7 @@ def _vc(d, n, ratio=0.05, seed=3, prod=False):
     vc = V.VarCoef(np.asarray(vp.problem.beta), [vp.beta_fn(k) for k in range(d)],
                    [vp.rho_fn(k) for k in range(d)], vp.rho0,
                    [vp.prod_fn(k) for k in range(d)] if prod else None)
+    vp.prod = prod
     return vp, vc
 
 

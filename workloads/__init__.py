@@ -285,6 +285,7 @@ class VarCoefProblem:
     amp: np.ndarray
     rho_c: np.ndarray
     rho0: float
+    prod: bool = False
 
     def beta_fn(self, k):
         b, a = float(self.problem.beta[k]), float(self.amp[k])
@@ -305,14 +306,16 @@ class VarCoefProblem:
 
 
 def config_varcoef(seed: int = 9, d: int = 6, n: int = 32, ratio: float = 1e-3, tol: float = 1e-8,
-                   rmax: int = 20) -> VarCoefProblem:
+                   rmax: int = 20, prod: bool = False) -> VarCoefProblem:
     """Variable convection beta_k(x_k) (amplitudes a_k in [0.2, 0.5] around a
     seeded unit vector) and reaction rho0 + sum_k c_k (1 + x_k^2) (rho0 = 0.5,
-    c_k in [0, 0.3]); u* the rank-4 recipe of config1 with the same seed."""
+    c_k in [0, 0.3]), plus with `prod` the paper's product reaction
+    prod_k (1/2 - (x_k + 11/10)(x_k - 1/2)(x_k + 1/2)(x_k - 11/10)); u* the
+    rank-4 recipe of config1 with the same seed."""
     base = config1(seed_beta=seed, seed_terms=seed + 1, d=d, n=n, ratio=ratio, rmax=rmax, tol=tol)
-    base.name = f"varcoef d={d} n={n} ratio={ratio:g}"
+    base.name = f"varcoef{'+prod' if prod else ''} d={d} n={n} ratio={ratio:g}"
     rng = np.random.default_rng(seed + 2)
-    return VarCoefProblem(base, rng.uniform(0.2, 0.5, d), rng.uniform(0.0, 0.3, d), 0.5)
+    return VarCoefProblem(base, rng.uniform(0.2, 0.5, d), rng.uniform(0.0, 0.3, d), 0.5, prod)
 
 
 def sine_problem(d: int, n: int, ratio: float, seed: int = 5, tol: float = 1e-8,
