@@ -8,7 +8,7 @@
 //     every CTA:  partial Gram of its own vectors (compact lower triangle)
 //                                                             (grid sync)
 //     CTA b:      sums its slice of the Gram over all partials (grid sync)
-//     every CTA:  loads the Gram; if it is within kOrthDev of the identity
+//     every CTA:  loads the Gram; if it is within kOrthDev / c of the identity
 //                 this pass is the last one (and pass 0 runs unshifted);
 //                 (Gram + shift I) = L D L^T, semidefinite (pivots below
 //                 64 u max diag zeroed), with L^{-1} built in the same
@@ -36,6 +36,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <atomic>
 
 #include "fastmath.cuh"
@@ -52,7 +54,11 @@ constexpr int kThreads = 256;
 constexpr int kCholQrMaxSmem = 200 * 1024;
 constexpr int kMaxGrid = 128;    // CTAs of one factorisation
 constexpr int kPerTarget = 8;    // vectors per CTA
-constexpr float kOrthDev = 1e-3f;
+// a pass is the last one when every entry of its Gram is within kOrthDev / c
+// of the identity's: then the spectral distance is at most kOrthDev, the
+// block's condition number at most sqrt(3), and one more CholeskyQR pass
+// leaves Q orthonormal to working precision (the CholeskyQR2 argument)
+constexpr float kOrthDev = 0.5f;
 constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
 
 struct CholQrArgs {
@@ -67,7 +73,19 @@ struct CholQrArgs {
   int nlong, c, per;  // vectors, their length, vectors per CTA
   int tall;
   double shift_rel;
+  unsigned long long* tstamp;  // diagnostics: phase times of CTA 0 (null: off)
 };
+
+constexpr int kQrStamps = 2 + 6 * 3 + 1;
+
+#define QR_STAMP(k)                                                                   \
+  do {                                                                                \
+    if (a.tstamp && blockIdx.x == 0 && threadIdx.x == 0) {                            \
+      unsigned long long ts_;                                                         \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(ts_));                         \
+      a.tstamp[k] = ts_;                                                              \
+    }                                                                                 \
+  } while (0)
 
 __host__ __device__ inline int tri_count(int c) { return c * (c + 1) / 2; }
 
@@ -96,6 +114,7 @@ __device__ __forceinline__ double pivot_rcp(double v, float f) {
 
 __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
   pdl_trigger();
+  QR_STAMP(0);
   cg::grid_group grid = cg::this_grid();
   extern __shared__ double sm[];
   const int c = a.c, T = tri_count(c);
@@ -126,6 +145,7 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
     for (int ib = 0; ib <= ia; ++ib) tri[ia * (ia + 1) / 2 + ib] = (ia << 8) | ib;
   if (t == 0) bad = 0;
   __syncthreads();
+  QR_STAMP(1);
   const int sl = (T + G - 1) / G;  // Gram entries summed by each CTA
   int pass = 0;
   for (;; ++pass) {
@@ -137,6 +157,7 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
       a.part[(long)b * T + e] = s;
     }
     grid.sync();
+    QR_STAMP(2 + 6 * pass + 0);
     // (2) this CTA's slice of the Gram: lanes over the partials, then a fixed
     // shuffle tree
     for (int e = b * sl + warp; e < min(T, (b + 1) * sl); e += kThreads / 32) {
@@ -147,6 +168,7 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
       if (lane == 0) a.gsum[e] = s;
     }
     grid.sync();
+    QR_STAMP(2 + 6 * pass + 1);
     // (3) load the Gram; the largest diagonal and the distance from the
     // identity as integer maxima of bit patterns (non-negative values order
     // like their bits); exactly zero columns, left by zeroed pivots, do not
@@ -174,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
     if (t == 0) {
       unsigned M = 0, D = 0;
       for (int w = 0; w < kThreads / 32; ++w) M = max(M, ired[0][w]), D = max(D, ired[1][w]);
-      const bool fin = (__uint_as_float(D) <= kOrthDev) || c == 1 || pass == 2;
+      const bool fin = (__uint_as_float(D) * c <= kOrthDev) || c == 1 || pass == 2;
       const double mx = __hiloint2double((int)M, 0);
       // shift of the first pass, with c * (largest diagonal) >= trace
       const double sh = (pass == 0 && !fin) ? a.shift_rel * c * mx : 0.0;
@@ -205,6 +227,7 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
       }
     }
     __syncthreads();
+    QR_STAMP(2 + 6 * pass + 2);
     // (4) L D L^T: step j takes column j out of the trailing block and out of
     // the rows of L^{-1} below j.  Thread 0 updates the next pivot and takes
     // its reciprocal; the other threads do the rest.
@@ -241,6 +264,7 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
       sdn[i] = d * is;
     }
     __syncthreads();
+    QR_STAMP(2 + 6 * pass + 3);
     // (5) v <- D^{-1/2} L^{-1} v for own vectors; rows i and c-1-i together,
     // so that every thread runs c + 1 products
     {
@@ -265,6 +289,7 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
       A[i * c + j] = (i == j) ? sdn[j] * sc : A[i * c + j] * isdn[j] * sc;
     }
     __syncthreads();
+    QR_STAMP(2 + 6 * pass + 4);
     // (6) own rows of Lacc <- Lacc L D^{1/2}
     for (int e = t; e < nrow * c; e += kThreads) {
       const int q = e / c, k = e % c, i = b + q * G;
@@ -277,6 +302,7 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
       Lr2[q * c + k] = s;
     }
     __syncthreads();
+    QR_STAMP(2 + 6 * pass + 5);
     double* tmp = Lr;
     Lr = Lr2;
     Lr2 = tmp;
@@ -294,6 +320,7 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
     if (a.tall) a.R[k * c + i] = Lr[q * c + k];
     else a.R[i * c + k] = Lr[q * c + k];
   }
+  QR_STAMP(kQrStamps - 1);
   if (b == 0 && t == 0 && a.status) *a.status = bad;
 }
 
@@ -361,12 +388,44 @@ t2s2_status cholqr3_fused(const double* W, double* Q, double* R, int nlong, int 
   a.per = per;
   a.tall = tall ? 1 : 0;
   a.shift_rel = shift_rel;
+  a.tstamp = nullptr;
+  // T2S2_QR_TIMING=N: the N-th fused factorisation of the process prints the
+  // phase times of its CTA 0 (diagnostics; synchronises that one call)
+  static const int stamp_at = [] {
+    const char* e = std::getenv("T2S2_QR_TIMING");
+    return (e && e[0] >= '0' && e[0] <= '9') ? std::atoi(e) : -1;
+  }();
+  static std::atomic<int> calls{0};
+  static unsigned long long* stamp_buf = nullptr;
+  const bool stamp_this = stamp_at >= 0 && calls.fetch_add(1) == stamp_at;
+  if (stamp_this) {
+    if (!stamp_buf) T2S2_CUDA_TRY(cudaMalloc(&stamp_buf, sizeof(unsigned long long) * kQrStamps));
+    T2S2_CUDA_TRY(cudaMemsetAsync(stamp_buf, 0, sizeof(unsigned long long) * kQrStamps, st));
+    a.tstamp = stamp_buf;
+  }
   // work of two passes (the common case): Gram and triangular product
   // 2 n c^2 each, the L D L^T with its inverse 2 c^3 / 3
   const double fl = 2.0 * (4.0 * nlong * (double)c * c) + 2.0 * (2.0 * (double)c * c * c / 3.0);
   TraceScope ts(kTrCholQR, st, fl, 16.0 * nlong * c);
   void* args[] = {&a};
   T2S2_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)cholqr3_kernel, dim3(grid), dim3(kThreads), args, smem, st));
+  if (stamp_this) {
+    unsigned long long h[kQrStamps];
+    T2S2_CUDA_TRY(cudaMemcpyAsync(h, stamp_buf, sizeof(h), cudaMemcpyDeviceToHost, st));
+    T2S2_CUDA_TRY(cudaStreamSynchronize(st));
+    fprintf(stderr, "[t2s2] cholqr3 phase times (ns) nlong=%d c=%d grid=%d: load %lld", nlong, c, grid,
+            (long long)(h[1] - h[0]));
+    unsigned long long prev = h[1];
+    for (int p = 0; p < 3 && h[2 + 6 * p]; ++p) {
+      fprintf(stderr, " | pass %d:", p);
+      for (int k = 0; k < 6; ++k) {
+        fprintf(stderr, " %lld", (long long)(h[2 + 6 * p + k] - prev));
+        prev = h[2 + 6 * p + k];
+      }
+    }
+    fprintf(stderr, " | store %lld total %lld\n", (long long)(h[kQrStamps - 1] - prev),
+            (long long)(h[kQrStamps - 1] - h[0]));
+  }
   return T2S2_OK;
 }
 

@@ -29,4 +29,16 @@ t2s2_status cholqr3_fused(const double* W, double* Q, double* R, int nlong, int 
                           double* scratch, int* status, int grid, int per, size_t smem, cudaStream_t st,
                           const double* W2 = nullptr, int c1 = 0);
 
+// The same factorisation in one thread-block cluster of up to 16 CTAs
+// (cholqr_cluster.cu), for blocks that fit its shared memory: one cluster
+// barrier per pass instead of two grid barriers, and a launch that overlaps
+// the previous kernel.  Same layouts, outputs and status as cholqr3_fused;
+// plan first (false: take the full-grid kernel).  R is triangular unless
+// the last pass took the series of (I + E)^(-1/2), in which case it is a full
+// matrix (still W = Q R, resp. W = R Q).
+bool cqr_cluster_plan(int nlong, int c, int* cl, int* per, size_t* smem);
+t2s2_status cqr_cluster(const double* W, double* Q, double* R, int nlong, int c, bool tall, double shift_rel,
+                        int* status, int cl, int per, size_t smem, cudaStream_t st, const double* W2 = nullptr,
+                        int c1 = 0);
+
 }  // namespace t2s2

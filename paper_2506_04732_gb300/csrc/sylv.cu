@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
   cf* G = Inv + (size_t)m * ra * la;              // ra x lm: G, then Y in place
   cf* tv = G + ra * lm;                           // kSylvMaxRa: one right-hand side
   cf* prow = tv + kSylvMaxRa;                     // per warp: the pivot row
-  __shared__ double red[kSylvThreads / 32];
+  __shared__ double red[kSylvThreads / 32 + 1], red2[kSylvThreads / 32 + 1];
   __shared__ int fail;
   int nst = 0;
   auto stamp = [&]() {
@@ -214,21 +214,36 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
         if (step == 0) pfs = fma(Fr[e], Fr[e], pfs);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      prs += __shfl_xor_sync(0xffffffffu, prs, o);
-      pfs += __shfl_xor_sync(0xffffffffu, pfs, o);
+    // binary64 sums: a warp instruction holds an FP64 pipe for ~64 cycles
+    // whatever its active lanes, so only warps that hold terms reduce, and
+    // one warp combines the per-warp sums
+    const int wact = (min(kSylvThreads, ra * m) + 31) >> 5;
+    if (warp < wact) {
+      for (int o = 16; o > 0; o >>= 1) prs += __shfl_xor_sync(0xffffffffu, prs, o);
+      if (step == 0)
+        for (int o = 16; o > 0; o >>= 1) pfs += __shfl_xor_sync(0xffffffffu, pfs, o);
+      if (lane == 0) {
+        red[warp] = prs;
+        red2[warp] = pfs;
+      }
     }
-    if (lane == 0) red[warp] = prs;
     __syncthreads();
-    rr = 0.0;
-    for (int w = 0; w < kSylvThreads / 32; ++w) rr += red[w];
-    __syncthreads();
-    if (step == 0) {
-      if (lane == 0) red[warp] = pfs;
-      __syncthreads();
-      for (int w = 0; w < kSylvThreads / 32; ++w) ff += red[w];
-      __syncthreads();
+    if (warp == 0) {
+      double v = lane < wact ? red[lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      double f = 0.0;
+      if (step == 0) {
+        f = lane < wact ? red2[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+      }
+      if (lane == 0) {
+        red[kSylvThreads / 32] = v;
+        red2[kSylvThreads / 32] = f;
+      }
     }
+    __syncthreads();
+    rr = red[kSylvThreads / 32];
+    if (step == 0) ff = red2[kSylvThreads / 32];
     stamp();
     if (rr <= P.tol_rel * P.tol_rel * ff || rr == 0.0) break;  // converged
     if ((rr_prev >= 0.0 && rr > 0.01 * rr_prev) || step == kSylvMaxSteps) {

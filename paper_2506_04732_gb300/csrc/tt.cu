@@ -177,6 +177,11 @@ static bool qr_fused(Ctx& cx, const double* W, int nlong, int c, bool tall, doub
                      t2s2_status* st, const double* W2 = nullptr, int c1 = 0) {
   int grid = 0, per = 0;
   size_t smem = 0;
+  const double shift = 11.0 * ((double)nlong * c + (double)c * (c + 1)) * kUnit;
+  if (cqr_cluster_plan(nlong, c, &grid, &per, &smem)) {
+    *st = cqr_cluster(W, Q, R, nlong, c, tall, shift, cx.dstat, grid, per, smem, cx.st, W2, c1);
+    return true;
+  }
   if (!cholqr3_plan(nlong, c, cx.coop_ctas, &grid, &per, &smem)) return false;
   const size_t mk = cx.ar->mark();
   double* scratch = aget<double>(cx, cholqr3_scratch_doubles(nlong, c, grid));
@@ -184,7 +189,6 @@ static bool qr_fused(Ctx& cx, const double* W, int nlong, int c, bool tall, doub
     cx.ar->release(mk);
     return false;
   }
-  const double shift = 11.0 * ((double)nlong * c + (double)c * (c + 1)) * kUnit;
   *st = cholqr3_fused(W, Q, R, nlong, c, tall, shift, scratch, cx.dstat, grid, per, smem, cx.st, W2, c1);
   cx.ar->release(mk);
   return true;
@@ -195,11 +199,15 @@ bool qr_tall_async(Ctx& cx, const double* W, int rows, int cols, double* Q, doub
   int grid = 0, per = 0;
   size_t smem = 0;
   if (cols < 1 || cols > kSmallMax || rows < cols) return false;
+  const double shift = 11.0 * ((double)rows * cols + (double)cols * (cols + 1)) * kUnit;
+  if (cqr_cluster_plan(rows, cols, &grid, &per, &smem)) {
+    *st = cqr_cluster(W, Q, R, rows, cols, true, shift, cx.dstat, grid, per, smem, side);
+    return true;
+  }
   if (!cholqr3_plan(rows, cols, cx.coop_ctas, &grid, &per, &smem)) return false;
   // held (not released) until the caller joins the side stream
   double* scratch = aget<double>(cx, cholqr3_scratch_doubles(rows, cols, grid));
   if (!scratch) return false;
-  const double shift = 11.0 * ((double)rows * cols + (double)cols * (cols + 1)) * kUnit;
   *st = cholqr3_fused(W, Q, R, rows, cols, true, shift, scratch, cx.dstat, grid, per, smem, side);
   return true;
 }
