@@ -43,7 +43,7 @@ size_t sylv_smem_bytes(int ra, int m) {
   const size_t dbl = (size_t)ra * ra + (size_t)m * lm + 3 * (size_t)ra * m;
   const size_t cpx = 2 * (size_t)m * lm + (size_t)m * ra * la + (size_t)ra * lm + kSylvMaxRa +
                      (size_t)(kSylvThreads / 32) * kSylvMaxRa;
-  return sizeof(double) * dbl + sizeof(cf) * cpx;
+  return sizeof(double) * dbl + sizeof(cf) * cpx + sizeof(float) * (size_t)ra * ra;
 }
 
 __device__ __forceinline__ unsigned long long sylv_clock() {
@@ -62,7 +62,7 @@ __device__ __forceinline__ cf cinv(cf a) {
 // column for the pivot-row steps); segment-local maxima by shuffles within
 // the W lanes.  A vanishing pivot sets *fail.
 template <int W>
-__device__ void sylv_invert(cf* Inv, const cf* Ts, const double* PL, double pi, int ra, int la, int lm, int m,
+__device__ void sylv_invert(cf* Inv, const cf* Ts, const float* PL, double pi, int ra, int la, int lm, int m,
                             cf* prow_w, int warp, int nwarps, int lane, int* fail) {
   constexpr int S = 32 / W;
   const int seg = lane / W, sl = lane % W;
@@ -76,7 +76,7 @@ __device__ void sylv_invert(cf* Inv, const cf* Ts, const double* PL, double pi, 
       const cf s = cadd(Ts[i * lm + i], cmk((float)pi, 0.f));
       for (int e = sl; e < ra * ra; e += W) {
         const int p = e / ra, q = e % ra;
-        const cf v = cadd(cmk((float)PL[e], 0.f), p == q ? s : cmk(0.f, 0.f));
+        const cf v = cadd(cmk(PL[e], 0.f), p == q ? s : cmk(0.f, 0.f));
         A[p * la + q] = v;
         amax = fmaxf(amax, cabs2(v));
       }
@@ -146,7 +146,10 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
   double* PL = reinterpret_cast<double*>(smem);  // ra x ra
   double* Bp = PL + ra * ra;                      // m x lm
   double* X = Bp + m * lm;                        // ra x m
-  double* R = X + ra * m;                         // ra x m
+  // ra x m: the residual, kept in binary32 (it only feeds the binary32
+  // preconditioner, and a binary64 -> binary32 conversion holds the FP64 pipe)
+  float* Rf = reinterpret_cast<float*>(X + ra * m);
+  double* R = X + ra * m;                         // ra x m slot (holds Rf, then PLf)
   double* F = R + ra * m;                         // ra x m
   cf* Ts = reinterpret_cast<cf*>(F + ra * m);     // m x lm (upper triangle)
   cf* Z = Ts + m * lm;                            // m x lm
@@ -154,6 +157,7 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
   cf* G = Inv + (size_t)m * ra * la;              // ra x lm: G, then Y in place
   cf* tv = G + ra * lm;                           // kSylvMaxRa: one right-hand side
   cf* prow = tv + kSylvMaxRa;                     // per warp: the pivot row
+  float* PLf = reinterpret_cast<float*>(prow + (kSylvThreads / 32) * kSylvMaxRa);  // ra x ra, binary32
   __shared__ double red[kSylvThreads / 32 + 1], red2[kSylvThreads / 32 + 1];
   __shared__ int fail;
   int nst = 0;
@@ -163,7 +167,11 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
   stamp();
   const double pi = P.PR[0];
   const float cop = (float)P.c_op, sh = (float)P.shift;
-  for (int e = t; e < ra * ra; e += kSylvThreads) PL[e] = P.PL[e];
+  for (int e = t; e < ra * ra; e += kSylvThreads) {
+    const double v = P.PL[e];
+    PL[e] = v;
+    PLf[e] = (float)v;
+  }
   for (int e = t; e < m * m; e += kSylvThreads) {
     const int i = e / m, j = e % m;
     Bp[i * lm + j] = P.Bp[e];
@@ -180,9 +188,9 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
   // inverses of A_i = P_L + (Ts_ii + pi) I by Gauss-Jordan: two matrices per
   // warp (16-lane halves) when ra <= 16, else one
   if (ra <= 16)
-    sylv_invert<16>(Inv, Ts, PL, pi, ra, la, lm, m, prow + warp * kSylvMaxRa, warp, kSylvThreads / 32, lane, &fail);
+    sylv_invert<16>(Inv, Ts, PLf, pi, ra, la, lm, m, prow + warp * kSylvMaxRa, warp, kSylvThreads / 32, lane, &fail);
   else
-    sylv_invert<32>(Inv, Ts, PL, pi, ra, la, lm, m, prow + warp * kSylvMaxRa, warp, kSylvThreads / 32, lane, &fail);
+    sylv_invert<32>(Inv, Ts, PLf, pi, ra, la, lm, m, prow + warp * kSylvMaxRa, warp, kSylvThreads / 32, lane, &fail);
   __syncthreads();
   stamp();
   int status = fail ? 1 : 0;
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
       const double* __restrict__ Br = Bp;
       const double* __restrict__ Pr = PL;
       const double* __restrict__ Fr = F;
-      double* __restrict__ Rw = R;
+      float* __restrict__ Rw = Rf;
       for (int e = t; e < ra * m; e += kSylvThreads) {
         const int a = e / m, i = e % m;
         double s0 = pi * Xr[e], s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
         }
         for (; j < m; ++j) s1 = fma(Br[i * lm + j], Xr[a * m + j], s1);
         const double r = Fr[e] - ((s0 + s1) + (s2 + s3));
-        Rw[e] = r;
+        Rw[e] = (float)r;
         prs = fma(r, r, prs);
         if (step == 0) pfs = fma(Fr[e], Fr[e], pfs);
       }
@@ -253,7 +261,7 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
     rr_prev = rr;
     // G = R conj(Z)
     {
-      const double* __restrict__ Rr = R;
+      const float* __restrict__ Rr = Rf;
       const cf* __restrict__ Zr = Z;
       cf* __restrict__ Gw = G;
       for (int e = t; e < ra * m; e += kSylvThreads) {
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
         float gr = 0.f, gi = 0.f, hr = 0.f, hi = 0.f;
         int j = 0;
         for (; j + 1 < m; j += 2) {
-          const float rv = (float)Rr[a * m + j], rw = (float)Rr[a * m + j + 1];
+          const float rv = Rr[a * m + j], rw = Rr[a * m + j + 1];
           const cf z = Zr[j * lm + i], w = Zr[(j + 1) * lm + i];
           gr = fmaf(rv, z.x, gr);
           gi = fmaf(-rv, z.y, gi);
@@ -269,7 +277,7 @@ __global__ void __launch_bounds__(kSylvThreads) sylv_rb1_kernel(SylvProblem P) {
           hi = fmaf(-rw, w.y, hi);
         }
         if (j < m) {
-          const float rv = (float)Rr[a * m + j];
+          const float rv = Rr[a * m + j];
           const cf z = Zr[j * lm + i];
           gr = fmaf(rv, z.x, gr);
           gi = fmaf(-rv, z.y, gi);
