@@ -188,14 +188,14 @@ ALU_FAMILIES = ("gemm", "apply", "local_solve", "small_factor", "cholqr", "sylve
 # family's dominant kernel from an ncu capture of the current build, with the
 # summary it comes from; a family without a current capture is left out.
 KERNEL_DRAM_BYTES = {
-    "sylvester": (110848.0, "profiles/sylv_rb1_kernel_steady_d6n32.md"),
-    "cholqr": (97664.0, "profiles/cholqr3_kernel_steady_d6n32.md"),
+    "sylvester": (107008.0, "profiles/sylv_rb1_kernel_steady_d6n32.md"),
+    "cholqr": (104064.0, "profiles/cqr_cluster_kernel_steady_d6n32.md"),
 }
 
 
 def kernel_family(name: str) -> str:
     """Trace family of a kernel, by its (demangled) name."""
-    table = (("cholqr3_kernel", "cholqr"), ("sylv_rb1_kernel", "sylvester"), ("tt_norm2_dd_kernel", "dots"),
+    table = (("cholqr3_kernel", "cholqr"), ("cqr_cluster_kernel", "cholqr"), ("sylv_rb1_kernel", "sylvester"), ("tt_norm2_dd_kernel", "dots"),
              ("tt_dots_kernel", "dots"), ("small_group_kernel", "gemm"), ("small_kernel", "gemm"),
              ("gemm_tc_kernel", "gemm_tc"), ("gemm_kernel", "gemm"), ("splitk", "gemm"),
              ("apply_tc_kernel", "apply_tc"), ("apply_kernel", "apply"), ("gmres_team_kernel", "local_solve"),

@@ -114,6 +114,7 @@ def test_kernel_names_map_to_trace_families():
     # families; unknown kernels (torch's own) are "other"
     kf = bench.kernel_family
     assert kf("void t2s2::(anonymous namespace)::cholqr3_kernel<26>(t2s2::CqrArgs)") == "cholqr"
+    assert kf("t2s2::(anonymous namespace)::cqr_cluster_kernel(t2s2::(anonymous namespace)::CqrArgs)") == "cholqr"
     assert kf("t2s2::sylv_rb1_kernel(t2s2::SylvProblem)") == "sylvester"
     assert kf("void t2s2::small_group_kernel<8, 16>(t2s2::GroupArgs)") == "gemm"
     assert kf("void t2s2::small_kernel<4, 4>(t2s2::Gemm<double>)") == "gemm"
