@@ -115,6 +115,8 @@ __device__ __forceinline__ void stamp(const CqrArgs& a, int k) {
 }
 
 __global__ void __launch_bounds__(kThr) cqr_cluster_kernel(CqrArgs a) {
+  pdl_wait();  // W comes from the previous kernel of the stream
+  pdl_trigger();
   cg::cluster_group cl = cg::this_cluster();
   const int CL = (int)cl.num_blocks();
   const int b = (int)cl.block_rank();
@@ -141,8 +143,6 @@ __global__ void __launch_bounds__(kThr) cqr_cluster_kernel(CqrArgs a) {
   __shared__ double shift, sc, isc;
   __shared__ float tauf;
   __shared__ int bad, last, nterm;
-  pdl_wait();  // W comes from the previous kernel of the stream
-  pdl_trigger();
   stamp(a, 0);
   for (int e = t; e < cnt * c; e += kThr) {
     const int r = a.tall ? e / c : e % cnt, j = a.tall ? e % c : e / cnt;

@@ -31,6 +31,11 @@ def test_every_pdl_launched_kernel_waits_first():
     launched = set()
     for s in srcs.values():
         launched |= set(re.findall(r"launch_pdl\(\s*([A-Za-z_][A-Za-z_0-9]*)", s))
+        # cluster launches through cudaLaunchKernelEx with the programmatic
+        # attribute: the stage kernels' cluster variants and the cluster QR
+        launched |= set(re.findall(r"launch_stages\([^;]*?([A-Za-z_][A-Za-z_0-9]*)<true>", s))
+        launched |= set(re.findall(r"cudaLaunchKernelEx\(&cfg,\s*([A-Za-z_][A-Za-z_0-9]*)", s))
+    launched.discard("clus")  # launch_stages' parameter: its kernels are found above
     assert len(launched) >= 10
     for k in sorted(launched):
         bodies = [b for s in srcs.values() for b in _kernel_bodies(s, k)]
@@ -44,6 +49,9 @@ def test_cooperative_kernels_are_not_pdl_launched():
     coop = set()
     for s in srcs.values():
         coop |= set(re.findall(r"cudaLaunchCooperativeKernel\(\s*\(\s*(?:const\s+)?void\s*\*\s*\)\s*([A-Za-z_][A-Za-z_0-9]*)", s))
+        # launch_stages(coop, cluster, ...): the first is launched cooperatively
+        coop |= set(re.findall(r"launch_stages\(\s*([A-Za-z_][A-Za-z_0-9]*)<false>", s))
+    coop.discard("coop")
     assert {"cholqr3_kernel", "tt_dots_kernel", "tt_norm2_dd_kernel", "gmres_team_kernel"} <= coop
     for s in srcs.values():
         for k in coop:
