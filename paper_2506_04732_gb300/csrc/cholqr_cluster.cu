@@ -57,7 +57,7 @@ constexpr size_t kClMaxSmem = 200 * 1024;
 constexpr float kOrthDev = 0.5f;  // spectral distance of the last pass's Gram from I
 constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
 // binary64 Gram products per CTA and pass the plan aims at (~0.3 us)
-constexpr long kWorkPerCta = 1024;
+constexpr long kWorkPerCta = 2048;
 // blocks above this many Gram products go to the full-grid kernel
 constexpr long kMaxWork = 16L * 16384;
 constexpr int kStamps = 2 + 6 * 3 + 1;
@@ -67,6 +67,11 @@ constexpr float kPolyDev = 1e-3f;
 constexpr int kPolyMaxC = 32;
 constexpr int kPolyMaxTerms = 6;
 constexpr int kSumBatch = 4;  // remote partial-Gram loads in flight per thread
+
+// binom(-1/2, p) and binom(1/2, p), p = 0..6: dyadic, exact in binary64
+__constant__ double kSeriesA[kPolyMaxTerms + 1] = {1.0, -0.5, 0.375, -0.3125, 0.2734375, -0.24609375, 0.2255859375};
+__constant__ double kSeriesB[kPolyMaxTerms + 1] = {1.0, 0.5, -0.125, 0.0625, -0.0390625, 0.02734375,
+                                                   -0.0205078125};
 
 struct CqrArgs {
   const double* W;
@@ -100,10 +105,23 @@ __device__ __forceinline__ double win(const CqrArgs& a, int i, int j) {
   return a.W[vidx(a, i, j)];
 }
 
-// binary32 seed and one binary64 Newton step: 1/v to about 2^-46
-__device__ __forceinline__ double pivot_rcp(double v, float f) {
-  double y = (double)__frcp_rn(f);
+// 1/v for a pivot v of the scaled Gram (tau < v < 4, so v's exponent is a
+// binary32 one): a binary32 seed from v's bits (truncated, integer
+// operations -- a binary64 <-> binary32 conversion holds the FP64 pipe like a
+// multiply), its reciprocal widened the same way, one binary64 Newton step:
+// about 2^-46.
+__device__ __forceinline__ double pivot_rcp(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const float f = __uint_as_float(((hi - ((1023u - 127u) << 20)) << 3) | (lo >> 29));
+  const unsigned yb = __float_as_uint(__frcp_rn(f));
+  const double y = __hiloint2double((int)((yb >> 3) + ((1023u - 127u) << 20)), (int)(yb << 29));
   return y * fma(-v, y, 2.0);
+}
+
+// v > tau for positive tau by the bit patterns (non-negative doubles order
+// like their bits, negative ones are negative integers): no FP64 compare
+__device__ __forceinline__ bool pivot_kept(double v, long long tau_bits) {
+  return __double_as_longlong(v) > tau_bits;
 }
 
 __device__ __forceinline__ void stamp(const CqrArgs& a, int k) {
@@ -141,7 +159,7 @@ __global__ void __launch_bounds__(kThr) cqr_cluster_kernel(CqrArgs a) {
   int* tri = reinterpret_cast<int*>(PX + (c <= kPolyMaxC ? 3 * c * c : 0));  // (row << 8) | col, lower triangle
   __shared__ unsigned ired[2][kThr / 32];
   __shared__ double shift, sc, isc;
-  __shared__ float tauf;
+  __shared__ long long taub;  // bits of the pivot threshold (a positive double)
   __shared__ int bad, last, nterm;
   stamp(a, 0);
   for (int e = t; e < cnt * c; e += kThr) {
@@ -236,7 +254,7 @@ __global__ void __launch_bounds__(kThr) cqr_cluster_kernel(CqrArgs a) {
       sc = __longlong_as_double((long long)(1023 + k2) << 52);
       isc = __longlong_as_double((long long)(1023 - k2) << 52);
       const double s2 = __longlong_as_double((long long)(1023 - 2 * k2) << 52);
-      tauf = (float)(64.0 * kUnitRoundoff * (mx + sh) * s2);
+      taub = __double_as_longlong(64.0 * kUnitRoundoff * (mx + sh) * s2);
     }
     __syncthreads();
     // every read of this pass's partials is done: on the last pass the
@@ -267,11 +285,6 @@ __global__ void __launch_bounds__(kThr) cqr_cluster_kernel(CqrArgs a) {
         Ti[k * c + j] = Ti[j * c + k] = fma(0.5, ev, id);
       }
       __syncthreads();
-      // binom(-1/2, p) and binom(1/2, p), p = 0..6: dyadic, exact in binary64
-      constexpr double kSeriesA[kPolyMaxTerms + 1] = {1.0, -0.5, 0.375, -0.3125, 0.2734375, -0.24609375,
-                                                      0.2255859375};
-      constexpr double kSeriesB[kPolyMaxTerms + 1] = {1.0, 0.5, -0.125, 0.0625, -0.0390625, 0.02734375,
-                                                      -0.0205078125};
       for (int p = 2; p <= nterm; ++p) {
         const double ca = kSeriesA[p], cb = kSeriesB[p];
         for (int e = t; e < c * c; e += kThr) {
@@ -317,9 +330,8 @@ __global__ void __launch_bounds__(kThr) cqr_cluster_kernel(CqrArgs a) {
           const double v = (A[k * c + j] + (k == j ? sh : 0.0)) * s2;
           A[k * c + j] = v;
           if (e == 0) {
-            const float f = (float)v;
-            const bool z = !(f > tauf);
-            rv[0] = z ? 0.0 : pivot_rcp(v, f);
+            const bool z = !pivot_kept(v, taub);
+            rv[0] = z ? 0.0 : pivot_rcp(v);
             dv[0] = z ? 0.0 : v;
             if (z) bad = 1;
           }
@@ -338,9 +350,8 @@ __global__ void __launch_bounds__(kThr) cqr_cluster_kernel(CqrArgs a) {
           const double l = A[i * c + j];
           const double v = fma(-(l * r), l, A[i * c + i]);
           A[i * c + i] = v;
-          const float f = (float)v;
-          const bool z = !(f > tauf);
-          rv[i] = z ? 0.0 : pivot_rcp(v, z ? 1.0f : f);
+          const bool z = !pivot_kept(v, taub);
+          rv[i] = z ? 0.0 : pivot_rcp(v);
           dv[i] = z ? 0.0 : v;
           if (z) bad = 1;
         } else if (t < kUpd) {
