@@ -86,13 +86,57 @@ t2s2_status d2d(Ctx& cx, double* dst, const double* src, size_t n) {
   T2S2_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, cx.st));
   return T2S2_OK;
 }
-t2s2_status set_scalar(Ctx& cx, double* dst, double v) { return dev_fill(cx, dst, 1, v); }
+t2s2_status set_scalars(Ctx& cx, double* p0, double v0, double* p1, double v1, double* p2, double v2, double* p3,
+                        double v3, double* p4, double v4);
 
 // The next core of the sweep, (Q^T U S V^T) x_1 X1, in one CTA when X1 fits
 // in shared memory: C = Q^T U (one warp per entry, lanes over the rows, fixed
 // shuffle tree), CS = C S V^T, then X1 <- CS x_1 X1 in place (X1 is staged
 // in shared memory first).
 constexpr size_t kNextCoreSmem = 40 * 1024;
+
+// Five interface boundary values (the 1 x 1 interfaces at bond 0 or d) in
+// one launch.
+struct ScalarSet {
+  double* p[5];
+  double v[5];
+};
+__global__ void k_set_scalars(ScalarSet s) {
+  pdl_wait();
+  pdl_trigger();
+  if (threadIdx.x < 5) *s.p[threadIdx.x] = s.v[threadIdx.x];
+}
+
+// B'_k = c_op B_k + shift I for every dimension in one launch.
+struct BprimeArgs {
+  int d;
+  double* out[T2S2_MAX_D];
+  const double* B[T2S2_MAX_D];
+  const double* I[T2S2_MAX_D];
+  int mm[T2S2_MAX_D];  // m_k^2
+  double c_op, shift;
+};
+__global__ void k_bprime(BprimeArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  const int stride = gridDim.x * blockDim.x;
+  for (int k = 0; k < a.d; ++k)
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < a.mm[k]; e += stride)
+      a.out[k][e] = fma(a.shift, a.I[k][e], a.c_op * a.B[k][e]);
+}
+
+t2s2_status set_scalars(Ctx& cx, double* p0, double v0, double* p1, double v1, double* p2, double v2, double* p3,
+                        double v3, double* p4, double v4) {
+  ScalarSet s;
+  s.p[0] = p0, s.p[1] = p1, s.p[2] = p2, s.p[3] = p3, s.p[4] = p4;
+  s.v[0] = v0, s.v[1] = v1, s.v[2] = v2, s.v[3] = v3, s.v[4] = v4;
+  {
+    TraceScope ts_(kTrElem, cx.st, 0.0, 40.0);
+    (void)launch_pdl(k_set_scalars, 1, 32, 0, cx.st, s);
+  }
+  T2S2_CUDA_TRY(cudaGetLastError());
+  return T2S2_OK;
+}
 
 __global__ void k_next_core(const double* Q, const double* U, const double* SV, int rows, int rn, int rk, int rb,
                             double* X1, int mn, int rnn) {
@@ -351,13 +395,28 @@ struct Amen {
     if (mmax > kLocalMaxM) return T2S2_EINVAL;
     R = std::max(std::max(rcap, rfmax), kick);
     const size_t core = (size_t)R * mmax * R;
-    // B'_k = c_op B_k + (c_mass / d) I
-    for (int k = 0; k < d; ++k) {
-      const int m = op->m[k];
-      Bp[k] = aget<double>(c, (size_t)m * m);
-      if (!Bp[k]) return T2S2_ENOMEM;
-      T2S2_TRY(dev_scale_copy(c, Bp[k], op->dB[k], (size_t)m * m, c_op));
-      T2S2_TRY(dev_axpy(c, Bp[k], op->dI[k], (size_t)m * m, c_mass / d));
+    // B'_k = c_op B_k + (c_mass / d) I, every dimension in one launch
+    {
+      BprimeArgs ba;
+      ba.d = d;
+      ba.c_op = c_op;
+      ba.shift = c_mass / d;
+      int mmx = 1;
+      for (int k = 0; k < d; ++k) {
+        const int m = op->m[k];
+        Bp[k] = aget<double>(c, (size_t)m * m);
+        if (!Bp[k]) return T2S2_ENOMEM;
+        ba.out[k] = Bp[k];
+        ba.B[k] = op->dB[k];
+        ba.I[k] = op->dI[k];
+        ba.mm[k] = m * m;
+        mmx = std::max(mmx, m * m);
+      }
+      {
+        TraceScope ts_(kTrElem, c.st, 2.0 * d * mmx, 24.0 * d * mmx);
+        (void)launch_pdl(k_bprime, (unsigned)std::min(64, (mmx + 255) / 256), 256, 0, c.st, ba);
+      }
+      T2S2_CUDA_TRY(cudaGetLastError());
     }
     // transformed right-hand side f = M^{-1} b (mode-k products with Rt_k^{-1})
     // (always FP64: the right-hand side fixes what the inner solve converges to)
@@ -473,11 +532,7 @@ struct Amen {
   // Right interfaces for bonds d-1 .. 1 from right-orthonormal x (and z).
   t2s2_status right_interfaces() {
     Ctx& c = *cx;
-    T2S2_TRY(set_scalar(c, PR[d], 0.0));
-    T2S2_TRY(set_scalar(c, FR[d], 1.0));
-    T2S2_TRY(set_scalar(c, ZIR[d], 1.0));
-    T2S2_TRY(set_scalar(c, ZBR[d], 0.0));
-    T2S2_TRY(set_scalar(c, ZFR[d], 1.0));
+    T2S2_TRY(set_scalars(c, PR[d], 0.0, FR[d], 1.0, ZIR[d], 1.0, ZBR[d], 0.0, ZFR[d], 1.0));
     for (int k = d - 1; k >= 1; --k) {
       const int m = op->m[k];
       const int ra = x.r[k], rb = x.r[k + 1], fa = f.r[k], fb = f.r[k + 1], za = z.r[k], zb = z.r[k + 1];
@@ -508,11 +563,7 @@ struct Amen {
 
   t2s2_status left_boundary() {
     Ctx& c = *cx;
-    T2S2_TRY(set_scalar(c, PL[0], 0.0));
-    T2S2_TRY(set_scalar(c, FL[0], 1.0));
-    T2S2_TRY(set_scalar(c, ZIL[0], 1.0));
-    T2S2_TRY(set_scalar(c, ZBL[0], 0.0));
-    T2S2_TRY(set_scalar(c, ZFL[0], 1.0));
+    T2S2_TRY(set_scalars(c, PL[0], 0.0, FL[0], 1.0, ZIL[0], 1.0, ZBL[0], 0.0, ZFL[0], 1.0));
     return T2S2_OK;
   }
 
