@@ -352,6 +352,9 @@ struct Amen {
   double c_op = 1.0, c_mass = 0.0;
   int gm_restart = 40, gm_maxit = 600;
   bool tstamp_req = false, tstamp_done = false;
+  // first sweep of a solve: a rank-1-right local solve runs the Sylvester
+  // solver alone, without the general solver queued behind it (see local_solve)
+  bool sylv_no_fallback = false;
   int tstamp_target = 0, local_count = 0;
   unsigned long long* tstamp_dev = nullptr;
 
@@ -637,6 +640,16 @@ struct Amen {
         fprintf(stderr, "\n");
         P.tstamp = nullptr;
       }
+      // In the first sweep the general solver (an eigendecomposition launch
+      // and a cooperative GMRES launch that return at once when the Sylvester
+      // solver succeeded) is not queued: when the Sylvester solver stops short
+      // of the local tolerance its iterate (the guess, or its last refinement)
+      // stays in X, the global residual after the sweep decides, and every
+      // later sweep queues the general solver again.
+      if (sylv_no_fallback) {
+        if (stamp_this) tstamp_done = true;
+        return T2S2_OK;
+      }
     }
     T2S2_TRY(local_gmres<double>(P, c.st));
     if (stamp_this) {
@@ -908,6 +921,7 @@ t2s2_status solve_impl(t2s2_op op, Ctx& cx, const DevTT& b, DevTT& xio, double c
   double mark = res;
   int mark_sweep = 0;
   while (res > tol && sweeps < max_sweeps) {
+    am.sylv_no_fallback = sweeps == 0;
     T2S2_TRY(am.sweep());
     ++sweeps;
     am.ph(9);
