@@ -15,6 +15,7 @@
 // the true residual ||b - (c_mass M + c_op A) x|| / ||b|| of the ORIGINAL
 // collocation system is evaluated in FP64 and decides convergence.
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -94,6 +95,142 @@ t2s2_status set_scalars(Ctx& cx, double* p0, double v0, double* p1, double v1, d
 // shuffle tree), CS = C S V^T, then X1 <- CS x_1 X1 in place (X1 is staged
 // in shared memory first).
 constexpr size_t kNextCoreSmem = 40 * 1024;
+
+// The enrichment and z-update residuals of one core, slice by slice.  With
+// Xt = U S V^T the local solution (ra x m x rb) and BX = B' x_2 Xt, every
+// remaining product of
+//   res  = (FL F) x_3 ZFR - (BX + PL x_1 Xt) x_3 ZIR - Xt x_3 ZBR,
+//   zres = (ZFL F) x_3 ZFR - (ZBL x_1 Xt + ZIL x_1 BX) x_3 ZIR - (ZIL x_1 Xt) x_3 ZBR
+// acts on one slice i of the cores, so CTA i computes slice i of res and zres
+// in shared memory, in binary64 with sums in a fixed order: one launch instead
+// of four grouped ones.  When the whole of Xt fits shared memory (the first
+// sweep, rb = 1), every CTA also forms its slice of BX from row i of B';
+// otherwise BX comes from a product launched before.
+struct EnrichArgs {
+  int ra, rb, fa, fb, za, zb, m;
+  const double *Xt, *BX, *T1, *F, *Bp;            // cores (a, i, b) row-major; B' m x m
+  const double *PL, *ZBL, *ZIL, *ZFL;             // left interfaces: (rows) x (ra | fa)
+  const double *ZFR, *ZIR, *ZBR;                  // right interfaces: zb x (fb | rb)
+  double *res, *zres;                             // ra x m x zb, za x m x zb
+  int bx_here;                                    // 1: BX from Xt and B' in this kernel
+};
+
+constexpr int kEnrichThreads = 256;
+constexpr size_t kEnrichMaxSmem = 96 * 1024;
+
+__host__ __device__ inline size_t enrich_smem_doubles(const EnrichArgs& a) {
+  const size_t ra = a.ra, rb = a.rb, fa = a.fa, fb = a.fb, za = a.za, zb = a.zb;
+  size_t n = 3 * ra * rb + ra * fb + fa * fb + ra * ra + 2 * za * ra + za * fa + zb * fb + 2 * zb * rb +
+             2 * za * rb + za * fb;
+  if (a.bx_here) n += ra * (size_t)a.m * rb + a.m;
+  return n;
+}
+
+__global__ void __launch_bounds__(kEnrichThreads) k_enrich(EnrichArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ double es[];
+  const int i = blockIdx.x, t = threadIdx.x, m = a.m;
+  const int ra = a.ra, rb = a.rb, fa = a.fa, fb = a.fb, za = a.za, zb = a.zb;
+  double* xs = es;               // ra x rb: Xt[:, i, :]
+  double* bs = xs + ra * rb;     // ra x rb: BX[:, i, :]
+  double* y1 = bs + ra * rb;     // ra x rb
+  double* ts = y1 + ra * rb;     // ra x fb: T1[:, i, :]
+  double* fs = ts + ra * fb;     // fa x fb: F[:, i, :]
+  double* pl = fs + fa * fb;     // ra x ra
+  double* zbl = pl + ra * ra;    // za x ra
+  double* zil = zbl + za * ra;   // za x ra
+  double* zfl = zil + za * ra;   // za x fa
+  double* zfr = zfl + za * fa;   // zb x fb
+  double* zir = zfr + zb * fb;   // zb x rb
+  double* zbr = zir + zb * rb;   // zb x rb
+  double* t2 = zbr + zb * rb;    // za x rb
+  double* t2b = t2 + za * rb;    // za x rb
+  double* tz = t2b + za * rb;    // za x fb
+  double* xall = tz + za * fb;   // bx_here: ra x m x rb, then row i of B'
+  double* brow = xall + (a.bx_here ? ra * m * rb : 0);
+  for (int e = t; e < ra * rb; e += kEnrichThreads) {
+    const int p = e / rb, q = e % rb;
+    xs[e] = a.Xt[((long)p * m + i) * rb + q];
+    if (!a.bx_here) bs[e] = a.BX[((long)p * m + i) * rb + q];
+  }
+  for (int e = t; e < ra * fb; e += kEnrichThreads) ts[e] = a.T1[((long)(e / fb) * m + i) * fb + e % fb];
+  for (int e = t; e < fa * fb; e += kEnrichThreads) fs[e] = a.F[((long)(e / fb) * m + i) * fb + e % fb];
+  for (int e = t; e < ra * ra; e += kEnrichThreads) pl[e] = a.PL[e];
+  for (int e = t; e < za * ra; e += kEnrichThreads) {
+    zbl[e] = a.ZBL[e];
+    zil[e] = a.ZIL[e];
+  }
+  for (int e = t; e < za * fa; e += kEnrichThreads) zfl[e] = a.ZFL[e];
+  for (int e = t; e < zb * fb; e += kEnrichThreads) zfr[e] = a.ZFR[e];
+  for (int e = t; e < zb * rb; e += kEnrichThreads) {
+    zir[e] = a.ZIR[e];
+    zbr[e] = a.ZBR[e];
+  }
+  if (a.bx_here) {
+    for (int e = t; e < ra * m * rb; e += kEnrichThreads) xall[e] = a.Xt[e];
+    for (int j = t; j < m; j += kEnrichThreads) brow[j] = a.Bp[(long)i * m + j];
+  }
+  __syncthreads();
+  if (a.bx_here) {
+    // BX[:, i, :] = sum_j B'[i, j] Xt[:, j, :]
+    for (int e = t; e < ra * rb; e += kEnrichThreads) {
+      const int p = e / rb, q = e % rb;
+      double s0 = 0.0, s1 = 0.0;
+      int j = 0;
+      for (; j + 1 < m; j += 2) {
+        s0 = fma(brow[j], xall[((long)p * m + j) * rb + q], s0);
+        s1 = fma(brow[j + 1], xall[((long)p * m + j + 1) * rb + q], s1);
+      }
+      if (j < m) s0 = fma(brow[j], xall[((long)p * m + j) * rb + q], s0);
+      bs[e] = s0 + s1;
+    }
+    __syncthreads();
+  }
+  // Y1 = BX + PL Xt,  T2 = ZBL Xt + ZIL BX,  T2b = ZIL Xt,  Tz = ZFL F (slice i)
+  for (int e = t; e < ra * rb; e += kEnrichThreads) {
+    const int p = e / rb, q = e % rb;
+    double s = bs[e];
+    for (int c = 0; c < ra; ++c) s = fma(pl[p * ra + c], xs[c * rb + q], s);
+    y1[e] = s;
+  }
+  for (int e = t; e < za * rb; e += kEnrichThreads) {
+    const int p = e / rb, q = e % rb;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int c = 0; c < ra; ++c) {
+      s0 = fma(zbl[p * ra + c], xs[c * rb + q], s0);
+      s1 = fma(zil[p * ra + c], bs[c * rb + q], s1);
+      s2 = fma(zil[p * ra + c], xs[c * rb + q], s2);
+    }
+    t2[e] = s0 + s1;
+    t2b[e] = s2;
+  }
+  for (int e = t; e < za * fb; e += kEnrichThreads) {
+    const int p = e / fb, q = e % fb;
+    double s = 0.0;
+    for (int c = 0; c < fa; ++c) s = fma(zfl[p * fa + c], fs[c * fb + q], s);
+    tz[e] = s;
+  }
+  __syncthreads();
+  // res[:, i, :] = T1 ZFR^T - Y1 ZIR^T - Xt ZBR^T;  zres[:, i, :] = Tz ZFR^T - T2 ZIR^T - T2b ZBR^T
+  for (int e = t; e < (ra + za) * zb; e += kEnrichThreads) {
+    const int row = e / zb, q = e % zb;
+    const bool top = row < ra;
+    const int p = top ? row : row - ra;
+    const double* u = top ? ts + p * fb : tz + p * fb;
+    const double* v = top ? y1 + p * rb : t2 + p * rb;
+    const double* w = top ? xs + p * rb : t2b + p * rb;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int c = 0; c < fb; ++c) s0 = fma(u[c], zfr[q * fb + c], s0);
+    for (int c = 0; c < rb; ++c) {
+      s1 = fma(v[c], zir[q * rb + c], s1);
+      s2 = fma(w[c], zbr[q * rb + c], s2);
+    }
+    const double r = s0 - s1 - s2;
+    if (top) a.res[((long)p * m + i) * zb + q] = r;
+    else a.zres[((long)p * m + i) * zb + q] = r;
+  }
+}
 
 // Five interface boundary values (the 1 x 1 interfaces at bond 0 or d) in
 // one launch.
@@ -782,11 +919,45 @@ struct Amen {
       //   res  = (FL F) x_3 ZFR - (B' Xt + PL Xt) x_3 ZIR - Xt x_3 ZBR,
       // --- z update: residual on (z-left) x m x (z-right),
       //   zres = (ZFL F) x_3 ZFR - (ZBL Xt + ZIL B' Xt) x_3 ZIR - (ZIL Xt) x_3 ZBR;
-      // four launches of independent products.  tmp[0] still holds FL[k] x_1 F
-      // from the local right-hand side.
+      // one launch slice by slice (k_enrich) where the cores fit shared
+      // memory, else four launches of independent products.  tmp[0] still
+      // holds FL[k] x_1 F from the local right-hand side.
       double *Tz = tmp[2], *T2b = tmp[3];  // T1 = tmp[0], T2 = tmp[1]
       double *BX = tmp[5], *Y1 = tmp[6], *res = tmp[7], *zres = tmp[8];
-      {
+      bool fused = false;
+      if (c.contract_prec != T2S2_BF16_REFINE && c.contract_prec != T2S2_TF32_REFINE) {
+        EnrichArgs ea;
+        ea.ra = ra, ea.rb = rb, ea.fa = fa, ea.fb = fb, ea.za = za, ea.zb = zb, ea.m = m;
+        ea.Xt = Xt, ea.BX = BX, ea.T1 = T1, ea.F = F, ea.Bp = Bp[k];
+        ea.PL = PL[k], ea.ZBL = ZBL[k], ea.ZIL = ZIL[k], ea.ZFL = ZFL[k];
+        ea.ZFR = ZFR[k + 1], ea.ZIR = ZIR[k + 1], ea.ZBR = ZBR[k + 1];
+        ea.res = res, ea.zres = zres;
+        ea.bx_here = 1;
+        size_t sm = enrich_smem_doubles(ea) * sizeof(double);
+        if (sm > kEnrichMaxSmem) {
+          ea.bx_here = 0;
+          sm = enrich_smem_doubles(ea) * sizeof(double);
+        }
+        if (sm <= kEnrichMaxSmem) {
+          static std::once_flag attr;
+          std::call_once(attr, [] {
+            if (cudaFuncSetAttribute(k_enrich, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEnrichMaxSmem) !=
+                cudaSuccess)
+              cudaGetLastError();
+          });
+          if (!ea.bx_here) T2S2_TRY(contract_gemm(c, g_mode2(Bp[k], m, Xt, ra, rb, BX)));
+          {
+            const double fl = 2.0 * m * ((double)ra * rb * (ra + 2.0 * za) + (double)za * fa * fb +
+                                         (double)(ra + za) * zb * (fb + 2.0 * rb)) +
+                              (ea.bx_here ? 2.0 * ra * m * (double)m * rb : 0.0);
+            TraceScope ts_(kTrGemm, c.st, fl, 8.0 * m * ((double)ra * rb + ra * fb + fa * fb + (ra + za) * zb));
+            (void)launch_pdl(k_enrich, (unsigned)m, kEnrichThreads, sm, c.st, ea);
+          }
+          T2S2_CUDA_TRY(cudaGetLastError());
+          fused = true;
+        }
+      }
+      if (!fused) {
         const Gemm<double> s1[] = {g_mode2(Bp[k], m, Xt, ra, rb, BX),
                                    g_mode2(Bp[k], m, Xt, ra, rb, Y1),
                                    g_mode1(ZFL[k], za, fa, F, m, fb, Tz),
