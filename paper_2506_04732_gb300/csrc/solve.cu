@@ -232,6 +232,56 @@ __global__ void __launch_bounds__(kEnrichThreads) k_enrich(EnrichArgs a) {
   }
 }
 
+// The local right-hand side of core k, slice by slice: T1 = FL x_1 F (kept
+// for the enrichment) and rhs = T1 x_3 FR, CTA i forming slice i of both in
+// shared memory (binary64, fixed-order sums): one launch instead of two.
+struct RhsArgs {
+  int ra, rb, fa, fb, m;
+  const double *FL, *F, *FR;  // ra x fa, fa x m x fb, rb x fb
+  double *T1, *rhs;           // ra x m x fb, ra x m x rb
+};
+
+__global__ void __launch_bounds__(kEnrichThreads) k_local_rhs(RhsArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ double rs[];
+  const int i = blockIdx.x, t = threadIdx.x, m = a.m;
+  const int ra = a.ra, rb = a.rb, fa = a.fa, fb = a.fb;
+  double* fl = rs;             // ra x fa
+  double* fs = fl + ra * fa;   // fa x fb
+  double* fr = fs + fa * fb;   // rb x fb
+  double* t1 = fr + rb * fb;   // ra x fb
+  for (int e = t; e < ra * fa; e += kEnrichThreads) fl[e] = a.FL[e];
+  for (int e = t; e < fa * fb; e += kEnrichThreads) fs[e] = a.F[((long)(e / fb) * m + i) * fb + e % fb];
+  for (int e = t; e < rb * fb; e += kEnrichThreads) fr[e] = a.FR[e];
+  __syncthreads();
+  for (int e = t; e < ra * fb; e += kEnrichThreads) {
+    const int p = e / fb, q = e % fb;
+    double s0 = 0.0, s1 = 0.0;
+    int c = 0;
+    for (; c + 1 < fa; c += 2) {
+      s0 = fma(fl[p * fa + c], fs[c * fb + q], s0);
+      s1 = fma(fl[p * fa + c + 1], fs[(c + 1) * fb + q], s1);
+    }
+    if (c < fa) s0 = fma(fl[p * fa + c], fs[c * fb + q], s0);
+    const double v = s0 + s1;
+    t1[e] = v;
+    a.T1[((long)p * m + i) * fb + q] = v;
+  }
+  __syncthreads();
+  for (int e = t; e < ra * rb; e += kEnrichThreads) {
+    const int p = e / rb, q = e % rb;
+    double s0 = 0.0, s1 = 0.0;
+    int c = 0;
+    for (; c + 1 < fb; c += 2) {
+      s0 = fma(t1[p * fb + c], fr[q * fb + c], s0);
+      s1 = fma(t1[p * fb + c + 1], fr[q * fb + c + 1], s1);
+    }
+    if (c < fb) s0 = fma(t1[p * fb + c], fr[q * fb + c], s0);
+    a.rhs[((long)p * m + i) * rb + q] = s0 + s1;
+  }
+}
+
 // Five interface boundary values (the 1 x 1 interfaces at bond 0 or d) in
 // one launch.
 struct ScalarSet {
@@ -855,9 +905,31 @@ struct Amen {
       const int ra = x.r[k], rb = x.r[k + 1], fa = f.r[k], fb = f.r[k + 1], za = z.r[k], zb = z.r[k + 1];
       const double* F = f.c[k];
       double *rhs = tmp[3], *X = tmp[4], *T1 = tmp[0], *T2 = tmp[1];
-      // local rhs = FL[k] x_1 F x_3 FR[k+1]
-      T2S2_TRY(mode1(c, FL[k], ra, fa, F, m, fb, T1));
-      T2S2_TRY(mode3(c, T1, ra, m, fb, FR[k + 1], rb, rhs));
+      // local rhs = FL[k] x_1 F x_3 FR[k+1] (one launch slice by slice where
+      // the matrices fit shared memory)
+      {
+        const size_t sm = sizeof(double) * ((size_t)ra * fa + (size_t)fa * fb + (size_t)rb * fb + (size_t)ra * fb);
+        if (c.contract_prec != T2S2_BF16_REFINE && c.contract_prec != T2S2_TF32_REFINE && sm <= kEnrichMaxSmem) {
+          static std::once_flag attr;
+          std::call_once(attr, [] {
+            if (cudaFuncSetAttribute(k_local_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEnrichMaxSmem) !=
+                cudaSuccess)
+              cudaGetLastError();
+          });
+          RhsArgs ar;
+          ar.ra = ra, ar.rb = rb, ar.fa = fa, ar.fb = fb, ar.m = m;
+          ar.FL = FL[k], ar.F = F, ar.FR = FR[k + 1], ar.T1 = T1, ar.rhs = rhs;
+          {
+            TraceScope ts_(kTrGemm, c.st, 2.0 * m * (double)ra * fb * (fa + rb),
+                           8.0 * m * ((double)fa * fb + ra * fb + ra * rb));
+            (void)launch_pdl(k_local_rhs, (unsigned)m, kEnrichThreads, sm, c.st, ar);
+          }
+          T2S2_CUDA_TRY(cudaGetLastError());
+        } else {
+          T2S2_TRY(mode1(c, FL[k], ra, fa, F, m, fb, T1));
+          T2S2_TRY(mode3(c, T1, ra, m, fb, FR[k + 1], rb, rhs));
+        }
+      }
       T2S2_TRY(d2d(c, X, x.c[k], (size_t)ra * m * rb));
       ph(3);
       T2S2_TRY(local_solve(k, rhs, X));
