@@ -1,4 +1,4 @@
-// Shifted CholeskyQR (up to three passes) in ONE cooperative launch.
+// Shifted CholeskyQR (up to four passes) in ONE cooperative launch.
 //
 // The orthogonalisations of the TT sweeps (Methods: QR of the unfoldings
 // before every truncation) factor tall-skinny blocks of nlong vectors of
@@ -76,7 +76,7 @@ struct CholQrArgs {
   unsigned long long* tstamp;  // diagnostics: phase times of CTA 0 (null: off)
 };
 
-constexpr int kQrStamps = 2 + 6 * 3 + 1;
+constexpr int kQrStamps = 2 + 6 * kCqrMaxPass + 1;
 
 #define QR_STAMP(k)                                                                   \
   do {                                                                                \
@@ -196,10 +196,10 @@ __global__ void __launch_bounds__(kThreads) cholqr3_kernel(CholQrArgs a) {
     if (t == 0) {
       unsigned M = 0, D = 0;
       for (int w = 0; w < kThreads / 32; ++w) M = max(M, ired[0][w]), D = max(D, ired[1][w]);
-      const bool fin = (__uint_as_float(D) * c <= kOrthDev) || c == 1 || pass == 2;
+      const bool fin = (__uint_as_float(D) * c <= kOrthDev) || c == 1 || pass == kCqrMaxPass - 1;
       const double mx = __hiloint2double((int)M, 0);
       // shift of the first pass, with c * (largest diagonal) >= trace
-      const double sh = (pass == 0 && !fin) ? a.shift_rel * c * mx : 0.0;
+      const double sh = (pass < kCqrShiftedPasses && !fin) ? a.shift_rel * c * mx : 0.0;
       shift = sh;
       last = fin;
       // exact power-of-4 scaling: the largest diagonal lands in [1, 4)
@@ -416,7 +416,7 @@ t2s2_status cholqr3_fused(const double* W, double* Q, double* R, int nlong, int 
     fprintf(stderr, "[t2s2] cholqr3 phase times (ns) nlong=%d c=%d grid=%d: load %lld", nlong, c, grid,
             (long long)(h[1] - h[0]));
     unsigned long long prev = h[1];
-    for (int p = 0; p < 3 && h[2 + 6 * p]; ++p) {
+    for (int p = 0; p < kCqrMaxPass && h[2 + 6 * p]; ++p) {
       fprintf(stderr, " | pass %d:", p);
       for (int k = 0; k < 6; ++k) {
         fprintf(stderr, " %lld", (long long)(h[2 + 6 * p + k] - prev));

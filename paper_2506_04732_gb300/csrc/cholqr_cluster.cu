@@ -1,4 +1,4 @@
-// Shifted CholeskyQR (up to three passes) in ONE thread-block cluster.
+// Shifted CholeskyQR (up to four passes) in ONE thread-block cluster.
 //
 // The same factorisation as cholqr.cu (shifted CholeskyQR3 of Fukaya et al.,
 // L D L^T form with L^{-1} built in the same elimination steps, the
@@ -60,7 +60,7 @@ constexpr double kUnitRoundoff = 1.1102230246251565e-16;  // 2^-53
 constexpr long kWorkPerCta = 2048;
 // blocks above this many Gram products go to the full-grid kernel
 constexpr long kMaxWork = 16L * 16384;
-constexpr int kStamps = 2 + 6 * 3 + 1;
+constexpr int kStamps = 2 + 6 * kCqrMaxPass + 1;
 // the last pass takes the binomial series of (I + E)^(-1/2) instead of a
 // Cholesky factorisation when its Gram is this close to I (spectral bound)
 constexpr float kPolyDev = 1e-3f;
@@ -232,9 +232,9 @@ __global__ void __launch_bounds__(kThr) cqr_cluster_kernel(CqrArgs a) {
     if (t == 0) {
       unsigned M = 0, D = 0;
       for (int w = 0; w < kThr / 32; ++w) M = max(M, ired[0][w]), D = max(D, ired[1][w]);
-      const bool fin = (__uint_as_float(D) * c <= kOrthDev) || c == 1 || pass == 2;
+      const bool fin = (__uint_as_float(D) * c <= kOrthDev) || c == 1 || pass == kCqrMaxPass - 1;
       const double mx = __hiloint2double((int)M, 0);
-      const double sh = (pass == 0 && !fin) ? a.shift_rel * c * mx : 0.0;
+      const double sh = (pass < kCqrShiftedPasses && !fin) ? a.shift_rel * c * mx : 0.0;
       shift = sh;
       last = fin;
       // terms of the series: the first K with dev^(K+1) <= 2^-56
@@ -558,7 +558,7 @@ t2s2_status cqr_cluster(const double* W, double* Q, double* R, int nlong, int c,
     fprintf(stderr, "[t2s2] cluster cholqr phase times (ns) nlong=%d c=%d cluster=%d: load %lld", nlong, c, cl,
             (long long)(h[1] - h[0]));
     unsigned long long prev = h[1];
-    for (int p = 0; p < 3 && h[2 + 6 * p]; ++p) {
+    for (int p = 0; p < kCqrMaxPass && h[2 + 6 * p]; ++p) {
       fprintf(stderr, " | pass %d:", p);
       for (int k = 0; k < 5; ++k) {
         fprintf(stderr, " %lld", (long long)(h[2 + 6 * p + k] - prev));

@@ -6,6 +6,19 @@ namespace t2s2 {
 
 constexpr int kSmallMax = 96;
 
+// Passes of the shifted CholeskyQR (cholqr.cu, cholqr_cluster.cu and the
+// chol_inv fallback): the first two passes that are not the last take the
+// shift 11 (n c + c (c + 1)) u max(diag G); the rest are plain.  One shifted
+// pass maps a direction of W with singular value sigma to ~sigma / sqrt(s) in
+// Q; when that is near the roundoff of the next Gram (sigma below ~1e-12 of
+// the largest), a plain second pass would zero its pivot in column order and
+// lose the whole remainder of that column of W, not just sigma.  A second
+// shift lifts such directions above roundoff first; a pass whose Gram is
+// within 0.5 / c of the identity is the last, so well-conditioned blocks still
+// take two passes.
+constexpr int kCqrMaxPass = 4;
+constexpr int kCqrShiftedPasses = 2;
+
 // L L^T = G + shift_rel * trace(G) * I and Linv = L^{-1}; status[0] = 1 if a
 // pivot was not positive (then replaced by a tiny value).
 t2s2_status chol_inv(const double* G, int c, double shift_rel, double* L, double* Linv, int* status,
@@ -16,8 +29,8 @@ t2s2_status jacobi_svd(const double* A, int p, int q, double* U, double* s, doub
                        cudaStream_t st);
 
 // Shifted CholeskyQR of nlong vectors of length c in one cooperative launch
-// (cholqr.cu): up to three passes, fewer when a pass's Gram certifies that
-// the next one finishes.  tall: W is nlong x c row-major, W = Q R (R = c x c upper);
+// (cholqr.cu): up to kCqrMaxPass passes, fewer when a pass's Gram certifies
+// that the next one finishes.  tall: W is nlong x c row-major, W = Q R (R = c x c upper);
 // wide: W is c x nlong row-major, W = R Q (R lower).  Plan first: false if
 // the grid cannot be co-resident or shared memory would not fit; max_grid > 0
 // caps the number of CTAs.

@@ -230,10 +230,10 @@ t2s2_status qr_tall(Ctx& cx, const double* W, int rows, int cols, double* Q, dou
   if (!G || !L || !Li || !Lacc || !Ltmp || !T0 || !T1) return T2S2_ENOMEM;
   const double shift = 11.0 * ((double)rows * c + (double)c * (c + 1)) * kUnit;
   const double* cur = W;
-  double* outs[3] = {T0, T1, Q};
-  for (int pass = 0; pass < 3; ++pass) {
+  double* outs[kCqrMaxPass] = {T0, T1, T0, Q};
+  for (int pass = 0; pass < kCqrMaxPass; ++pass) {
     T2S2_TRY(gemm_ex<double>(cx, c, c, rows, true, false, 1.0, cur, c, cur, c, 0.0, G, c));
-    T2S2_TRY(chol_inv(G, c, pass == 0 ? shift : 0.0, L, Li, cx.dstat, cx.st));
+    T2S2_TRY(chol_inv(G, c, pass < kCqrShiftedPasses ? shift : 0.0, L, Li, cx.dstat, cx.st));
     // cur = next * L^T  =>  next = cur * L^{-T}
     T2S2_TRY(gemm_ex<double>(cx, rows, c, c, false, true, 1.0, cur, c, Li, c, 0.0, outs[pass], c));
     if (pass == 0) {
@@ -285,11 +285,11 @@ t2s2_status lq_wide(Ctx& cx, const double* W, int rows, int cols, double* Q, dou
   if (!G || !L || !Li || !Lacc || !Ltmp || !T0 || !T1) return T2S2_ENOMEM;
   const double shift = 11.0 * ((double)rows * cols + (double)c * (c + 1)) * kUnit;
   const double* cur = W;
-  double* outs[3] = {T0, T1, Q};
-  for (int pass = 0; pass < 3; ++pass) {
+  double* outs[kCqrMaxPass] = {T0, T1, T0, Q};
+  for (int pass = 0; pass < kCqrMaxPass; ++pass) {
     // G = cur cur^T
     T2S2_TRY(gemm_ex<double>(cx, c, c, cols, false, true, 1.0, cur, cols, cur, cols, 0.0, G, c));
-    T2S2_TRY(chol_inv(G, c, pass == 0 ? shift : 0.0, L, Li, cx.dstat, cx.st));
+    T2S2_TRY(chol_inv(G, c, pass < kCqrShiftedPasses ? shift : 0.0, L, Li, cx.dstat, cx.st));
     // cur = L next  =>  next = L^{-1} cur
     T2S2_TRY(gemm_ex<double>(cx, c, cols, c, false, false, 1.0, Li, c, cur, cols, 0.0, outs[pass], cols));
     if (pass == 0) {

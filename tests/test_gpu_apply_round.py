@@ -137,6 +137,38 @@ def test_round_exact_low_rank(T):
     assert OT.diff_norm(tx.cores(), OT.scale(x, 1.5)) <= 1e-13 * OT.norm(x)
 
 
+def _cancelling_train(d, m, r, seed, scale=1e3):
+    """t1 - t1 + 1e-12 t2 + t3 as one train of rank 4r (an exactly cancelling
+    pair and a part at 1e-12 ahead of the dominant part, the structure of
+    b - A x near convergence), with the norm moved from the first core to the
+    last."""
+    t1 = W.random_tt(d, m, [1] + [r] * (d - 1) + [1], seed=seed)
+    t2 = W.random_tt(d, m, [1] + [r] * (d - 1) + [1], seed=seed + 1)
+    t3 = W.random_tt(d, m, [1] + [r] * (d - 1) + [1], seed=seed + 2)
+    x = OT.add(OT.add(OT.add(t1, OT.scale(t1, -1.0)), OT.scale(t2, 1e-12)), t3)
+    x[0] = x[0] / scale
+    x[-1] = x[-1] * scale
+    return x, t3
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_round_keeps_a_train_with_a_cancelling_pair(T, seed):
+    # Methods, TT rounding: the orthogonalisation must represent the train to
+    # working precision however rank-deficient its unfoldings are; a plain
+    # second CholeskyQR pass that zeroed small pivots in column order lost
+    # ~1e-12 of such a train (up to 1e-6 on solver right-hand sides)
+    p = W.config1(d=6, n=32)
+    op, _ = _op(T, p)
+    x, t3 = _cancelling_train(6, 30, 8, seed)
+    tx = T.TT.from_cores(x)
+    T.t2s2_round(op, tx, 0.0)
+    assert OT.diff_norm(tx.cores(), x) <= 1e-13 * OT.norm(x)
+    tx = T.TT.from_cores(x)
+    T.t2s2_round(op, tx, 1e-10)
+    assert max(tx.r) <= 8
+    assert OT.diff_norm(tx.cores(), t3) <= 1e-10 * OT.norm(t3)
+
+
 def test_norm_and_residual(T):
     p = W.config1(d=4, n=18)
     op, ops = _op(T, p)
