@@ -17,7 +17,8 @@ namespace t2s2 {
 namespace {
 
 constexpr int kThreads = 512;
-constexpr size_t kJacobiMaxSmem = 200 * 1024;
+constexpr size_t kJacobiSepSmem = 200 * 1024;  // pre-rotation with separate product buffers
+constexpr size_t kJacobiMaxSmem = 224 * 1024;  // pre-rotation with in-place products
 
 // G (c x c, row-major, ld c) -> L lower (G + shift I = L L^T), Linv = L^{-1}.
 __global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __restrict__ G, int c,
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
   double* Vs = sm + rows * cols;         // cols x cols, column-major
   double* nrm = Vs + cols * cols;        // cols
   __shared__ int rotated;
+  __shared__ unsigned top32;
   __shared__ int order[kSmallMax];
   const int t = threadIdx.x;
   for (int e = t; e < rows * cols; e += blockDim.x) {
@@ -150,15 +152,31 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
   // singular values keep full binary64 relative accuracy: they come from
   // binary64 column norms after the binary64 rotations.
   if (prerotate) {
+    // prerotate 1: separate binary64 buffers for V^T V, the Newton-Schulz
+    // iterate and W V; prerotate 2 (blocks too large for those): V^T V over
+    // the binary32 copies (cols^2 doubles <= (rows + cols) cols floats) and
+    // both products row by row in place -- a warp reads a row of V (or W)
+    // whole before it writes it, and no other warp touches that row
+    const bool inplace = prerotate == 2;
     float* Wf = reinterpret_cast<float*>(nrm + cols);
     float* Vf = Wf + rows * cols;
     // keep Wt 8-byte aligned: pad the float arrays to an even count
-    double* Wt = reinterpret_cast<double*>(Vf + cols * cols + ((rows * cols + cols * cols) & 1));
+    double* Wt = inplace ? reinterpret_cast<double*>(Wf)
+                         : reinterpret_cast<double*>(Vf + cols * cols + ((rows * cols + cols * cols) & 1));
     for (int e = t; e < rows * cols; e += blockDim.x) Wf[e] = (float)W[e];
     for (int e = t; e < cols * cols; e += blockDim.x) Vf[e] = (e % cols == e / cols) ? 1.f : 0.f;
     const float negl32 = (float)(1e-14 * fro2);
+    // the sweeps stop when no rotation exceeds |gamma| = 1e-6 sqrt(alpha beta);
+    // for the large blocks also when the largest one is below ~3e-5 and no
+    // longer shrinks tenfold a sweep: binary32 dot products of long columns
+    // carry ~1e-7 relative noise per term, so the last rotations can stall
+    // at the noise, and the binary64 sweeps below converge from there
+    float prev_top = 1.f;
     for (int sw = 0; sw < 30; ++sw) {
-      if (t == 0) rotated = 0;
+      if (t == 0) {
+        rotated = 0;
+        top32 = 0u;
+      }
       __syncthreads();
       for (int round = 0; round < ncol - 1; ++round) {
         for (int pr = warp; pr < npair; pr += nwarps) {
@@ -195,18 +213,23 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
               va[i] = cs * x - sn * y;
               vb[i] = sn * x + cs * y;
             }
-            if (lane == 0) rotated = 1;
+            if (lane == 0) {
+              rotated = 1;
+              // non-negative binary32 values order like their bit patterns
+              if (inplace) atomicMax(&top32, __float_as_uint(gamma * gamma / (alpha * beta)));
+            }
           }
         }
         __syncthreads();
       }
-      if (!rotated) break;
+      const float top = __uint_as_float(top32);
+      if (!rotated || (inplace && top < 1e-9f && top > 0.01f * prev_top)) break;
+      prev_top = top;
       __syncthreads();
     }
     // V32 is orthogonal only to ~1e-7: make it orthogonal in binary64 with
     // two Newton-Schulz steps V <- V (3 I - V^T V) / 2 (quadratic: 1e-7 ->
     // 1e-14 -> roundoff), so that W0 = W V^T stays exact for the caller
-    double* V2 = Wt + rows * cols;  // cols x cols
     for (int e = t; e < cols * cols; e += blockDim.x) Vs[e] = (double)Vf[e];
     __syncthreads();
     for (int it = 0; it < 2; ++it) {
@@ -217,26 +240,71 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
         Wt[e] = acc;
       }
       __syncthreads();
-      for (int e = t; e < cols * cols; e += blockDim.x) {  // V2 <- V (3 I - V^T V) / 2
-        const int k = e % cols, j = e / cols;
-        double acc = 0.0;
-        for (int i = 0; i < cols; ++i) acc = fma(Vs[i * cols + k], ((i == j) ? 3.0 : 0.0) - Wt[j * cols + i], acc);
-        V2[e] = 0.5 * acc;
+      if (inplace) {
+        for (int r = warp; r < cols; r += nwarps) {  // row r of V <- 1.5 V_r - 0.5 V_r Wt
+          double o[kSmallMax / 32];
+#pragma unroll
+          for (int u = 0; u < kSmallMax / 32; ++u) {
+            const int j = lane + 32 * u;
+            if (j < cols) {
+              double acc = 0.0;
+              for (int c = 0; c < cols; ++c) acc = fma(Vs[c * cols + r], Wt[j * cols + c], acc);
+              o[u] = fma(1.5, Vs[j * cols + r], -0.5 * acc);
+            }
+          }
+          __syncwarp();
+#pragma unroll
+          for (int u = 0; u < kSmallMax / 32; ++u) {
+            const int j = lane + 32 * u;
+            if (j < cols) Vs[j * cols + r] = o[u];
+          }
+        }
+        __syncthreads();
+      } else {
+        double* V2 = Wt + rows * cols;  // cols x cols
+        for (int e = t; e < cols * cols; e += blockDim.x) {  // V2 <- V (3 I - V^T V) / 2
+          const int k = e % cols, j = e / cols;
+          double acc = 0.0;
+          for (int i = 0; i < cols; ++i) acc = fma(Vs[i * cols + k], ((i == j) ? 3.0 : 0.0) - Wt[j * cols + i], acc);
+          V2[e] = 0.5 * acc;
+        }
+        __syncthreads();
+        for (int e = t; e < cols * cols; e += blockDim.x) Vs[e] = V2[e];
+        __syncthreads();
       }
-      __syncthreads();
-      for (int e = t; e < cols * cols; e += blockDim.x) Vs[e] = V2[e];
-      __syncthreads();
     }
     // W <- W V, in binary64
-    for (int e = t; e < rows * cols; e += blockDim.x) {
-      const int i = e % rows, j = e / rows;
-      double acc = 0.0;
-      for (int k = 0; k < cols; ++k) acc = fma(W[k * rows + i], Vs[j * cols + k], acc);
-      Wt[e] = acc;
+    if (inplace) {
+      for (int r = warp; r < rows; r += nwarps) {
+        double o[kSmallMax / 32];
+#pragma unroll
+        for (int u = 0; u < kSmallMax / 32; ++u) {
+          const int j = lane + 32 * u;
+          if (j < cols) {
+            double acc = 0.0;
+            for (int k = 0; k < cols; ++k) acc = fma(W[k * rows + r], Vs[j * cols + k], acc);
+            o[u] = acc;
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kSmallMax / 32; ++u) {
+          const int j = lane + 32 * u;
+          if (j < cols) W[j * rows + r] = o[u];
+        }
+      }
+      __syncthreads();
+    } else {
+      for (int e = t; e < rows * cols; e += blockDim.x) {
+        const int i = e % rows, j = e / rows;
+        double acc = 0.0;
+        for (int k = 0; k < cols; ++k) acc = fma(W[k * rows + i], Vs[j * cols + k], acc);
+        Wt[e] = acc;
+      }
+      __syncthreads();
+      for (int e = t; e < rows * cols; e += blockDim.x) W[e] = Wt[e];
+      __syncthreads();
     }
-    __syncthreads();
-    for (int e = t; e < rows * cols; e += blockDim.x) W[e] = Wt[e];
-    __syncthreads();
   }
   int sweep = 0;
   for (sweep = 0; sweep < 60; ++sweep) {
@@ -378,11 +446,19 @@ t2s2_status jacobi_svd(const double* A, int p, int q, double* U, double* s, doub
   int transpose = p < q;
   int rows = transpose ? q : p, cols = transpose ? p : q;
   size_t smem = ((size_t)rows * cols + (size_t)cols * cols + cols) * sizeof(double);
-  // binary32 pre-rotation when its copies and the product buffer fit
-  const size_t extra = ((size_t)rows * cols + (size_t)cols * cols + 1) * sizeof(float) +
-                       ((size_t)rows * cols + (size_t)cols * cols) * sizeof(double) + 16;
-  const int prerotate = (smem + extra <= kJacobiMaxSmem) ? 1 : 0;
-  if (prerotate) smem += extra;
+  // binary32 pre-rotation: with separate product buffers when they fit in
+  // kJacobiSepSmem, else with the products in place when the binary32
+  // copies fit in kJacobiMaxSmem
+  const size_t copies = ((size_t)rows * cols + (size_t)cols * cols + 1) * sizeof(float) + 16;
+  const size_t buffers = ((size_t)rows * cols + (size_t)cols * cols) * sizeof(double);
+  int prerotate = 0;
+  if (smem + copies + buffers <= kJacobiSepSmem) {
+    prerotate = 1;
+    smem += copies + buffers;
+  } else if (smem + copies <= kJacobiMaxSmem) {
+    prerotate = 2;
+    smem += copies;
+  }
   static bool attr = false;
   if (!attr) {
     T2S2_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
