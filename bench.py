@@ -48,13 +48,15 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle CPU work for the cpu_baseline sample")
     ap.add_argument("--workload", default="steady",
-                    choices=["steady", "batched", "cn", "warm", "contract", "spacetime", "stability"],
+                    choices=["steady", "batched", "cn", "warm", "contract", "spacetime", "stability", "round"],
                     help="steady: d=6 n=32 solve (headline); batched: 256 d=5 instances; "
                          "cn: Crank-Nicolson steps at d=7 n=64; warm: learned warm start "
                          "(--instances training solves); contract: grouped core contractions of "
                          "--instances d=5 problems in one launch; spacetime: d=5 space plus time "
                          "(n=32, n_t=24) solved as one collocation system; stability: the Plain-SC / "
-                         "superconsistent stability map (d=6) through the batched solve")
+                         "superconsistent stability map (d=6) through the batched solve; round: TT rounding of the "
+                         "Crank-Nicolson right-hand side (d=7, n=64, rank 80 -> 40) and of the 256 batched "
+                         "instances after an apply (rank 32 -> 16), against HBM and the FP64 ALU")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--holdout", type=int, default=1000, help="held-out problems of --workload warm")
     ap.add_argument("--warm-rank", type=int, default=1, help="TT rank of the warm-start network's output")
@@ -716,6 +718,128 @@ def run_contract(args, T, P, W, torch):
     return 0
 
 
+def round_counts(m, r_in, r_out):
+    """Algorithmic cost of one TT rounding (Methods, TT rounding: right-to-left
+    QR orthogonalisation, then left-to-right truncated SVDs), counted for
+    Householder QR with the factor Q formed (4 M N^2 - 4 N^3 / 3 for an M x N
+    unfolding), an N x N SVD with vectors (12 N^3), and the products that
+    carry R, resp. S V^T, into the neighbouring core.  Bytes: the
+    orthogonalisation reads and writes every core, the truncation reads it
+    again and writes the rounded core: 8 (3 N_in + N_out)."""
+    d = len(m)
+    fl = 0.0
+    r = list(r_in)
+    for k in range(d - 1, 0, -1):            # right-to-left QR of core k^T
+        M, N = m[k] * r[k + 1], r[k]
+        fl += 4 * M * N * N - 4 * N ** 3 / 3
+        fl += 2 * r[k - 1] * m[k - 1] * r[k] * r[k]
+    ro = list(r_out)
+    for k in range(d - 1):                   # left-to-right truncated SVD
+        M, N, keep = ro[k] * m[k], r[k + 1], ro[k + 1]
+        fl += 4 * M * N * N - 4 * N ** 3 / 3 + 12 * N ** 3 + 2 * M * N * keep
+        fl += 2 * keep * N * m[k + 1] * r[k + 2]
+    n_in = sum(r_in[k] * m[k] * r_in[k + 1] for k in range(d))
+    n_out = sum(r_out[k] * m[k] * r_out[k + 1] for k in range(d))
+    return fl, 8.0 * (3 * n_in + n_out), n_in
+
+
+def run_round(args, T, P, W, torch):
+    """TT rounding alone, on the two working sets larger than one core's worth
+    of L2 reuse: (a) the Crank-Nicolson right-hand side (M - dt/2 A) u of a
+    rank-40 state at d=7, n=64 (rank 80, ~23 MB), rounded to tol 1e-8 and
+    rank 40; (b) the 256 batched d=5 instances after an apply of rank-16
+    trains (rank 32, ~0.3 GB together), each rounded to tol 1e-8 and rank 16,
+    one after another on one stream.  Each timed rounding starts from a fresh
+    copy of its input with L2 flushed (256 MB write), both untimed; CUDA
+    events on the launching stream bracket the rounding calls."""
+    import numpy as np
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    pk, src = peaks()
+
+    def copy_into(dst, src_tt):
+        for a, b in zip(dst.buffers, src_tt.buffers):
+            a.copy_(b)
+        dst.r = list(src_tt.r)
+
+    def timed(pairs):
+        """pairs: [(op, y, z, rmax)]: z <- y, flush, then round every z; returns ms."""
+        for op, y, z, _ in pairs:
+            copy_into(z, y)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for op, y, z, rmax in pairs:
+            T.t2s2_round(op, z, 1e-8, rmax)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def measure(name, pairs, workload):
+        for _ in range(args.warmup):
+            timed(pairs)
+        ms = [timed(pairs) for _ in range(args.steps)]
+        ms_mean = sum(ms) / len(ms)
+        fl = by = n_in = 0.0
+        for op, y, z, _ in pairs:
+            f, b, n = round_counts(z.m, y.r, z.r)
+            fl, by, n_in = fl + f, by + b, n_in + n
+        gbs = by / (ms_mean * 1e-3) / 1e9
+        gfl = fl / (ms_mean * 1e-3) / 1e9
+        t_hbm = by / (pk["hbm_gbs"] * 1e9) * 1e3
+        t_alu = fl / (FP64_ALU_PEAK_GFLOPS * 1e9) * 1e3
+        return {"workload": workload, "roundings": len(pairs), "ms": ms_mean, "ms_runs": ms,
+                "input_bytes": 8 * n_in, "algorithmic_bytes": by, "fp64_flops": fl,
+                "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"], "fp64_gflops": gfl,
+                "fp64_frac": gfl / FP64_ALU_PEAK_GFLOPS,
+                "roofline_ms": max(t_hbm, t_alu), "bound": "fp64 alu" if t_alu > t_hbm else "hbm",
+                "roofline_frac": max(t_hbm, t_alu) / ms_mean,
+                "ranks_in": list(pairs[0][1].r), "ranks_out": list(pairs[0][2].r)}
+
+    out = {}
+    # (a) the Crank-Nicolson right-hand side of a rank-40 state
+    p2 = W.config2()
+    op2 = P.build_operator(p2)
+    m2 = [n - 2 for n in p2.n]
+    r40 = [1] + [p2.rmax] * (p2.d - 1) + [1]
+    u = T.TT.from_cores(W.random_tt(p2.d, m2[0], r40, seed=911), rcap=p2.rmax)
+    y2 = T.TT.empty(m2, 2 * p2.rmax)
+    T.t2s2_apply(op2, u, y2, 1.0, -0.5 * p2.dt)
+    z2 = T.TT.empty(m2, 2 * p2.rmax)
+    out["cn_rhs"] = measure("cn_rhs", [(op2, y2, z2, p2.rmax)],
+                            f"(M - dt/2 A) u, d={p2.d} n={p2.n[0]}, u random rank {p2.rmax}: rank "
+                            f"{2 * p2.rmax} -> {p2.rmax}")
+    del op2, u, y2, z2
+    # (b) the 256 batched instances after an apply
+    ops, pairs = [], []
+    for i in range(args.instances):
+        p = W.config3(i)
+        m = [n - 2 for n in p.n]
+        op = P.build_operator(p)
+        r = [1] + [16] * (p.d - 1) + [1]
+        x = T.TT.from_cores(W.random_tt(p.d, m[0], r, seed=700 + i))
+        y = T.TT.empty(m, 32)
+        T.t2s2_apply(op, x, y, 0.0, 1.0)
+        z = T.TT.empty(m, 32)
+        ops.append(op)
+        pairs.append((op, y, z, 16))
+    if pairs:
+        out["batched"] = measure("batched", pairs, f"{args.instances} instances d=5 n in {{16,24,32,48}}, "
+                                                   "A x of random rank-16 x: rank 32 -> 16, one stream")
+    a = out["cn_rhs"]
+    line = {"metric": "TT roundings/sec (Crank-Nicolson right-hand side, d=7, n=64, rank 80 -> 40)",
+            "value": 1e3 / a["ms"], "unit": "roundings/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": a["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": a["workload"], "l2": "flushed before every timed rounding (256 MB write)"},
+            "rounding": out, "hbm_peak_gbs": pk["hbm_gbs"], "peak_source": src,
+            "fp64_peak_gflops": FP64_ALU_PEAK_GFLOPS,
+            "fp64_peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 1.965 GHz"}
+    print(json.dumps(line))
+    return 0
+
+
 def measure_contraction(T, P, W, torch, instances=256, reps=10):
     """Grouped core contractions (t2s2_apply_batched): every core of `instances`
     d=5 problems (n in {16,24,32,48}, TT ranks 16) in one persistent launch.
@@ -809,7 +933,7 @@ def main():
         from paper_2506_04732_gb300 import problem as P
         import workloads as W
         fn = {"batched": run_batched, "cn": run_cn, "warm": run_warm, "contract": run_contract,
-              "spacetime": run_spacetime, "stability": run_stability}[args.workload]
+              "spacetime": run_spacetime, "stability": run_stability, "round": run_round}[args.workload]
         return fn(args, T, P, W, torch)
     ws, rank, local = dist_env()
     import torch

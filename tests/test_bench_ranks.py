@@ -124,3 +124,23 @@ def test_kernel_names_map_to_trace_families():
     assert kf("t2s2::(anonymous namespace)::k_sumsq(double const*, unsigned long, double*)") == "elementwise"
     assert kf("void at::native::vectorized_elementwise_kernel<4, at::native::FillFunctor<unsigned char>>") == "other"
     assert set(bench.ALU_FAMILIES) <= set(bench.FAMILIES)
+
+
+def test_round_counts_of_a_matrix_and_their_scaling():
+    """d = 2 is one matrix: one QR of the m1 x r unfolding (Q formed), R
+    carried into core 0, then one SVD step of the m0 x r unfolding; bytes
+    read and written per pass.  Doubling every rank and mode size multiplies
+    the FLOPs by 16 (m r^3 terms) and the bytes by 8 (r m r cores; 4 for the
+    two end cores)."""
+    m0, m1, r, keep = 10, 12, 6, 3
+    fl, by, n_in = bench.round_counts([m0, m1], [1, r, 1], [1, keep, 1])
+    qr = 4 * m1 * r * r - 4 * r ** 3 / 3 + 2 * 1 * m0 * r * r
+    svd = 4 * m0 * r * r - 4 * r ** 3 / 3 + 12 * r ** 3 + 2 * m0 * r * keep + 2 * keep * r * m1 * 1
+    assert fl == pytest.approx(qr + svd)
+    assert n_in == m0 * r + r * m1
+    assert by == 8 * (3 * (m0 * r + r * m1) + (m0 * keep + keep * m1))
+    m, rin, rout = [20] * 5, [1, 8, 8, 8, 8, 1], [1, 4, 4, 4, 4, 1]
+    f1, b1, _ = bench.round_counts(m, rin, rout)
+    f2, b2, _ = bench.round_counts([2 * v for v in m], [1] + [16] * 4 + [1], [1] + [8] * 4 + [1])
+    assert 12 < f2 / f1 < 16.5
+    assert 7 < b2 / b1 < 8.01
