@@ -166,11 +166,11 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
     for (int e = t; e < rows * cols; e += blockDim.x) Wf[e] = (float)W[e];
     for (int e = t; e < cols * cols; e += blockDim.x) Vf[e] = (e % cols == e / cols) ? 1.f : 0.f;
     const float negl32 = (float)(1e-14 * fro2);
-    // the sweeps stop when no rotation exceeds |gamma| = 1e-6 sqrt(alpha beta);
-    // for the large blocks also when the largest one is below ~3e-5 and no
-    // longer shrinks tenfold a sweep: binary32 dot products of long columns
-    // carry ~1e-7 relative noise per term, so the last rotations can stall
-    // at the noise, and the binary64 sweeps below converge from there
+    // the sweeps stop when no rotation exceeds |gamma| = 1e-6 sqrt(alpha beta),
+    // or when the largest one is below ~3e-5 and no longer shrinks tenfold a
+    // sweep: binary32 dot products carry ~1e-7 relative noise per term, so the
+    // last rotations can stall at the noise (without this stop such blocks
+    // ran all 30 sweeps), and the binary64 sweeps below converge from there
     float prev_top = 1.f;
     for (int sw = 0; sw < 30; ++sw) {
       if (t == 0) {
@@ -216,14 +216,14 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
             if (lane == 0) {
               rotated = 1;
               // non-negative binary32 values order like their bit patterns
-              if (inplace) atomicMax(&top32, __float_as_uint(gamma * gamma / (alpha * beta)));
+              atomicMax(&top32, __float_as_uint(gamma * gamma / (alpha * beta)));
             }
           }
         }
         __syncthreads();
       }
       const float top = __uint_as_float(top32);
-      if (!rotated || (inplace && top < 1e-9f && top > 0.01f * prev_top)) break;
+      if (!rotated || (top < 1e-9f && top > 0.01f * prev_top)) break;
       prev_top = top;
       __syncthreads();
     }
@@ -370,12 +370,14 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
             va[i] = cs * x - sn * y;
             vb[i] = sn * x + cs * y;
           }
-          // a sweep whose rotations were all below 1e-6 (relative) leaves
-          // off-diagonals of ~1e-12 (quadratic convergence): it is the last.
-          // Singular values then carry ~1e-24 relative error, and the left
-          // vectors are orthogonal to ~1e-12 (the sweeps that consume them
-          // re-orthogonalise with CholeskyQR3 anyway)
-          if (lane == 0 && gamma * gamma > 1e-12 * alpha * beta) rotated = 1;
+          // a sweep whose rotations were all below 1e-4 (relative) leaves
+          // off-diagonals of ~1e-8 (quadratic convergence): it is the last.
+          // The column norms then carry ~1e-16 relative error as singular
+          // values, W = U diag(s) V^T holds with V orthogonal to roundoff,
+          // and the left vectors are orthogonal to ~1e-8 (the sweeps that
+          // consume them re-orthogonalise with CholeskyQR anyway).  After
+          // the binary32 pre-rotation this is the first binary64 sweep.
+          if (lane == 0 && gamma * gamma > 1e-8 * alpha * beta) rotated = 1;
         }
       }
       __syncthreads();
