@@ -17,6 +17,9 @@ namespace t2s2 {
 namespace {
 
 constexpr int kThreads = 512;
+// the sweeps' column pairs: kPairLanes lanes each, kPairsPerWarp per warp
+constexpr int kPairLanes = 8;
+constexpr int kPairsPerWarp = 32 / kPairLanes;
 constexpr size_t kJacobiSepSmem = 200 * 1024;  // pre-rotation with separate product buffers
 constexpr size_t kJacobiMaxSmem = 224 * 1024;  // pre-rotation with in-place products
 
@@ -142,6 +145,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
   // stirs roundoff, and the sweeps would never settle
   const double negligible = 1e-32 * fro2;
   const int warp = t / 32, lane = t % 32, nwarps = blockDim.x / 32;
+  const int grp = lane / kPairLanes, gl = lane % kPairLanes;  // pair group, lane in it
   const int npair = (cols + 1) / 2;  // round-robin with a dummy column when cols is odd
   const int ncol = 2 * npair;
   // Binary32 pre-rotation.  A binary64 instruction costs a warp ~64 issue
@@ -179,41 +183,46 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
       }
       __syncthreads();
       for (int round = 0; round < ncol - 1; ++round) {
-        for (int pr = warp; pr < npair; pr += nwarps) {
+        for (int pr0 = warp * kPairsPerWarp; pr0 < npair; pr0 += nwarps * kPairsPerWarp) {
+          // kPairsPerWarp pairs per warp, kPairLanes lanes each (the shuffle
+          // trip counts stay warp-uniform: idle groups reduce zeros)
+          const int pr = pr0 + grp;
           int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (ncol - 1);
           int b = 1 + (ncol - 2 - pr + round) % (ncol - 1);
-          if (a >= cols || b >= cols) continue;
+          const bool act = pr < npair && a < cols && b < cols;
           if (a > b) { int tmp = a; a = b; b = tmp; }
-          float* wa = Wf + a * rows;
-          float* wb = Wf + b * rows;
+          float* wa = Wf + (act ? a : 0) * rows;
+          float* wb = Wf + (act ? b : 0) * rows;
           float alpha = 0.f, beta = 0.f, gamma = 0.f;
-          for (int i = lane; i < rows; i += 32) {
-            alpha = fmaf(wa[i], wa[i], alpha);
-            beta = fmaf(wb[i], wb[i], beta);
-            gamma = fmaf(wa[i], wb[i], gamma);
+          if (act) {
+            for (int i = gl; i < rows; i += kPairLanes) {
+              alpha = fmaf(wa[i], wa[i], alpha);
+              beta = fmaf(wb[i], wb[i], beta);
+              gamma = fmaf(wa[i], wb[i], gamma);
+            }
           }
-          for (int o = 16; o > 0; o >>= 1) {
+          for (int o = kPairLanes / 2; o > 0; o >>= 1) {
             alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
             beta += __shfl_xor_sync(0xffffffffu, beta, o);
             gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
           }
-          if (gamma != 0.f && gamma * gamma > 1e-12f * alpha * beta && alpha > negl32 && beta > negl32) {
+          if (act && gamma != 0.f && gamma * gamma > 1e-12f * alpha * beta && alpha > negl32 && beta > negl32) {
             const float diff = beta - alpha, g2 = 2.f * gamma;
             const float tf = (diff >= 0.f ? g2 : -g2) / (fabsf(diff) + sqrtf(fmaf(diff, diff, g2 * g2)));
             const float cs = rsqrtf(fmaf(tf, tf, 1.f)), sn = cs * tf;
-            for (int i = lane; i < rows; i += 32) {
+            for (int i = gl; i < rows; i += kPairLanes) {
               const float x = wa[i], y = wb[i];
               wa[i] = cs * x - sn * y;
               wb[i] = sn * x + cs * y;
             }
             float* va = Vf + a * cols;
             float* vb = Vf + b * cols;
-            for (int i = lane; i < cols; i += 32) {
+            for (int i = gl; i < cols; i += kPairLanes) {
               const float x = va[i], y = vb[i];
               va[i] = cs * x - sn * y;
               vb[i] = sn * x + cs * y;
             }
-            if (lane == 0) {
+            if (gl == 0) {
               rotated = 1;
               // non-negative binary32 values order like their bit patterns
               atomicMax(&top32, __float_as_uint(gamma * gamma / (alpha * beta)));
@@ -311,26 +320,31 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
     if (t == 0) rotated = 0;
     __syncthreads();
     for (int round = 0; round < ncol - 1; ++round) {
-      for (int pr = warp; pr < npair; pr += nwarps) {
-        // round-robin pairing: position 0 fixed, others rotate
+      for (int pr0 = warp * kPairsPerWarp; pr0 < npair; pr0 += nwarps * kPairsPerWarp) {
+        // round-robin pairing: position 0 fixed, others rotate; kPairsPerWarp
+        // pairs per warp share each binary64 instruction (a binary64 warp
+        // instruction costs the same ~64 cycles with 8 or 32 lanes busy)
+        const int pr = pr0 + grp;
         int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (ncol - 1);
         int b = 1 + (ncol - 2 - pr + round) % (ncol - 1);
-        if (a >= cols || b >= cols) continue;
+        const bool act = pr < npair && a < cols && b < cols;
         if (a > b) { int tmp = a; a = b; b = tmp; }
-        double* wa = W + a * rows;
-        double* wb = W + b * rows;
+        double* wa = W + (act ? a : 0) * rows;
+        double* wb = W + (act ? b : 0) * rows;
         double alpha = 0, beta = 0, gamma = 0;
-        for (int i = lane; i < rows; i += 32) {
-          alpha += wa[i] * wa[i];
-          beta += wb[i] * wb[i];
-          gamma += wa[i] * wb[i];
+        if (act) {
+          for (int i = gl; i < rows; i += kPairLanes) {
+            alpha += wa[i] * wa[i];
+            beta += wb[i] * wb[i];
+            gamma += wa[i] * wb[i];
+          }
         }
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = kPairLanes / 2; o > 0; o >>= 1) {
           alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
           beta += __shfl_xor_sync(0xffffffffu, beta, o);
           gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
         }
-        if (gamma != 0.0 && gamma * gamma > 1e-30 * alpha * beta && alpha > negligible && beta > negligible) {
+        if (act && gamma != 0.0 && gamma * gamma > 1e-30 * alpha * beta && alpha > negligible && beta > negligible) {
           // Rotation angle in binary32 (only its orthogonality must be exact):
           // t = 2 gamma sign(beta - alpha) / (|beta - alpha| + sqrt((beta - alpha)^2 + 4 gamma^2)).
           // Near convergence a binary32 angle still cuts gamma by ~1e-7 per sweep.
@@ -358,14 +372,14 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
           f = fma(-0.5, n2, 1.5);
           cs *= f;
           sn *= f;
-          for (int i = lane; i < rows; i += 32) {
+          for (int i = gl; i < rows; i += kPairLanes) {
             double x = wa[i], y = wb[i];
             wa[i] = cs * x - sn * y;
             wb[i] = sn * x + cs * y;
           }
           double* va = Vs + a * cols;
           double* vb = Vs + b * cols;
-          for (int i = lane; i < cols; i += 32) {
+          for (int i = gl; i < cols; i += kPairLanes) {
             double x = va[i], y = vb[i];
             va[i] = cs * x - sn * y;
             vb[i] = sn * x + cs * y;
@@ -377,7 +391,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
           // and the left vectors are orthogonal to ~1e-8 (the sweeps that
           // consume them re-orthogonalise with CholeskyQR anyway).  After
           // the binary32 pre-rotation this is the first binary64 sweep.
-          if (lane == 0 && gamma * gamma > 1e-8 * alpha * beta) rotated = 1;
+          if (gl == 0 && gamma * gamma > 1e-8 * alpha * beta) rotated = 1;
         }
       }
       __syncthreads();
