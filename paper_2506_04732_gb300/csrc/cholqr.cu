@@ -16,7 +16,10 @@
 //                 vectors; its own rows of Lacc <- Lacc L D^{1/2}
 //
 // with the shift of the first pass as in Fukaya et al.'s shifted
-// CholeskyQR3.  The stopping test is the CholeskyQR2 argument: a Gram close
+// CholeskyQR3, and the same shift in the second pass when it is not the last
+// (kCqrShiftedPasses, small.h: a plain second pass would zero the pivots of
+// directions that the first shift pushed to roundoff in column order, and
+// lose more of W than those directions hold).  The stopping test is the CholeskyQR2 argument: a Gram close
 // to the identity means a condition number close to 1, for which one more
 // CholeskyQR pass yields Q orthonormal to working precision; blocks with one
 // column need a single unshifted pass.  "Vectors" are the rows of a row-major

@@ -1,6 +1,7 @@
 // FP64 tensor-train arithmetic on the device.
 //
-// Orthogonalisation uses shifted CholeskyQR3 (Fukaya et al. 2020): three
+// Orthogonalisation uses shifted CholeskyQR (Fukaya et al. 2020, with a
+// second shifted pass for nearly rank-deficient blocks): two to four
 // Gram / Cholesky / triangular-multiply passes whose heavy parts are GEMMs
 // spread over all SMs, instead of a Householder QR that would serialise on
 // one SM's FP64 pipe.  Truncation takes a one-sided Jacobi SVD of the small
