@@ -12,10 +12,9 @@ shows, with the oracle's residual of the original collocation system, that
   solution (oracle residual <= 5e-9);
 * its best rank-16 approximation in the SVD sense (the oracle's rounding
   with cap 16) leaves a residual above 1e-8 and above ten times the tight
-  solve's, so the cap of 16, not the solver, stops these instances;
+  solve's: rank 16 alone cannot reach the tolerance, the solver is not what
+  falls short;
 * the GPU solver reaches 1e-8 once its cap is raised to 40.
-
-So for these instances the cap of 16 is what decides, not the solver.
 """
 import numpy as np
 import pytest
