@@ -1,7 +1,7 @@
 // Small dense factorisations (c x c, c <= kSmallMax) done by one CTA in
 // shared memory, FP64:
 //  * chol_inv: G + s I = L L^T (Cholesky) and L^{-1}, for CholeskyQR.  The
-//    shift s makes the first pass of shifted CholeskyQR3 (Fukaya, Kannan,
+//    shift s makes the shifted passes of CholeskyQR (Fukaya, Kannan,
 //    Nakatsukasa, Yamamoto, Yanagisawa 2020) succeed for any conditioning.
 //  * jacobi_svd: one-sided Jacobi SVD A = U diag(s) V^T of a p x q matrix
 //    (Hestenes' method, columns orthogonalised by plane rotations in a
@@ -150,9 +150,10 @@ __global__ void __launch_bounds__(kThreads) jacobi_svd_kernel(const double* __re
   const int ncol = 2 * npair;
   // Binary32 pre-rotation.  A binary64 instruction costs a warp ~64 issue
   // cycles on this part (2 DFMA/clk/SM), binary32 one: the sweeps run in
-  // binary32 on a rounded copy until its columns are orthogonal to ~1e-6,
-  // W <- W V32 in binary64, and the binary64 sweeps below (starting from
-  // V = V32) need one or two passes to converge quadratically.  Small
+  // binary32 on a rounded copy until its columns are orthogonal to ~1e-6
+  // (or the binary32 noise stops them), W <- W V32 in binary64, and one
+  // binary64 sweep below (starting from V = V32) converges quadratically
+  // to the stopping test.  Small
   // singular values keep full binary64 relative accuracy: they come from
   // binary64 column norms after the binary64 rotations.
   if (prerotate) {
