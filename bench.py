@@ -191,7 +191,6 @@ ALU_FAMILIES = ("gemm", "apply", "local_solve", "small_factor", "cholqr", "sylve
 # summary it comes from; a family without a current capture is left out.
 KERNEL_DRAM_BYTES = {
     "sylvester": (107008.0, "profiles/sylv_rb1_kernel_steady_d6n32.md"),
-    "cholqr": (104064.0, "profiles/cqr_cluster_kernel_steady_d6n32.md"),
 }
 
 
