@@ -113,6 +113,28 @@ def test_duplicated_rank1_rounds_back_to_rank1():
     assert np.linalg.norm(T.full(y) - 1.5 * T.full(x)) < 1e-12 * np.linalg.norm(T.full(x))
 
 
+def test_rounding_of_a_cancelling_pair_against_dense():
+    """t1 - t1 + 1e-9 t2 + t3 on a grid small enough to hold densely: at
+    tolerance 0 the rounding reproduces the dense tensor to roundoff, and at
+    a tolerance above the 1e-9 part it keeps rank <= r and lands within the
+    error bound of t3 + 1e-9 t2 (the exactly cancelling pair carries
+    nothing)."""
+    d, m, r = 4, 6, 2
+    t1 = W.random_tt(d, m, [1] + [r] * (d - 1) + [1], seed=41)
+    t2 = W.random_tt(d, m, [1] + [r] * (d - 1) + [1], seed=42)
+    t3 = W.random_tt(d, m, [1] + [r] * (d - 1) + [1], seed=43)
+    x = T.add(T.add(T.add(t1, T.scale(t1, -1.0)), T.scale(t2, 1e-9)), t3)
+    x[0] = x[0] / 1e3
+    x[-1] = x[-1] * 1e3
+    dense = T.full(t3) + 1e-9 * T.full(t2)
+    assert np.linalg.norm(T.full(x) - dense) <= 1e-14 * np.linalg.norm(dense)
+    y0 = T.round_tt(x, 0.0)
+    assert np.linalg.norm(T.full(y0) - dense) <= 1e-13 * np.linalg.norm(dense)
+    y = T.round_tt(x, 1e-6)
+    assert max(T.ranks(y)) <= r
+    assert np.linalg.norm(T.full(y) - dense) <= 1e-6 * np.linalg.norm(dense)
+
+
 def test_add_scale_dot_norm_against_dense():
     x = W.random_tt(4, (3, 4, 5, 3), [1, 2, 3, 2, 1], seed=1)
     y = W.random_tt(4, (3, 4, 5, 3), [1, 3, 2, 4, 1], seed=2)
